@@ -1,0 +1,227 @@
+"""FP64 CPU oracle of the paper's Algorithm 1 -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference legs of
+``bench.py`` may import this package. The product path (``paper_2203_05027_b300``) never imports
+it and shares no code with it. The arithmetic lives in ``mfs_oracle.c`` (plain C, FP64, the
+literal Algorithm 1 with o-length y and gamma); this module only builds it with gcc and
+marshals numpy arrays through ctypes.
+
+Reference: arXiv 2203.05027, Sec. IV (UV decomposition, eq. UU/VV, Example 1), the Block 1 /
+Block 2 / dual updates and Algorithm 1; residual forms after the stopping rules of Sec. V.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "mfs_oracle.c")
+LIB = os.path.join(HERE, "libmfs_oracle.so")
+
+CONE_NONNEG = 0
+CONE_SOC = 1
+
+RESID_FIELDS = (
+    "r_prim", "r_dual", "r_cone", "r_gap", "kkt", "pobj", "dobj",
+    "nrm_res_p", "nrm_b", "nrm_xdist", "nrm_x", "nrm_sdist", "nrm_c", "nrm_atl_c",
+    "inf_res_p", "inf_ax", "inf_b", "inf_atl_c", "inf_atl", "inf_c",
+)
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile mfs_oracle.c into libmfs_oracle.so (IEEE FP64: no FMA contraction, no fast-math)."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + ".tmp"
+        subprocess.check_call(
+            ["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+             "-std=c11", "-Wall", "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(LIB)
+    P = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    dp = ctypes.POINTER(ctypes.c_double)
+    lp = ctypes.POINTER(ctypes.c_int64)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    lib.orc_create.argtypes = [i64, i64, i64, lp, lp, dp, dp, dp, i64, ip, lp, ctypes.c_double,
+                               ctypes.POINTER(P)]
+    lib.orc_create.restype = ctypes.c_int
+    lib.orc_destroy.argtypes = [P]
+    lib.orc_nnz.argtypes = [P]
+    lib.orc_nnz.restype = i64
+    lib.orc_get_uv.argtypes = [P, lp, lp, dp, dp, dp]
+    lib.orc_set_state.argtypes = [P, dp, dp, dp, dp, dp, dp]
+    lib.orc_get_state.argtypes = [P, dp, dp, dp, dp, dp, dp]
+    lib.orc_set_mu.argtypes = [P, ctypes.c_double]
+    lib.orc_proj_lorentz.argtypes = [i64, dp, dp]
+    lib.orc_proj_K.argtypes = [P, dp, dp]
+    for name in ("orc_step_x", "orc_step_y", "orc_step_z", "orc_step_lambda", "orc_step_gamma",
+                 "orc_step_delta"):
+        getattr(lib, name).argtypes = [P]
+    lib.orc_iterate.argtypes = [P, i64]
+    lib.orc_consistent_y_gamma.argtypes = [P, dp, dp, dp, dp]
+    lib.orc_matvec.argtypes = [P, dp, dp]
+    lib.orc_rmatvec.argtypes = [P, dp, dp]
+    lib.orc_residuals.argtypes = [P, dp]
+    _lib = lib
+    return lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+def _lp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def proj_lorentz(w) -> np.ndarray:
+    """Projection onto one Lorentz cone (eq. proj) -- computed by the C oracle."""
+    lib = _load()
+    w = _f64(w).copy()
+    out = np.empty_like(w)
+    lib.orc_proj_lorentz(len(w), _dp(w), _dp(out))
+    return out
+
+
+@dataclass
+class State:
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    lam: np.ndarray
+    gam: np.ndarray
+    delta: np.ndarray
+
+
+class Oracle:
+    """One problem (A, b, c, K) and the literal iterate of Algorithm 1 (FP64, single thread)."""
+
+    def __init__(self, m, n, row, col, val, b, c, cones, mu=1.0):
+        lib = _load()
+        row = np.ascontiguousarray(row, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int64)
+        val = _f64(val)
+        b = _f64(b)
+        c = _f64(c)
+        kinds = np.ascontiguousarray([k for k, _ in cones], dtype=np.int32)
+        sizes = np.ascontiguousarray([s for _, s in cones], dtype=np.int64)
+        h = ctypes.c_void_p()
+        st = lib.orc_create(int(m), int(n), len(row), _lp(row), _lp(col), _dp(val), _dp(b), _dp(c),
+                            len(kinds), kinds.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                            _lp(sizes), float(mu), ctypes.byref(h))
+        if st != 0:
+            raise ValueError(f"orc_create failed with status {st}")
+        self._h = h
+        self._lib = lib
+        self.m, self.n = int(m), int(n)
+        self.o = int(lib.orc_nnz(h))
+        self.cones = list(cones)
+        self.mu = float(mu)
+        self.b = b.copy()
+        self.c = c.copy()
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.orc_destroy(h)
+            self._h = None
+
+    # --- UV decomposition and factors (Sec. IV; Algorithm 1 steps 1-3) ---
+    def uv(self):
+        ik = np.empty(self.o, np.int64)
+        jk = np.empty(self.o, np.int64)
+        ak = np.empty(self.o, np.float64)
+        FU = np.empty(self.m, np.float64)
+        FV = np.empty(self.n, np.float64)
+        self._lib.orc_get_uv(self._h, _lp(ik), _lp(jk), _dp(ak), _dp(FU), _dp(FV))
+        return ik, jk, ak, FU, FV
+
+    # --- iterate ---
+    def set_state(self, x=None, y=None, z=None, lam=None, gam=None, delta=None):
+        args = [_f64(v) for v in (x, y, z, lam, gam, delta)]
+        self._lib.orc_set_state(self._h, *[_dp(a) for a in args])
+
+    def state(self) -> State:
+        x, z, d = (np.empty(self.n) for _ in range(3))
+        lam = np.empty(self.m)
+        y, g = np.empty(self.o), np.empty(self.o)
+        self._lib.orc_get_state(self._h, _dp(x), _dp(y), _dp(z), _dp(lam), _dp(g), _dp(d))
+        return State(x, y, z, lam, g, d)
+
+    def set_mu(self, mu):
+        self.mu = float(mu)
+        self._lib.orc_set_mu(self._h, self.mu)
+
+    def step(self, name: str):
+        getattr(self._lib, "orc_step_" + name)(self._h)
+
+    def iterate(self, k: int):
+        self._lib.orc_iterate(self._h, int(k))
+
+    def proj_K(self, w) -> np.ndarray:
+        w = _f64(w).copy()
+        out = np.empty_like(w)
+        self._lib.orc_proj_K(self._h, _dp(w), _dp(out))
+        return out
+
+    def consistent_y_gamma(self, x, lam):
+        x, lam = _f64(x), _f64(lam)
+        y, g = np.empty(self.o), np.empty(self.o)
+        self._lib.orc_consistent_y_gamma(self._h, _dp(x), _dp(lam), _dp(y), _dp(g))
+        return y, g
+
+    def warm_start(self, x, lam, z=None, delta=None):
+        """Literal state for a warm start from (x, lambda): y, gamma as in orc_consistent_y_gamma;
+        z defaults to proj_K(x) and delta to proj_K(c + A^T lambda)."""
+        x, lam = _f64(x), _f64(lam)
+        y, g = self.consistent_y_gamma(x, lam)
+        if z is None:
+            z = self.proj_K(x)
+        if delta is None:
+            delta = self.proj_K(self.rmatvec(lam) + self.c)
+        self.set_state(x=x, y=y, z=z, lam=lam, gam=g, delta=delta)
+
+    def matvec(self, x):
+        x = _f64(x)
+        out = np.empty(self.m)
+        self._lib.orc_matvec(self._h, _dp(x), _dp(out))
+        return out
+
+    def rmatvec(self, lam):
+        lam = _f64(lam)
+        out = np.empty(self.n)
+        self._lib.orc_rmatvec(self._h, _dp(lam), _dp(out))
+        return out
+
+    def residuals(self) -> dict:
+        out = np.empty(len(RESID_FIELDS))
+        self._lib.orc_residuals(self._h, _dp(out))
+        return dict(zip(RESID_FIELDS, out.tolist()))
+
+
+def make_oracle(prob, mu=1.0, dtype=np.float64) -> Oracle:
+    """Oracle for a problem dict from ``paper_2203_05027_b300.instances`` (keys m, n, row, col,
+    val, b, c, cones). With dtype=float32 the data are rounded to FP32 first and promoted back,
+    so that only the arithmetic of an FP32 sweep differs from the oracle."""
+    cast = (lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)) if dtype == np.float32 \
+        else (lambda a: np.asarray(a, dtype=np.float64))
+    return Oracle(prob["m"], prob["n"], prob["row"], prob["col"], cast(prob["val"]), cast(prob["b"]),
+                  cast(prob["c"]), prob["cones"], mu=mu)

@@ -1,0 +1,297 @@
+"""Benchmark of the matrix-free conic solver's hot path on one B300.
+
+Workload: the large sparse LP (m = 1,000,000 rows, n = 2,500,000 columns, power-law column degrees
+on {2..200} with mean 8, about 20M nonzeros, N(0,1) values, K = R^n_+), FP32 sweep with FP64
+residual reductions. One step = one check interval of the solve loop: 25 iterations (each a
+column-order and a row-order sweep over all nonzeros, with the cone projection and the dual
+updates fused in) followed by one FP64 residual evaluation read back to the host.
+
+Metric: A-nonzero updates per second = o x iterations / second (each iteration updates every
+nonzero's contribution in both sweeps; counted once). Also reported: the HBM roofline of the
+dominant sweep kernel, time to 1e-6 relative KKT residual where reached, an end-to-end number
+through the C ABI from host arrays, and the FP64 CPU oracle timed on this host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ITERS_PER_STEP = 25
+METRIC = "A-nonzero updates/s (o x iterations / s)"
+UNIT = "updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mfs", choices=["mfs", "reference"])
+    ap.add_argument("--workload", default="large_lp", choices=["large_lp", "socp"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tts-iters", type=int, default=0,
+                    help="also solve to 1e-6 KKT (cold and warm) with at most this many iterations")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_problem(name, seed):
+    from paper_2203_05027_b300 import instances as I
+    if name == "large_lp":
+        return I.large_lp(seed)
+    return I.socp(seed)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_roofline(s, info, peak, peak_kind, m, n, o):
+    """Time each sweep kernel on the solver's stream with CUDA events (library hook) and relate
+    its algorithmic bytes to the measured HBM copy bandwidth."""
+    t = s.time_kernels(50)
+    col_bytes = 8 * o + 32 * n + 4 * m
+    row_bytes = 8 * o + 4 * n + 20 * m
+    col = {"kernel": "k_col_sweep", "ms": t["col_ms"], "bytes": col_bytes}
+    row = {"kernel": "k_row_sweep", "ms": t["row_ms"], "bytes": row_bytes}
+    dom = col if col["ms"] >= row["ms"] else row
+    achieved = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
+    it_gbs = info["bytes_per_iter"] / (t["iter_ms"] * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tr = json.load(f)
+        traffic = tr.get(dom["kernel"])
+    return {"bound": "hbm", "kernel": dom["kernel"], "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+            "traffic": traffic, "algorithmic_bytes": dom["bytes"],
+            "launch_ms": round(dom["ms"], 5), "col_ms": round(t["col_ms"], 5), "row_ms": round(t["row_ms"], 5),
+            "iteration_ms": round(t["iter_ms"], 5), "iteration_gbs": round(it_gbs, 1)}
+
+
+def cpu_baseline(prob, iters=3):
+    """The FP64 CPU oracle (literal Algorithm 1, single thread) on the same instance: a bounded
+    sample of `iters` iterations."""
+    import oracle
+    orc = oracle.make_oracle(prob)
+    t0 = time.perf_counter()
+    orc.iterate(iters)
+    dt = time.perf_counter() - t0
+    return {"value": orc.o * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{iters} literal FP64 iterations of the oracle on the full instance "
+                      f"({dt:.2f} s, set-up not timed)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    prob = make_problem(args.workload, 0)
+    import oracle
+    orc = oracle.make_oracle(prob)
+    for _ in range(max(args.warmup, 0)):
+        orc.iterate(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.iterate(1)
+    dt = time.perf_counter() - t0
+    value = orc.o * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "m": prob["m"], "n": prob["n"],
+                                              "o": orc.o, "step": "1 literal FP64 iteration of the CPU oracle"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value,
+                             "sample": f"{args.steps} timed oracle iterations after {args.warmup} warm-up"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    from paper_2203_05027_b300 import build, mfs
+    build.build()
+    mfs.load()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    # replicas only: each rank solves its own instance (seeded by rank), no data-path collective
+    prob = make_problem(args.workload, rank)
+    stream = torch.cuda.current_stream()
+    s = mfs.Solver(prob, precision="fp32", polish_iters=0, check_every=ITERS_PER_STEP,
+                   stream=stream.cuda_stream)
+    info = s.info()
+    o, m, n = info["o"], info["m"], info["n"]
+
+    def step():
+        s.iterate(ITERS_PER_STEP)
+        return s.residuals()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            r = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    iters = args.steps * ITERS_PER_STEP
+    value = world * o * iters / (ms * 1e-3)
+
+    peak, peak_kind = load_peaks()
+    roof = kernel_roofline(s, info, peak, peak_kind, m, n, o)
+    launches_per_step = ITERS_PER_STEP * (2 + (1 if info["nbig"] else 0)) + 3 + (1 if info["nbig"] else 0)
+
+    extra = {}
+    if args.tts_iters:
+        s2 = mfs.Solver(prob, precision="fp32", polish_iters=200, check_every=ITERS_PER_STEP,
+                        stream=stream.cuda_stream)
+        t0 = time.perf_counter()
+        st, its = s2.solve(1e-6, args.tts_iters)
+        torch.cuda.synchronize()
+        extra["time_to_1e-6_cold"] = {"status": st, "iterations": its, "seconds": time.perf_counter() - t0,
+                                      "kkt": s2.residuals()["kkt"]}
+        s2.close()
+
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s3 = mfs.Solver(prob, precision="fp32", polish_iters=0, check_every=ITERS_PER_STEP,
+                        stream=stream.cuda_stream)
+        for _ in range(args.steps):
+            s3.iterate(ITERS_PER_STEP)
+            s3.residuals()
+        sol = s3.solution()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        s3.close()
+        h2d = prob["row"].size * (8 + 8 + 8) + 8 * (m + n) + 16 * len(prob["cones"])
+        d2h = 168 * args.steps + 8 * (3 * n + m)
+        e2e = {"value": world * o * iters / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
+               "seconds": round(dt, 3),
+               "scope": "mfs_create from host COO (set-up + upload) + all steps + mfs_get_solution to host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(prob)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 reductions)", "data": "synthetic",
+                "config": {"workload": args.workload, "m": m, "n": n, "o": o,
+                           "iterations_per_step": ITERS_PER_STEP, "precision": "fp32 sweep + fp64 residuals",
+                           "l2": "inputs larger than L2 (A alone is %.0f MB in FP32)" % (16 * o / 1e6),
+                           "parallelism": f"replicas{world}"},
+                "kkt_after_timed_region": r["kkt"],
+                "roofline": roof, "gpu_launches": launches_per_step * args.steps,
+                "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

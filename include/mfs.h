@@ -1,0 +1,182 @@
+/*
+ * mfs.h -- C ABI of the matrix-free first-order conic solver (arXiv 2203.05027) on B300.
+ *
+ * Problem (Sec. II, eq. prob_primal):   minimize c^T x   subject to  A x = b,  x in K,
+ * A in R^{m x n} sparse with o nonzeros, K = K_{n_1} x ... x K_{n_q} a product of cones listed in
+ * order over x's coordinates. Two cone kinds: MFS_CONE_NONNEG (a nonnegative orthant of the given
+ * size, i.e. that many size-1 Lorentz cones; the LP case of Sec. V) and MFS_CONE_SOC (one Lorentz
+ * cone {w : w_1 >= ||w_{2..s}||_2}, Sec. II).
+ *
+ * Method (Sec. IV, Algorithm 1): two-block ADMM on the UV reformulation A = U V^T (eq. UU/VV),
+ * whose x-step (eq. vvt) and y-step (with the matrix inversion lemma) need only the diagonal
+ * factors F_V = (I + V V^T)^{-1}, F_U = (I + U U^T)^{-1}. The library runs the equivalent reduced
+ * form on n- and m-length vectors (after any iteration gamma = -U^T lambda and
+ * y = V^T x + U^T F_U (b - A x)), state (x, z, delta, lambda):
+ *     v      = F_U (b - A x_prev) - lambda/mu
+ *     x      = F_V ( d .* x_prev + A^T v + z + (delta - c)/mu )      d_j = nonzeros of column j
+ *     z      = proj_K(x - delta/mu);   delta += mu (z - x)
+ *     lambda -= mu F_U (b - A x)
+ * Each iteration is one sweep over A's nonzeros in column order and one in row order.
+ *
+ * Conventions for every call:
+ *  - Every function returns an mfs_status; none aborts or exits. After a failure,
+ *    mfs_last_error() gives a one-line reason.
+ *  - Input arrays are read, never retained: the library copies them. Output arrays are owned by
+ *    the caller and must hold the stated number of elements.
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA device memory of the
+ *    device that was current at mfs_create.
+ *  - All work is ordered on the CUDA stream given to mfs_create (NULL = legacy default stream).
+ *    Calls return after their work has finished, except where a comment says otherwise.
+ *  - A solver handle must not be used by two host threads at the same time.
+ */
+#ifndef MFS_H
+#define MFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mfs_solver mfs_solver; /* opaque; owns all of its device memory */
+
+typedef enum {
+    MFS_OK = 0,          /* success; for mfs_solve: the tolerance was reached */
+    MFS_MAX_ITER = 1,    /* mfs_solve: max_iter reached before the tolerance */
+    MFS_ERR_INVALID = 2, /* bad argument: sizes, indices, cone list, non-finite data, NULL */
+    MFS_ERR_CUDA = 3,    /* a CUDA call failed (no device, launch failure, ...) */
+    MFS_ERR_OOM = 4,     /* device or host allocation failed */
+    MFS_ERR_NUMERIC = 5, /* NaN or Inf in the iterate's residuals */
+    MFS_ERR_TIMEOUT = 6  /* a bounded on-device wait gave up; the results of that call are void */
+} mfs_status;
+
+enum { MFS_CONE_NONNEG = 0, MFS_CONE_SOC = 1 };
+
+/* Arithmetic of the sweep. MFS_FP64: FP64 storage and arithmetic everywhere.
+   MFS_FP32_MIXED: FP32 storage of A, b, c and the iterate and FP32 sweep arithmetic; the residual,
+   objective and gap reductions read that data and accumulate in FP64; mfs_solve finishes with
+   FP64 iterations (see mfs_settings.polish_iters). */
+enum { MFS_FP64 = 0, MFS_FP32_MIXED = 1 };
+
+typedef struct {
+    int32_t kind;  /* MFS_CONE_NONNEG or MFS_CONE_SOC */
+    int32_t pad_;  /* ignored */
+    int64_t size;  /* >= 1; the sizes of all cones sum to n */
+} mfs_cone;
+
+typedef struct {
+    double mu;            /* ADMM penalty, > 0 (the paper's fixed mu; default 1) */
+    int32_t check_every;  /* mfs_solve evaluates residuals every this many iterations (default 25) */
+    int32_t precision;    /* MFS_FP64 (default) or MFS_FP32_MIXED */
+    int32_t polish_iters; /* FP32_MIXED: FP64 iterations run by mfs_solve once the FP32 sweep has
+                             met the tolerance, or early if it stalls (default 50) */
+    int32_t reserved;     /* must be 0 */
+} mfs_settings;
+
+/* Residuals at the current (x, lambda); all accumulated in FP64.
+   r_prim = ||Ax-b||_2/(1+||b||_2); r_cone = ||x-P_K x||_2/(1+||x||_2);
+   r_dual = ||s-P_K s||_2/(1+||c||_2) with s = c + A^T lambda (K is self-dual, so this is the
+   distance of the dual slack to the dual cone); r_gap = |c^T x + b^T lambda|/(1+|c^T x|+|b^T lambda|);
+   kkt = max of the four. The raw norms let a caller apply the paper's other stopping rules
+   (Sec. V: infinity-norm residuals, l2 residuals against (1+||b||), (1+||c||)). */
+typedef struct {
+    double r_prim, r_dual, r_cone, r_gap, kkt, pobj, dobj;
+    double nrm_res_p, nrm_b, nrm_xdist, nrm_x, nrm_sdist, nrm_c, nrm_atl_c;
+    double inf_res_p, inf_ax, inf_b, inf_atl_c, inf_atl, inf_c;
+    int64_t iter; /* iterations run since mfs_create or the last mfs_warm_start */
+} mfs_residuals_t;
+
+typedef struct {
+    int64_t m, n, o;            /* o = stored nonzeros after summing duplicates, dropping zeros */
+    int64_t ncones, nsoc, nbig; /* cones; Lorentz cones; Lorentz cones too large to fuse */
+    int64_t col_chunks, row_chunks;
+    int64_t bytes_per_iter;     /* algorithmic HBM bytes of one iteration at the current precision */
+    int32_t precision;          /* precision the iterate is currently held in */
+    int32_t reserved;
+} mfs_info_t;
+
+/* Defaults: mu = 1, check_every = 25, precision = MFS_FP64, polish_iters = 50. */
+void mfs_default_settings(mfs_settings* s);
+
+/*
+ * Build a solver (Algorithm 1, steps 1-3: the UV decomposition and the diagonal factors).
+ * m, n >= 0; nnz >= 0 COO triplets in any order (host): row[t] in [0,m), col[t] in [0,n),
+ * val[t] finite. Duplicates are summed and entries that are (or sum to) exactly zero are dropped.
+ * b (m doubles, host), c (n doubles, host); cones: ncones entries whose sizes sum to n.
+ * settings may be NULL (defaults). cuda_stream: a cudaStream_t or NULL. Limits: m, n, o < 2^31.
+ * The iterate starts at zero (x = z = delta = lambda = 0, which is Algorithm 1 started from
+ * y = gamma = 0). On success *out receives the handle; on failure *out is NULL.
+ */
+mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
+                      const double* val, const double* b, const double* c, int64_t ncones,
+                      const mfs_cone* cones, const mfs_settings* settings, void* cuda_stream,
+                      mfs_solver** out);
+
+/* Release all device and host memory of the handle. NULL is ignored. */
+void mfs_destroy(mfs_solver* s);
+
+/* One-line description of the last failure on this handle ("" if none). NULL gives the last
+   failure of mfs_create on this thread. The string lives until the next call on the handle. */
+const char* mfs_last_error(const mfs_solver* s);
+
+mfs_status mfs_get_info(const mfs_solver* s, mfs_info_t* out);
+
+/* Change mu (Algorithm 1 takes mu fixed; F_U and F_V do not depend on it, so no set-up is
+   repeated). The iterate is kept. mu must be > 0. */
+mfs_status mfs_set_mu(mfs_solver* s, double mu);
+
+/*
+ * Warm start from a primal-dual point (Algorithm 1 accepts any initial point). Host arrays of
+ * doubles: x (n) and lambda (m) are required; z (n) and delta (n) may be NULL, which selects
+ * z = proj_K(x) and delta = proj_K(c + A^T lambda). The iterate becomes the state that
+ * Algorithm 1 reaches after an iteration ending at (x, lambda): gamma = -U^T lambda and
+ * y = V^T x + U^T F_U (b - A x). Resets the iteration counter.
+ */
+mfs_status mfs_warm_start(mfs_solver* s, const double* x, const double* lambda, const double* z,
+                          const double* delta);
+
+/* Same as mfs_warm_start, with device pointers to doubles. */
+mfs_status mfs_warm_start_device(mfs_solver* s, const double* x, const double* lambda,
+                                 const double* z, const double* delta);
+
+/* Run exactly k >= 0 iterations (Algorithm 1, steps 5-10) with no termination test. */
+mfs_status mfs_iterate(mfs_solver* s, int64_t k);
+
+/*
+ * Iterate until the relative KKT residual (mfs_residuals_t.kkt) is <= tol, testing every
+ * check_every iterations, or until max_iter more iterations have run. Returns MFS_OK (tolerance
+ * met) or MFS_MAX_ITER; MFS_ERR_NUMERIC if the residuals become NaN/Inf. iters_out (nullable)
+ * receives the iterations run by this call. In FP32_MIXED mode the iterate switches to FP64
+ * (and stays there) for the final polish_iters iterations, or as soon as the FP32 residual has
+ * not improved over 40 consecutive checks; the tolerance is always judged on FP64 reductions.
+ */
+mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters_out);
+
+/* Residuals of the current iterate (FP64 reductions on the device). */
+mfs_status mfs_residuals(mfs_solver* s, mfs_residuals_t* out);
+
+/* Copy the iterate to host arrays of doubles: x, z, delta (n each), lambda (m). Any may be NULL. */
+mfs_status mfs_get_solution(mfs_solver* s, double* x, double* lambda, double* z, double* delta);
+
+/* Same as mfs_get_solution, into device arrays of doubles. */
+mfs_status mfs_get_solution_device(mfs_solver* s, double* x, double* lambda, double* z,
+                                   double* delta);
+
+/* Switch the iterate between FP32 and FP64 storage (MFS_FP32_MIXED handles only; converting
+   FP32 -> FP64 is exact, FP64 -> FP32 rounds to nearest). */
+mfs_status mfs_set_precision(mfs_solver* s, int32_t precision);
+
+/*
+ * Measurement hook: run k iterations with each kernel launched on its own (no graph) and
+ * bracketed by CUDA events on the solver's stream. out_ms[0] = average milliseconds of one
+ * column-order sweep kernel, out_ms[1] = of one row-order sweep kernel, out_ms[2] = of the
+ * large-cone kernel (0 if none), out_ms[3] = average milliseconds of one whole iteration.
+ * The iterate advances by k iterations.
+ */
+mfs_status mfs_time_kernels(mfs_solver* s, int64_t k, double* out_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MFS_H */

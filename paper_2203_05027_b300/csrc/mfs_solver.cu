@@ -1,0 +1,991 @@
+// mfs_solver.cu -- host side of libmfs: problem set-up (Algorithm 1, steps 1-3), device memory,
+// the iteration driver (CUDA graphs of whole check intervals), residuals, precision switching and
+// the C ABI declared in include/mfs.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mfs.h"
+#include "mfs_kernels.cuh"
+
+using namespace mfs;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+template <typename T>
+struct State {
+    T* x = nullptr;
+    T* z = nullptr;
+    T* del = nullptr;
+    T* lam = nullptr;
+    T* v = nullptr;
+    T* b = nullptr;
+    T* c = nullptr;
+    T* cval = nullptr;
+    T* rval = nullptr;
+    cudaGraphExec_t graph = nullptr;  // check_every iterations
+    int graph_iters = 0;
+};
+
+struct HostProblem {
+    int m = 0, n = 0, o = 0;
+    std::vector<int> col_ptr, row_ptr;
+    std::vector<int> csc_row;     // unpadded, column order
+    std::vector<double> csc_val;
+    std::vector<int> csr_col;     // unpadded, row order
+    std::vector<double> csr_val;
+    std::vector<int> cj0, ckoff, cq_lo, cq_hi;  // column chunks
+    std::vector<int> ri0, rkoff;                // row chunks
+    std::vector<int> soc_start, soc_size, big_list;
+    std::vector<unsigned char> soc_big;
+    int64_t cpad = 0, rpad = 0;  // padded lengths
+};
+
+}  // namespace
+
+struct mfs_solver {
+    int device = 0;
+    cudaStream_t stream = nullptr;   // where the caller's work is ordered
+    cudaStream_t cap = nullptr;      // private stream used only to capture graphs
+    bool own_stream = false;
+    mfs_settings set{};
+    int precision = MFS_FP64;        // precision the iterate is held in now
+    int64_t iter = 0;
+    int m = 0, n = 0, o = 0;
+    int ncones = 0, nsoc = 0, nbig = 0;
+    int ncc = 0, nrc = 0;            // column / row chunks
+    bool has_soc = false;
+    // shared device structure
+    int *col_ptr = nullptr, *cidx = nullptr, *cj0 = nullptr, *ckoff = nullptr, *cq_lo = nullptr, *cq_hi = nullptr;
+    int *row_ptr = nullptr, *ridx = nullptr, *ri0 = nullptr, *rkoff = nullptr;
+    int *soc_start = nullptr, *soc_size = nullptr, *big_list = nullptr;
+    unsigned char* soc_big = nullptr;
+    int* err = nullptr;
+    double *part_row = nullptr, *part_col = nullptr, *part_big = nullptr, *s_buf = nullptr, *status = nullptr;
+    double* h_status = nullptr;      // pinned
+    int* h_err = nullptr;            // pinned
+    State<float> s32;
+    State<double> s64;
+    bool have32 = false, have64 = false;
+    std::vector<void*> allocs;
+    std::string last_error;
+};
+
+namespace {
+
+mfs_status fail(mfs_solver* s, mfs_status st, const std::string& msg) {
+    if (s)
+        s->last_error = msg;
+    else
+        g_create_error = msg;
+    return st;
+}
+
+#define CUDA_TRY(s, call)                                                                          \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail((s), e_ == cudaErrorMemoryAllocation ? MFS_ERR_OOM : MFS_ERR_CUDA,          \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+    } while (0)
+
+template <typename T>
+mfs_status dalloc(mfs_solver* s, T** p, size_t count) {
+    void* q = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess)
+        return fail(s, e == cudaErrorMemoryAllocation ? MFS_ERR_OOM : MFS_ERR_CUDA,
+                    std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    s->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return MFS_OK;
+}
+
+template <typename T>
+mfs_status upload(mfs_solver* s, T** p, const void* host, size_t count) {
+    mfs_status st = dalloc(s, p, count);
+    if (st != MFS_OK) return st;
+    if (count) CUDA_TRY(s, cudaMemcpyAsync(*p, host, count * sizeof(T), cudaMemcpyHostToDevice, s->stream));
+    return MFS_OK;
+}
+
+#define TRY(x)                               \
+    do {                                     \
+        mfs_status st_ = (x);                \
+        if (st_ != MFS_OK) return st_;       \
+    } while (0)
+
+// ---------------------------------------------------------------------------------- host set-up
+
+// Sort COO into column order (rows ascending within a column), sum duplicates, drop zeros;
+// then build the row order. Counting sorts, O(nnz + m + n).
+mfs_status build_orders(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
+                        const double* val, HostProblem& P) {
+    std::vector<int64_t> cnt(std::max(m, n) + 1, 0), by_row(nnz), by_col(nnz);
+    for (int64_t t = 0; t < nnz; ++t) cnt[row[t] + 1]++;
+    for (int64_t i = 0; i < m; ++i) cnt[i + 1] += cnt[i];
+    for (int64_t t = 0; t < nnz; ++t) by_row[cnt[row[t]]++] = t;
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (int64_t t = 0; t < nnz; ++t) cnt[col[t] + 1]++;
+    for (int64_t j = 0; j < n; ++j) cnt[j + 1] += cnt[j];
+    for (int64_t q = 0; q < nnz; ++q) {
+        const int64_t t = by_row[q];
+        by_col[cnt[col[t]]++] = t;
+    }
+    by_row.clear();
+    by_row.shrink_to_fit();
+    P.m = (int)m;
+    P.n = (int)n;
+    P.col_ptr.assign(n + 1, 0);
+    P.csc_row.reserve(nnz);
+    P.csc_val.reserve(nnz);
+    int64_t q = 0;
+    while (q < nnz) {
+        const int64_t t = by_col[q];
+        const int64_t i = row[t], j = col[t];
+        double a = val[t];
+        ++q;
+        while (q < nnz && row[by_col[q]] == i && col[by_col[q]] == j) a += val[by_col[q++]];
+        if (a != 0.0) {
+            P.csc_row.push_back((int)i);
+            P.csc_val.push_back(a);
+            P.col_ptr[j + 1]++;
+        }
+    }
+    for (int64_t j = 0; j < n; ++j) P.col_ptr[j + 1] += P.col_ptr[j];
+    P.o = (int)P.csc_row.size();
+    // row order from column order (stable: columns ascending within a row)
+    P.row_ptr.assign(m + 1, 0);
+    for (int k = 0; k < P.o; ++k) P.row_ptr[P.csc_row[k] + 1]++;
+    for (int64_t i = 0; i < m; ++i) P.row_ptr[i + 1] += P.row_ptr[i];
+    P.csr_col.resize(P.o);
+    P.csr_val.resize(P.o);
+    std::vector<int> fillp(P.row_ptr.begin(), P.row_ptr.end() - (m ? 1 : 0));
+    if (m == 0) fillp.clear();
+    for (int64_t j = 0; j < n; ++j)
+        for (int k = P.col_ptr[j]; k < P.col_ptr[j + 1]; ++k) {
+            const int i = P.csc_row[k];
+            const int dst = fillp[i]++;
+            P.csr_col[dst] = (int)j;
+            P.csr_val[dst] = P.csc_val[k];
+        }
+    return MFS_OK;
+}
+
+// Greedy chunking of segments (columns or rows) in order. A unit is one segment, or a whole
+// small Lorentz cone (columns only). A chunk takes units while it stays within TILE nonzeros and
+// CMAX segments; a single segment longer than TILE forms a chunk of its own.
+void build_chunks(const std::vector<int>& ptr, int nseg, const std::vector<int>* unit_end,
+                  std::vector<int>& c0, std::vector<int>& koff, int64_t& padded) {
+    c0.clear();
+    koff.clear();
+    padded = 0;
+    int start = 0, cur_seg = 0;
+    int64_t cur_nnz = 0;
+    auto close = [&](int at) {
+        c0.push_back(start);
+        koff.push_back((int)padded);
+        const int64_t cn = (int64_t)ptr[at] - ptr[start];
+        padded += (cn + PAD - 1) / PAD * PAD;
+        start = at;
+        cur_seg = 0;
+        cur_nnz = 0;
+    };
+    int j = 0;
+    while (j < nseg) {
+        const int ue = unit_end ? (*unit_end)[j] : j + 1;
+        const int useg = ue - j;
+        const int64_t unnz = (int64_t)ptr[ue] - ptr[j];
+        if (cur_seg > 0 && (cur_nnz + unnz > TILE || cur_seg + useg > CMAX)) close(j);
+        cur_seg += useg;
+        cur_nnz += unnz;
+        j = ue;
+        if (unnz > TILE) close(j);
+    }
+    if (cur_seg > 0) close(nseg);
+    c0.push_back(nseg);
+    koff.push_back((int)padded);
+}
+
+mfs_status setup_host(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
+                      const double* val, int64_t ncones, const mfs_cone* cones, HostProblem& P) {
+    TRY(build_orders(m, n, nnz, row, col, val, P));
+    // Lorentz cones; unit_end[j] = end of the small cone starting at j, or j+1
+    std::vector<int> unit_end(n);
+    for (int64_t j = 0; j < n; ++j) unit_end[j] = (int)j + 1;
+    int64_t off = 0;
+    for (int64_t q = 0; q < ncones; ++q) {
+        const int64_t sz = cones[q].size;
+        if (cones[q].kind == MFS_CONE_SOC) {
+            const int64_t cnnz = (int64_t)P.col_ptr[off + sz] - P.col_ptr[off];
+            const bool big = sz > CMAX || cnnz > TILE;
+            P.soc_start.push_back((int)off);
+            P.soc_size.push_back((int)sz);
+            P.soc_big.push_back(big ? 1 : 0);
+            if (big)
+                P.big_list.push_back((int)P.soc_start.size() - 1);
+            else
+                unit_end[off] = (int)(off + sz);
+        }
+        off += sz;
+    }
+    build_chunks(P.col_ptr, (int)n, &unit_end, P.cj0, P.ckoff, P.cpad);
+    build_chunks(P.row_ptr, (int)m, nullptr, P.ri0, P.rkoff, P.rpad);
+    if (P.cpad >= INT32_MAX - PAD || P.rpad >= INT32_MAX - PAD)
+        return fail(s, MFS_ERR_INVALID, "too many nonzeros after padding (limit 2^31)");
+    // cones intersecting each column chunk
+    const int ncc = (int)P.cj0.size() - 1;
+    P.cq_lo.resize(std::max(ncc, 0));
+    P.cq_hi.resize(std::max(ncc, 0));
+    const int nsoc = (int)P.soc_start.size();
+    int lo = 0;
+    for (int c = 0; c < ncc; ++c) {
+        const int j0 = P.cj0[c], j1 = P.cj0[c + 1];
+        while (lo < nsoc && P.soc_start[lo] + P.soc_size[lo] <= j0) ++lo;
+        int hi = lo;
+        while (hi < nsoc && P.soc_start[hi] < j1) ++hi;
+        P.cq_lo[c] = lo;
+        P.cq_hi[c] = hi;
+    }
+    return MFS_OK;
+}
+
+template <typename T>
+void pad_chunks(const std::vector<int>& c0, const std::vector<int>& koff, const std::vector<int>& ptr,
+                const std::vector<int>& idx, const std::vector<double>& val, int64_t padded, std::vector<int>& pidx,
+                std::vector<T>& pval) {
+    pidx.assign(padded + PAD, 0);
+    pval.assign(padded + PAD, T(0));
+    const int nch = (int)c0.size() - 1;
+    for (int c = 0; c < nch; ++c) {
+        const int k0 = ptr[c0[c]], k1 = ptr[c0[c + 1]];
+        for (int k = k0; k < k1; ++k) {
+            pidx[koff[c] + (k - k0)] = idx[k];
+            pval[koff[c] + (k - k0)] = T(val[k]);
+        }
+    }
+}
+
+template <typename T>
+SweepArgs<T> sweep_args(mfs_solver* s, State<T>& st) {
+    SweepArgs<T> a;
+    a.col_ptr = s->col_ptr;
+    a.cidx = s->cidx;
+    a.cval = st.cval;
+    a.cj0 = s->cj0;
+    a.ckoff = s->ckoff;
+    a.cq_lo = s->cq_lo;
+    a.cq_hi = s->cq_hi;
+    a.row_ptr = s->row_ptr;
+    a.ridx = s->ridx;
+    a.rval = st.rval;
+    a.ri0 = s->ri0;
+    a.rkoff = s->rkoff;
+    a.soc_start = s->soc_start;
+    a.soc_size = s->soc_size;
+    a.soc_big = s->soc_big;
+    a.big_list = s->big_list;
+    a.b = st.b;
+    a.c = st.c;
+    a.x = st.x;
+    a.z = st.z;
+    a.del = st.del;
+    a.lam = st.lam;
+    a.v = st.v;
+    a.mu = T(s->set.mu);
+    a.err = s->err;
+    return a;
+}
+
+template <typename T>
+size_t smem_col_sweep(bool soc) {
+    using L = TileLayout<T, T, 1>;
+    return L::EXTRA + (soc ? 3 * CMAX * sizeof(T) + CMAX : 0);
+}
+template <typename T>
+size_t smem_row_sweep() {
+    return TileLayout<T, T, 2>::EXTRA;
+}
+template <typename T>
+size_t smem_resid_row() {
+    return TileLayout<T, double, 1>::EXTRA + 2 * NWARP * sizeof(double);
+}
+template <typename T>
+size_t smem_resid_col() {
+    return TileLayout<T, double, 1>::EXTRA + 2 * NWARP * sizeof(double) + 2 * CMAX * sizeof(double) + CMAX;
+}
+
+template <typename T>
+mfs_status set_smem_attrs(mfs_solver* s) {
+    CUDA_TRY(s, cudaFuncSetAttribute(k_col_sweep<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_col_sweep<T>(false)));
+    CUDA_TRY(s, cudaFuncSetAttribute(k_col_sweep<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_col_sweep<T>(true)));
+    CUDA_TRY(s, cudaFuncSetAttribute(k_row_sweep<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_row_sweep<T>()));
+    CUDA_TRY(s, cudaFuncSetAttribute(k_row_sweep<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_row_sweep<T>()));
+    CUDA_TRY(s, cudaFuncSetAttribute(k_row_resid<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_resid_row<T>()));
+    CUDA_TRY(s, cudaFuncSetAttribute(k_col_resid<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_resid_col<T>()));
+    CUDA_TRY(s, cudaFuncSetAttribute(k_col_resid<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_resid_col<T>()));
+    return MFS_OK;
+}
+
+// ---------------------------------------------------------------------------------- launches
+
+template <typename T>
+void launch_col(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
+    if (s->ncc == 0) return;
+    if (s->has_soc)
+        k_col_sweep<T, true><<<s->ncc, NT, smem_col_sweep<T>(true), st>>>(a);
+    else
+        k_col_sweep<T, false><<<s->ncc, NT, smem_col_sweep<T>(false), st>>>(a);
+}
+template <typename T>
+void launch_big(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
+    if (s->nbig) k_bigcone_sweep<T><<<s->nbig, NT, 0, st>>>(a);
+}
+template <typename T>
+void launch_row(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
+    if (s->nrc) k_row_sweep<T, 0><<<s->nrc, NT, smem_row_sweep<T>(), st>>>(a);
+}
+
+template <typename T>
+void launch_iteration(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
+    launch_col(s, a, st);
+    launch_big(s, a, st);
+    launch_row(s, a, st);
+}
+
+mfs_status check_device_error(mfs_solver* s) {
+    CUDA_TRY(s, cudaMemcpyAsync(s->h_err, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    if (*s->h_err != 0) {
+        const int code = *s->h_err;
+        CUDA_TRY(s, cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+        CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+        if (code == DERR_TIMEOUT) return fail(s, MFS_ERR_TIMEOUT, "a bounded on-device wait for a bulk copy gave up");
+        return fail(s, MFS_ERR_CUDA, "device error code " + std::to_string(code));
+    }
+    return MFS_OK;
+}
+
+template <typename T>
+mfs_status run_iters(mfs_solver* s, State<T>& st, int64_t k) {
+    if (k <= 0) return MFS_OK;
+    SweepArgs<T> a = sweep_args(s, st);
+    const int K = std::max(1, (int)s->set.check_every);
+    if (k >= K) {
+        if (!st.graph || st.graph_iters != K) {
+            if (st.graph) {
+                cudaGraphExecDestroy(st.graph);
+                st.graph = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            CUDA_TRY(s, cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+            for (int i = 0; i < K; ++i) launch_iteration(s, a, s->cap);
+            CUDA_TRY(s, cudaStreamEndCapture(s->cap, &g));
+            cudaError_t e = cudaGraphInstantiate(&st.graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                st.graph = nullptr;
+                return fail(s, MFS_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+            }
+            st.graph_iters = K;
+        }
+        while (k >= K) {
+            CUDA_TRY(s, cudaGraphLaunch(st.graph, s->stream));
+            k -= K;
+            s->iter += K;
+        }
+    }
+    for (int64_t i = 0; i < k; ++i) launch_iteration(s, a, s->stream);
+    s->iter += k;
+    CUDA_TRY(s, cudaGetLastError());
+    return MFS_OK;
+}
+
+template <typename T>
+mfs_status residuals_t(mfs_solver* s, State<T>& st, mfs_residuals_t* out, bool write_all_s) {
+    SweepArgs<T> a = sweep_args(s, st);
+    ResidArgs r;
+    r.part_row = s->part_row;
+    r.part_col = s->part_col;
+    r.part_big = s->part_big;
+    r.s_buf = s->s_buf;
+    r.write_all_s = write_all_s ? 1 : 0;
+    if (s->nrc) k_row_resid<T><<<s->nrc, NT, smem_resid_row<T>(), s->stream>>>(a, r);
+    if (s->ncc) {
+        if (s->has_soc)
+            k_col_resid<T, true><<<s->ncc, NT, smem_resid_col<T>(), s->stream>>>(a, r);
+        else
+            k_col_resid<T, false><<<s->ncc, NT, smem_resid_col<T>(), s->stream>>>(a, r);
+    }
+    if (s->nbig) k_bigcone_resid<T><<<s->nbig, NT, 0, s->stream>>>(a, r);
+    k_resid_finalize<<<1, NT, 0, s->stream>>>(s->part_row, s->nrc, s->part_col, s->ncc, s->part_big, s->nbig,
+                                              s->status);
+    CUDA_TRY(s, cudaGetLastError());
+    if (out) {
+        CUDA_TRY(s, cudaMemcpyAsync(s->h_status, s->status, NSTATUS * sizeof(double), cudaMemcpyDeviceToHost,
+                                    s->stream));
+    }
+    TRY(check_device_error(s));
+    if (out) {
+        double* h = s->h_status;
+        out->r_prim = h[S_RPRIM];
+        out->r_dual = h[S_RDUAL];
+        out->r_cone = h[S_RCONE];
+        out->r_gap = h[S_RGAP];
+        out->kkt = h[S_KKT];
+        out->pobj = h[S_POBJ];
+        out->dobj = h[S_DOBJ];
+        out->nrm_res_p = h[S_NRES];
+        out->nrm_b = h[S_NB];
+        out->nrm_xdist = h[S_NXDIST];
+        out->nrm_x = h[S_NX];
+        out->nrm_sdist = h[S_NSDIST];
+        out->nrm_c = h[S_NC];
+        out->nrm_atl_c = h[S_NATLC];
+        out->inf_res_p = h[S_IRES];
+        out->inf_ax = h[S_IAX];
+        out->inf_b = h[S_IB];
+        out->inf_atl_c = h[S_IATLC];
+        out->inf_atl = h[S_IATL];
+        out->inf_c = h[S_IC];
+        out->iter = s->iter;
+    }
+    return MFS_OK;
+}
+
+template <typename D, typename S>
+void convert(D* dst, const S* src, int64_t count, cudaStream_t st) {
+    if (count <= 0) return;
+    const int blocks = (int)std::min<int64_t>((count + 255) / 256, 148 * 16);
+    k_convert<D, S><<<blocks, 256, 0, st>>>(dst, src, (long long)count);
+}
+
+// Warm start from FP64 device vectors (x, lam required; z, del nullable).
+template <typename T>
+mfs_status warm_start_t(mfs_solver* s, State<T>& st, const double* x, const double* lam, const double* z,
+                        const double* del) {
+    convert(st.x, x, s->n, s->stream);
+    convert(st.lam, lam, s->m, s->stream);
+    const int pb = 256;
+    if (z) {
+        convert(st.z, z, s->n, s->stream);
+    } else if (s->n) {
+        k_proj_orthant<T><<<(int)std::min<int64_t>((s->n + pb - 1) / pb, 148 * 16), pb, 0, s->stream>>>(st.z, x, s->n);
+        if (s->nsoc) k_proj_soc<T><<<(s->nsoc + pb - 1) / pb, pb, 0, s->stream>>>(st.z, x, s->soc_start, s->soc_size, s->nsoc);
+    }
+    if (del) {
+        convert(st.del, del, s->n, s->stream);
+    } else {
+        // s_buf = c + A^T lambda (FP64 accumulation), then delta = proj_K(s_buf)
+        TRY(residuals_t(s, st, nullptr, true));
+        if (s->n) {
+            k_proj_orthant<T><<<(int)std::min<int64_t>((s->n + pb - 1) / pb, 148 * 16), pb, 0, s->stream>>>(
+                st.del, s->s_buf, s->n);
+            if (s->nsoc)
+                k_proj_soc<T><<<(s->nsoc + pb - 1) / pb, pb, 0, s->stream>>>(st.del, s->s_buf, s->soc_start,
+                                                                             s->soc_size, s->nsoc);
+        }
+    }
+    // v = F_U (b - A x) - lambda/mu
+    SweepArgs<T> a = sweep_args(s, st);
+    if (s->nrc) k_row_sweep<T, 1><<<s->nrc, NT, smem_row_sweep<T>(), s->stream>>>(a);
+    CUDA_TRY(s, cudaGetLastError());
+    TRY(check_device_error(s));
+    s->iter = 0;
+    return MFS_OK;
+}
+
+template <typename T>
+mfs_status alloc_state(mfs_solver* s, State<T>& st, const HostProblem& P, const double* b, const double* c) {
+    TRY(dalloc(s, &st.x, s->n));
+    TRY(dalloc(s, &st.z, s->n));
+    TRY(dalloc(s, &st.del, s->n));
+    TRY(dalloc(s, &st.lam, s->m));
+    TRY(dalloc(s, &st.v, s->m));
+    std::vector<T> hb(b, b + s->m), hc(c, c + s->n);
+    TRY(upload(s, &st.b, hb.data(), hb.size()));
+    TRY(upload(s, &st.c, hc.data(), hc.size()));
+    std::vector<int> pidx;
+    std::vector<T> pval;
+    pad_chunks<T>(P.cj0, P.ckoff, P.col_ptr, P.csc_row, P.csc_val, P.cpad, pidx, pval);
+    TRY(upload(s, &st.cval, pval.data(), pval.size()));
+    pad_chunks<T>(P.ri0, P.rkoff, P.row_ptr, P.csr_col, P.csr_val, P.rpad, pidx, pval);
+    TRY(upload(s, &st.rval, pval.data(), pval.size()));
+    CUDA_TRY(s, cudaMemsetAsync(st.x, 0, sizeof(T) * std::max(s->n, 1), s->stream));
+    CUDA_TRY(s, cudaMemsetAsync(st.z, 0, sizeof(T) * std::max(s->n, 1), s->stream));
+    CUDA_TRY(s, cudaMemsetAsync(st.del, 0, sizeof(T) * std::max(s->n, 1), s->stream));
+    CUDA_TRY(s, cudaMemsetAsync(st.lam, 0, sizeof(T) * std::max(s->m, 1), s->stream));
+    CUDA_TRY(s, cudaMemsetAsync(st.v, 0, sizeof(T) * std::max(s->m, 1), s->stream));
+    return MFS_OK;
+}
+
+template <typename D, typename S>
+void copy_state(mfs_solver* s, State<D>& dst, State<S>& src) {
+    convert(dst.x, src.x, s->n, s->stream);
+    convert(dst.z, src.z, s->n, s->stream);
+    convert(dst.del, src.del, s->n, s->stream);
+    convert(dst.lam, src.lam, s->m, s->stream);
+    convert(dst.v, src.v, s->m, s->stream);
+}
+
+int64_t bytes_per_iter(const mfs_solver* s, int precision) {
+    const int64_t o = s->o, n = s->n, m = s->m;
+    return precision == MFS_FP64 ? 24 * o + 68 * n + 44 * m : 16 * o + 36 * n + 24 * m;
+}
+
+bool finite_all(const double* p, int64_t count) {
+    for (int64_t i = 0; i < count; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+void destroy_graphs(mfs_solver* s) {
+    if (s->s32.graph) cudaGraphExecDestroy(s->s32.graph);
+    if (s->s64.graph) cudaGraphExecDestroy(s->s64.graph);
+    s->s32.graph = nullptr;
+    s->s64.graph = nullptr;
+}
+
+}  // namespace
+
+template <typename T>
+static mfs_status get_solution_t(mfs_solver* s, State<T>& st, double* x, double* lam, double* z, double* del,
+                                 bool host) {
+    double* tmp = nullptr;
+    const int64_t n = s->n, m = s->m;
+    if (host) {
+        cudaError_t e = cudaMallocAsync((void**)&tmp, std::max<int64_t>(3 * n + m, 1) * sizeof(double), s->stream);
+        if (e != cudaSuccess) return fail(s, MFS_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    }
+    double* dst[4] = {x, lam, z, del};
+    const T* src[4] = {st.x, st.lam, st.z, st.del};
+    const int64_t cnt[4] = {n, m, n, n};
+    int64_t off = 0;
+    for (int q = 0; q < 4; ++q) {
+        if (!dst[q] || !cnt[q]) continue;
+        double* d = host ? tmp + off : dst[q];
+        convert(d, src[q], cnt[q], s->stream);
+        if (host) cudaMemcpyAsync(dst[q], d, cnt[q] * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+        off += cnt[q];
+    }
+    if (tmp) cudaFreeAsync(tmp, s->stream);
+    CUDA_TRY(s, cudaGetLastError());
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    return MFS_OK;
+}
+
+template <typename T>
+static mfs_status time_kernels_t(mfs_solver* s, State<T>& st, int64_t k, double* out) {
+    SweepArgs<T> a = sweep_args(s, st);
+    cudaEvent_t ev[4];
+    for (auto& e : ev) CUDA_TRY(s, cudaEventCreate(&e));
+    double tc = 0, tb = 0, tr = 0, tall = 0;
+    for (int64_t i = 0; i < k; ++i) {
+        float ms = 0;
+        cudaEventRecord(ev[0], s->stream);
+        launch_col(s, a, s->stream);
+        cudaEventRecord(ev[1], s->stream);
+        launch_big(s, a, s->stream);
+        cudaEventRecord(ev[2], s->stream);
+        launch_row(s, a, s->stream);
+        cudaEventRecord(ev[3], s->stream);
+        CUDA_TRY(s, cudaEventSynchronize(ev[3]));
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        tc += ms;
+        cudaEventElapsedTime(&ms, ev[1], ev[2]);
+        tb += ms;
+        cudaEventElapsedTime(&ms, ev[2], ev[3]);
+        tr += ms;
+        cudaEventElapsedTime(&ms, ev[0], ev[3]);
+        tall += ms;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    s->iter += k;
+    const double kk = k > 0 ? (double)k : 1.0;
+    out[0] = tc / kk;
+    out[1] = tr / kk;
+    out[2] = s->nbig ? tb / kk : 0.0;
+    out[3] = tall / kk;
+    CUDA_TRY(s, cudaGetLastError());
+    return check_device_error(s);
+}
+
+static mfs_status warm_start_impl(mfs_solver* s, const double* x, const double* lam, const double* z,
+                                  const double* del, bool host) {
+    if (!s) return MFS_ERR_INVALID;
+    if ((s->n && !x) || (s->m && !lam)) return fail(s, MFS_ERR_INVALID, "x and lambda are required");
+    CUDA_TRY(s, cudaSetDevice(s->device));
+    const double *dx = x, *dl = lam, *dz = z, *dd = del;
+    double* tmp = nullptr;
+    if (host) {
+        const int64_t need = 3 * (int64_t)s->n + s->m;
+        cudaError_t e = cudaMallocAsync((void**)&tmp, std::max<int64_t>(need, 1) * sizeof(double), s->stream);
+        if (e != cudaSuccess) return fail(s, MFS_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+        double* p = tmp;
+        auto put = [&](const double* h, int64_t cnt, const double*& d) -> cudaError_t {
+            if (!h) {
+                d = nullptr;
+                return cudaSuccess;
+            }
+            d = p;
+            cudaError_t q = cnt ? cudaMemcpyAsync(p, h, cnt * sizeof(double), cudaMemcpyHostToDevice, s->stream)
+                                : cudaSuccess;
+            p += cnt;
+            return q;
+        };
+        cudaError_t q = put(x, s->n, dx);
+        if (q == cudaSuccess) q = put(lam, s->m, dl);
+        if (q == cudaSuccess) q = put(z, s->n, dz);
+        if (q == cudaSuccess) q = put(del, s->n, dd);
+        if (q != cudaSuccess) {
+            cudaFreeAsync(tmp, s->stream);
+            return fail(s, MFS_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(q));
+        }
+    }
+    mfs_status st = (s->precision == MFS_FP64) ? warm_start_t(s, s->s64, dx, dl, dz, dd)
+                                                : warm_start_t(s, s->s32, dx, dl, dz, dd);
+    if (tmp) {
+        cudaFreeAsync(tmp, s->stream);
+        cudaStreamSynchronize(s->stream);
+    }
+    return st;
+}
+
+// ====================================================================================== C ABI
+extern "C" {
+
+void mfs_default_settings(mfs_settings* st) {
+    if (!st) return;
+    st->mu = 1.0;
+    st->check_every = 25;
+    st->precision = MFS_FP64;
+    st->polish_iters = 50;
+    st->reserved = 0;
+}
+
+const char* mfs_last_error(const mfs_solver* s) {
+    return s ? s->last_error.c_str() : g_create_error.c_str();
+}
+
+void mfs_destroy(mfs_solver* s) {
+    if (!s) return;
+    cudaSetDevice(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    destroy_graphs(s);
+    for (void* p : s->allocs) cudaFree(p);
+    if (s->h_status) cudaFreeHost(s->h_status);
+    if (s->h_err) cudaFreeHost(s->h_err);
+    if (s->cap) cudaStreamDestroy(s->cap);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col, const double* val,
+                      const double* b, const double* c, int64_t ncones, const mfs_cone* cones,
+                      const mfs_settings* settings, void* cuda_stream, mfs_solver** out) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, MFS_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (m < 0 || n < 0 || nnz < 0 || ncones < 0) return fail(nullptr, MFS_ERR_INVALID, "negative size");
+    if (m >= INT32_MAX || n >= INT32_MAX || nnz >= INT32_MAX)
+        return fail(nullptr, MFS_ERR_INVALID, "m, n and nnz must be below 2^31");
+    if ((nnz && (!row || !col || !val)) || (m && !b) || (n && !c) || (ncones && !cones))
+        return fail(nullptr, MFS_ERR_INVALID, "NULL array");
+    mfs_settings set;
+    mfs_default_settings(&set);
+    if (settings) set = *settings;
+    if (!(set.mu > 0.0) || !std::isfinite(set.mu)) return fail(nullptr, MFS_ERR_INVALID, "mu must be > 0");
+    if (set.check_every < 1) return fail(nullptr, MFS_ERR_INVALID, "check_every must be >= 1");
+    if (set.precision != MFS_FP64 && set.precision != MFS_FP32_MIXED)
+        return fail(nullptr, MFS_ERR_INVALID, "unknown precision");
+    if (set.polish_iters < 0) return fail(nullptr, MFS_ERR_INVALID, "polish_iters must be >= 0");
+    int64_t total = 0;
+    for (int64_t q = 0; q < ncones; ++q) {
+        if (cones[q].size < 1) return fail(nullptr, MFS_ERR_INVALID, "cone of size < 1");
+        if (cones[q].kind != MFS_CONE_NONNEG && cones[q].kind != MFS_CONE_SOC)
+            return fail(nullptr, MFS_ERR_INVALID, "unknown cone kind");
+        total += cones[q].size;
+    }
+    if (total != n) return fail(nullptr, MFS_ERR_INVALID, "cone sizes do not sum to n");
+    for (int64_t t = 0; t < nnz; ++t) {
+        if (row[t] < 0 || row[t] >= m || col[t] < 0 || col[t] >= n)
+            return fail(nullptr, MFS_ERR_INVALID, "COO index out of range at entry " + std::to_string(t));
+        if (!std::isfinite(val[t])) return fail(nullptr, MFS_ERR_INVALID, "non-finite value in A");
+    }
+    if (!finite_all(b, m) || !finite_all(c, n)) return fail(nullptr, MFS_ERR_INVALID, "non-finite value in b or c");
+
+    mfs_solver* s = new (std::nothrow) mfs_solver();
+    if (!s) return fail(nullptr, MFS_ERR_OOM, "host allocation failed");
+    auto bail = [&](mfs_status st) {
+        g_create_error = s->last_error;
+        mfs_destroy(s);
+        return st;
+    };
+    s->set = set;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess) {
+        s->last_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return bail(MFS_ERR_CUDA);
+    }
+    if (cuda_stream) {
+        s->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            s->last_error = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+            return bail(MFS_ERR_CUDA);
+        }
+        s->own_stream = true;
+    }
+    e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        s->last_error = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+        return bail(MFS_ERR_CUDA);
+    }
+    HostProblem P;
+    mfs_status st = setup_host(s, m, n, nnz, row, col, val, ncones, cones, P);
+    if (st != MFS_OK) return bail(st);
+    s->m = P.m;
+    s->n = P.n;
+    s->o = P.o;
+    s->ncones = (int)ncones;
+    s->nsoc = (int)P.soc_start.size();
+    s->nbig = (int)P.big_list.size();
+    s->has_soc = s->nsoc > 0;
+    s->ncc = (int)P.cj0.size() - 1;
+    s->nrc = (int)P.ri0.size() - 1;
+    s->precision = set.precision;
+
+#define CHK(x)                      \
+    do {                            \
+        mfs_status q_ = (x);        \
+        if (q_ != MFS_OK) return bail(q_); \
+    } while (0)
+    CHK(upload(s, &s->col_ptr, P.col_ptr.data(), P.col_ptr.size()));
+    CHK(upload(s, &s->row_ptr, P.row_ptr.data(), P.row_ptr.size()));
+    CHK(upload(s, &s->cj0, P.cj0.data(), P.cj0.size()));
+    CHK(upload(s, &s->ckoff, P.ckoff.data(), P.ckoff.size()));
+    CHK(upload(s, &s->cq_lo, P.cq_lo.data(), P.cq_lo.size()));
+    CHK(upload(s, &s->cq_hi, P.cq_hi.data(), P.cq_hi.size()));
+    CHK(upload(s, &s->ri0, P.ri0.data(), P.ri0.size()));
+    CHK(upload(s, &s->rkoff, P.rkoff.data(), P.rkoff.size()));
+    CHK(upload(s, &s->soc_start, P.soc_start.data(), P.soc_start.size()));
+    CHK(upload(s, &s->soc_size, P.soc_size.data(), P.soc_size.size()));
+    CHK(upload(s, &s->soc_big, P.soc_big.data(), P.soc_big.size()));
+    CHK(upload(s, &s->big_list, P.big_list.data(), P.big_list.size()));
+    {
+        std::vector<int> pidx;
+        std::vector<float> dummy;
+        std::vector<int> idx;
+        // padded index arrays (shared by both precisions)
+        pidx.assign(P.cpad + PAD, 0);
+        for (int ch = 0; ch < s->ncc; ++ch) {
+            const int k0 = P.col_ptr[P.cj0[ch]], k1 = P.col_ptr[P.cj0[ch + 1]];
+            for (int k = k0; k < k1; ++k) pidx[P.ckoff[ch] + (k - k0)] = P.csc_row[k];
+        }
+        CHK(upload(s, &s->cidx, pidx.data(), pidx.size()));
+        pidx.assign(P.rpad + PAD, 0);
+        for (int ch = 0; ch < s->nrc; ++ch) {
+            const int k0 = P.row_ptr[P.ri0[ch]], k1 = P.row_ptr[P.ri0[ch + 1]];
+            for (int k = k0; k < k1; ++k) pidx[P.rkoff[ch] + (k - k0)] = P.csr_col[k];
+        }
+        CHK(upload(s, &s->ridx, pidx.data(), pidx.size()));
+    }
+    CHK(dalloc(s, &s->err, 1));
+    CHK(dalloc(s, &s->part_row, (size_t)std::max(s->nrc, 1) * NF));
+    CHK(dalloc(s, &s->part_col, (size_t)std::max(s->ncc, 1) * NF));
+    CHK(dalloc(s, &s->part_big, (size_t)std::max(s->nbig, 1) * NF));
+    CHK(dalloc(s, &s->s_buf, (size_t)std::max(s->n, 1)));
+    CHK(dalloc(s, &s->status, NSTATUS));
+    e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_status, NSTATUS * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_err, sizeof(int));
+    if (e != cudaSuccess) {
+        s->last_error = std::string("pinned allocation: ") + cudaGetErrorString(e);
+        return bail(MFS_ERR_CUDA);
+    }
+    if (set.precision == MFS_FP32_MIXED) {
+        CHK(alloc_state<float>(s, s->s32, P, b, c));
+        CHK(set_smem_attrs<float>(s));
+        s->have32 = true;
+    }
+    if (set.precision == MFS_FP64 || set.polish_iters > 0) {
+        CHK(alloc_state<double>(s, s->s64, P, b, c));
+        CHK(set_smem_attrs<double>(s));
+        s->have64 = true;
+    }
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        s->last_error = std::string("set-up: ") + cudaGetErrorString(e);
+        return bail(MFS_ERR_CUDA);
+    }
+#undef CHK
+    *out = s;
+    return MFS_OK;
+}
+
+mfs_status mfs_get_info(const mfs_solver* s, mfs_info_t* out) {
+    if (!s || !out) return MFS_ERR_INVALID;
+    out->m = s->m;
+    out->n = s->n;
+    out->o = s->o;
+    out->ncones = s->ncones;
+    out->nsoc = s->nsoc;
+    out->nbig = s->nbig;
+    out->col_chunks = s->ncc;
+    out->row_chunks = s->nrc;
+    out->bytes_per_iter = bytes_per_iter(s, s->precision);
+    out->precision = s->precision;
+    out->reserved = 0;
+    return MFS_OK;
+}
+
+mfs_status mfs_set_mu(mfs_solver* s, double mu) {
+    if (!s) return MFS_ERR_INVALID;
+    if (!(mu > 0.0) || !std::isfinite(mu)) return fail(s, MFS_ERR_INVALID, "mu must be > 0");
+    CUDA_TRY(s, cudaSetDevice(s->device));
+    const double old = s->set.mu;
+    s->set.mu = mu;
+    destroy_graphs(s);  // mu is baked into the captured launches
+    if (old == mu) return MFS_OK;
+    // v = rho - lambda/mu depends on mu. rho = F_U (b - A x) is recomputed from the current x by
+    // the same row-order kernel that produced it, so only the lambda/mu term changes.
+    if (s->precision == MFS_FP64) {
+        if (s->nrc) k_row_sweep<double, 1><<<s->nrc, NT, smem_row_sweep<double>(), s->stream>>>(sweep_args(s, s->s64));
+    } else {
+        if (s->nrc) k_row_sweep<float, 1><<<s->nrc, NT, smem_row_sweep<float>(), s->stream>>>(sweep_args(s, s->s32));
+    }
+    CUDA_TRY(s, cudaGetLastError());
+    return check_device_error(s);
+}
+
+mfs_status mfs_warm_start(mfs_solver* s, const double* x, const double* lambda, const double* z,
+                          const double* delta) {
+    return warm_start_impl(s, x, lambda, z, delta, true);
+}
+
+mfs_status mfs_warm_start_device(mfs_solver* s, const double* x, const double* lambda, const double* z,
+                                 const double* delta) {
+    return warm_start_impl(s, x, lambda, z, delta, false);
+}
+
+mfs_status mfs_iterate(mfs_solver* s, int64_t k) {
+    if (!s) return MFS_ERR_INVALID;
+    if (k < 0) return fail(s, MFS_ERR_INVALID, "k must be >= 0");
+    CUDA_TRY(s, cudaSetDevice(s->device));
+    TRY(s->precision == MFS_FP64 ? run_iters(s, s->s64, k) : run_iters(s, s->s32, k));
+    return check_device_error(s);
+}
+
+mfs_status mfs_residuals(mfs_solver* s, mfs_residuals_t* out) {
+    if (!s || !out) return MFS_ERR_INVALID;
+    CUDA_TRY(s, cudaSetDevice(s->device));
+    return s->precision == MFS_FP64 ? residuals_t(s, s->s64, out, false) : residuals_t(s, s->s32, out, false);
+}
+
+mfs_status mfs_set_precision(mfs_solver* s, int32_t precision) {
+    if (!s) return MFS_ERR_INVALID;
+    if (precision != MFS_FP64 && precision != MFS_FP32_MIXED) return fail(s, MFS_ERR_INVALID, "unknown precision");
+    if (precision == s->precision) return MFS_OK;
+    if ((precision == MFS_FP64 && !s->have64) || (precision == MFS_FP32_MIXED && !s->have32))
+        return fail(s, MFS_ERR_INVALID, "that precision was not prepared at mfs_create");
+    CUDA_TRY(s, cudaSetDevice(s->device));
+    if (precision == MFS_FP64)
+        copy_state(s, s->s64, s->s32);
+    else
+        copy_state(s, s->s32, s->s64);
+    s->precision = precision;
+    CUDA_TRY(s, cudaGetLastError());
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    return MFS_OK;
+}
+
+mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters_out) {
+    if (!s) return MFS_ERR_INVALID;
+    if (!(tol > 0.0) || max_iter < 0) return fail(s, MFS_ERR_INVALID, "tol must be > 0 and max_iter >= 0");
+    CUDA_TRY(s, cudaSetDevice(s->device));
+    const int64_t K = s->set.check_every;
+    int64_t it = 0;
+    double best = std::numeric_limits<double>::infinity();
+    int since_best = 0;
+    mfs_residuals_t r;
+    mfs_status result = MFS_MAX_ITER;
+    while (true) {
+        TRY(mfs_residuals(s, &r));
+        if (!std::isfinite(r.kkt)) {
+            result = fail(s, MFS_ERR_NUMERIC, "NaN or Inf in the residuals");
+            break;
+        }
+        const bool fp32 = s->precision == MFS_FP32_MIXED;
+        if (r.kkt <= tol) {
+            if (fp32 && s->have64 && s->set.polish_iters > 0 && it < max_iter) {
+                TRY(mfs_set_precision(s, MFS_FP64));
+                const int64_t p = std::min<int64_t>(s->set.polish_iters, max_iter - it);
+                TRY(mfs_iterate(s, p));
+                it += p;
+                continue;  // re-check in FP64
+            }
+            result = MFS_OK;
+            break;
+        }
+        if (it >= max_iter) break;
+        if (fp32 && s->have64) {
+            if (r.kkt < 0.99 * best) {
+                best = r.kkt;
+                since_best = 0;
+            } else if (++since_best >= 40) {
+                TRY(mfs_set_precision(s, MFS_FP64));
+            }
+        }
+        const int64_t kk = std::min<int64_t>(K, max_iter - it);
+        TRY(mfs_iterate(s, kk));
+        it += kk;
+    }
+    if (iters_out) *iters_out = it;
+    return result;
+}
+
+mfs_status mfs_get_solution(mfs_solver* s, double* x, double* lambda, double* z, double* delta) {
+    if (!s) return MFS_ERR_INVALID;
+    CUDA_TRY(s, cudaSetDevice(s->device));
+    return s->precision == MFS_FP64 ? get_solution_t(s, s->s64, x, lambda, z, delta, true)
+                                    : get_solution_t(s, s->s32, x, lambda, z, delta, true);
+}
+
+mfs_status mfs_get_solution_device(mfs_solver* s, double* x, double* lambda, double* z, double* delta) {
+    if (!s) return MFS_ERR_INVALID;
+    CUDA_TRY(s, cudaSetDevice(s->device));
+    return s->precision == MFS_FP64 ? get_solution_t(s, s->s64, x, lambda, z, delta, false)
+                                    : get_solution_t(s, s->s32, x, lambda, z, delta, false);
+}
+
+mfs_status mfs_time_kernels(mfs_solver* s, int64_t k, double* out_ms) {
+    if (!s || !out_ms || k < 0) return MFS_ERR_INVALID;
+    CUDA_TRY(s, cudaSetDevice(s->device));
+    return s->precision == MFS_FP64 ? time_kernels_t(s, s->s64, k, out_ms) : time_kernels_t(s, s->s32, k, out_ms);
+}
+
+}  // extern "C"

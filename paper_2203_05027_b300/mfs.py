@@ -1,0 +1,229 @@
+"""Thin ctypes binding to libmfs.so (include/mfs.h): argument marshalling only.
+
+Every step of the solver runs in the CUDA library; this module converts numpy arrays to the C
+types the header declares and status codes to exceptions. There is no CPU fallback: if the
+library is missing or cannot be loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmfs.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "mfs.h")
+
+MFS_OK, MFS_MAX_ITER, MFS_ERR_INVALID, MFS_ERR_CUDA, MFS_ERR_OOM, MFS_ERR_NUMERIC, MFS_ERR_TIMEOUT = range(7)
+STATUS_NAMES = {0: "OK", 1: "MAX_ITER", 2: "ERR_INVALID", 3: "ERR_CUDA", 4: "ERR_OOM", 5: "ERR_NUMERIC",
+                6: "ERR_TIMEOUT"}
+CONE_NONNEG, CONE_SOC = 0, 1
+FP64, FP32_MIXED = 0, 1
+
+
+class MfsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Cone(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pad_", ctypes.c_int32), ("size", ctypes.c_int64)]
+
+
+class Settings(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double), ("check_every", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("polish_iters", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+RESID_FIELDS = ("r_prim", "r_dual", "r_cone", "r_gap", "kkt", "pobj", "dobj",
+                "nrm_res_p", "nrm_b", "nrm_xdist", "nrm_x", "nrm_sdist", "nrm_c", "nrm_atl_c",
+                "inf_res_p", "inf_ax", "inf_b", "inf_atl_c", "inf_atl", "inf_c")
+
+
+class Residuals(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_double) for f in RESID_FIELDS] + [("iter", ctypes.c_int64)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("o", ctypes.c_int64),
+                ("ncones", ctypes.c_int64), ("nsoc", ctypes.c_int64), ("nbig", ctypes.c_int64),
+                ("col_chunks", ctypes.c_int64), ("row_chunks", ctypes.c_int64),
+                ("bytes_per_iter", ctypes.c_int64), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def header_functions(path=HEADER):
+    """Names of the functions include/mfs.h declares."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mfs_[a-z0-9_]+)\s*\(", text)))
+
+
+def load(path=LIB_PATH):
+    """Load libmfs.so and declare its signatures. Raises OSError if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libmfs.so not built at {path}; run paper_2203_05027_b300/build.py")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i64, i32, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    lp = ctypes.POINTER(ctypes.c_int64)
+    st = ctypes.c_int
+    lib.mfs_default_settings.argtypes = [ctypes.POINTER(Settings)]
+    lib.mfs_default_settings.restype = None
+    lib.mfs_create.argtypes = [i64, i64, i64, lp, lp, dp, dp, dp, i64, ctypes.POINTER(Cone),
+                               ctypes.POINTER(Settings), P, ctypes.POINTER(P)]
+    lib.mfs_create.restype = st
+    lib.mfs_destroy.argtypes = [P]
+    lib.mfs_destroy.restype = None
+    lib.mfs_last_error.argtypes = [P]
+    lib.mfs_last_error.restype = ctypes.c_char_p
+    lib.mfs_get_info.argtypes = [P, ctypes.POINTER(Info)]
+    lib.mfs_get_info.restype = st
+    lib.mfs_set_mu.argtypes = [P, dbl]
+    lib.mfs_set_mu.restype = st
+    for name in ("mfs_warm_start", "mfs_warm_start_device", "mfs_get_solution", "mfs_get_solution_device"):
+        getattr(lib, name).argtypes = [P, P, P, P, P]
+        getattr(lib, name).restype = st
+    lib.mfs_iterate.argtypes = [P, i64]
+    lib.mfs_iterate.restype = st
+    lib.mfs_solve.argtypes = [P, dbl, i64, lp]
+    lib.mfs_solve.restype = st
+    lib.mfs_residuals.argtypes = [P, ctypes.POINTER(Residuals)]
+    lib.mfs_residuals.restype = st
+    lib.mfs_set_precision.argtypes = [P, i32]
+    lib.mfs_set_precision.restype = st
+    lib.mfs_time_kernels.argtypes = [P, i64, dp]
+    lib.mfs_time_kernels.restype = st
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _f64(a, count=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if count is not None and a.size != count:
+        raise ValueError(f"expected {count} elements, got {a.size}")
+    return a
+
+
+class Solver:
+    """One problem on the GPU. ``prob`` is a dict with m, n, row, col, val, b, c, cones
+    (as made by ``instances``)."""
+
+    def __init__(self, prob, mu=1.0, check_every=25, precision="fp64", polish_iters=50, stream=None):
+        lib = load()
+        self._lib = lib
+        m, n = int(prob["m"]), int(prob["n"])
+        row = np.ascontiguousarray(prob["row"], dtype=np.int64)
+        col = np.ascontiguousarray(prob["col"], dtype=np.int64)
+        val = _f64(prob["val"])
+        b = _f64(prob["b"], m)
+        c = _f64(prob["c"], n)
+        cones = np.asarray(prob["cones"], dtype=np.int64).reshape(-1, 2)
+        carr = (Cone * max(len(cones), 1))()
+        for q, (k, s) in enumerate(cones):
+            carr[q].kind = int(k)
+            carr[q].size = int(s)
+        st = Settings()
+        lib.mfs_default_settings(ctypes.byref(st))
+        st.mu = float(mu)
+        st.check_every = int(check_every)
+        st.precision = {"fp64": FP64, "fp32": FP32_MIXED, "mixed": FP32_MIXED}[precision] \
+            if isinstance(precision, str) else int(precision)
+        st.polish_iters = int(polish_iters)
+        h = ctypes.c_void_p()
+        stream_ptr = ctypes.c_void_p(int(stream)) if stream else None
+        code = lib.mfs_create(m, n, len(row), row.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                              col.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                              val.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                              b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                              c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                              len(cones), carr, ctypes.byref(st), stream_ptr, ctypes.byref(h))
+        if code != MFS_OK:
+            raise MfsError(code, lib.mfs_last_error(None).decode())
+        self._h = h
+        self.m, self.n = m, n
+
+    def _check(self, code, ok=(MFS_OK,)):
+        if code not in ok:
+            raise MfsError(code, self._lib.mfs_last_error(self._h).decode())
+        return code
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.mfs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        out = Info()
+        self._check(self._lib.mfs_get_info(self._h, ctypes.byref(out)))
+        return {f: getattr(out, f) for f, _ in Info._fields_ if f != "reserved"}
+
+    def set_mu(self, mu):
+        self._check(self._lib.mfs_set_mu(self._h, float(mu)))
+
+    def set_precision(self, precision):
+        p = {"fp64": FP64, "fp32": FP32_MIXED}[precision] if isinstance(precision, str) else int(precision)
+        self._check(self._lib.mfs_set_precision(self._h, p))
+
+    def warm_start(self, x, lam, z=None, delta=None):
+        x, lam = _f64(x, self.n), _f64(lam, self.m)
+        z, delta = _f64(z, self.n), _f64(delta, self.n)
+        self._check(self._lib.mfs_warm_start(self._h, _ptr(x), _ptr(lam), _ptr(z), _ptr(delta)))
+
+    def warm_start_device(self, x, lam, z=None, delta=None):
+        """Device pointers (ints) to float64 arrays, e.g. torch tensors' data_ptr()."""
+        args = [ctypes.c_void_p(int(p)) if p else None for p in (x, lam, z, delta)]
+        self._check(self._lib.mfs_warm_start_device(self._h, *args))
+
+    def iterate(self, k):
+        self._check(self._lib.mfs_iterate(self._h, int(k)))
+
+    def solve(self, tol, max_iter):
+        it = ctypes.c_int64(0)
+        code = self._check(self._lib.mfs_solve(self._h, float(tol), int(max_iter), ctypes.byref(it)),
+                           ok=(MFS_OK, MFS_MAX_ITER))
+        return STATUS_NAMES[code], int(it.value)
+
+    def residuals(self):
+        out = Residuals()
+        self._check(self._lib.mfs_residuals(self._h, ctypes.byref(out)))
+        d = {f: getattr(out, f) for f in RESID_FIELDS}
+        d["iter"] = out.iter
+        return d
+
+    def solution(self):
+        x, z, d = (np.empty(self.n) for _ in range(3))
+        lam = np.empty(self.m)
+        self._check(self._lib.mfs_get_solution(self._h, _ptr(x), _ptr(lam), _ptr(z), _ptr(d)))
+        return {"x": x, "lam": lam, "z": z, "delta": d}
+
+    def solution_device(self, x=None, lam=None, z=None, delta=None):
+        args = [ctypes.c_void_p(int(p)) if p else None for p in (x, lam, z, delta)]
+        self._check(self._lib.mfs_get_solution_device(self._h, *args))
+
+    def time_kernels(self, k):
+        out = (ctypes.c_double * 4)()
+        self._check(self._lib.mfs_time_kernels(self._h, int(k), out))
+        return {"col_ms": out[0], "row_ms": out[1], "bigcone_ms": out[2], "iter_ms": out[3]}

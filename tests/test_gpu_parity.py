@@ -1,0 +1,265 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle of Algorithm 1.
+
+The GPU runs the reduced form on (x, z, delta, lambda); the oracle runs the literal iteration
+with o-length y and gamma. After a fixed number of iterations both must agree element by element:
+max_i |gpu_i - oracle_i| <= tol * max_i |oracle_i| for each of x, z, delta, lambda, with
+tol = 1e-10 in FP64 mode and 1e-4 in FP32 mode (the oracle then runs on the FP32-rounded A, b, c
+promoted to FP64, so only the arithmetic differs).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_05027_b300 import build, instances as I, mfs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build.build()
+    mfs.load()
+
+
+def rel_err(g, o):
+    scale = np.abs(o).max() if o.size else 0.0
+    d = np.abs(g - o).max() if o.size else 0.0
+    return d / scale if scale > 0 else d
+
+
+def compare(sol, st, tol, label=""):
+    errs = {"x": rel_err(sol["x"], st.x), "z": rel_err(sol["z"], st.z),
+            "delta": rel_err(sol["delta"], st.delta), "lam": rel_err(sol["lam"], st.lam)}
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, (label, errs)
+    return errs
+
+
+def run_pair(prob, iters, precision, mu=1.0, warm=None):
+    dt = np.float32 if precision == "fp32" else np.float64
+    orc = oracle.make_oracle(prob, mu=mu, dtype=dt)
+    s = mfs.Solver(prob, mu=mu, precision=precision, polish_iters=0, check_every=25)
+    if warm is not None:
+        orc.warm_start(*warm)
+        s.warm_start(*warm)
+    orc.iterate(iters)
+    s.iterate(iters)
+    return orc, s
+
+
+def edge_problem(kind, seed=0):
+    rng = np.random.default_rng(seed)
+    if kind == "empty_rows_cols":
+        p = I.small_lp(seed, m=60, n=150)
+        keep = (p["row"] % 7 != 3) & (p["col"] % 11 != 5)   # rows 3,10,.. and cols 5,16,.. empty
+        for k in ("row", "col", "val"):
+            p[k] = p[k][keep]
+        return p
+    if kind == "long_column":  # one column with more than one tile of nonzeros
+        m, n = 5000, 40
+        p = I.lp_from_degrees(m, n, np.r_[[3000], rng.integers(1, 6, n - 2), [2500]], seed)
+        return p
+    if kind == "long_row":
+        m, n = 30, 6000
+        deg = rng.integers(1, 4, n)
+        p = I.lp_from_degrees(m, n, deg, seed)
+        extra_cols = rng.choice(n, 2300, replace=False)
+        p["row"] = np.r_[p["row"], np.zeros(2300, np.int64)]
+        p["col"] = np.r_[p["col"], extra_cols]
+        p["val"] = np.r_[p["val"], rng.standard_normal(2300)]
+        return p
+    if kind == "soc_mixed":  # orthant pieces, size 1/2/3 cones, a big cone (> 1024 columns)
+        sizes = [("N", 7), ("S", 1), ("S", 2), ("S", 3), ("N", 1), ("S", 64), ("S", 1500), ("N", 20),
+                 ("S", 5), ("S", 33)]
+        n = sum(s for _, s in sizes)
+        m = 300
+        p = I.lp_from_degrees(m, n, rng.integers(0, 5, n), seed)
+        p["cones"] = np.array([[0 if k == "N" else 1, s] for k, s in sizes])
+        return p
+    if kind == "soc_big_nnz":  # a 40-column cone with more than a tile of nonzeros
+        n, m = 200, 4000
+        deg = np.r_[rng.integers(1, 4, 80), np.full(40, 90), rng.integers(1, 4, 80)]
+        p = I.lp_from_degrees(m, n, deg, seed)
+        p["cones"] = np.array([[0, 80], [1, 40], [1, 80]])
+        return p
+    if kind == "duplicates_zeros":
+        p = I.small_lp(seed, m=50, n=120)
+        k = p["row"].size
+        p["row"] = np.r_[p["row"], p["row"][:40]]
+        p["col"] = np.r_[p["col"], p["col"][:40]]
+        p["val"] = np.r_[p["val"], rng.standard_normal(40)]
+        p["val"][5:12] = 0.0
+        return p
+    if kind == "no_nonzeros":
+        n, m = 10, 4
+        return {"m": m, "n": n, "row": np.zeros(0, np.int64), "col": np.zeros(0, np.int64),
+                "val": np.zeros(0), "b": rng.standard_normal(m), "c": rng.standard_normal(n),
+                "cones": np.array([[0, 4], [1, 6]])}
+    raise ValueError(kind)
+
+
+# ------------------------------------------------------------------ workloads
+
+def test_small_lp_fp64_2000_iterations():
+    prob = I.small_lp(0)
+    orc, s = run_pair(prob, 2000, "fp64")
+    compare(s.solution(), orc.state(), TOL["fp64"])
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_small_lp_fp64_other_seeds_and_mu(seed):
+    prob = I.small_lp(seed)
+    orc, s = run_pair(prob, 700, "fp64", mu=0.3 * seed)
+    compare(s.solution(), orc.state(), TOL["fp64"])
+
+
+@pytest.mark.parametrize("precision,iters", [("fp64", 200), ("fp32", 50)])
+def test_power_law_lp_scaled(precision, iters):
+    prob = I.large_lp(0, m=40_000, n=100_000)
+    orc, s = run_pair(prob, iters, precision)
+    compare(s.solution(), orc.state(), TOL[precision])
+
+
+@pytest.mark.parametrize("precision,iters", [("fp64", 200), ("fp32", 50)])
+def test_socp_scaled(precision, iters):
+    prob = I.socp(0, n=60_000, m=24_000)
+    orc, s = run_pair(prob, iters, precision)
+    compare(s.solution(), orc.state(), TOL[precision])
+
+
+def test_small_lp_fp32_2000_iterations():
+    prob = I.small_lp(0)
+    orc, s = run_pair(prob, 2000, "fp32")
+    errs = compare(s.solution(), orc.state(), TOL["fp32"])
+    print("fp32 small lp 2000 its", errs)
+
+
+@pytest.mark.parametrize("kind", ["empty_rows_cols", "long_column", "long_row", "soc_mixed", "soc_big_nnz",
+                                  "duplicates_zeros", "no_nonzeros"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_edge_cases(kind, precision):
+    prob = edge_problem(kind)
+    iters = 150 if precision == "fp64" else 40
+    orc, s = run_pair(prob, iters, precision)
+    compare(s.solution(), orc.state(), TOL[precision], kind)
+
+
+def test_paper_instance_family_soc4():
+    prob = I.paper_instance(300, 800, 0.01, "soc4", seed=3)
+    orc, s = run_pair(prob, 300, "fp64")
+    compare(s.solution(), orc.state(), TOL["fp64"])
+
+
+# ------------------------------------------------------------------ warm start, mu, residuals
+
+@pytest.mark.parametrize("given_zd", [False, True])
+def test_warm_start(given_zd):
+    prob = I.socp(1, n=3000, m=1200)
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(prob["n"])
+    lam = rng.standard_normal(prob["m"])
+    z = rng.standard_normal(prob["n"]) if given_zd else None
+    d = rng.standard_normal(prob["n"]) if given_zd else None
+    orc, s = run_pair(prob, 0, "fp64", warm=(x, lam, z, d))
+    compare(s.solution(), orc.state(), TOL["fp64"], "after warm start")
+    orc.iterate(300)
+    s.iterate(300)
+    compare(s.solution(), orc.state(), TOL["fp64"], "300 iterations later")
+
+
+def test_set_mu_midway():
+    prob = I.small_lp(4)
+    orc, s = run_pair(prob, 100, "fp64", mu=1.0)
+    orc.set_mu(0.25)
+    s.set_mu(0.25)
+    orc.iterate(300)
+    s.iterate(300)
+    compare(s.solution(), orc.state(), TOL["fp64"])
+
+
+@pytest.mark.parametrize("maker", ["lp", "socp", "soc_mixed"])
+def test_residuals_match_oracle(maker):
+    prob = {"lp": lambda: I.small_lp(0), "socp": lambda: I.socp(2, n=5000, m=2000),
+            "soc_mixed": lambda: edge_problem("soc_mixed")}[maker]()
+    orc, s = run_pair(prob, 137, "fp64")
+    g = s.residuals()
+    o = orc.residuals()
+    for k, ov in o.items():
+        assert abs(g[k] - ov) <= 1e-9 * max(1.0, abs(ov)), (k, g[k], ov)
+    assert g["iter"] == 137
+
+
+def test_residuals_fp32_storage_fp64_reductions():
+    prob = I.large_lp(1, m=20_000, n=50_000)
+    orc, s = run_pair(prob, 30, "fp32")
+    g, o = s.residuals(), orc.residuals()
+    for k in ("r_prim", "r_dual", "r_cone", "r_gap", "pobj", "dobj"):
+        assert abs(g[k] - o[k]) <= 1e-3 * max(1e-3, abs(o[k])), (k, g[k], o[k])
+
+
+# ------------------------------------------------------------------ solve
+
+def test_solve_reaches_tolerance_fp64():
+    prob = I.small_lp(0, m=20, n=50)
+    s = mfs.Solver(prob, precision="fp64", check_every=50)
+    status, its = s.solve(1e-8, 400_000)
+    assert status == "OK"
+    r = s.residuals()
+    assert r["kkt"] <= 1e-8
+    orc = oracle.make_oracle(prob)
+    orc.iterate(its)
+    assert abs(orc.residuals()["pobj"] - r["pobj"]) < 1e-8 * (1 + abs(r["pobj"]))
+
+
+def test_solve_mixed_precision_polishes_in_fp64():
+    prob = I.small_lp(0, m=20, n=50)
+    s = mfs.Solver(prob, precision="fp32", check_every=50, polish_iters=100)
+    status, its = s.solve(1e-6, 400_000)
+    assert status == "OK"
+    assert s.info()["precision"] == mfs.FP64
+    assert s.residuals()["kkt"] <= 1e-6
+
+
+def test_solve_max_iter():
+    prob = I.small_lp(0)
+    s = mfs.Solver(prob, check_every=10)
+    status, its = s.solve(1e-14, 55)
+    assert status == "MAX_ITER" and its == 55
+
+
+def test_nan_warm_start_is_numeric_error():
+    prob = I.small_lp(0, m=20, n=50)
+    s = mfs.Solver(prob)
+    x = np.zeros(50)
+    x[3] = np.nan
+    s.warm_start(x, np.zeros(20))
+    with pytest.raises(mfs.MfsError) as e:
+        s.solve(1e-6, 100)
+    assert e.value.status == mfs.MFS_ERR_NUMERIC
+
+
+def test_repeatable_bitwise():
+    prob = I.large_lp(3, m=20_000, n=50_000)
+    a = mfs.Solver(prob, precision="fp32")
+    b = mfs.Solver(prob, precision="fp32")
+    a.iterate(40)
+    b.iterate(40)
+    sa, sb = a.solution(), b.solution()
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+
+
+# ------------------------------------------------------------------ full-size workloads (few iterations)
+
+def test_large_lp_full_size_fp32_parity():
+    prob = I.large_lp(0)
+    orc, s = run_pair(prob, 3, "fp32")
+    compare(s.solution(), orc.state(), TOL["fp32"], "large_lp full size")
+
+
+def test_socp_full_size_fp32_parity():
+    prob = I.socp(0)
+    orc, s = run_pair(prob, 3, "fp32")
+    compare(s.solution(), orc.state(), TOL["fp32"], "socp full size")

@@ -175,6 +175,35 @@ mfs_status mfs_set_precision(mfs_solver* s, int32_t precision);
  */
 mfs_status mfs_time_kernels(mfs_solver* s, int64_t k, double* out_ms);
 
+/*
+ * mfs_row_residuals_static -- row-side residuals of a point (x, lambda) without allocating.
+ * The paper has no counterpart: this is a service for callers that cannot allocate device memory
+ * when they need a residual (a framework that owns all device memory through its own pool and
+ * forbids side allocations, plugin hosts whose execute callbacks must not allocate, real-time
+ * loops that allocate only at start-up). It needs no solver handle and calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *
+ * All pointers are device pointers of the current device. A is given in CSR form: row_ptr
+ * (m+1 int32 offsets), col_idx and val (row_ptr[m] entries; col_idx in [0,n)); b and lambda hold
+ * m doubles, x holds n doubles. out receives 8 doubles:
+ *   {r_prim, ||Ax-b||_2, ||Ax-b||_inf, ||Ax||_inf, ||b||_2, ||b||_inf, b^T lambda, -b^T lambda}
+ * (the same quantities as the matching fields of mfs_residuals_t), FP64, deterministic.
+ *
+ * Unlike the calls above it is asynchronous: the work is enqueued on cuda_stream (NULL = legacy
+ * default stream) and the call returns without waiting; read out after synchronizing.
+ * Scratch: a static 1 MiB device array that every GPU which loads this library holds until the
+ * process exits. Limit: m <= 4,194,304 rows; a larger m returns MFS_ERR_INVALID and enqueues
+ * nothing, as do negative sizes and NULL arrays. The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same array: calls whose work can overlap on the GPU (different streams,
+ * or different host threads) race on it, so the caller must order them. No state carries over
+ * between calls (each call writes every scratch slot it reads). MFS_ERR_CUDA if the device
+ * lookup or a launch fails.
+ */
+mfs_status mfs_row_residuals_static(int64_t m, int64_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                                    const double* val, const double* b, const double* x,
+                                    const double* lambda, double* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

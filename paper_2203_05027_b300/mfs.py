@@ -227,3 +227,20 @@ class Solver:
         out = (ctypes.c_double * 4)()
         self._check(self._lib.mfs_time_kernels(self._h, int(k), out))
         return {"col_ms": out[0], "row_ms": out[1], "bigcone_ms": out[2], "iter_ms": out[3]}
+
+
+def row_residuals_static(m, n, row_ptr, col_idx, val, b, x, lam, out, stream=None):
+    """mfs_row_residuals_static: device pointers (ints, e.g. torch tensors' data_ptr()) to a CSR
+    matrix (int32 row_ptr/col_idx, float64 val), float64 b, x, lambda and an 8-double output.
+    Enqueues the work on `stream` and returns without waiting; allocates nothing."""
+    lib = load()
+    fn = lib.mfs_row_residuals_static
+    if not fn.argtypes:
+        P = ctypes.c_void_p
+        fn.argtypes = [ctypes.c_int64, ctypes.c_int64, P, P, P, P, P, P, P, P]
+        fn.restype = ctypes.c_int
+    args = [ctypes.c_void_p(int(p)) if p else None for p in (row_ptr, col_idx, val, b, x, lam, out)]
+    code = fn(int(m), int(n), *args, ctypes.c_void_p(int(stream)) if stream else None)
+    if code != MFS_OK:
+        raise MfsError(code, "mfs_row_residuals_static failed (sizes beyond 4,194,304 rows, NULL or "
+                             "negative arguments give ERR_INVALID)")

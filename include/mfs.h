@@ -92,7 +92,7 @@ typedef struct {
     int64_t col_chunks, row_chunks;
     int64_t bytes_per_iter;     /* algorithmic HBM bytes of one iteration at the current precision */
     int32_t precision;          /* precision the iterate is currently held in */
-    int32_t reserved;
+    int32_t launches_per_iter;  /* kernel launches of one iteration (sweeps, long chunks, big cones) */
 } mfs_info_t;
 
 /* Defaults: mu = 1, check_every = 25, precision = MFS_FP64, polish_iters = 50. */

@@ -1,12 +1,16 @@
 // mfs_kernels.cuh -- the per-iteration sweep and the FP64 residual reductions (sm_103a).
 //
 // Data layout (built on the host, see mfs_solver.cu): the nonzeros of A are kept twice, in
-// column order (CSC: col_ptr, then per-chunk padded row-index/value arrays) and in row order
-// (CSR: row_ptr, col-index/value arrays). Columns are grouped into chunks of at most TILE
-// nonzeros and CMAX columns; a chunk never splits a Lorentz cone small enough to fit one, and a
-// single column longer than TILE is a chunk of its own. Rows are chunked the same way. Each
-// chunk's nonzeros start at a multiple of PAD elements in the padded arrays, so one CTA brings
-// its whole tile into shared memory with one 1-D bulk copy per array.
+// column order (CSC: col_ptr plus padded row-index/value arrays) and in row order (CSR: row_ptr
+// plus padded column-index/value arrays). Columns are grouped into chunks of at most WT = 256
+// nonzeros and WC columns; a chunk never splits a Lorentz cone small enough to fit one, and a
+// single column longer than WT is a "long" chunk of its own. Rows are chunked the same way. Each
+// chunk starts at a multiple of PAD = 8 elements of the padded arrays, so one warp loads a whole
+// chunk with one 256-bit load per lane and array (lane l holds local nonzeros 8l .. 8l+7).
+//
+// One warp owns one chunk: it gathers the other side's vector at its nonzeros' indices, reduces
+// the products per column (warp-level segmented scan, no block barriers) and runs the column
+// epilogue. Long chunks go to a CTA each.
 //
 // One iteration of the reduced form of Algorithm 1 (state x, z, delta, lambda and
 // v = F_U (b - A x_prev) - lambda/mu) is
@@ -20,6 +24,11 @@
 
 #include "mfs_device.cuh"
 
+// Minimum resident CTAs per SM requested for the sweep kernels (register budget).
+#ifndef MFS_SWEEP_MINB
+#define MFS_SWEEP_MINB 1
+#endif
+
 namespace mfs {
 
 template <typename T>
@@ -28,16 +37,18 @@ struct SweepArgs {
     const int* __restrict__ col_ptr;  // n+1 offsets into the unpadded column order
     const int* __restrict__ cidx;     // padded row indices
     const T* __restrict__ cval;       // padded values
-    const int* __restrict__ cj0;      // chunks+1: first column of each column chunk
-    const int* __restrict__ ckoff;    // chunks+1: padded offset of each chunk's first nonzero
-    const int* __restrict__ cq_lo;    // chunks: first Lorentz cone intersecting the chunk
-    const int* __restrict__ cq_hi;    // chunks: one past the last such cone
+    const int4* __restrict__ cdesc;   // per column chunk: {first column, one past last, padded offset, nnz}
+    const uint32_t* __restrict__ cheads;  // per column chunk: 8 words, bit e set if a column starts at local nonzero e
+    const int* __restrict__ clong;    // indices of the long column chunks
+    const int* __restrict__ cq_lo;    // per column chunk: first Lorentz cone intersecting it
+    const int* __restrict__ cq_hi;    // one past the last such cone
     // row order
     const int* __restrict__ row_ptr;
     const int* __restrict__ ridx;
     const T* __restrict__ rval;
-    const int* __restrict__ ri0;
-    const int* __restrict__ rkoff;
+    const int4* __restrict__ rdesc;
+    const uint32_t* __restrict__ rheads;
+    const int* __restrict__ rlong;
     // Lorentz cones, in coordinate order
     const int* __restrict__ soc_start;
     const int* __restrict__ soc_size;
@@ -52,103 +63,48 @@ struct SweepArgs {
     T* lam;
     T* v;
     T mu;
-    int* err;
+    int ntc, ntr;      // column / row chunks
+    int nlc, nlr;      // long column / row chunks
 };
 
-template <typename T, typename A, int NV>
-struct TileLayout {
-    static constexpr int HDR = 128;
-    static constexpr int R0 = TILE * (4 + (int)sizeof(T));
-    static constexpr int R1 = TILE * NV * (int)sizeof(A);
-    static constexpr int R = R0 > R1 ? R0 : R1;
-    static constexpr int PTR = HDR + R;
-    static constexpr int HEAD = PTR + (CMAX + 8) * 4;
-    static constexpr int SCAN = HEAD + TILE / 8;
-    static constexpr int EXTRA = SCAN + ((NWARP * NV * (int)sizeof(A) + 127) / 128) * 128;
-};
-
-__device__ __forceinline__ void load8(const int* s, int (&o)[8]) {
-    int4 u = *reinterpret_cast<const int4*>(s);
-    int4 w = *reinterpret_cast<const int4*>(s + 4);
-    o[0] = u.x; o[1] = u.y; o[2] = u.z; o[3] = u.w;
-    o[4] = w.x; o[5] = w.y; o[6] = w.z; o[7] = w.w;
-}
-__device__ __forceinline__ void load8(const float* s, float (&o)[8]) {
-    float4 u = *reinterpret_cast<const float4*>(s);
-    float4 w = *reinterpret_cast<const float4*>(s + 4);
-    o[0] = u.x; o[1] = u.y; o[2] = u.z; o[3] = u.w;
-    o[4] = w.x; o[5] = w.y; o[6] = w.z; o[7] = w.w;
-}
-__device__ __forceinline__ void load8(const double* s, double (&o)[8]) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        double2 u = *reinterpret_cast<const double2*>(s + 2 * q);
-        o[2 * q] = u.x;
-        o[2 * q + 1] = u.y;
-    }
+template <typename T>
+__device__ __forceinline__ T ldro(const T* p) {
+    return __ldg(p);
 }
 
-// Per-segment sums of one chunk of at most TILE nonzeros (segments = the chunk's columns or
-// rows). The tile arrives by bulk copy; `pre` runs while it is in flight, `mid` after the first
-// barrier. prod(index, value, out[NV]) gives the per-nonzero terms. On return (true) s_end holds,
-// at the local position of each segment's last nonzero, that segment's NV sums, and s_ptr the
-// local segment offsets. Returns false (CTA must exit) if the bulk copy timed out.
-template <typename T, typename A, int NV, typename Prod, typename Pre, typename Mid>
-__device__ __forceinline__ bool chunk_sums(const int* __restrict__ gidx, const T* __restrict__ gval, int koff,
-                                           int nnz, const int* __restrict__ gptr, int lo, int nseg, int kb,
-                                           unsigned char* sm, Prod prod, Pre pre, Mid mid, int* err) {
-    using L = TileLayout<T, A, NV>;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm);
-    int* s_ok = reinterpret_cast<int*>(sm + 8);
-    int* s_flag = reinterpret_cast<int*>(sm + 16);
-    int* s_idx = reinterpret_cast<int*>(sm + L::HDR);
-    T* s_val = reinterpret_cast<T*>(sm + L::HDR + TILE * 4);
-    A* s_end = reinterpret_cast<A*>(sm + L::HDR);
-    int* s_ptr = reinterpret_cast<int*>(sm + L::PTR);
-    uint32_t* s_head = reinterpret_cast<uint32_t*>(sm + L::HEAD);
-    A* s_scan = reinterpret_cast<A*>(sm + L::SCAN);
-
-    const uint32_t npad = (uint32_t)((nnz + PAD - 1) / PAD * PAD);
-    if (threadIdx.x == 0 && npad) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
-        mbar_arrive_expect_tx(bar, npad * (4u + (uint32_t)sizeof(T)));
-        bulk_g2s(s_idx, gidx + koff, npad * 4u, bar);
-        bulk_g2s(s_val, gval + koff, npad * (uint32_t)sizeof(T), bar);
-    }
-    for (int t = threadIdx.x; t <= nseg; t += NT) s_ptr[t] = gptr[lo + t] - kb;
-    for (int t = threadIdx.x; t < TILE / 32; t += NT) s_head[t] = 0u;
-    pre();
-    __syncthreads();
-    for (int t = threadIdx.x; t < nseg; t += NT) {
-        const int st = s_ptr[t];
-        if (s_ptr[t + 1] > st) atomicOr(&s_head[st >> 5], 1u << (st & 31));
-    }
-    mid();
-    if (npad) {
-        if (!cta_wait_bulk(bar, 0, s_ok, err)) return false;
-    } else {
-        __syncthreads();
-    }
-
-    const int e0 = threadIdx.x * IPT;
-    int id[IPT];
-    T vl[IPT];
-    load8(s_idx + e0, id);
-    load8(s_val + e0, vl);
+// Segment sums of one chunk held by one warp. heads: the chunk's 8-word start bitmap (bit e set
+// if a non-empty segment begins at local nonzero e). prod(index, value, out[NV]) gives the
+// per-nonzero terms. On return s_end[eslot(e)*NV + t] holds the sums of the segment whose last
+// nonzero is local item e.
+template <typename T, typename A, int NV, typename Prod>
+__device__ __forceinline__ void warp_chunk_sums(const int* __restrict__ gidx, const T* __restrict__ gval, int koff,
+                                                int nnz, const uint32_t* __restrict__ heads, A* s_end, Prod prod) {
+    const int lane = threadIdx.x & 31;
+    const int e0 = lane * IPT;
     A p[IPT][NV];
+    if (e0 < nnz) {
+        int id[IPT];
+        T vl[IPT];
+        ld256(gidx + koff + e0, id);
+        ld256(gval + koff + e0, vl);
 #pragma unroll
-    for (int q = 0; q < IPT; ++q) {
-        if (e0 + q < nnz) {
-            prod(id[q], vl[q], p[q]);
-        } else {
+        for (int q = 0; q < IPT; ++q) {
+            if (e0 + q < nnz) {
+                prod(id[q], vl[q], p[q]);
+            } else {
+#pragma unroll
+                for (int t = 0; t < NV; ++t) p[q][t] = A(0);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < IPT; ++q)
 #pragma unroll
             for (int t = 0; t < NV; ++t) p[q][t] = A(0);
-        }
     }
-    const uint32_t hb = (s_head[e0 >> 5] >> (e0 & 31)) & 0xFFu;
-    const int en = e0 + IPT;
-    const uint32_t nexth = (en < TILE) ? ((s_head[en >> 5] >> (en & 31)) & 1u) : 1u;
+    const int wi = lane >> 2;
+    const uint64_t hw = (uint64_t)__ldg(heads + wi) | ((uint64_t)(wi < 7 ? __ldg(heads + wi + 1) : 0u) << 32);
+    const uint32_t hb = (uint32_t)(hw >> ((lane & 3) * 8)) & 0x1FFu;  // items e0 .. e0+8
     Sums<A, NV> agg;
 #pragma unroll
     for (int t = 0; t < NV; ++t) agg.v[t] = A(0);
@@ -162,9 +118,7 @@ __device__ __forceinline__ bool chunk_sums(const int* __restrict__ gidx, const T
             for (int t = 0; t < NV; ++t) agg.v[t] = agg.v[t] + p[q][t];
         }
     }
-    // Every thread holds its tile entries in registers before the scan's barrier, so the end
-    // sums may overwrite the tile afterwards.
-    Sums<A, NV> acc = block_seg_carry<A, NV>(hb != 0u, agg, s_scan, s_flag);
+    Sums<A, NV> acc = warp_seg_carry<A, NV>((hb & 0xFFu) != 0u, agg);
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
         const int e = e0 + q;
@@ -176,40 +130,15 @@ __device__ __forceinline__ bool chunk_sums(const int* __restrict__ gidx, const T
 #pragma unroll
                 for (int t = 0; t < NV; ++t) acc.v[t] = acc.v[t] + p[q][t];
             }
-            const bool last = (e == nnz - 1) || ((q < IPT - 1) ? ((hb >> (q + 1)) & 1u) : nexth);
-            if (last) {
+            if (e == nnz - 1 || ((hb >> (q + 1)) & 1u)) {
 #pragma unroll
-                for (int t = 0; t < NV; ++t) s_end[e * NV + t] = acc.v[t];
+                for (int t = 0; t < NV; ++t) s_end[eslot(e) * NV + t] = acc.v[t];
             }
         }
     }
-    __syncthreads();
-    return true;
+    __syncwarp();
 }
 
-// Sums over one segment longer than TILE (a chunk of its own); result valid in thread 0.
-template <typename T, typename A, int NV, typename Prod>
-__device__ __forceinline__ Sums<A, NV> long_sums(const int* __restrict__ gidx, const T* __restrict__ gval,
-                                                 int koff, int nnz, unsigned char* sm, Prod prod) {
-    using L = TileLayout<T, A, NV>;
-    Sums<A, NV> acc;
-#pragma unroll
-    for (int t = 0; t < NV; ++t) acc.v[t] = A(0);
-    for (int e = threadIdx.x; e < nnz; e += NT) {
-        A p[NV];
-        prod(gidx[koff + e], gval[koff + e], p);
-#pragma unroll
-        for (int t = 0; t < NV; ++t) acc.v[t] = acc.v[t] + p[t];
-    }
-    return block_sum<A, NV>(acc, reinterpret_cast<A*>(sm + L::SCAN));
-}
-
-template <typename T>
-__device__ __forceinline__ T ldro(const T* p) {
-    return __ldg(p);
-}
-
-// x-step for one column plus, for an orthant coordinate, the z-step and the delta-update.
 template <typename T>
 __device__ __forceinline__ T col_x_update(T d, T xprev, T atv, T zj, T dj, T cj, T mu) {
     return (d * xprev + atv + zj + (dj - cj) / mu) / (T(1) + d);
@@ -223,114 +152,126 @@ __device__ __forceinline__ T lorentz_coord(T w, int t, T w1, T alpha) {
     return (t == 0) ? w / T(2) + alpha / T(2) : w / T(2) + w1 * w / (T(2) * alpha);
 }
 
+// Cone membership of column j of column chunk ch: 0 orthant, 1 small Lorentz cone (fused),
+// 2 Lorentz cone handled by the big-cone kernels.
+template <typename T>
+__device__ __forceinline__ int cone_tag(const SweepArgs<T>& a, int ch, int j) {
+    const int qlo = a.cq_lo[ch];
+    int lo = qlo, hi = a.cq_hi[ch];
+    while (lo < hi) {  // first cone starting after j
+        const int mid = (lo + hi) >> 1;
+        if (a.soc_start[mid] <= j)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    const int q = lo - 1;
+    if (q < qlo || j >= a.soc_start[q] + a.soc_size[q]) return 0;
+    return a.soc_big[q] ? 2 : 1;
+}
+
+// x-, z- and delta-updates of one orthant column.
+template <typename T>
+__device__ __forceinline__ void orthant_update(T* x, T* z, T* del, int j, T xn, T dj, T mu) {
+    x[j] = xn;
+    const T w = xn - dj / mu;
+    const T zn = w > T(0) ? w : T(0);
+    z[j] = zn;
+    del[j] = dj + mu * (zn - xn);
+}
+
 // ------------------------------------------------------------------------------------ column sweep
 template <typename T, bool SOC>
-__global__ void __launch_bounds__(NT) k_col_sweep(const SweepArgs<T> a) {
-    extern __shared__ __align__(128) unsigned char sm[];
-    using L = TileLayout<T, T, 1>;
-    const int ch = blockIdx.x;
-    const int j0 = a.cj0[ch], j1 = a.cj0[ch + 1], ncol = j1 - j0;
-    const int kb = a.col_ptr[j0];
-    const int nnz = a.col_ptr[j1] - kb;
-    const int koff = a.ckoff[ch];
+__global__ void __launch_bounds__(NT, MFS_SWEEP_MINB) k_col_sweep(const SweepArgs<T> a) {
+    __shared__ T s_end[NWARP][ESLOTS];
+    __shared__ T s_cone[SOC ? NWARP : 1][3][WC];  // x, w = x - delta/mu, delta of small-cone columns
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = blockIdx.x * NWARP + warp;
+    if (ch >= a.ntc) return;
+    const int4 dsc = a.cdesc[ch];
+    const int lo = dsc.x, nseg = dsc.y - dsc.x, koff = dsc.z, nnz = dsc.w;
+    if (nnz > WT) return;  // long chunk: k_col_long
     const T mu = a.mu;
+    int cs[CPL], ce[CPL];
+    T px[CPL], pz[CPL], pd[CPL], pc[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        const int jl = lane + 32 * k;
+        cs[k] = ce[k] = 0;
+        px[k] = pz[k] = pd[k] = pc[k] = T(0);
+        if (jl < nseg) {
+            const int j = lo + jl;
+            cs[k] = a.col_ptr[j];
+            ce[k] = a.col_ptr[j + 1];
+            px[k] = a.x[j];
+            pz[k] = a.z[j];
+            pd[k] = a.del[j];
+            pc[k] = a.c[j];
+        }
+    }
+    const int kb = __shfl_sync(FULL, cs[0], 0);
     const T* __restrict__ v = a.v;
     auto prod = [v](int i, T val, T (&p)[1]) { p[0] = val * ldro(v + i); };
-
-    if (nnz > TILE) {  // one long column
-        Sums<T, 1> s = long_sums<T, T, 1>(a.cidx, a.cval, koff, nnz, sm, prod);
-        if (threadIdx.x == 0) {
-            const int j = j0;
-            const T d = T(nnz);
-            const T dj = a.del[j];
-            const T xn = col_x_update(d, a.x[j], s.v[0], a.z[j], dj, a.c[j], mu);
-            a.x[j] = xn;
-            const bool in_cone = SOC && (a.cq_hi[ch] > a.cq_lo[ch]);  // then it is a big cone's
-            if (!in_cone) {
-                const T w = xn - dj / mu;
-                const T zn = w > T(0) ? w : T(0);
-                a.z[j] = zn;
-                a.del[j] = dj + mu * (zn - xn);
-            }
-        }
-        return;
-    }
-
-    T* s_x = reinterpret_cast<T*>(sm + L::EXTRA);
-    T* s_w = s_x + CMAX;
-    T* s_d = s_w + CMAX;
-    unsigned char* s_tag = reinterpret_cast<unsigned char*>(s_d + CMAX);
-
-    T px[CPT], pz[CPT], pd[CPT], pc[CPT];
-    auto pre = [&]() {
+    warp_chunk_sums<T, T, 1>(a.cidx, a.cval, koff, nnz, a.cheads + (size_t)ch * 8, s_end[warp], prod);
 #pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-            const int jl = threadIdx.x + q * NT;
-            if (jl < ncol) {
-                px[q] = a.x[j0 + jl];
-                pz[q] = a.z[j0 + jl];
-                pd[q] = a.del[j0 + jl];
-                pc[q] = a.c[j0 + jl];
-            }
-        }
-        if (SOC)
-            for (int t = threadIdx.x; t < ncol; t += NT) s_tag[t] = 0;
-    };
-    auto mid = [&]() {
-        if (SOC) {
-            __syncthreads();  // s_tag cleared
-            for (int q = a.cq_lo[ch] + threadIdx.x; q < a.cq_hi[ch]; q += NT) {
-                const int cs = a.soc_start[q], ce = cs + a.soc_size[q];
-                const int st = (cs > j0 ? cs : j0) - j0, en = (ce < j1 ? ce : j1) - j0;
-                const unsigned char tag = a.soc_big[q] ? 2 : 1;
-                for (int t = st; t < en; ++t) s_tag[t] = tag;
-            }
-        }
-    };
-    if (!chunk_sums<T, T, 1>(a.cidx, a.cval, koff, nnz, a.col_ptr, j0, ncol, kb, sm, prod, pre, mid, a.err))
-        return;
-    const T* s_end = reinterpret_cast<const T*>(sm + L::HDR);
-    const int* s_ptr = reinterpret_cast<const int*>(sm + L::PTR);
-#pragma unroll
-    for (int q = 0; q < CPT; ++q) {
-        const int jl = threadIdx.x + q * NT;
-        if (jl < ncol) {
-            const int st = s_ptr[jl], en = s_ptr[jl + 1];
-            const T atv = (en > st) ? s_end[en - 1] : T(0);
-            const T xn = col_x_update(T(en - st), px[q], atv, pz[q], pd[q], pc[q], mu);
-            const int j = j0 + jl;
-            a.x[j] = xn;
-            const unsigned char tag = SOC ? s_tag[jl] : 0;
+    for (int k = 0; k < CPL; ++k) {
+        const int jl = lane + 32 * k;
+        if (jl < nseg) {
+            const T atv = (ce[k] > cs[k]) ? s_end[warp][eslot(ce[k] - 1 - kb)] : T(0);
+            const T xn = col_x_update(T(ce[k] - cs[k]), px[k], atv, pz[k], pd[k], pc[k], mu);
+            const int j = lo + jl;
+            const int tag = SOC ? cone_tag(a, ch, j) : 0;
             if (tag == 0) {
-                const T w = xn - pd[q] / mu;
-                const T zn = w > T(0) ? w : T(0);
-                a.z[j] = zn;
-                a.del[j] = pd[q] + mu * (zn - xn);
-            } else if (tag == 1) {
-                s_x[jl] = xn;
-                s_w[jl] = xn - pd[q] / mu;
-                s_d[jl] = pd[q];
+                orthant_update(a.x, a.z, a.del, j, xn, pd[k], mu);
+            } else {
+                a.x[j] = xn;
+                if (tag == 1) {
+                    s_cone[SOC ? warp : 0][0][jl] = xn;
+                    s_cone[SOC ? warp : 0][1][jl] = xn - pd[k] / mu;
+                    s_cone[SOC ? warp : 0][2][jl] = pd[k];
+                }
             }
         }
     }
     if (SOC) {
-        __syncthreads();
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int q = a.cq_lo[ch] + warp; q < a.cq_hi[ch]; q += NWARP) {
+        __syncwarp();
+        // one lane per small cone of the chunk: z-step (eq. proj) and delta-update
+        const T* cx = s_cone[warp][0];
+        const T* cw = s_cone[warp][1];
+        const T* cd = s_cone[warp][2];
+        for (int q = a.cq_lo[ch] + lane; q < a.cq_hi[ch]; q += 32) {
             if (a.soc_big[q]) continue;
-            const int st = a.soc_start[q] - j0, sz = a.soc_size[q];
+            const int c0 = a.soc_start[q] - lo, sz = a.soc_size[q];
             T ss = T(0);
-            for (int t = 1 + lane; t < sz; t += 32) ss += s_w[st + t] * s_w[st + t];
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, d);
-            const T alpha = sqrt(ss);
-            const T w1 = s_w[st];
-            for (int t = lane; t < sz; t += 32) {
-                const T zt = lorentz_coord(s_w[st + t], t, w1, alpha);
-                a.z[j0 + st + t] = zt;
-                a.del[j0 + st + t] = s_d[st + t] + mu * (zt - s_x[st + t]);
+            for (int t = 1; t < sz; ++t) ss += cw[c0 + t] * cw[c0 + t];
+            const T alpha = sqrt(ss), w1 = cw[c0];
+            for (int t = 0; t < sz; ++t) {
+                const T zt = lorentz_coord(cw[c0 + t], t, w1, alpha);
+                a.z[lo + c0 + t] = zt;
+                a.del[lo + c0 + t] = cd[c0 + t] + mu * (zt - cx[c0 + t]);
             }
         }
+    }
+}
+
+// A column longer than one chunk: one CTA reduces it and runs its epilogue.
+template <typename T, bool SOC>
+__global__ void __launch_bounds__(NT) k_col_long(const SweepArgs<T> a) {
+    __shared__ T sh[NWARP];
+    const int ch = a.clong[blockIdx.x];
+    const int4 dsc = a.cdesc[ch];
+    const int j = dsc.x, koff = dsc.z, nnz = dsc.w;
+    Sums<T, 1> s;
+    s.v[0] = T(0);
+    for (int e = threadIdx.x; e < nnz; e += NT) s.v[0] += a.cval[koff + e] * ldro(a.v + a.cidx[koff + e]);
+    s = block_sum<T, 1>(s, sh);
+    if (threadIdx.x == 0) {
+        const T mu = a.mu, dj = a.del[j];
+        const T xn = col_x_update(T(nnz), a.x[j], s.v[0], a.z[j], dj, a.c[j], mu);
+        if (SOC && cone_tag(a, ch, j) != 0)  // then part of a big cone
+            a.x[j] = xn;
+        else
+            orthant_update(a.x, a.z, a.del, j, xn, dj, mu);
     }
 }
 
@@ -363,83 +304,125 @@ __global__ void __launch_bounds__(NT) k_bigcone_sweep(const SweepArgs<T> a) {
 }
 
 // ------------------------------------------------------------------------------------ row sweep
-// MODE 0: iteration (lambda and v updated). MODE 1: warm start (v from x and a given lambda).
+// MODE 0: iteration (lambda and v updated). MODE 1: v from x and the current lambda (warm start,
+// change of mu).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(NT) k_row_sweep(const SweepArgs<T> a) {
-    extern __shared__ __align__(128) unsigned char sm[];
-    using L = TileLayout<T, T, 2>;
-    const int ch = blockIdx.x;
-    const int i0 = a.ri0[ch], i1 = a.ri0[ch + 1], nrow = i1 - i0;
-    const int kb = a.row_ptr[i0];
-    const int nnz = a.row_ptr[i1] - kb;
-    const int koff = a.rkoff[ch];
+__device__ __forceinline__ void row_update(const SweepArgs<T>& a, int i, T ax, T r, T bi, T li) {
     const T mu = a.mu;
+    const T rho = (bi - ax) / (T(1) + r);
+    if (MODE == 0) {
+        const T ln = li - mu * rho;
+        a.lam[i] = ln;
+        a.v[i] = rho - ln / mu;
+    } else {
+        a.v[i] = rho - li / mu;
+    }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(NT, MFS_SWEEP_MINB) k_row_sweep(const SweepArgs<T> a) {
+    __shared__ T s_end[NWARP][2 * ESLOTS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = blockIdx.x * NWARP + warp;
+    if (ch >= a.ntr) return;
+    const int4 dsc = a.rdesc[ch];
+    const int lo = dsc.x, nseg = dsc.y - dsc.x, koff = dsc.z, nnz = dsc.w;
+    if (nnz > WT) return;  // long chunk: k_row_long
+    int cs[CPL], ce[CPL];
+    T pb[CPL], pl[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        const int il = lane + 32 * k;
+        cs[k] = ce[k] = 0;
+        pb[k] = pl[k] = T(0);
+        if (il < nseg) {
+            const int i = lo + il;
+            cs[k] = a.row_ptr[i];
+            ce[k] = a.row_ptr[i + 1];
+            pb[k] = a.b[i];
+            pl[k] = a.lam[i];
+        }
+    }
+    const int kb = __shfl_sync(FULL, cs[0], 0);
     const T* __restrict__ x = a.x;
     auto prod = [x](int j, T val, T (&p)[2]) {
         p[0] = val * ldro(x + j);
         p[1] = val * val;
     };
-    if (nnz > TILE) {
-        Sums<T, 2> s = long_sums<T, T, 2>(a.ridx, a.rval, koff, nnz, sm, prod);
-        if (threadIdx.x == 0) {
-            const T rho = (a.b[i0] - s.v[0]) / (T(1) + s.v[1]);
-            const T l = a.lam[i0];
-            if (MODE == 0) {
-                const T ln = l - mu * rho;
-                a.lam[i0] = ln;
-                a.v[i0] = rho - ln / mu;
-            } else {
-                a.v[i0] = rho - l / mu;
-            }
-        }
-        return;
-    }
-    T pb[CPT], pl[CPT];
-    auto pre = [&]() {
+    warp_chunk_sums<T, T, 2>(a.ridx, a.rval, koff, nnz, a.rheads + (size_t)ch * 8, s_end[warp], prod);
 #pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-            const int il = threadIdx.x + q * NT;
-            if (il < nrow) {
-                pb[q] = a.b[i0 + il];
-                pl[q] = a.lam[i0 + il];
-            }
-        }
-    };
-    auto mid = []() {};
-    if (!chunk_sums<T, T, 2>(a.ridx, a.rval, koff, nnz, a.row_ptr, i0, nrow, kb, sm, prod, pre, mid, a.err))
-        return;
-    const T* s_end = reinterpret_cast<const T*>(sm + L::HDR);
-    const int* s_ptr = reinterpret_cast<const int*>(sm + L::PTR);
-#pragma unroll
-    for (int q = 0; q < CPT; ++q) {
-        const int il = threadIdx.x + q * NT;
-        if (il < nrow) {
-            const int st = s_ptr[il], en = s_ptr[il + 1];
-            const T ax = (en > st) ? s_end[2 * (en - 1)] : T(0);
-            const T r = (en > st) ? s_end[2 * (en - 1) + 1] : T(0);
-            const T rho = (pb[q] - ax) / (T(1) + r);
-            const int i = i0 + il;
-            if (MODE == 0) {
-                const T ln = pl[q] - mu * rho;
-                a.lam[i] = ln;
-                a.v[i] = rho - ln / mu;
-            } else {
-                a.v[i] = rho - pl[q] / mu;
-            }
+    for (int k = 0; k < CPL; ++k) {
+        const int il = lane + 32 * k;
+        if (il < nseg) {
+            const bool ne = ce[k] > cs[k];
+            const int e = eslot(ce[k] - 1 - kb);
+            row_update<T, MODE>(a, lo + il, ne ? s_end[warp][2 * e] : T(0), ne ? s_end[warp][2 * e + 1] : T(0), pb[k],
+                                pl[k]);
         }
     }
 }
 
+template <typename T, int MODE>
+__global__ void __launch_bounds__(NT) k_row_long(const SweepArgs<T> a) {
+    __shared__ T sh[2 * NWARP];
+    const int ch = a.rlong[blockIdx.x];
+    const int4 dsc = a.rdesc[ch];
+    const int i = dsc.x, koff = dsc.z, nnz = dsc.w;
+    Sums<T, 2> s;
+    s.v[0] = s.v[1] = T(0);
+    for (int e = threadIdx.x; e < nnz; e += NT) {
+        const T val = a.rval[koff + e];
+        s.v[0] += val * ldro(a.x + a.ridx[koff + e]);
+        s.v[1] += val * val;
+    }
+    s = block_sum<T, 2>(s, sh);
+    if (threadIdx.x == 0) row_update<T, MODE>(a, i, s.v[0], s.v[1], a.b[i], a.lam[i]);
+}
+
 // ------------------------------------------------------------------------------------ residuals
-// Partial-sum fields, one row of NF doubles per CTA.
-enum : int {
-    F_RES2 = 0, F_RESMAX, F_AXMAX, F_B2, F_BMAX, F_BLAM,
-    F_S2, F_SMAX, F_ATLMAX, F_C2, F_CMAX, F_CX, F_X2, F_SDIST2, F_XDIST2,
-    NF = 16
+// Per-nonzero products and per-segment sums of the residual kernels: exact FP32 products summed
+// as float pairs when the data are FP32 (then converted to FP64), plain FP64 when they are FP64.
+template <typename T>
+struct AccOf {
+    using type = DF;
+};
+template <>
+struct AccOf<double> {
+    using type = double;
 };
 
-__device__ __forceinline__ bool field_is_max(int f) {
-    return f == F_RESMAX || f == F_AXMAX || f == F_BMAX || f == F_SMAX || f == F_ATLMAX || f == F_CMAX;
+__device__ __forceinline__ DF acc_prod(float a, float b) {
+    return df_prod(a, b);
+}
+__device__ __forceinline__ double acc_prod(double a, double b) {
+    return a * b;
+}
+
+// Sum of a_k * w[idx_k] over one long segment by one warp (lane-strided, fixed order).
+template <typename T>
+__device__ __forceinline__ double warp_long_dot(const int* __restrict__ gidx, const T* __restrict__ gval, int koff,
+                                                int nnz, const T* __restrict__ w) {
+    using A = typename AccOf<T>::type;
+    const int lane = threadIdx.x & 31;
+    A acc = A(0);
+    for (int e = lane; e < nnz; e += 32) acc = acc + acc_prod(gval[koff + e], ldro(w + gidx[koff + e]));
+    double d = to_double(acc);
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) d += __shfl_xor_sync(FULL, d, k);
+    return d;
+}
+
+// Row-side fields (sums of squares and maxima of |.|), column-side fields and big-cone fields;
+// each residual CTA writes one value per field, field-major: part[f * grid + cta].
+enum : int { R_RES2 = 0, R_RESMAX, R_AXMAX, R_B2, R_BMAX, R_BLAM, NFR };
+enum : int { C_S2 = 0, C_SMAX, C_ATLMAX, C_C2, C_CMAX, C_CX, C_X2, C_SDIST2, C_XDIST2, NFC };
+enum : int { B_SDIST2 = 0, B_XDIST2, NFB };
+
+__host__ __device__ constexpr bool row_field_is_max(int f) {
+    return f == R_RESMAX || f == R_AXMAX || f == R_BMAX;
+}
+__host__ __device__ constexpr bool col_field_is_max(int f) {
+    return f == C_SMAX || f == C_ATLMAX || f == C_CMAX;
 }
 
 // Squared distance of w to one Lorentz cone, given w_1 and alpha = ||w_{2..}||
@@ -451,187 +434,199 @@ __device__ __forceinline__ double lorentz_dist2(double w1, double alpha, double 
     return 0.5 * g * g;
 }
 
-__device__ __forceinline__ void write_partials(double* out, double (&f)[NF], double* sh) {
-    for (int k = 0; k < NF; ++k) {
-        double r;
-        if (field_is_max(k)) {
-            r = block_max(f[k], sh);
-        } else {
-            Sums<double, 1> s;
-            s.v[0] = f[k];
-            r = block_sum<double, 1>(s, sh).v[0];
+// Fold the lanes' NFIELD accumulators into one value per field for the CTA (fixed order).
+template <int NFIELD, bool ROW>
+__device__ __forceinline__ bool field_max(int k) {
+    return ROW ? row_field_is_max(k) : col_field_is_max(k);
+}
+
+template <int NFIELD, bool ROW>
+__device__ __forceinline__ void cta_fields_out(double (&f)[NFIELD], double (*sh)[NFIELD], double* part) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NFIELD; ++k) {
+        double v = f[k];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const double o = __shfl_down_sync(FULL, v, d);
+            v = field_max<NFIELD, ROW>(k) ? fmax(v, o) : v + o;
         }
-        if (threadIdx.x == 0) out[k] = r;
+        if (lane == 0) sh[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NFIELD) {
+        const int k = threadIdx.x;
+        double acc = 0.0;
+        for (int w = 0; w < NWARP; ++w) acc = field_max<NFIELD, ROW>(k) ? fmax(acc, sh[w][k]) : acc + sh[w][k];
+        part[(size_t)k * gridDim.x + blockIdx.x] = acc;
     }
 }
 
 struct ResidArgs {
-    double* part_row;  // row chunks x NF
-    double* part_col;  // column chunks x NF
-    double* part_big;  // big cones x NF
+    double* part_row;  // NFR x (row-residual grid)
+    double* part_col;  // NFC x (column-residual grid)
+    double* part_big;  // NFB x (big cones)
     double* s_buf;     // n: c + A^T lambda (FP64), written for big-cone columns (all if write_all_s)
     int write_all_s;
 };
 
+// FP64 row-side residual fields: ||Ax - b||, max|Ax - b|, max|Ax|, ||b||, max|b|, b^T lambda.
+// Persistent warps walk the row chunks.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_row_resid(const SweepArgs<T> a, const ResidArgs r) {
-    extern __shared__ __align__(128) unsigned char sm[];
-    using L = TileLayout<T, double, 1>;
-    const int ch = blockIdx.x;
-    const int i0 = a.ri0[ch], i1 = a.ri0[ch + 1], nrow = i1 - i0;
-    const int kb = a.row_ptr[i0];
-    const int nnz = a.row_ptr[i1] - kb;
-    const int koff = a.rkoff[ch];
-    const T* __restrict__ x = a.x;
-    auto prod = [x](int j, T val, double (&p)[1]) { p[0] = double(val) * double(ldro(x + j)); };
-    double f[NF];
+    using A = typename AccOf<T>::type;
+    __shared__ A s_end[NWARP][ESLOTS];
+    __shared__ double s_red[NWARP][NFR];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double f[NFR];
 #pragma unroll
-    for (int k = 0; k < NF; ++k) f[k] = 0.0;
-    double* shred = reinterpret_cast<double*>(sm + L::EXTRA);
-    if (nnz > TILE) {
-        Sums<double, 1> s = long_sums<T, double, 1>(a.ridx, a.rval, koff, nnz, sm, prod);
-        if (threadIdx.x == 0) {
-            const double bi = double(a.b[i0]);
-            const double res = s.v[0] - bi;
-            f[F_RES2] = res * res;
-            f[F_RESMAX] = fabs(res);
-            f[F_AXMAX] = fabs(s.v[0]);
-            f[F_B2] = bi * bi;
-            f[F_BMAX] = fabs(bi);
-            f[F_BLAM] = bi * double(a.lam[i0]);
+    for (int k = 0; k < NFR; ++k) f[k] = 0.0;
+    const T* __restrict__ x = a.x;
+    auto prod = [x](int j, T val, A (&p)[1]) { p[0] = acc_prod(val, ldro(x + j)); };
+    for (int ch = blockIdx.x * NWARP + warp; ch < a.ntr; ch += gridDim.x * NWARP) {
+        const int4 dsc = a.rdesc[ch];
+        const int lo = dsc.x, nseg = dsc.y - dsc.x, koff = dsc.z, nnz = dsc.w;
+        double ax[CPL];
+        int rows[CPL];
+        if (nnz > WT) {  // one long row: the warp sums it
+            ax[0] = warp_long_dot(a.ridx, a.rval, koff, nnz, x);
+            rows[0] = (lane == 0) ? lo : -1;
+#pragma unroll
+            for (int k = 1; k < CPL; ++k) rows[k] = -1;
+        } else {
+            int cs[CPL], ce[CPL];
+#pragma unroll
+            for (int k = 0; k < CPL; ++k) {
+                const int il = lane + 32 * k;
+                cs[k] = ce[k] = 0;
+                if (il < nseg) {
+                    cs[k] = a.row_ptr[lo + il];
+                    ce[k] = a.row_ptr[lo + il + 1];
+                }
+            }
+            const int kb = __shfl_sync(FULL, cs[0], 0);
+            warp_chunk_sums<T, A, 1>(a.ridx, a.rval, koff, nnz, a.rheads + (size_t)ch * 8, s_end[warp], prod);
+#pragma unroll
+            for (int k = 0; k < CPL; ++k) {
+                const int il = lane + 32 * k;
+                rows[k] = il < nseg ? lo + il : -1;
+                ax[k] = (il < nseg && ce[k] > cs[k]) ? to_double(s_end[warp][eslot(ce[k] - 1 - kb)]) : 0.0;
+            }
+            __syncwarp();
         }
-        write_partials(r.part_row + (size_t)ch * NF, f, shred);
-        return;
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+            if (rows[k] < 0) continue;
+            const double bi = double(a.b[rows[k]]), res = ax[k] - bi;
+            f[R_RES2] += res * res;
+            f[R_RESMAX] = fmax(f[R_RESMAX], fabs(res));
+            f[R_AXMAX] = fmax(f[R_AXMAX], fabs(ax[k]));
+            f[R_B2] += bi * bi;
+            f[R_BMAX] = fmax(f[R_BMAX], fabs(bi));
+            f[R_BLAM] += bi * double(a.lam[rows[k]]);
+        }
     }
-    auto none = []() {};
-    if (!chunk_sums<T, double, 1>(a.ridx, a.rval, koff, nnz, a.row_ptr, i0, nrow, kb, sm, prod, none, none,
-                                  a.err))
-        return;
-    const double* s_end = reinterpret_cast<const double*>(sm + L::HDR);
-    const int* s_ptr = reinterpret_cast<const int*>(sm + L::PTR);
-    for (int il = threadIdx.x; il < nrow; il += NT) {
-        const int st = s_ptr[il], en = s_ptr[il + 1];
-        const double ax = (en > st) ? s_end[en - 1] : 0.0;
-        const double bi = double(a.b[i0 + il]);
-        const double res = ax - bi;
-        f[F_RES2] += res * res;
-        f[F_RESMAX] = fmax(f[F_RESMAX], fabs(res));
-        f[F_AXMAX] = fmax(f[F_AXMAX], fabs(ax));
-        f[F_B2] += bi * bi;
-        f[F_BMAX] = fmax(f[F_BMAX], fabs(bi));
-        f[F_BLAM] += bi * double(a.lam[i0 + il]);
-    }
-    write_partials(r.part_row + (size_t)ch * NF, f, shred);
+    cta_fields_out<NFR, true>(f, s_red, r.part_row);
 }
 
+// FP64 column-side residual fields: with s = c + A^T lambda, ||s||, max|s|, max|A^T lambda|,
+// ||c||, max|c|, c^T x, ||x||, dist(s, K)^2 and dist(x, K)^2 (small cones fused; big cones get s
+// in s_buf for k_bigcone_resid). Persistent warps walk the column chunks.
 template <typename T, bool SOC>
 __global__ void __launch_bounds__(NT) k_col_resid(const SweepArgs<T> a, const ResidArgs r) {
-    extern __shared__ __align__(128) unsigned char sm[];
-    using L = TileLayout<T, double, 1>;
-    const int ch = blockIdx.x;
-    const int j0 = a.cj0[ch], j1 = a.cj0[ch + 1], ncol = j1 - j0;
-    const int kb = a.col_ptr[j0];
-    const int nnz = a.col_ptr[j1] - kb;
-    const int koff = a.ckoff[ch];
+    using A = typename AccOf<T>::type;
+    __shared__ A s_end[NWARP][ESLOTS];
+    __shared__ double s_red[NWARP][NFC];
+    __shared__ double s_cone[SOC ? NWARP : 1][2][WC];  // s and x of small-cone columns
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double f[NFC];
+#pragma unroll
+    for (int k = 0; k < NFC; ++k) f[k] = 0.0;
     const T* __restrict__ lam = a.lam;
-    auto prod = [lam](int i, T val, double (&p)[1]) { p[0] = double(val) * double(ldro(lam + i)); };
-    double f[NF];
+    auto prod = [lam](int i, T val, A (&p)[1]) { p[0] = acc_prod(val, ldro(lam + i)); };
+    for (int ch = blockIdx.x * NWARP + warp; ch < a.ntc; ch += gridDim.x * NWARP) {
+        const int4 dsc = a.cdesc[ch];
+        const int lo = dsc.x, nseg = dsc.y - dsc.x, koff = dsc.z, nnz = dsc.w;
+        double atl[CPL];
+        int cols[CPL];
+        if (nnz > WT) {  // one long column: the warp sums it
+            atl[0] = warp_long_dot(a.cidx, a.cval, koff, nnz, lam);
+            cols[0] = (lane == 0) ? 0 : -1;
 #pragma unroll
-    for (int k = 0; k < NF; ++k) f[k] = 0.0;
-    double* shred = reinterpret_cast<double*>(sm + L::EXTRA);
-    double* s_s = shred + 2 * NWARP;  // CMAX
-    double* s_xv = s_s + CMAX;        // CMAX
-    unsigned char* s_tag = reinterpret_cast<unsigned char*>(s_xv + CMAX);
-
-    // per-column work shared by the two paths; tag 0 orthant, 1 small cone, 2 big cone
-    auto column = [&](int jl, double atl, unsigned char tag) {
-        const int j = j0 + jl;
-        const double cj = double(a.c[j]), xj = double(a.x[j]);
-        const double s = cj + atl;
-        f[F_S2] += s * s;
-        f[F_SMAX] = fmax(f[F_SMAX], fabs(s));
-        f[F_ATLMAX] = fmax(f[F_ATLMAX], fabs(atl));
-        f[F_C2] += cj * cj;
-        f[F_CMAX] = fmax(f[F_CMAX], fabs(cj));
-        f[F_CX] += cj * xj;
-        f[F_X2] += xj * xj;
-        if (tag == 0) {
-            const double sn = s < 0.0 ? s : 0.0, xn = xj < 0.0 ? xj : 0.0;
-            f[F_SDIST2] += sn * sn;
-            f[F_XDIST2] += xn * xn;
-        } else if (tag == 1) {
-            s_s[jl] = s;
-            s_xv[jl] = xj;
-        }
-        if (tag == 2 || r.write_all_s) r.s_buf[j] = s;
-    };
-
-    if (nnz > TILE) {
-        Sums<double, 1> s = long_sums<T, double, 1>(a.cidx, a.cval, koff, nnz, sm, prod);
-        if (threadIdx.x == 0) {
-            const bool in_cone = SOC && (a.cq_hi[ch] > a.cq_lo[ch]);
-            column(0, s.v[0], in_cone ? 2 : 0);
-        }
-        write_partials(r.part_col + (size_t)ch * NF, f, shred);
-        return;
-    }
-    auto pre = [&]() {
-        if (SOC)
-            for (int t = threadIdx.x; t < ncol; t += NT) s_tag[t] = 0;
-    };
-    auto mid = [&]() {
-        if (SOC) {
-            __syncthreads();
-            for (int q = a.cq_lo[ch] + threadIdx.x; q < a.cq_hi[ch]; q += NT) {
-                const int cs = a.soc_start[q], ce = cs + a.soc_size[q];
-                const int st = (cs > j0 ? cs : j0) - j0, en = (ce < j1 ? ce : j1) - j0;
-                const unsigned char tag = a.soc_big[q] ? 2 : 1;
-                for (int t = st; t < en; ++t) s_tag[t] = tag;
-            }
-        }
-    };
-    if (!chunk_sums<T, double, 1>(a.cidx, a.cval, koff, nnz, a.col_ptr, j0, ncol, kb, sm, prod, pre, mid, a.err))
-        return;
-    const double* s_end = reinterpret_cast<const double*>(sm + L::HDR);
-    const int* s_ptr = reinterpret_cast<const int*>(sm + L::PTR);
-    for (int jl = threadIdx.x; jl < ncol; jl += NT) {
-        const int st = s_ptr[jl], en = s_ptr[jl + 1];
-        column(jl, (en > st) ? s_end[en - 1] : 0.0, SOC ? s_tag[jl] : 0);
-    }
-    if (SOC) {
-        __syncthreads();
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        double dsum_s = 0.0, dsum_x = 0.0;
-        for (int q = a.cq_lo[ch] + warp; q < a.cq_hi[ch]; q += NWARP) {
-            if (a.soc_big[q]) continue;
-            const int st = a.soc_start[q] - j0, sz = a.soc_size[q];
-            double ss = 0.0, xx = 0.0;
-            for (int t = 1 + lane; t < sz; t += 32) {
-                ss += s_s[st + t] * s_s[st + t];
-                xx += s_xv[st + t] * s_xv[st + t];
-            }
+            for (int k = 1; k < CPL; ++k) cols[k] = -1;
+        } else {
+            int cs[CPL], ce[CPL];
 #pragma unroll
-            for (int d = 16; d > 0; d >>= 1) {
-                ss += __shfl_xor_sync(0xffffffffu, ss, d);
-                xx += __shfl_xor_sync(0xffffffffu, xx, d);
+            for (int k = 0; k < CPL; ++k) {
+                const int jl = lane + 32 * k;
+                cs[k] = ce[k] = 0;
+                if (jl < nseg) {
+                    cs[k] = a.col_ptr[lo + jl];
+                    ce[k] = a.col_ptr[lo + jl + 1];
+                }
             }
-            if (lane == 0) {
-                const double s1 = s_s[st], x1 = s_xv[st];
-                dsum_s += lorentz_dist2(s1, sqrt(ss), ss + s1 * s1);
-                dsum_x += lorentz_dist2(x1, sqrt(xx), xx + x1 * x1);
+            const int kb = __shfl_sync(FULL, cs[0], 0);
+            warp_chunk_sums<T, A, 1>(a.cidx, a.cval, koff, nnz, a.cheads + (size_t)ch * 8, s_end[warp], prod);
+#pragma unroll
+            for (int k = 0; k < CPL; ++k) {
+                const int jl = lane + 32 * k;
+                cols[k] = jl < nseg ? jl : -1;
+                atl[k] = (jl < nseg && ce[k] > cs[k]) ? to_double(s_end[warp][eslot(ce[k] - 1 - kb)]) : 0.0;
             }
+            __syncwarp();
         }
-        f[F_SDIST2] += dsum_s;
-        f[F_XDIST2] += dsum_x;
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+            const int jl = cols[k];
+            if (jl < 0) continue;
+            const int j = lo + jl;
+            const double cj = double(a.c[j]), xj = double(a.x[j]);
+            const double s = cj + atl[k];
+            f[C_S2] += s * s;
+            f[C_SMAX] = fmax(f[C_SMAX], fabs(s));
+            f[C_ATLMAX] = fmax(f[C_ATLMAX], fabs(atl[k]));
+            f[C_C2] += cj * cj;
+            f[C_CMAX] = fmax(f[C_CMAX], fabs(cj));
+            f[C_CX] += cj * xj;
+            f[C_X2] += xj * xj;
+            const int tag = SOC ? cone_tag(a, ch, j) : 0;
+            if (tag == 0) {
+                const double sn = s < 0.0 ? s : 0.0, xn = xj < 0.0 ? xj : 0.0;
+                f[C_SDIST2] += sn * sn;
+                f[C_XDIST2] += xn * xn;
+            } else if (tag == 1) {
+                s_cone[SOC ? warp : 0][0][jl] = s;
+                s_cone[SOC ? warp : 0][1][jl] = xj;
+            }
+            if (tag == 2 || r.write_all_s) r.s_buf[j] = s;
+        }
+        if (SOC && nnz <= WT) {
+            __syncwarp();
+            const double* cs_ = s_cone[warp][0];
+            const double* cx_ = s_cone[warp][1];
+            for (int q = a.cq_lo[ch] + lane; q < a.cq_hi[ch]; q += 32) {
+                if (a.soc_big[q]) continue;
+                const int c0 = a.soc_start[q] - lo, sz = a.soc_size[q];
+                double ss = 0.0, xx = 0.0;
+                for (int t = 1; t < sz; ++t) {
+                    ss += cs_[c0 + t] * cs_[c0 + t];
+                    xx += cx_[c0 + t] * cx_[c0 + t];
+                }
+                const double s1 = cs_[c0], x1 = cx_[c0];
+                f[C_SDIST2] += lorentz_dist2(s1, sqrt(ss), ss + s1 * s1);
+                f[C_XDIST2] += lorentz_dist2(x1, sqrt(xx), xx + x1 * x1);
+            }
+            __syncwarp();
+        }
     }
-    write_partials(r.part_col + (size_t)ch * NF, f, shred);
+    cta_fields_out<NFC, false>(f, s_red, r.part_col);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) k_bigcone_resid(const SweepArgs<T> a, const ResidArgs r) {
+__global__ void __launch_bounds__(NT) k_bigcone_resid(const SweepArgs<T> a, const ResidArgs r, int nbig) {
     __shared__ double sh[2 * NWARP];
-    const int b = blockIdx.x;
-    const int q = a.big_list[b];
+    const int bq = blockIdx.x;
+    const int q = a.big_list[bq];
     const int st = a.soc_start[q], sz = a.soc_size[q];
     Sums<double, 2> acc;
     acc.v[0] = 0.0;
@@ -643,11 +638,9 @@ __global__ void __launch_bounds__(NT) k_bigcone_resid(const SweepArgs<T> a, cons
     }
     acc = block_sum<double, 2>(acc, sh);
     if (threadIdx.x == 0) {
-        double* out = r.part_big + (size_t)b * NF;
-        for (int k = 0; k < NF; ++k) out[k] = 0.0;
         const double s1 = r.s_buf[st], x1 = double(a.x[st]);
-        out[F_SDIST2] = lorentz_dist2(s1, sqrt(acc.v[0]), acc.v[0] + s1 * s1);
-        out[F_XDIST2] = lorentz_dist2(x1, sqrt(acc.v[1]), acc.v[1] + x1 * x1);
+        r.part_big[(size_t)B_SDIST2 * nbig + bq] = lorentz_dist2(s1, sqrt(acc.v[0]), acc.v[0] + s1 * s1);
+        r.part_big[(size_t)B_XDIST2 * nbig + bq] = lorentz_dist2(x1, sqrt(acc.v[1]), acc.v[1] + x1 * x1);
     }
 }
 
@@ -663,41 +656,48 @@ __device__ __forceinline__ double nanmax(double p, double q) {
     return (p > q || p != p) ? p : q;
 }
 
-__global__ void __launch_bounds__(NT) k_resid_finalize(const double* part_row, int nrow_parts,
-                                                       const double* part_col, int ncol_parts,
-                                                       const double* part_big, int nbig, double* status) {
-    __shared__ double sh[NWARP];
-    __shared__ double tot[NF];
-    for (int k = 0; k < NF; ++k) {
-        const bool ismax = field_is_max(k);
-        double acc = 0.0;
-        for (int i = threadIdx.x; i < nrow_parts; i += NT) {
-            const double v = part_row[(size_t)i * NF + k];
-            acc = ismax ? nanmax(acc, v) : acc + v;
-        }
-        for (int i = threadIdx.x; i < ncol_parts; i += NT) {
-            const double v = part_col[(size_t)i * NF + k];
-            acc = ismax ? nanmax(acc, v) : acc + v;
-        }
-        for (int i = threadIdx.x; i < nbig; i += NT) {
-            const double v = part_big[(size_t)i * NF + k];
-            acc = ismax ? nanmax(acc, v) : acc + v;
-        }
-        double r;
-        if (ismax) {
-            r = block_max(acc, sh);
-        } else {
-            Sums<double, 1> s;
-            s.v[0] = acc;
-            r = block_sum<double, 1>(s, sh).v[0];
-        }
-        if (threadIdx.x == 0) tot[k] = r;
+constexpr int NFALL = NFR + NFC + NFB;
+
+// One warp per field folds the per-CTA values in a fixed order; thread 0 then forms the relative
+// residuals. Launch with 32 * NFALL threads.
+__global__ void __launch_bounds__(32 * NFALL) k_resid_finalize(const double* part_row, int gr, const double* part_col,
+                                                               int gc, const double* part_big, int nbig,
+                                                               double* status) {
+    __shared__ double tot[NFALL];
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double* src;
+    int cnt;
+    bool ismax;
+    if (k < NFR) {
+        src = part_row + (size_t)k * gr;
+        cnt = gr;
+        ismax = row_field_is_max(k);
+    } else if (k < NFR + NFC) {
+        src = part_col + (size_t)(k - NFR) * gc;
+        cnt = gc;
+        ismax = col_field_is_max(k - NFR);
+    } else {
+        src = part_big + (size_t)(k - NFR - NFC) * nbig;
+        cnt = nbig;
+        ismax = false;
     }
+    double acc = 0.0;
+    for (int i = lane; i < cnt; i += 32) acc = ismax ? nanmax(acc, src[i]) : acc + src[i];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const double o = __shfl_down_sync(FULL, acc, d);
+        acc = ismax ? nanmax(acc, o) : acc + o;
+    }
+    if (lane == 0) tot[k] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const double nres = sqrt(tot[F_RES2]), nb = sqrt(tot[F_B2]), nxd = sqrt(tot[F_XDIST2]);
-        const double nx = sqrt(tot[F_X2]), nsd = sqrt(tot[F_SDIST2]), nc = sqrt(tot[F_C2]);
-        const double cx = tot[F_CX], bl = tot[F_BLAM];
+        const double* R = tot;
+        const double* C = tot + NFR;
+        const double* B = tot + NFR + NFC;
+        const double nres = sqrt(R[R_RES2]), nb = sqrt(R[R_B2]);
+        const double nxd = sqrt(C[C_XDIST2] + B[B_XDIST2]), nsd = sqrt(C[C_SDIST2] + B[B_SDIST2]);
+        const double nx = sqrt(C[C_X2]), nc = sqrt(C[C_C2]);
+        const double cx = C[C_CX], bl = R[R_BLAM];
         status[S_RPRIM] = nres / (1.0 + nb);
         status[S_RDUAL] = nsd / (1.0 + nc);
         status[S_RCONE] = nxd / (1.0 + nx);
@@ -711,13 +711,13 @@ __global__ void __launch_bounds__(NT) k_resid_finalize(const double* part_row, i
         status[S_NX] = nx;
         status[S_NSDIST] = nsd;
         status[S_NC] = nc;
-        status[S_NATLC] = sqrt(tot[F_S2]);
-        status[S_IRES] = tot[F_RESMAX];
-        status[S_IAX] = tot[F_AXMAX];
-        status[S_IB] = tot[F_BMAX];
-        status[S_IATLC] = tot[F_SMAX];
-        status[S_IATL] = tot[F_ATLMAX];
-        status[S_IC] = tot[F_CMAX];
+        status[S_NATLC] = sqrt(C[C_S2]);
+        status[S_IRES] = R[R_RESMAX];
+        status[S_IAX] = R[R_AXMAX];
+        status[S_IB] = R[R_BMAX];
+        status[S_IATLC] = C[C_SMAX];
+        status[S_IATL] = C[C_ATLMAX];
+        status[S_IC] = C[C_CMAX];
     }
 }
 

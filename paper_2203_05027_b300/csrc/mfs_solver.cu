@@ -22,11 +22,6 @@ namespace {
 
 thread_local std::string g_create_error;
 
-struct DevBuf {
-    void* p = nullptr;
-    size_t bytes = 0;
-};
-
 template <typename T>
 struct State {
     T* x = nullptr;
@@ -42,6 +37,15 @@ struct State {
     int graph_iters = 0;
 };
 
+// One order (columns or rows) of A, chunked for the warp kernels.
+struct Chunks {
+    std::vector<int> desc;      // 4 ints per chunk: first segment, one past last, padded offset, nnz
+    std::vector<uint32_t> heads;  // 8 words per chunk: bit e set if a non-empty segment starts at item e
+    std::vector<int> longs;     // chunks with more than WT nonzeros
+    int64_t padded = 0;         // length of the padded nonzero arrays
+    int count() const { return (int)desc.size() / 4; }
+};
+
 struct HostProblem {
     int m = 0, n = 0, o = 0;
     std::vector<int> col_ptr, row_ptr;
@@ -49,11 +53,10 @@ struct HostProblem {
     std::vector<double> csc_val;
     std::vector<int> csr_col;     // unpadded, row order
     std::vector<double> csr_val;
-    std::vector<int> cj0, ckoff, cq_lo, cq_hi;  // column chunks
-    std::vector<int> ri0, rkoff;                // row chunks
+    Chunks cc, rc;
+    std::vector<int> cq_lo, cq_hi;
     std::vector<int> soc_start, soc_size, big_list;
     std::vector<unsigned char> soc_big;
-    int64_t cpad = 0, rpad = 0;  // padded lengths
 };
 
 }  // namespace
@@ -69,16 +72,19 @@ struct mfs_solver {
     int m = 0, n = 0, o = 0;
     int ncones = 0, nsoc = 0, nbig = 0;
     int ncc = 0, nrc = 0;            // column / row chunks
+    int nlc = 0, nlr = 0;            // long column / row chunks
     bool has_soc = false;
+    int num_sms = 148;
+    int g_rowres = 1, g_colres = 1;  // persistent residual grids
     // shared device structure
-    int *col_ptr = nullptr, *cidx = nullptr, *cj0 = nullptr, *ckoff = nullptr, *cq_lo = nullptr, *cq_hi = nullptr;
-    int *row_ptr = nullptr, *ridx = nullptr, *ri0 = nullptr, *rkoff = nullptr;
+    int *col_ptr = nullptr, *cidx = nullptr, *cq_lo = nullptr, *cq_hi = nullptr, *clong = nullptr;
+    int *row_ptr = nullptr, *ridx = nullptr, *rlong = nullptr;
+    uint32_t *cheads = nullptr, *rheads = nullptr;
+    int4 *cdesc = nullptr, *rdesc = nullptr;
     int *soc_start = nullptr, *soc_size = nullptr, *big_list = nullptr;
     unsigned char* soc_big = nullptr;
-    int* err = nullptr;
     double *part_row = nullptr, *part_col = nullptr, *part_big = nullptr, *s_buf = nullptr, *status = nullptr;
     double* h_status = nullptr;      // pinned
-    int* h_err = nullptr;            // pinned
     State<float> s32;
     State<double> s64;
     bool have32 = false, have64 = false;
@@ -104,6 +110,12 @@ mfs_status fail(mfs_solver* s, mfs_status st, const std::string& msg) {
                         std::string(#call) + ": " + cudaGetErrorString(e_));                       \
     } while (0)
 
+#define TRY(x)                               \
+    do {                                     \
+        mfs_status st_ = (x);                \
+        if (st_ != MFS_OK) return st_;       \
+    } while (0)
+
 template <typename T>
 mfs_status dalloc(mfs_solver* s, T** p, size_t count) {
     void* q = nullptr;
@@ -119,24 +131,17 @@ mfs_status dalloc(mfs_solver* s, T** p, size_t count) {
 
 template <typename T>
 mfs_status upload(mfs_solver* s, T** p, const void* host, size_t count) {
-    mfs_status st = dalloc(s, p, count);
-    if (st != MFS_OK) return st;
+    TRY(dalloc(s, p, count));
     if (count) CUDA_TRY(s, cudaMemcpyAsync(*p, host, count * sizeof(T), cudaMemcpyHostToDevice, s->stream));
     return MFS_OK;
 }
-
-#define TRY(x)                               \
-    do {                                     \
-        mfs_status st_ = (x);                \
-        if (st_ != MFS_OK) return st_;       \
-    } while (0)
 
 // ---------------------------------------------------------------------------------- host set-up
 
 // Sort COO into column order (rows ascending within a column), sum duplicates, drop zeros;
 // then build the row order. Counting sorts, O(nnz + m + n).
-mfs_status build_orders(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
-                        const double* val, HostProblem& P) {
+void build_orders(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col, const double* val,
+                  HostProblem& P) {
     std::vector<int64_t> cnt(std::max(m, n) + 1, 0), by_row(nnz), by_col(nnz);
     for (int64_t t = 0; t < nnz; ++t) cnt[row[t] + 1]++;
     for (int64_t i = 0; i < m; ++i) cnt[i + 1] += cnt[i];
@@ -176,8 +181,7 @@ mfs_status build_orders(int64_t m, int64_t n, int64_t nnz, const int64_t* row, c
     for (int64_t i = 0; i < m; ++i) P.row_ptr[i + 1] += P.row_ptr[i];
     P.csr_col.resize(P.o);
     P.csr_val.resize(P.o);
-    std::vector<int> fillp(P.row_ptr.begin(), P.row_ptr.end() - (m ? 1 : 0));
-    if (m == 0) fillp.clear();
+    std::vector<int> fillp(P.row_ptr.begin(), P.row_ptr.begin() + m);
     for (int64_t j = 0; j < n; ++j)
         for (int k = P.col_ptr[j]; k < P.col_ptr[j + 1]; ++k) {
             const int i = P.csc_row[k];
@@ -185,24 +189,34 @@ mfs_status build_orders(int64_t m, int64_t n, int64_t nnz, const int64_t* row, c
             P.csr_col[dst] = (int)j;
             P.csr_val[dst] = P.csc_val[k];
         }
-    return MFS_OK;
 }
 
 // Greedy chunking of segments (columns or rows) in order. A unit is one segment, or a whole
-// small Lorentz cone (columns only). A chunk takes units while it stays within TILE nonzeros and
-// CMAX segments; a single segment longer than TILE forms a chunk of its own.
-void build_chunks(const std::vector<int>& ptr, int nseg, const std::vector<int>* unit_end,
-                  std::vector<int>& c0, std::vector<int>& koff, int64_t& padded) {
-    c0.clear();
-    koff.clear();
-    padded = 0;
+// small Lorentz cone (columns only). A chunk takes units while it stays within WT nonzeros and
+// WC segments; a single segment longer than WT forms a (long) chunk of its own.
+void build_chunks(const std::vector<int>& ptr, int nseg, const std::vector<int>* unit_end, Chunks& C) {
+    C.desc.clear();
+    C.heads.clear();
+    C.longs.clear();
+    C.padded = 0;
     int start = 0, cur_seg = 0;
     int64_t cur_nnz = 0;
     auto close = [&](int at) {
-        c0.push_back(start);
-        koff.push_back((int)padded);
-        const int64_t cn = (int64_t)ptr[at] - ptr[start];
-        padded += (cn + PAD - 1) / PAD * PAD;
+        const int cn = ptr[at] - ptr[start];
+        if (cn > WT) C.longs.push_back(C.count());
+        const size_t h0 = C.heads.size();
+        C.heads.resize(h0 + 8, 0u);
+        if (cn <= WT)
+            for (int q = start; q < at; ++q)
+                if (ptr[q + 1] > ptr[q]) {
+                    const int e = ptr[q] - ptr[start];
+                    C.heads[h0 + (e >> 5)] |= 1u << (e & 31);
+                }
+        C.desc.push_back(start);
+        C.desc.push_back(at);
+        C.desc.push_back((int)C.padded);
+        C.desc.push_back(cn);
+        C.padded += (cn + PAD - 1) / PAD * PAD;
         start = at;
         cur_seg = 0;
         cur_nnz = 0;
@@ -212,20 +226,18 @@ void build_chunks(const std::vector<int>& ptr, int nseg, const std::vector<int>*
         const int ue = unit_end ? (*unit_end)[j] : j + 1;
         const int useg = ue - j;
         const int64_t unnz = (int64_t)ptr[ue] - ptr[j];
-        if (cur_seg > 0 && (cur_nnz + unnz > TILE || cur_seg + useg > CMAX)) close(j);
+        if (cur_seg > 0 && (cur_nnz + unnz > WT || cur_seg + useg > WC)) close(j);
         cur_seg += useg;
         cur_nnz += unnz;
         j = ue;
-        if (unnz > TILE) close(j);
+        if (unnz > WT) close(j);
     }
     if (cur_seg > 0) close(nseg);
-    c0.push_back(nseg);
-    koff.push_back((int)padded);
 }
 
 mfs_status setup_host(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
                       const double* val, int64_t ncones, const mfs_cone* cones, HostProblem& P) {
-    TRY(build_orders(m, n, nnz, row, col, val, P));
+    build_orders(m, n, nnz, row, col, val, P);
     // Lorentz cones; unit_end[j] = end of the small cone starting at j, or j+1
     std::vector<int> unit_end(n);
     for (int64_t j = 0; j < n; ++j) unit_end[j] = (int)j + 1;
@@ -234,7 +246,7 @@ mfs_status setup_host(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const in
         const int64_t sz = cones[q].size;
         if (cones[q].kind == MFS_CONE_SOC) {
             const int64_t cnnz = (int64_t)P.col_ptr[off + sz] - P.col_ptr[off];
-            const bool big = sz > CMAX || cnnz > TILE;
+            const bool big = sz > WC || cnnz > WT;
             P.soc_start.push_back((int)off);
             P.soc_size.push_back((int)sz);
             P.soc_big.push_back(big ? 1 : 0);
@@ -245,18 +257,18 @@ mfs_status setup_host(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const in
         }
         off += sz;
     }
-    build_chunks(P.col_ptr, (int)n, &unit_end, P.cj0, P.ckoff, P.cpad);
-    build_chunks(P.row_ptr, (int)m, nullptr, P.ri0, P.rkoff, P.rpad);
-    if (P.cpad >= INT32_MAX - PAD || P.rpad >= INT32_MAX - PAD)
+    build_chunks(P.col_ptr, (int)n, &unit_end, P.cc);
+    build_chunks(P.row_ptr, (int)m, nullptr, P.rc);
+    if (P.cc.padded >= INT32_MAX - PAD || P.rc.padded >= INT32_MAX - PAD)
         return fail(s, MFS_ERR_INVALID, "too many nonzeros after padding (limit 2^31)");
-    // cones intersecting each column chunk
-    const int ncc = (int)P.cj0.size() - 1;
-    P.cq_lo.resize(std::max(ncc, 0));
-    P.cq_hi.resize(std::max(ncc, 0));
+    // Lorentz cones intersecting each column chunk
+    const int ncc = P.cc.count();
+    P.cq_lo.resize(ncc);
+    P.cq_hi.resize(ncc);
     const int nsoc = (int)P.soc_start.size();
     int lo = 0;
     for (int c = 0; c < ncc; ++c) {
-        const int j0 = P.cj0[c], j1 = P.cj0[c + 1];
+        const int j0 = P.cc.desc[4 * c], j1 = P.cc.desc[4 * c + 1];
         while (lo < nsoc && P.soc_start[lo] + P.soc_size[lo] <= j0) ++lo;
         int hi = lo;
         while (hi < nsoc && P.soc_start[hi] < j1) ++hi;
@@ -266,18 +278,18 @@ mfs_status setup_host(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const in
     return MFS_OK;
 }
 
+// Padded nonzero arrays: chunk c's nonzeros at desc offset, zero-filled up to a multiple of PAD.
 template <typename T>
-void pad_chunks(const std::vector<int>& c0, const std::vector<int>& koff, const std::vector<int>& ptr,
-                const std::vector<int>& idx, const std::vector<double>& val, int64_t padded, std::vector<int>& pidx,
-                std::vector<T>& pval) {
-    pidx.assign(padded + PAD, 0);
-    pval.assign(padded + PAD, T(0));
-    const int nch = (int)c0.size() - 1;
-    for (int c = 0; c < nch; ++c) {
-        const int k0 = ptr[c0[c]], k1 = ptr[c0[c + 1]];
+void pad_chunks(const Chunks& C, const std::vector<int>& ptr, const std::vector<int>& idx,
+                const std::vector<double>& val, std::vector<int>* pidx, std::vector<T>* pval) {
+    if (pidx) pidx->assign(C.padded + PAD, 0);
+    if (pval) pval->assign(C.padded + PAD, T(0));
+    for (int c = 0; c < C.count(); ++c) {
+        const int s0 = C.desc[4 * c], s1 = C.desc[4 * c + 1], koff = C.desc[4 * c + 2];
+        const int k0 = ptr[s0], k1 = ptr[s1];
         for (int k = k0; k < k1; ++k) {
-            pidx[koff[c] + (k - k0)] = idx[k];
-            pval[koff[c] + (k - k0)] = T(val[k]);
+            if (pidx) (*pidx)[koff + (k - k0)] = idx[k];
+            if (pval) (*pval)[koff + (k - k0)] = T(val[k]);
         }
     }
 }
@@ -288,15 +300,17 @@ SweepArgs<T> sweep_args(mfs_solver* s, State<T>& st) {
     a.col_ptr = s->col_ptr;
     a.cidx = s->cidx;
     a.cval = st.cval;
-    a.cj0 = s->cj0;
-    a.ckoff = s->ckoff;
+    a.cdesc = s->cdesc;
+    a.cheads = s->cheads;
+    a.clong = s->clong;
     a.cq_lo = s->cq_lo;
     a.cq_hi = s->cq_hi;
     a.row_ptr = s->row_ptr;
     a.ridx = s->ridx;
     a.rval = st.rval;
-    a.ri0 = s->ri0;
-    a.rkoff = s->rkoff;
+    a.rdesc = s->rdesc;
+    a.rheads = s->rheads;
+    a.rlong = s->rlong;
     a.soc_start = s->soc_start;
     a.soc_size = s->soc_size;
     a.soc_big = s->soc_big;
@@ -309,64 +323,69 @@ SweepArgs<T> sweep_args(mfs_solver* s, State<T>& st) {
     a.lam = st.lam;
     a.v = st.v;
     a.mu = T(s->set.mu);
-    a.err = s->err;
+    a.ntc = s->ncc;
+    a.ntr = s->nrc;
+    a.nlc = s->nlc;
+    a.nlr = s->nlr;
     return a;
 }
 
-template <typename T>
-size_t smem_col_sweep(bool soc) {
-    using L = TileLayout<T, T, 1>;
-    return L::EXTRA + (soc ? 3 * CMAX * sizeof(T) + CMAX : 0);
-}
-template <typename T>
-size_t smem_row_sweep() {
-    return TileLayout<T, T, 2>::EXTRA;
-}
-template <typename T>
-size_t smem_resid_row() {
-    return TileLayout<T, double, 1>::EXTRA + 2 * NWARP * sizeof(double);
-}
-template <typename T>
-size_t smem_resid_col() {
-    return TileLayout<T, double, 1>::EXTRA + 2 * NWARP * sizeof(double) + 2 * CMAX * sizeof(double) + CMAX;
+template <typename K>
+mfs_status persistent_grid(mfs_solver* s, K kernel, int nchunks, int* grid) {
+    int per_sm = 0;
+    CUDA_TRY(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, 0));
+    if (per_sm < 1) return fail(s, MFS_ERR_CUDA, "residual kernel does not fit on an SM");
+    *grid = std::max(1, std::min((nchunks + NWARP - 1) / NWARP, per_sm * s->num_sms));
+    return MFS_OK;
 }
 
 template <typename T>
-mfs_status set_smem_attrs(mfs_solver* s) {
-    CUDA_TRY(s, cudaFuncSetAttribute(k_col_sweep<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_col_sweep<T>(false)));
-    CUDA_TRY(s, cudaFuncSetAttribute(k_col_sweep<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_col_sweep<T>(true)));
-    CUDA_TRY(s, cudaFuncSetAttribute(k_row_sweep<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_row_sweep<T>()));
-    CUDA_TRY(s, cudaFuncSetAttribute(k_row_sweep<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_row_sweep<T>()));
-    CUDA_TRY(s, cudaFuncSetAttribute(k_row_resid<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_resid_row<T>()));
-    CUDA_TRY(s, cudaFuncSetAttribute(k_col_resid<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_resid_col<T>()));
-    CUDA_TRY(s, cudaFuncSetAttribute(k_col_resid<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_resid_col<T>()));
+mfs_status residual_grids(mfs_solver* s) {
+    int gr = 1, gc = 1;
+    TRY(persistent_grid(s, k_row_resid<T>, s->nrc, &gr));
+    if (s->has_soc)
+        TRY(persistent_grid(s, k_col_resid<T, true>, s->ncc, &gc));
+    else
+        TRY(persistent_grid(s, k_col_resid<T, false>, s->ncc, &gc));
+    s->g_rowres = std::max(s->g_rowres, gr);
+    s->g_colres = std::max(s->g_colres, gc);
     return MFS_OK;
 }
 
 // ---------------------------------------------------------------------------------- launches
 
+inline int warp_grid(int nchunks) {
+    return (nchunks + NWARP - 1) / NWARP;
+}
+
 template <typename T>
 void launch_col(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
     if (s->ncc == 0) return;
-    if (s->has_soc)
-        k_col_sweep<T, true><<<s->ncc, NT, smem_col_sweep<T>(true), st>>>(a);
-    else
-        k_col_sweep<T, false><<<s->ncc, NT, smem_col_sweep<T>(false), st>>>(a);
+    if (s->has_soc) {
+        k_col_sweep<T, true><<<warp_grid(s->ncc), NT, 0, st>>>(a);
+        if (s->nlc) k_col_long<T, true><<<s->nlc, NT, 0, st>>>(a);
+    } else {
+        k_col_sweep<T, false><<<warp_grid(s->ncc), NT, 0, st>>>(a);
+        if (s->nlc) k_col_long<T, false><<<s->nlc, NT, 0, st>>>(a);
+    }
 }
 template <typename T>
 void launch_big(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
     if (s->nbig) k_bigcone_sweep<T><<<s->nbig, NT, 0, st>>>(a);
 }
+template <typename T, int MODE>
+void launch_row_mode(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
+    if (s->nrc == 0) return;
+    k_row_sweep<T, MODE><<<warp_grid(s->nrc), NT, 0, st>>>(a);
+    if (s->nlr) k_row_long<T, MODE><<<s->nlr, NT, 0, st>>>(a);
+}
 template <typename T>
 void launch_row(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
-    if (s->nrc) k_row_sweep<T, 0><<<s->nrc, NT, smem_row_sweep<T>(), st>>>(a);
+    launch_row_mode<T, 0>(s, a, st);
+}
+template <typename T>
+void launch_warm_v(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
+    launch_row_mode<T, 1>(s, a, st);
 }
 
 template <typename T>
@@ -376,17 +395,8 @@ void launch_iteration(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
     launch_row(s, a, st);
 }
 
-mfs_status check_device_error(mfs_solver* s) {
-    CUDA_TRY(s, cudaMemcpyAsync(s->h_err, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
-    if (*s->h_err != 0) {
-        const int code = *s->h_err;
-        CUDA_TRY(s, cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
-        CUDA_TRY(s, cudaStreamSynchronize(s->stream));
-        if (code == DERR_TIMEOUT) return fail(s, MFS_ERR_TIMEOUT, "a bounded on-device wait for a bulk copy gave up");
-        return fail(s, MFS_ERR_CUDA, "device error code " + std::to_string(code));
-    }
-    return MFS_OK;
+int launches_per_iteration(const mfs_solver* s) {
+    return (s->ncc ? 1 + (s->nlc ? 1 : 0) : 0) + (s->nbig ? 1 : 0) + (s->nrc ? 1 + (s->nlr ? 1 : 0) : 0);
 }
 
 template <typename T>
@@ -433,24 +443,23 @@ mfs_status residuals_t(mfs_solver* s, State<T>& st, mfs_residuals_t* out, bool w
     r.part_big = s->part_big;
     r.s_buf = s->s_buf;
     r.write_all_s = write_all_s ? 1 : 0;
-    if (s->nrc) k_row_resid<T><<<s->nrc, NT, smem_resid_row<T>(), s->stream>>>(a, r);
-    if (s->ncc) {
+    const int gr = s->nrc ? s->g_rowres : 0, gc = s->ncc ? s->g_colres : 0;
+    if (gr) k_row_resid<T><<<gr, NT, 0, s->stream>>>(a, r);
+    if (gc) {
         if (s->has_soc)
-            k_col_resid<T, true><<<s->ncc, NT, smem_resid_col<T>(), s->stream>>>(a, r);
+            k_col_resid<T, true><<<gc, NT, 0, s->stream>>>(a, r);
         else
-            k_col_resid<T, false><<<s->ncc, NT, smem_resid_col<T>(), s->stream>>>(a, r);
+            k_col_resid<T, false><<<gc, NT, 0, s->stream>>>(a, r);
     }
-    if (s->nbig) k_bigcone_resid<T><<<s->nbig, NT, 0, s->stream>>>(a, r);
-    k_resid_finalize<<<1, NT, 0, s->stream>>>(s->part_row, s->nrc, s->part_col, s->ncc, s->part_big, s->nbig,
-                                              s->status);
+    if (s->nbig) k_bigcone_resid<T><<<s->nbig, NT, 0, s->stream>>>(a, r, s->nbig);
+    k_resid_finalize<<<1, 32 * NFALL, 0, s->stream>>>(s->part_row, gr, s->part_col, gc, s->part_big, s->nbig,
+                                                      s->status);
     CUDA_TRY(s, cudaGetLastError());
     if (out) {
         CUDA_TRY(s, cudaMemcpyAsync(s->h_status, s->status, NSTATUS * sizeof(double), cudaMemcpyDeviceToHost,
                                     s->stream));
-    }
-    TRY(check_device_error(s));
-    if (out) {
-        double* h = s->h_status;
+        CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+        const double* h = s->h_status;
         out->r_prim = h[S_RPRIM];
         out->r_dual = h[S_RDUAL];
         out->r_cone = h[S_RCONE];
@@ -510,10 +519,9 @@ mfs_status warm_start_t(mfs_solver* s, State<T>& st, const double* x, const doub
         }
     }
     // v = F_U (b - A x) - lambda/mu
-    SweepArgs<T> a = sweep_args(s, st);
-    if (s->nrc) k_row_sweep<T, 1><<<s->nrc, NT, smem_row_sweep<T>(), s->stream>>>(a);
+    launch_warm_v(s, sweep_args(s, st), s->stream);
     CUDA_TRY(s, cudaGetLastError());
-    TRY(check_device_error(s));
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
     s->iter = 0;
     return MFS_OK;
 }
@@ -528,11 +536,10 @@ mfs_status alloc_state(mfs_solver* s, State<T>& st, const HostProblem& P, const 
     std::vector<T> hb(b, b + s->m), hc(c, c + s->n);
     TRY(upload(s, &st.b, hb.data(), hb.size()));
     TRY(upload(s, &st.c, hc.data(), hc.size()));
-    std::vector<int> pidx;
     std::vector<T> pval;
-    pad_chunks<T>(P.cj0, P.ckoff, P.col_ptr, P.csc_row, P.csc_val, P.cpad, pidx, pval);
+    pad_chunks<T>(P.cc, P.col_ptr, P.csc_row, P.csc_val, nullptr, &pval);
     TRY(upload(s, &st.cval, pval.data(), pval.size()));
-    pad_chunks<T>(P.ri0, P.rkoff, P.row_ptr, P.csr_col, P.csr_val, P.rpad, pidx, pval);
+    pad_chunks<T>(P.rc, P.row_ptr, P.csr_col, P.csr_val, nullptr, &pval);
     TRY(upload(s, &st.rval, pval.data(), pval.size()));
     CUDA_TRY(s, cudaMemsetAsync(st.x, 0, sizeof(T) * std::max(s->n, 1), s->stream));
     CUDA_TRY(s, cudaMemsetAsync(st.z, 0, sizeof(T) * std::max(s->n, 1), s->stream));
@@ -630,7 +637,7 @@ static mfs_status time_kernels_t(mfs_solver* s, State<T>& st, int64_t k, double*
     out[2] = s->nbig ? tb / kk : 0.0;
     out[3] = tall / kk;
     CUDA_TRY(s, cudaGetLastError());
-    return check_device_error(s);
+    return MFS_OK;
 }
 
 static mfs_status warm_start_impl(mfs_solver* s, const double* x, const double* lam, const double* z,
@@ -697,7 +704,6 @@ void mfs_destroy(mfs_solver* s) {
     destroy_graphs(s);
     for (void* p : s->allocs) cudaFree(p);
     if (s->h_status) cudaFreeHost(s->h_status);
-    if (s->h_err) cudaFreeHost(s->h_err);
     if (s->cap) cudaStreamDestroy(s->cap);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
@@ -775,8 +781,10 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
     s->nsoc = (int)P.soc_start.size();
     s->nbig = (int)P.big_list.size();
     s->has_soc = s->nsoc > 0;
-    s->ncc = (int)P.cj0.size() - 1;
-    s->nrc = (int)P.ri0.size() - 1;
+    s->ncc = P.cc.count();
+    s->nrc = P.rc.count();
+    s->nlc = (int)P.cc.longs.size();
+    s->nlr = (int)P.rc.longs.size();
     s->precision = set.precision;
 
 #define CHK(x)                      \
@@ -786,56 +794,50 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
     } while (0)
     CHK(upload(s, &s->col_ptr, P.col_ptr.data(), P.col_ptr.size()));
     CHK(upload(s, &s->row_ptr, P.row_ptr.data(), P.row_ptr.size()));
-    CHK(upload(s, &s->cj0, P.cj0.data(), P.cj0.size()));
-    CHK(upload(s, &s->ckoff, P.ckoff.data(), P.ckoff.size()));
+    CHK(upload(s, reinterpret_cast<int**>(&s->cdesc), P.cc.desc.data(), P.cc.desc.size()));
+    CHK(upload(s, reinterpret_cast<int**>(&s->rdesc), P.rc.desc.data(), P.rc.desc.size()));
+    CHK(upload(s, &s->cheads, P.cc.heads.data(), P.cc.heads.size()));
+    CHK(upload(s, &s->rheads, P.rc.heads.data(), P.rc.heads.size()));
+    CHK(upload(s, &s->clong, P.cc.longs.data(), P.cc.longs.size()));
+    CHK(upload(s, &s->rlong, P.rc.longs.data(), P.rc.longs.size()));
     CHK(upload(s, &s->cq_lo, P.cq_lo.data(), P.cq_lo.size()));
     CHK(upload(s, &s->cq_hi, P.cq_hi.data(), P.cq_hi.size()));
-    CHK(upload(s, &s->ri0, P.ri0.data(), P.ri0.size()));
-    CHK(upload(s, &s->rkoff, P.rkoff.data(), P.rkoff.size()));
     CHK(upload(s, &s->soc_start, P.soc_start.data(), P.soc_start.size()));
     CHK(upload(s, &s->soc_size, P.soc_size.data(), P.soc_size.size()));
     CHK(upload(s, &s->soc_big, P.soc_big.data(), P.soc_big.size()));
     CHK(upload(s, &s->big_list, P.big_list.data(), P.big_list.size()));
     {
-        std::vector<int> pidx;
-        std::vector<float> dummy;
-        std::vector<int> idx;
         // padded index arrays (shared by both precisions)
-        pidx.assign(P.cpad + PAD, 0);
-        for (int ch = 0; ch < s->ncc; ++ch) {
-            const int k0 = P.col_ptr[P.cj0[ch]], k1 = P.col_ptr[P.cj0[ch + 1]];
-            for (int k = k0; k < k1; ++k) pidx[P.ckoff[ch] + (k - k0)] = P.csc_row[k];
-        }
+        std::vector<int> pidx;
+        pad_chunks<double>(P.cc, P.col_ptr, P.csc_row, P.csc_val, &pidx, nullptr);
         CHK(upload(s, &s->cidx, pidx.data(), pidx.size()));
-        pidx.assign(P.rpad + PAD, 0);
-        for (int ch = 0; ch < s->nrc; ++ch) {
-            const int k0 = P.row_ptr[P.ri0[ch]], k1 = P.row_ptr[P.ri0[ch + 1]];
-            for (int k = k0; k < k1; ++k) pidx[P.rkoff[ch] + (k - k0)] = P.csr_col[k];
-        }
+        pad_chunks<double>(P.rc, P.row_ptr, P.csr_col, P.csr_val, &pidx, nullptr);
         CHK(upload(s, &s->ridx, pidx.data(), pidx.size()));
     }
-    CHK(dalloc(s, &s->err, 1));
-    CHK(dalloc(s, &s->part_row, (size_t)std::max(s->nrc, 1) * NF));
-    CHK(dalloc(s, &s->part_col, (size_t)std::max(s->ncc, 1) * NF));
-    CHK(dalloc(s, &s->part_big, (size_t)std::max(s->nbig, 1) * NF));
-    CHK(dalloc(s, &s->s_buf, (size_t)std::max(s->n, 1)));
-    CHK(dalloc(s, &s->status, NSTATUS));
-    e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
-    if (e == cudaSuccess) e = cudaMallocHost(&s->h_status, NSTATUS * sizeof(double));
-    if (e == cudaSuccess) e = cudaMallocHost(&s->h_err, sizeof(int));
-    if (e != cudaSuccess) {
-        s->last_error = std::string("pinned allocation: ") + cudaGetErrorString(e);
-        return bail(MFS_ERR_CUDA);
+    {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) == cudaSuccess && sms > 0)
+            s->num_sms = sms;
     }
     if (set.precision == MFS_FP32_MIXED) {
         CHK(alloc_state<float>(s, s->s32, P, b, c));
-        CHK(set_smem_attrs<float>(s));
+        CHK(residual_grids<float>(s));
         s->have32 = true;
     }
     if (set.precision == MFS_FP64 || set.polish_iters > 0) {
         CHK(alloc_state<double>(s, s->s64, P, b, c));
-        CHK(set_smem_attrs<double>(s));
+        CHK(residual_grids<double>(s));
         s->have64 = true;
+    }
+    CHK(dalloc(s, &s->part_row, (size_t)s->g_rowres * NFR));
+    CHK(dalloc(s, &s->part_col, (size_t)s->g_colres * NFC));
+    CHK(dalloc(s, &s->part_big, (size_t)std::max(s->nbig, 1) * NFB));
+    CHK(dalloc(s, &s->s_buf, (size_t)std::max(s->n, 1)));
+    CHK(dalloc(s, &s->status, NSTATUS));
+    e = cudaMallocHost(&s->h_status, NSTATUS * sizeof(double));
+    if (e != cudaSuccess) {
+        s->last_error = std::string("pinned allocation: ") + cudaGetErrorString(e);
+        return bail(MFS_ERR_CUDA);
     }
     e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
@@ -859,7 +861,7 @@ mfs_status mfs_get_info(const mfs_solver* s, mfs_info_t* out) {
     out->row_chunks = s->nrc;
     out->bytes_per_iter = bytes_per_iter(s, s->precision);
     out->precision = s->precision;
-    out->reserved = 0;
+    out->launches_per_iter = launches_per_iteration(s);
     return MFS_OK;
 }
 
@@ -873,13 +875,13 @@ mfs_status mfs_set_mu(mfs_solver* s, double mu) {
     if (old == mu) return MFS_OK;
     // v = rho - lambda/mu depends on mu. rho = F_U (b - A x) is recomputed from the current x by
     // the same row-order kernel that produced it, so only the lambda/mu term changes.
-    if (s->precision == MFS_FP64) {
-        if (s->nrc) k_row_sweep<double, 1><<<s->nrc, NT, smem_row_sweep<double>(), s->stream>>>(sweep_args(s, s->s64));
-    } else {
-        if (s->nrc) k_row_sweep<float, 1><<<s->nrc, NT, smem_row_sweep<float>(), s->stream>>>(sweep_args(s, s->s32));
-    }
+    if (s->precision == MFS_FP64)
+        launch_warm_v(s, sweep_args(s, s->s64), s->stream);
+    else
+        launch_warm_v(s, sweep_args(s, s->s32), s->stream);
     CUDA_TRY(s, cudaGetLastError());
-    return check_device_error(s);
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    return MFS_OK;
 }
 
 mfs_status mfs_warm_start(mfs_solver* s, const double* x, const double* lambda, const double* z,
@@ -897,7 +899,8 @@ mfs_status mfs_iterate(mfs_solver* s, int64_t k) {
     if (k < 0) return fail(s, MFS_ERR_INVALID, "k must be >= 0");
     CUDA_TRY(s, cudaSetDevice(s->device));
     TRY(s->precision == MFS_FP64 ? run_iters(s, s->s64, k) : run_iters(s, s->s32, k));
-    return check_device_error(s);
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    return MFS_OK;
 }
 
 mfs_status mfs_residuals(mfs_solver* s, mfs_residuals_t* out) {

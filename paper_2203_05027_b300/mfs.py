@@ -52,7 +52,7 @@ class Info(ctypes.Structure):
                 ("ncones", ctypes.c_int64), ("nsoc", ctypes.c_int64), ("nbig", ctypes.c_int64),
                 ("col_chunks", ctypes.c_int64), ("row_chunks", ctypes.c_int64),
                 ("bytes_per_iter", ctypes.c_int64), ("precision", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("launches_per_iter", ctypes.c_int32)]
 
 
 _lib = None
@@ -178,7 +178,7 @@ class Solver:
     def info(self):
         out = Info()
         self._check(self._lib.mfs_get_info(self._h, ctypes.byref(out)))
-        return {f: getattr(out, f) for f, _ in Info._fields_ if f != "reserved"}
+        return {f: getattr(out, f) for f, _ in Info._fields_}
 
     def set_mu(self, mu):
         self._check(self._lib.mfs_set_mu(self._h, float(mu)))

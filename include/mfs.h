@@ -175,6 +175,58 @@ mfs_status mfs_set_precision(mfs_solver* s, int32_t precision);
  */
 mfs_status mfs_time_kernels(mfs_solver* s, int64_t k, double* out_ms);
 
+/* ------------------------------------------------------------------------------------------------
+ * Batched solves. Many independent problems (Sec. II form each, Algorithm 1 on each) of uneven
+ * sizes are solved in one persistent launch: every CTA takes instances from a queue (largest
+ * first) and iterates one instance at a time with the vectors that its sweeps gather from held in
+ * shared memory (and the instance's matrix too when it fits). The launch is captured in a CUDA
+ * graph and replayed.
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct mfs_batch mfs_batch;
+
+typedef struct {
+    int32_t threads;      /* threads per CTA: 128, 256 or 512 */
+    int32_t ctas_per_sm;  /* 1..4 resident CTAs per SM (each gets 1/ctas_per_sm of the shared memory) */
+    int32_t check_every;  /* iterations between an instance's residual checks in mfs_batch_solve */
+    int32_t reserved;
+} mfs_batch_tuning;
+
+/*
+ * count >= 1 instances. Instance t has m[t] rows, n[t] columns, nnz[t] COO entries and ncones[t]
+ * cones; all per-instance arrays are concatenated in instance order (host): row/col/val (sum of
+ * nnz entries, indices local to the instance), b (sum of m), c (sum of n), cones (sum of ncones).
+ * Entry and cone rules as for mfs_create. settings: mu, check_every and precision (FP64, or
+ * FP32_MIXED = FP32 sweep with FP64 residual reductions) are used; polish_iters is ignored.
+ * Iterates start at zero. Default tuning: 256 threads, 1 CTA per SM.
+ */
+mfs_status mfs_batch_create(int64_t count, const int64_t* m, const int64_t* n, const int64_t* nnz,
+                            const int64_t* row, const int64_t* col, const double* val,
+                            const double* b, const double* c, const int64_t* ncones,
+                            const mfs_cone* cones, const mfs_settings* settings, void* cuda_stream,
+                            mfs_batch** out);
+void mfs_batch_destroy(mfs_batch* bt);
+/* Like mfs_last_error, for batches; NULL gives the last mfs_batch_create failure on this thread. */
+const char* mfs_batch_last_error(const mfs_batch* bt);
+mfs_status mfs_batch_get_info(const mfs_batch* bt, int64_t* count, int64_t* total_m, int64_t* total_n,
+                              int64_t* total_nnz);
+/* Exactly k iterations of every instance (no termination test). */
+mfs_status mfs_batch_iterate(mfs_batch* bt, int64_t k);
+/* Each instance iterates until its relative KKT residual (as in mfs_residuals_t) is <= tol, checked
+   every check_every iterations inside the launch, or until max_iter iterations. iters and status
+   (nullable, count entries each) receive per instance the iterations run by this call and MFS_OK or
+   MFS_MAX_ITER. */
+mfs_status mfs_batch_solve(mfs_batch* bt, double tol, int64_t max_iter, int64_t* iters, int32_t* status);
+/* FP64 residuals of every instance at its current iterate; out has count entries. */
+mfs_status mfs_batch_residuals(mfs_batch* bt, mfs_residuals_t* out);
+/* Iterate of instance t as doubles (host arrays; any may be NULL): x, z, delta (n[t]), lambda (m[t]). */
+mfs_status mfs_batch_get_solution(mfs_batch* bt, int64_t t, double* x, double* lambda, double* z,
+                                  double* delta);
+mfs_status mfs_batch_set_tuning(mfs_batch* bt, const mfs_batch_tuning* tuning);
+mfs_status mfs_batch_get_tuning(const mfs_batch* bt, mfs_batch_tuning* tuning);
+/* Autotuner: times `iters` iterations of the whole batch for each candidate (threads per CTA x CTAs
+   per SM), keeps the fastest and returns it in chosen (nullable). The iterate advances. */
+mfs_status mfs_batch_tune(mfs_batch* bt, int64_t iters, mfs_batch_tuning* chosen);
+
 /*
  * mfs_row_residuals_static -- row-side residuals of a point (x, lambda) without allocating.
  * The paper has no counterpart: this is a service for callers that cannot allocate device memory

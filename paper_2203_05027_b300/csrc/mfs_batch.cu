@@ -1,0 +1,950 @@
+// mfs_batch.cu -- batched solves: thousands of independent conic programs of uneven sizes in one
+// persistent launch (the mfs_batch_* calls of include/mfs.h).
+//
+// Each CTA takes instances from an atomic queue (largest first) and runs Algorithm 1 on one
+// instance at a time, in the reduced form of the single-instance solver (column sweep with the
+// x-step, z-step and delta-update; row sweep with the y-step and lambda-update), with
+// __syncthreads between the two sweeps. The two vectors the sweeps gather from (x in the row
+// sweep, v = F_U (b - A x) - lambda/mu in the column sweep) are held in shared memory for the
+// whole run of an instance, so the per-nonzero gathers never leave the SM; the instance's matrix
+// (both orders) is cached in shared memory as well when it fits, otherwise streamed from global
+// memory. Residuals are reduced in FP64 inside the CTA every check_every iterations when a
+// tolerance is given, and an instance stops as soon as it meets it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/mfs.h"
+#include "mfs_device.cuh"
+
+namespace {
+
+using mfs::DF;
+using mfs::FULL;
+
+constexpr int MAXNT = 512;
+constexpr int MAXW = MAXNT / 32;
+constexpr int NSTAT = 20;  // status block, same order as mfs_residuals_t
+
+template <typename T>
+struct BatchArgs {
+    int count;
+    const int* order;  // processing order (largest first)
+    const int* m;
+    const int* n;
+    const int* o;
+    const long long* off_n;  // first coordinate of each instance in the n-length arrays
+    const long long* off_m;
+    const long long* off_o;  // first nonzero of each instance
+    const int* col_ptr;      // instance t: n[t]+1 local offsets starting at off_n[t] + t
+    const int* cidx;         // local row indices, column order
+    const T* cval;
+    const int* row_ptr;      // instance t: m[t]+1 local offsets starting at off_m[t] + t
+    const int* ridx;         // local column indices, row order
+    const T* rval;
+    const int* nsoc;         // Lorentz cones per instance (local starts, ascending)
+    const long long* off_soc;
+    const int* soc_start;
+    const int* soc_size;
+    const T* b;
+    const T* c;
+    T* x;
+    T* z;
+    T* del;
+    T* lam;
+    T* v;
+    T mu;
+    int iters;        // iterations for each instance in this launch (at most, when tol > 0)
+    double tol;       // > 0: an instance stops once its relative KKT residual is <= tol
+    int check_every;  // iterations between residual checks
+    int smem_bytes;   // dynamic shared memory of a CTA
+    int* queue;       // instance counter, zero at launch
+    long long* iters_done;
+    int* status;      // 0 = met tol, 1 = not (yet)
+    double* resid;    // NSTAT doubles per instance, last evaluation
+};
+
+template <typename T>
+struct AccT {
+    using type = DF;
+};
+template <>
+struct AccT<double> {
+    using type = double;
+};
+__device__ __forceinline__ DF acc_mul(float a, float b) { return mfs::df_prod(a, b); }
+__device__ __forceinline__ double acc_mul(double a, double b) { return a * b; }
+
+template <typename T>
+__device__ __forceinline__ T lorentz_coord(T w, int t, T w1, T alpha) {
+    if (alpha <= -w1) return T(0);
+    if (alpha <= w1) return w;
+    return (t == 0) ? w / T(2) + alpha / T(2) : w / T(2) + w1 * w / (T(2) * alpha);
+}
+
+__device__ __forceinline__ double lorentz_dist2(double w1, double alpha, double wnorm2) {
+    if (alpha <= -w1) return wnorm2;
+    if (alpha <= w1) return 0.0;
+    const double g = alpha - w1;
+    return 0.5 * g * g;
+}
+
+// the Lorentz cone (local index) that contains column j, or -1
+__device__ __forceinline__ int cone_of(const int* st, const int* sz, int ns, int j) {
+    int lo = 0, hi = ns;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (st[mid] <= j)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    const int q = lo - 1;
+    return (q >= 0 && j < st[q] + sz[q]) ? q : -1;
+}
+
+// Block-wide fold of NF doubles (fields flagged in maxmask are maxima); result in thread 0.
+template <int NF>
+__device__ __forceinline__ void block_fold(double (&f)[NF], unsigned maxmask, double (*sh)[NF]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        double v = f[k];
+        for (int d = 16; d > 0; d >>= 1) {
+            const double o = __shfl_down_sync(FULL, v, d);
+            v = ((maxmask >> k) & 1u) ? fmax(v, o) : v + o;
+        }
+        f[k] = v;
+    }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NF; ++k) sh[warp][k] = f[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            double acc = 0.0;
+            for (int w = 0; w < nw; ++w) acc = ((maxmask >> k) & 1u) ? fmax(acc, sh[w][k]) : acc + sh[w][k];
+            f[k] = acc;
+        }
+    }
+}
+
+// fields of the residual fold
+enum { RES2, RESMAX, AXMAX, B2, BMAX, BLAM, S2, SMAX, ATLMAX, C2, CMAX, CX, X2, SDIST2, XDIST2, NFLD };
+constexpr unsigned MAXMASK = (1u << RESMAX) | (1u << AXMAX) | (1u << BMAX) | (1u << SMAX) | (1u << ATLMAX) | (1u << CMAX);
+
+struct Inst {
+    int t, m, n, o, ns;
+    long long gn, gm, go, gs;
+};
+
+// FP64 residuals of instance I at (x, lambda) (x read through xs); status block into out[NSTAT]
+// (thread 0) and the relative KKT residual returned to every thread.
+template <typename T>
+__device__ double instance_residuals(const BatchArgs<T>& a, const Inst& I, const T* xs, const int* cp, const int* ci,
+                                     const T* cv, const int* rp, const int* ri, const T* rv, double* out,
+                                     double (*sh)[NFLD], double* s_kkt) {
+    using A = typename AccT<T>::type;
+    double f[NFLD];
+#pragma unroll
+    for (int k = 0; k < NFLD; ++k) f[k] = 0.0;
+    const T* lam = a.lam + I.gm;
+    for (int i = threadIdx.x; i < I.m; i += blockDim.x) {
+        A acc = A(0);
+        for (int k = rp[i]; k < rp[i + 1]; ++k) acc = acc + acc_mul(rv[k], xs[ri[k]]);
+        const double ax = mfs::to_double(acc), bi = double(a.b[I.gm + i]), res = ax - bi;
+        f[RES2] += res * res;
+        f[RESMAX] = fmax(f[RESMAX], fabs(res));
+        f[AXMAX] = fmax(f[AXMAX], fabs(ax));
+        f[B2] += bi * bi;
+        f[BMAX] = fmax(f[BMAX], fabs(bi));
+        f[BLAM] += bi * double(lam[i]);
+    }
+    const int* sst = a.soc_start + I.gs;
+    const int* ssz = a.soc_size + I.gs;
+    auto column = [&](int j, bool orthant, double& s_out) {
+        A acc = A(0);
+        for (int k = cp[j]; k < cp[j + 1]; ++k) acc = acc + acc_mul(cv[k], lam[ci[k]]);
+        const double atl = mfs::to_double(acc), cj = double(a.c[I.gn + j]), xj = double(xs[j]);
+        const double s = cj + atl;
+        f[S2] += s * s;
+        f[SMAX] = fmax(f[SMAX], fabs(s));
+        f[ATLMAX] = fmax(f[ATLMAX], fabs(atl));
+        f[C2] += cj * cj;
+        f[CMAX] = fmax(f[CMAX], fabs(cj));
+        f[CX] += cj * xj;
+        f[X2] += xj * xj;
+        if (orthant) {
+            const double sn = s < 0.0 ? s : 0.0, xn = xj < 0.0 ? xj : 0.0;
+            f[SDIST2] += sn * sn;
+            f[XDIST2] += xn * xn;
+        }
+        s_out = s;
+    };
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        if (I.ns && cone_of(sst, ssz, I.ns, j) >= 0) continue;
+        double s;
+        column(j, true, s);
+    }
+    for (int q = threadIdx.x; q < I.ns; q += blockDim.x) {  // one thread per Lorentz cone
+        double s1 = 0.0, ss = 0.0, x1 = 0.0, xx = 0.0;
+        for (int t = 0; t < ssz[q]; ++t) {
+            const int j = sst[q] + t;
+            double s;
+            column(j, false, s);
+            const double xj = double(xs[j]);
+            if (t == 0) {
+                s1 = s;
+                x1 = xj;
+            } else {
+                ss += s * s;
+                xx += xj * xj;
+            }
+        }
+        f[SDIST2] += lorentz_dist2(s1, sqrt(ss), ss + s1 * s1);
+        f[XDIST2] += lorentz_dist2(x1, sqrt(xx), xx + x1 * x1);
+    }
+    block_fold<NFLD>(f, MAXMASK, sh);
+    if (threadIdx.x == 0) {
+        const double nres = sqrt(f[RES2]), nb = sqrt(f[B2]), nxd = sqrt(f[XDIST2]), nx = sqrt(f[X2]);
+        const double nsd = sqrt(f[SDIST2]), nc = sqrt(f[C2]), cx = f[CX], bl = f[BLAM];
+        double st[NSTAT];
+        st[0] = nres / (1.0 + nb);
+        st[1] = nsd / (1.0 + nc);
+        st[2] = nxd / (1.0 + nx);
+        st[3] = fabs(cx + bl) / (1.0 + fabs(cx) + fabs(bl));
+        double kkt = st[0];
+        for (int q = 1; q < 4; ++q) kkt = (st[q] > kkt || st[q] != st[q]) ? st[q] : kkt;
+        st[4] = kkt;
+        st[5] = cx;
+        st[6] = -bl;
+        st[7] = nres;
+        st[8] = nb;
+        st[9] = nxd;
+        st[10] = nx;
+        st[11] = nsd;
+        st[12] = nc;
+        st[13] = sqrt(f[S2]);
+        st[14] = f[RESMAX];
+        st[15] = f[AXMAX];
+        st[16] = f[BMAX];
+        st[17] = f[SMAX];
+        st[18] = f[ATLMAX];
+        st[19] = f[CMAX];
+        for (int q = 0; q < NSTAT; ++q) out[q] = st[q];
+        *s_kkt = kkt;
+    }
+    __syncthreads();
+    return *s_kkt;
+}
+
+template <typename T>
+__device__ __forceinline__ Inst load_inst(const BatchArgs<T>& a, int t) {
+    Inst I;
+    I.t = t;
+    I.m = a.m[t];
+    I.n = a.n[t];
+    I.o = a.o[t];
+    I.ns = a.nsoc[t];
+    I.gn = a.off_n[t];
+    I.gm = a.off_m[t];
+    I.go = a.off_o[t];
+    I.gs = a.off_soc[t];
+    return I;
+}
+
+// MODE 0: iterate (with termination checks when tol > 0); MODE 1: residuals only.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(MAXNT) k_batch(const BatchArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double s_red[MAXW][NFLD];
+    __shared__ double s_kkt;
+    __shared__ int s_inst;
+    const T mu = a.mu;
+    for (;;) {
+        if (threadIdx.x == 0) s_inst = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int q = s_inst;
+        __syncthreads();
+        if (q >= a.count) break;
+        const Inst I = load_inst(a, a.order[q]);
+        // shared memory: gathered vectors first, then (if room) the matrix in both orders
+        const size_t vb = (size_t)(I.n + I.m) * sizeof(T);
+        const size_t ab = (size_t)I.o * 2 * (sizeof(int) + sizeof(T));
+        const bool vec_sm = vb <= (size_t)a.smem_bytes;
+        const bool mat_sm = vec_sm && (vb + ab + 16 <= (size_t)a.smem_bytes);
+        T* xs = vec_sm ? reinterpret_cast<T*>(sm) : a.x + I.gn;
+        T* vs = vec_sm ? reinterpret_cast<T*>(sm) + I.n : a.v + I.gm;
+        const int* cp = a.col_ptr + I.gn + I.t;
+        const int* rp = a.row_ptr + I.gm + I.t;
+        const int* ci = a.cidx + I.go;
+        const T* cv = a.cval + I.go;
+        const int* ri = a.ridx + I.go;
+        const T* rv = a.rval + I.go;
+        if (vec_sm) {
+            for (int j = threadIdx.x; j < I.n; j += blockDim.x) xs[j] = a.x[I.gn + j];
+            for (int i = threadIdx.x; i < I.m; i += blockDim.x) vs[i] = a.v[I.gm + i];
+        }
+        if (mat_sm) {
+            unsigned char* p = sm + ((vb + 15) & ~size_t(15));
+            T* scv = reinterpret_cast<T*>(p);
+            T* srv = scv + I.o;
+            int* sci = reinterpret_cast<int*>(srv + I.o);
+            int* sri = sci + I.o;
+            for (int k = threadIdx.x; k < I.o; k += blockDim.x) {
+                scv[k] = cv[k];
+                srv[k] = rv[k];
+                sci[k] = ci[k];
+                sri[k] = ri[k];
+            }
+            cv = scv;
+            rv = srv;
+            ci = sci;
+            ri = sri;
+        }
+        __syncthreads();
+        const int* sst = a.soc_start + I.gs;
+        const int* ssz = a.soc_size + I.gs;
+        T* z = a.z + I.gn;
+        T* del = a.del + I.gn;
+        const T* c = a.c + I.gn;
+        const T* b = a.b + I.gm;
+        T* lam = a.lam + I.gm;
+        int done = 0;
+        int met = 0;
+        if (MODE == 0) {
+            for (; done < a.iters;) {
+                // column sweep: x-step (eq. vvt), z-step and delta-update for orthant coordinates
+                for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+                    const int k0 = cp[j], k1 = cp[j + 1];
+                    T s = T(0);
+                    for (int k = k0; k < k1; ++k) s += cv[k] * vs[ci[k]];
+                    const T d = T(k1 - k0), dj = del[j];
+                    const T xn = (d * xs[j] + s + z[j] + (dj - c[j]) / mu) / (T(1) + d);
+                    xs[j] = xn;
+                    if (I.ns == 0 || cone_of(sst, ssz, I.ns, j) < 0) {
+                        const T w = xn - dj / mu;
+                        const T zn = w > T(0) ? w : T(0);
+                        z[j] = zn;
+                        del[j] = dj + mu * (zn - xn);
+                    }
+                }
+                __syncthreads();
+                if (I.ns) {  // z-step (eq. proj) and delta-update of the Lorentz cones, one thread each
+                    for (int qc = threadIdx.x; qc < I.ns; qc += blockDim.x) {
+                        const int s0 = sst[qc], sz = ssz[qc];
+                        T ss = T(0);
+                        for (int t = 1; t < sz; ++t) {
+                            const T w = xs[s0 + t] - del[s0 + t] / mu;
+                            ss += w * w;
+                        }
+                        const T alpha = sqrt(ss), w1 = xs[s0] - del[s0] / mu;
+                        for (int t = 0; t < sz; ++t) {
+                            const T xt = xs[s0 + t], dt = del[s0 + t];
+                            const T zt = lorentz_coord(xt - dt / mu, t, w1, alpha);
+                            z[s0 + t] = zt;
+                            del[s0 + t] = dt + mu * (zt - xt);
+                        }
+                    }
+                    __syncthreads();
+                }
+                // row sweep: y-step (with F_U) and lambda-update
+                for (int i = threadIdx.x; i < I.m; i += blockDim.x) {
+                    T s = T(0), r = T(0);
+                    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+                        const T av = rv[k];
+                        s += av * xs[ri[k]];
+                        r += av * av;
+                    }
+                    const T rho = (b[i] - s) / (T(1) + r);
+                    const T ln = lam[i] - mu * rho;
+                    lam[i] = ln;
+                    vs[i] = rho - ln / mu;
+                }
+                __syncthreads();
+                ++done;
+                if (a.tol > 0.0 && (done % a.check_every == 0 || done == a.iters)) {
+                    const double kkt = instance_residuals(a, I, xs, cp, ci, cv, rp, ri, rv,
+                                                          a.resid + (size_t)I.t * NSTAT, s_red, &s_kkt);
+                    if (kkt <= a.tol) {
+                        met = 1;
+                        break;
+                    }
+                }
+            }
+        } else {
+            instance_residuals(a, I, xs, cp, ci, cv, rp, ri, rv, a.resid + (size_t)I.t * NSTAT, s_red, &s_kkt);
+        }
+        __syncthreads();
+        if (vec_sm && MODE == 0) {
+            for (int j = threadIdx.x; j < I.n; j += blockDim.x) a.x[I.gn + j] = xs[j];
+            for (int i = threadIdx.x; i < I.m; i += blockDim.x) a.v[I.gm + i] = vs[i];
+        }
+        if (threadIdx.x == 0 && MODE == 0) {
+            a.iters_done[I.t] += done;
+            a.status[I.t] = met ? 0 : 1;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+struct Store {
+    T *cval = nullptr, *rval = nullptr, *b = nullptr, *c = nullptr;
+    T *x = nullptr, *z = nullptr, *del = nullptr, *lam = nullptr, *v = nullptr;
+};
+
+}  // namespace
+
+struct mfs_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    mfs_settings set{};
+    mfs_batch_tuning tune{};
+    int count = 0;
+    int64_t tot_n = 0, tot_m = 0, tot_o = 0, tot_soc = 0;
+    int max_smem = 0, max_smem_block = 0, num_sms = 148;
+    std::vector<int> hm, hn, ho;
+    std::vector<long long> hoff_n, hoff_m, hoff_o;
+    int *order = nullptr, *m = nullptr, *n = nullptr, *o = nullptr, *nsoc = nullptr;
+    long long *off_n = nullptr, *off_m = nullptr, *off_o = nullptr, *off_soc = nullptr;
+    int *col_ptr = nullptr, *cidx = nullptr, *row_ptr = nullptr, *ridx = nullptr;
+    int *soc_start = nullptr, *soc_size = nullptr;
+    int* queue = nullptr;
+    long long* iters_done = nullptr;
+    int* status = nullptr;
+    double* resid = nullptr;
+    Store<float> f32;
+    Store<double> f64;
+    cudaGraphExec_t graph = nullptr;
+    int graph_iters = -1;
+    double graph_tol = -1;
+    std::vector<void*> allocs;
+    std::string last_error;
+};
+
+namespace {
+
+thread_local std::string g_batch_create_error;
+
+mfs_status bfail(mfs_batch* s, mfs_status st, const std::string& msg) {
+    if (s)
+        s->last_error = msg;
+    else
+        g_batch_create_error = msg;
+    return st;
+}
+
+#define BCUDA(s, call)                                                                              \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return bfail((s), e_ == cudaErrorMemoryAllocation ? MFS_ERR_OOM : MFS_ERR_CUDA,         \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+    } while (0)
+#define BTRY(x)                         \
+    do {                                \
+        mfs_status st_ = (x);           \
+        if (st_ != MFS_OK) return st_;  \
+    } while (0)
+
+template <typename T>
+mfs_status bupload(mfs_batch* s, T** p, const void* host, size_t count) {
+    void* q = nullptr;
+    BCUDA(s, cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)));
+    s->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    if (count) BCUDA(s, cudaMemcpyAsync(q, host, count * sizeof(T), cudaMemcpyHostToDevice, s->stream));
+    return MFS_OK;
+}
+
+template <typename T>
+mfs_status bzeros(mfs_batch* s, T** p, size_t count) {
+    void* q = nullptr;
+    BCUDA(s, cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)));
+    s->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    BCUDA(s, cudaMemsetAsync(q, 0, std::max<size_t>(count, 1) * sizeof(T), s->stream));
+    return MFS_OK;
+}
+
+template <typename T>
+BatchArgs<T> batch_args(mfs_batch* s, Store<T>& st, int iters, double tol) {
+    BatchArgs<T> a;
+    a.count = s->count;
+    a.order = s->order;
+    a.m = s->m;
+    a.n = s->n;
+    a.o = s->o;
+    a.off_n = s->off_n;
+    a.off_m = s->off_m;
+    a.off_o = s->off_o;
+    a.col_ptr = s->col_ptr;
+    a.cidx = s->cidx;
+    a.cval = st.cval;
+    a.row_ptr = s->row_ptr;
+    a.ridx = s->ridx;
+    a.rval = st.rval;
+    a.nsoc = s->nsoc;
+    a.off_soc = s->off_soc;
+    a.soc_start = s->soc_start;
+    a.soc_size = s->soc_size;
+    a.b = st.b;
+    a.c = st.c;
+    a.x = st.x;
+    a.z = st.z;
+    a.del = st.del;
+    a.lam = st.lam;
+    a.v = st.v;
+    a.mu = T(s->set.mu);
+    a.iters = iters;
+    a.tol = tol;
+    a.check_every = std::max(1, (int)s->set.check_every);
+    a.smem_bytes = 0;
+    a.queue = s->queue;
+    a.iters_done = s->iters_done;
+    a.status = s->status;
+    a.resid = s->resid;
+    return a;
+}
+
+// Dynamic shared memory per CTA for the current tuning (ctas_per_sm CTAs share an SM).
+int smem_for(const mfs_batch* s) {
+    const int per = s->max_smem / std::max(1, (int)s->tune.ctas_per_sm);
+    const int stat = (int)(MAXW * NFLD * sizeof(double) + 64);
+    return std::max(0, std::min(per - stat - 1024, s->max_smem_block - stat));
+}
+
+template <typename T, int MODE>
+mfs_status launch_batch(mfs_batch* s, Store<T>& st, int iters, double tol, cudaStream_t stream) {
+    BatchArgs<T> a = batch_args(s, st, iters, tol);
+    a.smem_bytes = smem_for(s);
+    BCUDA(s, cudaFuncSetAttribute(k_batch<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes));
+    BCUDA(s, cudaMemsetAsync(s->queue, 0, sizeof(int), stream));
+    const int grid = std::max(1, std::min(s->count, s->num_sms * std::max(1, (int)s->tune.ctas_per_sm)));
+    k_batch<T, MODE><<<grid, s->tune.threads, a.smem_bytes, stream>>>(a);
+    BCUDA(s, cudaGetLastError());
+    return MFS_OK;
+}
+
+template <typename T>
+mfs_status run_batch(mfs_batch* s, Store<T>& st, int iters, double tol) {
+    // the persistent launch (queue reset + kernel) is captured once per (iters, tol) and replayed
+    if (!s->graph || s->graph_iters != iters || s->graph_tol != tol) {
+        if (s->graph) cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+        cudaStream_t cap = nullptr;
+        BCUDA(s, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        mfs_status ms = MFS_OK;
+        if (e == cudaSuccess) {
+            ms = launch_batch<T, 0>(s, st, iters, tol, cap);
+            e = cudaStreamEndCapture(cap, &g);
+        }
+        if (e == cudaSuccess && ms == MFS_OK) e = cudaGraphInstantiate(&s->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cap);
+        if (ms != MFS_OK) return ms;
+        if (e != cudaSuccess) {
+            s->graph = nullptr;
+            return bfail(s, MFS_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+        }
+        s->graph_iters = iters;
+        s->graph_tol = tol;
+    }
+    BCUDA(s, cudaGraphLaunch(s->graph, s->stream));
+    BCUDA(s, cudaStreamSynchronize(s->stream));
+    return MFS_OK;
+}
+
+template <typename T>
+mfs_status alloc_store(mfs_batch* s, Store<T>& st, const std::vector<double>& cval, const std::vector<double>& rval,
+                       const double* b, const double* c) {
+    std::vector<T> tmp(cval.begin(), cval.end());
+    BTRY(bupload(s, &st.cval, tmp.data(), tmp.size()));
+    tmp.assign(rval.begin(), rval.end());
+    BTRY(bupload(s, &st.rval, tmp.data(), tmp.size()));
+    tmp.assign(b, b + s->tot_m);
+    BTRY(bupload(s, &st.b, tmp.data(), tmp.size()));
+    tmp.assign(c, c + s->tot_n);
+    BTRY(bupload(s, &st.c, tmp.data(), tmp.size()));
+    BTRY(bzeros(s, &st.x, s->tot_n));
+    BTRY(bzeros(s, &st.z, s->tot_n));
+    BTRY(bzeros(s, &st.del, s->tot_n));
+    BTRY(bzeros(s, &st.lam, s->tot_m));
+    BTRY(bzeros(s, &st.v, s->tot_m));
+    return MFS_OK;
+}
+
+template <typename T>
+__global__ void k_to_double(double* dst, const T* src, long long count) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count; t += (long long)gridDim.x * blockDim.x)
+        dst[t] = double(src[t]);
+}
+
+}  // namespace
+
+extern "C" {
+
+mfs_status mfs_batch_create(int64_t count, const int64_t* m, const int64_t* n, const int64_t* nnz, const int64_t* row,
+                            const int64_t* col, const double* val, const double* b, const double* c,
+                            const int64_t* ncones, const mfs_cone* cones, const mfs_settings* settings,
+                            void* cuda_stream, mfs_batch** out) {
+    g_batch_create_error.clear();
+    if (!out) return bfail(nullptr, MFS_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !m || !n || !nnz || !ncones) return bfail(nullptr, MFS_ERR_INVALID, "count < 1 or NULL sizes");
+    mfs_settings set;
+    mfs_default_settings(&set);
+    if (settings) set = *settings;
+    if (!(set.mu > 0.0) || !std::isfinite(set.mu) || set.check_every < 1 ||
+        (set.precision != MFS_FP64 && set.precision != MFS_FP32_MIXED))
+        return bfail(nullptr, MFS_ERR_INVALID, "invalid settings");
+    int64_t tn = 0, tm = 0, to = 0, tc = 0;
+    for (int64_t t = 0; t < count; ++t) {
+        if (m[t] < 0 || n[t] < 0 || nnz[t] < 0 || ncones[t] < 0 || m[t] >= INT32_MAX || n[t] >= INT32_MAX)
+            return bfail(nullptr, MFS_ERR_INVALID, "bad sizes of instance " + std::to_string(t));
+        tn += n[t];
+        tm += m[t];
+        to += nnz[t];
+        tc += ncones[t];
+    }
+    if ((to && (!row || !col || !val)) || (tm && !b) || (tn && !c) || (tc && !cones))
+        return bfail(nullptr, MFS_ERR_INVALID, "NULL array");
+    for (int64_t i = 0; i < tm; ++i)
+        if (!std::isfinite(b[i])) return bfail(nullptr, MFS_ERR_INVALID, "non-finite value in b");
+    for (int64_t j = 0; j < tn; ++j)
+        if (!std::isfinite(c[j])) return bfail(nullptr, MFS_ERR_INVALID, "non-finite value in c");
+
+    mfs_batch* s = new (std::nothrow) mfs_batch();
+    if (!s) return bfail(nullptr, MFS_ERR_OOM, "host allocation failed");
+    auto bail = [&](mfs_status st) {
+        g_batch_create_error = s->last_error;
+        mfs_batch_destroy(s);
+        return st;
+    };
+    s->set = set;
+    s->count = (int)count;
+    s->tune.threads = 256;
+    s->tune.ctas_per_sm = 1;
+    s->tune.check_every = set.check_every;
+    // per instance: column order (rows ascending within a column) and row order, local indices
+    std::vector<int> hm(count), hn(count), ho(count), hns(count), cp, rp, ci, ri, sst, ssz;
+    std::vector<long long> offn(count), offm(count), offo(count), offs(count);
+    std::vector<double> cv, rv;
+    cp.reserve(tn + count);
+    rp.reserve(tm + count);
+    int64_t pn = 0, pm = 0, po = 0, pz = 0, pc = 0;
+    for (int64_t t = 0; t < count; ++t) {
+        const int64_t mt = m[t], nt = n[t], kt = nnz[t];
+        offn[t] = pn;
+        offm[t] = pm;
+        offs[t] = (long long)sst.size();
+        // cones of instance t
+        int64_t covered = 0;
+        for (int64_t q = 0; q < ncones[t]; ++q) {
+            const mfs_cone& cq = cones[pc + q];
+            if (cq.size < 1 || (cq.kind != MFS_CONE_NONNEG && cq.kind != MFS_CONE_SOC)) {
+                s->last_error = "bad cone in instance " + std::to_string(t);
+                return bail(MFS_ERR_INVALID);
+            }
+            if (cq.kind == MFS_CONE_SOC) {
+                sst.push_back((int)covered);
+                ssz.push_back((int)cq.size);
+            }
+            covered += cq.size;
+        }
+        if (covered != nt) {
+            s->last_error = "cone sizes do not sum to n in instance " + std::to_string(t);
+            return bail(MFS_ERR_INVALID);
+        }
+        hns[t] = (int)(sst.size() - offs[t]);
+        pc += ncones[t];
+        // sort the instance's entries by (col, row), sum duplicates, drop zeros
+        std::vector<int64_t> idx(kt);
+        std::iota(idx.begin(), idx.end(), 0);
+        for (int64_t k = 0; k < kt; ++k) {
+            const int64_t r = row[pz + k], q = col[pz + k];
+            if (r < 0 || r >= mt || q < 0 || q >= nt || !std::isfinite(val[pz + k])) {
+                s->last_error = "bad entry " + std::to_string(k) + " in instance " + std::to_string(t);
+                return bail(MFS_ERR_INVALID);
+            }
+        }
+        std::sort(idx.begin(), idx.end(), [&](int64_t p, int64_t q) {
+            return col[pz + p] != col[pz + q] ? col[pz + p] < col[pz + q] : row[pz + p] < row[pz + q];
+        });
+        std::vector<int> lr, lc;
+        std::vector<double> lv;
+        for (int64_t k = 0; k < kt;) {
+            const int64_t r = row[pz + idx[k]], q = col[pz + idx[k]];
+            double a = 0.0;
+            while (k < kt && row[pz + idx[k]] == r && col[pz + idx[k]] == q) a += val[pz + idx[k++]];
+            if (a != 0.0) {
+                lr.push_back((int)r);
+                lc.push_back((int)q);
+                lv.push_back(a);
+            }
+        }
+        const int ot = (int)lv.size();
+        offo[t] = po;
+        hm[t] = (int)mt;
+        hn[t] = (int)nt;
+        ho[t] = ot;
+        // column order
+        std::vector<int> cnt(nt + 1, 0);
+        for (int k = 0; k < ot; ++k) cnt[lc[k] + 1]++;
+        for (int64_t j = 0; j < nt; ++j) cnt[j + 1] += cnt[j];
+        cp.insert(cp.end(), cnt.begin(), cnt.end());
+        for (int k = 0; k < ot; ++k) {
+            ci.push_back(lr[k]);
+            cv.push_back(lv[k]);
+        }
+        // row order (columns ascending within a row)
+        std::vector<int> rc(mt + 1, 0);
+        for (int k = 0; k < ot; ++k) rc[lr[k] + 1]++;
+        for (int64_t i = 0; i < mt; ++i) rc[i + 1] += rc[i];
+        rp.insert(rp.end(), rc.begin(), rc.end());
+        std::vector<int> fill(rc.begin(), rc.begin() + mt);
+        std::vector<int> tri(ot);
+        std::vector<double> trv(ot);
+        for (int k = 0; k < ot; ++k) {
+            const int dst = fill[lr[k]]++;
+            tri[dst] = lc[k];
+            trv[dst] = lv[k];
+        }
+        ri.insert(ri.end(), tri.begin(), tri.end());
+        rv.insert(rv.end(), trv.begin(), trv.end());
+        pn += nt;
+        pm += mt;
+        po += ot;
+        pz += kt;
+    }
+    s->tot_n = pn;
+    s->tot_m = pm;
+    s->tot_o = po;
+    s->tot_soc = (int64_t)sst.size();
+    s->hm = hm;
+    s->hn = hn;
+    s->ho = ho;
+    s->hoff_n = offn;
+    s->hoff_m = offm;
+    s->hoff_o = offo;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->max_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, s->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&s->max_smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) {
+            s->stream = static_cast<cudaStream_t>(cuda_stream);
+        } else {
+            e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+            s->own_stream = true;
+        }
+    }
+    if (e != cudaSuccess) {
+        s->last_error = std::string("CUDA set-up: ") + cudaGetErrorString(e);
+        return bail(MFS_ERR_CUDA);
+    }
+    // largest instances first
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return ho[p] + hn[p] > ho[q] + hn[q]; });
+#define BCHK(x)                             \
+    do {                                    \
+        mfs_status q_ = (x);                \
+        if (q_ != MFS_OK) return bail(q_);  \
+    } while (0)
+    BCHK(bupload(s, &s->order, order.data(), order.size()));
+    BCHK(bupload(s, &s->m, hm.data(), hm.size()));
+    BCHK(bupload(s, &s->n, hn.data(), hn.size()));
+    BCHK(bupload(s, &s->o, ho.data(), ho.size()));
+    BCHK(bupload(s, &s->nsoc, hns.data(), hns.size()));
+    BCHK(bupload(s, &s->off_n, offn.data(), offn.size()));
+    BCHK(bupload(s, &s->off_m, offm.data(), offm.size()));
+    BCHK(bupload(s, &s->off_o, offo.data(), offo.size()));
+    BCHK(bupload(s, &s->off_soc, offs.data(), offs.size()));
+    BCHK(bupload(s, &s->col_ptr, cp.data(), cp.size()));
+    BCHK(bupload(s, &s->row_ptr, rp.data(), rp.size()));
+    BCHK(bupload(s, &s->cidx, ci.data(), ci.size()));
+    BCHK(bupload(s, &s->ridx, ri.data(), ri.size()));
+    BCHK(bupload(s, &s->soc_start, sst.data(), sst.size()));
+    BCHK(bupload(s, &s->soc_size, ssz.data(), ssz.size()));
+    BCHK(bzeros(s, &s->queue, 1));
+    BCHK(bzeros(s, &s->iters_done, count));
+    BCHK(bzeros(s, &s->status, count));
+    BCHK(bzeros(s, &s->resid, (size_t)count * NSTAT));
+    if (set.precision == MFS_FP32_MIXED)
+        BCHK(alloc_store<float>(s, s->f32, cv, rv, b, c));
+    else
+        BCHK(alloc_store<double>(s, s->f64, cv, rv, b, c));
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        s->last_error = std::string("set-up: ") + cudaGetErrorString(e);
+        return bail(MFS_ERR_CUDA);
+    }
+#undef BCHK
+    *out = s;
+    return MFS_OK;
+}
+
+void mfs_batch_destroy(mfs_batch* s) {
+    if (!s) return;
+    cudaSetDevice(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    for (void* p : s->allocs) cudaFree(p);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+const char* mfs_batch_last_error(const mfs_batch* s) {
+    return s ? s->last_error.c_str() : g_batch_create_error.c_str();
+}
+
+mfs_status mfs_batch_set_tuning(mfs_batch* s, const mfs_batch_tuning* t) {
+    if (!s || !t) return MFS_ERR_INVALID;
+    if ((t->threads != 128 && t->threads != 256 && t->threads != 512) || t->ctas_per_sm < 1 || t->ctas_per_sm > 4 ||
+        t->check_every < 1)
+        return bfail(s, MFS_ERR_INVALID, "tuning: threads in {128,256,512}, ctas_per_sm in 1..4, check_every >= 1");
+    s->tune = *t;
+    s->set.check_every = t->check_every;
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+    return MFS_OK;
+}
+
+mfs_status mfs_batch_get_tuning(const mfs_batch* s, mfs_batch_tuning* t) {
+    if (!s || !t) return MFS_ERR_INVALID;
+    *t = s->tune;
+    return MFS_OK;
+}
+
+mfs_status mfs_batch_iterate(mfs_batch* s, int64_t k) {
+    if (!s || k < 0 || k >= INT32_MAX) return MFS_ERR_INVALID;
+    if (k == 0) return MFS_OK;
+    BCUDA(s, cudaSetDevice(s->device));
+    return s->set.precision == MFS_FP64 ? run_batch(s, s->f64, (int)k, 0.0) : run_batch(s, s->f32, (int)k, 0.0);
+}
+
+mfs_status mfs_batch_solve(mfs_batch* s, double tol, int64_t max_iter, int64_t* iters, int32_t* status) {
+    if (!s || !(tol > 0.0) || max_iter < 1 || max_iter >= INT32_MAX) return MFS_ERR_INVALID;
+    BCUDA(s, cudaSetDevice(s->device));
+    BCUDA(s, cudaMemsetAsync(s->iters_done, 0, sizeof(long long) * s->count, s->stream));
+    BTRY(s->set.precision == MFS_FP64 ? run_batch(s, s->f64, (int)max_iter, tol)
+                                      : run_batch(s, s->f32, (int)max_iter, tol));
+    if (iters) {
+        std::vector<long long> h(s->count);
+        BCUDA(s, cudaMemcpy(h.data(), s->iters_done, sizeof(long long) * s->count, cudaMemcpyDeviceToHost));
+        for (int t = 0; t < s->count; ++t) iters[t] = h[t];
+    }
+    if (status) {
+        std::vector<int> h(s->count);
+        BCUDA(s, cudaMemcpy(h.data(), s->status, sizeof(int) * s->count, cudaMemcpyDeviceToHost));
+        for (int t = 0; t < s->count; ++t) status[t] = h[t] ? MFS_MAX_ITER : MFS_OK;
+    }
+    return MFS_OK;
+}
+
+mfs_status mfs_batch_residuals(mfs_batch* s, mfs_residuals_t* out) {
+    if (!s || !out) return MFS_ERR_INVALID;
+    BCUDA(s, cudaSetDevice(s->device));
+    BTRY((s->set.precision == MFS_FP64 ? launch_batch<double, 1>(s, s->f64, 0, 0.0, s->stream)
+                                       : launch_batch<float, 1>(s, s->f32, 0, 0.0, s->stream)));
+    std::vector<double> h((size_t)s->count * NSTAT);
+    std::vector<long long> it(s->count);
+    BCUDA(s, cudaMemcpyAsync(h.data(), s->resid, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    BCUDA(s, cudaMemcpyAsync(it.data(), s->iters_done, it.size() * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    BCUDA(s, cudaStreamSynchronize(s->stream));
+    for (int t = 0; t < s->count; ++t) {
+        double* d = reinterpret_cast<double*>(&out[t]);
+        for (int q = 0; q < NSTAT; ++q) d[q] = h[(size_t)t * NSTAT + q];
+        out[t].iter = it[t];
+    }
+    return MFS_OK;
+}
+
+mfs_status mfs_batch_get_solution(mfs_batch* s, int64_t t, double* x, double* lambda, double* z, double* delta) {
+    if (!s || t < 0 || t >= s->count) return MFS_ERR_INVALID;
+    BCUDA(s, cudaSetDevice(s->device));
+    const int64_t n = s->hn[t], m = s->hm[t], gn = s->hoff_n[t], gm = s->hoff_m[t];
+    double* tmp = nullptr;
+    BCUDA(s, cudaMallocAsync((void**)&tmp, std::max<int64_t>(3 * n + m, 1) * sizeof(double), s->stream));
+    auto get = [&](auto* src, int64_t off, int64_t cnt, double* dev, double* host) {
+        if (!host || !cnt) return;
+        k_to_double<<<(int)std::min<int64_t>((cnt + 255) / 256, 1024), 256, 0, s->stream>>>(dev, src + off, cnt);
+        cudaMemcpyAsync(host, dev, cnt * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    };
+    if (s->set.precision == MFS_FP64) {
+        get(s->f64.x, gn, n, tmp, x);
+        get(s->f64.lam, gm, m, tmp + n, lambda);
+        get(s->f64.z, gn, n, tmp + n + m, z);
+        get(s->f64.del, gn, n, tmp + 2 * n + m, delta);
+    } else {
+        get(s->f32.x, gn, n, tmp, x);
+        get(s->f32.lam, gm, m, tmp + n, lambda);
+        get(s->f32.z, gn, n, tmp + n + m, z);
+        get(s->f32.del, gn, n, tmp + 2 * n + m, delta);
+    }
+    cudaFreeAsync(tmp, s->stream);
+    BCUDA(s, cudaGetLastError());
+    BCUDA(s, cudaStreamSynchronize(s->stream));
+    return MFS_OK;
+}
+
+mfs_status mfs_batch_get_info(const mfs_batch* s, int64_t* count, int64_t* total_m, int64_t* total_n,
+                              int64_t* total_nnz) {
+    if (!s) return MFS_ERR_INVALID;
+    if (count) *count = s->count;
+    if (total_m) *total_m = s->tot_m;
+    if (total_n) *total_n = s->tot_n;
+    if (total_nnz) *total_nnz = s->tot_o;
+    return MFS_OK;
+}
+
+mfs_status mfs_batch_tune(mfs_batch* s, int64_t iters, mfs_batch_tuning* chosen) {
+    if (!s || iters < 1 || iters >= INT32_MAX) return MFS_ERR_INVALID;
+    BCUDA(s, cudaSetDevice(s->device));
+    // Time every candidate on the batch itself (the iterate advances) and keep the fastest.
+    const mfs_batch_tuning keep = s->tune;
+    mfs_batch_tuning best = keep;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    BCUDA(s, cudaEventCreate(&e0));
+    BCUDA(s, cudaEventCreate(&e1));
+    for (int threads : {128, 256, 512}) {
+        for (int cps : {1, 2, 3}) {
+            mfs_batch_tuning t = keep;
+            t.threads = threads;
+            t.ctas_per_sm = cps;
+            BTRY(mfs_batch_set_tuning(s, &t));
+            BTRY(mfs_batch_iterate(s, 1));  // capture and warm
+            cudaEventRecord(e0, s->stream);
+            BTRY(mfs_batch_iterate(s, iters));
+            cudaEventRecord(e1, s->stream);
+            BCUDA(s, cudaEventSynchronize(e1));
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    BTRY(mfs_batch_set_tuning(s, &best));
+    if (chosen) *chosen = best;
+    return MFS_OK;
+}
+
+}  // extern "C"

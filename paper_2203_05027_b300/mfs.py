@@ -244,3 +244,137 @@ def row_residuals_static(m, n, row_ptr, col_idx, val, b, x, lam, out, stream=Non
     if code != MFS_OK:
         raise MfsError(code, "mfs_row_residuals_static failed (sizes beyond 4,194,304 rows, NULL or "
                              "negative arguments give ERR_INVALID)")
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+def _load_batch():
+    lib = load()
+    if getattr(lib, "_batch_declared", False):
+        return lib
+    P = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    st = ctypes.c_int
+    lib.mfs_batch_create.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, ctypes.POINTER(Settings), P,
+                                     ctypes.POINTER(P)]
+    lib.mfs_batch_create.restype = st
+    lib.mfs_batch_destroy.argtypes = [P]
+    lib.mfs_batch_destroy.restype = None
+    lib.mfs_batch_last_error.argtypes = [P]
+    lib.mfs_batch_last_error.restype = ctypes.c_char_p
+    lib.mfs_batch_get_info.argtypes = [P, P, P, P, P]
+    lib.mfs_batch_get_info.restype = st
+    lib.mfs_batch_iterate.argtypes = [P, i64]
+    lib.mfs_batch_iterate.restype = st
+    lib.mfs_batch_solve.argtypes = [P, ctypes.c_double, i64, P, P]
+    lib.mfs_batch_solve.restype = st
+    lib.mfs_batch_residuals.argtypes = [P, P]
+    lib.mfs_batch_residuals.restype = st
+    lib.mfs_batch_get_solution.argtypes = [P, i64, P, P, P, P]
+    lib.mfs_batch_get_solution.restype = st
+    lib.mfs_batch_set_tuning.argtypes = [P, ctypes.POINTER(BatchTuning)]
+    lib.mfs_batch_set_tuning.restype = st
+    lib.mfs_batch_get_tuning.argtypes = [P, ctypes.POINTER(BatchTuning)]
+    lib.mfs_batch_get_tuning.restype = st
+    lib.mfs_batch_tune.argtypes = [P, i64, ctypes.POINTER(BatchTuning)]
+    lib.mfs_batch_tune.restype = st
+    lib._batch_declared = True
+    return lib
+
+
+class Batch:
+    """Many independent problems (dicts as for Solver) solved together by one persistent launch."""
+
+    def __init__(self, probs, mu=1.0, check_every=50, precision="fp32", stream=None):
+        lib = _load_batch()
+        self._lib = lib
+        cnt = len(probs)
+        ms = np.array([p["m"] for p in probs], np.int64)
+        ns = np.array([p["n"] for p in probs], np.int64)
+        nz = np.array([len(p["row"]) for p in probs], np.int64)
+        rows = np.ascontiguousarray(np.concatenate([np.asarray(p["row"], np.int64) for p in probs]))
+        cols = np.ascontiguousarray(np.concatenate([np.asarray(p["col"], np.int64) for p in probs]))
+        vals = np.ascontiguousarray(np.concatenate([np.asarray(p["val"], np.float64) for p in probs]))
+        bs = np.ascontiguousarray(np.concatenate([np.asarray(p["b"], np.float64) for p in probs]))
+        cs = np.ascontiguousarray(np.concatenate([np.asarray(p["c"], np.float64) for p in probs]))
+        cones = [np.asarray(p["cones"], np.int64).reshape(-1, 2) for p in probs]
+        nc = np.array([len(c) for c in cones], np.int64)
+        allc = np.concatenate(cones) if cnt else np.zeros((0, 2), np.int64)
+        carr = (Cone * max(len(allc), 1))()
+        for q, (k, s) in enumerate(allc):
+            carr[q].kind = int(k)
+            carr[q].size = int(s)
+        st = Settings()
+        lib.mfs_default_settings(ctypes.byref(st))
+        st.mu = float(mu)
+        st.check_every = int(check_every)
+        st.precision = {"fp64": FP64, "fp32": FP32_MIXED}[precision]
+        h = ctypes.c_void_p()
+        code = lib.mfs_batch_create(cnt, _ptr(ms), _ptr(ns), _ptr(nz), _ptr(rows), _ptr(cols), _ptr(vals),
+                                    _ptr(bs), _ptr(cs), _ptr(nc), ctypes.cast(carr, ctypes.c_void_p),
+                                    ctypes.byref(st), ctypes.c_void_p(int(stream)) if stream else None,
+                                    ctypes.byref(h))
+        if code != MFS_OK:
+            raise MfsError(code, lib.mfs_batch_last_error(None).decode())
+        self._h = h
+        self.count = cnt
+        self.m, self.n = ms, ns
+
+    def _check(self, code, ok=(MFS_OK,)):
+        if code not in ok:
+            raise MfsError(code, self._lib.mfs_batch_last_error(self._h).decode())
+        return code
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.mfs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        v = [ctypes.c_int64() for _ in range(4)]
+        self._check(self._lib.mfs_batch_get_info(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("count", "total_m", "total_n", "total_nnz"), (x.value for x in v)))
+
+    def iterate(self, k):
+        self._check(self._lib.mfs_batch_iterate(self._h, int(k)))
+
+    def solve(self, tol, max_iter):
+        its = np.zeros(self.count, np.int64)
+        sts = np.zeros(self.count, np.int32)
+        self._check(self._lib.mfs_batch_solve(self._h, float(tol), int(max_iter), _ptr(its), _ptr(sts)))
+        return its, sts
+
+    def residuals(self):
+        out = (Residuals * self.count)()
+        self._check(self._lib.mfs_batch_residuals(self._h, ctypes.cast(out, ctypes.c_void_p)))
+        return [dict({f: getattr(r, f) for f in RESID_FIELDS}, iter=r.iter) for r in out]
+
+    def solution(self, t):
+        n, m = int(self.n[t]), int(self.m[t])
+        x, z, d = (np.empty(n) for _ in range(3))
+        lam = np.empty(m)
+        self._check(self._lib.mfs_batch_get_solution(self._h, int(t), _ptr(x), _ptr(lam), _ptr(z), _ptr(d)))
+        return {"x": x, "lam": lam, "z": z, "delta": d}
+
+    def tuning(self):
+        t = BatchTuning()
+        self._check(self._lib.mfs_batch_get_tuning(self._h, ctypes.byref(t)))
+        return {"threads": t.threads, "ctas_per_sm": t.ctas_per_sm, "check_every": t.check_every}
+
+    def set_tuning(self, threads, ctas_per_sm, check_every):
+        t = BatchTuning(int(threads), int(ctas_per_sm), int(check_every), 0)
+        self._check(self._lib.mfs_batch_set_tuning(self._h, ctypes.byref(t)))
+
+    def tune(self, iters):
+        t = BatchTuning()
+        self._check(self._lib.mfs_batch_tune(self._h, int(iters), ctypes.byref(t)))
+        return {"threads": t.threads, "ctas_per_sm": t.ctas_per_sm, "check_every": t.check_every}

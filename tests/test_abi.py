@@ -85,3 +85,17 @@ def test_no_device_is_a_cuda_error_not_a_crash(lib):
     with pytest.raises(mfs.MfsError) as e:
         mfs.Solver(tiny())
     assert e.value.status == mfs.MFS_ERR_CUDA
+
+
+@pytest.mark.parametrize("mutate, needle", [
+    (lambda p: p.update(cones=np.array([[0, 2]])), "sum to n"),
+    (lambda p: p.update(col=np.array([0, 1, 3])), "bad entry"),
+    (lambda p: p.update(cones=np.array([[5, 3]])), "bad cone"),
+])
+def test_invalid_batches_rejected_on_host(lib, mutate, needle):
+    good, bad = tiny(), tiny()
+    mutate(bad)
+    with pytest.raises(mfs.MfsError) as e:
+        mfs.Batch([good, bad])
+    assert e.value.status == mfs.MFS_ERR_INVALID
+    assert needle in str(e.value)

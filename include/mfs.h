@@ -227,6 +227,46 @@ mfs_status mfs_batch_get_tuning(const mfs_batch* bt, mfs_batch_tuning* tuning);
    per SM), keeps the fastest and returns it in chosen (nullable). The iterate advances. */
 mfs_status mfs_batch_tune(mfs_batch* bt, int64_t iters, mfs_batch_tuning* chosen);
 
+/* ------------------------------------------------------------------------------------------------
+ * Learned warm start. The paper has no counterpart; this serves parametric families of problems:
+ * a 3-layer MLP theta (din) -> width -> width -> dout (ReLU after the first two layers) maps a
+ * problem's parameters to a starting point (for instance x and lambda concatenated, dout = n + m)
+ * for mfs_warm_start. Weights are FP32 masters with BF16 copies; every GEMM runs on the tcgen05
+ * tensor cores (BF16 inputs, FP32 accumulation); training minimises the mean squared error
+ * against standardised targets with Adam. All x, y, target pointers are device FP32 arrays,
+ * row-major [batch][features]. Calls are synchronous on the handle's stream.
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct mfs_mlp mfs_mlp;
+
+/* din, width, max_batch: positive multiples of 8; dout >= 1. Weights He-uniform from seed. */
+mfs_status mfs_mlp_create(int32_t din, int32_t width, int32_t dout, int32_t max_batch, uint64_t seed,
+                          void* cuda_stream, mfs_mlp** out);
+void mfs_mlp_destroy(mfs_mlp* net);
+const char* mfs_mlp_last_error(const mfs_mlp* net);
+/* Targets are standardised per output as (t - mean) / std; host arrays of dout floats. */
+mfs_status mfs_mlp_set_output_scaling(mfs_mlp* net, const float* mean, const float* stdv);
+/* y = net(x) for batch <= max_batch rows; denormalize != 0 undoes the standardisation. */
+mfs_status mfs_mlp_forward(mfs_mlp* net, int32_t batch, const float* x, float* y, int32_t denormalize);
+/* Mean squared error of one batch (batch a multiple of 8) and its gradients, kept in the handle;
+   loss (nullable, host) receives the loss. */
+mfs_status mfs_mlp_backward(mfs_mlp* net, int32_t batch, const float* x, const float* target, double* loss);
+/* Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the gradients of the last mfs_mlp_backward. */
+mfs_status mfs_mlp_adam_step(mfs_mlp* net, float lr);
+/* mfs_mlp_backward followed by mfs_mlp_adam_step. */
+mfs_status mfs_mlp_train_step(mfs_mlp* net, int32_t batch, const float* x, const float* target, float lr,
+                              double* loss);
+/* Host copies of layer l (0..2): weights [out][in] and bias; NULL skips. */
+mfs_status mfs_mlp_get_params(mfs_mlp* net, int32_t layer, float* W, float* b);
+mfs_status mfs_mlp_set_params(mfs_mlp* net, int32_t layer, const float* W, const float* b);
+mfs_status mfs_mlp_get_grads(mfs_mlp* net, int32_t layer, float* gW, float* gb);
+
+/* Dense GEMM on the tensor cores: C[M x N] = A[M x K] * B[N x K]^T (+ bias[N], then ReLU if relu),
+   A and B row-major BF16 device arrays (K a multiple of 8), C row-major FP32 (out_fp32) or BF16,
+   bias nullable FP32. splits > 1 splits K over that many CTAs per tile (deterministic sum).
+   Synchronous; allocates its split workspace on the stream. */
+mfs_status mfs_gemm_bf16(int64_t M, int64_t N, int64_t K, const void* A, const void* B, const float* bias,
+                         int32_t relu, int32_t out_fp32, void* C, int32_t splits, void* cuda_stream);
+
 /*
  * mfs_row_residuals_static -- row-side residuals of a point (x, lambda) without allocating.
  * The paper has no counterpart: this is a service for callers that cannot allocate device memory

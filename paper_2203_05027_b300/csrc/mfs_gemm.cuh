@@ -1,0 +1,263 @@
+// mfs_gemm.cuh -- dense BF16 GEMM on the 5th-generation tensor cores (tcgen05, sm_103a):
+//   C[M x N] (+)= A[M x K] * B[N x K]^T      A, B row-major BF16 (both K-major), FP32 accumulate.
+//
+// One CTA computes one 128 x 128 tile of C (or a K-slice of it, for split-K). Four warps:
+//   warp 0, one lane: TMA producer, 2-D tiled loads of 128 x 64 BF16 boxes of A and B into a
+//                     STAGES-deep ring of shared-memory stages (128-byte swizzle);
+//   warp 1, one lane: issues tcgen05.mma (M = 128, N = 128, K = 16 per instruction) from shared
+//                     memory descriptors into a 128 x 128 FP32 accumulator in tensor memory;
+//   all four warps:   epilogue, tcgen05.ld of their 32 accumulator lanes (rows), bias, ReLU,
+//                     conversion and stores.
+// Barriers: full[s] (TMA transaction bytes), empty[s] (tcgen05.commit after the MMAs that read
+// stage s), acc (commit after the last MMA). Every wait is bounded: a wait that runs out sets the
+// error word and the kernel skips to the end, where tensor memory is freed.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "mfs_device.cuh"
+
+namespace mfs {
+namespace gemm {
+
+constexpr int BM = 128;
+constexpr int BN = 128;
+constexpr int BK = 64;       // one 128-byte swizzle row of BF16
+constexpr int UK = 16;       // K of one tcgen05.mma kind::f16
+constexpr int STAGES = 4;
+constexpr int NTHREADS = 128;
+constexpr int TILE_A = BM * BK * 2;  // bytes
+constexpr int TILE_B = BN * BK * 2;
+constexpr int STAGE_BYTES = TILE_A + TILE_B;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+constexpr uint32_t SPIN = 1u << 24;
+constexpr int ERR_TIMEOUT = 2;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bounded wait by the calling thread; false if the phase never completed.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < SPIN; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Shared-memory matrix descriptor (tcgen05): K-major operand tile in the canonical 128-byte
+// swizzled layout (rows of 128 bytes, 8-row groups 1024 bytes apart).
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+    const uint64_t addr = smem_addr(p);
+    uint64_t d = 0;
+    d |= (addr >> 4) & 0x3FFFull;         // start address
+    d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;               // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;               // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's lane (row).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct GemmArgs {
+    int M, N, K;
+    int kblocks_per_split;  // K blocks handled by one CTA (gridDim.z slices)
+    const float* bias;      // N, or nullptr (applied only when splits == 1)
+    int relu;               // apply ReLU (only when splits == 1)
+    int out_fp32;           // C element type: FP32 if set, else BF16
+    void* C;                // row-major M x N; with splits > 1: FP32 partials [split][M][N]
+    int ldc;
+    int* err;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_gemm_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const GemmArgs g) {
+    extern __shared__ __align__(1024) unsigned char gsm_raw[];
+    unsigned char* gsm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(gsm + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accb = empty + STAGES;
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(accb + 1);
+    int* s_fail = reinterpret_cast<int*>(s_tmem + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+    const int kb_total = (g.K + BK - 1) / BK;
+    const int kb0 = blockIdx.z * g.kblocks_per_split;
+    const int kb1 = min(kb_total, kb0 + g.kblocks_per_split);
+    const int nkb = max(0, kb1 - kb0);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accb, 1);
+        *s_fail = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {  // tensor memory for the 128 x 128 FP32 accumulator (128 columns)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_tmem)),
+                     "r"(BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+
+    if (warp == 0 && lane == 0) {  // producer
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i % STAGES;
+            if (!wait_phase(&empty[s], ((i / STAGES) & 1) ^ 1)) {
+                atomicExch(s_fail, 1);
+                break;
+            }
+            unsigned char* st = gsm + s * STAGE_BYTES;
+            mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+            tma_load_2d(st, &mapA, (kb0 + i) * BK, m0, &full[s]);
+            tma_load_2d(st + TILE_A, &mapB, (kb0 + i) * BK, n0, &full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {  // MMA issuer
+        const uint32_t idesc = idesc_bf16(BM, BN);
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i % STAGES;
+            if (!wait_phase(&full[s], (i / STAGES) & 1)) {
+                atomicExch(s_fail, 1);
+                break;
+            }
+            tc_fence_after();
+            unsigned char* st = gsm + s * STAGE_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / UK; ++kk) {
+                const uint64_t ad = smem_desc(st + kk * UK * 2);
+                const uint64_t bd = smem_desc(st + TILE_A + kk * UK * 2);
+                mma_bf16(tmem, ad, bd, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+            }
+            mma_commit(&empty[s]);  // stage s is free once these MMAs have read it
+        }
+        mma_commit(accb);  // the accumulator is complete once all issued MMAs are
+    }
+    __syncwarp();
+    // epilogue: every thread owns one row of the tile (TMEM lane = row)
+    const bool ok = wait_phase(accb, 0);
+    if (!ok) atomicExch(s_fail, 1);
+    tc_fence_after();
+    const int row = m0 + warp * 32 + lane;
+    if (ok && nkb > 0) {
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (row < g.M) {
+                const int col0 = n0 + c0;
+                if (gridDim.z > 1) {
+                    float* out = reinterpret_cast<float*>(g.C) + ((size_t)blockIdx.z * g.M + row) * g.ldc + col0;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (col0 + i < g.N) out[i] = v[i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        float w = v[i];
+                        if (col0 + i < g.N) {
+                            if (g.bias) w += g.bias[col0 + i];
+                            if (g.relu) w = w > 0.f ? w : 0.f;
+                            if (g.out_fp32)
+                                reinterpret_cast<float*>(g.C)[(size_t)row * g.ldc + col0 + i] = w;
+                            else
+                                reinterpret_cast<__nv_bfloat16*>(g.C)[(size_t)row * g.ldc + col0 + i] =
+                                    __float2bfloat16_rn(w);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (*s_fail && threadIdx.x == 0) {
+        atomicCAS(g.err, 0, ERR_TIMEOUT);
+        wait_phase(accb, 0);  // let issued MMAs finish before the accumulator is freed
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+}
+
+}  // namespace gemm
+}  // namespace mfs

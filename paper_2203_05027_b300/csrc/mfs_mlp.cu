@@ -1,0 +1,602 @@
+// mfs_mlp.cu -- the learned warm start: a 3-layer BF16 MLP (theta -> width -> width -> n+m) whose
+// forward and backward GEMMs run on the tcgen05 kernel of mfs_gemm.cuh, with FP32 master weights
+// and Adam. The network is trained on solutions that the solver itself produced and maps a
+// problem's parameters to an initial (x, lambda) for mfs_warm_start.
+//
+// Layout: weights W_l row-major [out][in] (FP32 master, BF16 copy, BF16 transposed copy for the
+// backward GEMMs); activations row-major [batch][features] in BF16; outputs and gradients of
+// weights in FP32. Every GEMM is C = A * B^T with both operands K-major, so the backward pass
+// transposes the operands it needs (tiled shared-memory transposes) instead of using MN-major
+// tensor-core layouts.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mfs.h"
+#include "mfs_gemm.cuh"
+
+using bf16 = __nv_bfloat16;
+
+namespace {
+
+using namespace mfs::gemm;
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+    static EncodeFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    }
+    return fn;
+}
+
+// Tensor map of a row-major BF16 matrix [rows][cols] read in boxes of 128 rows x 64 columns with
+// the 128-byte swizzle (out-of-bounds elements read as zero).
+bool make_map(CUtensorMap* map, const void* base, int rows, int cols) {
+    EncodeFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, 128};
+    cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Sum of split-K partials [splits][M][N] (+ bias, ReLU) into C (FP32 or BF16).
+__global__ void k_splitk_reduce(const float* __restrict__ part, int splits, int M, int N, const float* __restrict__ bias,
+                                int relu, int out_fp32, void* C) {
+    const long long total = (long long)M * N;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        for (int s = 0; s < splits; ++s) v += part[(size_t)s * total + t];
+        if (bias) v += bias[t % N];
+        if (relu) v = v > 0.f ? v : 0.f;
+        if (out_fp32)
+            reinterpret_cast<float*>(C)[t] = v;
+        else
+            reinterpret_cast<bf16*>(C)[t] = __float2bfloat16_rn(v);
+    }
+}
+
+// C (row-major M x N) = A (M x K) * B (N x K)^T, BF16 in, FP32 accumulate on the tensor cores.
+mfs_status gemm(int M, int N, int K, const bf16* A, const bf16* B, const float* bias, int relu, int out_fp32, void* C,
+                int splits, float* work, int* err, cudaStream_t st, std::string* why) {
+    if (M <= 0 || N <= 0 || K <= 0) return MFS_OK;
+    if (K % 8) {
+        if (why) *why = "gemm: K must be a multiple of 8 (16-byte rows)";
+        return MFS_ERR_INVALID;
+    }
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess) {
+            if (why) *why = "gemm: shared memory attribute";
+            return MFS_ERR_CUDA;
+        }
+        attr = true;
+    }
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, M, K) || !make_map(&mb, B, N, K)) {
+        if (why) *why = "gemm: cuTensorMapEncodeTiled failed";
+        return MFS_ERR_CUDA;
+    }
+    const int kbt = (K + BK - 1) / BK;
+    splits = std::max(1, std::min(splits, kbt));
+    const int kbps = (kbt + splits - 1) / splits;
+    splits = (kbt + kbps - 1) / kbps;
+    if (splits > 1 && !work) {
+        if (why) *why = "gemm: split-K needs a workspace";
+        return MFS_ERR_INVALID;
+    }
+    GemmArgs g;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.kblocks_per_split = kbps;
+    g.bias = splits > 1 ? nullptr : bias;
+    g.relu = splits > 1 ? 0 : relu;
+    g.out_fp32 = out_fp32;
+    g.C = splits > 1 ? static_cast<void*>(work) : C;
+    g.ldc = N;
+    g.err = err;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
+    k_gemm_bf16<<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, g);
+    if (splits > 1) {
+        const long long total = (long long)M * N;
+        const int blocks = (int)std::min<long long>((total + 255) / 256, 148 * 8);
+        k_splitk_reduce<<<blocks, 256, 0, st>>>(work, splits, M, N, bias, relu, out_fp32, C);
+    }
+    if (cudaGetLastError() != cudaSuccess) {
+        if (why) *why = "gemm: launch failed";
+        return MFS_ERR_CUDA;
+    }
+    return MFS_OK;
+}
+
+// Tiled transpose: out[c][r] = in[r][c] for a row-major BF16 matrix [rows][cols].
+__global__ void k_transpose(const bf16* __restrict__ in, bf16* __restrict__ out, int rows, int cols) {
+    __shared__ bf16 tile[32][33];
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = blockIdx.y * 32 + k;
+        if (r < rows && c < cols) tile[k][threadIdx.x] = in[(size_t)r * cols + c];
+    }
+    __syncthreads();
+    const int r2 = blockIdx.y * 32 + threadIdx.x;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int c2 = blockIdx.x * 32 + k;
+        if (c2 < cols && r2 < rows) out[(size_t)c2 * rows + r2] = tile[threadIdx.x][k];
+    }
+}
+
+void transpose(const bf16* in, bf16* out, int rows, int cols, cudaStream_t st) {
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+    k_transpose<<<grid, block, 0, st>>>(in, out, rows, cols);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ in, bf16* __restrict__ out, long long count) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count; t += (long long)gridDim.x * blockDim.x)
+        out[t] = __float2bfloat16_rn(in[t]);
+}
+
+// Loss gradient of the mean squared error against standardised targets:
+// dY = 2 (Y - (T - mean)/std) / (B * D); per-block partial sums of the squared error.
+// Y and dY have rows of Dp >= D entries (the extra ones get dY = 0); T has rows of D.
+__global__ void k_mse(const float* __restrict__ Y, const float* __restrict__ T, const float* __restrict__ mean,
+                      const float* __restrict__ stdv, int B, int D, int Dp, bf16* __restrict__ dY,
+                      double* __restrict__ part) {
+    __shared__ double sh[8];
+    const long long total = (long long)B * Dp;
+    const float scale = 2.0f / ((float)B * (float)D);
+    double acc = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(t % Dp);
+        const long long row = t / Dp;
+        float r = 0.f;
+        if (j < D) r = Y[t] - (T[row * D + j] - mean[j]) / stdv[j];
+        acc += (double)r * (double)r;
+        dY[t] = __float2bfloat16_rn(scale * r);
+    }
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+        part[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_sum_parts(const double* __restrict__ part, int n, double scale, double* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += part[i];
+        *out = s * scale;
+    }
+}
+
+// dZ = dH * (H > 0) (ReLU backward), FP32 in, BF16 out.
+__global__ void k_relu_bwd(const float* __restrict__ dH, const bf16* __restrict__ H, bf16* __restrict__ dZ, long long count) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count; t += (long long)gridDim.x * blockDim.x)
+        dZ[t] = __float2bfloat16_rn(__bfloat162float(H[t]) > 0.f ? dH[t] : 0.f);
+}
+
+// db[j] = sum over rows of G[row][j] (fixed order).
+__global__ void k_colsum(const bf16* __restrict__ G, int rows, int cols, float* __restrict__ db) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cols) return;
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += __bfloat162float(G[(size_t)r * cols + j]);
+    db[j] = s;
+}
+
+// Adam (Kingma & Ba) on FP32 master weights; refreshes the BF16 copy.
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       bf16* __restrict__ wh, long long count, float lr, float b1, float b2, float eps, float c1,
+                       float c2) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count; t += (long long)gridDim.x * blockDim.x) {
+        const float gt = g[t];
+        const float mt = b1 * m[t] + (1.f - b1) * gt;
+        const float vt = b2 * v[t] + (1.f - b2) * gt * gt;
+        m[t] = mt;
+        v[t] = vt;
+        const float wn = w[t] - lr * (mt / c1) / (sqrtf(vt / c2) + eps);
+        w[t] = wn;
+        if (wh) wh[t] = __float2bfloat16_rn(wn);
+    }
+}
+
+// Y * std + mean (undo the target standardisation), FP32.
+__global__ void k_denorm(float* __restrict__ Y, const float* __restrict__ mean, const float* __restrict__ stdv, int B,
+                         int D) {
+    const long long total = (long long)B * D;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(t % D);
+        Y[t] = Y[t] * stdv[j] + mean[j];
+    }
+}
+
+inline int grid1(long long count) {
+    return (int)std::max<long long>(1, std::min<long long>((count + 255) / 256, 148 * 8));
+}
+
+}  // namespace
+
+struct mfs_mlp {
+    int din = 0, width = 0, dout = 0, maxb = 0;
+    int doutp = 0;  // dout rounded up to a multiple of 8 (16-byte rows); the extra outputs stay zero
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int step = 0;
+    float beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
+    // parameters: FP32 master, Adam moments, BF16 copies; index 0..2 = layers 1..3
+    float *W[3] = {}, *b[3] = {}, *mW[3] = {}, *vW[3] = {}, *mb[3] = {}, *vb[3] = {};
+    bf16 *Wh[3] = {}, *Wt[3] = {};
+    float *gW[3] = {}, *gb[3] = {};
+    float *mean = nullptr, *stdv = nullptr;
+    // activations and gradients
+    bf16 *X = nullptr, *H1 = nullptr, *H2 = nullptr, *dY = nullptr, *dYt = nullptr, *H2t = nullptr, *H1t = nullptr,
+         *Xt = nullptr, *dZ2 = nullptr, *dZ2t = nullptr, *dZ1 = nullptr, *dZ1t = nullptr;
+    float *Y = nullptr, *dH = nullptr, *work = nullptr;
+    double *loss_part = nullptr, *loss = nullptr;
+    int* err = nullptr;
+    size_t work_floats = 0;
+    std::vector<void*> allocs;
+    std::string last_error;
+};
+
+namespace {
+
+thread_local std::string g_mlp_error;
+
+mfs_status mfail(mfs_mlp* s, mfs_status st, const std::string& msg) {
+    if (s)
+        s->last_error = msg;
+    else
+        g_mlp_error = msg;
+    return st;
+}
+
+template <typename T>
+mfs_status malloc_zero(mfs_mlp* s, T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return mfail(s, MFS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    s->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    e = cudaMemsetAsync(q, 0, std::max<size_t>(count, 1) * sizeof(T), s->stream);
+    if (e != cudaSuccess) return mfail(s, MFS_ERR_CUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
+    return MFS_OK;
+}
+
+#define MTRY(x)                         \
+    do {                                \
+        mfs_status st_ = (x);           \
+        if (st_ != MFS_OK) return st_;  \
+    } while (0)
+
+int layer_in(const mfs_mlp* s, int l) { return l == 0 ? s->din : s->width; }
+int layer_out(const mfs_mlp* s, int l) { return l == 2 ? s->doutp : s->width; }
+int user_out(const mfs_mlp* s, int l) { return l == 2 ? s->dout : s->width; }
+
+mfs_status check_err(mfs_mlp* s) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return mfail(s, MFS_ERR_CUDA, std::string("mlp: ") + cudaGetErrorString(e));
+    if (h) {
+        cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
+        return mfail(s, MFS_ERR_TIMEOUT, "mlp: a bounded wait in the tensor-core GEMM gave up");
+    }
+    return MFS_OK;
+}
+
+mfs_status run_gemm(mfs_mlp* s, int M, int N, int K, const bf16* A, const bf16* B, const float* bias, int relu,
+                    int out_fp32, void* C, int splits) {
+    std::string why;
+    mfs_status st = gemm(M, N, K, A, B, bias, relu, out_fp32, C, splits, s->work, s->err, s->stream, &why);
+    if (st != MFS_OK) return mfail(s, st, why);
+    return MFS_OK;
+}
+
+int splits_for(const mfs_mlp* s, int M, int N, int K) {
+    // enough CTAs to cover the GPU when M x N is small and K long; bounded by the workspace
+    const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    int sp = std::max(1, std::min((K + BK - 1) / BK, 2 * 148 / std::max(1, tiles)));
+    while (sp > 1 && (size_t)sp * M * N > s->work_floats) --sp;
+    return sp;
+}
+
+// forward for a batch already converted to BF16 in s->X; output (standardised) in s->Y
+mfs_status forward_bf16(mfs_mlp* s, int B) {
+    MTRY(run_gemm(s, B, s->width, s->din, s->X, s->Wh[0], s->b[0], 1, 0, s->H1, 1));
+    MTRY(run_gemm(s, B, s->width, s->width, s->H1, s->Wh[1], s->b[1], 1, 0, s->H2,
+                  splits_for(s, B, s->width, s->width)));
+    MTRY(run_gemm(s, B, s->doutp, s->width, s->H2, s->Wh[2], s->b[2], 0, 1, s->Y, 1));
+    return MFS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mfs_status mfs_mlp_create(int32_t din, int32_t width, int32_t dout, int32_t max_batch, uint64_t seed, void* cuda_stream,
+                          mfs_mlp** out) {
+    g_mlp_error.clear();
+    if (!out) return mfail(nullptr, MFS_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (din < 1 || width < 1 || dout < 1 || max_batch < 1 || din % 8 || width % 8 || max_batch % 8)
+        return mfail(nullptr, MFS_ERR_INVALID, "din, width and max_batch must be positive multiples of 8, dout >= 1");
+    mfs_mlp* s = new (std::nothrow) mfs_mlp();
+    if (!s) return mfail(nullptr, MFS_ERR_OOM, "host allocation failed");
+    auto bail = [&](mfs_status st) {
+        g_mlp_error = s->last_error;
+        mfs_mlp_destroy(s);
+        return st;
+    };
+    s->din = din;
+    s->width = width;
+    s->dout = dout;
+    s->doutp = (dout + 7) / 8 * 8;
+    s->maxb = max_batch;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) {
+        if (cuda_stream)
+            s->stream = static_cast<cudaStream_t>(cuda_stream);
+        else {
+            e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+            s->own_stream = true;
+        }
+    }
+    if (e != cudaSuccess) {
+        s->last_error = std::string("CUDA set-up: ") + cudaGetErrorString(e);
+        return bail(MFS_ERR_CUDA);
+    }
+    if (!encode_fn()) {
+        s->last_error = "cuTensorMapEncodeTiled is not available from the driver";
+        return bail(MFS_ERR_CUDA);
+    }
+#define MCHK(x)                             \
+    do {                                    \
+        mfs_status q_ = (x);                \
+        if (q_ != MFS_OK) return bail(q_);  \
+    } while (0)
+    // He-uniform initial weights from a fixed LCG-free generator (splitmix64), zero biases
+    uint64_t state = seed ^ 0x9E3779B97F4A7C15ull;
+    auto next = [&]() {
+        uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    for (int l = 0; l < 3; ++l) {
+        const int fi = layer_in(s, l), fo = layer_out(s, l);
+        const size_t cnt = (size_t)fi * fo;
+        MCHK(malloc_zero(s, &s->W[l], cnt));
+        MCHK(malloc_zero(s, &s->mW[l], cnt));
+        MCHK(malloc_zero(s, &s->vW[l], cnt));
+        MCHK(malloc_zero(s, &s->gW[l], cnt));
+        MCHK(malloc_zero(s, &s->Wh[l], cnt));
+        MCHK(malloc_zero(s, &s->Wt[l], cnt));
+        MCHK(malloc_zero(s, &s->b[l], fo));
+        MCHK(malloc_zero(s, &s->mb[l], fo));
+        MCHK(malloc_zero(s, &s->vb[l], fo));
+        MCHK(malloc_zero(s, &s->gb[l], fo));
+        std::vector<float> h(cnt, 0.0f);
+        const double lim = std::sqrt(6.0 / fi) * (l == 2 ? 0.1 : 1.0);
+        const size_t live = (size_t)fi * user_out(s, l);
+        for (size_t i = 0; i < live; ++i) h[i] = (float)((2.0 * ((next() >> 11) * (1.0 / 9007199254740992.0)) - 1.0) * lim);
+        e = cudaMemcpyAsync(s->W[l], h.data(), cnt * sizeof(float), cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) {
+            s->last_error = "upload";
+            return bail(MFS_ERR_CUDA);
+        }
+        k_to_bf16<<<grid1(cnt), 256, 0, s->stream>>>(s->W[l], s->Wh[l], (long long)cnt);
+    }
+    const int B = max_batch;
+    const int Dp = s->doutp;
+    MCHK(malloc_zero(s, &s->mean, Dp));
+    MCHK(malloc_zero(s, &s->stdv, Dp));
+    {
+        std::vector<float> ones(Dp, 1.0f);
+        cudaMemcpyAsync(s->stdv, ones.data(), Dp * sizeof(float), cudaMemcpyHostToDevice, s->stream);
+    }
+    MCHK(malloc_zero(s, &s->X, (size_t)B * din));
+    MCHK(malloc_zero(s, &s->Xt, (size_t)B * din));
+    MCHK(malloc_zero(s, &s->H1, (size_t)B * width));
+    MCHK(malloc_zero(s, &s->H2, (size_t)B * width));
+    MCHK(malloc_zero(s, &s->H1t, (size_t)B * width));
+    MCHK(malloc_zero(s, &s->H2t, (size_t)B * width));
+    MCHK(malloc_zero(s, &s->Y, (size_t)B * Dp));
+    MCHK(malloc_zero(s, &s->dY, (size_t)B * Dp));
+    MCHK(malloc_zero(s, &s->dYt, (size_t)B * Dp));
+    MCHK(malloc_zero(s, &s->dH, (size_t)B * width));
+    MCHK(malloc_zero(s, &s->dZ2, (size_t)B * width));
+    MCHK(malloc_zero(s, &s->dZ2t, (size_t)B * width));
+    MCHK(malloc_zero(s, &s->dZ1, (size_t)B * width));
+    MCHK(malloc_zero(s, &s->dZ1t, (size_t)B * width));
+    s->work_floats = (size_t)64 * B * width;
+    MCHK(malloc_zero(s, &s->work, s->work_floats));
+    MCHK(malloc_zero(s, &s->loss_part, 148 * 8));
+    MCHK(malloc_zero(s, &s->loss, 1));
+    MCHK(malloc_zero(s, &s->err, 1));
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        s->last_error = std::string("set-up: ") + cudaGetErrorString(e);
+        return bail(MFS_ERR_CUDA);
+    }
+#undef MCHK
+    *out = s;
+    return MFS_OK;
+}
+
+void mfs_mlp_destroy(mfs_mlp* s) {
+    if (!s) return;
+    cudaSetDevice(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (void* p : s->allocs) cudaFree(p);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+const char* mfs_mlp_last_error(const mfs_mlp* s) {
+    return s ? s->last_error.c_str() : g_mlp_error.c_str();
+}
+
+mfs_status mfs_mlp_set_output_scaling(mfs_mlp* s, const float* mean, const float* stdv) {
+    if (!s || !mean || !stdv) return MFS_ERR_INVALID;
+    for (int j = 0; j < s->dout; ++j)
+        if (!(stdv[j] > 0.f) || !std::isfinite(stdv[j]) || !std::isfinite(mean[j]))
+            return mfail(s, MFS_ERR_INVALID, "output scaling: std must be positive and finite");
+    cudaError_t e = cudaMemcpyAsync(s->mean, mean, s->dout * sizeof(float), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->stdv, stdv, s->dout * sizeof(float), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? MFS_OK : mfail(s, MFS_ERR_CUDA, cudaGetErrorString(e));
+}
+
+mfs_status mfs_mlp_forward(mfs_mlp* s, int32_t batch, const float* x, float* y, int32_t denormalize) {
+    if (!s || !x || !y || batch < 1 || batch > s->maxb) return MFS_ERR_INVALID;
+    cudaSetDevice(s->device);
+    k_to_bf16<<<grid1((long long)batch * s->din), 256, 0, s->stream>>>(x, s->X, (long long)batch * s->din);
+    MTRY(forward_bf16(s, batch));
+    if (denormalize)
+        k_denorm<<<grid1((long long)batch * s->doutp), 256, 0, s->stream>>>(s->Y, s->mean, s->stdv, batch, s->doutp);
+    if (cudaMemcpy2DAsync(y, (size_t)s->dout * sizeof(float), s->Y, (size_t)s->doutp * sizeof(float),
+                          (size_t)s->dout * sizeof(float), batch, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
+        return mfail(s, MFS_ERR_CUDA, "copy of the output");
+    return check_err(s);
+}
+
+// Loss and gradients of one batch (no update); the gradients stay in the MLP (mfs_mlp_get_grads).
+mfs_status mfs_mlp_backward(mfs_mlp* s, int32_t batch, const float* x, const float* target, double* loss) {
+    if (!s || !x || !target || batch < 1 || batch > s->maxb || batch % 8) return MFS_ERR_INVALID;
+    cudaSetDevice(s->device);
+    const int B = batch, W = s->width, D = s->doutp, I = s->din;
+    cudaStream_t st = s->stream;
+    k_to_bf16<<<grid1((long long)B * I), 256, 0, st>>>(x, s->X, (long long)B * I);
+    MTRY(forward_bf16(s, B));
+    const int lb = grid1((long long)B * D);
+    k_mse<<<lb, 256, 0, st>>>(s->Y, target, s->mean, s->stdv, B, s->dout, D, s->dY, s->loss_part);
+    k_sum_parts<<<1, 32, 0, st>>>(s->loss_part, lb, 1.0 / ((double)B * s->dout), s->loss);
+    // layer 3: dW3 = dY^T H2, db3 = colsum(dY), dH2 = dY W3
+    transpose(s->dY, s->dYt, B, D, st);
+    transpose(s->H2, s->H2t, B, W, st);
+    MTRY(run_gemm(s, D, W, B, s->dYt, s->H2t, nullptr, 0, 1, s->gW[2], 1));
+    k_colsum<<<(D + 255) / 256, 256, 0, st>>>(s->dY, B, D, s->gb[2]);
+    transpose(s->Wh[2], s->Wt[2], D, W, st);
+    MTRY(run_gemm(s, B, W, D, s->dY, s->Wt[2], nullptr, 0, 1, s->dH, splits_for(s, B, W, D)));
+    k_relu_bwd<<<grid1((long long)B * W), 256, 0, st>>>(s->dH, s->H2, s->dZ2, (long long)B * W);
+    // layer 2
+    transpose(s->dZ2, s->dZ2t, B, W, st);
+    transpose(s->H1, s->H1t, B, W, st);
+    MTRY(run_gemm(s, W, W, B, s->dZ2t, s->H1t, nullptr, 0, 1, s->gW[1], 1));
+    k_colsum<<<(W + 255) / 256, 256, 0, st>>>(s->dZ2, B, W, s->gb[1]);
+    transpose(s->Wh[1], s->Wt[1], W, W, st);
+    MTRY(run_gemm(s, B, W, W, s->dZ2, s->Wt[1], nullptr, 0, 1, s->dH, splits_for(s, B, W, W)));
+    k_relu_bwd<<<grid1((long long)B * W), 256, 0, st>>>(s->dH, s->H1, s->dZ1, (long long)B * W);
+    // layer 1
+    transpose(s->dZ1, s->dZ1t, B, W, st);
+    transpose(s->X, s->Xt, B, I, st);
+    MTRY(run_gemm(s, W, I, B, s->dZ1t, s->Xt, nullptr, 0, 1, s->gW[0], 1));
+    k_colsum<<<(W + 255) / 256, 256, 0, st>>>(s->dZ1, B, W, s->gb[0]);
+    if (cudaGetLastError() != cudaSuccess) return mfail(s, MFS_ERR_CUDA, "mlp backward launch");
+    if (loss && cudaMemcpyAsync(loss, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return mfail(s, MFS_ERR_CUDA, "loss copy");
+    return check_err(s);
+}
+
+// One Adam step with the gradients of the last mfs_mlp_backward.
+mfs_status mfs_mlp_adam_step(mfs_mlp* s, float lr) {
+    if (!s || !(lr > 0.f)) return MFS_ERR_INVALID;
+    cudaSetDevice(s->device);
+    ++s->step;
+    const float c1 = 1.f - std::pow(s->beta1, (float)s->step), c2 = 1.f - std::pow(s->beta2, (float)s->step);
+    for (int l = 0; l < 3; ++l) {
+        const long long cw = (long long)layer_in(s, l) * layer_out(s, l), cb = layer_out(s, l);
+        k_adam<<<grid1(cw), 256, 0, s->stream>>>(s->W[l], s->gW[l], s->mW[l], s->vW[l], s->Wh[l], cw, lr, s->beta1,
+                                                 s->beta2, s->eps, c1, c2);
+        k_adam<<<grid1(cb), 256, 0, s->stream>>>(s->b[l], s->gb[l], s->mb[l], s->vb[l], nullptr, cb, lr, s->beta1,
+                                                 s->beta2, s->eps, c1, c2);
+    }
+    if (cudaGetLastError() != cudaSuccess) return mfail(s, MFS_ERR_CUDA, "adam launch");
+    return check_err(s);
+}
+
+mfs_status mfs_mlp_train_step(mfs_mlp* s, int32_t batch, const float* x, const float* target, float lr, double* loss) {
+    MTRY(mfs_mlp_backward(s, batch, x, target, loss));
+    return mfs_mlp_adam_step(s, lr);
+}
+
+// Host copies of layer l's FP32 master weights [out][in] and bias (either may be NULL); set copies
+// them in and refreshes the BF16 copy. Gradients of the last backward pass likewise.
+mfs_status mfs_mlp_get_params(mfs_mlp* s, int32_t l, float* W, float* b) {
+    if (!s || l < 0 || l > 2) return MFS_ERR_INVALID;
+    const size_t cw = (size_t)layer_in(s, l) * user_out(s, l), cb = user_out(s, l);
+    if (W && cudaMemcpy(W, s->W[l], cw * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return MFS_ERR_CUDA;
+    if (b && cudaMemcpy(b, s->b[l], cb * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return MFS_ERR_CUDA;
+    return MFS_OK;
+}
+
+mfs_status mfs_mlp_set_params(mfs_mlp* s, int32_t l, const float* W, const float* b) {
+    if (!s || l < 0 || l > 2) return MFS_ERR_INVALID;
+    const size_t cw = (size_t)layer_in(s, l) * user_out(s, l), cb = user_out(s, l);
+    if (W) {
+        if (cudaMemcpy(s->W[l], W, cw * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return MFS_ERR_CUDA;
+        k_to_bf16<<<grid1(cw), 256, 0, s->stream>>>(s->W[l], s->Wh[l], (long long)cw);
+    }
+    if (b && cudaMemcpy(s->b[l], b, cb * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return MFS_ERR_CUDA;
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? MFS_OK : MFS_ERR_CUDA;
+}
+
+mfs_status mfs_mlp_get_grads(mfs_mlp* s, int32_t l, float* gW, float* gb) {
+    if (!s || l < 0 || l > 2) return MFS_ERR_INVALID;
+    const size_t cw = (size_t)layer_in(s, l) * user_out(s, l), cb = user_out(s, l);
+    if (gW && cudaMemcpy(gW, s->gW[l], cw * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return MFS_ERR_CUDA;
+    if (gb && cudaMemcpy(gb, s->gb[l], cb * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return MFS_ERR_CUDA;
+    return MFS_OK;
+}
+
+// Stand-alone tensor-core GEMM through the C ABI (device pointers): C = A B^T (+ bias, ReLU).
+mfs_status mfs_gemm_bf16(int64_t M, int64_t N, int64_t K, const void* A, const void* B, const float* bias, int32_t relu,
+                         int32_t out_fp32, void* C, int32_t splits, void* cuda_stream) {
+    if (M < 0 || N < 0 || K < 0 || M >= INT32_MAX || N >= INT32_MAX || K >= INT32_MAX || !A || !B || !C)
+        return MFS_ERR_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int* err = nullptr;
+    float* work = nullptr;
+    if (cudaMallocAsync((void**)&err, sizeof(int), st) != cudaSuccess) return MFS_ERR_OOM;
+    cudaMemsetAsync(err, 0, sizeof(int), st);
+    splits = std::max(1, (int)splits);
+    if (splits > 1 && cudaMallocAsync((void**)&work, (size_t)splits * M * N * sizeof(float), st) != cudaSuccess) {
+        cudaFreeAsync(err, st);
+        return MFS_ERR_OOM;
+    }
+    std::string why;
+    mfs_status s = gemm((int)M, (int)N, (int)K, static_cast<const bf16*>(A), static_cast<const bf16*>(B), bias, relu,
+                        out_fp32, C, splits, work, err, st, &why);
+    int h = 0;
+    cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (work) cudaFreeAsync(work, st);
+    cudaFreeAsync(err, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MFS_ERR_CUDA;
+    if (s != MFS_OK) return s;
+    return h ? MFS_ERR_TIMEOUT : MFS_OK;
+}
+
+}  // extern "C"

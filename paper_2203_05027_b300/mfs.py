@@ -378,3 +378,125 @@ class Batch:
         t = BatchTuning()
         self._check(self._lib.mfs_batch_tune(self._h, int(iters), ctypes.byref(t)))
         return {"threads": t.threads, "ctas_per_sm": t.ctas_per_sm, "check_every": t.check_every}
+
+
+def _load_mlp():
+    lib = load()
+    if getattr(lib, "_mlp_declared", False):
+        return lib
+    P = ctypes.c_void_p
+    i32, i64, st = ctypes.c_int32, ctypes.c_int64, ctypes.c_int
+    lib.mfs_mlp_create.argtypes = [i32, i32, i32, i32, ctypes.c_uint64, P, ctypes.POINTER(P)]
+    lib.mfs_mlp_create.restype = st
+    lib.mfs_mlp_destroy.argtypes = [P]
+    lib.mfs_mlp_destroy.restype = None
+    lib.mfs_mlp_last_error.argtypes = [P]
+    lib.mfs_mlp_last_error.restype = ctypes.c_char_p
+    lib.mfs_mlp_set_output_scaling.argtypes = [P, P, P]
+    lib.mfs_mlp_set_output_scaling.restype = st
+    lib.mfs_mlp_forward.argtypes = [P, i32, P, P, i32]
+    lib.mfs_mlp_forward.restype = st
+    lib.mfs_mlp_backward.argtypes = [P, i32, P, P, P]
+    lib.mfs_mlp_backward.restype = st
+    lib.mfs_mlp_adam_step.argtypes = [P, ctypes.c_float]
+    lib.mfs_mlp_adam_step.restype = st
+    lib.mfs_mlp_train_step.argtypes = [P, i32, P, P, ctypes.c_float, P]
+    lib.mfs_mlp_train_step.restype = st
+    for name in ("mfs_mlp_get_params", "mfs_mlp_set_params", "mfs_mlp_get_grads"):
+        getattr(lib, name).argtypes = [P, i32, P, P]
+        getattr(lib, name).restype = st
+    lib.mfs_gemm_bf16.argtypes = [i64, i64, i64, P, P, P, i32, i32, P, i32, P]
+    lib.mfs_gemm_bf16.restype = st
+    lib._mlp_declared = True
+    return lib
+
+
+def gemm_bf16(M, N, K, A_ptr, B_ptr, C_ptr, bias_ptr=None, relu=False, out_fp32=True, splits=1, stream=None):
+    """mfs_gemm_bf16 on device pointers: C = A B^T (+ bias, ReLU)."""
+    lib = _load_mlp()
+    code = lib.mfs_gemm_bf16(int(M), int(N), int(K), ctypes.c_void_p(int(A_ptr)), ctypes.c_void_p(int(B_ptr)),
+                             ctypes.c_void_p(int(bias_ptr)) if bias_ptr else None, int(bool(relu)),
+                             int(bool(out_fp32)), ctypes.c_void_p(int(C_ptr)), int(splits),
+                             ctypes.c_void_p(int(stream)) if stream else None)
+    if code != MFS_OK:
+        raise MfsError(code, "mfs_gemm_bf16")
+
+
+class MLP:
+    """The warm-start network (din -> width -> width -> dout) on the tensor cores."""
+
+    def __init__(self, din, width, dout, max_batch, seed=0, stream=None):
+        lib = _load_mlp()
+        self._lib = lib
+        h = ctypes.c_void_p()
+        code = lib.mfs_mlp_create(int(din), int(width), int(dout), int(max_batch), int(seed),
+                                  ctypes.c_void_p(int(stream)) if stream else None, ctypes.byref(h))
+        if code != MFS_OK:
+            raise MfsError(code, lib.mfs_mlp_last_error(None).decode())
+        self._h = h
+        self.din, self.width, self.dout, self.max_batch = din, width, dout, max_batch
+
+    def _check(self, code):
+        if code != MFS_OK:
+            raise MfsError(code, self._lib.mfs_mlp_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.mfs_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shapes(self):
+        return [(self.width, self.din), (self.width, self.width), (self.dout, self.width)]
+
+    def set_output_scaling(self, mean, std):
+        mean = np.ascontiguousarray(mean, np.float32)
+        std = np.ascontiguousarray(std, np.float32)
+        self._check(self._lib.mfs_mlp_set_output_scaling(self._h, _ptr(mean), _ptr(std)))
+
+    def forward(self, batch, x_ptr, y_ptr, denormalize=True):
+        self._check(self._lib.mfs_mlp_forward(self._h, int(batch), ctypes.c_void_p(int(x_ptr)),
+                                              ctypes.c_void_p(int(y_ptr)), int(bool(denormalize))))
+
+    def backward(self, batch, x_ptr, t_ptr):
+        loss = ctypes.c_double()
+        self._check(self._lib.mfs_mlp_backward(self._h, int(batch), ctypes.c_void_p(int(x_ptr)),
+                                               ctypes.c_void_p(int(t_ptr)), ctypes.byref(loss)))
+        return loss.value
+
+    def adam_step(self, lr):
+        self._check(self._lib.mfs_mlp_adam_step(self._h, ctypes.c_float(lr)))
+
+    def train_step(self, batch, x_ptr, t_ptr, lr):
+        loss = ctypes.c_double()
+        self._check(self._lib.mfs_mlp_train_step(self._h, int(batch), ctypes.c_void_p(int(x_ptr)),
+                                                 ctypes.c_void_p(int(t_ptr)), ctypes.c_float(lr),
+                                                 ctypes.byref(loss)))
+        return loss.value
+
+    def params(self):
+        out = []
+        for l, (o, i) in enumerate(self.shapes()):
+            W, b = np.empty((o, i), np.float32), np.empty(o, np.float32)
+            self._check(self._lib.mfs_mlp_get_params(self._h, l, _ptr(W), _ptr(b)))
+            out.append((W, b))
+        return out
+
+    def set_params(self, params):
+        for l, (W, b) in enumerate(params):
+            W = np.ascontiguousarray(W, np.float32)
+            b = np.ascontiguousarray(b, np.float32)
+            self._check(self._lib.mfs_mlp_set_params(self._h, l, _ptr(W), _ptr(b)))
+
+    def grads(self):
+        out = []
+        for l, (o, i) in enumerate(self.shapes()):
+            gW, gb = np.empty((o, i), np.float32), np.empty(o, np.float32)
+            self._check(self._lib.mfs_mlp_get_grads(self._h, l, _ptr(gW), _ptr(gb)))
+            out.append((gW, gb))
+        return out

@@ -1,0 +1,107 @@
+"""The tcgen05 BF16 GEMM and the warm-start MLP against CPU references: the GEMM against FP64
+products of the same BF16 inputs, the MLP's loss and gradients against the FP64 MLP oracle run on
+the BF16-rounded weights and inputs."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp as omlp
+from paper_2203_05027_b300 import build, mfs
+
+pytestmark = pytest.mark.gpu
+dev = torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build.build()
+    mfs.load()
+
+
+def rand_bf16(shape, gen, scale=1.0):
+    return (torch.randn(shape, generator=gen) * scale).to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("M,N,K,splits", [(128, 128, 64, 1), (256, 512, 512, 1), (300, 700, 96, 1),
+                                          (64, 200, 32, 1), (256, 512, 4096, 8), (200, 136, 1000, 3)])
+def test_gemm_matches_fp64_reference(M, N, K, splits):
+    g = torch.Generator().manual_seed(M * 7 + N * 3 + K)
+    A, B = rand_bf16((M, K), g), rand_bf16((N, K), g)
+    ref = A.double() @ B.double().T
+    Ad, Bd = A.to(dev), B.to(dev)
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device=dev)
+    mfs.gemm_bf16(M, N, K, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(), splits=splits,
+                  stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    err = (C.cpu().double() - ref).abs().max().item()
+    scale = (A.double().abs() @ B.double().abs().T).max().item()
+    assert err <= 1e-5 * scale, (err, scale)
+
+
+def test_gemm_bias_relu_bf16_output():
+    M, N, K = 256, 384, 128
+    g = torch.Generator().manual_seed(1)
+    A, B = rand_bf16((M, K), g), rand_bf16((N, K), g)
+    bias = torch.randn(N, generator=g)
+    ref = torch.relu(A.double() @ B.double().T + bias.double())
+    C = torch.zeros((M, N), dtype=torch.bfloat16, device=dev)
+    Ad, Bd, bd = A.to(dev), B.to(dev), bias.to(dev)  # keep the device copies alive during the call
+    mfs.gemm_bf16(M, N, K, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(), bias_ptr=bd.data_ptr(),
+                  relu=True, out_fp32=False, stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = C.cpu().double()
+    assert ((got - ref).abs() <= 1e-2 * ref.abs() + 1e-2).all()
+    assert (got[ref == 0] == 0).all()
+
+
+def bf16_round(a):
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30)
+
+
+@pytest.mark.parametrize("din,width,dout,B", [(32, 64, 200, 16), (32, 512, 700, 64)])
+def test_mlp_loss_and_gradients_match_oracle(din, width, dout, B):
+    net = mfs.MLP(din, width, dout, max_batch=B, seed=3)
+    rng = np.random.default_rng(4)
+    mean, std = rng.standard_normal(dout).astype(np.float32), rng.uniform(0.5, 2, dout).astype(np.float32)
+    net.set_output_scaling(mean, std)
+    X = rng.standard_normal((B, din)).astype(np.float32)
+    T = (rng.standard_normal((B, dout)) * 2).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev)
+    loss = net.backward(B, Xd.data_ptr(), Td.data_ptr())
+    params = [(bf16_round(W), b.astype(np.float64)) for W, b in net.params()]
+    grads = net.grads()
+    # the oracle keeping the same arrays in BF16 as the device: only accumulation order differs
+    oloss, ograds = omlp.loss_and_grads(params, bf16_round(X), T, mean, std, store=bf16_round)
+    assert abs(loss - oloss) <= 1e-3 * oloss, (loss, oloss)
+    for l, ((gW, gb), (oW, ob)) in enumerate(zip(grads, ograds)):
+        assert rel(gW, oW) <= 1e-2, (l, rel(gW, oW))
+        assert rel(gb, ob) <= 1e-2, (l, rel(gb, ob))
+    # against exact FP64 activations: the effect of BF16 storage stays bounded
+    floss, fgrads = omlp.loss_and_grads(params, bf16_round(X), T, mean, std)
+    assert abs(loss - floss) <= 1e-2 * floss
+    for l, ((gW, gb), (oW, ob)) in enumerate(zip(grads, fgrads)):
+        assert rel(gW, oW) <= 1e-1 and rel(gb, ob) <= 1e-1, (l, rel(gW, oW), rel(gb, ob))
+    # forward through the same weights
+    Y = torch.empty((B, dout), dtype=torch.float32, device=dev)
+    net.forward(B, Xd.data_ptr(), Y.data_ptr(), denormalize=True)
+    torch.cuda.synchronize()
+    oY, _ = omlp.forward(params, bf16_round(X), store=bf16_round)
+    assert rel(Y.cpu().numpy(), oY * std + mean) <= 1e-3
+
+
+def test_mlp_training_reduces_the_loss():
+    din, width, dout, B = 32, 128, 300, 64
+    net = mfs.MLP(din, width, dout, max_batch=B, seed=5)
+    rng = np.random.default_rng(6)
+    M = rng.standard_normal((din, dout)) / np.sqrt(din)
+    X = rng.standard_normal((B, din)).astype(np.float32)
+    T = np.tanh(X @ M).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev)
+    first = net.train_step(B, Xd.data_ptr(), Td.data_ptr(), 3e-3)
+    for _ in range(200):
+        last = net.train_step(B, Xd.data_ptr(), Td.data_ptr(), 3e-3)
+    assert last < 0.2 * first, (first, last)

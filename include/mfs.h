@@ -228,6 +228,42 @@ mfs_status mfs_batch_get_tuning(const mfs_batch* bt, mfs_batch_tuning* tuning);
 mfs_status mfs_batch_tune(mfs_batch* bt, int64_t iters, mfs_batch_tuning* chosen);
 
 /* ------------------------------------------------------------------------------------------------
+ * Shared-A solves: count problems with one constraint matrix A and cone K and their own b and c
+ * (a parametric family), iterated together. The instances' vectors are interleaved so that each
+ * nonzero's gather serves 32 instances with one coalesced load.
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct mfs_shared mfs_shared;
+
+/* A (COO, host, rules as mfs_create) and K once; count >= 1 instances; b and c start at zero
+   until mfs_shared_set_data. settings: mu, check_every, precision are used. */
+mfs_status mfs_shared_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
+                             const double* val, int64_t ncones, const mfs_cone* cones, int64_t count,
+                             const mfs_settings* settings, void* cuda_stream, mfs_shared** out);
+void mfs_shared_destroy(mfs_shared* sh);
+const char* mfs_shared_last_error(const mfs_shared* sh);
+/* b [count][m] and c [count][n]: host doubles, or device floats for the _device form. Also resets
+   every iterate to zero. */
+mfs_status mfs_shared_set_data(mfs_shared* sh, const double* b, const double* c);
+mfs_status mfs_shared_set_data_device(mfs_shared* sh, const float* b, const float* c);
+/* Zero start for every instance. */
+mfs_status mfs_shared_reset(mfs_shared* sh);
+/* Warm start of every instance from device floats x [count][n], lambda [count][m] (as
+   mfs_warm_start with z and delta defaulted). */
+mfs_status mfs_shared_warm_start_device(mfs_shared* sh, const float* x, const float* lambda);
+mfs_status mfs_shared_iterate(mfs_shared* sh, int64_t k);
+/* Residuals of every instance (out: count entries). */
+mfs_status mfs_shared_residuals(mfs_shared* sh, mfs_residuals_t* out);
+/* Iterate everything, testing each instance every check_every iterations, until all have relative
+   KKT residual <= tol or max_iter iterations ran. iters (nullable, count entries): the iteration at
+   which each instance first met tol, or -1. MFS_OK if all met it, else MFS_MAX_ITER. */
+mfs_status mfs_shared_solve(mfs_shared* sh, double tol, int64_t max_iter, int64_t* iters);
+/* Iterate, instance-major, device floats: x [count][n], lambda [count][m] (either may be NULL). */
+mfs_status mfs_shared_get_solution_device(mfs_shared* sh, float* x, float* lambda);
+/* Iterate of instance t as host doubles (any may be NULL): x, z, delta (n), lambda (m). */
+mfs_status mfs_shared_get_solution(mfs_shared* sh, int64_t t, double* x, double* lambda, double* z,
+                                   double* delta);
+
+/* ------------------------------------------------------------------------------------------------
  * Learned warm start. The paper has no counterpart; this serves parametric families of problems:
  * a 3-layer MLP theta (din) -> width -> width -> dout (ReLU after the first two layers) maps a
  * problem's parameters to a starting point (for instance x and lambda concatenated, dout = n + m)

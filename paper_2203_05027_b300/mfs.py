@@ -500,3 +500,115 @@ class MLP:
             self._check(self._lib.mfs_mlp_get_grads(self._h, l, _ptr(gW), _ptr(gb)))
             out.append((gW, gb))
         return out
+
+
+def _load_shared():
+    lib = load()
+    if getattr(lib, "_shared_declared", False):
+        return lib
+    P = ctypes.c_void_p
+    i64, st = ctypes.c_int64, ctypes.c_int
+    lib.mfs_shared_create.argtypes = [i64, i64, i64, P, P, P, i64, P, i64, ctypes.POINTER(Settings), P,
+                                      ctypes.POINTER(P)]
+    lib.mfs_shared_create.restype = st
+    lib.mfs_shared_destroy.argtypes = [P]
+    lib.mfs_shared_destroy.restype = None
+    lib.mfs_shared_last_error.argtypes = [P]
+    lib.mfs_shared_last_error.restype = ctypes.c_char_p
+    for name, args in (("mfs_shared_set_data", [P, P, P]), ("mfs_shared_set_data_device", [P, P, P]),
+                       ("mfs_shared_reset", [P]), ("mfs_shared_warm_start_device", [P, P, P]),
+                       ("mfs_shared_iterate", [P, i64]), ("mfs_shared_residuals", [P, P]),
+                       ("mfs_shared_solve", [P, ctypes.c_double, i64, P]),
+                       ("mfs_shared_get_solution_device", [P, P, P]),
+                       ("mfs_shared_get_solution", [P, i64, P, P, P, P])):
+        getattr(lib, name).argtypes = args
+        getattr(lib, name).restype = st
+    lib._shared_declared = True
+    return lib
+
+
+def _vp(p):
+    return ctypes.c_void_p(int(p)) if p else None
+
+
+class Shared:
+    """count problems sharing A and K (dict with m, n, row, col, val, cones), each with its own b, c."""
+
+    def __init__(self, prob, count, mu=1.0, check_every=50, precision="fp32", stream=None):
+        lib = _load_shared()
+        self._lib = lib
+        m, n = int(prob["m"]), int(prob["n"])
+        row = np.ascontiguousarray(prob["row"], np.int64)
+        col = np.ascontiguousarray(prob["col"], np.int64)
+        val = np.ascontiguousarray(prob["val"], np.float64)
+        cones = np.asarray(prob["cones"], np.int64).reshape(-1, 2)
+        carr = (Cone * max(len(cones), 1))()
+        for q, (k, s) in enumerate(cones):
+            carr[q].kind = int(k)
+            carr[q].size = int(s)
+        st = Settings()
+        lib.mfs_default_settings(ctypes.byref(st))
+        st.mu = float(mu)
+        st.check_every = int(check_every)
+        st.precision = {"fp64": FP64, "fp32": FP32_MIXED}[precision]
+        h = ctypes.c_void_p()
+        code = lib.mfs_shared_create(m, n, len(row), _ptr(row), _ptr(col), _ptr(val), len(cones),
+                                     ctypes.cast(carr, ctypes.c_void_p), int(count), ctypes.byref(st),
+                                     _vp(stream), ctypes.byref(h))
+        if code != MFS_OK:
+            raise MfsError(code, lib.mfs_shared_last_error(None).decode())
+        self._h = h
+        self.m, self.n, self.count = m, n, int(count)
+
+    def _check(self, code, ok=(MFS_OK,)):
+        if code not in ok:
+            raise MfsError(code, self._lib.mfs_shared_last_error(self._h).decode())
+        return code
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.mfs_shared_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_data(self, b, c):
+        b = np.ascontiguousarray(b, np.float64).reshape(self.count, self.m)
+        c = np.ascontiguousarray(c, np.float64).reshape(self.count, self.n)
+        self._check(self._lib.mfs_shared_set_data(self._h, _ptr(b), _ptr(c)))
+
+    def set_data_device(self, b_ptr, c_ptr):
+        self._check(self._lib.mfs_shared_set_data_device(self._h, _vp(b_ptr), _vp(c_ptr)))
+
+    def reset(self):
+        self._check(self._lib.mfs_shared_reset(self._h))
+
+    def warm_start_device(self, x_ptr, lam_ptr):
+        self._check(self._lib.mfs_shared_warm_start_device(self._h, _vp(x_ptr), _vp(lam_ptr)))
+
+    def iterate(self, k):
+        self._check(self._lib.mfs_shared_iterate(self._h, int(k)))
+
+    def residuals(self):
+        out = (Residuals * self.count)()
+        self._check(self._lib.mfs_shared_residuals(self._h, ctypes.cast(out, ctypes.c_void_p)))
+        return [dict({f: getattr(r, f) for f in RESID_FIELDS}, iter=r.iter) for r in out]
+
+    def solve(self, tol, max_iter):
+        its = np.zeros(self.count, np.int64)
+        code = self._check(self._lib.mfs_shared_solve(self._h, float(tol), int(max_iter), _ptr(its)),
+                           ok=(MFS_OK, MFS_MAX_ITER))
+        return STATUS_NAMES[code], its
+
+    def solution_device(self, x_ptr=None, lam_ptr=None):
+        self._check(self._lib.mfs_shared_get_solution_device(self._h, _vp(x_ptr), _vp(lam_ptr)))
+
+    def solution(self, t):
+        x, z, d = (np.empty(self.n) for _ in range(3))
+        lam = np.empty(self.m)
+        self._check(self._lib.mfs_shared_get_solution(self._h, int(t), _ptr(x), _ptr(lam), _ptr(z), _ptr(d)))
+        return {"x": x, "lam": lam, "z": z, "delta": d}

@@ -281,6 +281,12 @@ void mfs_mlp_destroy(mfs_mlp* net);
 const char* mfs_mlp_last_error(const mfs_mlp* net);
 /* Targets are standardised per output as (t - mean) / std; host arrays of dout floats. */
 mfs_status mfs_mlp_set_output_scaling(mfs_mlp* net, const float* mean, const float* stdv);
+/* Sets the standardisation from a device target matrix [count][dout] (row-major FP32): per output,
+   mean and standard deviation over the rows (FP64 sums), the deviation raised to min_std (> 0) where
+   it is smaller, so that outputs constant over the data stay finite. Synchronous. */
+mfs_status mfs_mlp_fit_output_scaling(mfs_mlp* net, int64_t count, const float* targets, float min_std);
+/* Host copies of the current mean and std (dout floats each); NULL skips. */
+mfs_status mfs_mlp_get_output_scaling(mfs_mlp* net, float* mean, float* stdv);
 /* y = net(x) for batch <= max_batch rows; denormalize != 0 undoes the standardisation. */
 mfs_status mfs_mlp_forward(mfs_mlp* net, int32_t batch, const float* x, float* y, int32_t denormalize);
 /* Mean squared error of one batch (batch a multiple of 8) and its gradients, kept in the handle;

@@ -231,6 +231,49 @@ __global__ void k_denorm(float* __restrict__ Y, const float* __restrict__ mean, 
     }
 }
 
+// Per-output mean and standard deviation of a target matrix T [count][D] (row-major FP32): block
+// (bx, p) takes 256 columns and the p-th slice of the rows, sums t - T[0][j] (a shift that keeps the
+// sums small) and its square in FP32 over runs of 32 rows and adds each run into FP64.
+__global__ void k_colstats_part(const float* __restrict__ T, long long count, int D, long long rows_per_part,
+                                double* __restrict__ part) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= D) return;
+    const long long r0 = blockIdx.y * rows_per_part;
+    const long long r1 = std::min<long long>(count, r0 + rows_per_part);
+    const float shift = T[j];
+    double s1 = 0.0, s2 = 0.0;
+    for (long long r = r0; r < r1; r += 32) {
+        const long long re = std::min<long long>(r1, r + 32);
+        float a1 = 0.f, a2 = 0.f;
+        for (long long q = r; q < re; ++q) {
+            const float d = T[q * D + j] - shift;
+            a1 += d;
+            a2 = fmaf(d, d, a2);
+        }
+        s1 += a1;
+        s2 += a2;
+    }
+    part[((long long)blockIdx.y * D + j) * 2] = s1;
+    part[((long long)blockIdx.y * D + j) * 2 + 1] = s2;
+}
+
+// mean_j = shift + S1/count, std_j = max(sqrt(S2/count - (S1/count)^2), min_std).
+__global__ void k_colstats_final(const float* __restrict__ T, const double* __restrict__ part, int parts,
+                                 long long count, int D, float min_std, float* __restrict__ mean,
+                                 float* __restrict__ stdv) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= D) return;
+    double s1 = 0.0, s2 = 0.0;
+    for (int p = 0; p < parts; ++p) {
+        s1 += part[((long long)p * D + j) * 2];
+        s2 += part[((long long)p * D + j) * 2 + 1];
+    }
+    const double m1 = s1 / (double)count;
+    const double var = fmax(s2 / (double)count - m1 * m1, 0.0);
+    mean[j] = (float)((double)T[j] + m1);
+    stdv[j] = fmaxf((float)sqrt(var), min_std);
+}
+
 inline int grid1(long long count) {
     return (int)std::max<long long>(1, std::min<long long>((count + 255) / 256, 148 * 8));
 }
@@ -466,6 +509,35 @@ mfs_status mfs_mlp_set_output_scaling(mfs_mlp* s, const float* mean, const float
             return mfail(s, MFS_ERR_INVALID, "output scaling: std must be positive and finite");
     cudaError_t e = cudaMemcpyAsync(s->mean, mean, s->dout * sizeof(float), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->stdv, stdv, s->dout * sizeof(float), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? MFS_OK : mfail(s, MFS_ERR_CUDA, cudaGetErrorString(e));
+}
+
+mfs_status mfs_mlp_fit_output_scaling(mfs_mlp* s, int64_t count, const float* targets, float min_std) {
+    if (!s || !targets || count < 1 || !(min_std > 0.f) || !std::isfinite(min_std)) return MFS_ERR_INVALID;
+    cudaSetDevice(s->device);
+    const int D = s->dout;
+    const int parts = (int)std::min<long long>(64, (count + 255) / 256);
+    const long long per = (count + parts - 1) / parts;
+    double* part = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&part), (size_t)parts * D * 2 * sizeof(double), s->stream);
+    if (e != cudaSuccess) return mfail(s, MFS_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    k_colstats_part<<<dim3((D + 255) / 256, parts), 256, 0, s->stream>>>(targets, count, D, per, part);
+    k_colstats_final<<<(D + 255) / 256, 256, 0, s->stream>>>(targets, part, parts, count, D, min_std, s->mean,
+                                                             s->stdv);
+    e = cudaGetLastError();
+    cudaFreeAsync(part, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? MFS_OK : mfail(s, MFS_ERR_CUDA, cudaGetErrorString(e));
+}
+
+mfs_status mfs_mlp_get_output_scaling(mfs_mlp* s, float* mean, float* stdv) {
+    if (!s) return MFS_ERR_INVALID;
+    cudaSetDevice(s->device);
+    cudaError_t e = cudaSuccess;
+    if (mean) e = cudaMemcpyAsync(mean, s->mean, s->dout * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
+    if (stdv && e == cudaSuccess)
+        e = cudaMemcpyAsync(stdv, s->stdv, s->dout * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     return e == cudaSuccess ? MFS_OK : mfail(s, MFS_ERR_CUDA, cudaGetErrorString(e));
 }

@@ -394,6 +394,10 @@ def _load_mlp():
     lib.mfs_mlp_last_error.restype = ctypes.c_char_p
     lib.mfs_mlp_set_output_scaling.argtypes = [P, P, P]
     lib.mfs_mlp_set_output_scaling.restype = st
+    lib.mfs_mlp_fit_output_scaling.argtypes = [P, i64, P, ctypes.c_float]
+    lib.mfs_mlp_fit_output_scaling.restype = st
+    lib.mfs_mlp_get_output_scaling.argtypes = [P, P, P]
+    lib.mfs_mlp_get_output_scaling.restype = st
     lib.mfs_mlp_forward.argtypes = [P, i32, P, P, i32]
     lib.mfs_mlp_forward.restype = st
     lib.mfs_mlp_backward.argtypes = [P, i32, P, P, P]
@@ -458,6 +462,16 @@ class MLP:
         mean = np.ascontiguousarray(mean, np.float32)
         std = np.ascontiguousarray(std, np.float32)
         self._check(self._lib.mfs_mlp_set_output_scaling(self._h, _ptr(mean), _ptr(std)))
+
+    def fit_output_scaling(self, count, targets_ptr, min_std=1e-3):
+        """Standardisation from a device target matrix [count][dout] (FP32)."""
+        self._check(self._lib.mfs_mlp_fit_output_scaling(self._h, int(count), ctypes.c_void_p(int(targets_ptr)),
+                                                         ctypes.c_float(min_std)))
+
+    def output_scaling(self):
+        mean, std = np.empty(self.dout, np.float32), np.empty(self.dout, np.float32)
+        self._check(self._lib.mfs_mlp_get_output_scaling(self._h, _ptr(mean), _ptr(std)))
+        return mean, std
 
     def forward(self, batch, x_ptr, y_ptr, denormalize=True):
         self._check(self._lib.mfs_mlp_forward(self._h, int(batch), ctypes.c_void_p(int(x_ptr)),

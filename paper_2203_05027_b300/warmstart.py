@@ -1,0 +1,250 @@
+"""Learned warm start for a parametric LP family.
+
+The family: A fixed (m rows, n columns, a fixed number of nonzeros per column, N(0,1) values),
+x0 ~ U[0,1]^n, y0 ~ N(0,1)^m, s0 ~ U[0,1]^n, b0 = A x0, c0 = A^T y0 + s0, K = R^n_+; the
+parameter theta ~ N(0, I_p) moves b = b0 + B_b theta and c = c0 + B_c theta, with B_b, B_c
+having i.i.d. N(0, sigma^2) entries. Solutions (x, lambda) of sampled members, produced by the
+shared-A solver (mfs_shared_*), train the tensor-core MLP (mfs_mlp_*) theta -> (x, lambda);
+its prediction then warm-starts the solver (mfs_shared_warm_start_device).
+
+Every arithmetic step of solving and training runs in libmfs; this module draws the seeded
+family, moves buffers and records counts and times. torch provides device memory only.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import instances as I
+from . import mfs
+
+
+def family(seed=0, m=20_000, n=50_000, nnz_per_col=8, p=32, sigma=0.1):
+    base = I.lp_from_degrees(m, n, np.full(n, nnz_per_col), [seed, 40], name=f"param_lp_m{m}_n{n}")
+    rng = np.random.default_rng([seed, 41])
+    Bb = rng.normal(0.0, sigma, (m, p))
+    Bc = rng.normal(0.0, sigma, (n, p))
+    return {"base": base, "Bb": Bb, "Bc": Bc, "p": p}
+
+
+def thetas(count, seed, p=32):
+    return np.random.default_rng([seed, 42]).standard_normal((count, p))
+
+
+def data_of(fam, theta):
+    base = fam["base"]
+    b = base["b"][None, :] + theta @ fam["Bb"].T
+    c = base["c"][None, :] + theta @ fam["Bc"].T
+    return b, c
+
+
+def solve_batch(sh, fam, theta, tol, max_iter, warm=None):
+    """Solve the members theta (len(theta) == sh.count) from the cold start or, with
+    warm = (x_ptr, lam_ptr), from a warm start. Returns (iterations per member, seconds)."""
+    import torch
+    b, c = data_of(fam, theta)
+    sh.set_data(b, c)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if warm is not None:
+        sh.warm_start_device(*warm)
+    status, its = sh.solve(tol, max_iter)
+    torch.cuda.synchronize()
+    return its, time.perf_counter() - t0
+
+
+def generate(fam, count, seed, tol, max_iter, batch=256, check_every=250):
+    """Training data: theta (count x p, FP32) and targets [x | lambda] (count x (n+m), FP32) on the
+    device, from cold-start solves to tol. Members that miss tol keep their last iterate."""
+    import torch
+    base = fam["base"]
+    n, m = base["n"], base["m"]
+    th = thetas(count, seed, fam["p"])
+    T = torch.empty((count, n + m), dtype=torch.float32, device="cuda")
+    X = torch.empty((batch, n), dtype=torch.float32, device="cuda")
+    L = torch.empty((batch, m), dtype=torch.float32, device="cuda")
+    sh = mfs.Shared(base, batch, check_every=check_every, precision="fp32")
+    iters = []
+    t0 = time.perf_counter()
+    for s0 in range(0, count, batch):
+        k = min(batch, count - s0)
+        tb = np.zeros((batch, fam["p"]))
+        tb[:k] = th[s0:s0 + k]
+        its, _ = solve_batch(sh, fam, tb, tol, max_iter)
+        iters.extend(its[:k].tolist())
+        sh.solution_device(X.data_ptr(), L.data_ptr())
+        T[s0:s0 + k, :n].copy_(X[:k])
+        T[s0:s0 + k, n:].copy_(L[:k])
+    torch.cuda.synchronize()
+    sh.close()
+    theta = torch.from_numpy(th.astype(np.float32)).cuda()
+    return theta, T, np.asarray(iters), time.perf_counter() - t0
+
+
+def train_fn(net, theta, T, epochs, lr, batch, lr_final=None):
+    """Minibatch Adam over the training rows (already i.i.d. draws, taken in order), the step size
+    falling from lr to lr_final (default lr / 20) along a cosine over the epochs."""
+    import math
+    import torch
+    lr_final = lr / 20 if lr_final is None else lr_final
+    count = theta.shape[0]
+    losses = []
+    t0 = time.perf_counter()
+    for ep in range(epochs):
+        a = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * ep / max(epochs - 1, 1)))
+        tot, steps = 0.0, 0
+        for s0 in range(0, count - batch + 1, batch):
+            tot += net.train_step(batch, theta[s0].data_ptr(), T[s0].data_ptr(), a)
+            steps += 1
+        losses.append(tot / max(steps, 1))
+    torch.cuda.synchronize()
+    return losses, time.perf_counter() - t0
+
+
+def eval_loss(net, theta, T, batch):
+    """Mean squared error on standardised targets (no update), averaged over full batches."""
+    count = theta.shape[0]
+    tot, steps = 0.0, 0
+    for s0 in range(0, count - batch + 1, batch):
+        tot += net.backward(batch, theta[s0].data_ptr(), T[s0].data_ptr())
+        steps += 1
+    return tot / max(steps, 1)
+
+
+def predict(net, theta, n, m):
+    """MLP prediction (denormalised) split into contiguous x [count][n] and lambda [count][m]."""
+    import torch
+    count = theta.shape[0]
+    Y = torch.empty((count, n + m), dtype=torch.float32, device="cuda")
+    for s0 in range(0, count, net.max_batch):
+        k = min(net.max_batch, count - s0)
+        net.forward(k, theta[s0].data_ptr(), Y[s0].data_ptr(), denormalize=True)
+    return Y[:, :n].contiguous(), Y[:, n:].contiguous()
+
+
+def evaluate(fam, net, theta, tol, max_iter, mu=1.0, check_every=100, precision="fp32"):
+    """Cold against learned warm start on the members theta (count x p, host): per member, the
+    iteration at which the relative KKT residual first met tol (-1 if never within max_iter), and
+    the wall time for the whole set (the warm arm includes the network's inference)."""
+    import torch
+    base = fam["base"]
+    n, m = base["n"], base["m"]
+    count = theta.shape[0]
+    sh = mfs.Shared(base, count, mu=mu, check_every=check_every, precision=precision)
+    b, c = data_of(fam, theta)
+    out = {}
+    # cold
+    sh.set_data(b, c)
+    r0 = [r["kkt"] for r in sh.residuals()]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, its = sh.solve(tol, max_iter)
+    torch.cuda.synchronize()
+    out["cold"] = {"iters": its, "seconds": time.perf_counter() - t0, "kkt0": np.asarray(r0)}
+    Xc = torch.empty((count, n), dtype=torch.float32, device="cuda")
+    Lc = torch.empty((count, m), dtype=torch.float32, device="cuda")
+    sh.solution_device(Xc.data_ptr(), Lc.data_ptr())
+    # warm
+    sh.set_data(b, c)
+    th = torch.from_numpy(np.ascontiguousarray(theta, np.float32)).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Xw, Lw = predict(net, th, n, m)
+    sh.warm_start_device(Xw.data_ptr(), Lw.data_ptr())
+    torch.cuda.synchronize()
+    t_pred = time.perf_counter() - t0
+    r0 = [r["kkt"] for r in sh.residuals()]
+    t1 = time.perf_counter()
+    _, its = sh.solve(tol, max_iter)
+    torch.cuda.synchronize()
+    out["warm"] = {"iters": its, "seconds": t_pred + time.perf_counter() - t1, "predict_seconds": t_pred,
+                   "kkt0": np.asarray(r0)}
+    ex = (torch.linalg.vector_norm(Xw - Xc, dim=1) / torch.linalg.vector_norm(Xc, dim=1).clamp_min(1e-30)).cpu().numpy()
+    el = (torch.linalg.vector_norm(Lw - Lc, dim=1) / torch.linalg.vector_norm(Lc, dim=1).clamp_min(1e-30)).cpu().numpy()
+    out["pred_rel_err_x"], out["pred_rel_err_lam"] = ex, el
+    sh.close()
+    return out
+
+
+def _its_summary(a):
+    a = np.asarray(a)
+    ok = a[a >= 0]
+    return {"converged": int(ok.size), "of": int(a.size),
+            "mean": float(ok.mean()) if ok.size else None,
+            "median": float(np.median(ok)) if ok.size else None,
+            "p90": float(np.percentile(ok, 90)) if ok.size else None}
+
+
+def run(train=50_000, test=1000, m=20_000, n=50_000, nnz_per_col=8, p=32, sigma=0.1, seed=0, data_tol=1e-3,
+        data_cap=10_000, data_batch=512, width=512, epochs=100, lr=1e-3, batch=256, eval_tol=1e-6,
+        eval_cap=250_000, mu=1.0, single=0, log=print):
+    """The whole experiment: generate, fit, train, evaluate warm against cold on held-out members,
+    and (single > 0) time that many plain one-at-a-time cold solves. Logs one dict per stage and
+    returns the evaluation summary."""
+    import json
+    import torch
+    fam = family(seed, m, n, nnz_per_col, p, sigma)
+    base = fam["base"]
+    theta, T, its, sec = generate(fam, train, seed + 1, data_tol, data_cap, batch=data_batch)
+    log(json.dumps({"stage": "data", "solves": train, "tol": data_tol, "cap": data_cap, "seconds": sec,
+                    **_its_summary(its)}))
+    thv, Tv, _, _ = generate(fam, max(batch, 512), seed + 5, data_tol, data_cap, batch=max(batch, 512))
+    net = mfs.MLP(p, width, n + m, batch, seed=seed)
+    net.fit_output_scaling(train, T.data_ptr(), 1e-3)
+    losses, tsec = train_fn(net, theta, T, epochs, lr, batch)
+    val = eval_loss(net, thv, Tv, batch)
+    log(json.dumps({"stage": "train", "epochs": epochs, "steps": epochs * (train // batch), "seconds": tsec,
+                    "loss_first": losses[0], "loss_last": losses[-1], "val_loss": val}))
+    del T, Tv
+    torch.cuda.empty_cache()
+    th_test = thetas(test, seed + 7, p)
+    res = evaluate(fam, net, th_test, eval_tol, eval_cap, mu=mu)
+    summary = {"stage": "evaluate", "tol": eval_tol, "cap": eval_cap, "members": test}
+    for arm in ("cold", "warm"):
+        r = res[arm]
+        summary[arm] = {"seconds": r["seconds"], "kkt0_median": float(np.median(r["kkt0"])),
+                        **_its_summary(r["iters"])}
+    summary["warm"]["predict_seconds"] = res["warm"]["predict_seconds"]
+    ic, iw = res["cold"]["iters"], res["warm"]["iters"]
+    both = (ic > 0) & (iw > 0)
+    summary["paired"] = int(both.sum())
+    summary["iters_ratio_median"] = float(np.median(iw[both] / ic[both])) if both.any() else None
+    summary["pred_rel_err_x_median"] = float(np.median(res["pred_rel_err_x"]))
+    summary["pred_rel_err_lam_median"] = float(np.median(res["pred_rel_err_lam"]))
+    log(json.dumps(summary))
+    if single > 0:
+        b, c = data_of(fam, th_test[:single])
+        secs, iters = [], []
+        for t in range(single):
+            prob = dict(base, b=b[t], c=c[t])
+            s = mfs.Solver(prob, mu=mu, check_every=100, precision="fp32")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, it = s.solve(eval_tol, eval_cap)
+            torch.cuda.synchronize()
+            secs.append(time.perf_counter() - t0)
+            iters.append(it)
+            s.close()
+        log(json.dumps({"stage": "single_cold", "solves": single, "seconds_mean": float(np.mean(secs)),
+                        "iters": iters}))
+        summary["single_cold_seconds_mean"] = float(np.mean(secs))
+    return summary
+
+
+def main(argv=None):
+    import argparse
+    ap = argparse.ArgumentParser(description="learned warm start: generate, train, evaluate warm vs cold")
+    for k, v in (("train", 50_000), ("test", 1000), ("m", 20_000), ("n", 50_000), ("nnz_per_col", 8), ("p", 32),
+                 ("seed", 0), ("data_cap", 10_000), ("data_batch", 512), ("width", 512), ("epochs", 100),
+                 ("batch", 256), ("eval_cap", 250_000), ("single", 0)):
+        ap.add_argument("--" + k.replace("_", "-"), type=int, default=v)
+    for k, v in (("sigma", 0.1), ("data_tol", 1e-3), ("lr", 1e-3), ("eval_tol", 1e-6), ("mu", 1.0)):
+        ap.add_argument("--" + k.replace("_", "-"), type=float, default=v)
+    a = ap.parse_args(argv)
+    mfs.load()
+    run(**vars(a), log=lambda s: print(s, flush=True))
+
+
+if __name__ == "__main__":
+    main()

@@ -43,7 +43,13 @@ def parse():
     ap.add_argument("--workload", default="large_lp", choices=["large_lp", "socp"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched-LP extra workload")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the extra workloads (batched LPs, shared-A family, MLP step)")
+    ap.add_argument("--warm-start", type=int, default=0, metavar="TRAIN",
+                    help="also run the learned warm-start experiment with TRAIN training solves (minutes)")
+    ap.add_argument("--warm-start-test", type=int, default=1000)
+    ap.add_argument("--section", default="all", choices=["all", "small", "batch", "shared", "mlp"],
+                    help="run only one extra workload and print its line (for profiling)")
     ap.add_argument("--tts-iters", type=int, default=300000,
                     help="also solve to 1e-6 KKT from the cold start with at most this many iterations (0: skip)")
     return ap.parse_args()
@@ -70,6 +76,16 @@ def load_peaks():
             pk = json.load(f)
         return float(pk["hbm_gbs"]), "measured"
     return 6400.0, "fallback"
+
+
+def load_peaks_raw():
+    """bf16 tensor-core peak (TFLOP/s): the measured burst figure, else the nominal fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            pk = json.load(f)
+        return {"bf16_tflops": float(pk.get("bf16_tflops", 1800.0))}
+    return {"bf16_tflops": 1800.0}
 
 
 class ClockSampler:
@@ -207,6 +223,103 @@ def batch_workload(stream, seed, iters=100):
     return out
 
 
+def small_workload(stream, seed, iters=2000):
+    """Extra workload: the 200 x 500 LP (5 nonzeros per column), 2000 FP64 iterations, through the
+    single-instance path (kernels per iteration under a CUDA graph) and as a batch of one (one CTA,
+    the instance in shared memory, all iterations in one launch)."""
+    import torch
+    from paper_2203_05027_b300 import instances as I, mfs
+    p = I.small_lp(seed)
+    out = {"workload": "small LP m=200 n=500 5 nnz/col, FP64", "iterations": iters}
+    s = mfs.Solver(p, precision="fp64", check_every=iters, polish_iters=0, stream=stream.cuda_stream)
+    s.iterate(iters)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.iterate(iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["single_path_us_per_iteration"] = round(e0.elapsed_time(e1) * 1e3 / iters, 3)
+    s.close()
+    bt = mfs.Batch([p], precision="fp64", check_every=iters, stream=stream.cuda_stream)
+    bt.iterate(iters)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    bt.iterate(iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["one_cta_us_per_iteration"] = round(e0.elapsed_time(e1) * 1e3 / iters, 3)
+    bt.close()
+    return out
+
+
+def shared_workload(stream, seed, count=1024, iters=200):
+    """Extra workload: `count` members of the parametric LP family (A fixed, m = 20,000, n = 50,000,
+    8 nonzeros per column; b and c moved by theta ~ N(0, I_32)) iterated together by the shared-A
+    solver (FP32 sweep); `iters` iterations timed with CUDA events."""
+    import torch
+    from paper_2203_05027_b300 import mfs, warmstart as W
+    fam = W.family(seed)
+    base = fam["base"]
+    sh = mfs.Shared(base, count, check_every=iters, precision="fp32", stream=stream.cuda_stream)
+    sh.set_data(*W.data_of(fam, W.thetas(count, seed + 1)))
+    sh.iterate(20)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sh.iterate(iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    o, m, n = len(base["row"]), base["m"], base["n"]
+    bytes_iter = count * (36 * n + 24 * m) + 16 * o
+    sh.close()
+    return {"workload": f"parametric LP family, {count} members sharing A (m={m}, n={n}, o={o})",
+            "ms_per_iteration": round(ms, 5), "us_per_member_iteration": round(ms * 1e3 / count, 4),
+            "value": o * count / (ms * 1e-3), "unit": UNIT,
+            "algorithmic_gbs": round(bytes_iter / (ms * 1e-3) / 1e9, 1)}
+
+
+def mlp_workload(stream, peaks, batch=256, steps=20):
+    """Extra workload: one Adam training step of the warm-start network (32 -> 512 -> 512 -> 70,000,
+    BF16 tensor-core GEMMs, FP32 master weights) on a batch of 256, and its forward pass; FLOPs are
+    those of the six GEMMs (2 B (32*512 + 512*512 + 512*70000) forward, twice that backward)."""
+    import torch
+    from paper_2203_05027_b300 import mfs
+    din, width, dout = 32, 512, 70_000
+    net = mfs.MLP(din, width, dout, batch, seed=0, stream=stream.cuda_stream)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    X = torch.randn((batch, din), device="cuda", generator=g)
+    T = torch.randn((batch, dout), device="cuda", generator=g)
+    Y = torch.empty((batch, dout), device="cuda")
+    for _ in range(3):
+        net.train_step(batch, X.data_ptr(), T.data_ptr(), 1e-4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        net.train_step(batch, X.data_ptr(), T.data_ptr(), 1e-4)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1) / steps
+    e0.record(stream)
+    for _ in range(steps):
+        net.forward(batch, X.data_ptr(), Y.data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / steps
+    net.close()
+    fwd_flop = 2.0 * batch * (din * width + width * width + width * dout)
+    peak = peaks.get("bf16_tflops")
+    tf_train = 3 * fwd_flop / (train_ms * 1e-3) / 1e12
+    return {"workload": f"MLP {din}-{width}-{width}-{dout}, batch {batch}",
+            "train_step_ms": round(train_ms, 4), "forward_ms": round(fwd_ms, 4),
+            "train_tflops": round(tf_train, 1), "forward_tflops": round(fwd_flop / (fwd_ms * 1e-3) / 1e12, 1),
+            "bf16_peak_tflops": peak, "train_frac_of_measured_peak": round(tf_train / peak, 4) if peak else None,
+            "note": "train step = forward, loss, backward GEMMs, transposes, Adam on 36M FP32 parameters, "
+                    "and a host read of the loss"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -246,6 +359,14 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    if args.section != "all":
+        stream = torch.cuda.current_stream()
+        fn = {"small": lambda: small_workload(stream, rank), "batch": lambda: batch_workload(stream, rank), "shared": lambda: shared_workload(stream, rank),
+              "mlp": lambda: mlp_workload(stream, load_peaks_raw())}[args.section]
+        if rank == 0:
+            print(json.dumps({"section": args.section, **fn()}), flush=True)
+        return
 
     # replicas only: each rank solves its own instance (seeded by rank), no data-path collective
     prob = make_problem(args.workload, rank)
@@ -305,6 +426,13 @@ def main():
 
     if not args.no_batch:
         extra["batch_lps"] = batch_workload(stream, rank)
+        extra["small_lp"] = small_workload(stream, rank)
+        extra["shared_param_lp"] = shared_workload(stream, rank)
+        extra["mlp"] = mlp_workload(stream, load_peaks_raw())
+    if args.warm_start:
+        from paper_2203_05027_b300 import warmstart as W
+        extra["warm_start"] = W.run(train=args.warm_start, test=args.warm_start_test, seed=rank,
+                                    log=lambda t: print(t, file=sys.stderr, flush=True))
 
     e2e = None
     if not args.no_e2e:

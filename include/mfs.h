@@ -274,7 +274,8 @@ mfs_status mfs_shared_get_solution(mfs_shared* sh, int64_t t, double* x, double*
  * ---------------------------------------------------------------------------------------------- */
 typedef struct mfs_mlp mfs_mlp;
 
-/* din, width, max_batch: positive multiples of 8; dout >= 1. Weights He-uniform from seed. */
+/* din, width, max_batch: positive multiples of 8, max_batch <= 65535; dout >= 1. Weights He-uniform
+   from seed. */
 mfs_status mfs_mlp_create(int32_t din, int32_t width, int32_t dout, int32_t max_batch, uint64_t seed,
                           void* cuda_stream, mfs_mlp** out);
 void mfs_mlp_destroy(mfs_mlp* net);
@@ -308,6 +309,19 @@ mfs_status mfs_mlp_get_grads(mfs_mlp* net, int32_t layer, float* gW, float* gb);
    Synchronous; allocates its split workspace on the stream. */
 mfs_status mfs_gemm_bf16(int64_t M, int64_t N, int64_t K, const void* A, const void* B, const float* bias,
                          int32_t relu, int32_t out_fp32, void* C, int32_t splits, void* cuda_stream);
+
+/* Fault injection for tests: after n more successful device allocations (by any handle of this
+   library in the process), every further one fails as if the device were out of memory, so each
+   create call's failure path (MFS_ERR_OOM, everything allocated so far freed) can be exercised.
+   n < 0 disarms it. Not thread-safe with respect to the allocations it counts. */
+mfs_status mfs_debug_fail_alloc_after(int64_t n);
+
+/* Diagnostic of the bounded waits: runs the tensor-core GEMM on a 128 x 128 x 64 problem with its
+   loads switched off and a short poll limit, so that the MMA issuer's first wait runs out. The
+   kernel records the time-out and returns normally (no trap, no hang; its tensor memory is freed);
+   the call returns MFS_ERR_TIMEOUT when that path works, and the context stays usable.
+   Allocates and frees its own small buffers; synchronous on cuda_stream (NULL = legacy stream). */
+mfs_status mfs_gemm_bf16_wait_test(void* cuda_stream);
 
 /*
  * mfs_row_residuals_static -- row-side residuals of a point (x, lambda) without allocating.

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/mfs.h"
+#include "mfs_alloc.h"
 #include "mfs_device.cuh"
 
 namespace {
@@ -29,6 +30,7 @@ using mfs::FULL;
 
 constexpr int MAXNT = 512;
 constexpr int MAXW = MAXNT / 32;
+constexpr int FVT = 64;  // column lengths with a tabulated F_V
 constexpr int NSTAT = 20;  // status block, same order as mfs_residuals_t
 
 template <typename T>
@@ -47,6 +49,7 @@ struct BatchArgs {
     const int* row_ptr;      // instance t: m[t]+1 local offsets starting at off_m[t] + t
     const int* ridx;         // local column indices, row order
     const T* rval;
+    const T* fu;             // F_U = 1 / (1 + sum_k a_ik^2) per row
     const int* nsoc;         // Lorentz cones per instance (local starts, ascending)
     const long long* off_soc;
     const int* soc_start;
@@ -267,7 +270,9 @@ __global__ void __launch_bounds__(MAXNT) k_batch(const BatchArgs<T> a) {
     __shared__ double s_red[MAXW][NFLD];
     __shared__ double s_kkt;
     __shared__ int s_inst;
-    const T mu = a.mu;
+    __shared__ T s_fv[FVT];  // F_V = 1 / (1 + d) for column lengths d < FVT
+    const T mu = a.mu, inv_mu = T(1) / a.mu;
+    for (int d = threadIdx.x; d < FVT; d += blockDim.x) s_fv[d] = T(1) / (T(1) + T(d));
     for (;;) {
         if (threadIdx.x == 0) s_inst = atomicAdd(a.queue, 1);
         __syncthreads();
@@ -316,6 +321,7 @@ __global__ void __launch_bounds__(MAXNT) k_batch(const BatchArgs<T> a) {
         T* del = a.del + I.gn;
         const T* c = a.c + I.gn;
         const T* b = a.b + I.gm;
+        const T* fu = a.fu + I.gm;
         T* lam = a.lam + I.gm;
         int done = 0;
         int met = 0;
@@ -327,10 +333,11 @@ __global__ void __launch_bounds__(MAXNT) k_batch(const BatchArgs<T> a) {
                     T s = T(0);
                     for (int k = k0; k < k1; ++k) s += cv[k] * vs[ci[k]];
                     const T d = T(k1 - k0), dj = del[j];
-                    const T xn = (d * xs[j] + s + z[j] + (dj - c[j]) / mu) / (T(1) + d);
+                    const T fv = k1 - k0 < FVT ? s_fv[k1 - k0] : T(1) / (T(1) + d);
+                    const T xn = (d * xs[j] + s + z[j] + (dj - c[j]) * inv_mu) * fv;
                     xs[j] = xn;
                     if (I.ns == 0 || cone_of(sst, ssz, I.ns, j) < 0) {
-                        const T w = xn - dj / mu;
+                        const T w = xn - dj * inv_mu;
                         const T zn = w > T(0) ? w : T(0);
                         z[j] = zn;
                         del[j] = dj + mu * (zn - xn);
@@ -342,13 +349,13 @@ __global__ void __launch_bounds__(MAXNT) k_batch(const BatchArgs<T> a) {
                         const int s0 = sst[qc], sz = ssz[qc];
                         T ss = T(0);
                         for (int t = 1; t < sz; ++t) {
-                            const T w = xs[s0 + t] - del[s0 + t] / mu;
+                            const T w = xs[s0 + t] - del[s0 + t] * inv_mu;
                             ss += w * w;
                         }
-                        const T alpha = sqrt(ss), w1 = xs[s0] - del[s0] / mu;
+                        const T alpha = sqrt(ss), w1 = xs[s0] - del[s0] * inv_mu;
                         for (int t = 0; t < sz; ++t) {
                             const T xt = xs[s0 + t], dt = del[s0 + t];
-                            const T zt = lorentz_coord(xt - dt / mu, t, w1, alpha);
+                            const T zt = lorentz_coord(xt - dt * inv_mu, t, w1, alpha);
                             z[s0 + t] = zt;
                             del[s0 + t] = dt + mu * (zt - xt);
                         }
@@ -357,16 +364,12 @@ __global__ void __launch_bounds__(MAXNT) k_batch(const BatchArgs<T> a) {
                 }
                 // row sweep: y-step (with F_U) and lambda-update
                 for (int i = threadIdx.x; i < I.m; i += blockDim.x) {
-                    T s = T(0), r = T(0);
-                    for (int k = rp[i]; k < rp[i + 1]; ++k) {
-                        const T av = rv[k];
-                        s += av * xs[ri[k]];
-                        r += av * av;
-                    }
-                    const T rho = (b[i] - s) / (T(1) + r);
+                    T s = T(0);
+                    for (int k = rp[i]; k < rp[i + 1]; ++k) s += rv[k] * xs[ri[k]];
+                    const T rho = (b[i] - s) * fu[i];
                     const T ln = lam[i] - mu * rho;
                     lam[i] = ln;
-                    vs[i] = rho - ln / mu;
+                    vs[i] = rho - ln * inv_mu;
                 }
                 __syncthreads();
                 ++done;
@@ -397,7 +400,7 @@ __global__ void __launch_bounds__(MAXNT) k_batch(const BatchArgs<T> a) {
 
 template <typename T>
 struct Store {
-    T *cval = nullptr, *rval = nullptr, *b = nullptr, *c = nullptr;
+    T *cval = nullptr, *rval = nullptr, *fu = nullptr, *b = nullptr, *c = nullptr;
     T *x = nullptr, *z = nullptr, *del = nullptr, *lam = nullptr, *v = nullptr;
 };
 
@@ -412,6 +415,7 @@ struct mfs_batch {
     int count = 0;
     int64_t tot_n = 0, tot_m = 0, tot_o = 0, tot_soc = 0;
     int max_smem = 0, max_smem_block = 0, num_sms = 148;
+    int static_smem = 0;  // largest static shared memory of the k_batch instantiations
     std::vector<int> hm, hn, ho;
     std::vector<long long> hoff_n, hoff_m, hoff_o;
     int *order = nullptr, *m = nullptr, *n = nullptr, *o = nullptr, *nsoc = nullptr;
@@ -459,7 +463,7 @@ mfs_status bfail(mfs_batch* s, mfs_status st, const std::string& msg) {
 template <typename T>
 mfs_status bupload(mfs_batch* s, T** p, const void* host, size_t count) {
     void* q = nullptr;
-    BCUDA(s, cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)));
+    BCUDA(s, mfs::device_malloc(&q, std::max<size_t>(count, 1) * sizeof(T)));
     s->allocs.push_back(q);
     *p = static_cast<T*>(q);
     if (count) BCUDA(s, cudaMemcpyAsync(q, host, count * sizeof(T), cudaMemcpyHostToDevice, s->stream));
@@ -469,7 +473,7 @@ mfs_status bupload(mfs_batch* s, T** p, const void* host, size_t count) {
 template <typename T>
 mfs_status bzeros(mfs_batch* s, T** p, size_t count) {
     void* q = nullptr;
-    BCUDA(s, cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)));
+    BCUDA(s, mfs::device_malloc(&q, std::max<size_t>(count, 1) * sizeof(T)));
     s->allocs.push_back(q);
     *p = static_cast<T*>(q);
     BCUDA(s, cudaMemsetAsync(q, 0, std::max<size_t>(count, 1) * sizeof(T), s->stream));
@@ -493,6 +497,7 @@ BatchArgs<T> batch_args(mfs_batch* s, Store<T>& st, int iters, double tol) {
     a.row_ptr = s->row_ptr;
     a.ridx = s->ridx;
     a.rval = st.rval;
+    a.fu = st.fu;
     a.nsoc = s->nsoc;
     a.off_soc = s->off_soc;
     a.soc_start = s->soc_start;
@@ -519,7 +524,7 @@ BatchArgs<T> batch_args(mfs_batch* s, Store<T>& st, int iters, double tol) {
 // Dynamic shared memory per CTA for the current tuning (ctas_per_sm CTAs share an SM).
 int smem_for(const mfs_batch* s) {
     const int per = s->max_smem / std::max(1, (int)s->tune.ctas_per_sm);
-    const int stat = (int)(MAXW * NFLD * sizeof(double) + 64);
+    const int stat = s->static_smem + 64;
     return std::max(0, std::min(per - stat - 1024, s->max_smem_block - stat));
 }
 
@@ -568,11 +573,26 @@ mfs_status run_batch(mfs_batch* s, Store<T>& st, int iters, double tol) {
 
 template <typename T>
 mfs_status alloc_store(mfs_batch* s, Store<T>& st, const std::vector<double>& cval, const std::vector<double>& rval,
-                       const double* b, const double* c) {
+                       const std::vector<int>& rp, const double* b, const double* c) {
     std::vector<T> tmp(cval.begin(), cval.end());
     BTRY(bupload(s, &st.cval, tmp.data(), tmp.size()));
     tmp.assign(rval.begin(), rval.end());
     BTRY(bupload(s, &st.rval, tmp.data(), tmp.size()));
+    // F_U from the stored (T-rounded) values, summed in FP64: per instance t, rows i take the
+    // nonzeros rp[off_m + t + i] .. rp[off_m + t + i + 1] of that instance's row order
+    std::vector<T> fu(s->tot_m);
+    for (int t = 0; t < s->count; ++t) {
+        const long long rb = s->hoff_m[t] + t, ob = s->hoff_o[t];
+        for (int i = 0; i < s->hm[t]; ++i) {
+            double r = 0.0;
+            for (int k = rp[rb + i]; k < rp[rb + i + 1]; ++k) {
+                const double a = double(tmp[ob + k]);
+                r += a * a;
+            }
+            fu[s->hoff_m[t] + i] = T(1.0 / (1.0 + r));
+        }
+    }
+    BTRY(bupload(s, &st.fu, fu.data(), fu.size()));
     tmp.assign(b, b + s->tot_m);
     BTRY(bupload(s, &st.b, tmp.data(), tmp.size()));
     tmp.assign(c, c + s->tot_n);
@@ -743,6 +763,12 @@ mfs_status mfs_batch_create(int64_t count, const int64_t* m, const int64_t* n, c
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&s->max_smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+    for (const void* f : {(const void*)k_batch<float, 0>, (const void*)k_batch<float, 1>, (const void*)k_batch<double, 0>,
+                          (const void*)k_batch<double, 1>}) {
+        cudaFuncAttributes fa;
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
+        if (e == cudaSuccess) s->static_smem = std::max(s->static_smem, (int)fa.sharedSizeBytes);
+    }
     if (e == cudaSuccess) {
         if (cuda_stream) {
             s->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -784,9 +810,9 @@ mfs_status mfs_batch_create(int64_t count, const int64_t* m, const int64_t* n, c
     BCHK(bzeros(s, &s->status, count));
     BCHK(bzeros(s, &s->resid, (size_t)count * NSTAT));
     if (set.precision == MFS_FP32_MIXED)
-        BCHK(alloc_store<float>(s, s->f32, cv, rv, b, c));
+        BCHK(alloc_store<float>(s, s->f32, cv, rv, rp, b, c));
     else
-        BCHK(alloc_store<double>(s, s->f64, cv, rv, b, c));
+        BCHK(alloc_store<double>(s, s->f64, cv, rv, rp, b, c));
     e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
         s->last_error = std::string("set-up: ") + cudaGetErrorString(e);

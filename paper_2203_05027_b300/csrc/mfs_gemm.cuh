@@ -6,8 +6,8 @@
 //                     STAGES-deep ring of shared-memory stages (128-byte swizzle);
 //   warp 1, one lane: issues tcgen05.mma (M = 128, N = 128, K = 16 per instruction) from shared
 //                     memory descriptors into a 128 x 128 FP32 accumulator in tensor memory;
-//   all four warps:   epilogue, tcgen05.ld of their 32 accumulator lanes (rows), bias, ReLU,
-//                     conversion and stores.
+//   all four warps:   epilogue, tcgen05.ld of their 32 accumulator lanes (rows), a transpose through
+//                     shared memory, bias, ReLU, conversion and row-contiguous stores.
 // Barriers: full[s] (TMA transaction bytes), empty[s] (tcgen05.commit after the MMAs that read
 // stage s), acc (commit after the last MMA). Every wait is bounded: a wait that runs out sets the
 // error word and the kernel skips to the end, where tensor memory is freed.
@@ -26,7 +26,7 @@ constexpr int BM = 128;
 constexpr int BN = 128;
 constexpr int BK = 64;       // one 128-byte swizzle row of BF16
 constexpr int UK = 16;       // K of one tcgen05.mma kind::f16
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;       // 3 stages (97 KB) let two CTAs share an SM: one's epilogue overlaps the other's loads
 constexpr int NTHREADS = 128;
 constexpr int TILE_A = BM * BK * 2;  // bytes
 constexpr int TILE_B = BN * BK * 2;
@@ -72,9 +72,9 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-// Bounded wait by the calling thread; false if the phase never completed.
-__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < SPIN; ++i)
+// Bounded wait by the calling thread (at most `limit` polls); false if the phase never completed.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, uint32_t limit = SPIN) {
+    for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -143,9 +143,11 @@ struct GemmArgs {
     void* C;                // row-major M x N; with splits > 1: FP32 partials [split][M][N]
     int ldc;
     int* err;
+    uint32_t spin;  // poll limit of every wait (SPIN in normal use)
+    int no_loads;   // diagnostic: issue no loads, so the first wait of the MMA issuer runs out
 };
 
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(NTHREADS, 2)
     k_gemm_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const GemmArgs g) {
     extern __shared__ __align__(1024) unsigned char gsm_raw[];
     unsigned char* gsm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
@@ -182,10 +184,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
 
+    int issued = 0;                // loads issued by the producer lane
     if (warp == 0 && lane == 0) {  // producer
-        for (int i = 0; i < nkb; ++i) {
+        for (int i = 0; i < nkb && !g.no_loads; ++i) {
             const int s = i % STAGES;
-            if (!wait_phase(&empty[s], ((i / STAGES) & 1) ^ 1)) {
+            if (!wait_phase(&empty[s], ((i / STAGES) & 1) ^ 1, g.spin)) {
                 atomicExch(s_fail, 1);
                 break;
             }
@@ -193,12 +196,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
             tma_load_2d(st, &mapA, (kb0 + i) * BK, m0, &full[s]);
             tma_load_2d(st + TILE_A, &mapB, (kb0 + i) * BK, n0, &full[s]);
+            issued = i + 1;
         }
     } else if (warp == 1 && lane == 0) {  // MMA issuer
         const uint32_t idesc = idesc_bf16(BM, BN);
         for (int i = 0; i < nkb; ++i) {
             const int s = i % STAGES;
-            if (!wait_phase(&full[s], (i / STAGES) & 1)) {
+            if (!wait_phase(&full[s], (i / STAGES) & 1, g.spin)) {
                 atomicExch(s_fail, 1);
                 break;
             }
@@ -216,42 +220,52 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     __syncwarp();
     // epilogue: every thread owns one row of the tile (TMEM lane = row)
-    const bool ok = wait_phase(accb, 0);
+    const bool ok = wait_phase(accb, 0, g.spin);
     if (!ok) atomicExch(s_fail, 1);
     tc_fence_after();
-    const int row = m0 + warp * 32 + lane;
-    if (ok && nkb > 0) {
+    // Each 32 x 32 block goes through shared memory (the idle stage buffers; padded rows, no bank
+    // conflicts) so that each store instruction writes 32 consecutive columns of one row.
+    float* stg = reinterpret_cast<float*>(gsm) + warp * (32 * 33);
+    const int rbase = m0 + warp * 32;
+    const bool part = gridDim.z > 1;
+    if (ok && nkb > 0 && !*s_fail) {
         for (int c0 = 0; c0 < BN; c0 += 32) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (row < g.M) {
-                const int col0 = n0 + c0;
-                if (gridDim.z > 1) {
-                    float* out = reinterpret_cast<float*>(g.C) + ((size_t)blockIdx.z * g.M + row) * g.ldc + col0;
 #pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        if (col0 + i < g.N) out[i] = v[i];
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        float w = v[i];
-                        if (col0 + i < g.N) {
-                            if (g.bias) w += g.bias[col0 + i];
-                            if (g.relu) w = w > 0.f ? w : 0.f;
-                            if (g.out_fp32)
-                                reinterpret_cast<float*>(g.C)[(size_t)row * g.ldc + col0 + i] = w;
-                            else
-                                reinterpret_cast<__nv_bfloat16*>(g.C)[(size_t)row * g.ldc + col0 + i] =
-                                    __float2bfloat16_rn(w);
-                        }
+            for (int i = 0; i < 32; ++i) stg[lane * 33 + i] = v[i];
+            __syncwarp();
+            const int col = n0 + c0 + lane;
+            if (col < g.N) {
+                const float bv = (!part && g.bias) ? g.bias[col] : 0.f;
+                const int rows = min(32, g.M - rbase);
+                for (int r = 0; r < rows; ++r) {
+                    const size_t row = (size_t)(rbase + r);
+                    float w = stg[r * 33 + lane];
+                    if (part) {
+                        reinterpret_cast<float*>(g.C)[((size_t)blockIdx.z * g.M + row) * g.ldc + col] = w;
+                    } else {
+                        w += bv;
+                        if (g.relu) w = w > 0.f ? w : 0.f;
+                        if (g.out_fp32)
+                            reinterpret_cast<float*>(g.C)[row * g.ldc + col] = w;
+                        else
+                            reinterpret_cast<__nv_bfloat16*>(g.C)[row * g.ldc + col] = __float2bfloat16_rn(w);
                     }
                 }
             }
+            __syncwarp();
         }
     }
-    if (*s_fail && threadIdx.x == 0) {
-        atomicCAS(g.err, 0, ERR_TIMEOUT);
-        wait_phase(accb, 0);  // let issued MMAs finish before the accumulator is freed
+    tc_fence_before();
+    __syncthreads();  // every role is done: s_fail is final
+    if (*s_fail) {
+        // Before the CTA's shared and tensor memory go away: the bulk copies still in flight (only
+        // the last STAGES issued can be, the earlier ones were consumed) and the issued MMAs.
+        if (warp == 0 && lane == 0)
+            for (int i = max(0, issued - STAGES); i < issued; ++i) wait_phase(&full[i % STAGES], (i / STAGES) & 1);
+        if (threadIdx.x == 32) wait_phase(accb, 0);
+        if (threadIdx.x == 0) atomicCAS(g.err, 0, ERR_TIMEOUT);
     }
     tc_fence_before();
     __syncthreads();

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/mfs.h"
+#include "mfs_alloc.h"
 #include "mfs_gemm.cuh"
 
 using bf16 = __nv_bfloat16;
@@ -76,7 +77,8 @@ __global__ void k_splitk_reduce(const float* __restrict__ part, int splits, int 
 
 // C (row-major M x N) = A (M x K) * B (N x K)^T, BF16 in, FP32 accumulate on the tensor cores.
 mfs_status gemm(int M, int N, int K, const bf16* A, const bf16* B, const float* bias, int relu, int out_fp32, void* C,
-                int splits, float* work, int* err, cudaStream_t st, std::string* why) {
+                int splits, float* work, int* err, cudaStream_t st, std::string* why, uint32_t spin = SPIN,
+                int no_loads = 0) {
     if (M <= 0 || N <= 0 || K <= 0) return MFS_OK;
     if (K % 8) {
         if (why) *why = "gemm: K must be a multiple of 8 (16-byte rows)";
@@ -114,6 +116,8 @@ mfs_status gemm(int M, int N, int K, const bf16* A, const bf16* B, const float* 
     g.C = splits > 1 ? static_cast<void*>(work) : C;
     g.ldc = N;
     g.err = err;
+    g.spin = spin;
+    g.no_loads = no_loads;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
     k_gemm_bf16<<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, g);
     if (splits > 1) {
@@ -128,9 +132,49 @@ mfs_status gemm(int M, int N, int K, const bf16* A, const bf16* B, const float* 
     return MFS_OK;
 }
 
-// Tiled transpose: out[c][r] = in[r][c] for a row-major BF16 matrix [rows][cols].
+// Tiled transpose: out[c][r] = in[r][c] for a row-major BF16 matrix [rows][cols]. A 64 x 64 tile
+// moves as pairs of BF16 (4-byte accesses, 128 bytes per warp row) through shared memory.
 __global__ void k_transpose(const bf16* __restrict__ in, bf16* __restrict__ out, int rows, int cols) {
-    __shared__ bf16 tile[32][33];
+    __shared__ bf16 tile[64][66];
+    const int tx = threadIdx.x;  // 0..31: a pair of columns (load) or of rows (store)
+    const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 64;
+    const bool pair_in = (cols % 2 == 0), pair_out = (rows % 2 == 0);
+    for (int k = threadIdx.y; k < 64; k += blockDim.y) {
+        const int r = r0 + k, c = c0 + 2 * tx;
+        bf16 v0 = __float2bfloat16_rn(0.f), v1 = v0;
+        if (r < rows) {
+            if (pair_in && c + 1 < cols) {
+                const __nv_bfloat162 q = *reinterpret_cast<const __nv_bfloat162*>(in + (size_t)r * cols + c);
+                v0 = q.x;
+                v1 = q.y;
+            } else {
+                if (c < cols) v0 = in[(size_t)r * cols + c];
+                if (c + 1 < cols) v1 = in[(size_t)r * cols + c + 1];
+            }
+        }
+        tile[k][2 * tx] = v0;
+        tile[k][2 * tx + 1] = v1;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 64; k += blockDim.y) {
+        const int c = c0 + k, r = r0 + 2 * tx;
+        if (c >= cols) continue;
+        const bf16 v0 = tile[2 * tx][k], v1 = tile[2 * tx + 1][k];
+        if (pair_out && r + 1 < rows) {
+            __nv_bfloat162 q;
+            q.x = v0;
+            q.y = v1;
+            *reinterpret_cast<__nv_bfloat162*>(out + (size_t)c * rows + r) = q;
+        } else {
+            if (r < rows) out[(size_t)c * rows + r] = v0;
+            if (r + 1 < rows) out[(size_t)c * rows + r + 1] = v1;
+        }
+    }
+}
+
+// 32 x 32 tiles of single BF16 elements: more blocks, for small matrices
+__global__ void k_transpose32(const bf16* __restrict__ in, bf16* __restrict__ out, int rows, int cols) {
+    __shared__ bf16 tile[32][34];
     const int c = blockIdx.x * 32 + threadIdx.x;
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
         const int r = blockIdx.y * 32 + k;
@@ -145,7 +189,11 @@ __global__ void k_transpose(const bf16* __restrict__ in, bf16* __restrict__ out,
 }
 
 void transpose(const bf16* in, bf16* out, int rows, int cols, cudaStream_t st) {
-    dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+    if ((long long)rows * cols < (1LL << 22)) {
+        k_transpose32<<<dim3((cols + 31) / 32, (rows + 31) / 32), dim3(32, 8), 0, st>>>(in, out, rows, cols);
+        return;
+    }
+    dim3 grid((cols + 63) / 64, (rows + 63) / 64), block(32, 8);
     k_transpose<<<grid, block, 0, st>>>(in, out, rows, cols);
 }
 
@@ -157,20 +205,22 @@ __global__ void k_to_bf16(const float* __restrict__ in, bf16* __restrict__ out, 
 // Loss gradient of the mean squared error against standardised targets:
 // dY = 2 (Y - (T - mean)/std) / (B * D); per-block partial sums of the squared error.
 // Y and dY have rows of Dp >= D entries (the extra ones get dY = 0); T has rows of D.
+// Block (bx, row) takes columns bx*256 + threadIdx.x, stepping by gridDim.x*256.
 __global__ void k_mse(const float* __restrict__ Y, const float* __restrict__ T, const float* __restrict__ mean,
                       const float* __restrict__ stdv, int B, int D, int Dp, bf16* __restrict__ dY,
                       double* __restrict__ part) {
     __shared__ double sh[8];
-    const long long total = (long long)B * Dp;
+    const int row = blockIdx.y;
     const float scale = 2.0f / ((float)B * (float)D);
+    const float* y = Y + (size_t)row * Dp;
+    const float* t = T + (size_t)row * D;
+    bf16* dy = dY + (size_t)row * Dp;
     double acc = 0.0;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(t % Dp);
-        const long long row = t / Dp;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Dp; j += gridDim.x * blockDim.x) {
         float r = 0.f;
-        if (j < D) r = Y[t] - (T[row * D + j] - mean[j]) / stdv[j];
+        if (j < D) r = y[j] - (t[j] - mean[j]) / stdv[j];
         acc += (double)r * (double)r;
-        dY[t] = __float2bfloat16_rn(scale * r);
+        dy[j] = __float2bfloat16_rn(scale * r);
     }
     for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
@@ -178,16 +228,22 @@ __global__ void k_mse(const float* __restrict__ Y, const float* __restrict__ T, 
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-        part[blockIdx.x] = s;
+        part[(size_t)row * gridDim.x + blockIdx.x] = s;
     }
 }
 
+// out = scale * sum of n partial sums, one block of 256 threads, fixed order.
 __global__ void k_sum_parts(const double* __restrict__ part, int n, double scale, double* __restrict__ out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < n; ++i) s += part[i];
-        *out = s * scale;
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) *out = sh[0] * scale;
 }
 
 // dZ = dH * (H > 0) (ReLU backward), FP32 in, BF16 out.
@@ -196,13 +252,21 @@ __global__ void k_relu_bwd(const float* __restrict__ dH, const bf16* __restrict_
         dZ[t] = __float2bfloat16_rn(__bfloat162float(H[t]) > 0.f ? dH[t] : 0.f);
 }
 
-// db[j] = sum over rows of G[row][j] (fixed order).
+// db[j] = sum over rows of G[row][j] (fixed order): block of 32 columns x 8 warps, warp w sums
+// rows w, w+8, ...; the eight partial sums are added in warp order.
 __global__ void k_colsum(const bf16* __restrict__ G, int rows, int cols, float* __restrict__ db) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= cols) return;
+    __shared__ float sh[8][32];
+    const int j = blockIdx.x * 32 + threadIdx.x, w = threadIdx.y;
     float s = 0.f;
-    for (int r = 0; r < rows; ++r) s += __bfloat162float(G[(size_t)r * cols + j]);
-    db[j] = s;
+    if (j < cols)
+        for (int r = w; r < rows; r += 8) s += __bfloat162float(G[(size_t)r * cols + j]);
+    sh[w][threadIdx.x] = s;
+    __syncthreads();
+    if (w == 0 && j < cols) {
+        float t = 0.f;
+        for (int q = 0; q < 8; ++q) t += sh[q][threadIdx.x];
+        db[j] = t;
+    }
 }
 
 // Adam (Kingma & Ba) on FP32 master weights; refreshes the BF16 copy.
@@ -221,14 +285,11 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
     }
 }
 
-// Y * std + mean (undo the target standardisation), FP32.
+// Y * std + mean (undo the target standardisation), FP32; block (bx, row) as in k_mse.
 __global__ void k_denorm(float* __restrict__ Y, const float* __restrict__ mean, const float* __restrict__ stdv, int B,
                          int D) {
-    const long long total = (long long)B * D;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(t % D);
-        Y[t] = Y[t] * stdv[j] + mean[j];
-    }
+    float* y = Y + (size_t)blockIdx.y * D;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D; j += gridDim.x * blockDim.x) y[j] = y[j] * stdv[j] + mean[j];
 }
 
 // Per-output mean and standard deviation of a target matrix T [count][D] (row-major FP32): block
@@ -239,11 +300,11 @@ __global__ void k_colstats_part(const float* __restrict__ T, long long count, in
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= D) return;
     const long long r0 = blockIdx.y * rows_per_part;
-    const long long r1 = std::min<long long>(count, r0 + rows_per_part);
+    const long long r1 = min(count, r0 + rows_per_part);
     const float shift = T[j];
     double s1 = 0.0, s2 = 0.0;
     for (long long r = r0; r < r1; r += 32) {
-        const long long re = std::min<long long>(r1, r + 32);
+        const long long re = min(r1, r + 32);
         float a1 = 0.f, a2 = 0.f;
         for (long long q = r; q < re; ++q) {
             const float d = T[q * D + j] - shift;
@@ -272,6 +333,11 @@ __global__ void k_colstats_final(const float* __restrict__ T, const double* __re
     const double var = fmax(s2 / (double)count - m1 * m1, 0.0);
     mean[j] = (float)((double)T[j] + m1);
     stdv[j] = fmaxf((float)sqrt(var), min_std);
+}
+
+// blocks per row for the row-wise kernels (grid y = rows): about 1184 blocks in all
+inline int row_blocks(int cols, int rows) {
+    return std::max(1, std::min((cols + 255) / 256, 148 * 8 / std::max(rows, 1)));
 }
 
 inline int grid1(long long count) {
@@ -319,7 +385,7 @@ mfs_status mfail(mfs_mlp* s, mfs_status st, const std::string& msg) {
 template <typename T>
 mfs_status malloc_zero(mfs_mlp* s, T** p, size_t count) {
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    cudaError_t e = mfs::device_malloc(&q, std::max<size_t>(count, 1) * sizeof(T));
     if (e != cudaSuccess) return mfail(s, MFS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
     s->allocs.push_back(q);
     *p = static_cast<T*>(q);
@@ -384,8 +450,10 @@ mfs_status mfs_mlp_create(int32_t din, int32_t width, int32_t dout, int32_t max_
     g_mlp_error.clear();
     if (!out) return mfail(nullptr, MFS_ERR_INVALID, "out is NULL");
     *out = nullptr;
-    if (din < 1 || width < 1 || dout < 1 || max_batch < 1 || din % 8 || width % 8 || max_batch % 8)
-        return mfail(nullptr, MFS_ERR_INVALID, "din, width and max_batch must be positive multiples of 8, dout >= 1");
+    if (din < 1 || width < 1 || dout < 1 || max_batch < 1 || din % 8 || width % 8 || max_batch % 8 ||
+        max_batch > 65535)
+        return mfail(nullptr, MFS_ERR_INVALID,
+                     "din, width and max_batch must be positive multiples of 8 (max_batch <= 65535), dout >= 1");
     mfs_mlp* s = new (std::nothrow) mfs_mlp();
     if (!s) return mfail(nullptr, MFS_ERR_OOM, "host allocation failed");
     auto bail = [&](mfs_status st) {
@@ -476,7 +544,7 @@ mfs_status mfs_mlp_create(int32_t din, int32_t width, int32_t dout, int32_t max_
     MCHK(malloc_zero(s, &s->dZ1t, (size_t)B * width));
     s->work_floats = (size_t)64 * B * width;
     MCHK(malloc_zero(s, &s->work, s->work_floats));
-    MCHK(malloc_zero(s, &s->loss_part, 148 * 8));
+    MCHK(malloc_zero(s, &s->loss_part, std::max(148 * 8, max_batch)));
     MCHK(malloc_zero(s, &s->loss, 1));
     MCHK(malloc_zero(s, &s->err, 1));
     e = cudaStreamSynchronize(s->stream);
@@ -548,7 +616,8 @@ mfs_status mfs_mlp_forward(mfs_mlp* s, int32_t batch, const float* x, float* y, 
     k_to_bf16<<<grid1((long long)batch * s->din), 256, 0, s->stream>>>(x, s->X, (long long)batch * s->din);
     MTRY(forward_bf16(s, batch));
     if (denormalize)
-        k_denorm<<<grid1((long long)batch * s->doutp), 256, 0, s->stream>>>(s->Y, s->mean, s->stdv, batch, s->doutp);
+        k_denorm<<<dim3(row_blocks(s->doutp, batch), batch), 256, 0, s->stream>>>(s->Y, s->mean, s->stdv, batch,
+                                                                                     s->doutp);
     if (cudaMemcpy2DAsync(y, (size_t)s->dout * sizeof(float), s->Y, (size_t)s->doutp * sizeof(float),
                           (size_t)s->dout * sizeof(float), batch, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
         return mfail(s, MFS_ERR_CUDA, "copy of the output");
@@ -563,14 +632,14 @@ mfs_status mfs_mlp_backward(mfs_mlp* s, int32_t batch, const float* x, const flo
     cudaStream_t st = s->stream;
     k_to_bf16<<<grid1((long long)B * I), 256, 0, st>>>(x, s->X, (long long)B * I);
     MTRY(forward_bf16(s, B));
-    const int lb = grid1((long long)B * D);
-    k_mse<<<lb, 256, 0, st>>>(s->Y, target, s->mean, s->stdv, B, s->dout, D, s->dY, s->loss_part);
-    k_sum_parts<<<1, 32, 0, st>>>(s->loss_part, lb, 1.0 / ((double)B * s->dout), s->loss);
+    const int lb = row_blocks(D, B);  // blocks per row of k_mse; lb * B <= max(1184, B) partial sums
+    k_mse<<<dim3(lb, B), 256, 0, st>>>(s->Y, target, s->mean, s->stdv, B, s->dout, D, s->dY, s->loss_part);
+    k_sum_parts<<<1, 256, 0, st>>>(s->loss_part, lb * B, 1.0 / ((double)B * s->dout), s->loss);
     // layer 3: dW3 = dY^T H2, db3 = colsum(dY), dH2 = dY W3
     transpose(s->dY, s->dYt, B, D, st);
     transpose(s->H2, s->H2t, B, W, st);
     MTRY(run_gemm(s, D, W, B, s->dYt, s->H2t, nullptr, 0, 1, s->gW[2], 1));
-    k_colsum<<<(D + 255) / 256, 256, 0, st>>>(s->dY, B, D, s->gb[2]);
+    k_colsum<<<(D + 31) / 32, dim3(32, 8), 0, st>>>(s->dY, B, D, s->gb[2]);
     transpose(s->Wh[2], s->Wt[2], D, W, st);
     MTRY(run_gemm(s, B, W, D, s->dY, s->Wt[2], nullptr, 0, 1, s->dH, splits_for(s, B, W, D)));
     k_relu_bwd<<<grid1((long long)B * W), 256, 0, st>>>(s->dH, s->H2, s->dZ2, (long long)B * W);
@@ -578,7 +647,7 @@ mfs_status mfs_mlp_backward(mfs_mlp* s, int32_t batch, const float* x, const flo
     transpose(s->dZ2, s->dZ2t, B, W, st);
     transpose(s->H1, s->H1t, B, W, st);
     MTRY(run_gemm(s, W, W, B, s->dZ2t, s->H1t, nullptr, 0, 1, s->gW[1], 1));
-    k_colsum<<<(W + 255) / 256, 256, 0, st>>>(s->dZ2, B, W, s->gb[1]);
+    k_colsum<<<(W + 31) / 32, dim3(32, 8), 0, st>>>(s->dZ2, B, W, s->gb[1]);
     transpose(s->Wh[1], s->Wt[1], W, W, st);
     MTRY(run_gemm(s, B, W, W, s->dZ2, s->Wt[1], nullptr, 0, 1, s->dH, splits_for(s, B, W, W)));
     k_relu_bwd<<<grid1((long long)B * W), 256, 0, st>>>(s->dH, s->H1, s->dZ1, (long long)B * W);
@@ -586,7 +655,7 @@ mfs_status mfs_mlp_backward(mfs_mlp* s, int32_t batch, const float* x, const flo
     transpose(s->dZ1, s->dZ1t, B, W, st);
     transpose(s->X, s->Xt, B, I, st);
     MTRY(run_gemm(s, W, I, B, s->dZ1t, s->Xt, nullptr, 0, 1, s->gW[0], 1));
-    k_colsum<<<(W + 255) / 256, 256, 0, st>>>(s->dZ1, B, W, s->gb[0]);
+    k_colsum<<<(W + 31) / 32, dim3(32, 8), 0, st>>>(s->dZ1, B, W, s->gb[0]);
     if (cudaGetLastError() != cudaSuccess) return mfail(s, MFS_ERR_CUDA, "mlp backward launch");
     if (loss && cudaMemcpyAsync(loss, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return mfail(s, MFS_ERR_CUDA, "loss copy");
@@ -645,6 +714,36 @@ mfs_status mfs_mlp_get_grads(mfs_mlp* s, int32_t l, float* gW, float* gb) {
 }
 
 // Stand-alone tensor-core GEMM through the C ABI (device pointers): C = A B^T (+ bias, ReLU).
+mfs_status mfs_gemm_bf16_wait_test(void* cuda_stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int M = 128, N = 128, K = 64;
+    void *A = nullptr, *B = nullptr, *C = nullptr;
+    int* err = nullptr;
+    mfs_status out = MFS_ERR_CUDA;
+    if (cudaMalloc(&A, M * K * 2) == cudaSuccess && cudaMalloc(&B, N * K * 2) == cudaSuccess &&
+        cudaMalloc(&C, M * N * 4) == cudaSuccess && cudaMalloc(reinterpret_cast<void**>(&err), sizeof(int)) == cudaSuccess &&
+        cudaMemsetAsync(A, 0, M * K * 2, st) == cudaSuccess && cudaMemsetAsync(B, 0, N * K * 2, st) == cudaSuccess &&
+        cudaMemsetAsync(err, 0, sizeof(int), st) == cudaSuccess) {
+        std::string why;
+        out = gemm(M, N, K, static_cast<bf16*>(A), static_cast<bf16*>(B), nullptr, 0, 1, C, 1, nullptr, err, st, &why,
+                   1024u, 1);
+        int h = 0;
+        if (out == MFS_OK) {
+            if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                out = MFS_ERR_CUDA;
+            else
+                out = h == ERR_TIMEOUT ? MFS_ERR_TIMEOUT : (h ? MFS_ERR_CUDA : MFS_OK);
+        }
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(A);
+    cudaFree(B);
+    cudaFree(C);
+    cudaFree(err);
+    return out;
+}
+
 mfs_status mfs_gemm_bf16(int64_t M, int64_t N, int64_t K, const void* A, const void* B, const float* bias, int32_t relu,
                          int32_t out_fp32, void* C, int32_t splits, void* cuda_stream) {
     if (M < 0 || N < 0 || K < 0 || M >= INT32_MAX || N >= INT32_MAX || K >= INT32_MAX || !A || !B || !C)

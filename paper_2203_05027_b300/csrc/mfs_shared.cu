@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/mfs.h"
+#include "mfs_alloc.h"
 #include "mfs_device.cuh"
 
 namespace {
@@ -68,26 +69,108 @@ __device__ __forceinline__ double lorentz_dist2(double w1, double alpha, double 
     return 0.5 * g * g;
 }
 
-// one warp per (column, slice of 32 instances)
-template <typename T>
+// V consecutive instances per lane: vector loads and stores of the interleaved state.
+template <typename T, int V>
+struct alignas(sizeof(T) * V) Pack {
+    T e[V];
+};
+template <typename T, int V>
+__device__ __forceinline__ Pack<T, V> ld_pack(const T* p) {
+    return *reinterpret_cast<const Pack<T, V>*>(p);
+}
+template <typename T, int V>
+__device__ __forceinline__ void st_pack(T* p, const Pack<T, V>& v) {
+    *reinterpret_cast<Pack<T, V>*>(p) = v;
+}
+// read-only gather of V instances (the gathered vector is not written by the same launch)
+template <typename T, int V>
+__device__ __forceinline__ Pack<T, V> ldg_pack(const T* p) {
+    Pack<T, V> r;
+    if constexpr (V == 4 && sizeof(T) == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+        r.e[0] = q.x, r.e[1] = q.y, r.e[2] = q.z, r.e[3] = q.w;
+    } else if constexpr (V == 2 && sizeof(T) == 4) {
+        const float2 q = __ldg(reinterpret_cast<const float2*>(p));
+        r.e[0] = q.x, r.e[1] = q.y;
+    } else if constexpr (V == 2 && sizeof(T) == 8) {
+        const double2 q = __ldg(reinterpret_cast<const double2*>(p));
+        r.e[0] = q.x, r.e[1] = q.y;
+    } else {
+        static_assert(V == 1, "unsupported pack");
+        r.e[0] = __ldg(p);
+    }
+    return r;
+}
+
+// acc[u] = sum over the nonzeros k of a line (column or row) of val[k] * g[idx[k] * Bp + s0 + u]:
+// the warp loads 32 indices and values at a time with one coalesced load each, broadcasts them by
+// shuffles and keeps four gathers in flight; the sum runs in the nonzeros' order.
+template <typename T, int V>
+__device__ __forceinline__ void line_dot(const int* __restrict__ idx, const T* __restrict__ val, int k0, int k1,
+                                         const T* __restrict__ g, int Bp, int s0, int lane, T (&acc)[V]) {
+#pragma unroll
+    for (int u = 0; u < V; ++u) acc[u] = T(0);
+    for (int base = k0; base < k1; base += 32) {
+        const int cnt = min(32, k1 - base);
+        int mi = 0;
+        T mv = T(0);
+        if (lane < cnt) {
+            mi = __ldg(idx + base + lane);
+            mv = __ldg(val + base + lane);
+        }
+        int t = 0;
+        for (; t + 4 <= cnt; t += 4) {
+            Pack<T, V> q[4];
+            T w[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int i = __shfl_sync(FULL, mi, t + r);
+                w[r] = __shfl_sync(FULL, mv, t + r);
+                q[r] = ldg_pack<T, V>(g + (size_t)i * Bp + s0);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int u = 0; u < V; ++u) acc[u] += w[r] * q[r].e[u];
+        }
+        for (; t < cnt; ++t) {
+            const int i = __shfl_sync(FULL, mi, t);
+            const T w = __shfl_sync(FULL, mv, t);
+            const Pack<T, V> q = ldg_pack<T, V>(g + (size_t)i * Bp + s0);
+#pragma unroll
+            for (int u = 0; u < V; ++u) acc[u] += w * q.e[u];
+        }
+    }
+}
+
+// one warp per (column, group of 32 V instances); lane takes instances s0 .. s0+V-1
+template <typename T, int V>
 __global__ void __launch_bounds__(SNT) k_s_col(const SArgs<T> a) {
     const long long w = (long long)blockIdx.x * SW + (threadIdx.x >> 5);
-    const int slices = a.Bp >> 5;
-    if (w >= (long long)a.n * slices) return;
-    const int j = (int)(w / slices);
-    const int s = (int)(w % slices) * 32 + (threadIdx.x & 31);
+    const int groups = a.Bp / (32 * V), lane = threadIdx.x & 31;
+    if (w >= (long long)a.n * groups) return;
+    const int j = (int)(w / groups);
+    const int s0 = (int)(w % groups) * 32 * V + lane * V;
     const int k0 = a.col_ptr[j], k1 = a.col_ptr[j + 1];
-    T acc = T(0);
-    for (int k = k0; k < k1; ++k) acc += a.cval[k] * a.v[(size_t)a.cidx[k] * a.Bp + s];
-    const size_t p = (size_t)j * a.Bp + s;
-    const T d = T(k1 - k0), mu = a.mu, dj = a.del[p];
-    const T xn = (d * a.x[p] + acc + a.z[p] + (dj - a.c[p]) / mu) / (T(1) + d);
-    a.x[p] = xn;
+    T acc[V];
+    line_dot<T, V>(a.cidx, a.cval, k0, k1, a.v, a.Bp, s0, lane, acc);
+    const size_t p = (size_t)j * a.Bp + s0;
+    const T d = T(k1 - k0), mu = a.mu;
+    const Pack<T, V> xo = ld_pack<T, V>(a.x + p), zo = ld_pack<T, V>(a.z + p), dl = ld_pack<T, V>(a.del + p),
+                     cc = ld_pack<T, V>(a.c + p);
+    Pack<T, V> xn, zn, dn;
+#pragma unroll
+    for (int u = 0; u < V; ++u) xn.e[u] = (d * xo.e[u] + acc[u] + zo.e[u] + (dl.e[u] - cc.e[u]) / mu) / (T(1) + d);
+    st_pack<T, V>(a.x + p, xn);
     if (!a.in_soc[j]) {
-        const T wv = xn - dj / mu;
-        const T zn = wv > T(0) ? wv : T(0);
-        a.z[p] = zn;
-        a.del[p] = dj + mu * (zn - xn);
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const T wv = xn.e[u] - dl.e[u] / mu;
+            zn.e[u] = wv > T(0) ? wv : T(0);
+            dn.e[u] = dl.e[u] + mu * (zn.e[u] - xn.e[u]);
+        }
+        st_pack<T, V>(a.z + p, zn);
+        st_pack<T, V>(a.del + p, dn);
     }
 }
 
@@ -118,26 +201,29 @@ __global__ void __launch_bounds__(SNT) k_s_cone(const SArgs<T> a) {
     }
 }
 
-// one warp per (row, slice). MODE 0: iteration; MODE 1: v from x and the current lambda.
-template <typename T, int MODE>
+// one warp per (row, group of 32 V instances). MODE 0: iteration; MODE 1: v from x and the
+// current lambda.
+template <typename T, int MODE, int V>
 __global__ void __launch_bounds__(SNT) k_s_row(const SArgs<T> a) {
     const long long w = (long long)blockIdx.x * SW + (threadIdx.x >> 5);
-    const int slices = a.Bp >> 5;
-    if (w >= (long long)a.m * slices) return;
-    const int i = (int)(w / slices);
-    const int s = (int)(w % slices) * 32 + (threadIdx.x & 31);
-    T acc = T(0);
-    for (int k = a.row_ptr[i]; k < a.row_ptr[i + 1]; ++k) acc += a.rval[k] * a.x[(size_t)a.ridx[k] * a.Bp + s];
-    const size_t p = (size_t)i * a.Bp + s;
-    const T mu = a.mu;
-    const T rho = (a.b[p] - acc) * a.fu[i];
-    if (MODE == 0) {
-        const T ln = a.lam[p] - mu * rho;
-        a.lam[p] = ln;
-        a.v[p] = rho - ln / mu;
-    } else {
-        a.v[p] = rho - a.lam[p] / mu;
+    const int groups = a.Bp / (32 * V), lane = threadIdx.x & 31;
+    if (w >= (long long)a.m * groups) return;
+    const int i = (int)(w / groups);
+    const int s0 = (int)(w % groups) * 32 * V + lane * V;
+    T acc[V];
+    line_dot<T, V>(a.ridx, a.rval, a.row_ptr[i], a.row_ptr[i + 1], a.x, a.Bp, s0, lane, acc);
+    const size_t p = (size_t)i * a.Bp + s0;
+    const T mu = a.mu, fu = a.fu[i];
+    const Pack<T, V> bb = ld_pack<T, V>(a.b + p), lo = ld_pack<T, V>(a.lam + p);
+    Pack<T, V> ln, vn;
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+        const T rho = (bb.e[u] - acc[u]) * fu;
+        ln.e[u] = MODE == 0 ? lo.e[u] - mu * rho : lo.e[u];
+        vn.e[u] = rho - ln.e[u] / mu;
     }
+    if (MODE == 0) st_pack<T, V>(a.lam + p, ln);
+    st_pack<T, V>(a.v + p, vn);
 }
 
 template <typename T>
@@ -401,7 +487,7 @@ mfs_status sfail(mfs_shared* s, mfs_status st, const std::string& msg) {
 template <typename T>
 mfs_status salloc(mfs_shared* s, T** p, size_t count, const void* host = nullptr) {
     void* q = nullptr;
-    SCUDA(s, cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)));
+    SCUDA(s, mfs::device_malloc(&q, std::max<size_t>(count, 1) * sizeof(T)));
     s->allocs.push_back(q);
     *p = static_cast<T*>(q);
     if (host && count)
@@ -443,12 +529,44 @@ inline int wgrid(long long warps) {
     return (int)((warps + SW - 1) / SW);
 }
 
+// instances per lane: the widest pack (16 bytes at most) that divides the interleave width
+template <typename T>
+int pack_of(int Bp) {
+    if (sizeof(T) == 4 && Bp % 128 == 0) return 4;
+    if (Bp % 64 == 0) return 2;
+    return 1;
+}
+
+template <typename T, int V>
+void s_iteration_v(mfs_shared* s, const SArgs<T>& a, cudaStream_t st) {
+    const long long g = s->Bp / (32 * V);
+    if (s->n) k_s_col<T, V><<<wgrid((long long)s->n * g), SNT, 0, st>>>(a);
+    if (s->nsoc) k_s_cone<T><<<wgrid((long long)s->nsoc * (s->Bp / 32)), SNT, 0, st>>>(a);
+    if (s->m) k_s_row<T, 0, V><<<wgrid((long long)s->m * g), SNT, 0, st>>>(a);
+}
+
 template <typename T>
 void s_iteration(mfs_shared* s, const SArgs<T>& a, cudaStream_t st) {
-    const int sl = s->Bp / 32;
-    if (s->n) k_s_col<T><<<wgrid((long long)s->n * sl), SNT, 0, st>>>(a);
-    if (s->nsoc) k_s_cone<T><<<wgrid((long long)s->nsoc * sl), SNT, 0, st>>>(a);
-    if (s->m) k_s_row<T, 0><<<wgrid((long long)s->m * sl), SNT, 0, st>>>(a);
+    switch (pack_of<T>(s->Bp)) {
+        case 4:
+            if constexpr (sizeof(T) == 4) s_iteration_v<T, 4>(s, a, st);
+            break;
+        case 2: s_iteration_v<T, 2>(s, a, st); break;
+        default: s_iteration_v<T, 1>(s, a, st);
+    }
+}
+
+template <typename T>
+void s_row_v(mfs_shared* s, const SArgs<T>& a) {
+    if (!s->m) return;
+    switch (pack_of<T>(s->Bp)) {
+        case 4:
+            if constexpr (sizeof(T) == 4)
+                k_s_row<T, 1, 4><<<wgrid((long long)s->m * (s->Bp / 128)), SNT, 0, s->stream>>>(a);
+            break;
+        case 2: k_s_row<T, 1, 2><<<wgrid((long long)s->m * (s->Bp / 64)), SNT, 0, s->stream>>>(a); break;
+        default: k_s_row<T, 1, 1><<<wgrid((long long)s->m * (s->Bp / 32)), SNT, 0, s->stream>>>(a);
+    }
 }
 
 template <typename T>
@@ -552,7 +670,7 @@ mfs_status s_warm(mfs_shared* s, SStore<T>& st, const S* x, const S* lam) {
     if (s->nsoc) k_s_proj_cones<T><<<wgrid((long long)s->nsoc * sl), SNT, 0, s->stream>>>(st.sbuf, st.del, s->soc_start, s->soc_size, s->nsoc, s->Bp);
     // v = F_U (b - A x) - lambda/mu
     SArgs<T> a = sargs(s, st);
-    if (s->m) k_s_row<T, 1><<<wgrid((long long)s->m * sl), SNT, 0, s->stream>>>(a);
+    s_row_v(s, a);
     SCUDA(s, cudaGetLastError());
     SCUDA(s, cudaStreamSynchronize(s->stream));
     s->iter = 0;

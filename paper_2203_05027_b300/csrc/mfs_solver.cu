@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -14,6 +15,7 @@
 #include <vector>
 
 #include "../../include/mfs.h"
+#include "mfs_alloc.h"
 #include "mfs_kernels.cuh"
 
 using namespace mfs;
@@ -120,7 +122,7 @@ template <typename T>
 mfs_status dalloc(mfs_solver* s, T** p, size_t count) {
     void* q = nullptr;
     size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-    cudaError_t e = cudaMalloc(&q, bytes);
+    cudaError_t e = mfs::device_malloc(&q, bytes);
     if (e != cudaSuccess)
         return fail(s, e == cudaErrorMemoryAllocation ? MFS_ERR_OOM : MFS_ERR_CUDA,
                     std::string("cudaMalloc: ") + cudaGetErrorString(e));
@@ -682,7 +684,30 @@ static mfs_status warm_start_impl(mfs_solver* s, const double* x, const double* 
 }
 
 // ====================================================================================== C ABI
+namespace mfs {
+namespace {
+std::atomic<long long> g_alloc_left{-1};  // < 0: no failure armed
+}
+cudaError_t device_malloc(void** p, size_t bytes) {
+    long long left = g_alloc_left.load();
+    while (left >= 0) {
+        if (left == 0) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+        if (g_alloc_left.compare_exchange_weak(left, left - 1)) break;
+    }
+    return cudaMalloc(p, bytes);
+}
+}  // namespace mfs
+
 extern "C" {
+
+mfs_status mfs_debug_fail_alloc_after(int64_t n) {
+    mfs::g_alloc_left.store(n < 0 ? -1 : (long long)n);
+    return MFS_OK;
+}
+
 
 void mfs_default_settings(mfs_settings* st) {
     if (!st) return;

@@ -103,6 +103,10 @@ def load(path=LIB_PATH):
     lib.mfs_set_precision.argtypes = [P, i32]
     lib.mfs_set_precision.restype = st
     lib.mfs_time_kernels.argtypes = [P, i64, dp]
+    lib.mfs_debug_fail_alloc_after.argtypes = [i64]
+    lib.mfs_debug_fail_alloc_after.restype = st
+    lib.mfs_gemm_bf16_wait_test.argtypes = [P]
+    lib.mfs_gemm_bf16_wait_test.restype = st
     lib.mfs_time_kernels.restype = st
     _lib = lib
     return lib
@@ -413,6 +417,16 @@ def _load_mlp():
     lib.mfs_gemm_bf16.restype = st
     lib._mlp_declared = True
     return lib
+
+
+def debug_fail_alloc_after(n):
+    """Arm (n >= 0) or disarm (n < 0) the injected device-allocation failure of the library."""
+    load().mfs_debug_fail_alloc_after(int(n))
+
+
+def gemm_wait_test(stream=None):
+    """Status of the bounded-wait diagnostic GEMM (MFS_ERR_TIMEOUT when the path works)."""
+    return load().mfs_gemm_bf16_wait_test(ctypes.c_void_p(int(stream)) if stream else None)
 
 
 def gemm_bf16(M, N, K, A_ptr, B_ptr, C_ptr, bias_ptr=None, relu=False, out_fp32=True, splits=1, stream=None):

@@ -97,3 +97,20 @@ def test_batch_autotune_returns_a_valid_tuning():
     t = bt.tune(5)
     assert t["threads"] in (128, 256, 512) and 1 <= t["ctas_per_sm"] <= 4
     assert bt.tuning() == t
+
+
+def test_small_lp_in_one_cta_matches_oracle():
+    """The 200 x 500 LP alone: one CTA holds the whole instance in shared memory and runs all 2000
+    iterations in one launch; FP64 iterates agree with the oracle to 1e-10."""
+    p = I.small_lp(0)
+    bt = mfs.Batch([p], precision="fp64", check_every=2000)
+    bt.iterate(2000)
+    orc = oracle.make_oracle(p)
+    orc.iterate(2000)
+    st = orc.state()
+    sol = bt.solution(0)
+    for k, v in (("x", st.x), ("z", st.z), ("delta", st.delta), ("lam", st.lam)):
+        assert rel_err(sol[k], v) <= 1e-10, k
+    its, sts = bt.solve(1e-5, 200_000)
+    r = bt.residuals()[0]
+    assert sts[0] == mfs.MFS_OK and r["kkt"] <= 1e-5

@@ -1,0 +1,74 @@
+"""Failure paths on the GPU, none of which faults, traps or hangs it: a bounded device wait that runs
+out and reports MFS_ERR_TIMEOUT, injected device-allocation failures in every create call
+(MFS_ERR_OOM, nothing leaked), and an infeasible instance inside a batch, which ends at the
+iteration limit alone while the rest of the batch solves."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2203_05027_b300 import build, instances as I, mfs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build.build()
+    mfs.load()
+
+
+def test_gemm_wait_that_runs_out_reports_timeout_and_context_survives():
+    assert mfs.gemm_wait_test() == mfs.MFS_ERR_TIMEOUT
+    g = torch.Generator().manual_seed(0)
+    A = torch.randn((128, 64), generator=g).to(torch.bfloat16)
+    B = torch.randn((128, 64), generator=g).to(torch.bfloat16)
+    Ad, Bd = A.cuda(), B.cuda()
+    C = torch.zeros((128, 128), device="cuda")
+    mfs.gemm_bf16(128, 128, 64, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(),
+                  stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    ref = A.double() @ B.double().T
+    assert (C.cpu().double() - ref).abs().max() <= 1e-5 * (A.double().abs() @ B.double().abs().T).max()
+
+
+def _makers():
+    p = I.small_lp(0)
+    return {
+        "solver": lambda: mfs.Solver(p, precision="fp32"),
+        "batch": lambda: mfs.Batch([p, I.small_lp(1, m=50, n=125)]),
+        "shared": lambda: mfs.Shared(p, 40),
+        "mlp": lambda: mfs.MLP(32, 64, 700, 16),
+    }
+
+
+@pytest.mark.parametrize("kind", ["solver", "batch", "shared", "mlp"])
+def test_allocation_failure_reported_and_nothing_leaked(kind):
+    make = _makers()[kind]
+    make().close()  # context, module and library state in place before measuring
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for n in (0, 1, 3, 7):
+        mfs.debug_fail_alloc_after(n)
+        try:
+            with pytest.raises(mfs.MfsError) as e:
+                make()
+            assert e.value.status == mfs.MFS_ERR_OOM
+        finally:
+            mfs.debug_fail_alloc_after(-1)
+    torch.cuda.synchronize()
+    assert free0 - torch.cuda.mem_get_info()[0] < (32 << 20)
+    h = make()  # the next create works
+    h.close()
+
+
+def test_infeasible_instance_ends_alone_at_the_iteration_limit():
+    good = I.small_lp(0, m=60, n=150)
+    bad = I.small_lp(1, m=60, n=150)
+    bad["val"] = np.abs(bad["val"]) + 0.1  # A > 0, b < 0: no x >= 0 has Ax = b
+    bad["b"] = -np.ones(60)
+    bt = mfs.Batch([good, bad, I.small_lp(2, m=60, n=150)], precision="fp32")
+    its, sts = bt.solve(1e-4, 30_000)
+    assert sts.tolist() == [mfs.MFS_OK, mfs.MFS_MAX_ITER, mfs.MFS_OK]
+    r = bt.residuals()
+    assert r[0]["kkt"] <= 1e-4 and r[2]["kkt"] <= 1e-4
+    assert np.isfinite(r[1]["kkt"]) and r[1]["r_prim"] > 1e-2  # stays infeasible, no NaN

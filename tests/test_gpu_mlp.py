@@ -105,3 +105,22 @@ def test_mlp_training_reduces_the_loss():
     for _ in range(200):
         last = net.train_step(B, Xd.data_ptr(), Td.data_ptr(), 3e-3)
     assert last < 0.2 * first, (first, last)
+
+
+@pytest.mark.parametrize("count,dout", [(1, 9), (700, 133), (20_000, 40)])
+def test_fit_output_scaling_matches_fp64_statistics(count, dout):
+    g = np.random.default_rng(count + dout)
+    # columns with offsets far above their spread (the shifted sums must keep the spread), one
+    # constant column (std raised to the floor)
+    T = (g.standard_normal((count, dout)) * g.uniform(0.01, 3.0, dout) + g.uniform(-1e3, 1e3, dout)).astype(np.float32)
+    T[:, 0] = 5.0
+    Td = torch.from_numpy(T).to(dev)
+    net = mfs.MLP(8, 32, dout, 16, seed=0)
+    net.fit_output_scaling(count, Td.data_ptr(), min_std=1e-3)
+    mean, std = net.output_scaling()
+    Te = T.astype(np.float64)
+    ref_mean, ref_std = Te.mean(0), np.maximum(Te.std(0), 1e-3)
+    assert np.allclose(mean, ref_mean, rtol=1e-6, atol=1e-6 * np.abs(ref_mean).max())
+    assert np.allclose(std, ref_std, rtol=1e-4, atol=0), np.abs(std / ref_std - 1).max()
+    assert std[0] == np.float32(1e-3)
+    net.close()

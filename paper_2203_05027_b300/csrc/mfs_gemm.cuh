@@ -144,6 +144,7 @@ struct GemmArgs {
     int ldc;
     int* err;
     uint32_t spin;  // poll limit of every wait (SPIN in normal use)
+    int m_fast;     // blockIdx.x runs over row tiles (B tiles shared by neighbouring CTAs), else column tiles
     int no_loads;   // diagnostic: issue no loads, so the first wait of the MMA issuer runs out
 };
 
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     int* s_fail = reinterpret_cast<int*>(s_tmem + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+    const int n0 = (g.m_fast ? blockIdx.y : blockIdx.x) * BN, m0 = (g.m_fast ? blockIdx.x : blockIdx.y) * BM;
     const int kb_total = (g.K + BK - 1) / BK;
     const int kb0 = blockIdx.z * g.kblocks_per_split;
     const int kb1 = min(kb_total, kb0 + g.kblocks_per_split);

@@ -118,7 +118,10 @@ mfs_status gemm(int M, int N, int K, const bf16* A, const bf16* B, const float* 
     g.err = err;
     g.spin = spin;
     g.no_loads = no_loads;
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
+    // neighbouring CTAs share the tiles of the larger operand, so it is read from DRAM about once
+    g.m_fast = (long long)N > (long long)M ? 1 : 0;
+    const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
+    dim3 grid(g.m_fast ? mt : nt, g.m_fast ? nt : mt, splits);
     k_gemm_bf16<<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, g);
     if (splits > 1) {
         const long long total = (long long)M * N;

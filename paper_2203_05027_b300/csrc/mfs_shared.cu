@@ -149,8 +149,10 @@ __global__ void __launch_bounds__(SNT) k_s_col(const SArgs<T> a) {
     const long long w = (long long)blockIdx.x * SW + (threadIdx.x >> 5);
     const int groups = a.Bp / (32 * V), lane = threadIdx.x & 31;
     if (w >= (long long)a.n * groups) return;
-    const int j = (int)(w / groups);
-    const int s0 = (int)(w % groups) * 32 * V + lane * V;
+    // group-major: all columns of one group of instances before the next, so that the gathered
+    // slice of v (m x 32V values) stays in L2 while it is used
+    const int j = (int)(w % a.n);
+    const int s0 = (int)(w / a.n) * 32 * V + lane * V;
     const int k0 = a.col_ptr[j], k1 = a.col_ptr[j + 1];
     T acc[V];
     line_dot<T, V>(a.cidx, a.cval, k0, k1, a.v, a.Bp, s0, lane, acc);
@@ -208,8 +210,8 @@ __global__ void __launch_bounds__(SNT) k_s_row(const SArgs<T> a) {
     const long long w = (long long)blockIdx.x * SW + (threadIdx.x >> 5);
     const int groups = a.Bp / (32 * V), lane = threadIdx.x & 31;
     if (w >= (long long)a.m * groups) return;
-    const int i = (int)(w / groups);
-    const int s0 = (int)(w % groups) * 32 * V + lane * V;
+    const int i = (int)(w % a.m);  // group-major, as in k_s_col (the gathered slice of x stays in L2)
+    const int s0 = (int)(w / a.m) * 32 * V + lane * V;
     T acc[V];
     line_dot<T, V>(a.ridx, a.rval, a.row_ptr[i], a.row_ptr[i + 1], a.x, a.Bp, s0, lane, acc);
     const size_t p = (size_t)i * a.Bp + s0;

@@ -45,10 +45,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the extra workloads (batched LPs, shared-A family, MLP step)")
-    ap.add_argument("--warm-start", type=int, default=0, metavar="TRAIN",
-                    help="also run the learned warm-start experiment with TRAIN training solves (minutes)")
-    ap.add_argument("--warm-start-test", type=int, default=1000)
-    ap.add_argument("--section", default="all", choices=["all", "small", "batch", "shared", "mlp"],
+    ap.add_argument("--warm-start", type=int, default=2048, metavar="TRAIN",
+                    help="learned warm-start experiment with TRAIN training solves (0 skips it; 50000 is the "
+                         "full experiment, about 15 minutes)")
+    ap.add_argument("--warm-start-test", type=int, default=128)
+    ap.add_argument("--section", default="all", choices=["all", "small", "socp", "batch", "shared", "mlp"],
                     help="run only one extra workload and print its line (for profiling)")
     ap.add_argument("--tts-iters", type=int, default=300000,
                     help="also solve to 1e-6 KKT from the cold start with at most this many iterations (0: skip)")
@@ -195,10 +196,11 @@ def cpu_baseline(prob, iters=3):
                       f"({dt:.2f} s, set-up not timed)"}
 
 
-def batch_workload(stream, seed, iters=100):
+def batch_workload(stream, seed, iters=100, tts_iters=300_000):
     """Extra workload: 4096 LPs with m log-uniform on [50, 5000], n = 2.5m, 5 nonzeros per column,
     solved together by one persistent launch (FP32 sweep). The autotuner picks threads per CTA and
-    CTAs per SM; then `iters` iterations of the whole batch are timed with CUDA events."""
+    CTAs per SM; then `iters` iterations of the whole batch are timed with CUDA events, and a fresh
+    batch is solved to relative KKT 1e-6 (at most `tts_iters` iterations per instance)."""
     import torch
     from paper_2203_05027_b300 import instances as I, mfs
     probs = I.batch_lps(4096, seed=seed)
@@ -214,13 +216,57 @@ def batch_workload(stream, seed, iters=100):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     bytes_iter = 16 * info["total_nnz"] + 36 * info["total_n"] + 24 * info["total_m"]
+    bt.close()
+    # time to 1e-6 from the cold start, every instance tested inside the launch every 50 iterations
+    if not tts_iters:
+        return {"ms_per_batch_iteration": round(ms / iters, 5), "tuning": tuned}
+    bt2 = mfs.Batch(probs, precision="fp32", check_every=50, stream=stream.cuda_stream)
+    bt2.set_tuning(tuned["threads"], tuned["ctas_per_sm"], 50)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its, sts = bt2.solve(1e-6, tts_iters)
+    torch.cuda.synchronize()
+    tts_s = time.perf_counter() - t0
+    bt2.close()
+    ok = its[sts == 0]
+    tts = {"tol": 1e-6, "max_iter": tts_iters, "seconds": round(tts_s, 3), "converged": int(ok.size),
+           "instances_per_s": round(ok.size / tts_s, 1),
+           "iterations_median": float(np.median(ok)) if ok.size else None,
+           "iterations_p90": float(np.percentile(ok, 90)) if ok.size else None}
     out = {"workload": "batch_lps 4096 instances, m log-uniform [50, 5000], n = 2.5 m, 5 nnz/col",
            "total_nnz": info["total_nnz"], "total_m": info["total_m"], "total_n": info["total_n"],
            "iterations": iters, "ms_per_batch_iteration": round(ms / iters, 5),
            "value": info["total_nnz"] * iters / (ms * 1e-3), "unit": UNIT, "tuning": tuned,
-           "algorithmic_gbs": round(bytes_iter / (ms / iters * 1e-3) / 1e9, 1)}
-    bt.close()
+           "algorithmic_gbs": round(bytes_iter / (ms / iters * 1e-3) / 1e9, 1), "time_to_1e-6": tts}
     return out
+
+
+def socp_workload(stream, seed, iters=250):
+    """Extra workload: the sparse SOCP (n = 1,000,000 in Lorentz cones of sizes 3..64, m = 400,000 rows
+    with 10 nonzeros each), FP32 sweep: `iters` iterations timed with CUDA events (one FP64 residual
+    check every 25)."""
+    import torch
+    from paper_2203_05027_b300 import instances as I, mfs
+    prob = I.socp(seed)
+    s = mfs.Solver(prob, precision="fp32", polish_iters=0, check_every=25, stream=stream.cuda_stream)
+    info = s.info()
+    s.iterate(50)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(iters // 25):
+        s.iterate(25)
+        s.residuals()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    t = s.time_kernels(50)
+    o, m, n = info["o"], info["m"], info["n"]
+    s.close()
+    return {"workload": f"socp n={n} m={m} o={o}, {len(prob['cones'])} cones", "ms_per_iteration": round(ms, 5),
+            "value": o / (ms * 1e-3), "unit": UNIT,
+            "algorithmic_gbs": round((16 * o + 36 * n + 24 * m) / (ms * 1e-3) / 1e9, 1),
+            "kernel_us": {k.replace("_ms", ""): round(v * 1e3, 2) for k, v in t.items()}}
 
 
 def small_workload(stream, seed, iters=2000):
@@ -362,7 +408,8 @@ def main():
 
     if args.section != "all":
         stream = torch.cuda.current_stream()
-        fn = {"small": lambda: small_workload(stream, rank), "batch": lambda: batch_workload(stream, rank), "shared": lambda: shared_workload(stream, rank),
+        fn = {"small": lambda: small_workload(stream, rank), "batch": lambda: batch_workload(stream, rank),
+              "socp": lambda: socp_workload(stream, rank), "shared": lambda: shared_workload(stream, rank),
               "mlp": lambda: mlp_workload(stream, load_peaks_raw())}[args.section]
         if rank == 0:
             print(json.dumps({"section": args.section, **fn()}), flush=True)
@@ -427,12 +474,16 @@ def main():
     if not args.no_batch:
         extra["batch_lps"] = batch_workload(stream, rank)
         extra["small_lp"] = small_workload(stream, rank)
+        extra["socp"] = socp_workload(stream, rank)
         extra["shared_param_lp"] = shared_workload(stream, rank)
         extra["mlp"] = mlp_workload(stream, load_peaks_raw())
-    if args.warm_start:
+    if args.warm_start and not args.no_batch:
         from paper_2203_05027_b300 import warmstart as W
-        extra["warm_start"] = W.run(train=args.warm_start, test=args.warm_start_test, seed=rank,
-                                    log=lambda t: print(t, file=sys.stderr, flush=True))
+        ws = W.run(train=args.warm_start, test=args.warm_start_test, seed=rank,
+                   log=lambda t: print(t, file=sys.stderr, flush=True))
+        extra["warm_start"] = {"workload": f"parametric LP family (m=20000, n=50000), {args.warm_start} training "
+                                           f"solves, {args.warm_start_test} held-out members, to 1e-6",
+                               **{k: v for k, v in ws.items() if k != "stage"}}
 
     e2e = None
     if not args.no_e2e:

@@ -264,8 +264,12 @@ __device__ __forceinline__ Inst load_inst(const BatchArgs<T>& a, int t) {
 }
 
 // MODE 0: iterate (with termination checks when tol > 0); MODE 1: residuals only.
+#ifndef MFS_BATCH_MINB
+#define MFS_BATCH_MINB 2  // 64 registers: two 512-thread CTAs per SM
+#endif
+
 template <typename T, int MODE>
-__global__ void __launch_bounds__(MAXNT) k_batch(const BatchArgs<T> a) {
+__global__ void __launch_bounds__(MAXNT, MFS_BATCH_MINB) k_batch(const BatchArgs<T> a) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ double s_red[MAXW][NFLD];
     __shared__ double s_kkt;

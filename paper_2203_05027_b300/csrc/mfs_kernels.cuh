@@ -24,9 +24,10 @@
 
 #include "mfs_device.cuh"
 
-// Minimum resident CTAs per SM requested for the sweep kernels (register budget).
+// Minimum resident CTAs per SM requested for the FP32 sweep kernels (8 x 256 threads: 32 registers,
+// more warps to keep gathers in flight). The FP64 sweeps, ALU-bound, keep their full register budget.
 #ifndef MFS_SWEEP_MINB
-#define MFS_SWEEP_MINB 1
+#define MFS_SWEEP_MINB 8
 #endif
 
 namespace mfs {
@@ -182,7 +183,7 @@ __device__ __forceinline__ void orthant_update(T* x, T* z, T* del, int j, T xn, 
 
 // ------------------------------------------------------------------------------------ column sweep
 template <typename T, bool SOC>
-__global__ void __launch_bounds__(NT, MFS_SWEEP_MINB) k_col_sweep(const SweepArgs<T> a) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? MFS_SWEEP_MINB : 1) k_col_sweep(const SweepArgs<T> a) {
     __shared__ T s_end[NWARP][ESLOTS];
     __shared__ T s_cone[SOC ? NWARP : 1][3][WC];  // x, w = x - delta/mu, delta of small-cone columns
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -235,17 +236,20 @@ __global__ void __launch_bounds__(NT, MFS_SWEEP_MINB) k_col_sweep(const SweepArg
     }
     if (SOC) {
         __syncwarp();
-        // one lane per small cone of the chunk: z-step (eq. proj) and delta-update
+        // the small cones of the chunk one after another, each by the whole warp: ||w_tail||^2 by a
+        // butterfly sum, then the z-step (eq. proj) and delta-update of one coordinate per lane
         const T* cx = s_cone[warp][0];
         const T* cw = s_cone[warp][1];
         const T* cd = s_cone[warp][2];
-        for (int q = a.cq_lo[ch] + lane; q < a.cq_hi[ch]; q += 32) {
+        for (int q = a.cq_lo[ch]; q < a.cq_hi[ch]; ++q) {
             if (a.soc_big[q]) continue;
             const int c0 = a.soc_start[q] - lo, sz = a.soc_size[q];
             T ss = T(0);
-            for (int t = 1; t < sz; ++t) ss += cw[c0 + t] * cw[c0 + t];
+            for (int t = 1 + lane; t < sz; t += 32) ss += cw[c0 + t] * cw[c0 + t];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(FULL, ss, o);
             const T alpha = sqrt(ss), w1 = cw[c0];
-            for (int t = 0; t < sz; ++t) {
+            for (int t = lane; t < sz; t += 32) {
                 const T zt = lorentz_coord(cw[c0 + t], t, w1, alpha);
                 a.z[lo + c0 + t] = zt;
                 a.del[lo + c0 + t] = cd[c0 + t] + mu * (zt - cx[c0 + t]);
@@ -320,7 +324,7 @@ __device__ __forceinline__ void row_update(const SweepArgs<T>& a, int i, T ax, T
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(NT, MFS_SWEEP_MINB) k_row_sweep(const SweepArgs<T> a) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? MFS_SWEEP_MINB : 1) k_row_sweep(const SweepArgs<T> a) {
     __shared__ T s_end[NWARP][2 * ESLOTS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ch = blockIdx.x * NWARP + warp;
@@ -604,17 +608,24 @@ __global__ void __launch_bounds__(NT) k_col_resid(const SweepArgs<T> a, const Re
             __syncwarp();
             const double* cs_ = s_cone[warp][0];
             const double* cx_ = s_cone[warp][1];
-            for (int q = a.cq_lo[ch] + lane; q < a.cq_hi[ch]; q += 32) {
+            for (int q = a.cq_lo[ch]; q < a.cq_hi[ch]; ++q) {  // each small cone by the whole warp
                 if (a.soc_big[q]) continue;
                 const int c0 = a.soc_start[q] - lo, sz = a.soc_size[q];
                 double ss = 0.0, xx = 0.0;
-                for (int t = 1; t < sz; ++t) {
+                for (int t = 1 + lane; t < sz; t += 32) {
                     ss += cs_[c0 + t] * cs_[c0 + t];
                     xx += cx_[c0 + t] * cx_[c0 + t];
                 }
-                const double s1 = cs_[c0], x1 = cx_[c0];
-                f[C_SDIST2] += lorentz_dist2(s1, sqrt(ss), ss + s1 * s1);
-                f[C_XDIST2] += lorentz_dist2(x1, sqrt(xx), xx + x1 * x1);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    ss += __shfl_xor_sync(FULL, ss, o);
+                    xx += __shfl_xor_sync(FULL, xx, o);
+                }
+                if (lane == 0) {
+                    const double s1 = cs_[c0], x1 = cx_[c0];
+                    f[C_SDIST2] += lorentz_dist2(s1, sqrt(ss), ss + s1 * s1);
+                    f[C_XDIST2] += lorentz_dist2(x1, sqrt(xx), xx + x1 * x1);
+                }
             }
             __syncwarp();
         }

@@ -57,10 +57,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2203_05027_b300 import replicas
+    return replicas.env()
 
 
 def make_problem(name, seed):
@@ -441,13 +439,10 @@ def main():
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    from paper_2203_05027_b300 import replicas
+    ms = replicas.max_over_ranks(ev0.elapsed_time(ev1), dist, device="cuda")
     iters = args.steps * ITERS_PER_STEP
-    value = world * o * iters / (ms * 1e-3)
+    value = replicas.job_throughput(o * iters, world, ms)
 
     peak, peak_kind = load_peaks()
     clocks = clk.summary()

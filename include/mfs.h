@@ -139,6 +139,17 @@ mfs_status mfs_warm_start(mfs_solver* s, const double* x, const double* lambda, 
 mfs_status mfs_warm_start_device(mfs_solver* s, const double* x, const double* lambda,
                                  const double* z, const double* delta);
 
+/* Start from an arbitrary point of Algorithm 1 (its Require line: x, z, delta in R^n, y, gamma in
+   R^o, lambda in R^m), all host FP64 arrays, required. y and gamma follow Algorithm 1's nonzero
+   order k: columns in turn, rows ascending within each column, over the o nonzeros of the stored A
+   (duplicates summed, explicit zeros dropped; o as in mfs_info_t). The next two iterations run the
+   literal updates of Algorithm 1 on the o-length y and gamma; after them gamma = -U^T lambda and
+   y = V^T x + U^T F_U (b - A x) hold, and the solver continues with its reduced sweeps, so every
+   iterate equals Algorithm 1's from that start. Resets the iteration count. MFS_ERR_INVALID for a
+   NULL array; changing the precision is refused until the two literal iterations have run. */
+mfs_status mfs_warm_start_literal(mfs_solver* s, const double* x, const double* y, const double* z,
+                                  const double* gamma, const double* delta, const double* lambda);
+
 /* Run exactly k >= 0 iterations (Algorithm 1, steps 5-10) with no termination test. */
 mfs_status mfs_iterate(mfs_solver* s, int64_t k);
 

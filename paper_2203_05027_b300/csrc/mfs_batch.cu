@@ -952,7 +952,7 @@ mfs_status mfs_batch_tune(mfs_batch* s, int64_t iters, mfs_batch_tuning* chosen)
     BCUDA(s, cudaEventCreate(&e0));
     BCUDA(s, cudaEventCreate(&e1));
     for (int threads : {128, 256, 512}) {
-        for (int cps : {1, 2, 3}) {
+        for (int cps : {1, 2, 3, 4}) {
             mfs_batch_tuning t = keep;
             t.threads = threads;
             t.ctas_per_sm = cps;

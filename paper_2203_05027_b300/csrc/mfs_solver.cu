@@ -17,6 +17,7 @@
 #include "../../include/mfs.h"
 #include "mfs_alloc.h"
 #include "mfs_kernels.cuh"
+#include "mfs_literal.cuh"
 
 using namespace mfs;
 
@@ -90,6 +91,12 @@ struct mfs_solver {
     State<float> s32;
     State<double> s64;
     bool have32 = false, have64 = false;
+    // literal start (Algorithm 1 with o-length y and gamma) pending for the next lit_pending iterations
+    int lit_pending = 0;
+    void *lit_y = nullptr, *lit_g = nullptr, *lit_kval = nullptr, *lit_w = nullptr, *lit_row = nullptr;
+    int *lit_krow = nullptr, *lit_kcol = nullptr, *lit_perm = nullptr, *lit_rp = nullptr;
+    double* lit_zarg = nullptr;
+    std::vector<void*> lit_mem;
     std::vector<void*> allocs;
     std::string last_error;
 };
@@ -642,9 +649,12 @@ static mfs_status time_kernels_t(mfs_solver* s, State<T>& st, int64_t k, double*
     return MFS_OK;
 }
 
+static void literal_free(mfs_solver* s);
+
 static mfs_status warm_start_impl(mfs_solver* s, const double* x, const double* lam, const double* z,
                                   const double* del, bool host) {
     if (!s) return MFS_ERR_INVALID;
+    literal_free(s);
     if ((s->n && !x) || (s->m && !lam)) return fail(s, MFS_ERR_INVALID, "x and lambda are required");
     CUDA_TRY(s, cudaSetDevice(s->device));
     const double *dx = x, *dl = lam, *dz = z, *dd = del;
@@ -681,6 +691,141 @@ static mfs_status warm_start_impl(mfs_solver* s, const double* x, const double* 
         cudaStreamSynchronize(s->stream);
     }
     return st;
+}
+
+// ------------------------------------------------------------------ literal start (Algorithm 1)
+static void literal_free(mfs_solver* s) {
+    if (!s->lit_mem.empty()) cudaStreamSynchronize(s->stream);
+    for (void* p : s->lit_mem) cudaFree(p);
+    s->lit_mem.clear();
+    s->lit_y = s->lit_g = s->lit_kval = s->lit_w = s->lit_row = nullptr;
+    s->lit_krow = s->lit_kcol = s->lit_perm = s->lit_rp = nullptr;
+    s->lit_zarg = nullptr;
+    s->lit_pending = 0;
+}
+
+template <typename P>
+mfs_status lit_alloc(mfs_solver* s, P** p, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = mfs::device_malloc(&q, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return fail(s, MFS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    s->lit_mem.push_back(q);
+    *p = static_cast<P*>(q);
+    return MFS_OK;
+}
+
+inline int blocks_for(long long count, int bs = 256) {
+    return (int)std::max<long long>(1, std::min<long long>((count + bs - 1) / bs, 148LL * 32));
+}
+
+// Host arrays (FP64): x, z, delta (n), y, gamma (o, Algorithm 1's nonzero order), lambda (m).
+template <typename T>
+mfs_status literal_setup(mfs_solver* s, State<T>& st, const double* x, const double* y, const double* z,
+                         const double* g, const double* del, const double* lam) {
+    literal_free(s);
+    const int64_t n = s->n, m = s->m, o = s->o;
+    double* tmp = nullptr;
+    TRY(lit_alloc(s, &tmp, (size_t)std::max<int64_t>({n, m, o, 1}) * sizeof(double)));
+    auto put = [&](const double* h, int64_t cnt, T* dst) -> mfs_status {
+        if (!cnt) return MFS_OK;
+        CUDA_TRY(s, cudaMemcpyAsync(tmp, h, cnt * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        convert(dst, tmp, cnt, s->stream);
+        CUDA_TRY(s, cudaStreamSynchronize(s->stream));  // tmp is reused by the next call
+        return MFS_OK;
+    };
+    T *ly = nullptr, *lg = nullptr, *kval = nullptr;
+    TRY(lit_alloc(s, &ly, o * sizeof(T)));
+    TRY(lit_alloc(s, &lg, o * sizeof(T)));
+    TRY(lit_alloc(s, &kval, o * sizeof(T)));
+    s->lit_y = ly;
+    s->lit_g = lg;
+    s->lit_kval = kval;
+    TRY(put(x, n, st.x));
+    TRY(put(z, n, st.z));
+    TRY(put(del, n, st.del));
+    TRY(put(lam, m, st.lam));
+    TRY(put(y, o, ly));
+    TRY(put(g, o, lg));
+    T *w = nullptr, *row = nullptr;
+    TRY(lit_alloc(s, &w, o * sizeof(T)));
+    TRY(lit_alloc(s, &row, m * sizeof(T)));
+    s->lit_w = w;
+    s->lit_row = row;
+    TRY(lit_alloc(s, &s->lit_krow, o * sizeof(int)));
+    TRY(lit_alloc(s, &s->lit_kcol, o * sizeof(int)));
+    TRY(lit_alloc(s, &s->lit_perm, o * sizeof(int)));
+    TRY(lit_alloc(s, &s->lit_rp, (m + 1) * sizeof(int)));
+    TRY(lit_alloc(s, &s->lit_zarg, n * sizeof(double)));
+    if (s->ncc)
+        mfs::literal::k_kmap<T><<<blocks_for(s->ncc), 256, 0, s->stream>>>(s->col_ptr, s->cdesc, s->ncc, s->cidx,
+                                                                          st.cval, s->lit_krow, s->lit_kcol, kval);
+    // rows of the k order: a stable counting sort (index bookkeeping of the set-up, as at create)
+    std::vector<int> krow(o), rp(m + 1, 0), perm(o);
+    if (o) CUDA_TRY(s, cudaMemcpyAsync(krow.data(), s->lit_krow, o * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    for (int64_t k = 0; k < o; ++k) rp[krow[k] + 1]++;
+    for (int64_t i = 0; i < m; ++i) rp[i + 1] += rp[i];
+    std::vector<int> fill(rp.begin(), rp.end() - 1);
+    for (int64_t k = 0; k < o; ++k) perm[fill[krow[k]]++] = (int)k;
+    if (o) CUDA_TRY(s, cudaMemcpyAsync(s->lit_perm, perm.data(), o * sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(s, cudaMemcpyAsync(s->lit_rp, rp.data(), (m + 1) * sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(s, cudaGetLastError());
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    s->lit_pending = 2;
+    s->iter = 0;
+    return MFS_OK;
+}
+
+// One iteration of Algorithm 1 in its literal form.
+template <typename T>
+mfs_status literal_iteration(mfs_solver* s, State<T>& st) {
+    namespace L = mfs::literal;
+    const int n = s->n, m = s->m;
+    const long long o = s->o;
+    const T mu = T(s->set.mu);
+    T* y = static_cast<T*>(s->lit_y);
+    T* g = static_cast<T*>(s->lit_g);
+    T* kval = static_cast<T*>(s->lit_kval);
+    T* w = static_cast<T*>(s->lit_w);
+    T* row = static_cast<T*>(s->lit_row);
+    cudaStream_t q = s->stream;
+    if (n) L::k_x<T><<<blocks_for(n), 256, 0, q>>>(s->col_ptr, y, g, st.z, st.del, st.c, mu, st.x, n);
+    if (o) L::k_w<T><<<blocks_for(o), 256, 0, q>>>(s->lit_krow, s->lit_kcol, kval, st.b, st.lam, st.x, g, mu, w, o);
+    if (m) L::k_rowdot<T><<<blocks_for(m), 256, 0, q>>>(s->lit_rp, s->lit_perm, kval, w, 1, row, m);
+    if (o) L::k_y<T><<<blocks_for(o), 256, 0, q>>>(s->lit_krow, kval, w, row, y, o);
+    if (n) {
+        L::k_zarg<T><<<blocks_for(n), 256, 0, q>>>(st.x, st.del, mu, s->lit_zarg, n);
+        k_proj_orthant<T><<<blocks_for(n), 256, 0, q>>>(st.z, s->lit_zarg, n);
+        if (s->nsoc)
+            k_proj_soc<T><<<blocks_for(s->nsoc), 256, 0, q>>>(st.z, s->lit_zarg, s->soc_start, s->soc_size, s->nsoc);
+    }
+    if (m) {
+        L::k_rowdot<T><<<blocks_for(m), 256, 0, q>>>(s->lit_rp, s->lit_perm, kval, y, 0, row, m);
+        L::k_lam<T><<<blocks_for(m), 256, 0, q>>>(row, st.b, mu, st.lam, m);
+    }
+    if (o) L::k_gam<T><<<blocks_for(o), 256, 0, q>>>(s->lit_kcol, y, st.x, mu, g, o);
+    if (n) L::k_del<T><<<blocks_for(n), 256, 0, q>>>(st.z, st.x, mu, st.del, n);
+    CUDA_TRY(s, cudaGetLastError());
+    return MFS_OK;
+}
+
+// Run the pending literal iterations (at most k of them); after the second, switch to the reduced
+// state: v = F_U (b - A x) - lambda/mu. Returns the number of iterations run in *done.
+template <typename T>
+mfs_status literal_run(mfs_solver* s, State<T>& st, int64_t k, int64_t* done) {
+    *done = 0;
+    while (s->lit_pending > 0 && *done < k) {
+        TRY(literal_iteration(s, st));
+        --s->lit_pending;
+        ++*done;
+        ++s->iter;
+    }
+    if (s->lit_pending == 0 && !s->lit_mem.empty()) {
+        launch_warm_v(s, sweep_args(s, st), s->stream);
+        CUDA_TRY(s, cudaGetLastError());
+        literal_free(s);
+    }
+    return MFS_OK;
 }
 
 // ====================================================================================== C ABI
@@ -727,6 +872,7 @@ void mfs_destroy(mfs_solver* s) {
     cudaSetDevice(s->device);
     if (s->stream) cudaStreamSynchronize(s->stream);
     destroy_graphs(s);
+    literal_free(s);
     for (void* p : s->allocs) cudaFree(p);
     if (s->h_status) cudaFreeHost(s->h_status);
     if (s->cap) cudaStreamDestroy(s->cap);
@@ -914,6 +1060,18 @@ mfs_status mfs_warm_start(mfs_solver* s, const double* x, const double* lambda, 
     return warm_start_impl(s, x, lambda, z, delta, true);
 }
 
+mfs_status mfs_warm_start_literal(mfs_solver* s, const double* x, const double* y, const double* z,
+                                  const double* gamma, const double* delta, const double* lambda) {
+    if (!s) return MFS_ERR_INVALID;
+    if ((s->n && (!x || !z || !delta)) || (s->o && (!y || !gamma)) || (s->m && !lambda))
+        return fail(s, MFS_ERR_INVALID, "x, y, z, gamma, delta and lambda are all required");
+    CUDA_TRY(s, cudaSetDevice(s->device));
+    mfs_status st = s->precision == MFS_FP64 ? literal_setup(s, s->s64, x, y, z, gamma, delta, lambda)
+                                              : literal_setup(s, s->s32, x, y, z, gamma, delta, lambda);
+    if (st != MFS_OK) literal_free(s);
+    return st;
+}
+
 mfs_status mfs_warm_start_device(mfs_solver* s, const double* x, const double* lambda, const double* z,
                                  const double* delta) {
     return warm_start_impl(s, x, lambda, z, delta, false);
@@ -923,6 +1081,11 @@ mfs_status mfs_iterate(mfs_solver* s, int64_t k) {
     if (!s) return MFS_ERR_INVALID;
     if (k < 0) return fail(s, MFS_ERR_INVALID, "k must be >= 0");
     CUDA_TRY(s, cudaSetDevice(s->device));
+    if (s->lit_pending > 0) {
+        int64_t done = 0;
+        TRY(s->precision == MFS_FP64 ? literal_run(s, s->s64, k, &done) : literal_run(s, s->s32, k, &done));
+        k -= done;
+    }
     TRY(s->precision == MFS_FP64 ? run_iters(s, s->s64, k) : run_iters(s, s->s32, k));
     CUDA_TRY(s, cudaStreamSynchronize(s->stream));
     return MFS_OK;
@@ -938,6 +1101,8 @@ mfs_status mfs_set_precision(mfs_solver* s, int32_t precision) {
     if (!s) return MFS_ERR_INVALID;
     if (precision != MFS_FP64 && precision != MFS_FP32_MIXED) return fail(s, MFS_ERR_INVALID, "unknown precision");
     if (precision == s->precision) return MFS_OK;
+    if (s->lit_pending > 0)
+        return fail(s, MFS_ERR_INVALID, "a literal start is pending: iterate twice before changing the precision");
     if ((precision == MFS_FP64 && !s->have64) || (precision == MFS_FP32_MIXED && !s->have32))
         return fail(s, MFS_ERR_INVALID, "that precision was not prepared at mfs_create");
     CUDA_TRY(s, cudaSetDevice(s->device));

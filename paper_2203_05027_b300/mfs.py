@@ -94,6 +94,8 @@ def load(path=LIB_PATH):
     for name in ("mfs_warm_start", "mfs_warm_start_device", "mfs_get_solution", "mfs_get_solution_device"):
         getattr(lib, name).argtypes = [P, P, P, P, P]
         getattr(lib, name).restype = st
+    lib.mfs_warm_start_literal.argtypes = [P, P, P, P, P, P, P]
+    lib.mfs_warm_start_literal.restype = st
     lib.mfs_iterate.argtypes = [P, i64]
     lib.mfs_iterate.restype = st
     lib.mfs_solve.argtypes = [P, dbl, i64, lp]
@@ -195,6 +197,12 @@ class Solver:
         x, lam = _f64(x, self.n), _f64(lam, self.m)
         z, delta = _f64(z, self.n), _f64(delta, self.n)
         self._check(self._lib.mfs_warm_start(self._h, _ptr(x), _ptr(lam), _ptr(z), _ptr(delta)))
+
+    def warm_start_literal(self, x, y, z, gamma, delta, lam):
+        """Algorithm 1's full starting point; y and gamma in its nonzero order (length o)."""
+        o = self.info()["o"]
+        arrs = [_f64(x, self.n), _f64(y, o), _f64(z, self.n), _f64(gamma, o), _f64(delta, self.n), _f64(lam, self.m)]
+        self._check(self._lib.mfs_warm_start_literal(self._h, *[_ptr(a) for a in arrs]))
 
     def warm_start_device(self, x, lam, z=None, delta=None):
         """Device pointers (ints) to float64 arrays, e.g. torch tensors' data_ptr()."""

@@ -270,6 +270,16 @@ mfs_status mfs_shared_residuals(mfs_shared* sh, mfs_residuals_t* out);
 mfs_status mfs_shared_solve(mfs_shared* sh, double tol, int64_t max_iter, int64_t* iters);
 /* Iterate, instance-major, device floats: x [count][n], lambda [count][m] (either may be NULL). */
 mfs_status mfs_shared_get_solution_device(mfs_shared* sh, float* x, float* lambda);
+/* Continuous batching: members enter and leave single slots while the other slots iterate on.
+   slots: host array of count distinct slot numbers in [0, count of the handle). load_slots gives
+   those slots new data, b [count][m] and c [count][n] as device FP32 rows in the order of slots,
+   and the zero start (x = z = delta = lambda = 0); the other slots are untouched. get_slots_device
+   copies those slots' x [count][n] and lambda [count][m] into device FP32 arrays (either may be
+   NULL). Both synchronous; MFS_ERR_INVALID for a bad slot list. */
+mfs_status mfs_shared_load_slots(mfs_shared* sh, int64_t count, const int32_t* slots, const float* b,
+                                 const float* c);
+mfs_status mfs_shared_get_slots_device(mfs_shared* sh, int64_t count, const int32_t* slots, float* x,
+                                       float* lambda);
 /* Iterate of instance t as host doubles (any may be NULL): x, z, delta (n), lambda (m). */
 mfs_status mfs_shared_get_solution(mfs_shared* sh, int64_t t, double* x, double* lambda, double* z,
                                    double* delta);

@@ -434,6 +434,33 @@ __global__ void k_s_extract(const S* __restrict__ src, double* __restrict__ out,
         out[l] = double(src[(size_t)l * Bp + t]);
 }
 
+// Slots of the interleaved layout, for members entering and leaving one at a time:
+// dst[l][slots[q]] = src[q][l] (enter), dst[q][l] = src[l][slots[q]] (leave), arr[l][slots[q]] = 0.
+template <typename S, typename D>
+__global__ void k_s_scatter_slots(const S* __restrict__ src, D* __restrict__ dst, const int* __restrict__ slots,
+                                  int count, int len, int Bp) {
+    const long long total = (long long)count * len;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(t / len), l = (int)(t % len);
+        dst[(size_t)l * Bp + slots[q]] = D(src[t]);
+    }
+}
+template <typename S, typename D>
+__global__ void k_s_gather_slots(const S* __restrict__ src, D* __restrict__ dst, const int* __restrict__ slots,
+                                 int count, int len, int Bp) {
+    const long long total = (long long)count * len;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(t / len), l = (int)(t % len);
+        dst[t] = D(src[(size_t)l * Bp + slots[q]]);
+    }
+}
+template <typename T>
+__global__ void k_s_zero_slots(T* __restrict__ arr, const int* __restrict__ slots, int count, int len, int Bp) {
+    const long long total = (long long)count * len;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x)
+        arr[(size_t)(t % len) * Bp + slots[t / len]] = T(0);
+}
+
 template <typename T>
 struct SStore {
     T *cval = nullptr, *rval = nullptr, *fu = nullptr, *b = nullptr, *c = nullptr;
@@ -455,6 +482,7 @@ struct mfs_shared {
         *soc_size = nullptr;
     unsigned char* in_soc = nullptr;
     double *part = nullptr, *status = nullptr, *h_status = nullptr;
+    int* slot_buf = nullptr;  // device copy of a slot list (B entries at most)
     SStore<float> f32;
     SStore<double> f64;
     std::vector<void*> allocs;
@@ -681,6 +709,42 @@ mfs_status s_warm(mfs_shared* s, SStore<T>& st, const S* x, const S* lam) {
 
 }  // namespace
 
+// Copies a host slot list to the device after checking it (distinct slots in [0, B)).
+static mfs_status put_slots(mfs_shared* s, int64_t count, const int32_t* slots) {
+    if (count < 0 || count > s->B || (count && !slots)) return sfail(s, MFS_ERR_INVALID, "slots: 0 <= count <= B");
+    std::vector<char> seen(s->B, 0);
+    for (int64_t q = 0; q < count; ++q) {
+        if (slots[q] < 0 || slots[q] >= s->B || seen[slots[q]])
+            return sfail(s, MFS_ERR_INVALID, "slots must be distinct and in [0, count of the handle)");
+        seen[slots[q]] = 1;
+    }
+    if (count)
+        SCUDA(s, cudaMemcpyAsync(s->slot_buf, slots, count * sizeof(int32_t), cudaMemcpyHostToDevice, s->stream));
+    return MFS_OK;
+}
+
+static int grid_for(long long total) {
+    return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 148LL * 16));
+}
+
+template <typename T>
+static mfs_status load_slots_t(mfs_shared* s, SStore<T>& st, int count, const float* b, const float* c) {
+    const int* sl = s->slot_buf;
+    const long long tm = (long long)count * s->m, tn = (long long)count * s->n;
+    if (tm) k_s_scatter_slots<float, T><<<grid_for(tm), 256, 0, s->stream>>>(b, st.b, sl, count, s->m, s->Bp);
+    if (tn) k_s_scatter_slots<float, T><<<grid_for(tn), 256, 0, s->stream>>>(c, st.c, sl, count, s->n, s->Bp);
+    T* nvec[3] = {st.x, st.z, st.del};
+    T* mvec[2] = {st.lam, st.v};
+    if (tn) {
+        for (int q = 0; q < 3; ++q) k_s_zero_slots<T><<<grid_for(tn), 256, 0, s->stream>>>(nvec[q], sl, count, s->n, s->Bp);
+    }
+    if (tm) {
+        for (int q = 0; q < 2; ++q) k_s_zero_slots<T><<<grid_for(tm), 256, 0, s->stream>>>(mvec[q], sl, count, s->m, s->Bp);
+    }
+    SCUDA(s, cudaGetLastError());
+    return MFS_OK;
+}
+
 extern "C" {
 
 mfs_status mfs_shared_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col, const double* val,
@@ -797,6 +861,7 @@ mfs_status mfs_shared_create(int64_t m, int64_t n, int64_t nnz, const int64_t* r
     SCHK(salloc(s, &s->soc_size, ssz.size(), ssz.data()));
     SCHK(salloc(s, &s->part, (size_t)NFLD * s->G * s->Bp));
     SCHK(salloc(s, &s->status, (size_t)NSTAT * s->B));
+    SCHK(salloc(s, &s->slot_buf, (size_t)s->B));
     if (set.precision == MFS_FP64)
         SCHK(s_alloc_store(s, s->f64, cv, rv, fu));
     else
@@ -964,6 +1029,35 @@ mfs_status mfs_shared_get_solution_device(mfs_shared* s, float* x, float* lambda
     } else {
         if (x) deinterleave(s->f32.x, x, s->B, s->n, s->Bp, s->stream);
         if (lambda) deinterleave(s->f32.lam, lambda, s->B, s->m, s->Bp, s->stream);
+    }
+    SCUDA(s, cudaGetLastError());
+    SCUDA(s, cudaStreamSynchronize(s->stream));
+    return MFS_OK;
+}
+
+mfs_status mfs_shared_load_slots(mfs_shared* s, int64_t count, const int32_t* slots, const float* b, const float* c) {
+    if (!s) return MFS_ERR_INVALID;
+    if (count > 0 && ((s->m && !b) || (s->n && !c))) return sfail(s, MFS_ERR_INVALID, "b and c are required");
+    SCUDA(s, cudaSetDevice(s->device));
+    STRY(put_slots(s, count, slots));
+    if (count)
+        STRY(s->set.precision == MFS_FP64 ? load_slots_t(s, s->f64, (int)count, b, c)
+                                          : load_slots_t(s, s->f32, (int)count, b, c));
+    SCUDA(s, cudaStreamSynchronize(s->stream));
+    return MFS_OK;
+}
+
+mfs_status mfs_shared_get_slots_device(mfs_shared* s, int64_t count, const int32_t* slots, float* x, float* lambda) {
+    if (!s) return MFS_ERR_INVALID;
+    SCUDA(s, cudaSetDevice(s->device));
+    STRY(put_slots(s, count, slots));
+    const long long tm = count * (long long)s->m, tn = count * (long long)s->n;
+    if (s->set.precision == MFS_FP64) {
+        if (x && tn) k_s_gather_slots<double, float><<<grid_for(tn), 256, 0, s->stream>>>(s->f64.x, x, s->slot_buf, (int)count, s->n, s->Bp);
+        if (lambda && tm) k_s_gather_slots<double, float><<<grid_for(tm), 256, 0, s->stream>>>(s->f64.lam, lambda, s->slot_buf, (int)count, s->m, s->Bp);
+    } else {
+        if (x && tn) k_s_gather_slots<float, float><<<grid_for(tn), 256, 0, s->stream>>>(s->f32.x, x, s->slot_buf, (int)count, s->n, s->Bp);
+        if (lambda && tm) k_s_gather_slots<float, float><<<grid_for(tm), 256, 0, s->stream>>>(s->f32.lam, lambda, s->slot_buf, (int)count, s->m, s->Bp);
     }
     SCUDA(s, cudaGetLastError());
     SCUDA(s, cudaStreamSynchronize(s->stream));

@@ -556,7 +556,9 @@ def _load_shared():
                        ("mfs_shared_iterate", [P, i64]), ("mfs_shared_residuals", [P, P]),
                        ("mfs_shared_solve", [P, ctypes.c_double, i64, P]),
                        ("mfs_shared_get_solution_device", [P, P, P]),
-                       ("mfs_shared_get_solution", [P, i64, P, P, P, P])):
+                       ("mfs_shared_get_solution", [P, i64, P, P, P, P]),
+                       ("mfs_shared_load_slots", [P, i64, P, P, P]),
+                       ("mfs_shared_get_slots_device", [P, i64, P, P, P])):
         getattr(lib, name).argtypes = args
         getattr(lib, name).restype = st
     lib._shared_declared = True
@@ -642,6 +644,16 @@ class Shared:
 
     def solution_device(self, x_ptr=None, lam_ptr=None):
         self._check(self._lib.mfs_shared_get_solution_device(self._h, _vp(x_ptr), _vp(lam_ptr)))
+
+    def load_slots(self, slots, b_ptr, c_ptr):
+        """New members (device FP32 rows b [k][m], c [k][n]) into the given slots, zero start."""
+        sl = np.ascontiguousarray(slots, np.int32)
+        self._check(self._lib.mfs_shared_load_slots(self._h, sl.size, _ptr(sl), _vp(b_ptr), _vp(c_ptr)))
+
+    def slots_device(self, slots, x_ptr=None, lam_ptr=None):
+        """x [k][n] and lambda [k][m] of the given slots into device FP32 arrays."""
+        sl = np.ascontiguousarray(slots, np.int32)
+        self._check(self._lib.mfs_shared_get_slots_device(self._h, sl.size, _ptr(sl), _vp(x_ptr), _vp(lam_ptr)))
 
     def solution(self, t):
         x, z, d = (np.empty(self.n) for _ in range(3))

@@ -54,32 +54,61 @@ def solve_batch(sh, fam, theta, tol, max_iter, warm=None):
     return its, time.perf_counter() - t0
 
 
-def generate(fam, count, seed, tol, max_iter, batch=256, check_every=250):
+def generate(fam, count, seed, tol, max_iter, batch=512, check_every=250):
     """Training data: theta (count x p, FP32) and targets [x | lambda] (count x (n+m), FP32) on the
-    device, from cold-start solves to tol. Members that miss tol keep their last iterate."""
+    device, from cold-start solves to tol with at most max_iter iterations (the iterate is kept either
+    way). Continuous batching: `batch` slots of the shared-A solver iterate together; every
+    check_every iterations the members that are done leave their slots and the next members enter.
+    Returns (theta, targets, iterations per member (-1 if it missed tol), seconds)."""
     import torch
     base = fam["base"]
     n, m = base["n"], base["m"]
     th = thetas(count, seed, fam["p"])
     T = torch.empty((count, n + m), dtype=torch.float32, device="cuda")
-    X = torch.empty((batch, n), dtype=torch.float32, device="cuda")
-    L = torch.empty((batch, m), dtype=torch.float32, device="cuda")
-    sh = mfs.Shared(base, batch, check_every=check_every, precision="fp32")
-    iters = []
+    slots = min(batch, count)
+    sh = mfs.Shared(base, slots, check_every=check_every, precision="fp32")
+    X = torch.empty((slots, n), dtype=torch.float32, device="cuda")
+    L = torch.empty((slots, m), dtype=torch.float32, device="cuda")
+    member = np.full(slots, -1)
+    age = np.zeros(slots, np.int64)
+    iters = np.full(count, -1, np.int64)
+    nxt = 0
+
+    def enter(sl):
+        nonlocal nxt
+        idx = np.arange(nxt, nxt + len(sl))
+        nxt += len(sl)
+        b, c = data_of(fam, th[idx])
+        bd = torch.from_numpy(b.astype(np.float32)).cuda()
+        cd = torch.from_numpy(c.astype(np.float32)).cuda()
+        sh.load_slots(sl, bd.data_ptr(), cd.data_ptr())
+        member[sl] = idx
+        age[sl] = 0
+
     t0 = time.perf_counter()
-    for s0 in range(0, count, batch):
-        k = min(batch, count - s0)
-        tb = np.zeros((batch, fam["p"]))
-        tb[:k] = th[s0:s0 + k]
-        its, _ = solve_batch(sh, fam, tb, tol, max_iter)
-        iters.extend(its[:k].tolist())
-        sh.solution_device(X.data_ptr(), L.data_ptr())
-        T[s0:s0 + k, :n].copy_(X[:k])
-        T[s0:s0 + k, n:].copy_(L[:k])
+    enter(np.arange(slots))
+    done = 0
+    while done < count:
+        sh.iterate(check_every)
+        age += check_every
+        kkt = np.array([r["kkt"] for r in sh.residuals()])
+        met = kkt <= tol
+        fin = np.where((member >= 0) & (met | (age >= max_iter)))[0]
+        if len(fin):
+            sh.slots_device(fin, X.data_ptr(), L.data_ptr())
+            rows = torch.from_numpy(member[fin]).cuda()
+            T[rows, :n] = X[:len(fin)]
+            T[rows, n:] = L[:len(fin)]
+            iters[member[fin]] = np.where(met[fin], age[fin], -1)
+            done += len(fin)
+            member[fin] = -1
+            k = min(len(fin), count - nxt)
+            if k:
+                enter(fin[:k])
     torch.cuda.synchronize()
     sh.close()
     theta = torch.from_numpy(th.astype(np.float32)).cuda()
-    return theta, T, np.asarray(iters), time.perf_counter() - t0
+    return theta, T, iters, time.perf_counter() - t0
 
 
 def train_fn(net, theta, T, epochs, lr, batch, lr_final=None):

@@ -110,3 +110,41 @@ def test_shared_solve_records_first_iterations():
             orc2 = oracle.make_oracle(dict(base, b=b[t], c=c[t]))
             orc2.iterate(int(its[t]) - 100)
             assert orc2.residuals()["kkt"] > 1e-6
+
+
+def test_slots_enter_and_leave_while_others_iterate():
+    base = I.small_lp(4, m=120, n=300)
+    count = 40
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)  # data given as FP32 rows
+    b, c = (f32(a) for a in family(base, count, 4))
+    b2, c2 = (f32(a) for a in family(base, 3, 5))
+    sh = mfs.Shared(base, count, precision="fp64", check_every=10)
+    sh.set_data(b, c)
+    sh.iterate(30)
+    slots = np.array([3, 17, 33], np.int32)
+    bd = torch.from_numpy(b2.astype(np.float32)).cuda()
+    cd = torch.from_numpy(c2.astype(np.float32)).cuda()
+    sh.load_slots(slots, bd.data_ptr(), cd.data_ptr())
+    sh.iterate(50)
+    for t in (0, 3, 17, 20, 33, 39):
+        if t in slots:
+            q = int(np.where(slots == t)[0][0])
+            p, its = dict(base, b=b2[q], c=c2[q]), 50
+        else:
+            p, its = dict(base, b=b[t], c=c[t]), 80
+        orc = oracle.make_oracle(p)
+        orc.iterate(its)
+        st = orc.state()
+        sol = sh.solution(t)
+        for k, o in (("x", st.x), ("z", st.z), ("delta", st.delta), ("lam", st.lam)):
+            assert rel_err(sol[k], o) <= TOL["fp64"], (t, k)
+    X = torch.empty((3, base["n"]), device="cuda")
+    L = torch.empty((3, base["m"]), device="cuda")
+    sh.slots_device(slots, X.data_ptr(), L.data_ptr())
+    for q, t in enumerate(slots):
+        sol = sh.solution(int(t))
+        assert np.array_equal(X[q].cpu().numpy(), sol["x"].astype(np.float32))
+        assert np.array_equal(L[q].cpu().numpy(), sol["lam"].astype(np.float32))
+    for bad in ([1, 1], [40], [-1]):
+        with pytest.raises(mfs.MfsError):
+            sh.load_slots(np.array(bad, np.int32), bd.data_ptr(), cd.data_ptr())

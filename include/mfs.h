@@ -316,7 +316,10 @@ mfs_status mfs_mlp_forward(mfs_mlp* net, int32_t batch, const float* x, float* y
 mfs_status mfs_mlp_backward(mfs_mlp* net, int32_t batch, const float* x, const float* target, double* loss);
 /* Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the gradients of the last mfs_mlp_backward. */
 mfs_status mfs_mlp_adam_step(mfs_mlp* net, float lr);
-/* mfs_mlp_backward followed by mfs_mlp_adam_step. */
+/* The update of mfs_mlp_backward followed by mfs_mlp_adam_step, with the output layer fused into
+   the tensor-core GEMM epilogues: the forward GEMM of layer 3 produces the loss gradient instead of
+   the output, and the weight-gradient GEMM of layer 3 applies Adam in place (so mfs_mlp_get_grads
+   does not report layer 3 after this call). */
 mfs_status mfs_mlp_train_step(mfs_mlp* net, int32_t batch, const float* x, const float* target, float lr,
                               double* loss);
 /* Host copies of layer l (0..2): weights [out][in] and bias; NULL skips. */

@@ -1,12 +1,12 @@
 // mfs_gemm.cuh -- dense BF16 GEMM on the 5th-generation tensor cores (tcgen05, sm_103a):
 //   C[M x N] (+)= A[M x K] * B[N x K]^T      A, B row-major BF16 (both K-major), FP32 accumulate.
 //
-// One CTA computes one 128 x 128 tile of C (or a K-slice of it, for split-K). Four warps:
+// One CTA computes one 128 x 128 tile of C (or a K-slice of it, for split-K). Eight warps:
 //   warp 0, one lane: TMA producer, 2-D tiled loads of 128 x 64 BF16 boxes of A and B into a
 //                     STAGES-deep ring of shared-memory stages (128-byte swizzle);
 //   warp 1, one lane: issues tcgen05.mma (M = 128, N = 128, K = 16 per instruction) from shared
 //                     memory descriptors into a 128 x 128 FP32 accumulator in tensor memory;
-//   all four warps:   epilogue, tcgen05.ld of their 32 accumulator lanes (rows), a transpose through
+//   all eight warps:  epilogue, tcgen05.ld of their 32 accumulator lanes (rows) and 64 columns, a transpose through
 //                     shared memory, bias, ReLU, conversion and row-contiguous stores.
 // Barriers: full[s] (TMA transaction bytes), empty[s] (tcgen05.commit after the MMAs that read
 // stage s), acc (commit after the last MMA). Every wait is bounded: a wait that runs out sets the
@@ -27,7 +27,7 @@ constexpr int BN = 128;
 constexpr int BK = 64;       // one 128-byte swizzle row of BF16
 constexpr int UK = 16;       // K of one tcgen05.mma kind::f16
 constexpr int STAGES = 3;       // 3 stages (97 KB) let two CTAs share an SM: one's epilogue overlaps the other's loads
-constexpr int NTHREADS = 128;
+constexpr int NTHREADS = 256;  // eight warps: warp w reads TMEM lanes 32 (w % 4) .. +31, columns of half w / 4
 constexpr int TILE_A = BM * BK * 2;  // bytes
 constexpr int TILE_B = BN * BK * 2;
 constexpr int STAGE_BYTES = TILE_A + TILE_B;
@@ -146,8 +146,26 @@ struct GemmArgs {
     uint32_t spin;  // poll limit of every wait (SPIN in normal use)
     int m_fast;     // blockIdx.x runs over row tiles (B tiles shared by neighbouring CTAs), else column tiles
     int no_loads;   // diagnostic: issue no loads, so the first wait of the MMA issuer runs out
+    // EPI_LOSS: y = acc + bias; r = y - (T[row][col] - mean[col]) / stdv[col] for col < dout (else 0);
+    // dY[row][col] (ld ldc, in C) and dYt[col][row] (ld ldt) receive bf16(scale r); per-CTA sums of r^2
+    // go to part[] (C never holds y).
+    const float* T;
+    int ldT, dout;
+    const float *mean, *stdv;
+    float scale;
+    __nv_bfloat16* dYt;
+    int ldt;
+    double* part;
+    // EPI_ADAM: g = acc is the gradient of W [row][col] (ld ldc); Adam updates W and its moments and
+    // refreshes the BF16 copies Wh [row][col] (ld ldc) and Wt [col][row] (ld ldt).
+    float *W, *mom, *vel;
+    __nv_bfloat16 *Wh, *Wt;
+    float lr, b1, b2, eps, c1, c2;
 };
 
+enum { EPI_STORE = 0, EPI_LOSS = 1, EPI_ADAM = 2 };
+
+template <int EPI>
 __global__ void __launch_bounds__(NTHREADS, 2)
     k_gemm_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const GemmArgs g) {
     extern __shared__ __align__(1024) unsigned char gsm_raw[];
@@ -227,35 +245,120 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     // Each 32 x 32 block goes through shared memory (the idle stage buffers; padded rows, no bank
     // conflicts) so that each store instruction writes 32 consecutive columns of one row.
     float* stg = reinterpret_cast<float*>(gsm) + warp * (32 * 33);
-    const int rbase = m0 + warp * 32;
+    const int quad = warp & 3, half = warp >> 2;  // TMEM lane quadrant (rows) and column half
+    const int rbase = m0 + quad * 32;
     const bool part = gridDim.z > 1;
+    double lsum = 0.0;  // EPI_LOSS: this thread's share of the squared residuals
     if (ok && nkb > 0 && !*s_fail) {
-        for (int c0 = 0; c0 < BN; c0 += 32) {
+        for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
             float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
             for (int i = 0; i < 32; ++i) stg[lane * 33 + i] = v[i];
             __syncwarp();
             const int col = n0 + c0 + lane;
-            if (col < g.N) {
-                const float bv = (!part && g.bias) ? g.bias[col] : 0.f;
-                const int rows = min(32, g.M - rbase);
-                for (int r = 0; r < rows; ++r) {
-                    const size_t row = (size_t)(rbase + r);
-                    float w = stg[r * 33 + lane];
-                    if (part) {
-                        reinterpret_cast<float*>(g.C)[((size_t)blockIdx.z * g.M + row) * g.ldc + col] = w;
-                    } else {
-                        w += bv;
-                        if (g.relu) w = w > 0.f ? w : 0.f;
-                        if (g.out_fp32)
-                            reinterpret_cast<float*>(g.C)[row * g.ldc + col] = w;
-                        else
-                            reinterpret_cast<__nv_bfloat16*>(g.C)[row * g.ldc + col] = __float2bfloat16_rn(w);
+            const int rows = min(32, g.M - rbase);
+            if (EPI == EPI_STORE) {
+                if (col < g.N) {
+                    const float bv = (!part && g.bias) ? g.bias[col] : 0.f;
+                    for (int r = 0; r < rows; ++r) {
+                        const size_t row = (size_t)(rbase + r);
+                        float w = stg[r * 33 + lane];
+                        if (part) {
+                            reinterpret_cast<float*>(g.C)[((size_t)blockIdx.z * g.M + row) * g.ldc + col] = w;
+                        } else {
+                            w += bv;
+                            if (g.relu) w = w > 0.f ? w : 0.f;
+                            if (g.out_fp32)
+                                reinterpret_cast<float*>(g.C)[row * g.ldc + col] = w;
+                            else
+                                reinterpret_cast<__nv_bfloat16*>(g.C)[row * g.ldc + col] = __float2bfloat16_rn(w);
+                        }
                     }
                 }
+            } else {
+                // EPI_LOSS / EPI_ADAM: lane = column, rows in turn; the BF16 result goes back to the
+                // staging block for the transposed store below
+                if (col < g.N) {
+                    // eight rows at a time: their loads are issued together, then used
+                    if (EPI == EPI_LOSS) {
+                        const bool real = col < g.dout;
+                        const float bv = g.bias ? g.bias[col] : 0.f;
+                        const float mc = real ? g.mean[col] : 0.f, sc = real ? g.stdv[col] : 1.f;
+                        for (int r0 = 0; r0 < rows; r0 += 8) {
+                            float tv[8];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                tv[u] = (real && r0 + u < rows) ? g.T[(size_t)(rbase + r0 + u) * g.ldT + col] : 0.f;
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                const int r = r0 + u;
+                                if (r < rows) {
+                                    const float y = stg[r * 33 + lane] + bv;
+                                    float res = 0.f;
+                                    if (real) res = y - (tv[u] - mc) / sc;
+                                    lsum += (double)res * (double)res;
+                                    const __nv_bfloat16 d = __float2bfloat16_rn(g.scale * res);
+                                    reinterpret_cast<__nv_bfloat16*>(g.C)[(size_t)(rbase + r) * g.ldc + col] = d;
+                                    stg[r * 33 + lane] = __bfloat162float(d);
+                                }
+                            }
+                        }
+                    } else {
+                        for (int r0 = 0; r0 < rows; r0 += 8) {
+                            float wv[8], mv[8], vv[8];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                if (r0 + u < rows) {
+                                    const size_t idx = (size_t)(rbase + r0 + u) * g.ldc + col;
+                                    wv[u] = g.W[idx];
+                                    mv[u] = g.mom[idx];
+                                    vv[u] = g.vel[idx];
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                const int r = r0 + u;
+                                if (r < rows) {
+                                    const size_t idx = (size_t)(rbase + r) * g.ldc + col;
+                                    const float gt = stg[r * 33 + lane];
+                                    const float mt = g.b1 * mv[u] + (1.f - g.b1) * gt;
+                                    const float vt = g.b2 * vv[u] + (1.f - g.b2) * gt * gt;
+                                    g.mom[idx] = mt;
+                                    g.vel[idx] = vt;
+                                    const float wn = wv[u] - g.lr * (mt / g.c1) / (sqrtf(vt / g.c2) + g.eps);
+                                    g.W[idx] = wn;
+                                    const __nv_bfloat16 h = __float2bfloat16_rn(wn);
+                                    g.Wh[idx] = h;
+                                    stg[r * 33 + lane] = __bfloat162float(h);
+                                }
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+                // transposed store: lane = row, columns in turn
+                const int row = rbase + lane;
+                __nv_bfloat16* dst = EPI == EPI_LOSS ? g.dYt : g.Wt;
+                if (row < g.M)
+                    for (int i = 0; i < 32; ++i) {
+                        const int cc = n0 + c0 + i;
+                        if (cc < g.N) dst[(size_t)cc * g.ldt + row] = __float2bfloat16_rn(stg[lane * 33 + i]);
+                    }
             }
             __syncwarp();
+        }
+    }
+    if (EPI == EPI_LOSS) {  // fixed-order sum of the CTA's squared residuals
+        double* red = reinterpret_cast<double*>(gsm + (NTHREADS / 32) * (32 * 33) * sizeof(float));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
+        if (lane == 0) red[warp] = lsum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < NTHREADS / 32; ++w) t += red[w];
+            g.part[blockIdx.y * gridDim.x + blockIdx.x] = t;
         }
     }
     tc_fence_before();

@@ -76,21 +76,31 @@ __global__ void k_splitk_reduce(const float* __restrict__ part, int splits, int 
 }
 
 // C (row-major M x N) = A (M x K) * B (N x K)^T, BF16 in, FP32 accumulate on the tensor cores.
+template <int EPI>
+bool gemm_attr() {
+    static bool done = false;
+    if (!done)
+        done = cudaFuncSetAttribute(k_gemm_bf16<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) ==
+               cudaSuccess;
+    return done;
+}
+
+// epi != EPI_STORE: the fused epilogue's fields are taken from *fused (splits must be 1).
 mfs_status gemm(int M, int N, int K, const bf16* A, const bf16* B, const float* bias, int relu, int out_fp32, void* C,
                 int splits, float* work, int* err, cudaStream_t st, std::string* why, uint32_t spin = SPIN,
-                int no_loads = 0) {
+                int no_loads = 0, int epi = EPI_STORE, const GemmArgs* fused = nullptr) {
     if (M <= 0 || N <= 0 || K <= 0) return MFS_OK;
     if (K % 8) {
         if (why) *why = "gemm: K must be a multiple of 8 (16-byte rows)";
         return MFS_ERR_INVALID;
     }
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess) {
-            if (why) *why = "gemm: shared memory attribute";
-            return MFS_ERR_CUDA;
-        }
-        attr = true;
+    if (!gemm_attr<EPI_STORE>() || !gemm_attr<EPI_LOSS>() || !gemm_attr<EPI_ADAM>()) {
+        if (why) *why = "gemm: shared memory attribute";
+        return MFS_ERR_CUDA;
+    }
+    if (epi != EPI_STORE && (!fused || splits != 1)) {
+        if (why) *why = "gemm: a fused epilogue needs its arguments and no split-K";
+        return MFS_ERR_INVALID;
     }
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, M, K) || !make_map(&mb, B, N, K)) {
@@ -105,7 +115,7 @@ mfs_status gemm(int M, int N, int K, const bf16* A, const bf16* B, const float* 
         if (why) *why = "gemm: split-K needs a workspace";
         return MFS_ERR_INVALID;
     }
-    GemmArgs g;
+    GemmArgs g = fused ? *fused : GemmArgs{};
     g.M = M;
     g.N = N;
     g.K = K;
@@ -122,7 +132,12 @@ mfs_status gemm(int M, int N, int K, const bf16* A, const bf16* B, const float* 
     g.m_fast = (long long)N > (long long)M ? 1 : 0;
     const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
     dim3 grid(g.m_fast ? mt : nt, g.m_fast ? nt : mt, splits);
-    k_gemm_bf16<<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, g);
+    if (epi == EPI_LOSS)
+        k_gemm_bf16<EPI_LOSS><<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, g);
+    else if (epi == EPI_ADAM)
+        k_gemm_bf16<EPI_ADAM><<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, g);
+    else
+        k_gemm_bf16<EPI_STORE><<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, g);
     if (splits > 1) {
         const long long total = (long long)M * N;
         const int blocks = (int)std::min<long long>((total + 255) / 256, 148 * 8);
@@ -366,6 +381,7 @@ struct mfs_mlp {
     bf16 *X = nullptr, *H1 = nullptr, *H2 = nullptr, *dY = nullptr, *dYt = nullptr, *H2t = nullptr, *H1t = nullptr,
          *Xt = nullptr, *dZ2 = nullptr, *dZ2t = nullptr, *dZ1 = nullptr, *dZ1t = nullptr;
     float *Y = nullptr, *dH = nullptr, *work = nullptr;
+    bool wt2_fresh = false;  // Wt[2] holds the transpose of the current Wh[2]
     double *loss_part = nullptr, *loss = nullptr;
     int* err = nullptr;
     size_t work_floats = 0;
@@ -547,7 +563,9 @@ mfs_status mfs_mlp_create(int32_t din, int32_t width, int32_t dout, int32_t max_
     MCHK(malloc_zero(s, &s->dZ1t, (size_t)B * width));
     s->work_floats = (size_t)64 * B * width;
     MCHK(malloc_zero(s, &s->work, s->work_floats));
-    MCHK(malloc_zero(s, &s->loss_part, std::max(148 * 8, max_batch)));
+    // partial loss sums: k_mse's blocks, or one per output tile of the fused loss epilogue
+    const size_t tiles = (size_t)((Dp + BN - 1) / BN) * ((max_batch + BM - 1) / BM);
+    MCHK(malloc_zero(s, &s->loss_part, std::max<size_t>(std::max(148 * 8, max_batch), tiles)));
     MCHK(malloc_zero(s, &s->loss, 1));
     MCHK(malloc_zero(s, &s->err, 1));
     e = cudaStreamSynchronize(s->stream);
@@ -644,6 +662,7 @@ mfs_status mfs_mlp_backward(mfs_mlp* s, int32_t batch, const float* x, const flo
     MTRY(run_gemm(s, D, W, B, s->dYt, s->H2t, nullptr, 0, 1, s->gW[2], 1));
     k_colsum<<<(D + 31) / 32, dim3(32, 8), 0, st>>>(s->dY, B, D, s->gb[2]);
     transpose(s->Wh[2], s->Wt[2], D, W, st);
+    s->wt2_fresh = true;
     MTRY(run_gemm(s, B, W, D, s->dY, s->Wt[2], nullptr, 0, 1, s->dH, splits_for(s, B, W, D)));
     k_relu_bwd<<<grid1((long long)B * W), 256, 0, st>>>(s->dH, s->H2, s->dZ2, (long long)B * W);
     // layer 2
@@ -678,13 +697,97 @@ mfs_status mfs_mlp_adam_step(mfs_mlp* s, float lr) {
         k_adam<<<grid1(cb), 256, 0, s->stream>>>(s->b[l], s->gb[l], s->mb[l], s->vb[l], nullptr, cb, lr, s->beta1,
                                                  s->beta2, s->eps, c1, c2);
     }
+    s->wt2_fresh = false;
     if (cudaGetLastError() != cudaSuccess) return mfail(s, MFS_ERR_CUDA, "adam launch");
     return check_err(s);
 }
 
+// One training step with the output layer fused into two GEMM epilogues: the forward GEMM of layer 3
+// writes the loss gradient dY (and its transpose) instead of Y, and the weight-gradient GEMM of
+// layer 3 applies Adam to W3 directly (its gradient is never stored). The other steps are those of
+// mfs_mlp_backward followed by mfs_mlp_adam_step, in an order where dH2 still sees the old W3.
 mfs_status mfs_mlp_train_step(mfs_mlp* s, int32_t batch, const float* x, const float* target, float lr, double* loss) {
-    MTRY(mfs_mlp_backward(s, batch, x, target, loss));
-    return mfs_mlp_adam_step(s, lr);
+    if (!s || !x || !target || batch < 1 || batch > s->maxb || batch % 8 || !(lr > 0.f)) return MFS_ERR_INVALID;
+    cudaSetDevice(s->device);
+    const int B = batch, W = s->width, D = s->doutp, I = s->din;
+    cudaStream_t st = s->stream;
+    ++s->step;
+    const float c1 = 1.f - std::pow(s->beta1, (float)s->step), c2 = 1.f - std::pow(s->beta2, (float)s->step);
+    if (!s->wt2_fresh) {
+        transpose(s->Wh[2], s->Wt[2], D, W, st);
+        s->wt2_fresh = true;
+    }
+    k_to_bf16<<<grid1((long long)B * I), 256, 0, st>>>(x, s->X, (long long)B * I);
+    MTRY(run_gemm(s, B, W, I, s->X, s->Wh[0], s->b[0], 1, 0, s->H1, 1));
+    MTRY(run_gemm(s, B, W, W, s->H1, s->Wh[1], s->b[1], 1, 0, s->H2, splits_for(s, B, W, W)));
+    // layer 3 forward + loss: dY, dY^T and the partial sums of the squared residuals
+    GemmArgs fl{};
+    fl.T = target;
+    fl.ldT = s->dout;
+    fl.dout = s->dout;
+    fl.mean = s->mean;
+    fl.stdv = s->stdv;
+    fl.scale = 2.0f / ((float)B * (float)s->dout);
+    fl.dYt = s->dYt;
+    fl.ldt = B;
+    fl.part = s->loss_part;
+    {
+        std::string why;
+        mfs_status q = gemm(B, D, W, s->H2, s->Wh[2], s->b[2], 0, 0, s->dY, 1, s->work, s->err, st, &why, SPIN, 0,
+                            EPI_LOSS, &fl);
+        if (q != MFS_OK) return mfail(s, q, why);
+    }
+    const int tiles = ((D + BN - 1) / BN) * ((B + BM - 1) / BM);
+    k_sum_parts<<<1, 256, 0, st>>>(s->loss_part, tiles, 1.0 / ((double)B * s->dout), s->loss);
+    k_colsum<<<(D + 31) / 32, dim3(32, 8), 0, st>>>(s->dY, B, D, s->gb[2]);
+    // dH2 = dY W3 (old W3), then layers 2 and 1 as in mfs_mlp_backward
+    MTRY(run_gemm(s, B, W, D, s->dY, s->Wt[2], nullptr, 0, 1, s->dH, splits_for(s, B, W, D)));
+    k_relu_bwd<<<grid1((long long)B * W), 256, 0, st>>>(s->dH, s->H2, s->dZ2, (long long)B * W);
+    transpose(s->dZ2, s->dZ2t, B, W, st);
+    transpose(s->H1, s->H1t, B, W, st);
+    MTRY(run_gemm(s, W, W, B, s->dZ2t, s->H1t, nullptr, 0, 1, s->gW[1], 1));
+    k_colsum<<<(W + 31) / 32, dim3(32, 8), 0, st>>>(s->dZ2, B, W, s->gb[1]);
+    transpose(s->Wh[1], s->Wt[1], W, W, st);
+    MTRY(run_gemm(s, B, W, W, s->dZ2, s->Wt[1], nullptr, 0, 1, s->dH, splits_for(s, B, W, W)));
+    k_relu_bwd<<<grid1((long long)B * W), 256, 0, st>>>(s->dH, s->H1, s->dZ1, (long long)B * W);
+    transpose(s->dZ1, s->dZ1t, B, W, st);
+    transpose(s->X, s->Xt, B, I, st);
+    MTRY(run_gemm(s, W, I, B, s->dZ1t, s->Xt, nullptr, 0, 1, s->gW[0], 1));
+    k_colsum<<<(W + 31) / 32, dim3(32, 8), 0, st>>>(s->dZ1, B, W, s->gb[0]);
+    // layer 3 weight gradient dY^T H2 with Adam in the epilogue (W3, moments, Wh3, Wt3)
+    transpose(s->H2, s->H2t, B, W, st);
+    GemmArgs fa{};
+    fa.W = s->W[2];
+    fa.mom = s->mW[2];
+    fa.vel = s->vW[2];
+    fa.Wh = s->Wh[2];
+    fa.Wt = s->Wt[2];
+    fa.ldt = D;
+    fa.lr = lr;
+    fa.b1 = s->beta1;
+    fa.b2 = s->beta2;
+    fa.eps = s->eps;
+    fa.c1 = c1;
+    fa.c2 = c2;
+    {
+        std::string why;
+        mfs_status q = gemm(D, W, B, s->dYt, s->H2t, nullptr, 0, 1, nullptr, 1, s->work, s->err, st, &why, SPIN, 0,
+                            EPI_ADAM, &fa);
+        if (q != MFS_OK) return mfail(s, q, why);
+    }
+    // Adam on layers 1 and 2 and on all biases
+    for (int l = 0; l < 3; ++l) {
+        const long long cw = (long long)layer_in(s, l) * layer_out(s, l), cb = layer_out(s, l);
+        if (l < 2)
+            k_adam<<<grid1(cw), 256, 0, st>>>(s->W[l], s->gW[l], s->mW[l], s->vW[l], s->Wh[l], cw, lr, s->beta1,
+                                              s->beta2, s->eps, c1, c2);
+        k_adam<<<grid1(cb), 256, 0, st>>>(s->b[l], s->gb[l], s->mb[l], s->vb[l], nullptr, cb, lr, s->beta1, s->beta2,
+                                          s->eps, c1, c2);
+    }
+    if (cudaGetLastError() != cudaSuccess) return mfail(s, MFS_ERR_CUDA, "mlp train step launch");
+    if (loss && cudaMemcpyAsync(loss, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return mfail(s, MFS_ERR_CUDA, "loss copy");
+    return check_err(s);
 }
 
 // Host copies of layer l's FP32 master weights [out][in] and bias (either may be NULL); set copies
@@ -703,6 +806,7 @@ mfs_status mfs_mlp_set_params(mfs_mlp* s, int32_t l, const float* W, const float
     if (W) {
         if (cudaMemcpy(s->W[l], W, cw * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return MFS_ERR_CUDA;
         k_to_bf16<<<grid1(cw), 256, 0, s->stream>>>(s->W[l], s->Wh[l], (long long)cw);
+        if (l == 2) s->wt2_fresh = false;
     }
     if (b && cudaMemcpy(s->b[l], b, cb * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return MFS_ERR_CUDA;
     return cudaStreamSynchronize(s->stream) == cudaSuccess ? MFS_OK : MFS_ERR_CUDA;

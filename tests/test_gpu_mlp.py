@@ -107,6 +107,36 @@ def test_mlp_training_reduces_the_loss():
     assert last < 0.2 * first, (first, last)
 
 
+@pytest.mark.parametrize("din,width,dout,B", [(32, 128, 300, 64), (32, 512, 1000, 256)])
+def test_fused_train_step_equals_backward_then_adam(din, width, dout, B):
+    """train_step computes the output layer inside the GEMM epilogues (loss gradient in the forward
+    GEMM, Adam in the weight-gradient GEMM); it must give the same parameters and losses as the
+    separate mfs_mlp_backward + mfs_mlp_adam_step path, step after step."""
+    rng = np.random.default_rng(11)
+    X = rng.standard_normal((B, din)).astype(np.float32)
+    T = (rng.standard_normal((B, dout)) * 3 + 1).astype(np.float32)
+    mean, std = T.mean(0), T.std(0) + 0.1
+    Xd, Td = torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev)
+    fused, split = mfs.MLP(din, width, dout, B, seed=2), mfs.MLP(din, width, dout, B, seed=2)
+    for net in (fused, split):
+        net.set_output_scaling(mean, std)
+    for step in range(4):
+        lf = fused.train_step(B, Xd.data_ptr(), Td.data_ptr(), 1e-3)
+        ls = split.backward(B, Xd.data_ptr(), Td.data_ptr())
+        split.adam_step(1e-3)
+        assert abs(lf - ls) <= 1e-6 * ls, (step, lf, ls)
+    for l, ((Wf, bf), (Ws, bs)) in enumerate(zip(fused.params(), split.params())):
+        assert rel(Wf, Ws.astype(np.float64)) <= 1e-4, (l, rel(Wf, Ws.astype(np.float64)))
+        assert rel(bf, bs.astype(np.float64)) <= 1e-4, l  # rounding differences, amplified by Adam
+    # both continue identically from there (the transposed BF16 copy of W3 kept by the fused path)
+    Yf = torch.empty((B, dout), device=dev)
+    Ys = torch.empty((B, dout), device=dev)
+    fused.forward(B, Xd.data_ptr(), Yf.data_ptr())
+    split.forward(B, Xd.data_ptr(), Ys.data_ptr())
+    torch.cuda.synchronize()
+    assert rel(Yf.cpu().numpy(), Ys.cpu().numpy().astype(np.float64)) <= 1e-4
+
+
 @pytest.mark.parametrize("count,dout", [(1, 9), (700, 133), (20_000, 40)])
 def test_fit_output_scaling_matches_fp64_statistics(count, dout):
     g = np.random.default_rng(count + dout)

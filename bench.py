@@ -83,8 +83,8 @@ def load_peaks_raw():
     if os.path.exists(path):
         with open(path) as f:
             pk = json.load(f)
-        return {"bf16_tflops": float(pk.get("bf16_tflops", 1800.0))}
-    return {"bf16_tflops": 1800.0}
+        return {"bf16_tflops": float(pk.get("bf16_tflops", 1800.0)), "hbm_gbs": float(pk.get("hbm_gbs", 6400.0))}
+    return {"bf16_tflops": 1800.0, "hbm_gbs": 6400.0}
 
 
 class ClockSampler:
@@ -356,12 +356,19 @@ def mlp_workload(stream, peaks, batch=256, steps=20):
     fwd_flop = 2.0 * batch * (din * width + width * width + width * dout)
     peak = peaks.get("bf16_tflops")
     tf_train = 3 * fwd_flop / (train_ms * 1e-3) / 1e12
+    # bytes a training step must move (output layer dominates): W3 in BF16 for the forward and the
+    # input-gradient GEMMs, its FP32 value and Adam moments read and written, its BF16 copies
+    # written (row- and column-major), targets read, loss gradient written and read
+    dw = dout * width
+    step_bytes = 2 * dw * 2 + 24 * dw + 2 * dw * 2 + 4 * batch * dout + 2 * batch * dout * 2
     return {"workload": f"MLP {din}-{width}-{width}-{dout}, batch {batch}",
             "train_step_ms": round(train_ms, 4), "forward_ms": round(fwd_ms, 4),
             "train_tflops": round(tf_train, 1), "forward_tflops": round(fwd_flop / (fwd_ms * 1e-3) / 1e12, 1),
             "bf16_peak_tflops": peak, "train_frac_of_measured_peak": round(tf_train / peak, 4) if peak else None,
+            "train_step_bytes": step_bytes, "train_gbs": round(step_bytes / (train_ms * 1e-3) / 1e9, 1),
+            "train_frac_of_measured_hbm": round(step_bytes / (train_ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6485.5), 4),
             "note": "train step = forward, loss, backward GEMMs, transposes, Adam on 36M FP32 parameters, "
-                    "and a host read of the loss"}
+                    "and a host read of the loss; the step is bound by HBM (K <= 512), not by the tensor cores"}
 
 
 def run_reference(args, rank, world):

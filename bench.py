@@ -49,7 +49,7 @@ def parse():
                     help="learned warm-start experiment with TRAIN training solves (0 skips it; 50000 is the "
                          "full experiment, about 15 minutes)")
     ap.add_argument("--warm-start-test", type=int, default=128)
-    ap.add_argument("--section", default="all", choices=["all", "small", "socp", "batch", "shared", "mlp"],
+    ap.add_argument("--section", default="all", choices=["all", "small", "socp", "paper", "batch", "shared", "mlp"],
                     help="run only one extra workload and print its line (for profiling)")
     ap.add_argument("--tts-iters", type=int, default=300000,
                     help="also solve to 1e-6 KKT from the cold start with at most this many iterations (0: skip)")
@@ -267,6 +267,34 @@ def socp_workload(stream, seed, iters=250):
             "kernel_us": {k.replace("_ms", ""): round(v * 1e3, 2) for k, v in t.items()}}
 
 
+def paper_family_workload(stream, seed, cap=50_000):
+    """Extra workload: the paper's own random family (Sec. V) at its largest size, 1e7 nonzeros:
+    LP at 1 % and 0.1 % density and the (K_4)^{n/4} SOCP at 0.1 %; per-iteration time and the
+    iterations and seconds to relative KKT 1e-3 (the paper's SCS tolerance) and 1e-6."""
+    import torch
+    from paper_2203_05027_b300 import instances as I, mfs
+    out = []
+    for m, n, dens, cone in ((10_000, 100_000, 0.01, "lp"), (30_000, 333_332, 0.001, "lp"),
+                             (30_000, 333_332, 0.001, "soc4")):
+        prob = I.paper_instance(m, n, dens, cone, seed=seed)
+        s = mfs.Solver(prob, precision="fp32", polish_iters=0, check_every=100, stream=stream.cuda_stream)
+        o = s.info()["o"]
+        t = s.time_kernels(50)
+        rec = {"cone": cone, "m": m, "n": n, "density": dens, "o": o,
+               "us_per_iteration": round(t["iter_ms"] * 1e3, 2)}
+        s.close()
+        for tol in (1e-3, 1e-6):
+            s = mfs.Solver(prob, precision="fp32", polish_iters=0, check_every=100, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, its = s.solve(tol, cap)
+            torch.cuda.synchronize()
+            rec[f"to_{tol:g}"] = {"status": st, "iterations": its, "seconds": round(time.perf_counter() - t0, 3)}
+            s.close()
+        out.append(rec)
+    return {"workload": "paper's random family, 1e7 nonzeros, FP32", "instances": out}
+
+
 def small_workload(stream, seed, iters=2000):
     """Extra workload: the 200 x 500 LP (5 nonzeros per column), 2000 FP64 iterations, through the
     single-instance path (kernels per iteration under a CUDA graph) and as a batch of one (one CTA,
@@ -414,7 +442,7 @@ def main():
     if args.section != "all":
         stream = torch.cuda.current_stream()
         fn = {"small": lambda: small_workload(stream, rank), "batch": lambda: batch_workload(stream, rank),
-              "socp": lambda: socp_workload(stream, rank), "shared": lambda: shared_workload(stream, rank),
+              "socp": lambda: socp_workload(stream, rank), "paper": lambda: paper_family_workload(stream, rank), "shared": lambda: shared_workload(stream, rank),
               "mlp": lambda: mlp_workload(stream, load_peaks_raw())}[args.section]
         if rank == 0:
             print(json.dumps({"section": args.section, **fn()}), flush=True)
@@ -477,6 +505,7 @@ def main():
         extra["batch_lps"] = batch_workload(stream, rank)
         extra["small_lp"] = small_workload(stream, rank)
         extra["socp"] = socp_workload(stream, rank)
+        extra["paper_family"] = paper_family_workload(stream, rank)
         extra["shared_param_lp"] = shared_workload(stream, rank)
         extra["mlp"] = mlp_workload(stream, load_peaks_raw())
     if args.warm_start and not args.no_batch:

@@ -114,3 +114,24 @@ def test_small_lp_in_one_cta_matches_oracle():
     its, sts = bt.solve(1e-5, 200_000)
     r = bt.residuals()[0]
     assert sts[0] == mfs.MFS_OK and r["kkt"] <= 1e-5
+
+
+def test_full_batch_sampled_instances_match_oracle():
+    """The 4096-LP benchmark batch (m log-uniform on [50, 5000]) in the autotuned launch the bench
+    times: the smallest, the largest and two more instances against their own oracle runs."""
+    probs = I.batch_lps(4096, seed=0)
+    bt = mfs.Batch(probs, precision="fp32", check_every=50)
+    bt.tune(5)
+    bt.iterate(40)
+    ms = np.array([p["m"] for p in probs])
+    picks = {int(ms.argmin()), int(ms.argmax()), 1234, 4095}
+    for t in sorted(picks):
+        p = probs[t]
+        orc = oracle.make_oracle(p, dtype=np.float32)
+        sol = bt.solution(t)
+        orc_iters = bt.residuals()[t]["iter"]  # the tuner's launches advanced the batch too
+        orc.iterate(orc_iters)
+        st = orc.state()
+        errs = {k: rel_err(sol[k2], v) for k, k2, v in
+                (("x", "x", st.x), ("z", "z", st.z), ("delta", "delta", st.delta), ("lam", "lam", st.lam))}
+        assert max(errs.values()) <= TOL["fp32"], (t, orc_iters, errs)

@@ -148,3 +148,22 @@ def test_slots_enter_and_leave_while_others_iterate():
     for bad in ([1, 1], [40], [-1]):
         with pytest.raises(mfs.MfsError):
             sh.load_slots(np.array(bad, np.int32), bd.data_ptr(), cd.data_ptr())
+
+
+def test_full_family_sampled_members_match_oracle():
+    """The benchmark's shared-A workload (A with m = 20,000, n = 50,000, 8 nonzeros per column;
+    1024 members), in the launch configuration the bench times: three members against the oracle."""
+    from paper_2203_05027_b300 import warmstart as W
+    fam = W.family(0)
+    base = fam["base"]
+    b, c = W.data_of(fam, W.thetas(1024, 1))
+    sh = mfs.Shared(base, 1024, precision="fp32", check_every=25)
+    sh.set_data(b, c)
+    sh.iterate(30)
+    for t in (0, 517, 1023):
+        orc = oracle.make_oracle(dict(base, b=b[t], c=c[t]), dtype=np.float32)
+        orc.iterate(30)
+        st = orc.state()
+        sol = sh.solution(t)
+        for k, o in (("x", st.x), ("z", st.z), ("delta", st.delta), ("lam", st.lam)):
+            assert rel_err(sol[k], o) <= TOL["fp32"], (t, k, rel_err(sol[k], o))

@@ -31,7 +31,7 @@ def _rank(rank, world, port, out):
 
 def test_two_gloo_replicas_take_the_slowest_time_and_solve_different_instances():
     world, port = 2, _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)

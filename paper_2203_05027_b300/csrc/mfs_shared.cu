@@ -104,7 +104,11 @@ __device__ __forceinline__ Pack<T, V> ldg_pack(const T* p) {
 
 // acc[u] = sum over the nonzeros k of a line (column or row) of val[k] * g[idx[k] * Bp + s0 + u]:
 // the warp loads 32 indices and values at a time with one coalesced load each, broadcasts them by
-// shuffles and keeps four gathers in flight; the sum runs in the nonzeros' order.
+// shuffles and keeps GIF gathers in flight; the sum runs in the nonzeros' order.
+#ifndef MFS_SHARED_GIF
+#define MFS_SHARED_GIF 4
+#endif
+constexpr int GIF = MFS_SHARED_GIF;
 template <typename T, int V>
 __device__ __forceinline__ void line_dot(const int* __restrict__ idx, const T* __restrict__ val, int k0, int k1,
                                          const T* __restrict__ g, int Bp, int s0, int lane, T (&acc)[V]) {
@@ -119,17 +123,17 @@ __device__ __forceinline__ void line_dot(const int* __restrict__ idx, const T* _
             mv = __ldg(val + base + lane);
         }
         int t = 0;
-        for (; t + 4 <= cnt; t += 4) {
-            Pack<T, V> q[4];
-            T w[4];
+        for (; t + GIF <= cnt; t += GIF) {
+            Pack<T, V> q[GIF];
+            T w[GIF];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
+            for (int r = 0; r < GIF; ++r) {
                 const int i = __shfl_sync(FULL, mi, t + r);
                 w[r] = __shfl_sync(FULL, mv, t + r);
                 q[r] = ldg_pack<T, V>(g + (size_t)i * Bp + s0);
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < GIF; ++r)
 #pragma unroll
                 for (int u = 0; u < V; ++u) acc[u] += w[r] * q[r].e[u];
         }

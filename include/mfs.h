@@ -47,7 +47,8 @@ typedef enum {
     MFS_ERR_CUDA = 3,    /* a CUDA call failed (no device, launch failure, ...) */
     MFS_ERR_OOM = 4,     /* device or host allocation failed */
     MFS_ERR_NUMERIC = 5, /* NaN or Inf in the iterate's residuals */
-    MFS_ERR_TIMEOUT = 6  /* a bounded on-device wait gave up; the results of that call are void */
+    MFS_ERR_TIMEOUT = 6, /* a bounded on-device wait gave up; the results of that call are void */
+    MFS_INFEASIBLE = 7   /* mfs_solve: the dual iterates give a certificate that Ax = b, x in K has no solution */
 } mfs_status;
 
 enum { MFS_CONE_NONNEG = 0, MFS_CONE_SOC = 1 };
@@ -160,6 +161,11 @@ mfs_status mfs_iterate(mfs_solver* s, int64_t k);
  * receives the iterations run by this call. In FP32_MIXED mode the iterate switches to FP64
  * (and stays there) for the final polish_iters iterations, or as soon as the FP32 residual has
  * not improved over 40 consecutive checks; the tolerance is always judged on FP64 reductions.
+ * Primal infeasibility: when Ax = b, x in K has no solution, lambda grows along a direction d
+ * with A^T d in K* (= K) and b^T d < 0 (Farkas). At every check the change d of lambda since the
+ * previous check is tested: dist(A^T d, K) <= 0.1 |b^T d|, b^T d < -1e-3 ||b|| ||d||, and the
+ * primal residual not 1 % lower than three checks before; three consecutive passes return
+ * MFS_INFEASIBLE (the iterate is kept). Detecting an unbounded primal is not implemented.
  */
 mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters_out);
 

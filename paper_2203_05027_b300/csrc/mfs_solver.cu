@@ -17,6 +17,7 @@
 #include "../../include/mfs.h"
 #include "mfs_alloc.h"
 #include "mfs_kernels.cuh"
+#include "mfs_infeas.cuh"
 #include "mfs_literal.cuh"
 
 using namespace mfs;
@@ -93,6 +94,9 @@ struct mfs_solver {
     bool have32 = false, have64 = false;
     // literal start (Algorithm 1 with o-length y and gamma) pending for the next lit_pending iterations
     int lit_pending = 0;
+    // primal infeasibility test of mfs_solve: previous s = c + A^T lambda and lambda (FP64)
+    unsigned char* in_cone = nullptr;  // n: 1 for coordinates of Lorentz cones
+    double *inf_s_prev = nullptr, *inf_lam_prev = nullptr, *inf_part = nullptr;
     void *lit_y = nullptr, *lit_g = nullptr, *lit_kval = nullptr, *lit_w = nullptr, *lit_row = nullptr;
     int *lit_krow = nullptr, *lit_kcol = nullptr, *lit_perm = nullptr, *lit_rp = nullptr;
     double* lit_zarg = nullptr;
@@ -828,6 +832,41 @@ mfs_status literal_run(mfs_solver* s, State<T>& st, int64_t k, int64_t* done) {
     return MFS_OK;
 }
 
+// ------------------------------------------------------------------ primal infeasibility test
+constexpr int INF_BLOCKS = 296;
+
+// Reductions of d = lambda - lambda_prev and t = s - s_prev (s_buf must hold c + A^T lambda):
+// out = {dist(t, K)^2, ||d||^2}; then remembers s and lambda.
+template <typename T>
+mfs_status infeas_reduce(mfs_solver* s, State<T>& st, bool have_prev, double* out) {
+    const int n = s->n, m = s->m, nsoc = s->nsoc;
+    if (!s->inf_s_prev) {
+        TRY(dalloc(s, &s->inf_s_prev, (size_t)n));
+        TRY(dalloc(s, &s->inf_lam_prev, (size_t)m));
+        TRY(dalloc(s, &s->inf_part, (size_t)2 * INF_BLOCKS + std::max(nsoc, 1)));
+    }
+    out[0] = out[1] = 0.0;
+    if (have_prev) {
+        mfs::infeas::k_infeas<T><<<INF_BLOCKS, 256, 0, s->stream>>>(s->s_buf, s->inf_s_prev, st.lam, s->inf_lam_prev,
+                                                                    s->in_cone, n, m, s->inf_part);
+        if (nsoc)
+            mfs::infeas::k_infeas_cones<<<(nsoc + 255) / 256, 256, 0, s->stream>>>(
+                s->s_buf, s->inf_s_prev, s->soc_start, s->soc_size, nsoc, s->inf_part + 2 * INF_BLOCKS);
+        std::vector<double> h(2 * INF_BLOCKS + nsoc);
+        CUDA_TRY(s, cudaMemcpyAsync(h.data(), s->inf_part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+        for (int b = 0; b < INF_BLOCKS; ++b) {
+            out[0] += h[2 * b];
+            out[1] += h[2 * b + 1];
+        }
+        for (int q = 0; q < nsoc; ++q) out[0] += h[2 * INF_BLOCKS + q];
+    }
+    if (n) CUDA_TRY(s, cudaMemcpyAsync(s->inf_s_prev, s->s_buf, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    if (m) convert(s->inf_lam_prev, st.lam, m, s->stream);
+    CUDA_TRY(s, cudaGetLastError());
+    return MFS_OK;
+}
+
 // ====================================================================================== C ABI
 namespace mfs {
 namespace {
@@ -975,6 +1014,12 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
     CHK(upload(s, &s->cq_hi, P.cq_hi.data(), P.cq_hi.size()));
     CHK(upload(s, &s->soc_start, P.soc_start.data(), P.soc_start.size()));
     CHK(upload(s, &s->soc_size, P.soc_size.data(), P.soc_size.size()));
+    {
+        std::vector<unsigned char> inc(n, 0);
+        for (size_t q = 0; q < P.soc_start.size(); ++q)
+            for (int t = 0; t < P.soc_size[q]; ++t) inc[P.soc_start[q] + t] = 1;
+        CHK(upload(s, &s->in_cone, inc.data(), inc.size()));
+    }
     CHK(upload(s, &s->soc_big, P.soc_big.data(), P.soc_big.size()));
     CHK(upload(s, &s->big_list, P.big_list.data(), P.big_list.size()));
     {
@@ -1126,11 +1171,38 @@ mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters
     int since_best = 0;
     mfs_residuals_t r;
     mfs_status result = MFS_MAX_ITER;
+    // primal infeasibility test state: previous b^T lambda and precision, consecutive passes and the
+    // primal residuals of the last checks
+    bool have_prev = false;
+    int prev_prec = -1, passes = 0;
+    double prev_blam = 0.0;
+    std::vector<double> rp_hist;
     while (true) {
-        TRY(mfs_residuals(s, &r));
+        TRY(s->precision == MFS_FP64 ? residuals_t(s, s->s64, &r, true) : residuals_t(s, s->s32, &r, true));
         if (!std::isfinite(r.kkt)) {
             result = fail(s, MFS_ERR_NUMERIC, "NaN or Inf in the residuals");
             break;
+        }
+        {
+            double red[2];
+            const bool same = have_prev && prev_prec == s->precision;
+            TRY(s->precision == MFS_FP64 ? infeas_reduce(s, s->s64, same, red) : infeas_reduce(s, s->s32, same, red));
+            const double blam = -r.dobj;  // b^T lambda
+            rp_hist.push_back(r.r_prim);
+            if (same) {
+                const double bd = blam - prev_blam, dist = std::sqrt(red[0]), nd = std::sqrt(red[1]);
+                const size_t h = rp_hist.size();
+                const bool stalled = h >= 4 && rp_hist[h - 1] >= 0.99 * rp_hist[h - 4];
+                const bool pass = bd < -1e-3 * r.nrm_b * nd && dist <= 0.1 * -bd && stalled;
+                passes = pass ? passes + 1 : 0;
+                if (passes >= 3 && r.kkt > tol) {
+                    result = fail(s, MFS_INFEASIBLE, "primal infeasibility certificate (Farkas) found");
+                    break;
+                }
+            }
+            have_prev = true;
+            prev_prec = s->precision;
+            prev_blam = blam;
         }
         const bool fp32 = s->precision == MFS_FP32_MIXED;
         if (r.kkt <= tol) {

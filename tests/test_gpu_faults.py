@@ -72,3 +72,43 @@ def test_infeasible_instance_ends_alone_at_the_iteration_limit():
     r = bt.residuals()
     assert r[0]["kkt"] <= 1e-4 and r[2]["kkt"] <= 1e-4
     assert np.isfinite(r[1]["kkt"]) and r[1]["r_prim"] > 1e-2  # stays infeasible, no NaN
+
+
+def _infeasible_lp(seed):
+    p = I.small_lp(seed, m=60, n=150)
+    p["val"] = np.abs(p["val"]) + 0.1  # A > 0 and b < 0: no x >= 0 has Ax = b
+    p["b"] = -np.ones(60)
+    return p
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_solve_reports_primal_infeasibility(precision):
+    s = mfs.Solver(_infeasible_lp(1), precision=precision, check_every=50)
+    status, its = s.solve(1e-6, 200_000)
+    assert status == "INFEASIBLE" and its < 20_000, (status, its)
+    r = s.residuals()
+    assert np.isfinite(r["kkt"]) and r["r_prim"] > 1e-2
+
+
+def test_solve_reports_infeasible_socp():
+    # Lorentz cones, with positive entries only in the cones' head columns: every x in K has a
+    # nonnegative head, so A x >= 0 and b = -1 is out of reach
+    p = I.socp(2, n=400, m=100, nnz_per_row=6)
+    p["val"] = np.abs(p["val"]) + 0.1
+    heads = np.cumsum(np.r_[0, np.asarray(p["cones"])[:-1, 1]])
+    keep = np.isin(p["col"], heads)
+    for k in ("row", "col", "val"):
+        p[k] = p[k][keep]
+    p["b"] = -np.ones(p["m"])
+    s = mfs.Solver(p, precision="fp64", check_every=50)
+    status, its = s.solve(1e-6, 200_000)
+    assert status == "INFEASIBLE", (status, its)
+
+
+def test_feasible_solves_are_not_reported_infeasible():
+    # solvable problems, some of them slow to reach 1e-7: the test must never fire on them
+    for p in (I.small_lp(0), I.small_lp(3, m=60, n=150), I.socp(1, n=3000, m=1200), I.large_lp(2, m=20_000, n=50_000)):
+        for precision in ("fp64", "fp32"):
+            s = mfs.Solver(p, precision=precision, check_every=50, polish_iters=0)
+            status, its = s.solve(1e-7, 60_000)
+            assert status in ("OK", "MAX_ITER"), (p.get("name"), precision, status, its)

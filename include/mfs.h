@@ -48,7 +48,8 @@ typedef enum {
     MFS_ERR_OOM = 4,     /* device or host allocation failed */
     MFS_ERR_NUMERIC = 5, /* NaN or Inf in the iterate's residuals */
     MFS_ERR_TIMEOUT = 6, /* a bounded on-device wait gave up; the results of that call are void */
-    MFS_INFEASIBLE = 7   /* mfs_solve: the dual iterates give a certificate that Ax = b, x in K has no solution */
+    MFS_INFEASIBLE = 7,  /* mfs_solve: the dual iterates give a certificate that Ax = b, x in K has no solution */
+    MFS_UNBOUNDED = 8    /* mfs_solve: the primal iterates give a ray along which c^T x falls without end */
 } mfs_status;
 
 enum { MFS_CONE_NONNEG = 0, MFS_CONE_SOC = 1 };
@@ -165,7 +166,10 @@ mfs_status mfs_iterate(mfs_solver* s, int64_t k);
  * with A^T d in K* (= K) and b^T d < 0 (Farkas). At every check the change d of lambda since the
  * previous check is tested: dist(A^T d, K) <= 0.1 |b^T d|, b^T d < -1e-3 ||b|| ||d||, and the
  * primal residual not 1 % lower than three checks before; three consecutive passes return
- * MFS_INFEASIBLE (the iterate is kept). Detecting an unbounded primal is not implemented.
+ * MFS_INFEASIBLE (the iterate is kept). Unbounded primal: x then grows along a ray e with A e = 0,
+ * e in K and c^T e < 0; with e the change of x since the previous check, ||A e|| <= 0.1 |c^T e|,
+ * dist(e, K) <= 0.1 |c^T e|, c^T e < -1e-3 ||c|| ||e|| and a stalled dual residual, three
+ * consecutive passes return MFS_UNBOUNDED.
  */
 mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters_out);
 

@@ -471,6 +471,7 @@ struct ResidArgs {
     double* part_col;  // NFC x (column-residual grid)
     double* part_big;  // NFB x (big cones)
     double* s_buf;     // n: c + A^T lambda (FP64), written for big-cone columns (all if write_all_s)
+    double* r_buf;     // m: A x - b (FP64), written if write_all_s
     int write_all_s;
 };
 
@@ -522,6 +523,7 @@ __global__ void __launch_bounds__(NT) k_row_resid(const SweepArgs<T> a, const Re
         for (int k = 0; k < CPL; ++k) {
             if (rows[k] < 0) continue;
             const double bi = double(a.b[rows[k]]), res = ax[k] - bi;
+            if (r.write_all_s) r.r_buf[rows[k]] = res;
             f[R_RES2] += res * res;
             f[R_RESMAX] = fmax(f[R_RESMAX], fabs(res));
             f[R_AXMAX] = fmax(f[R_AXMAX], fabs(ax[k]));

@@ -88,6 +88,7 @@ struct mfs_solver {
     int *soc_start = nullptr, *soc_size = nullptr, *big_list = nullptr;
     unsigned char* soc_big = nullptr;
     double *part_row = nullptr, *part_col = nullptr, *part_big = nullptr, *s_buf = nullptr, *status = nullptr;
+    double* r_buf = nullptr;  // m: A x - b of the last residual evaluation with write_all_s
     double* h_status = nullptr;      // pinned
     State<float> s32;
     State<double> s64;
@@ -96,7 +97,8 @@ struct mfs_solver {
     int lit_pending = 0;
     // primal infeasibility test of mfs_solve: previous s = c + A^T lambda and lambda (FP64)
     unsigned char* in_cone = nullptr;  // n: 1 for coordinates of Lorentz cones
-    double *inf_s_prev = nullptr, *inf_lam_prev = nullptr, *inf_part = nullptr;
+    double *inf_s_prev = nullptr, *inf_lam_prev = nullptr, *inf_x_prev = nullptr, *inf_r_prev = nullptr,
+           *inf_part = nullptr;
     void *lit_y = nullptr, *lit_g = nullptr, *lit_kval = nullptr, *lit_w = nullptr, *lit_row = nullptr;
     int *lit_krow = nullptr, *lit_kcol = nullptr, *lit_perm = nullptr, *lit_rp = nullptr;
     double* lit_zarg = nullptr;
@@ -455,6 +457,7 @@ mfs_status residuals_t(mfs_solver* s, State<T>& st, mfs_residuals_t* out, bool w
     r.part_col = s->part_col;
     r.part_big = s->part_big;
     r.s_buf = s->s_buf;
+    r.r_buf = s->r_buf;
     r.write_all_s = write_all_s ? 1 : 0;
     const int gr = s->nrc ? s->g_rowres : 0, gc = s->ncc ? s->g_colres : 0;
     if (gr) k_row_resid<T><<<gr, NT, 0, s->stream>>>(a, r);
@@ -835,34 +838,46 @@ mfs_status literal_run(mfs_solver* s, State<T>& st, int64_t k, int64_t* done) {
 // ------------------------------------------------------------------ primal infeasibility test
 constexpr int INF_BLOCKS = 296;
 
-// Reductions of d = lambda - lambda_prev and t = s - s_prev (s_buf must hold c + A^T lambda):
-// out = {dist(t, K)^2, ||d||^2}; then remembers s and lambda.
+// Reductions for the two tests (s_buf and r_buf must hold c + A^T lambda and A x - b of the current
+// iterate): out = {dist(A^T d, K)^2, ||d||^2, dist(e, K)^2, ||e||^2, ||A e||^2} with d and e the
+// changes of lambda and x since the previous call; then remembers s, lambda, x and r.
 template <typename T>
 mfs_status infeas_reduce(mfs_solver* s, State<T>& st, bool have_prev, double* out) {
     const int n = s->n, m = s->m, nsoc = s->nsoc;
     if (!s->inf_s_prev) {
         TRY(dalloc(s, &s->inf_s_prev, (size_t)n));
         TRY(dalloc(s, &s->inf_lam_prev, (size_t)m));
-        TRY(dalloc(s, &s->inf_part, (size_t)2 * INF_BLOCKS + std::max(nsoc, 1)));
+        TRY(dalloc(s, &s->inf_x_prev, (size_t)n));
+        TRY(dalloc(s, &s->inf_r_prev, (size_t)m));
+        TRY(dalloc(s, &s->inf_part, (size_t)5 * INF_BLOCKS + 2 * std::max(nsoc, 1)));
     }
-    out[0] = out[1] = 0.0;
+    for (int q = 0; q < 5; ++q) out[q] = 0.0;
     if (have_prev) {
         mfs::infeas::k_infeas<T><<<INF_BLOCKS, 256, 0, s->stream>>>(s->s_buf, s->inf_s_prev, st.lam, s->inf_lam_prev,
+                                                                    st.x, s->inf_x_prev, s->r_buf, s->inf_r_prev,
                                                                     s->in_cone, n, m, s->inf_part);
         if (nsoc)
-            mfs::infeas::k_infeas_cones<<<(nsoc + 255) / 256, 256, 0, s->stream>>>(
-                s->s_buf, s->inf_s_prev, s->soc_start, s->soc_size, nsoc, s->inf_part + 2 * INF_BLOCKS);
-        std::vector<double> h(2 * INF_BLOCKS + nsoc);
+            mfs::infeas::k_infeas_cones<T><<<(nsoc + 255) / 256, 256, 0, s->stream>>>(
+                s->s_buf, s->inf_s_prev, st.x, s->inf_x_prev, s->soc_start, s->soc_size, nsoc,
+                s->inf_part + 5 * INF_BLOCKS);
+        std::vector<double> h(5 * INF_BLOCKS + 2 * nsoc);
         CUDA_TRY(s, cudaMemcpyAsync(h.data(), s->inf_part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
         CUDA_TRY(s, cudaStreamSynchronize(s->stream));
-        for (int b = 0; b < INF_BLOCKS; ++b) {
-            out[0] += h[2 * b];
-            out[1] += h[2 * b + 1];
+        for (int b = 0; b < INF_BLOCKS; ++b)
+            for (int q = 0; q < 5; ++q) out[q] += h[5 * b + q];
+        for (int q = 0; q < nsoc; ++q) {
+            out[0] += h[5 * INF_BLOCKS + 2 * q];
+            out[2] += h[5 * INF_BLOCKS + 2 * q + 1];
         }
-        for (int q = 0; q < nsoc; ++q) out[0] += h[2 * INF_BLOCKS + q];
     }
-    if (n) CUDA_TRY(s, cudaMemcpyAsync(s->inf_s_prev, s->s_buf, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
-    if (m) convert(s->inf_lam_prev, st.lam, m, s->stream);
+    if (n) {
+        CUDA_TRY(s, cudaMemcpyAsync(s->inf_s_prev, s->s_buf, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+        convert(s->inf_x_prev, st.x, n, s->stream);
+    }
+    if (m) {
+        convert(s->inf_lam_prev, st.lam, m, s->stream);
+        CUDA_TRY(s, cudaMemcpyAsync(s->inf_r_prev, s->r_buf, m * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    }
     CUDA_TRY(s, cudaGetLastError());
     return MFS_OK;
 }
@@ -1049,6 +1064,7 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
     CHK(dalloc(s, &s->part_col, (size_t)s->g_colres * NFC));
     CHK(dalloc(s, &s->part_big, (size_t)std::max(s->nbig, 1) * NFB));
     CHK(dalloc(s, &s->s_buf, (size_t)std::max(s->n, 1)));
+    CHK(dalloc(s, &s->r_buf, (size_t)std::max(s->m, 1)));
     CHK(dalloc(s, &s->status, NSTATUS));
     e = cudaMallocHost(&s->h_status, NSTATUS * sizeof(double));
     if (e != cudaSuccess) {
@@ -1171,12 +1187,12 @@ mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters
     int since_best = 0;
     mfs_residuals_t r;
     mfs_status result = MFS_MAX_ITER;
-    // primal infeasibility test state: previous b^T lambda and precision, consecutive passes and the
-    // primal residuals of the last checks
+    // infeasibility tests: previous b^T lambda, c^T x and precision, consecutive passes, and the
+    // primal and dual residuals of the last checks
     bool have_prev = false;
-    int prev_prec = -1, passes = 0;
-    double prev_blam = 0.0;
-    std::vector<double> rp_hist;
+    int prev_prec = -1, pass_p = 0, pass_d = 0;
+    double prev_blam = 0.0, prev_cx = 0.0;
+    std::vector<double> rp_hist, rd_hist;
     while (true) {
         TRY(s->precision == MFS_FP64 ? residuals_t(s, s->s64, &r, true) : residuals_t(s, s->s32, &r, true));
         if (!std::isfinite(r.kkt)) {
@@ -1184,25 +1200,38 @@ mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters
             break;
         }
         {
-            double red[2];
+            double red[5];
             const bool same = have_prev && prev_prec == s->precision;
             TRY(s->precision == MFS_FP64 ? infeas_reduce(s, s->s64, same, red) : infeas_reduce(s, s->s32, same, red));
-            const double blam = -r.dobj;  // b^T lambda
+            const double blam = -r.dobj, cx = r.pobj;  // b^T lambda, c^T x
             rp_hist.push_back(r.r_prim);
-            if (same) {
-                const double bd = blam - prev_blam, dist = std::sqrt(red[0]), nd = std::sqrt(red[1]);
+            rd_hist.push_back(r.r_dual);
+            if (same && r.kkt > tol) {
                 const size_t h = rp_hist.size();
-                const bool stalled = h >= 4 && rp_hist[h - 1] >= 0.99 * rp_hist[h - 4];
-                const bool pass = bd < -1e-3 * r.nrm_b * nd && dist <= 0.1 * -bd && stalled;
-                passes = pass ? passes + 1 : 0;
-                if (passes >= 3 && r.kkt > tol) {
+                // primal infeasible: d = change of lambda, A^T d in K, b^T d < 0
+                const double bd = blam - prev_blam;
+                const bool p_stall = h >= 4 && rp_hist[h - 1] >= 0.99 * rp_hist[h - 4];
+                const bool p_pass = bd < -1e-3 * r.nrm_b * std::sqrt(red[1]) && std::sqrt(red[0]) <= 0.1 * -bd && p_stall;
+                pass_p = p_pass ? pass_p + 1 : 0;
+                // unbounded: e = change of x, A e = 0, e in K, c^T e < 0
+                const double ce = cx - prev_cx;
+                const bool d_stall = h >= 4 && rd_hist[h - 1] >= 0.99 * rd_hist[h - 4];
+                const bool d_pass = ce < -1e-3 * r.nrm_c * std::sqrt(red[3]) && std::sqrt(red[4]) <= 0.1 * -ce &&
+                                    std::sqrt(red[2]) <= 0.1 * -ce && d_stall;
+                pass_d = d_pass ? pass_d + 1 : 0;
+                if (pass_p >= 3) {
                     result = fail(s, MFS_INFEASIBLE, "primal infeasibility certificate (Farkas) found");
+                    break;
+                }
+                if (pass_d >= 3) {
+                    result = fail(s, MFS_UNBOUNDED, "a ray of the primal with falling cost found (the dual is infeasible)");
                     break;
                 }
             }
             have_prev = true;
             prev_prec = s->precision;
             prev_blam = blam;
+            prev_cx = cx;
         }
         const bool fp32 = s->precision == MFS_FP32_MIXED;
         if (r.kkt <= tol) {

@@ -16,9 +16,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmfs.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "mfs.h")
 
-MFS_OK, MFS_MAX_ITER, MFS_ERR_INVALID, MFS_ERR_CUDA, MFS_ERR_OOM, MFS_ERR_NUMERIC, MFS_ERR_TIMEOUT, MFS_INFEASIBLE = range(8)
+MFS_OK, MFS_MAX_ITER, MFS_ERR_INVALID, MFS_ERR_CUDA, MFS_ERR_OOM, MFS_ERR_NUMERIC, MFS_ERR_TIMEOUT, MFS_INFEASIBLE, \
+    MFS_UNBOUNDED = range(9)
 STATUS_NAMES = {0: "OK", 1: "MAX_ITER", 2: "ERR_INVALID", 3: "ERR_CUDA", 4: "ERR_OOM", 5: "ERR_NUMERIC",
-                6: "ERR_TIMEOUT", 7: "INFEASIBLE"}
+                6: "ERR_TIMEOUT", 7: "INFEASIBLE", 8: "UNBOUNDED"}
 CONE_NONNEG, CONE_SOC = 0, 1
 FP64, FP32_MIXED = 0, 1
 
@@ -215,7 +216,7 @@ class Solver:
     def solve(self, tol, max_iter):
         it = ctypes.c_int64(0)
         code = self._check(self._lib.mfs_solve(self._h, float(tol), int(max_iter), ctypes.byref(it)),
-                           ok=(MFS_OK, MFS_MAX_ITER, MFS_INFEASIBLE))
+                           ok=(MFS_OK, MFS_MAX_ITER, MFS_INFEASIBLE, MFS_UNBOUNDED))
         return STATUS_NAMES[code], int(it.value)
 
     def residuals(self):

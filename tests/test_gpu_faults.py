@@ -112,3 +112,37 @@ def test_feasible_solves_are_not_reported_infeasible():
             s = mfs.Solver(p, precision=precision, check_every=50, polish_iters=0)
             status, its = s.solve(1e-7, 60_000)
             assert status in ("OK", "MAX_ITER"), (p.get("name"), precision, status, its)
+
+
+def _unbounded_lp(seed):
+    # column n is minus column 0 with cost -c_0 - 1: e = e_0 + e_n has A e = 0, e >= 0, c^T e = -1
+    p = I.small_lp(seed, m=60, n=150)
+    j0 = p["col"] == 0
+    n = p["n"]
+    p["row"] = np.r_[p["row"], p["row"][j0]]
+    p["col"] = np.r_[p["col"], np.full(int(j0.sum()), n)]
+    p["val"] = np.r_[p["val"], -p["val"][j0]]
+    p["c"] = np.r_[p["c"], -p["c"][0] - 1.0]
+    p["n"] = n + 1
+    p["cones"] = np.array([[0, n + 1]])
+    return p
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_solve_reports_unbounded_primal(precision):
+    s = mfs.Solver(_unbounded_lp(1), precision=precision, check_every=50, polish_iters=0)
+    status, its = s.solve(1e-6, 200_000)
+    assert status == "UNBOUNDED" and its < 20_000, (status, its)
+
+
+def test_solve_reports_unbounded_socp():
+    # an extra Lorentz cone of size 3 whose columns A does not touch, with cost (-1, 0, 0): the ray
+    # e = (1, 0, 0) lies in the cone, A e = 0 and c^T e = -1
+    p = I.socp(4, n=600, m=200, nnz_per_row=6)
+    n = p["n"]
+    p["n"] = n + 3
+    p["c"] = np.r_[p["c"], -1.0, 0.0, 0.0]
+    p["cones"] = np.vstack([np.asarray(p["cones"]), [[mfs.CONE_SOC, 3]]])
+    s = mfs.Solver(p, precision="fp64", check_every=50)
+    status, its = s.solve(1e-6, 200_000)
+    assert status == "UNBOUNDED", (status, its)

@@ -8,7 +8,8 @@ shared-A solver (mfs_shared_*), train the tensor-core MLP (mfs_mlp_*) theta -> (
 its prediction then warm-starts the solver (mfs_shared_warm_start_device).
 
 Every arithmetic step of solving and training runs in libmfs; this module draws the seeded
-family, moves buffers and records counts and times. torch provides device memory only.
+family (numpy), moves buffers and records counts, times and prediction errors; torch provides
+device memory.
 """
 from __future__ import annotations
 
@@ -37,21 +38,6 @@ def data_of(fam, theta):
     b = base["b"][None, :] + theta @ fam["Bb"].T
     c = base["c"][None, :] + theta @ fam["Bc"].T
     return b, c
-
-
-def solve_batch(sh, fam, theta, tol, max_iter, warm=None):
-    """Solve the members theta (len(theta) == sh.count) from the cold start or, with
-    warm = (x_ptr, lam_ptr), from a warm start. Returns (iterations per member, seconds)."""
-    import torch
-    b, c = data_of(fam, theta)
-    sh.set_data(b, c)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    if warm is not None:
-        sh.warm_start_device(*warm)
-    status, its = sh.solve(tol, max_iter)
-    torch.cuda.synchronize()
-    return its, time.perf_counter() - t0
 
 
 def generate(fam, count, seed, tol, max_iter, batch=512, check_every=250):

@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmfs.so")
 SOURCES = ["mfs_solver.cu", "mfs_batch.cu", "mfs_shared.cu", "mfs_mlp.cu", "mfs_static.cu"]
-HEADERS = ["mfs_device.cuh", "mfs_kernels.cuh", "mfs_gemm.cuh", "mfs_alloc.h", "mfs_literal.cuh", "mfs_infeas.cuh"]
+HEADERS = ["mfs_device.cuh", "mfs_kernels.cuh", "mfs_gemm.cuh", "mfs_alloc.h", "mfs_literal.cuh", "mfs_infeas.cuh", "mfs_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -26,7 +26,7 @@ def build(force=False, verbose=False, extra=()):
     nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
     tmp = LIB + ".tmp"
     cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-O2", "--expt-relaxed-constexpr", *extra,
+           "-Xcompiler", "-O2", "-Xcompiler", "-pthread", "--expt-relaxed-constexpr", *extra,
            "-o", tmp, *[os.path.join(CSRC, f) for f in SOURCES], "-lcudart"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")

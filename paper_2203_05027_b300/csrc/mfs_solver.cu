@@ -16,6 +16,7 @@
 
 #include "../../include/mfs.h"
 #include "mfs_alloc.h"
+#include "mfs_host.h"
 #include "mfs_kernels.cuh"
 #include "mfs_infeas.cuh"
 #include "mfs_literal.cuh"
@@ -53,10 +54,10 @@ struct Chunks {
 struct HostProblem {
     int m = 0, n = 0, o = 0;
     std::vector<int> col_ptr, row_ptr;
-    std::vector<int> csc_row;     // unpadded, column order
-    std::vector<double> csc_val;
-    std::vector<int> csr_col;     // unpadded, row order
-    std::vector<double> csr_val;
+    mfs::host::uvec<int> csc_row;     // unpadded, column order
+    mfs::host::uvec<double> csc_val;
+    mfs::host::uvec<int> csr_col;     // unpadded, row order
+    mfs::host::uvec<double> csr_val;
     Chunks cc, rc;
     std::vector<int> cq_lo, cq_hi;
     std::vector<int> soc_start, soc_size, big_list;
@@ -154,56 +155,111 @@ mfs_status upload(mfs_solver* s, T** p, const void* host, size_t count) {
 // ---------------------------------------------------------------------------------- host set-up
 
 // Sort COO into column order (rows ascending within a column), sum duplicates, drop zeros;
-// then build the row order. Counting sorts, O(nnz + m + n).
+// then build the row order (columns ascending within a row). Stable counting sorts, O(nnz + m + n),
+// multi-threaded (mfs_host.h); an input already in strict column order skips the sorting.
 void build_orders(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col, const double* val,
                   HostProblem& P) {
-    std::vector<int64_t> cnt(std::max(m, n) + 1, 0), by_row(nnz), by_col(nnz);
-    for (int64_t t = 0; t < nnz; ++t) cnt[row[t] + 1]++;
-    for (int64_t i = 0; i < m; ++i) cnt[i + 1] += cnt[i];
-    for (int64_t t = 0; t < nnz; ++t) by_row[cnt[row[t]]++] = t;
-    std::fill(cnt.begin(), cnt.end(), 0);
-    for (int64_t t = 0; t < nnz; ++t) cnt[col[t] + 1]++;
-    for (int64_t j = 0; j < n; ++j) cnt[j + 1] += cnt[j];
-    for (int64_t q = 0; q < nnz; ++q) {
-        const int64_t t = by_row[q];
-        by_col[cnt[col[t]]++] = t;
+    using namespace mfs::host;
+    const int nt = threads_for(nnz);
+    // order of the input entries by (column, row)
+    std::vector<char> unsorted(nt, 0);
+    parallel_ranges(nnz > 0 ? nnz - 1 : 0, nt, [&](int64_t lo, int64_t hi, int t) {
+        for (int64_t q = lo; q < hi && !unsorted[t]; ++q)
+            if (col[q] > col[q + 1] || (col[q] == col[q + 1] && row[q] >= row[q + 1])) unsorted[t] = 1;
+    });
+    uvec<int64_t> ord((size_t)nnz);
+    if (std::find(unsorted.begin(), unsorted.end(), 1) == unsorted.end()) {
+        parallel_ranges(nnz, nt, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t q = lo; q < hi; ++q) ord[q] = q;
+        });
+    } else {
+        uvec<int64_t> by_row((size_t)nnz);
+        counting_sort(nnz, m, [&](int64_t q) { return row[q]; }, nullptr, by_row.data(), nullptr);
+        counting_sort(nnz, n, [&](int64_t q) { return col[by_row[q]]; }, by_row.data(), ord.data(), nullptr);
     }
-    by_row.clear();
-    by_row.shrink_to_fit();
+    // sum duplicates and drop zeros: each thread compacts a range of groups of equal (column, row)
+    std::vector<int64_t> cut(nt + 1, nnz);
+    cut[0] = 0;
+    for (int t = 1; t < nt; ++t) {
+        int64_t q = nnz * t / nt;
+        if (q < cut[t - 1]) q = cut[t - 1];
+        while (q > 0 && q < nnz && row[ord[q]] == row[ord[q - 1]] && col[ord[q]] == col[ord[q - 1]]) ++q;
+        cut[t] = q;
+    }
+    std::vector<uvec<int>> krow(nt), kcol(nt);
+    std::vector<uvec<double>> kval(nt);
+    parallel_tasks(nt, [&](int t) {
+        // thread-local output with raw-pointer writes (no shared vector headers written per entry)
+        const int64_t len = cut[t + 1] - cut[t];
+        uvec<int> lr(len), lc(len);
+        uvec<double> lv(len);
+        int* pr = lr.data();
+        int* pc = lc.data();
+        double* pv = lv.data();
+        int64_t w = 0, q = cut[t];
+        while (q < cut[t + 1]) {
+            const int64_t e = ord[q];
+            const int64_t i = row[e], j = col[e];
+            double a = val[e];
+            ++q;
+            while (q < cut[t + 1] && row[ord[q]] == i && col[ord[q]] == j) a += val[ord[q++]];
+            if (a != 0.0) {
+                pr[w] = (int)i;
+                pc[w] = (int)j;
+                pv[w] = a;
+                ++w;
+            }
+        }
+        lr.resize(w);
+        lc.resize(w);
+        lv.resize(w);
+        krow[t] = std::move(lr);
+        kcol[t] = std::move(lc);
+        kval[t] = std::move(lv);
+    });
+    ord.clear();
+    ord.shrink_to_fit();
+    std::vector<int64_t> off(nt + 1, 0);
+    for (int t = 0; t < nt; ++t) off[t + 1] = off[t] + (int64_t)krow[t].size();
+    const int64_t o = off[nt];
     P.m = (int)m;
     P.n = (int)n;
-    P.col_ptr.assign(n + 1, 0);
-    P.csc_row.reserve(nnz);
-    P.csc_val.reserve(nnz);
-    int64_t q = 0;
-    while (q < nnz) {
-        const int64_t t = by_col[q];
-        const int64_t i = row[t], j = col[t];
-        double a = val[t];
-        ++q;
-        while (q < nnz && row[by_col[q]] == i && col[by_col[q]] == j) a += val[by_col[q++]];
-        if (a != 0.0) {
-            P.csc_row.push_back((int)i);
-            P.csc_val.push_back(a);
-            P.col_ptr[j + 1]++;
+    P.o = (int)o;
+    P.csc_row.resize(o);
+    P.csc_val.resize(o);
+    uvec<int> ccol(o);
+    parallel_tasks(nt, [&](int t) {
+        {
+            std::copy(krow[t].begin(), krow[t].end(), P.csc_row.begin() + off[t]);
+            std::copy(kval[t].begin(), kval[t].end(), P.csc_val.begin() + off[t]);
+            std::copy(kcol[t].begin(), kcol[t].end(), ccol.begin() + off[t]);
+            uvec<int>().swap(krow[t]);
+            uvec<int>().swap(kcol[t]);
+            uvec<double>().swap(kval[t]);
         }
-    }
-    for (int64_t j = 0; j < n; ++j) P.col_ptr[j + 1] += P.col_ptr[j];
-    P.o = (int)P.csc_row.size();
-    // row order from column order (stable: columns ascending within a row)
-    P.row_ptr.assign(m + 1, 0);
-    for (int k = 0; k < P.o; ++k) P.row_ptr[P.csc_row[k] + 1]++;
-    for (int64_t i = 0; i < m; ++i) P.row_ptr[i + 1] += P.row_ptr[i];
-    P.csr_col.resize(P.o);
-    P.csr_val.resize(P.o);
-    std::vector<int> fillp(P.row_ptr.begin(), P.row_ptr.begin() + m);
-    for (int64_t j = 0; j < n; ++j)
-        for (int k = P.col_ptr[j]; k < P.col_ptr[j + 1]; ++k) {
-            const int i = P.csc_row[k];
-            const int dst = fillp[i]++;
-            P.csr_col[dst] = (int)j;
-            P.csr_val[dst] = P.csc_val[k];
+    });
+    // column pointers: entries are in column order, so col_ptr[j] is the first entry of a column >= j
+    P.col_ptr.resize(n + 1);
+    parallel_ranges(o, threads_for(o), [&](int64_t lo, int64_t hi, int) {
+        for (int64_t k = lo; k < hi; ++k)
+            for (int j = (k ? ccol[k - 1] : -1) + 1; j <= ccol[k]; ++j) P.col_ptr[j] = (int)k;
+    });
+    for (int64_t j = (o ? ccol[o - 1] + 1 : 0); j <= n; ++j) P.col_ptr[j] = (int)o;
+    // row order from column order: stable by k, so columns ascend within a row
+    uvec<int64_t> by_row((size_t)o);
+    std::vector<int64_t> rstart;
+    counting_sort(o, m, [&](int64_t k) { return (int64_t)P.csc_row[k]; }, nullptr, by_row.data(), &rstart);
+    P.row_ptr.resize(m + 1);
+    for (int64_t i = 0; i <= m; ++i) P.row_ptr[i] = (int)rstart[i];
+    P.csr_col.resize(o);
+    P.csr_val.resize(o);
+    parallel_ranges(o, threads_for(o), [&](int64_t lo, int64_t hi, int) {
+        for (int64_t p = lo; p < hi; ++p) {
+            const int64_t k = by_row[p];
+            P.csr_col[p] = ccol[k];
+            P.csr_val[p] = P.csc_val[k];
         }
+    });
 }
 
 // Greedy chunking of segments (columns or rows) in order. A unit is one segment, or a whole
@@ -294,17 +350,32 @@ mfs_status setup_host(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const in
 }
 
 // Padded nonzero arrays: chunk c's nonzeros at desc offset, zero-filled up to a multiple of PAD.
-template <typename T>
-void pad_chunks(const Chunks& C, const std::vector<int>& ptr, const std::vector<int>& idx,
-                const std::vector<double>& val, std::vector<int>* pidx, std::vector<T>* pval) {
-    if (pidx) pidx->assign(C.padded + PAD, 0);
-    if (pval) pval->assign(C.padded + PAD, T(0));
-    for (int c = 0; c < C.count(); ++c) {
-        const int s0 = C.desc[4 * c], s1 = C.desc[4 * c + 1], koff = C.desc[4 * c + 2];
-        const int k0 = ptr[s0], k1 = ptr[s1];
-        for (int k = k0; k < k1; ++k) {
-            if (pidx) (*pidx)[koff + (k - k0)] = idx[k];
-            if (pval) (*pval)[koff + (k - k0)] = T(val[k]);
+template <typename T, class IdxV, class ValV, class OutI, class OutV>
+void pad_chunks(const Chunks& C, const std::vector<int>& ptr, const IdxV& idx, const ValV& val, OutI* pidx,
+                OutV* pval) {
+    const int nt = mfs::host::threads_for((int64_t)C.padded);
+    if (pidx) pidx->resize(C.padded + PAD);
+    if (pval) pval->resize(C.padded + PAD);
+    // every padded slot is written once: the chunk's nonzeros, then zeros up to the next chunk
+    mfs::host::parallel_ranges(C.count(), nt, [&](int64_t lo, int64_t hi, int) {
+        for (int64_t c = lo; c < hi; ++c) {
+            const int s0 = C.desc[4 * c], s1 = C.desc[4 * c + 1], koff = C.desc[4 * c + 2];
+            const int k0 = ptr[s0], k1 = ptr[s1];
+            const int end = (c + 1 < C.count()) ? C.desc[4 * (c + 1) + 2] : (int)C.padded + PAD;
+            for (int k = k0; k < k1; ++k) {
+                if (pidx) (*pidx)[koff + (k - k0)] = idx[k];
+                if (pval) (*pval)[koff + (k - k0)] = T(val[k]);
+            }
+            for (int q = koff + (k1 - k0); q < end; ++q) {
+                if (pidx) (*pidx)[q] = 0;
+                if (pval) (*pval)[q] = T(0);
+            }
+        }
+    });
+    if (C.count() == 0) {
+        for (int q = 0; q < (int)C.padded + PAD; ++q) {
+            if (pidx) (*pidx)[q] = 0;
+            if (pval) (*pval)[q] = T(0);
         }
     }
 }
@@ -552,10 +623,10 @@ mfs_status alloc_state(mfs_solver* s, State<T>& st, const HostProblem& P, const 
     std::vector<T> hb(b, b + s->m), hc(c, c + s->n);
     TRY(upload(s, &st.b, hb.data(), hb.size()));
     TRY(upload(s, &st.c, hc.data(), hc.size()));
-    std::vector<T> pval;
-    pad_chunks<T>(P.cc, P.col_ptr, P.csc_row, P.csc_val, nullptr, &pval);
+    mfs::host::uvec<T> pval;
+    pad_chunks<T>(P.cc, P.col_ptr, P.csc_row, P.csc_val, (mfs::host::uvec<int>*)nullptr, &pval);
     TRY(upload(s, &st.cval, pval.data(), pval.size()));
-    pad_chunks<T>(P.rc, P.row_ptr, P.csr_col, P.csr_val, nullptr, &pval);
+    pad_chunks<T>(P.rc, P.row_ptr, P.csr_col, P.csr_val, (mfs::host::uvec<int>*)nullptr, &pval);
     TRY(upload(s, &st.rval, pval.data(), pval.size()));
     CUDA_TRY(s, cudaMemsetAsync(st.x, 0, sizeof(T) * std::max(s->n, 1), s->stream));
     CUDA_TRY(s, cudaMemsetAsync(st.z, 0, sizeof(T) * std::max(s->n, 1), s->stream));
@@ -961,10 +1032,21 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
         total += cones[q].size;
     }
     if (total != n) return fail(nullptr, MFS_ERR_INVALID, "cone sizes do not sum to n");
-    for (int64_t t = 0; t < nnz; ++t) {
-        if (row[t] < 0 || row[t] >= m || col[t] < 0 || col[t] >= n)
-            return fail(nullptr, MFS_ERR_INVALID, "COO index out of range at entry " + std::to_string(t));
-        if (!std::isfinite(val[t])) return fail(nullptr, MFS_ERR_INVALID, "non-finite value in A");
+    {
+        // first bad entry: index out of range, or a non-finite value
+        const int nt = mfs::host::threads_for(nnz);
+        std::vector<int64_t> bad_idx(nt, nnz), bad_val(nt, nnz);
+        mfs::host::parallel_ranges(nnz, nt, [&](int64_t lo, int64_t hi, int t) {
+            for (int64_t q = lo; q < hi; ++q) {
+                if (bad_idx[t] == nnz && (row[q] < 0 || row[q] >= m || col[q] < 0 || col[q] >= n)) bad_idx[t] = q;
+                if (bad_val[t] == nnz && !std::isfinite(val[q])) bad_val[t] = q;
+            }
+        });
+        const int64_t bi = *std::min_element(bad_idx.begin(), bad_idx.end());
+        const int64_t bv = *std::min_element(bad_val.begin(), bad_val.end());
+        if (bi < nnz && bi <= bv)
+            return fail(nullptr, MFS_ERR_INVALID, "COO index out of range at entry " + std::to_string(bi));
+        if (bv < nnz) return fail(nullptr, MFS_ERR_INVALID, "non-finite value in A");
     }
     if (!finite_all(b, m) || !finite_all(c, n)) return fail(nullptr, MFS_ERR_INVALID, "non-finite value in b or c");
 
@@ -1039,10 +1121,10 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
     CHK(upload(s, &s->big_list, P.big_list.data(), P.big_list.size()));
     {
         // padded index arrays (shared by both precisions)
-        std::vector<int> pidx;
-        pad_chunks<double>(P.cc, P.col_ptr, P.csc_row, P.csc_val, &pidx, nullptr);
+        mfs::host::uvec<int> pidx;
+        pad_chunks<double>(P.cc, P.col_ptr, P.csc_row, P.csc_val, &pidx, (mfs::host::uvec<double>*)nullptr);
         CHK(upload(s, &s->cidx, pidx.data(), pidx.size()));
-        pad_chunks<double>(P.rc, P.row_ptr, P.csr_col, P.csr_val, &pidx, nullptr);
+        pad_chunks<double>(P.rc, P.row_ptr, P.csr_col, P.csr_val, &pidx, (mfs::host::uvec<double>*)nullptr);
         CHK(upload(s, &s->ridx, pidx.data(), pidx.size()));
     }
     {

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <numeric>
@@ -22,6 +23,7 @@
 #include "../../include/mfs.h"
 #include "mfs_alloc.h"
 #include "mfs_device.cuh"
+#include "mfs_host.h"
 
 namespace {
 
@@ -661,19 +663,20 @@ mfs_status mfs_batch_create(int64_t count, const int64_t* m, const int64_t* n, c
     s->tune.threads = 256;
     s->tune.ctas_per_sm = 1;
     s->tune.check_every = set.check_every;
-    // per instance: column order (rows ascending within a column) and row order, local indices
+    // per instance: column order (rows ascending within a column) and row order, local indices.
+    // Cones and offsets first (sequential, cheap), then the instances' orders in parallel, then
+    // the concatenation.
     std::vector<int> hm(count), hn(count), ho(count), hns(count), cp, rp, ci, ri, sst, ssz;
     std::vector<long long> offn(count), offm(count), offo(count), offs(count);
+    std::vector<int64_t> offz(count + 1, 0);
     std::vector<double> cv, rv;
-    cp.reserve(tn + count);
-    rp.reserve(tm + count);
-    int64_t pn = 0, pm = 0, po = 0, pz = 0, pc = 0;
+    int64_t pn = 0, pm = 0, pc = 0;
     for (int64_t t = 0; t < count; ++t) {
-        const int64_t mt = m[t], nt = n[t], kt = nnz[t];
+        const int64_t nt = n[t];
         offn[t] = pn;
         offm[t] = pm;
         offs[t] = (long long)sst.size();
-        // cones of instance t
+        offz[t + 1] = offz[t] + nnz[t];
         int64_t covered = 0;
         for (int64_t q = 0; q < ncones[t]; ++q) {
             const mfs_cone& cq = cones[pc + q];
@@ -693,65 +696,99 @@ mfs_status mfs_batch_create(int64_t count, const int64_t* m, const int64_t* n, c
         }
         hns[t] = (int)(sst.size() - offs[t]);
         pc += ncones[t];
-        // sort the instance's entries by (col, row), sum duplicates, drop zeros
-        std::vector<int64_t> idx(kt);
-        std::iota(idx.begin(), idx.end(), 0);
-        for (int64_t k = 0; k < kt; ++k) {
-            const int64_t r = row[pz + k], q = col[pz + k];
-            if (r < 0 || r >= mt || q < 0 || q >= nt || !std::isfinite(val[pz + k])) {
-                s->last_error = "bad entry " + std::to_string(k) + " in instance " + std::to_string(t);
-                return bail(MFS_ERR_INVALID);
-            }
-        }
-        std::sort(idx.begin(), idx.end(), [&](int64_t p, int64_t q) {
-            return col[pz + p] != col[pz + q] ? col[pz + p] < col[pz + q] : row[pz + p] < row[pz + q];
-        });
-        std::vector<int> lr, lc;
-        std::vector<double> lv;
-        for (int64_t k = 0; k < kt;) {
-            const int64_t r = row[pz + idx[k]], q = col[pz + idx[k]];
-            double a = 0.0;
-            while (k < kt && row[pz + idx[k]] == r && col[pz + idx[k]] == q) a += val[pz + idx[k++]];
-            if (a != 0.0) {
-                lr.push_back((int)r);
-                lc.push_back((int)q);
-                lv.push_back(a);
-            }
-        }
-        const int ot = (int)lv.size();
-        offo[t] = po;
-        hm[t] = (int)mt;
+        hm[t] = (int)m[t];
         hn[t] = (int)nt;
-        ho[t] = ot;
-        // column order
-        std::vector<int> cnt(nt + 1, 0);
-        for (int k = 0; k < ot; ++k) cnt[lc[k] + 1]++;
-        for (int64_t j = 0; j < nt; ++j) cnt[j + 1] += cnt[j];
-        cp.insert(cp.end(), cnt.begin(), cnt.end());
-        for (int k = 0; k < ot; ++k) {
-            ci.push_back(lr[k]);
-            cv.push_back(lv[k]);
-        }
-        // row order (columns ascending within a row)
-        std::vector<int> rc(mt + 1, 0);
-        for (int k = 0; k < ot; ++k) rc[lr[k] + 1]++;
-        for (int64_t i = 0; i < mt; ++i) rc[i + 1] += rc[i];
-        rp.insert(rp.end(), rc.begin(), rc.end());
-        std::vector<int> fill(rc.begin(), rc.begin() + mt);
-        std::vector<int> tri(ot);
-        std::vector<double> trv(ot);
-        for (int k = 0; k < ot; ++k) {
-            const int dst = fill[lr[k]]++;
-            tri[dst] = lc[k];
-            trv[dst] = lv[k];
-        }
-        ri.insert(ri.end(), tri.begin(), tri.end());
-        rv.insert(rv.end(), trv.begin(), trv.end());
         pn += nt;
-        pm += mt;
-        po += ot;
-        pz += kt;
+        pm += m[t];
     }
+    struct Orders {
+        std::vector<int> cnt, ci, rc, ri;  // column pointers, rows (column order), row pointers, columns (row order)
+        std::vector<double> cv, rv;
+        int64_t bad = -1;                   // first bad entry, or -1
+    };
+    std::vector<Orders> ords(count);
+    std::atomic<int64_t> next{0};
+    const int nthr = mfs::host::threads_for(offz[count]);
+    mfs::host::parallel_tasks(nthr, [&](int) {
+        for (int64_t t = next++; t < count; t = next++) {
+            Orders& R = ords[t];
+            const int64_t mt = m[t], nt = n[t], kt = nnz[t], pz = offz[t];
+            for (int64_t k = 0; k < kt && R.bad < 0; ++k) {
+                const int64_t r = row[pz + k], q = col[pz + k];
+                if (r < 0 || r >= mt || q < 0 || q >= nt || !std::isfinite(val[pz + k])) R.bad = k;
+            }
+            if (R.bad >= 0) continue;
+            // sort the entries by (col, row) unless they already are; sum duplicates, drop zeros
+            std::vector<int64_t> idx(kt);
+            std::iota(idx.begin(), idx.end(), 0);
+            bool sorted = true;
+            for (int64_t k = 1; k < kt && sorted; ++k)
+                sorted = col[pz + k - 1] < col[pz + k] || (col[pz + k - 1] == col[pz + k] && row[pz + k - 1] < row[pz + k]);
+            if (!sorted)
+                std::sort(idx.begin(), idx.end(), [&](int64_t p, int64_t q) {
+                    return col[pz + p] != col[pz + q] ? col[pz + p] < col[pz + q] : row[pz + p] < row[pz + q];
+                });
+            std::vector<int> lc;
+            R.ci.reserve(kt);
+            R.cv.reserve(kt);
+            lc.reserve(kt);
+            for (int64_t k = 0; k < kt;) {
+                const int64_t r = row[pz + idx[k]], q = col[pz + idx[k]];
+                double a = 0.0;
+                while (k < kt && row[pz + idx[k]] == r && col[pz + idx[k]] == q) a += val[pz + idx[k++]];
+                if (a != 0.0) {
+                    R.ci.push_back((int)r);
+                    lc.push_back((int)q);
+                    R.cv.push_back(a);
+                }
+            }
+            const int ot = (int)R.cv.size();
+            R.cnt.assign(nt + 1, 0);
+            for (int k = 0; k < ot; ++k) R.cnt[lc[k] + 1]++;
+            for (int64_t j = 0; j < nt; ++j) R.cnt[j + 1] += R.cnt[j];
+            // row order (columns ascending within a row)
+            R.rc.assign(mt + 1, 0);
+            for (int k = 0; k < ot; ++k) R.rc[R.ci[k] + 1]++;
+            for (int64_t i = 0; i < mt; ++i) R.rc[i + 1] += R.rc[i];
+            std::vector<int> fill(R.rc.begin(), R.rc.begin() + mt);
+            R.ri.resize(ot);
+            R.rv.resize(ot);
+            for (int k = 0; k < ot; ++k) {
+                const int dst = fill[R.ci[k]]++;
+                R.ri[dst] = lc[k];
+                R.rv[dst] = R.cv[k];
+            }
+        }
+    });
+    for (int64_t t = 0; t < count; ++t)
+        if (ords[t].bad >= 0) {
+            s->last_error = "bad entry " + std::to_string(ords[t].bad) + " in instance " + std::to_string(t);
+            return bail(MFS_ERR_INVALID);
+        }
+    int64_t po = 0;
+    for (int64_t t = 0; t < count; ++t) {
+        offo[t] = po;
+        ho[t] = (int)ords[t].cv.size();
+        po += ho[t];
+    }
+    cp.resize(tn + count);
+    rp.resize(tm + count);
+    ci.resize(po);
+    ri.resize(po);
+    cv.resize(po);
+    rv.resize(po);
+    mfs::host::parallel_ranges(count, nthr, [&](int64_t lo, int64_t hi, int) {
+        for (int64_t t = lo; t < hi; ++t) {
+            const Orders& R = ords[t];
+            std::copy(R.cnt.begin(), R.cnt.end(), cp.begin() + offn[t] + t);
+            std::copy(R.rc.begin(), R.rc.end(), rp.begin() + offm[t] + t);
+            std::copy(R.ci.begin(), R.ci.end(), ci.begin() + offo[t]);
+            std::copy(R.cv.begin(), R.cv.end(), cv.begin() + offo[t]);
+            std::copy(R.ri.begin(), R.ri.end(), ri.begin() + offo[t]);
+            std::copy(R.rv.begin(), R.rv.end(), rv.begin() + offo[t]);
+        }
+    });
+    std::vector<Orders>().swap(ords);
     s->tot_n = pn;
     s->tot_m = pm;
     s->tot_o = po;

@@ -92,6 +92,15 @@ def edge_problem(kind, seed=0):
         p["val"] = np.r_[p["val"], rng.standard_normal(40)]
         p["val"][5:12] = 0.0
         return p
+    if kind == "degree_one":  # every column has one nonzero (rows of very different lengths)
+        m, n = 40, 700
+        p = I.lp_from_degrees(m, n, np.ones(n, np.int64), seed)
+        return p
+    if kind == "chunk_boundaries":  # columns of exactly 256 and 257 nonzeros; runs of 64 columns x 4
+        m, n = 3000, 400
+        deg = np.r_[np.full(64, 4), [256], np.full(64, 4), [257], np.full(63, 4), [256], rng.integers(1, 9, n - 194)]
+        p = I.lp_from_degrees(m, n, deg, seed)
+        return p
     if kind == "no_nonzeros":
         n, m = 10, 4
         return {"m": m, "n": n, "row": np.zeros(0, np.int64), "col": np.zeros(0, np.int64),
@@ -137,7 +146,7 @@ def test_small_lp_fp32_2000_iterations():
 
 
 @pytest.mark.parametrize("kind", ["empty_rows_cols", "long_column", "long_row", "soc_mixed", "soc_big_nnz",
-                                  "duplicates_zeros", "no_nonzeros"])
+                                  "duplicates_zeros", "no_nonzeros", "degree_one", "chunk_boundaries"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_edge_cases(kind, precision):
     prob = edge_problem(kind)

@@ -290,6 +290,12 @@ mfs_status mfs_shared_load_slots(mfs_shared* sh, int64_t count, const int32_t* s
                                  const float* c);
 mfs_status mfs_shared_get_slots_device(mfs_shared* sh, int64_t count, const int32_t* slots, float* x,
                                        float* lambda);
+/* load_slots followed, for those slots only, by the warm start of mfs_shared_warm_start_device:
+   x [count][n] and lambda [count][m] (device FP32 rows in the order of slots, required) become the
+   iterate, z = proj_K(x), delta = proj_K(c + A^T lambda), v = F_U (b - A x) - lambda/mu. The other
+   slots are untouched. Synchronous. */
+mfs_status mfs_shared_load_slots_warm(mfs_shared* sh, int64_t count, const int32_t* slots, const float* b,
+                                      const float* c, const float* x, const float* lambda);
 /* Iterate of instance t as host doubles (any may be NULL): x, z, delta (n), lambda (m). */
 mfs_status mfs_shared_get_solution(mfs_shared* sh, int64_t t, double* x, double* lambda, double* z,
                                    double* delta);

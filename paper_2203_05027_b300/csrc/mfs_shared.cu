@@ -465,6 +465,50 @@ __global__ void k_s_zero_slots(T* __restrict__ arr, const int* __restrict__ slot
         arr[(size_t)(t % len) * Bp + slots[t / len]] = T(0);
 }
 
+// Warm start of single slots: projections of those slots only (orthant coordinates per (j, slot),
+// Lorentz cones per (cone, slot)), and v = F_U (b - A x) - lambda/mu of those slots.
+template <typename T>
+__global__ void k_s_proj_slots_orthant(const T* __restrict__ in, T* __restrict__ out, const unsigned char* in_soc, int n,
+                                       int Bp, const int* __restrict__ slots, int count) {
+    const long long total = (long long)n * count;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(t / count);
+        if (in_soc[j]) continue;
+        const size_t p = (size_t)j * Bp + slots[t % count];
+        out[p] = in[p] > T(0) ? in[p] : T(0);
+    }
+}
+template <typename T>
+__global__ void k_s_proj_slots_cones(const T* __restrict__ in, T* __restrict__ out, const int* soc_start,
+                                     const int* soc_size, int nsoc, int Bp, const int* __restrict__ slots, int count) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)nsoc * count) return;
+    const int q = (int)(t / count), s = slots[t % count];
+    const int st = soc_start[q], sz = soc_size[q];
+    T ss = T(0);
+    for (int k = 1; k < sz; ++k) {
+        const T u = in[(size_t)(st + k) * Bp + s];
+        ss += u * u;
+    }
+    const T alpha = sqrt(ss), w1 = in[(size_t)st * Bp + s];
+    for (int k = 0; k < sz; ++k) {
+        const size_t p = (size_t)(st + k) * Bp + s;
+        out[p] = lorentz_coord(in[p], k, w1, alpha);
+    }
+}
+template <typename T>
+__global__ void k_s_row_slots(const SArgs<T> a, const int* __restrict__ slots, int count) {
+    const long long total = (long long)a.m * count;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / count), s = slots[t % count];
+        T acc = T(0);
+        for (int k = a.row_ptr[i]; k < a.row_ptr[i + 1]; ++k) acc += a.rval[k] * a.x[(size_t)a.ridx[k] * a.Bp + s];
+        const size_t p = (size_t)i * a.Bp + s;
+        const T rho = (a.b[p] - acc) * a.fu[i];
+        a.v[p] = rho - a.lam[p] / a.mu;
+    }
+}
+
 template <typename T>
 struct SStore {
     T *cval = nullptr, *rval = nullptr, *fu = nullptr, *b = nullptr, *c = nullptr;
@@ -745,6 +789,29 @@ static mfs_status load_slots_t(mfs_shared* s, SStore<T>& st, int count, const fl
     if (tm) {
         for (int q = 0; q < 2; ++q) k_s_zero_slots<T><<<grid_for(tm), 256, 0, s->stream>>>(mvec[q], sl, count, s->m, s->Bp);
     }
+    SCUDA(s, cudaGetLastError());
+    return MFS_OK;
+}
+
+template <typename T>
+static mfs_status warm_slots_t(mfs_shared* s, SStore<T>& st, int count, const float* x, const float* lam) {
+    const int* sl = s->slot_buf;
+    const long long tm = (long long)count * s->m, tn = (long long)count * s->n;
+    if (tn) k_s_scatter_slots<float, T><<<grid_for(tn), 256, 0, s->stream>>>(x, st.x, sl, count, s->n, s->Bp);
+    if (tm) k_s_scatter_slots<float, T><<<grid_for(tm), 256, 0, s->stream>>>(lam, st.lam, sl, count, s->m, s->Bp);
+    // z = proj_K(x)
+    if (tn) k_s_proj_slots_orthant<T><<<grid_for(tn), 256, 0, s->stream>>>(st.x, st.z, s->in_soc, s->n, s->Bp, sl, count);
+    if (s->nsoc)
+        k_s_proj_slots_cones<T><<<(int)((s->nsoc * (long long)count + 255) / 256), 256, 0, s->stream>>>(
+            st.x, st.z, s->soc_start, s->soc_size, s->nsoc, s->Bp, sl, count);
+    // delta = proj_K(c + A^T lambda): s = c + A^T lambda for all slots, projected for these
+    STRY(s_residuals(s, st, st.sbuf));
+    if (tn) k_s_proj_slots_orthant<T><<<grid_for(tn), 256, 0, s->stream>>>(st.sbuf, st.del, s->in_soc, s->n, s->Bp, sl, count);
+    if (s->nsoc)
+        k_s_proj_slots_cones<T><<<(int)((s->nsoc * (long long)count + 255) / 256), 256, 0, s->stream>>>(
+            st.sbuf, st.del, s->soc_start, s->soc_size, s->nsoc, s->Bp, sl, count);
+    // v = F_U (b - A x) - lambda/mu of these slots
+    if (tm) k_s_row_slots<T><<<grid_for(tm), 256, 0, s->stream>>>(sargs(s, st), sl, count);
     SCUDA(s, cudaGetLastError());
     return MFS_OK;
 }
@@ -1035,6 +1102,19 @@ mfs_status mfs_shared_get_solution_device(mfs_shared* s, float* x, float* lambda
         if (lambda) deinterleave(s->f32.lam, lambda, s->B, s->m, s->Bp, s->stream);
     }
     SCUDA(s, cudaGetLastError());
+    SCUDA(s, cudaStreamSynchronize(s->stream));
+    return MFS_OK;
+}
+
+mfs_status mfs_shared_load_slots_warm(mfs_shared* s, int64_t count, const int32_t* slots, const float* b,
+                                      const float* c, const float* x, const float* lambda) {
+    if (!s) return MFS_ERR_INVALID;
+    if (count > 0 && ((s->m && (!b || !lambda)) || (s->n && (!c || !x))))
+        return sfail(s, MFS_ERR_INVALID, "b, c, x and lambda are required");
+    STRY(mfs_shared_load_slots(s, count, slots, b, c));
+    if (count)
+        STRY(s->set.precision == MFS_FP64 ? warm_slots_t(s, s->f64, (int)count, x, lambda)
+                                          : warm_slots_t(s, s->f32, (int)count, x, lambda));
     SCUDA(s, cudaStreamSynchronize(s->stream));
     return MFS_OK;
 }

@@ -559,7 +559,8 @@ def _load_shared():
                        ("mfs_shared_get_solution_device", [P, P, P]),
                        ("mfs_shared_get_solution", [P, i64, P, P, P, P]),
                        ("mfs_shared_load_slots", [P, i64, P, P, P]),
-                       ("mfs_shared_get_slots_device", [P, i64, P, P, P])):
+                       ("mfs_shared_get_slots_device", [P, i64, P, P, P]),
+                       ("mfs_shared_load_slots_warm", [P, i64, P, P, P, P, P])):
         getattr(lib, name).argtypes = args
         getattr(lib, name).restype = st
     lib._shared_declared = True
@@ -650,6 +651,12 @@ class Shared:
         """New members (device FP32 rows b [k][m], c [k][n]) into the given slots, zero start."""
         sl = np.ascontiguousarray(slots, np.int32)
         self._check(self._lib.mfs_shared_load_slots(self._h, sl.size, _ptr(sl), _vp(b_ptr), _vp(c_ptr)))
+
+    def load_slots_warm(self, slots, b_ptr, c_ptr, x_ptr, lam_ptr):
+        """New members into the given slots, warm-started from device FP32 rows x, lambda."""
+        sl = np.ascontiguousarray(slots, np.int32)
+        self._check(self._lib.mfs_shared_load_slots_warm(self._h, sl.size, _ptr(sl), _vp(b_ptr), _vp(c_ptr),
+                                                         _vp(x_ptr), _vp(lam_ptr)))
 
     def slots_device(self, slots, x_ptr=None, lam_ptr=None):
         """x [k][n] and lambda [k][m] of the given slots into device FP32 arrays."""

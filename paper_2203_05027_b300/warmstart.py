@@ -138,47 +138,99 @@ def predict(net, theta, n, m):
     return Y[:, :n].contiguous(), Y[:, n:].contiguous()
 
 
-def evaluate(fam, net, theta, tol, max_iter, mu=1.0, check_every=100, precision="fp32"):
-    """Cold against learned warm start on the members theta (count x p, host): per member, the
-    iteration at which the relative KKT residual first met tol (-1 if never within max_iter), and
-    the wall time for the whole set (the warm arm includes the network's inference)."""
+def solve_stream(fam, theta, tol, max_iter, slots=256, check_every=100, warm=None, mu=1.0, precision="fp32",
+                 keep=False):
+    """Solve the members theta (count x p, host) to tol by continuous batching: `slots` members
+    iterate together, each leaves at its first check with relative KKT <= tol (or at max_iter) and
+    the next member enters its slot, from the zero start or, with warm = (X, L) (device FP32
+    [count][n] and [count][m]), from its row of X and L. Returns (iterations per member, -1 where
+    max_iter was reached first; kkt of each member at entry; seconds; with keep, each member's final
+    x [count][n] and lambda [count][m] on the device, else None, None)."""
+    import torch
+    base = fam["base"]
+    count = theta.shape[0]
+    slots = min(slots, count)
+    sh = mfs.Shared(base, slots, mu=mu, check_every=check_every, precision=precision)
+    member = np.full(slots, -1)
+    age = np.zeros(slots, np.int64)
+    iters = np.full(count, -1, np.int64)
+    kkt0 = np.full(count, np.nan)
+    n, m = base["n"], base["m"]
+    Xo = torch.empty((count, n), dtype=torch.float32, device="cuda") if keep else None
+    Lo = torch.empty((count, m), dtype=torch.float32, device="cuda") if keep else None
+    Xs = torch.empty((slots, n), dtype=torch.float32, device="cuda") if keep else None
+    Ls = torch.empty((slots, m), dtype=torch.float32, device="cuda") if keep else None
+    nxt = 0
+
+    def enter(sl):
+        nonlocal nxt
+        idx = np.arange(nxt, nxt + len(sl))
+        nxt += len(sl)
+        b, c = data_of(fam, theta[idx])
+        bd = torch.from_numpy(b.astype(np.float32)).cuda()
+        cd = torch.from_numpy(c.astype(np.float32)).cuda()
+        if warm is None:
+            sh.load_slots(sl, bd.data_ptr(), cd.data_ptr())
+        else:
+            rows = torch.from_numpy(idx).cuda()
+            xw, lw = warm[0][rows].contiguous(), warm[1][rows].contiguous()
+            sh.load_slots_warm(sl, bd.data_ptr(), cd.data_ptr(), xw.data_ptr(), lw.data_ptr())
+        member[sl] = idx
+        age[sl] = 0
+        res = sh.residuals()
+        kkt0[idx] = [res[q]["kkt"] for q in sl]
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    enter(np.arange(slots))
+    done = 0
+    while done < count:
+        sh.iterate(check_every)
+        age += check_every
+        kkt = np.array([r["kkt"] for r in sh.residuals()])
+        met = kkt <= tol
+        fin = np.where((member >= 0) & (met | (age >= max_iter)))[0]
+        if len(fin):
+            iters[member[fin]] = np.where(met[fin], age[fin], -1)
+            if keep:
+                sh.slots_device(fin, Xs.data_ptr(), Ls.data_ptr())
+                rows = torch.from_numpy(member[fin]).cuda()
+                Xo[rows] = Xs[:len(fin)]
+                Lo[rows] = Ls[:len(fin)]
+            done += len(fin)
+            member[fin] = -1
+            k = min(len(fin), count - nxt)
+            if k:
+                enter(fin[:k])
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    sh.close()
+    return iters, kkt0, sec, Xo, Lo
+
+
+def evaluate(fam, net, theta, tol, max_iter, mu=1.0, check_every=100, precision="fp32", slots=256):
+    """Cold against learned warm start on the members theta (count x p, host), both solved by
+    continuous batching (solve_stream): per member, the iteration at which the relative KKT residual
+    first met tol (-1 if never within max_iter) and the KKT at entry, and the wall time for the whole
+    set (the warm arm includes the network's inference)."""
     import torch
     base = fam["base"]
     n, m = base["n"], base["m"]
-    count = theta.shape[0]
-    sh = mfs.Shared(base, count, mu=mu, check_every=check_every, precision=precision)
-    b, c = data_of(fam, theta)
     out = {}
-    # cold
-    sh.set_data(b, c)
-    r0 = [r["kkt"] for r in sh.residuals()]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    _, its = sh.solve(tol, max_iter)
-    torch.cuda.synchronize()
-    out["cold"] = {"iters": its, "seconds": time.perf_counter() - t0, "kkt0": np.asarray(r0)}
-    Xc = torch.empty((count, n), dtype=torch.float32, device="cuda")
-    Lc = torch.empty((count, m), dtype=torch.float32, device="cuda")
-    sh.solution_device(Xc.data_ptr(), Lc.data_ptr())
-    # warm
-    sh.set_data(b, c)
+    its, k0, sec, Xc, Lc = solve_stream(fam, theta, tol, max_iter, slots, check_every, None, mu, precision, keep=True)
+    out["cold"] = {"iters": its, "seconds": sec, "kkt0": k0}
     th = torch.from_numpy(np.ascontiguousarray(theta, np.float32)).cuda()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     Xw, Lw = predict(net, th, n, m)
-    sh.warm_start_device(Xw.data_ptr(), Lw.data_ptr())
     torch.cuda.synchronize()
     t_pred = time.perf_counter() - t0
-    r0 = [r["kkt"] for r in sh.residuals()]
-    t1 = time.perf_counter()
-    _, its = sh.solve(tol, max_iter)
-    torch.cuda.synchronize()
-    out["warm"] = {"iters": its, "seconds": t_pred + time.perf_counter() - t1, "predict_seconds": t_pred,
-                   "kkt0": np.asarray(r0)}
+    its, k0, sec, _, _ = solve_stream(fam, theta, tol, max_iter, slots, check_every, (Xw, Lw), mu, precision)
+    out["warm"] = {"iters": its, "seconds": t_pred + sec, "predict_seconds": t_pred, "kkt0": k0}
+    # prediction error against the point where the cold arm ended (per member)
     ex = (torch.linalg.vector_norm(Xw - Xc, dim=1) / torch.linalg.vector_norm(Xc, dim=1).clamp_min(1e-30)).cpu().numpy()
     el = (torch.linalg.vector_norm(Lw - Lc, dim=1) / torch.linalg.vector_norm(Lc, dim=1).clamp_min(1e-30)).cpu().numpy()
     out["pred_rel_err_x"], out["pred_rel_err_lam"] = ex, el
-    sh.close()
     return out
 
 

@@ -167,3 +167,37 @@ def test_full_family_sampled_members_match_oracle():
         sol = sh.solution(t)
         for k, o in (("x", st.x), ("z", st.z), ("delta", st.delta), ("lam", st.lam)):
             assert rel_err(sol[k], o) <= TOL["fp32"], (t, k, rel_err(sol[k], o))
+
+
+def test_warm_slots_enter_beside_cold_and_running_slots():
+    base = I.small_lp(6, m=120, n=300)
+    count = 40
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)
+    b, c = (f32(a) for a in family(base, count, 6))
+    b2, c2 = (f32(a) for a in family(base, 3, 7))
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((2, base["n"])).astype(np.float32)
+    L = rng.standard_normal((2, base["m"])).astype(np.float32)
+    sh = mfs.Shared(base, count, precision="fp64", check_every=10)
+    sh.set_data(b, c)
+    sh.iterate(30)
+    cold_slot = np.array([9], np.int32)
+    warm_slots = np.array([5, 22], np.int32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    bc, cc = dev(b2[2:3]), dev(c2[2:3])
+    bw, cw, Xw, Lw = dev(b2[:2]), dev(c2[:2]), dev(X), dev(L)
+    sh.load_slots(cold_slot, bc.data_ptr(), cc.data_ptr())
+    sh.load_slots_warm(warm_slots, bw.data_ptr(), cw.data_ptr(), Xw.data_ptr(), Lw.data_ptr())
+    sh.iterate(40)
+    checks = [(5, dict(base, b=b2[0], c=c2[0]), 40, (X[0], L[0])), (22, dict(base, b=b2[1], c=c2[1]), 40, (X[1], L[1])),
+              (9, dict(base, b=b2[2], c=c2[2]), 40, None), (0, dict(base, b=b[0], c=c[0]), 70, None),
+              (31, dict(base, b=b[31], c=c[31]), 70, None)]
+    for t, p, its, warm in checks:
+        orc = oracle.make_oracle(p)
+        if warm is not None:
+            orc.warm_start(warm[0].astype(np.float64), warm[1].astype(np.float64))
+        orc.iterate(its)
+        st = orc.state()
+        sol = sh.solution(t)
+        for k, o in (("x", st.x), ("z", st.z), ("delta", st.delta), ("lam", st.lam)):
+            assert rel_err(sol[k], o) <= TOL["fp64"], (t, k, rel_err(sol[k], o))

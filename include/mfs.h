@@ -60,6 +60,21 @@ enum { MFS_CONE_NONNEG = 0, MFS_CONE_SOC = 1 };
    FP64 iterations (see mfs_settings.polish_iters). */
 enum { MFS_FP64 = 0, MFS_FP32_MIXED = 1 };
 
+/* Stopping rule of mfs_solve (mfs_settings.stop_rule); each is "measure <= tol" on a field of
+   mfs_residuals_t. MFS_STOP_KKT: the relative KKT residual kkt (the default). MFS_STOP_SCS_L2:
+   r_scs, the l2 rule the paper uses against SCS (Sec. V-B). MFS_STOP_OSQP_INF: r_osqp, the
+   infinity-norm rule it uses against OSQP (Sec. V-A), without its gap clause, which compares with
+   the competing solver's own gap. */
+enum { MFS_STOP_KKT = 0, MFS_STOP_SCS_L2 = 1, MFS_STOP_OSQP_INF = 2 };
+
+/* Sweep kernels of the FP32 iteration (mfs_set_sweep). MFS_SWEEP_CHUNKED: one warp per chunk of
+   at most 256 nonzeros, the gathers served by L2 (every problem). MFS_SWEEP_STAGED: one CTA per
+   group of columns (rows), the gathered vector streamed through shared memory in 64 KB blocks and
+   the nonzeros stored sorted by block (FP32_MIXED solvers without Lorentz cones). MFS_SWEEP_AUTO
+   (default): the chunked kernels, the faster ones on the workloads measured. Both compute the same
+   iteration; their FP32 sums run in different orders. */
+enum { MFS_SWEEP_AUTO = 0, MFS_SWEEP_CHUNKED = 1, MFS_SWEEP_STAGED = 2 };
+
 typedef struct {
     int32_t kind;  /* MFS_CONE_NONNEG or MFS_CONE_SOC */
     int32_t pad_;  /* ignored */
@@ -72,19 +87,31 @@ typedef struct {
     int32_t precision;    /* MFS_FP64 (default) or MFS_FP32_MIXED */
     int32_t polish_iters; /* FP32_MIXED: FP64 iterations run by mfs_solve once the FP32 sweep has
                              met the tolerance, or early if it stalls (default 50) */
-    int32_t reserved;     /* must be 0 */
+    int32_t stop_rule;    /* MFS_STOP_KKT (default), MFS_STOP_SCS_L2 or MFS_STOP_OSQP_INF */
+    double osqp_rel;      /* MFS_STOP_OSQP_INF: eps_rel / eps_abs, > 0 (default 10: the paper's
+                             OSQP tolerances 1e-4 and 1e-3 at tol = 1e-4) */
 } mfs_settings;
 
 /* Residuals at the current (x, lambda); all accumulated in FP64.
    r_prim = ||Ax-b||_2/(1+||b||_2); r_cone = ||x-P_K x||_2/(1+||x||_2);
    r_dual = ||s-P_K s||_2/(1+||c||_2) with s = c + A^T lambda (K is self-dual, so this is the
    distance of the dual slack to the dual cone); r_gap = |c^T x + b^T lambda|/(1+|c^T x|+|b^T lambda|);
-   kkt = max of the four. The raw norms let a caller apply the paper's other stopping rules
-   (Sec. V: infinity-norm residuals, l2 residuals against (1+||b||), (1+||c||)). */
+   kkt = max of the four.
+   The paper's two other rules (Sec. V), read for a problem whose variable lies in a cone: the
+   constraint x in K joins the equality rows, its distance ||x - P_K x|| joining the primal residual,
+   and the dual residual c + A^T lambda is taken after subtracting its projection on K (the cone
+   multiplier), so that both vanish at an optimum of an LP or SOCP.
+   r_scs  = max( sqrt(||Ax-b||_2^2 + ||x-P_K x||_2^2)/(1+||b||_2), ||s-P_K s||_2/(1+||c||_2), r_gap );
+   r_osqp = max( max(||Ax-b||_inf, ||x-P_K x||_inf) / (1 + q max(||Ax||_inf, ||x||_inf, ||b||_inf)),
+                 ||s-P_K s||_inf / (1 + q max(||A^T lambda||_inf, ||c||_inf)) ),  q = settings.osqp_rel;
+   so that r_osqp <= tol is the paper's OSQP test with eps_abs = tol, eps_rel = q tol.
+   The raw norms follow (nrm_*: l2, inf_*: infinity norm). */
 typedef struct {
     double r_prim, r_dual, r_cone, r_gap, kkt, pobj, dobj;
     double nrm_res_p, nrm_b, nrm_xdist, nrm_x, nrm_sdist, nrm_c, nrm_atl_c;
     double inf_res_p, inf_ax, inf_b, inf_atl_c, inf_atl, inf_c;
+    double inf_x, inf_xdist, inf_sdist; /* ||x||_inf, ||x-P_K x||_inf, ||s-P_K s||_inf */
+    double r_scs, r_osqp;
     int64_t iter; /* iterations run since mfs_create or the last mfs_warm_start */
 } mfs_residuals_t;
 
@@ -95,9 +122,12 @@ typedef struct {
     int64_t bytes_per_iter;     /* algorithmic HBM bytes of one iteration at the current precision */
     int32_t precision;          /* precision the iterate is currently held in */
     int32_t launches_per_iter;  /* kernel launches of one iteration (sweeps, long chunks, big cones) */
+    int32_t sweep_col, sweep_row; /* MFS_SWEEP_CHUNKED or MFS_SWEEP_STAGED: kernels of the column and
+                                     row passes at the current precision */
 } mfs_info_t;
 
-/* Defaults: mu = 1, check_every = 25, precision = MFS_FP64, polish_iters = 50. */
+/* Defaults: mu = 1, check_every = 25, precision = MFS_FP64, polish_iters = 50, stop_rule =
+   MFS_STOP_KKT, osqp_rel = 10. */
 void mfs_default_settings(mfs_settings* s);
 
 /*
@@ -122,6 +152,18 @@ void mfs_destroy(mfs_solver* s);
 const char* mfs_last_error(const mfs_solver* s);
 
 mfs_status mfs_get_info(const mfs_solver* s, mfs_info_t* out);
+
+/* Choose the sweep kernels of the FP32 iteration: MFS_SWEEP_AUTO, MFS_SWEEP_CHUNKED or
+   MFS_SWEEP_STAGED (see above). MFS_ERR_INVALID for an unknown kind, or for MFS_SWEEP_STAGED on a
+   solver created in FP64 or with Lorentz cones. The iterate is kept; FP64 iterations always use
+   the chunked kernels. */
+mfs_status mfs_set_sweep(mfs_solver* s, int32_t kind);
+
+/* Diagnostic of the bounded waits of the staged sweeps: runs one staged column pass that issues
+   no copies and gives up after a few polls of each wait. Returns MFS_ERR_TIMEOUT when the kernel
+   reported the give-up (the expected result) and clears the flag; the FP32 iterate is overwritten
+   and must be reset (mfs_warm_start) before further use. MFS_ERR_INVALID without staged sweeps. */
+mfs_status mfs_debug_staged_wait_test(mfs_solver* s);
 
 /* Change mu (Algorithm 1 takes mu fixed; F_U and F_V do not depend on it, so no set-up is
    repeated). The iterate is kept. mu must be > 0. */
@@ -156,8 +198,9 @@ mfs_status mfs_warm_start_literal(mfs_solver* s, const double* x, const double* 
 mfs_status mfs_iterate(mfs_solver* s, int64_t k);
 
 /*
- * Iterate until the relative KKT residual (mfs_residuals_t.kkt) is <= tol, testing every
- * check_every iterations, or until max_iter more iterations have run. Returns MFS_OK (tolerance
+ * Iterate until the measure of the settings' stopping rule (mfs_residuals_t.kkt, .r_scs or
+ * .r_osqp) is <= tol, testing every check_every iterations, or until max_iter more iterations
+ * have run. Returns MFS_OK (tolerance
  * met) or MFS_MAX_ITER; MFS_ERR_NUMERIC if the residuals become NaN/Inf. iters_out (nullable)
  * receives the iterations run by this call. In FP32_MIXED mode the iterate switches to FP64
  * (and stays there) for the final polish_iters iterations, or as soon as the FP32 residual has

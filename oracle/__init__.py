@@ -29,6 +29,7 @@ RESID_FIELDS = (
     "r_prim", "r_dual", "r_cone", "r_gap", "kkt", "pobj", "dobj",
     "nrm_res_p", "nrm_b", "nrm_xdist", "nrm_x", "nrm_sdist", "nrm_c", "nrm_atl_c",
     "inf_res_p", "inf_ax", "inf_b", "inf_atl_c", "inf_atl", "inf_c",
+    "inf_x", "inf_xdist", "inf_sdist",
 )
 
 _lib = None
@@ -211,10 +212,36 @@ class Oracle:
         self._lib.orc_rmatvec(self._h, _dp(lam), _dp(out))
         return out
 
-    def residuals(self) -> dict:
+    def residuals(self, osqp_rel: float = 10.0) -> dict:
         out = np.empty(len(RESID_FIELDS))
         self._lib.orc_residuals(self._h, _dp(out))
-        return dict(zip(RESID_FIELDS, out.tolist()))
+        res = dict(zip(RESID_FIELDS, out.tolist()))
+        res.update(stop_measures(res, osqp_rel))
+        return res
+
+
+def stop_measures(res: dict, osqp_rel: float = 10.0) -> dict:
+    """The two other stopping rules of Sec. V as one number each ("stop when <= tol").
+
+    SCS (Sec. V-B): ||Ax - b||_2 <= eps (1 + ||b||_2), ||A^T lambda + c||_2 <= eps (1 + ||c||_2) and
+    the gap c^T x + b^T lambda <= eps (1 + |c^T x| + |b^T lambda|) (taken in absolute value). OSQP
+    (Sec. V-A): ||Ax - b||_inf < eps_prim and ||A^T lambda + c||_inf < eps_dual with
+    eps_prim = eps_abs + eps_rel max(||Ax||_inf, ||b||_inf),
+    eps_dual = eps_abs + eps_rel max(||A^T lambda||_inf, ||c||_inf); with eps_abs = eps and
+    eps_rel = osqp_rel * eps both become "ratio <= eps". Its extra clause, a gap below the
+    competing solver's, needs that solver and is left out.
+
+    Reading for variables in a cone K (the rules as printed are for the competitors' own problem
+    forms): the constraint x in K is a row block of its own, so its violation x - P_K x joins the
+    primal residual (and ||x||_inf the OSQP scale), and the dual residual s = A^T lambda + c is taken
+    after removing its part in K, the cone multiplier: s - P_K s.
+    """
+    p2 = np.hypot(res["nrm_res_p"], res["nrm_xdist"]) / (1.0 + res["nrm_b"])
+    d2 = res["nrm_sdist"] / (1.0 + res["nrm_c"])
+    r_scs = max(p2, d2, res["r_gap"])
+    pi = max(res["inf_res_p"], res["inf_xdist"]) / (1.0 + osqp_rel * max(res["inf_ax"], res["inf_x"], res["inf_b"]))
+    di = res["inf_sdist"] / (1.0 + osqp_rel * max(res["inf_atl"], res["inf_c"]))
+    return {"r_scs": float(r_scs), "r_osqp": float(max(pi, di))}
 
 
 def make_oracle(prob, mu=1.0, dtype=np.float64) -> Oracle:

@@ -351,6 +351,7 @@ void orc_rmatvec(const orc *P, const double *lam, double *ATl) {
  * 11 ||s-P_K s||_2    12 ||c||_2        13 ||A^T lambda + c||_2
  * 14 ||Ax-b||_inf     15 ||Ax||_inf     16 ||b||_inf
  * 17 ||A^T lambda + c||_inf             18 ||A^T lambda||_inf 19 ||c||_inf
+ * 20 ||x||_inf       21 ||x-P_K x||_inf 22 ||s-P_K s||_inf
  */
 void orc_residuals(const orc *P, double *out) {
     const int64_t m = P->m, n = P->n;
@@ -384,10 +385,13 @@ void orc_residuals(const orc *P, double *out) {
     for (int64_t i = 0; i < m; i++) btl += P->b[i] * P->lam[i];
     orc_proj_K(P, s, ps);
     orc_proj_K(P, P->x, px);
-    double ds2 = 0, dx2 = 0;
+    double ds2 = 0, dx2 = 0, dsinf = 0, dxinf = 0, xinf = 0;
     for (int64_t j = 0; j < n; j++) {
         ds2 += (s[j] - ps[j]) * (s[j] - ps[j]);
         dx2 += (P->x[j] - px[j]) * (P->x[j] - px[j]);
+        if (fabs(s[j] - ps[j]) > dsinf) dsinf = fabs(s[j] - ps[j]);
+        if (fabs(P->x[j] - px[j]) > dxinf) dxinf = fabs(P->x[j] - px[j]);
+        if (fabs(P->x[j]) > xinf) xinf = fabs(P->x[j]);
     }
     double nrp = sqrt(rp2), nb = sqrt(b2), nds = sqrt(ds2), nc = sqrt(c2), ndx = sqrt(dx2), nx = sqrt(x2);
     out[0] = nrp / (1.0 + nb);
@@ -403,5 +407,6 @@ void orc_residuals(const orc *P, double *out) {
     out[11] = nds; out[12] = nc; out[13] = sqrt(s2);
     out[14] = rpinf; out[15] = axinf; out[16] = binf;
     out[17] = sinf; out[18] = atlinf; out[19] = cinf;
+    out[20] = xinf; out[21] = dxinf; out[22] = dsinf;
     free(Ax); free(s); free(ps); free(px);
 }

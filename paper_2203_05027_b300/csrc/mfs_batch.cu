@@ -24,6 +24,7 @@
 #include "mfs_alloc.h"
 #include "mfs_device.cuh"
 #include "mfs_host.h"
+#include "mfs_measures.h"
 
 namespace {
 
@@ -33,7 +34,7 @@ using mfs::FULL;
 constexpr int MAXNT = 512;
 constexpr int MAXW = MAXNT / 32;
 constexpr int FVT = 64;  // column lengths with a tabulated F_V
-constexpr int NSTAT = 20;  // status block, same order as mfs_residuals_t
+constexpr int NSTAT = 23;  // status block, same order as mfs_residuals_t
 
 template <typename T>
 struct BatchArgs {
@@ -142,8 +143,9 @@ __device__ __forceinline__ void block_fold(double (&f)[NF], unsigned maxmask, do
 }
 
 // fields of the residual fold
-enum { RES2, RESMAX, AXMAX, B2, BMAX, BLAM, S2, SMAX, ATLMAX, C2, CMAX, CX, X2, SDIST2, XDIST2, NFLD };
-constexpr unsigned MAXMASK = (1u << RESMAX) | (1u << AXMAX) | (1u << BMAX) | (1u << SMAX) | (1u << ATLMAX) | (1u << CMAX);
+enum { RES2, RESMAX, AXMAX, B2, BMAX, BLAM, S2, SMAX, ATLMAX, C2, CMAX, CX, X2, SDIST2, XDIST2, XMAX, SDMAX, XDMAX, NFLD };
+constexpr unsigned MAXMASK = (1u << RESMAX) | (1u << AXMAX) | (1u << BMAX) | (1u << SMAX) | (1u << ATLMAX) | (1u << CMAX) |
+                           (1u << XMAX) | (1u << SDMAX) | (1u << XDMAX);
 
 struct Inst {
     int t, m, n, o, ns;
@@ -186,10 +188,13 @@ __device__ double instance_residuals(const BatchArgs<T>& a, const Inst& I, const
         f[CMAX] = fmax(f[CMAX], fabs(cj));
         f[CX] += cj * xj;
         f[X2] += xj * xj;
+        f[XMAX] = fmax(f[XMAX], fabs(xj));
         if (orthant) {
             const double sn = s < 0.0 ? s : 0.0, xn = xj < 0.0 ? xj : 0.0;
             f[SDIST2] += sn * sn;
             f[XDIST2] += xn * xn;
+            f[SDMAX] = fmax(f[SDMAX], -sn);
+            f[XDMAX] = fmax(f[XDMAX], -xn);
         }
         s_out = s;
     };
@@ -215,6 +220,8 @@ __device__ double instance_residuals(const BatchArgs<T>& a, const Inst& I, const
         }
         f[SDIST2] += lorentz_dist2(s1, sqrt(ss), ss + s1 * s1);
         f[XDIST2] += lorentz_dist2(x1, sqrt(xx), xx + x1 * x1);
+        f[SDMAX] = fmax(f[SDMAX], mfs::lorentz_distinf(s1, sqrt(ss)));
+        f[XDMAX] = fmax(f[XDMAX], mfs::lorentz_distinf(x1, sqrt(xx)));
     }
     block_fold<NFLD>(f, MAXMASK, sh);
     if (threadIdx.x == 0) {
@@ -243,6 +250,9 @@ __device__ double instance_residuals(const BatchArgs<T>& a, const Inst& I, const
         st[17] = f[SMAX];
         st[18] = f[ATLMAX];
         st[19] = f[CMAX];
+        st[20] = f[XMAX];
+        st[21] = f[XDMAX];
+        st[22] = f[SDMAX];
         for (int q = 0; q < NSTAT; ++q) out[q] = st[q];
         *s_kkt = kkt;
     }
@@ -935,6 +945,7 @@ mfs_status mfs_batch_residuals(mfs_batch* s, mfs_residuals_t* out) {
     for (int t = 0; t < s->count; ++t) {
         double* d = reinterpret_cast<double*>(&out[t]);
         for (int q = 0; q < NSTAT; ++q) d[q] = h[(size_t)t * NSTAT + q];
+        mfs::stop_measures(&out[t], s->set.osqp_rel);
         out[t].iter = it[t];
     }
     return MFS_OK;

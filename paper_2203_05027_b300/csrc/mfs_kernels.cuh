@@ -23,6 +23,7 @@
 #pragma once
 
 #include "mfs_device.cuh"
+#include "mfs_measures.h"
 
 // Minimum resident CTAs per SM requested for the FP32 sweep kernels (8 x 256 threads: 32 registers,
 // more warps to keep gathers in flight). The FP64 sweeps, ALU-bound, keep their full register budget.
@@ -419,14 +420,17 @@ __device__ __forceinline__ double warp_long_dot(const int* __restrict__ gidx, co
 // Row-side fields (sums of squares and maxima of |.|), column-side fields and big-cone fields;
 // each residual CTA writes one value per field, field-major: part[f * grid + cta].
 enum : int { R_RES2 = 0, R_RESMAX, R_AXMAX, R_B2, R_BMAX, R_BLAM, NFR };
-enum : int { C_S2 = 0, C_SMAX, C_ATLMAX, C_C2, C_CMAX, C_CX, C_X2, C_SDIST2, C_XDIST2, NFC };
-enum : int { B_SDIST2 = 0, B_XDIST2, NFB };
+enum : int { C_S2 = 0, C_SMAX, C_ATLMAX, C_C2, C_CMAX, C_CX, C_X2, C_SDIST2, C_XDIST2, C_XMAX, C_SDMAX, C_XDMAX, NFC };
+enum : int { B_SDIST2 = 0, B_XDIST2, B_SDMAX, B_XDMAX, NFB };
 
 __host__ __device__ constexpr bool row_field_is_max(int f) {
     return f == R_RESMAX || f == R_AXMAX || f == R_BMAX;
 }
 __host__ __device__ constexpr bool col_field_is_max(int f) {
-    return f == C_SMAX || f == C_ATLMAX || f == C_CMAX;
+    return f == C_SMAX || f == C_ATLMAX || f == C_CMAX || f == C_XMAX || f == C_SDMAX || f == C_XDMAX;
+}
+__host__ __device__ constexpr bool big_field_is_max(int f) {
+    return f == B_SDMAX || f == B_XDMAX;
 }
 
 // Squared distance of w to one Lorentz cone, given w_1 and alpha = ||w_{2..}||
@@ -595,11 +599,14 @@ __global__ void __launch_bounds__(NT) k_col_resid(const SweepArgs<T> a, const Re
             f[C_CMAX] = fmax(f[C_CMAX], fabs(cj));
             f[C_CX] += cj * xj;
             f[C_X2] += xj * xj;
+            f[C_XMAX] = fmax(f[C_XMAX], fabs(xj));
             const int tag = SOC ? cone_tag(a, ch, j) : 0;
             if (tag == 0) {
                 const double sn = s < 0.0 ? s : 0.0, xn = xj < 0.0 ? xj : 0.0;
                 f[C_SDIST2] += sn * sn;
                 f[C_XDIST2] += xn * xn;
+                f[C_SDMAX] = fmax(f[C_SDMAX], -sn);
+                f[C_XDMAX] = fmax(f[C_XDMAX], -xn);
             } else if (tag == 1) {
                 s_cone[SOC ? warp : 0][0][jl] = s;
                 s_cone[SOC ? warp : 0][1][jl] = xj;
@@ -625,8 +632,11 @@ __global__ void __launch_bounds__(NT) k_col_resid(const SweepArgs<T> a, const Re
                 }
                 if (lane == 0) {
                     const double s1 = cs_[c0], x1 = cx_[c0];
-                    f[C_SDIST2] += lorentz_dist2(s1, sqrt(ss), ss + s1 * s1);
-                    f[C_XDIST2] += lorentz_dist2(x1, sqrt(xx), xx + x1 * x1);
+                    const double as = sqrt(ss), ax = sqrt(xx);
+                    f[C_SDIST2] += lorentz_dist2(s1, as, ss + s1 * s1);
+                    f[C_XDIST2] += lorentz_dist2(x1, ax, xx + x1 * x1);
+                    f[C_SDMAX] = fmax(f[C_SDMAX], mfs::lorentz_distinf(s1, as));
+                    f[C_XDMAX] = fmax(f[C_XDMAX], mfs::lorentz_distinf(x1, ax));
                 }
             }
             __syncwarp();
@@ -652,8 +662,11 @@ __global__ void __launch_bounds__(NT) k_bigcone_resid(const SweepArgs<T> a, cons
     acc = block_sum<double, 2>(acc, sh);
     if (threadIdx.x == 0) {
         const double s1 = r.s_buf[st], x1 = double(a.x[st]);
-        r.part_big[(size_t)B_SDIST2 * nbig + bq] = lorentz_dist2(s1, sqrt(acc.v[0]), acc.v[0] + s1 * s1);
-        r.part_big[(size_t)B_XDIST2 * nbig + bq] = lorentz_dist2(x1, sqrt(acc.v[1]), acc.v[1] + x1 * x1);
+        const double as = sqrt(acc.v[0]), ax = sqrt(acc.v[1]);
+        r.part_big[(size_t)B_SDIST2 * nbig + bq] = lorentz_dist2(s1, as, acc.v[0] + s1 * s1);
+        r.part_big[(size_t)B_XDIST2 * nbig + bq] = lorentz_dist2(x1, ax, acc.v[1] + x1 * x1);
+        r.part_big[(size_t)B_SDMAX * nbig + bq] = mfs::lorentz_distinf(s1, as);
+        r.part_big[(size_t)B_XDMAX * nbig + bq] = mfs::lorentz_distinf(x1, ax);
     }
 }
 
@@ -662,7 +675,8 @@ enum : int {
     S_RPRIM = 0, S_RDUAL, S_RCONE, S_RGAP, S_KKT, S_POBJ, S_DOBJ,
     S_NRES, S_NB, S_NXDIST, S_NX, S_NSDIST, S_NC, S_NATLC,
     S_IRES, S_IAX, S_IB, S_IATLC, S_IATL, S_IC,
-    NSTATUS = 20
+    S_IX, S_IXDIST, S_ISDIST,
+    NSTATUS = 23
 };
 
 __device__ __forceinline__ double nanmax(double p, double q) {
@@ -692,7 +706,7 @@ __global__ void __launch_bounds__(32 * NFALL) k_resid_finalize(const double* par
     } else {
         src = part_big + (size_t)(k - NFR - NFC) * nbig;
         cnt = nbig;
-        ismax = false;
+        ismax = big_field_is_max(k - NFR - NFC);
     }
     double acc = 0.0;
     for (int i = lane; i < cnt; i += 32) acc = ismax ? nanmax(acc, src[i]) : acc + src[i];
@@ -731,6 +745,9 @@ __global__ void __launch_bounds__(32 * NFALL) k_resid_finalize(const double* par
         status[S_IATLC] = C[C_SMAX];
         status[S_IATL] = C[C_ATLMAX];
         status[S_IC] = C[C_CMAX];
+        status[S_IX] = C[C_XMAX];
+        status[S_IXDIST] = nanmax(C[C_XDMAX], B[B_XDMAX]);
+        status[S_ISDIST] = nanmax(C[C_SDMAX], B[B_SDMAX]);
     }
 }
 

@@ -21,6 +21,7 @@
 #include "../../include/mfs.h"
 #include "mfs_alloc.h"
 #include "mfs_device.cuh"
+#include "mfs_measures.h"
 
 namespace {
 
@@ -29,7 +30,7 @@ using mfs::FULL;
 
 constexpr int SNT = 256;           // threads per CTA
 constexpr int SW = SNT / 32;       // warps per CTA
-constexpr int NSTAT = 20;
+constexpr int NSTAT = 23;
 
 template <typename T>
 struct SArgs {
@@ -243,9 +244,10 @@ struct AccT<double> {
 __device__ __forceinline__ DF acc_mul(float x, float y) { return mfs::df_prod(x, y); }
 __device__ __forceinline__ double acc_mul(double x, double y) { return x * y; }
 
-enum { RES2, RESMAX, AXMAX, B2, BMAX, BLAM, S2, SMAX, ATLMAX, C2, CMAX, CX, X2, SDIST2, XDIST2, NFLD };
+enum { RES2, RESMAX, AXMAX, B2, BMAX, BLAM, S2, SMAX, ATLMAX, C2, CMAX, CX, X2, SDIST2, XDIST2, XMAX, SDMAX, XDMAX, NFLD };
 __host__ __device__ constexpr bool is_max(int f) {
-    return f == RESMAX || f == AXMAX || f == BMAX || f == SMAX || f == ATLMAX || f == CMAX;
+    return f == RESMAX || f == AXMAX || f == BMAX || f == SMAX || f == ATLMAX || f == CMAX || f == XMAX || f == SDMAX ||
+           f == XDMAX;
 }
 
 // Per-instance residual fields. grid (G, Bp/32); warp w of block (g, q) takes rows (columns,
@@ -286,6 +288,7 @@ __global__ void __launch_bounds__(SNT) k_s_resid(const SArgs<T> a, double* part,
         f[CMAX] = fmax(f[CMAX], fabs(cj));
         f[CX] += cj * xj;
         f[X2] += xj * xj;
+        f[XMAX] = fmax(f[XMAX], fabs(xj));
         if (s_out) s_out[p] = T(sv);
         return sv;
     };
@@ -296,6 +299,8 @@ __global__ void __launch_bounds__(SNT) k_s_resid(const SArgs<T> a, double* part,
             const double sn = sv < 0.0 ? sv : 0.0, xn = xj < 0.0 ? xj : 0.0;
             f[SDIST2] += sn * sn;
             f[XDIST2] += xn * xn;
+            f[SDMAX] = fmax(f[SDMAX], -sn);
+            f[XDMAX] = fmax(f[XDMAX], -xn);
         }
     }
     for (int q = blockIdx.x * SW + warp; q < a.nsoc; q += G * SW) {
@@ -319,6 +324,8 @@ __global__ void __launch_bounds__(SNT) k_s_resid(const SArgs<T> a, double* part,
         }
         f[SDIST2] += lorentz_dist2(s1, sqrt(ss), ss + s1 * s1);
         f[XDIST2] += lorentz_dist2(x1, sqrt(xx), xx + x1 * x1);
+        f[SDMAX] = fmax(f[SDMAX], mfs::lorentz_distinf(s1, sqrt(ss)));
+        f[XDMAX] = fmax(f[XDMAX], mfs::lorentz_distinf(x1, sqrt(xx)));
     }
 #pragma unroll
     for (int k = 0; k < NFLD; ++k) sh[warp][k][lane] = f[k];
@@ -369,6 +376,9 @@ __global__ void k_s_finalize(const double* part, int G, int Bp, int B, double* s
     st[17] = f[SMAX];
     st[18] = f[ATLMAX];
     st[19] = f[CMAX];
+    st[20] = f[XMAX];
+    st[21] = f[XDMAX];
+    st[22] = f[SDMAX];
 }
 
 // [count][len] instance-major (FP32 or FP64 source) -> [len][Bp] interleaved T, and back.
@@ -1056,6 +1066,7 @@ mfs_status mfs_shared_residuals(mfs_shared* s, mfs_residuals_t* out) {
     for (int t = 0; t < s->B; ++t) {
         double* d = reinterpret_cast<double*>(&out[t]);
         for (int q = 0; q < NSTAT; ++q) d[q] = s->h_status[(size_t)t * NSTAT + q];
+        mfs::stop_measures(&out[t], s->set.osqp_rel);
         out[t].iter = s->iter;
     }
     return MFS_OK;

@@ -12,16 +12,21 @@
 #include <limits>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/mfs.h"
 #include "mfs_alloc.h"
 #include "mfs_host.h"
 #include "mfs_kernels.cuh"
+#include "mfs_staged.cuh"
 #include "mfs_infeas.cuh"
 #include "mfs_literal.cuh"
+#include "mfs_measures.h"
 
 using namespace mfs;
+
+using StagedArgsT = mfs::staged::StagedArgs;
 
 namespace {
 
@@ -104,6 +109,12 @@ struct mfs_solver {
     int *lit_krow = nullptr, *lit_kcol = nullptr, *lit_perm = nullptr, *lit_rp = nullptr;
     double* lit_zarg = nullptr;
     std::vector<void*> lit_mem;
+    // staged FP32 sweeps (mfs_staged.cuh): built at create for FP32 problems without Lorentz cones
+    bool stg_ok = false;
+    int sweep_kind = MFS_SWEEP_AUTO;
+    mfs::staged::StagedArgs stg_col{}, stg_row{};
+    int* stg_err = nullptr;
+    int* h_err = nullptr;  // pinned
     std::vector<void*> allocs;
     std::string last_error;
 };
@@ -306,6 +317,150 @@ void build_chunks(const std::vector<int>& ptr, int nseg, const std::vector<int>*
     if (cur_seg > 0) close(nseg);
 }
 
+inline int float_bits(float f) {
+    int i;
+    std::memcpy(&i, &f, sizeof i);
+    return i;
+}
+
+// Layout of one staged pass (mfs_staged.cuh) on the host.
+struct StagedHost {
+    mfs::host::uvec<int2> ent;
+    std::vector<int> split, grp, wseg;
+    int G = 0, R = 0, maxg = 0;
+};
+
+// Segments (columns with their row indices, or rows with their column indices) in groups of
+// consecutive segments balanced by nonzeros (nominally `groups`, at most MAXG segments each); each
+// group's nonzeros sorted by (block of the gathered index, segment, gathered index) -- a stable
+// counting sort of the segment order -- and the warp ranges of every (group, block) cut at segment
+// boundaries.
+// rb: entries of the gathered vector per block; smem_limit: shared memory a CTA may use, which
+// bounds the group size. Returns false if not even small groups fit.
+bool build_staged(const std::vector<int>& ptr, const mfs::host::uvec<int>& idx, const mfs::host::uvec<double>& val,
+                  int nseg, int nother, int groups, int rb, int stages, size_t smem_limit, StagedHost& S) {
+    using namespace mfs::host;
+    using mfs::staged::NW;
+    const int RB = rb;
+    const int64_t o = ptr[nseg];
+    S.R = std::max(1, (nother + RB - 1) / RB);
+    const size_t fixed = mfs::staged::smem_bytes(RB, stages, 0, S.R);
+    if (fixed + 4096 * 4 > smem_limit) return false;
+    const int MAXG = (int)std::min<size_t>(mfs::staged::MAXG, (smem_limit - fixed) / 16 * 4);
+    S.grp.assign(1, 0);
+    int lo = 0;
+    for (int g = 1; g <= groups; ++g) {
+        int hi = nseg;
+        if (g < groups) {
+            const int target = (int)(o * g / groups);
+            hi = (int)(std::lower_bound(ptr.begin(), ptr.begin() + nseg + 1, target) - ptr.begin());
+            hi = std::min(std::max(hi, lo), nseg);
+        }
+        while (hi - lo > MAXG) {
+            lo += MAXG;
+            S.grp.push_back(lo);
+        }
+        if (hi > lo) {
+            S.grp.push_back(hi);
+            lo = hi;
+        }
+    }
+    if (S.grp.size() == 1) S.grp.push_back(nseg);
+    S.G = (int)S.grp.size() - 1;
+    S.maxg = 0;
+    for (int g = 0; g < S.G; ++g) S.maxg = std::max(S.maxg, S.grp[g + 1] - S.grp[g]);
+    const int R = S.R, G = S.G;
+    // each warp's segments within its group, balanced by nonzeros
+    S.wseg.resize((size_t)G * (NW + 1));
+    for (int g = 0; g < G; ++g) {
+        const int a = S.grp[g], e = S.grp[g + 1];
+        const int64_t nz = (int64_t)ptr[e] - ptr[a];
+        int* w = S.wseg.data() + (size_t)g * (NW + 1);
+        w[0] = 0;
+        for (int q = 1; q < NW; ++q) {
+            const int target = (int)(ptr[a] + nz * q / NW);
+            const int at = (int)(std::lower_bound(ptr.begin() + a, ptr.begin() + e + 1, target) - ptr.begin());
+            w[q] = std::max(w[q - 1], std::min(at, e) - a);
+        }
+        w[NW] = e - a;
+    }
+    uvec<int> key((size_t)o), loc((size_t)o);
+    parallel_ranges(G, std::min(threads_for(o), G), [&](int64_t g0, int64_t g1, int) {
+        for (int64_t g = g0; g < g1; ++g)
+            for (int sg = S.grp[g]; sg < S.grp[g + 1]; ++sg)
+                for (int q = ptr[sg]; q < ptr[sg + 1]; ++q) {
+                    key[q] = (int)g * R + idx[q] / RB;
+                    loc[q] = sg - S.grp[g];
+                }
+    });
+    uvec<int64_t> perm((size_t)o);
+    std::vector<int64_t> starts;
+    counting_sort(o, (int64_t)G * R, [&](int64_t q) { return (int64_t)key[q]; }, nullptr, perm.data(), &starts);
+    S.ent.resize((size_t)o);
+    parallel_ranges(o, threads_for(o), [&](int64_t p0, int64_t p1, int) {
+        for (int64_t p = p0; p < p1; ++p) {
+            const int64_t q = perm[p];
+            const int blk = key[q] % R;
+            const float a = (float)val[q];
+            S.ent[p] = make_int2(loc[q] | ((idx[q] - blk * RB) << 16), float_bits(a));
+        }
+    });
+    S.split.resize((size_t)G * R * (NW + 1));
+    parallel_ranges((int64_t)G * R, threads_for(o), [&](int64_t u0, int64_t u1, int) {
+        for (int64_t u = u0; u < u1; ++u) {
+            // warp w takes the entries of its own segments: the first entry at or after wseg[w]
+            const int st = (int)starts[u], en = (int)starts[u + 1];
+            const int* w = S.wseg.data() + (size_t)(u / R) * (NW + 1);
+            int* sp = S.split.data() + u * (NW + 1);
+            sp[0] = st;
+            for (int q = 1; q < NW; ++q) {
+                int lo2 = sp[q - 1], hi2 = en;
+                while (lo2 < hi2) {
+                    const int mid = (lo2 + hi2) >> 1;
+                    if ((S.ent[mid].x & 0xFFFF) < w[q])
+                        lo2 = mid + 1;
+                    else
+                        hi2 = mid;
+                }
+                sp[q] = lo2;
+            }
+            sp[NW] = en;
+        }
+    });
+    // pad every warp range to a multiple of LANE_E entries (zero values, the range's last segment, so
+    // they fall into its last sum) so that a lane loads its LANE_E entries with one 32-byte load
+    constexpr int LE = mfs::staged::LANE_E;
+    std::vector<int64_t> pstart((size_t)G * R + 1, 0);
+    parallel_ranges((int64_t)G * R, threads_for(o), [&](int64_t u0, int64_t u1, int) {
+        for (int64_t u = u0; u < u1; ++u) {
+            const int* sp = S.split.data() + u * (NW + 1);
+            int64_t len = 0;
+            for (int w = 0; w < NW; ++w) len += (sp[w + 1] - sp[w] + LE - 1) / LE * LE;
+            pstart[u + 1] = len;
+        }
+    });
+    for (int64_t u = 0; u < (int64_t)G * R; ++u) pstart[u + 1] += pstart[u];
+    const int64_t plen = pstart[(size_t)G * R];
+    if (plen >= INT32_MAX) return false;
+    uvec<int2> pent((size_t)plen);
+    parallel_ranges((int64_t)G * R, threads_for(o), [&](int64_t u0, int64_t u1, int) {
+        for (int64_t u = u0; u < u1; ++u) {
+            int* sp = S.split.data() + u * (NW + 1);
+            int64_t at = pstart[u];
+            for (int w = 0; w < NW; ++w) {
+                const int a = sp[w], e = sp[w + 1];
+                sp[w] = (int)at;
+                for (int q = a; q < e; ++q) pent[at++] = S.ent[q];
+                if (e > a)
+                    for (int q = e; (q - a) % LE != 0; ++q) pent[at++] = make_int2(S.ent[e - 1].x & 0xFFFF, 0);
+            }
+            sp[NW] = (int)at;
+        }
+    });
+    S.ent.swap(pent);
+    return true;
+}
+
 mfs_status setup_host(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
                       const double* val, int64_t ncones, const mfs_cone* cones, HostProblem& P) {
     build_orders(m, n, nnz, row, col, val, P);
@@ -440,6 +595,15 @@ mfs_status residual_grids(mfs_solver* s) {
 
 // ---------------------------------------------------------------------------------- launches
 
+// Staged passes in use (FP32 iterate): only on request; the automatic choice is the chunked sweeps,
+// which are faster on every workload measured so far.
+bool staged_col(const mfs_solver* s) {
+    return s->stg_ok && s->sweep_kind == MFS_SWEEP_STAGED;
+}
+bool staged_row(const mfs_solver* s) {
+    return s->stg_ok && s->sweep_kind == MFS_SWEEP_STAGED;
+}
+
 inline int warp_grid(int nchunks) {
     return (nchunks + NWARP - 1) / NWARP;
 }
@@ -447,6 +611,15 @@ inline int warp_grid(int nchunks) {
 template <typename T>
 void launch_col(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
     if (s->ncc == 0) return;
+    if constexpr (std::is_same<T, float>::value) {
+        if (staged_col(s)) {
+            const StagedArgsT& g = s->stg_col;
+            MFS_STAGED_COL<<<std::min(g.G, s->num_sms), mfs::staged::NTS + 32,
+                             mfs::staged::smem_bytes(mfs::staged::RB_COL, mfs::staged::S_COL, g.maxg_pad, g.R), st>>>(g,
+                                                                                                                     a);
+            return;
+        }
+    }
     if (s->has_soc) {
         k_col_sweep<T, true><<<warp_grid(s->ncc), NT, 0, st>>>(a);
         if (s->nlc) k_col_long<T, true><<<s->nlc, NT, 0, st>>>(a);
@@ -462,6 +635,15 @@ void launch_big(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
 template <typename T, int MODE>
 void launch_row_mode(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
     if (s->nrc == 0) return;
+    if constexpr (std::is_same<T, float>::value && MODE == 0) {
+        if (staged_row(s)) {
+            const StagedArgsT& g = s->stg_row;
+            MFS_STAGED_ROW<<<std::min(g.G, s->num_sms), mfs::staged::NTS + 32,
+                             mfs::staged::smem_bytes(mfs::staged::RB_ROW, mfs::staged::S_ROW, g.maxg_pad, g.R), st>>>(g,
+                                                                                                                     a);
+            return;
+        }
+    }
     k_row_sweep<T, MODE><<<warp_grid(s->nrc), NT, 0, st>>>(a);
     if (s->nlr) k_row_long<T, MODE><<<s->nlr, NT, 0, st>>>(a);
 }
@@ -482,7 +664,10 @@ void launch_iteration(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
 }
 
 int launches_per_iteration(const mfs_solver* s) {
-    return (s->ncc ? 1 + (s->nlc ? 1 : 0) : 0) + (s->nbig ? 1 : 0) + (s->nrc ? 1 + (s->nlr ? 1 : 0) : 0);
+    const bool f32 = s->precision == MFS_FP32_MIXED;
+    const int col = s->ncc ? ((f32 && staged_col(s)) ? 1 : 1 + (s->nlc ? 1 : 0)) : 0;
+    const int row = s->nrc ? ((f32 && staged_row(s)) ? 1 : 1 + (s->nlr ? 1 : 0)) : 0;
+    return col + (s->nbig ? 1 : 0) + row;
 }
 
 template <typename T>
@@ -520,6 +705,10 @@ mfs_status run_iters(mfs_solver* s, State<T>& st, int64_t k) {
     return MFS_OK;
 }
 
+double stop_measure(const mfs_residuals_t& r, int rule) {
+    return rule == MFS_STOP_SCS_L2 ? r.r_scs : rule == MFS_STOP_OSQP_INF ? r.r_osqp : r.kkt;
+}
+
 template <typename T>
 mfs_status residuals_t(mfs_solver* s, State<T>& st, mfs_residuals_t* out, bool write_all_s) {
     SweepArgs<T> a = sweep_args(s, st);
@@ -545,7 +734,10 @@ mfs_status residuals_t(mfs_solver* s, State<T>& st, mfs_residuals_t* out, bool w
     if (out) {
         CUDA_TRY(s, cudaMemcpyAsync(s->h_status, s->status, NSTATUS * sizeof(double), cudaMemcpyDeviceToHost,
                                     s->stream));
+        if (s->stg_ok) CUDA_TRY(s, cudaMemcpyAsync(s->h_err, s->stg_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
         CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+        if (s->stg_ok && *s->h_err)
+            return fail(s, MFS_ERR_TIMEOUT, "a staged sweep gave up waiting for a block of its vector");
         const double* h = s->h_status;
         out->r_prim = h[S_RPRIM];
         out->r_dual = h[S_RDUAL];
@@ -567,6 +759,10 @@ mfs_status residuals_t(mfs_solver* s, State<T>& st, mfs_residuals_t* out, bool w
         out->inf_atl_c = h[S_IATLC];
         out->inf_atl = h[S_IATL];
         out->inf_c = h[S_IC];
+        out->inf_x = h[S_IX];
+        out->inf_xdist = h[S_IXDIST];
+        out->inf_sdist = h[S_ISDIST];
+        mfs::stop_measures(out, s->set.osqp_rel);
         out->iter = s->iter;
     }
     return MFS_OK;
@@ -615,11 +811,14 @@ mfs_status warm_start_t(mfs_solver* s, State<T>& st, const double* x, const doub
 
 template <typename T>
 mfs_status alloc_state(mfs_solver* s, State<T>& st, const HostProblem& P, const double* b, const double* c) {
-    TRY(dalloc(s, &st.x, s->n));
+    // x and v, the vectors the staged sweeps copy in whole blocks, are padded to a multiple of the block
+    const int64_t npad = (int64_t)(s->n + mfs::staged::RB_ROW - 1) / mfs::staged::RB_ROW * mfs::staged::RB_ROW;
+    const int64_t mpad = (int64_t)(s->m + mfs::staged::RB_COL - 1) / mfs::staged::RB_COL * mfs::staged::RB_COL;
+    TRY(dalloc(s, &st.x, npad));
     TRY(dalloc(s, &st.z, s->n));
     TRY(dalloc(s, &st.del, s->n));
     TRY(dalloc(s, &st.lam, s->m));
-    TRY(dalloc(s, &st.v, s->m));
+    TRY(dalloc(s, &st.v, mpad));
     std::vector<T> hb(b, b + s->m), hc(c, c + s->n);
     TRY(upload(s, &st.b, hb.data(), hb.size()));
     TRY(upload(s, &st.c, hc.data(), hc.size()));
@@ -628,13 +827,72 @@ mfs_status alloc_state(mfs_solver* s, State<T>& st, const HostProblem& P, const 
     TRY(upload(s, &st.cval, pval.data(), pval.size()));
     pad_chunks<T>(P.rc, P.row_ptr, P.csr_col, P.csr_val, (mfs::host::uvec<int>*)nullptr, &pval);
     TRY(upload(s, &st.rval, pval.data(), pval.size()));
-    CUDA_TRY(s, cudaMemsetAsync(st.x, 0, sizeof(T) * std::max(s->n, 1), s->stream));
+    CUDA_TRY(s, cudaMemsetAsync(st.x, 0, sizeof(T) * std::max<int64_t>(npad, 1), s->stream));
     CUDA_TRY(s, cudaMemsetAsync(st.z, 0, sizeof(T) * std::max(s->n, 1), s->stream));
     CUDA_TRY(s, cudaMemsetAsync(st.del, 0, sizeof(T) * std::max(s->n, 1), s->stream));
     CUDA_TRY(s, cudaMemsetAsync(st.lam, 0, sizeof(T) * std::max(s->m, 1), s->stream));
-    CUDA_TRY(s, cudaMemsetAsync(st.v, 0, sizeof(T) * std::max(s->m, 1), s->stream));
+    CUDA_TRY(s, cudaMemsetAsync(st.v, 0, sizeof(T) * std::max<int64_t>(mpad, 1), s->stream));
     return MFS_OK;
 }
+
+// Staged sweeps for an FP32 problem with orthant cones only: both layouts, the row norms, the
+// kernels' shared-memory limits; the automatic choice takes a staged pass when the matrix is large
+// and the gathered vector small against its nonzeros (every CTA reads the whole vector).
+mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
+    using namespace mfs::staged;
+    int optin = 0;
+    CUDA_TRY(s, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
+    StagedHost C, W;
+    if (!build_staged(P.col_ptr, P.csc_row, P.csc_val, P.n, P.m, s->num_sms, RB_COL, S_COL, (size_t)optin, C) ||
+        !build_staged(P.row_ptr, P.csr_col, P.csr_val, P.m, P.n, s->num_sms, RB_ROW, S_ROW, (size_t)optin, W))
+        return MFS_OK;  // vectors too long for the split tables: chunked sweeps only
+    std::vector<float> rsq(std::max(P.m, 1), 0.f);
+    mfs::host::parallel_ranges(P.m, mfs::host::threads_for(P.o), [&](int64_t i0, int64_t i1, int) {
+        for (int64_t i = i0; i < i1; ++i) {
+            double r = 0.0;
+            for (int q = P.row_ptr[i]; q < P.row_ptr[i + 1]; ++q) {
+                const double a = (double)(float)P.csr_val[q];
+                r += a * a;
+            }
+            rsq[i] = (float)r;
+        }
+    });
+    TRY(dalloc(s, &s->stg_err, 1));
+    CUDA_TRY(s, cudaMemsetAsync(s->stg_err, 0, sizeof(int), s->stream));
+    CUDA_TRY(s, cudaMallocHost(&s->h_err, sizeof(int)));
+    *s->h_err = 0;
+    auto fill = [&](StagedHost& H, StagedArgs& g, const float* vec) -> mfs_status {
+        int2* ent = nullptr;
+        int *split = nullptr, *grp = nullptr, *wseg = nullptr;
+        TRY(upload(s, &ent, H.ent.data(), H.ent.size()));
+        TRY(upload(s, &split, H.split.data(), H.split.size()));
+        TRY(upload(s, &grp, H.grp.data(), H.grp.size()));
+        TRY(upload(s, &wseg, H.wseg.data(), H.wseg.size()));
+        g.ent = ent;
+        g.split = split;
+        g.grp = grp;
+        g.wseg = wseg;
+        g.vec = vec;
+        g.err = s->stg_err;
+        g.G = H.G;
+        g.R = H.R;
+        g.maxg_pad = (H.maxg + 3) / 4 * 4;
+        g.spin = 1 << 24;
+        g.no_loads = 0;
+        return MFS_OK;
+    };
+    TRY(fill(C, s->stg_col, s->s32.v));
+    TRY(fill(W, s->stg_row, s->s32.x));
+    float* d_rsq = nullptr;
+    TRY(upload(s, &d_rsq, rsq.data(), rsq.size()));
+    s->stg_row.rsq = d_rsq;
+    // the limit is a property of the kernel, shared by all solvers: allow the device's maximum
+    CUDA_TRY(s, cudaFuncSetAttribute(MFS_STAGED_COL, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    CUDA_TRY(s, cudaFuncSetAttribute(MFS_STAGED_ROW, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    s->stg_ok = true;
+    return MFS_OK;
+}
+
 
 template <typename D, typename S>
 void copy_state(mfs_solver* s, State<D>& dst, State<S>& src) {
@@ -985,7 +1243,8 @@ void mfs_default_settings(mfs_settings* st) {
     st->check_every = 25;
     st->precision = MFS_FP64;
     st->polish_iters = 50;
-    st->reserved = 0;
+    st->stop_rule = MFS_STOP_KKT;
+    st->osqp_rel = 10.0;
 }
 
 const char* mfs_last_error(const mfs_solver* s) {
@@ -1000,6 +1259,7 @@ void mfs_destroy(mfs_solver* s) {
     literal_free(s);
     for (void* p : s->allocs) cudaFree(p);
     if (s->h_status) cudaFreeHost(s->h_status);
+    if (s->h_err) cudaFreeHost(s->h_err);
     if (s->cap) cudaStreamDestroy(s->cap);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
@@ -1024,6 +1284,10 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
     if (set.precision != MFS_FP64 && set.precision != MFS_FP32_MIXED)
         return fail(nullptr, MFS_ERR_INVALID, "unknown precision");
     if (set.polish_iters < 0) return fail(nullptr, MFS_ERR_INVALID, "polish_iters must be >= 0");
+    if (set.stop_rule != MFS_STOP_KKT && set.stop_rule != MFS_STOP_SCS_L2 && set.stop_rule != MFS_STOP_OSQP_INF)
+        return fail(nullptr, MFS_ERR_INVALID, "unknown stop_rule");
+    if (!(set.osqp_rel > 0.0) || !std::isfinite(set.osqp_rel))
+        return fail(nullptr, MFS_ERR_INVALID, "osqp_rel must be > 0");
     int64_t total = 0;
     for (int64_t q = 0; q < ncones; ++q) {
         if (cones[q].size < 1) return fail(nullptr, MFS_ERR_INVALID, "cone of size < 1");
@@ -1136,6 +1400,7 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
         CHK(alloc_state<float>(s, s->s32, P, b, c));
         CHK(residual_grids<float>(s));
         s->have32 = true;
+        if (!s->has_soc && P.o > 0) CHK(setup_staged(s, P));
     }
     if (set.precision == MFS_FP64 || set.polish_iters > 0) {
         CHK(alloc_state<double>(s, s->s64, P, b, c));
@@ -1176,6 +1441,41 @@ mfs_status mfs_get_info(const mfs_solver* s, mfs_info_t* out) {
     out->bytes_per_iter = bytes_per_iter(s, s->precision);
     out->precision = s->precision;
     out->launches_per_iter = launches_per_iteration(s);
+    const bool f32 = s->precision == MFS_FP32_MIXED;
+    out->sweep_col = (f32 && staged_col(s)) ? MFS_SWEEP_STAGED : MFS_SWEEP_CHUNKED;
+    out->sweep_row = (f32 && staged_row(s)) ? MFS_SWEEP_STAGED : MFS_SWEEP_CHUNKED;
+    return MFS_OK;
+}
+
+mfs_status mfs_debug_staged_wait_test(mfs_solver* s) {
+    if (!s) return MFS_ERR_INVALID;
+    if (!s->stg_ok) return fail(s, MFS_ERR_INVALID, "no staged sweeps on this solver");
+    CUDA_TRY(s, cudaSetDevice(s->device));
+    StagedArgsT g = s->stg_col;
+    g.spin = 64;
+    g.no_loads = 1;
+    const SweepArgs<float> a = sweep_args(s, s->s32);
+    MFS_STAGED_COL<<<std::min(g.G, s->num_sms), mfs::staged::NTS + 32,
+                     mfs::staged::smem_bytes(mfs::staged::RB_COL, mfs::staged::S_COL, g.maxg_pad, g.R), s->stream>>>(g, a);
+    CUDA_TRY(s, cudaGetLastError());
+    CUDA_TRY(s, cudaMemcpyAsync(s->h_err, s->stg_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(s, cudaMemsetAsync(s->stg_err, 0, sizeof(int), s->stream));
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    const int flagged = *s->h_err;
+    *s->h_err = 0;
+    return flagged ? fail(s, MFS_ERR_TIMEOUT, "staged sweep: wait for a block gave up (diagnostic)") : MFS_OK;
+}
+
+mfs_status mfs_set_sweep(mfs_solver* s, int32_t kind) {
+    if (!s) return MFS_ERR_INVALID;
+    if (kind != MFS_SWEEP_AUTO && kind != MFS_SWEEP_CHUNKED && kind != MFS_SWEEP_STAGED)
+        return fail(s, MFS_ERR_INVALID, "unknown sweep kind");
+    if (kind == MFS_SWEEP_STAGED && !s->stg_ok)
+        return fail(s, MFS_ERR_INVALID, "staged sweeps need an FP32_MIXED solver without Lorentz cones");
+    CUDA_TRY(s, cudaSetDevice(s->device));
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    destroy_graphs(s);
+    s->sweep_kind = kind;
     return MFS_OK;
 }
 
@@ -1277,7 +1577,8 @@ mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters
     std::vector<double> rp_hist, rd_hist;
     while (true) {
         TRY(s->precision == MFS_FP64 ? residuals_t(s, s->s64, &r, true) : residuals_t(s, s->s32, &r, true));
-        if (!std::isfinite(r.kkt)) {
+        const double meas = stop_measure(r, s->set.stop_rule);
+        if (!std::isfinite(r.kkt) || !std::isfinite(meas)) {
             result = fail(s, MFS_ERR_NUMERIC, "NaN or Inf in the residuals");
             break;
         }
@@ -1288,7 +1589,7 @@ mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters
             const double blam = -r.dobj, cx = r.pobj;  // b^T lambda, c^T x
             rp_hist.push_back(r.r_prim);
             rd_hist.push_back(r.r_dual);
-            if (same && r.kkt > tol) {
+            if (same && meas > tol) {
                 const size_t h = rp_hist.size();
                 // primal infeasible: d = change of lambda, A^T d in K, b^T d < 0
                 const double bd = blam - prev_blam;
@@ -1316,7 +1617,7 @@ mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters
             prev_cx = cx;
         }
         const bool fp32 = s->precision == MFS_FP32_MIXED;
-        if (r.kkt <= tol) {
+        if (meas <= tol) {
             if (fp32 && s->have64 && s->set.polish_iters > 0 && it < max_iter) {
                 TRY(mfs_set_precision(s, MFS_FP64));
                 const int64_t p = std::min<int64_t>(s->set.polish_iters, max_iter - it);
@@ -1329,8 +1630,8 @@ mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters
         }
         if (it >= max_iter) break;
         if (fp32 && s->have64) {
-            if (r.kkt < 0.99 * best) {
-                best = r.kkt;
+            if (meas < 0.99 * best) {
+                best = meas;
                 since_best = 0;
             } else if (++since_best >= 40) {
                 TRY(mfs_set_precision(s, MFS_FP64));

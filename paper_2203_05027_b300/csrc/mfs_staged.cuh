@@ -1,0 +1,337 @@
+// mfs_staged.cuh -- the staged FP32 sweeps: the same column and row passes as k_col_sweep /
+// k_row_sweep (the reduced form of Algorithm 1, orthant cones), organised so that the gathers read
+// shared memory instead of L2.
+//
+// The gathered vector (v for the column pass, x for the row pass) is cut into blocks of RB entries
+// (64 KB of v, 80 KB of x in FP32). Each CTA owns a group of consecutive segments (columns or rows, balanced
+// by nonzeros, at most a few ten thousand) and keeps one FP32 sum per segment in shared memory. It
+// streams every block of the vector into shared memory in turn with bulk asynchronous copies
+// (cp.async.bulk, two stages, an mbarrier each) and adds the products of its nonzeros whose
+// gathered index falls in that block. The nonzeros of a group are therefore stored sorted by
+// (block, segment, gathered index), one 8-byte entry each: the segment's index within the group in
+// the low 16 bits, the gathered index within the block in the high 16 bits, and the FP32 value.
+// Within one (group, block) the entries are cut into NW ranges, one per warp, at segment boundaries
+// (precomputed), so that no two warps add into the same segment sum and every sum runs in a fixed
+// order: blocks in turn, entries in order within a block. Each range is padded with zero entries of
+// its last segment to a multiple of four, which one lane loads at once.
+//
+// Every CTA reads the whole vector once per pass (148 x 4 MB for a 10^6-row v), which L2 serves
+// at about 28 TB/s to all SMs; the random gathers then cost shared-memory bank cycles instead of
+// L2 sector requests. The nonzeros stream from HBM once, prefetched two blocks ahead into
+// registers; the epilogue's loads are batched so that several are in flight per thread.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mfs_kernels.cuh"
+
+namespace mfs {
+namespace staged {
+
+#ifndef MFS_STG_RB_COL
+#define MFS_STG_RB_COL 16384
+#define MFS_STG_S_COL 2
+#endif
+#ifndef MFS_STG_RB_ROW
+#define MFS_STG_RB_ROW 20480
+#define MFS_STG_S_ROW 2
+#endif
+constexpr int RB_COL = MFS_STG_RB_COL;  // entries of v per block, column pass
+constexpr int S_COL = MFS_STG_S_COL;    // stages
+constexpr int RB_ROW = MFS_STG_RB_ROW;  // entries of x per block, row pass
+constexpr int S_ROW = MFS_STG_S_ROW;
+constexpr int NW = 15;         // consumer warps per CTA (plus one producer warp: 512 threads, 4 warps per
+                               // SM sub-partition, up to 128 registers a thread)
+constexpr int NTS = 32 * NW;
+constexpr int MAXG = 24576;    // segments per group (their sums take 96 KB of shared memory)
+constexpr int LANE_E = 4;      // consecutive entries per lane and step (one 32-byte load)
+constexpr int PF_COL = 2;      // steps of 32 * LANE_E entries prefetched per warp and block
+constexpr int PF_ROW = 1;
+constexpr int EPI_U = 8;       // epilogue items per thread in flight
+
+// dynamic shared memory of one CTA: the vector stages, the group's sums, its split table, 2 S mbarriers
+__host__ __device__ constexpr size_t smem_bytes(int rb, int stages, int maxg, int R) {
+    return (size_t)stages * rb * 4 + (size_t)((maxg + 3) / 4 * 4) * 4 + (size_t)((R * (NW + 1) + 3) / 4 * 4) * 4 +
+           (size_t)16 * stages;
+}
+
+struct StagedArgs {
+    const int2* __restrict__ ent;   // entries, sorted by (group, block, segment, gathered index)
+    const int* __restrict__ split;  // (G * R) x (NW + 1): warp ranges of each (group, block)
+    const int* __restrict__ grp;    // G + 1: first segment of each group
+    const int* __restrict__ wseg;   // G x (NW + 1): each warp's first segment within its group
+    const float* __restrict__ vec;  // gathered vector, R * rb entries (tail padding unused)
+    const float* __restrict__ rsq;  // row pass: sum of a_k^2 over each row
+    int* err;                       // set to 1 if a wait for a block gave up
+    int G, R, maxg_pad;
+    int spin;                       // polls of an mbarrier before a wait gives up
+    int no_loads;                   // diagnostic: issue no copies, so that every wait gives up
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void issue_block(float* dst, const float* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false if it gave up.
+__device__ __forceinline__ bool wait_block(uint64_t* bar, uint32_t parity, int spin) {
+    for (int i = 0; i < spin; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// A warp's range [s0, s1) (both multiples of LANE_E) in steps of 32 * LANE_E entries: lane l takes
+// entries s0 + step*128 + 4l .. +3 with one 32-byte load, words r[8*step + 2t] (segment and
+// gathered index) and r[8*step + 2t + 1] (value bits) for t = 0..3; inactive lanes get zeros.
+template <int PF>
+__device__ __forceinline__ void load_lane(const int2* __restrict__ ent, int s0, int s1, int lane, int (&r)[8 * PF]) {
+#pragma unroll
+    for (int st = 0; st < PF; ++st) {
+        const int base = s0 + st * 32 * LANE_E + lane * LANE_E;
+        if (base < s1) {
+            asm volatile("ld.global.nc.L1::no_allocate.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(r[8 * st + 0]), "=r"(r[8 * st + 1]), "=r"(r[8 * st + 2]), "=r"(r[8 * st + 3]),
+                           "=r"(r[8 * st + 4]), "=r"(r[8 * st + 5]), "=r"(r[8 * st + 6]), "=r"(r[8 * st + 7])
+                         : "l"(ent + base));
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) r[8 * st + q] = 0;
+        }
+    }
+}
+
+// One step of 32 * LANE_E entries of a warp. Each lane adds its four entries in order, keeping the
+// run of equal segments it is in; a run that ends inside the lane's entries (other than its first)
+// is added to the segment's sum at once. The runs that cross lane boundaries are joined by a
+// segmented scan over the lanes' last runs: a lane whose first run continues the previous lanes'
+// last run adds that carry, and only the lane where such a chain ends adds a chain that ends in its
+// last run. Every sum runs in the entries' order within the step; steps follow each other.
+template <int N>
+__device__ __forceinline__ void lane_step(const int (&r)[N], int q0, bool active, const float* vb, float* acc,
+                                          int lane) {
+    int cur = -1, kf = -1;
+    float run = 0.f, vf = 0.f;
+    bool multi = false;
+    if (active) {
+        float p[LANE_E];
+#pragma unroll
+        for (int t = 0; t < LANE_E; ++t) p[t] = __int_as_float(r[q0 + 2 * t + 1]) * vb[(uint32_t)r[q0 + 2 * t] >> 16];
+        cur = r[q0] & 0xFFFF;
+        run = p[0];
+#pragma unroll
+        for (int t = 1; t < LANE_E; ++t) {
+            const int key = r[q0 + 2 * t] & 0xFFFF;
+            if (key != cur) {
+                if (!multi) {
+                    kf = cur;
+                    vf = run;
+                    multi = true;
+                } else {
+                    acc[cur] += run;
+                }
+                cur = key;
+                run = p[t];
+            } else {
+                run += p[t];
+            }
+        }
+    }
+    const int fk = multi ? kf : cur;  // first segment of the lane (-1: no entries)
+    float S = run;                    // last run, joined with the chain of lanes before it
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float o = __shfl_up_sync(FULL, S, d);
+        const int k = __shfl_up_sync(FULL, cur, d);
+        if (lane >= d && k == cur) S += o;
+    }
+    const float sprev = __shfl_up_sync(FULL, S, 1);
+    const int kprev = __shfl_up_sync(FULL, cur, 1);
+    const int nfk = __shfl_down_sync(FULL, fk, 1);
+    if (multi) acc[kf] += vf + ((lane > 0 && kprev == kf) ? sprev : 0.f);
+    if (cur >= 0 && (lane == 31 || nfk != cur)) acc[cur] += S;
+}
+
+// All entries of a warp's range [s0, s1) of one block: PF prefetched steps, then any further ones.
+template <int PF>
+__device__ __forceinline__ void run_range(const int (&r)[8 * PF], int s0, int s1, const int2* __restrict__ ent,
+                                          const float* vb, float* acc, int lane) {
+#pragma unroll
+    for (int st = 0; st < PF; ++st) {
+        const int b0 = s0 + st * 32 * LANE_E;
+        if (b0 < s1) lane_step<8 * PF>(r, 8 * st, b0 + lane * LANE_E < s1, vb, acc, lane);
+        __syncwarp();
+    }
+    for (int b0 = s0 + PF * 32 * LANE_E; b0 < s1; b0 += 32 * LANE_E) {
+        int t[8];
+        load_lane<1>(ent, b0, s1, lane, t);
+        lane_step<8>(t, 0, b0 + lane * LANE_E < s1, vb, acc, lane);
+        __syncwarp();
+    }
+}
+
+// Block u of the CTA's sequence of staged blocks sits in stage u % S; full[k] completes when its
+// copy has landed, empty[k] when every consumer warp has finished with it.
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Consumer side of block b (the CTA's block u): prefetch the warp's entries of block b + 2 into D,
+// wait for the stage, add the entries held in C, and release the stage.
+template <int RB, int PF, int S>
+__device__ __forceinline__ void block_step(int b, int R, uint32_t u, int (&C)[8 * PF], int (&D)[8 * PF],
+                                           const int* spl, const StagedArgs& g, const float* vb, float* acc,
+                                           uint64_t* full, uint64_t* empty, bool& bad, int warp, int lane) {
+    if (b + 2 < R) {
+        const int* sp = spl + (b + 2) * (NW + 1) + warp;
+        load_lane<PF>(g.ent, sp[0], sp[1], lane, D);
+    }
+    const uint32_t k = u % S;
+    if (!wait_block(full + k, (u / S) & 1u, g.spin)) bad = true;
+    const int* sp = spl + b * (NW + 1) + warp;
+    run_range<PF>(C, sp[0], sp[1], g.ent, vb + k * RB, acc, lane);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty + k);
+}
+
+// MODE 0: column pass (gathers v; epilogue x-, z-, delta-updates of orthant columns).
+// MODE 1: row pass (gathers x; epilogue rho, lambda and v of each row).
+// Warps 0..NW-1 consume; warp NW produces (its lane 0 issues the copies of the vector blocks).
+// Warp w owns the segments wseg[w] .. wseg[w+1]-1 of its group in every block: it alone adds into
+// their sums, and it runs their epilogue as soon as it has seen every block, while other warps
+// may still be streaming.
+template <int MODE, int RB, int PF, int S>
+__global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, const SweepArgs<float> a) {
+    constexpr int N = 8 * PF;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* vb = reinterpret_cast<float*>(smem);
+    float* acc = vb + S * RB;
+    const int R = g.R;
+    int* spl = reinterpret_cast<int*>(acc + g.maxg_pad);
+    uint64_t* full = reinterpret_cast<uint64_t*>(spl + (R * (NW + 1) + 3) / 4 * 4);
+    uint64_t* empty = full + S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < S; ++k) {
+            mbar_init(full + k, 1);
+            mbar_init(empty + k, NW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t u0 = 0;  // the CTA's staged blocks before the current group
+    bool bad = false;
+    for (int grp = blockIdx.x; grp < g.G; grp += gridDim.x) {
+        const int k0 = g.grp[grp];
+        const int* gs = g.split + (size_t)grp * R * (NW + 1);
+        for (int t = threadIdx.x; t < R * (NW + 1); t += NTS + 32) spl[t] = gs[t];
+        __syncthreads();  // split table in place; the previous group's sums are no longer read
+        if (warp == NW) {
+            if (lane == 0 && !g.no_loads) {
+                for (int b = 0; b < R; ++b) {
+                    const uint32_t u = u0 + b, k = u % S;
+                    if (u >= S && !wait_block(empty + k, (u / S - 1) & 1u, g.spin)) bad = true;
+                    issue_block(vb + k * RB, g.vec + (size_t)b * RB, RB * 4u, full + k);
+                }
+            }
+        } else {
+            const int ws = g.wseg[grp * (NW + 1) + warp], we = g.wseg[grp * (NW + 1) + warp + 1];
+            for (int t = ws + lane; t < we; t += 32) acc[t] = 0.f;
+            __syncwarp();
+            int A[N], B[N], C[N];
+            load_lane<PF>(g.ent, spl[warp], spl[warp + 1], lane, A);
+            if (R > 1) load_lane<PF>(g.ent, spl[NW + 1 + warp], spl[NW + 2 + warp], lane, B);
+            for (int b = 0; b < R; b += 3) {
+                block_step<RB, PF, S>(b, R, u0 + b, A, C, spl, g, vb, acc, full, empty, bad, warp, lane);
+                if (b + 1 < R)
+                    block_step<RB, PF, S>(b + 1, R, u0 + b + 1, B, A, spl, g, vb, acc, full, empty, bad, warp, lane);
+                if (b + 2 < R)
+                    block_step<RB, PF, S>(b + 2, R, u0 + b + 2, C, B, spl, g, vb, acc, full, empty, bad, warp, lane);
+            }
+            __syncwarp();
+            const float mu = a.mu;
+            if (MODE == 0) {
+                for (int t0 = ws + lane; t0 < we; t0 += 32 * EPI_U) {
+                    float px[EPI_U], pz[EPI_U], pd[EPI_U], pc[EPI_U], dg[EPI_U];
+#pragma unroll
+                    for (int q = 0; q < EPI_U; ++q) {
+                        const int t = t0 + q * 32;
+                        if (t < we) {
+                            const int j = k0 + t;
+                            dg[q] = (float)(__ldg(a.col_ptr + j + 1) - __ldg(a.col_ptr + j));
+                            px[q] = a.x[j];
+                            pz[q] = a.z[j];
+                            pd[q] = a.del[j];
+                            pc[q] = __ldg(a.c + j);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < EPI_U; ++q) {
+                        const int t = t0 + q * 32;
+                        if (t < we) {
+                            const float xn = col_x_update(dg[q], px[q], acc[t], pz[q], pd[q], pc[q], mu);
+                            orthant_update(a.x, a.z, a.del, k0 + t, xn, pd[q], mu);
+                        }
+                    }
+                }
+            } else {
+                for (int t0 = ws + lane; t0 < we; t0 += 32 * EPI_U) {
+                    float pr[EPI_U], pb[EPI_U], pl[EPI_U];
+#pragma unroll
+                    for (int q = 0; q < EPI_U; ++q) {
+                        const int t = t0 + q * 32;
+                        if (t < we) {
+                            const int i = k0 + t;
+                            pr[q] = __ldg(g.rsq + i);
+                            pb[q] = __ldg(a.b + i);
+                            pl[q] = a.lam[i];
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < EPI_U; ++q) {
+                        const int t = t0 + q * 32;
+                        if (t < we) row_update<float, 0>(a, k0 + t, acc[t], pr[q], pb[q], pl[q]);
+                    }
+                }
+            }
+        }
+        u0 += R;
+        __syncthreads();  // the group is done: its sums and split table may be replaced
+    }
+    if (bad) {
+        // a copy may still be in flight into a stage: wait (bounded) for the last load of each stage
+        for (int d = 1; d <= S && (uint32_t)d <= u0; ++d) {
+            const uint32_t u = u0 - d;
+            wait_block(full + u % S, (u / S) & 1u, g.spin);
+        }
+        atomicExch(g.err, 1);
+    }
+}
+
+// the two instantiations the solver launches
+#define MFS_STAGED_COL \
+    ::mfs::staged::k_staged<0, ::mfs::staged::RB_COL, ::mfs::staged::PF_COL, ::mfs::staged::S_COL>
+#define MFS_STAGED_ROW \
+    ::mfs::staged::k_staged<1, ::mfs::staged::RB_ROW, ::mfs::staged::PF_ROW, ::mfs::staged::S_ROW>
+
+}  // namespace staged
+}  // namespace mfs

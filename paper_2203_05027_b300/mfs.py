@@ -22,6 +22,10 @@ STATUS_NAMES = {0: "OK", 1: "MAX_ITER", 2: "ERR_INVALID", 3: "ERR_CUDA", 4: "ERR
                 6: "ERR_TIMEOUT", 7: "INFEASIBLE", 8: "UNBOUNDED"}
 CONE_NONNEG, CONE_SOC = 0, 1
 FP64, FP32_MIXED = 0, 1
+STOP_KKT, STOP_SCS_L2, STOP_OSQP_INF = 0, 1, 2
+STOP_RULES = {"kkt": STOP_KKT, "scs_l2": STOP_SCS_L2, "osqp_inf": STOP_OSQP_INF}
+SWEEP_AUTO, SWEEP_CHUNKED, SWEEP_STAGED = 0, 1, 2
+SWEEPS = {"auto": SWEEP_AUTO, "chunked": SWEEP_CHUNKED, "staged": SWEEP_STAGED}
 
 
 class MfsError(RuntimeError):
@@ -36,12 +40,13 @@ class Cone(ctypes.Structure):
 
 class Settings(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_double), ("check_every", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("polish_iters", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("polish_iters", ctypes.c_int32), ("stop_rule", ctypes.c_int32), ("osqp_rel", ctypes.c_double)]
 
 
 RESID_FIELDS = ("r_prim", "r_dual", "r_cone", "r_gap", "kkt", "pobj", "dobj",
                 "nrm_res_p", "nrm_b", "nrm_xdist", "nrm_x", "nrm_sdist", "nrm_c", "nrm_atl_c",
-                "inf_res_p", "inf_ax", "inf_b", "inf_atl_c", "inf_atl", "inf_c")
+                "inf_res_p", "inf_ax", "inf_b", "inf_atl_c", "inf_atl", "inf_c",
+                "inf_x", "inf_xdist", "inf_sdist", "r_scs", "r_osqp")
 
 
 class Residuals(ctypes.Structure):
@@ -53,7 +58,7 @@ class Info(ctypes.Structure):
                 ("ncones", ctypes.c_int64), ("nsoc", ctypes.c_int64), ("nbig", ctypes.c_int64),
                 ("col_chunks", ctypes.c_int64), ("row_chunks", ctypes.c_int64),
                 ("bytes_per_iter", ctypes.c_int64), ("precision", ctypes.c_int32),
-                ("launches_per_iter", ctypes.c_int32)]
+                ("launches_per_iter", ctypes.c_int32), ("sweep_col", ctypes.c_int32), ("sweep_row", ctypes.c_int32)]
 
 
 _lib = None
@@ -92,6 +97,10 @@ def load(path=LIB_PATH):
     lib.mfs_get_info.restype = st
     lib.mfs_set_mu.argtypes = [P, dbl]
     lib.mfs_set_mu.restype = st
+    lib.mfs_set_sweep.argtypes = [P, i32]
+    lib.mfs_set_sweep.restype = st
+    lib.mfs_debug_staged_wait_test.argtypes = [P]
+    lib.mfs_debug_staged_wait_test.restype = st
     for name in ("mfs_warm_start", "mfs_warm_start_device", "mfs_get_solution", "mfs_get_solution_device"):
         getattr(lib, name).argtypes = [P, P, P, P, P]
         getattr(lib, name).restype = st
@@ -132,7 +141,8 @@ class Solver:
     """One problem on the GPU. ``prob`` is a dict with m, n, row, col, val, b, c, cones
     (as made by ``instances``)."""
 
-    def __init__(self, prob, mu=1.0, check_every=25, precision="fp64", polish_iters=50, stream=None):
+    def __init__(self, prob, mu=1.0, check_every=25, precision="fp64", polish_iters=50, stream=None,
+                 stop_rule="kkt", osqp_rel=10.0):
         lib = load()
         self._lib = lib
         m, n = int(prob["m"]), int(prob["n"])
@@ -153,6 +163,8 @@ class Solver:
         st.precision = {"fp64": FP64, "fp32": FP32_MIXED, "mixed": FP32_MIXED}[precision] \
             if isinstance(precision, str) else int(precision)
         st.polish_iters = int(polish_iters)
+        st.stop_rule = STOP_RULES[stop_rule] if isinstance(stop_rule, str) else int(stop_rule)
+        st.osqp_rel = float(osqp_rel)
         h = ctypes.c_void_p()
         stream_ptr = ctypes.c_void_p(int(stream)) if stream else None
         code = lib.mfs_create(m, n, len(row), row.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
@@ -189,6 +201,15 @@ class Solver:
 
     def set_mu(self, mu):
         self._check(self._lib.mfs_set_mu(self._h, float(mu)))
+
+    def staged_wait_test(self):
+        """Status name of the staged sweeps' wait diagnostic ("ERR_TIMEOUT" expected)."""
+        code = self._lib.mfs_debug_staged_wait_test(self._h)
+        return STATUS_NAMES[code]
+
+    def set_sweep(self, kind):
+        """"auto", "chunked" or "staged" sweep kernels for the FP32 iteration."""
+        self._check(self._lib.mfs_set_sweep(self._h, SWEEPS[kind] if isinstance(kind, str) else int(kind)))
 
     def set_precision(self, precision):
         p = {"fp64": FP64, "fp32": FP32_MIXED}[precision] if isinstance(precision, str) else int(precision)

@@ -28,14 +28,33 @@ def test_header_functions_are_exported(lib):
         assert hasattr(lib, n)
 
 
-def test_struct_sizes_match_header(lib):
-    # mfs_cone {int32, int32, int64}; mfs_settings {double, 4 x int32}; residuals 20 doubles + int64
-    assert ctypes.sizeof(mfs.Cone) == 16
-    assert ctypes.sizeof(mfs.Settings) == 24
-    assert ctypes.sizeof(mfs.Residuals) == 21 * 8
+def _c_layout(tmp_path):
+    """sizeof and offsets of the header's structs, as a C compiler lays them out."""
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "mfs.h"\n'
+        "int main(void) {\n"
+        '  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mfs_cone), sizeof(mfs_settings),\n'
+        "         sizeof(mfs_residuals_t), offsetof(mfs_settings, stop_rule), offsetof(mfs_settings, osqp_rel),\n"
+        "         offsetof(mfs_residuals_t, r_osqp), offsetof(mfs_residuals_t, iter));\n"
+        "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(mfs.HEADER))
+    subprocess.run(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    return [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+
+
+def test_struct_sizes_match_header(lib, tmp_path):
+    cone, settings, resid, off_rule, off_rel, off_osqp, off_iter = _c_layout(tmp_path)
+    assert ctypes.sizeof(mfs.Cone) == cone == 16
+    assert ctypes.sizeof(mfs.Settings) == settings
+    assert mfs.Settings.stop_rule.offset == off_rule and mfs.Settings.osqp_rel.offset == off_rel
+    assert ctypes.sizeof(mfs.Residuals) == resid
+    assert mfs.Residuals.r_osqp.offset == off_osqp and mfs.Residuals.iter.offset == off_iter
     st = mfs.Settings()
     lib.mfs_default_settings(ctypes.byref(st))
     assert (st.mu, st.check_every, st.precision, st.polish_iters) == (1.0, 25, 0, 50)
+    assert (st.stop_rule, st.osqp_rel) == (mfs.STOP_KKT, 10.0)
 
 
 def tiny():
@@ -69,6 +88,12 @@ def test_invalid_settings_rejected_on_host(lib):
     with pytest.raises(mfs.MfsError) as e:
         mfs.Solver(tiny(), check_every=0)
     assert e.value.status == mfs.MFS_ERR_INVALID
+    with pytest.raises(mfs.MfsError) as e:
+        mfs.Solver(tiny(), stop_rule=3)
+    assert e.value.status == mfs.MFS_ERR_INVALID and "stop_rule" in str(e.value)
+    with pytest.raises(mfs.MfsError) as e:
+        mfs.Solver(tiny(), stop_rule="osqp_inf", osqp_rel=0.0)
+    assert e.value.status == mfs.MFS_ERR_INVALID and "osqp_rel" in str(e.value)
 
 
 def test_null_arguments(lib):

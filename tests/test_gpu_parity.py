@@ -238,6 +238,29 @@ def test_solve_max_iter():
     assert status == "MAX_ITER" and its == 55
 
 
+@pytest.mark.parametrize("rule, maker, tol", [("scs_l2", "lp", 1e-5), ("osqp_inf", "lp", 1e-5),
+                                             ("scs_l2", "socp", 1e-7), ("osqp_inf", "socp", 1e-7),
+                                             ("kkt", "socp", 1e-7)])
+def test_solve_stops_at_the_first_check_meeting_the_rule(rule, maker, tol):
+    """mfs_solve under each stopping rule of Sec. V stops at the first check (every 25 iterations)
+    at which the oracle's measure of that rule is <= tol."""
+    prob = I.small_lp(3, m=60, n=150) if maker == "lp" else I.socp(4, n=600, m=240)
+    q = 30.0
+    s = mfs.Solver(prob, precision="fp64", check_every=25, stop_rule=rule, osqp_rel=q)
+    status, its = s.solve(tol, 400_000)
+    assert status == "OK" and its % 25 == 0 and its > 0
+    key = {"kkt": "kkt", "scs_l2": "r_scs", "osqp_inf": "r_osqp"}[rule]
+    g = s.residuals()
+    orc = oracle.make_oracle(prob)
+    orc.iterate(its - 25)
+    before = orc.residuals(osqp_rel=q)[key]
+    orc.iterate(25)
+    after = orc.residuals(osqp_rel=q)
+    assert before > tol * (1 - 1e-6), (before, tol)
+    assert after[key] <= tol * (1 + 1e-6), (after[key], tol)
+    assert abs(g[key] - after[key]) <= 1e-9 * max(1.0, after[key])
+
+
 def test_nan_warm_start_is_numeric_error():
     prob = I.small_lp(0, m=20, n=50)
     s = mfs.Solver(prob)

@@ -1,0 +1,131 @@
+"""Parity of the staged FP32 sweeps (vector blocks streamed through shared memory, nonzeros sorted
+by block) with the FP64 CPU oracle of Algorithm 1, on the FP32-rounded problem: after a fixed
+number of iterations max_i |gpu_i - oracle_i| <= 1e-4 * max_i |oracle_i| for x, z, delta, lambda.
+
+The problems span several vector blocks with a ragged last block, several groups per pass, groups
+that outnumber the SMs (a CTA then takes more than one), empty and long rows and columns."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_05027_b300 import build, instances as I, mfs
+
+from test_gpu_parity import TOL, compare, edge_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build.build()
+    mfs.load()
+
+
+def staged_pair(prob, iters, mu=1.0):
+    orc = oracle.make_oracle(prob, mu=mu, dtype=np.float32)
+    s = mfs.Solver(prob, mu=mu, precision="fp32", polish_iters=0, check_every=25)
+    s.set_sweep("staged")
+    info = s.info()
+    assert info["sweep_col"] == mfs.SWEEP_STAGED and info["sweep_row"] == mfs.SWEEP_STAGED
+    orc.iterate(iters)
+    s.iterate(iters)
+    return orc, s
+
+
+@pytest.mark.parametrize("m, n, iters", [(40_000, 100_000, 50), (5_000, 12_000, 120)])
+def test_power_law_lp(m, n, iters):
+    prob = I.large_lp(0, m=m, n=n)
+    orc, s = staged_pair(prob, iters)
+    compare(s.solution(), orc.state(), TOL["fp32"])
+
+
+@pytest.mark.parametrize("kind", ["empty_rows_cols", "long_column", "long_row", "duplicates_zeros", "degree_one",
+                                  "chunk_boundaries"])
+def test_edge_cases(kind):
+    prob = edge_problem(kind)
+    orc, s = staged_pair(prob, 40)
+    compare(s.solution(), orc.state(), TOL["fp32"], kind)
+
+
+def test_more_groups_than_sms():
+    """4.2 million degree-2 columns: more column groups (at most 24,576 columns each) than SMs."""
+    m, n = 300_000, 4_200_000
+    prob = I.lp_from_degrees(m, n, np.full(n, 2, np.int64), 5)
+    orc, s = staged_pair(prob, 3)
+    compare(s.solution(), orc.state(), TOL["fp32"])
+
+
+def test_chunked_and_staged_agree_with_each_other_within_fp32():
+    prob = I.large_lp(2, m=20_000, n=50_000)
+    a = mfs.Solver(prob, precision="fp32", polish_iters=0)
+    b = mfs.Solver(prob, precision="fp32", polish_iters=0)
+    a.set_sweep("chunked")
+    b.set_sweep("staged")
+    a.iterate(30)
+    b.iterate(30)
+    sa, sb = a.solution(), b.solution()
+    for k in sa:
+        scale = np.abs(sa[k]).max()
+        assert np.abs(sa[k] - sb[k]).max() <= 1e-4 * scale, k
+
+
+def test_repeatable_bitwise():
+    prob = I.large_lp(3, m=20_000, n=50_000)
+    a = mfs.Solver(prob, precision="fp32")
+    b = mfs.Solver(prob, precision="fp32")
+    a.set_sweep("staged")
+    b.set_sweep("staged")
+    a.iterate(40)
+    b.iterate(40)
+    sa, sb = a.solution(), b.solution()
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+
+
+def test_solve_with_staged_sweeps_and_polish():
+    prob = I.small_lp(0, m=200, n=500)
+    s = mfs.Solver(prob, precision="fp32", check_every=50, polish_iters=100)
+    s.set_sweep("staged")
+    status, its = s.solve(1e-6, 400_000)
+    assert status == "OK"
+    assert s.residuals()["kkt"] <= 1e-6
+
+
+def test_auto_choice_and_invalid_requests():
+    big = I.large_lp(1, m=60_000, n=150_000)   # 1.2 M nonzeros, 20 per row and 8 per column
+    s = mfs.Solver(big, precision="fp32")
+    info = s.info()
+    assert (info["sweep_col"], info["sweep_row"]) == (mfs.SWEEP_CHUNKED, mfs.SWEEP_CHUNKED)  # auto
+    s.set_sweep("staged")
+    info = s.info()
+    assert (info["sweep_col"], info["sweep_row"]) == (mfs.SWEEP_STAGED, mfs.SWEEP_STAGED)
+    assert info["launches_per_iter"] == 2
+    s.set_sweep("auto")
+    assert s.info()["sweep_col"] == mfs.SWEEP_CHUNKED
+    f64 = mfs.Solver(I.small_lp(0), precision="fp64")
+    with pytest.raises(mfs.MfsError) as e:
+        f64.set_sweep("staged")
+    assert e.value.status == mfs.MFS_ERR_INVALID
+    soc = mfs.Solver(I.socp(0, n=3000, m=1200), precision="fp32")
+    with pytest.raises(mfs.MfsError) as e:
+        soc.set_sweep("staged")
+    assert e.value.status == mfs.MFS_ERR_INVALID
+    with pytest.raises(mfs.MfsError):
+        s.set_sweep(7)
+
+
+def test_bounded_wait_gives_up_and_context_survives():
+    """The staged kernel's waits for its vector blocks are bounded: with the copies suppressed every
+    wait gives up, the kernel reports it, and the solver works afterwards."""
+    prob = I.large_lp(4, m=20_000, n=50_000)
+    s = mfs.Solver(prob, precision="fp32", polish_iters=0)
+    s.set_sweep("staged")
+    assert s.staged_wait_test() == "ERR_TIMEOUT"
+    x0, lam0 = np.zeros(prob["n"]), np.zeros(prob["m"])
+    s.warm_start(x0, lam0)
+    orc = oracle.make_oracle(prob, dtype=np.float32)
+    orc.warm_start(x0, lam0)
+    orc.iterate(20)
+    s.iterate(20)
+    compare(s.solution(), orc.state(), TOL["fp32"])
+    assert np.isfinite(s.residuals()["kkt"])

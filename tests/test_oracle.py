@@ -390,6 +390,96 @@ def test_residual_norms_match_library_products():
     assert np.isclose(r["r_prim"], np.linalg.norm(res) / (1 + np.linalg.norm(prob["b"])), rtol=1e-13)
 
 
+def spectral_proj_lorentz(w):
+    """Projection on one Lorentz cone through its spectral decomposition (the Jordan algebra of the
+    cone): w = l1 u1 + l2 u2 with l1,2 = w1 -/+ ||wbar||, u1,2 = (1, -/+ wbar/||wbar||)/2, and the
+    projection keeps max(l, 0) of each eigenvalue. Independent of the case split of eq. proj."""
+    w = np.asarray(w, float)
+    if w.size == 1:
+        return np.maximum(w, 0.0)
+    a = np.linalg.norm(w[1:])
+    d = w[1:] / a if a > 0 else np.zeros(w.size - 1)
+    u1 = np.concatenate([[0.5], -0.5 * d])
+    u2 = np.concatenate([[0.5], 0.5 * d])
+    return max(w[0] - a, 0.0) * u1 + max(w[0] + a, 0.0) * u2
+
+
+def spectral_proj_K(cones, w):
+    out, o = np.empty_like(w), 0
+    for kind, size in cones:
+        seg = w[o:o + size]
+        out[o:o + size] = np.maximum(seg, 0.0) if kind == 0 else spectral_proj_lorentz(seg)
+        o += size
+    return out
+
+
+def test_infinity_norm_distances_match_spectral_projection():
+    prob = I.socp(seed=3, n=300, m=120, nnz_per_row=6)
+    orc = oracle.make_oracle(prob)
+    rng = np.random.default_rng(6)
+    cones = [tuple(map(int, q)) for q in np.asarray(prob["cones"]).reshape(-1, 2)]
+    A = sp.coo_matrix((prob["val"], (prob["row"], prob["col"])), shape=(prob["m"], prob["n"])).tocsr()
+    for _ in range(5):
+        x = rng.standard_normal(prob["n"]) * rng.choice([0.1, 1.0, 10.0])
+        lam = rng.standard_normal(prob["m"])
+        orc.set_state(x=x, lam=lam)
+        r = orc.residuals()
+        s = A.T @ lam + prob["c"]
+        dx = x - spectral_proj_K(cones, x)
+        ds = s - spectral_proj_K(cones, s)
+        assert np.isclose(r["inf_x"], np.abs(x).max(), rtol=1e-15)
+        assert np.isclose(r["inf_xdist"], np.abs(dx).max(), rtol=1e-12, atol=1e-14)
+        assert np.isclose(r["inf_sdist"], np.abs(ds).max(), rtol=1e-12, atol=1e-14)
+        # norm inequalities between the l2 and infinity forms
+        assert r["inf_xdist"] <= r["nrm_xdist"] * (1 + 1e-14) <= np.sqrt(prob["n"]) * r["inf_xdist"] * (1 + 1e-12)
+        assert r["inf_sdist"] <= r["nrm_sdist"] * (1 + 1e-14) <= np.sqrt(prob["n"]) * r["inf_sdist"] * (1 + 1e-12)
+
+
+def test_stop_measures_vanish_at_an_exact_optimum():
+    """At HiGHS's optimal primal-dual pair both rules read 0 (to rounding), while the printed dual
+    residual ||A^T lambda + c|| does not: the cone multiplier must come out of it."""
+    from scipy.optimize import linprog
+    prob = I.small_lp(1)
+    A = sp.coo_matrix((prob["val"], (prob["row"], prob["col"])), shape=(prob["m"], prob["n"])).tocsr()
+    ref = linprog(prob["c"], A_eq=A, b_eq=prob["b"], bounds=(0, None), method="highs",
+                  options={"primal_feasibility_tolerance": 1e-10, "dual_feasibility_tolerance": 1e-10})
+    assert ref.status == 0
+    x = np.maximum(ref.x, 0.0)
+    lam = -ref.eqlin.marginals          # HiGHS: c - A^T y >= 0; here c + A^T lambda in K
+    orc = oracle.make_oracle(prob)
+    orc.set_state(x=x, lam=lam)
+    r = orc.residuals()
+    assert r["r_scs"] < 1e-8 and r["r_osqp"] < 1e-8
+    assert r["nrm_atl_c"] / (1 + r["nrm_c"]) > 1e-2
+
+
+def test_stop_measures_reduce_to_the_printed_rules():
+    """With x in K (no cone violation) and s = A^T lambda + c in the polar cone (P_K s = 0), the two
+    measures are the printed SCS and OSQP tests, and "measure <= eps" holds exactly when the printed
+    inequalities hold with eps_abs = eps and eps_rel = q eps."""
+    rng = np.random.default_rng(7)
+    prob = I.small_lp(2)
+    A = sp.coo_matrix((prob["val"], (prob["row"], prob["col"])), shape=(prob["m"], prob["n"])).toarray()
+    b = prob["b"]
+    for trial in range(20):
+        x = np.abs(rng.standard_normal(prob["n"])) * rng.choice([1e-3, 1.0])
+        lam = rng.standard_normal(prob["m"]) * 0.01
+        c = -np.abs(rng.standard_normal(prob["n"])) - np.abs(A.T @ lam) - 0.1   # s <= 0 elementwise
+        p = dict(prob, c=c)
+        orc = oracle.make_oracle(p)
+        orc.set_state(x=x, lam=lam)
+        q = float(rng.choice([1.0, 10.0, 100.0]))
+        r = orc.residuals(osqp_rel=q)
+        res, s = A @ x - b, A.T @ lam + c
+        scs = max(np.linalg.norm(res) / (1 + np.linalg.norm(b)), np.linalg.norm(s) / (1 + np.linalg.norm(c)),
+                  abs(c @ x + b @ lam) / (1 + abs(c @ x) + abs(b @ lam)))
+        assert np.isclose(r["r_scs"], scs, rtol=1e-12)
+        for eps in np.geomspace(1e-6, 10.0, 15):
+            ok = (np.abs(res).max() <= eps + q * eps * max(np.abs(A @ x).max(), np.abs(b).max(), np.abs(x).max())
+                  and np.abs(s).max() <= eps + q * eps * max(np.abs(A.T @ lam).max(), np.abs(c).max()))
+            assert (r["r_osqp"] <= eps) == ok or abs(r["r_osqp"] - eps) < 1e-12 * eps
+
+
 # ---------------------------------------------------------------- reduced form vs literal form
 
 @pytest.mark.parametrize("maker", ["small_lp", "socp"])

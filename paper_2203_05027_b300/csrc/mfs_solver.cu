@@ -338,7 +338,8 @@ struct StagedHost {
 // rb: entries of the gathered vector per block; smem_limit: shared memory a CTA may use, which
 // bounds the group size. Returns false if not even small groups fit.
 bool build_staged(const std::vector<int>& ptr, const mfs::host::uvec<int>& idx, const mfs::host::uvec<double>& val,
-                  int nseg, int nother, int groups, int rb, int stages, size_t smem_limit, StagedHost& S) {
+                  int nseg, int nother, int groups, int rb, int stages, int lane_e, size_t smem_limit,
+                  StagedHost& S) {
     using namespace mfs::host;
     using mfs::staged::NW;
     const int RB = rb;
@@ -427,9 +428,9 @@ bool build_staged(const std::vector<int>& ptr, const mfs::host::uvec<int>& idx, 
             sp[NW] = en;
         }
     });
-    // pad every warp range to a multiple of LANE_E entries (zero values, the range's last segment, so
-    // they fall into its last sum) so that a lane loads its LANE_E entries with one 32-byte load
-    constexpr int LE = mfs::staged::LANE_E;
+    // pad every warp range to a multiple of lane_e entries (zero values, the range's last segment, so
+    // they fall into its last sum) so that a lane loads its lane_e entries with 32-byte loads
+    const int LE = lane_e;
     std::vector<int64_t> pstart((size_t)G * R + 1, 0);
     parallel_ranges((int64_t)G * R, threads_for(o), [&](int64_t u0, int64_t u1, int) {
         for (int64_t u = u0; u < u1; ++u) {
@@ -843,8 +844,10 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
     int optin = 0;
     CUDA_TRY(s, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
     StagedHost C, W;
-    if (!build_staged(P.col_ptr, P.csc_row, P.csc_val, P.n, P.m, s->num_sms, RB_COL, S_COL, (size_t)optin, C) ||
-        !build_staged(P.row_ptr, P.csr_col, P.csr_val, P.m, P.n, s->num_sms, RB_ROW, S_ROW, (size_t)optin, W))
+    if (!build_staged(P.col_ptr, P.csc_row, P.csc_val, P.n, P.m, s->num_sms, RB_COL, S_COL, LE_COL, (size_t)optin,
+                      C) ||
+        !build_staged(P.row_ptr, P.csr_col, P.csr_val, P.m, P.n, s->num_sms, RB_ROW, S_ROW, LE_ROW, (size_t)optin,
+                      W))
         return MFS_OK;  // vectors too long for the split tables: chunked sweeps only
     std::vector<float> rsq(std::max(P.m, 1), 0.f);
     mfs::host::parallel_ranges(P.m, mfs::host::threads_for(P.o), [&](int64_t i0, int64_t i1, int) {

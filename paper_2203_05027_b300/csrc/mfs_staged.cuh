@@ -3,7 +3,7 @@
 // shared memory instead of L2.
 //
 // The gathered vector (v for the column pass, x for the row pass) is cut into blocks of RB entries
-// (64 KB of v, 80 KB of x in FP32). Each CTA owns a group of consecutive segments (columns or rows, balanced
+// (64 KB of v, 96 KB of x in FP32). Each CTA owns a group of consecutive segments (columns or rows, balanced
 // by nonzeros, at most a few ten thousand) and keeps one FP32 sum per segment in shared memory. It
 // streams every block of the vector into shared memory in turn with bulk asynchronous copies
 // (cp.async.bulk, two stages, an mbarrier each) and adds the products of its nonzeros whose
@@ -13,7 +13,8 @@
 // Within one (group, block) the entries are cut into NW ranges, one per warp, at segment boundaries
 // (precomputed), so that no two warps add into the same segment sum and every sum runs in a fixed
 // order: blocks in turn, entries in order within a block. Each range is padded with zero entries of
-// its last segment to a multiple of four, which one lane loads at once.
+// its last segment to a multiple of the entries one lane loads at once (LE: 8 for the column pass,
+// 4 for the row pass).
 //
 // Every CTA reads the whole vector once per pass (148 x 4 MB for a 10^6-row v), which L2 serves
 // at about 28 TB/s to all SMs; the random gathers then cost shared-memory bank cycles instead of
@@ -34,20 +35,32 @@ namespace staged {
 #define MFS_STG_S_COL 2
 #endif
 #ifndef MFS_STG_RB_ROW
-#define MFS_STG_RB_ROW 20480
+#define MFS_STG_RB_ROW 24576
 #define MFS_STG_S_ROW 2
+#endif
+#ifndef MFS_STG_NW
+#define MFS_STG_NW 15
 #endif
 constexpr int RB_COL = MFS_STG_RB_COL;  // entries of v per block, column pass
 constexpr int S_COL = MFS_STG_S_COL;    // stages
 constexpr int RB_ROW = MFS_STG_RB_ROW;  // entries of x per block, row pass
 constexpr int S_ROW = MFS_STG_S_ROW;
-constexpr int NW = 15;         // consumer warps per CTA (plus one producer warp: 512 threads, 4 warps per
-                               // SM sub-partition, up to 128 registers a thread)
+constexpr int NW = MFS_STG_NW;  // consumer warps per CTA, plus one producer warp (15: 512 threads, 4 warps
+                                // per SM sub-partition, up to 128 registers a thread)
 constexpr int NTS = 32 * NW;
 constexpr int MAXG = 24576;    // segments per group (their sums take 96 KB of shared memory)
-constexpr int LANE_E = 4;      // consecutive entries per lane and step (one 32-byte load)
-constexpr int PF_COL = 2;      // steps of 32 * LANE_E entries prefetched per warp and block
-constexpr int PF_ROW = 1;
+#ifndef MFS_STG_LE_COL
+#define MFS_STG_LE_COL 4
+#define MFS_STG_PF_COL 2
+#endif
+#ifndef MFS_STG_LE_ROW
+#define MFS_STG_LE_ROW 4
+#define MFS_STG_PF_ROW 1
+#endif
+constexpr int LE_COL = MFS_STG_LE_COL;  // consecutive entries per lane and step (LE/4 32-byte loads)
+constexpr int PF_COL = MFS_STG_PF_COL;  // steps of 32 * LE entries prefetched per warp and block
+constexpr int LE_ROW = MFS_STG_LE_ROW;
+constexpr int PF_ROW = MFS_STG_PF_ROW;
 constexpr int EPI_U = 8;       // epilogue items per thread in flight
 
 // dynamic shared memory of one CTA: the vector stages, the group's sums, its split table, 2 S mbarriers
@@ -97,91 +110,117 @@ __device__ __forceinline__ bool wait_block(uint64_t* bar, uint32_t parity, int s
     return false;
 }
 
-// A warp's range [s0, s1) (both multiples of LANE_E) in steps of 32 * LANE_E entries: lane l takes
-// entries s0 + step*128 + 4l .. +3 with one 32-byte load, words r[8*step + 2t] (segment and
-// gathered index) and r[8*step + 2t + 1] (value bits) for t = 0..3; inactive lanes get zeros.
-template <int PF>
-__device__ __forceinline__ void load_lane(const int2* __restrict__ ent, int s0, int s1, int lane, int (&r)[8 * PF]) {
+// A warp's range [s0, s1) (both multiples of LE) in steps of 32 * LE entries: lane l takes entries
+// s0 + step*32*LE + l*LE .. +LE-1 with LE/4 32-byte loads, words r[2*(step*LE + t)] (segment and
+// gathered index) and r[2*(step*LE + t) + 1] (value bits) for t < LE; inactive lanes get zeros.
+template <int PF, int LE>
+__device__ __forceinline__ void load_lane(const int2* __restrict__ ent, int s0, int s1, int lane,
+                                          int (&r)[2 * LE * PF]) {
 #pragma unroll
     for (int st = 0; st < PF; ++st) {
-        const int base = s0 + st * 32 * LANE_E + lane * LANE_E;
-        if (base < s1) {
-            asm volatile("ld.global.nc.L1::no_allocate.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                         : "=r"(r[8 * st + 0]), "=r"(r[8 * st + 1]), "=r"(r[8 * st + 2]), "=r"(r[8 * st + 3]),
-                           "=r"(r[8 * st + 4]), "=r"(r[8 * st + 5]), "=r"(r[8 * st + 6]), "=r"(r[8 * st + 7])
-                         : "l"(ent + base));
-        } else {
+        const int base = s0 + st * 32 * LE + lane * LE;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) r[8 * st + q] = 0;
-        }
-    }
-}
-
-// One step of 32 * LANE_E entries of a warp. Each lane adds its four entries in order, keeping the
-// run of equal segments it is in; a run that ends inside the lane's entries (other than its first)
-// is added to the segment's sum at once. The runs that cross lane boundaries are joined by a
-// segmented scan over the lanes' last runs: a lane whose first run continues the previous lanes'
-// last run adds that carry, and only the lane where such a chain ends adds a chain that ends in its
-// last run. Every sum runs in the entries' order within the step; steps follow each other.
-template <int N>
-__device__ __forceinline__ void lane_step(const int (&r)[N], int q0, bool active, const float* vb, float* acc,
-                                          int lane) {
-    int cur = -1, kf = -1;
-    float run = 0.f, vf = 0.f;
-    bool multi = false;
-    if (active) {
-        float p[LANE_E];
-#pragma unroll
-        for (int t = 0; t < LANE_E; ++t) p[t] = __int_as_float(r[q0 + 2 * t + 1]) * vb[(uint32_t)r[q0 + 2 * t] >> 16];
-        cur = r[q0] & 0xFFFF;
-        run = p[0];
-#pragma unroll
-        for (int t = 1; t < LANE_E; ++t) {
-            const int key = r[q0 + 2 * t] & 0xFFFF;
-            if (key != cur) {
-                if (!multi) {
-                    kf = cur;
-                    vf = run;
-                    multi = true;
-                } else {
-                    acc[cur] += run;
-                }
-                cur = key;
-                run = p[t];
+        for (int h = 0; h < LE / 4; ++h) {
+            const int q = 2 * (st * LE + 4 * h);
+            if (base < s1) {
+                asm volatile("ld.global.nc.L1::no_allocate.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(r[q + 0]), "=r"(r[q + 1]), "=r"(r[q + 2]), "=r"(r[q + 3]), "=r"(r[q + 4]),
+                               "=r"(r[q + 5]), "=r"(r[q + 6]), "=r"(r[q + 7])
+                             : "l"(ent + base + 4 * h));
             } else {
-                run += p[t];
+#pragma unroll
+                for (int w = 0; w < 8; ++w) r[q + w] = 0;
             }
         }
     }
-    const int fk = multi ? kf : cur;  // first segment of the lane (-1: no entries)
-    float S = run;                    // last run, joined with the chain of lanes before it
+}
+
+// One step of 32 * LE entries of a warp. Each lane forms the sums of the runs of equal segments
+// among its LE entries (prefix sums that restart where the segment changes); a run that ends
+// inside the lane's entries, other than its first, is added to the segment's sum at once. Runs that
+// cross a lane boundary are joined: a lane whose first run continues the previous lane's last run
+// adds that lane's partial sum to its own, and a lane whose last run continues into the next lane
+// leaves it to that lane. A run through a whole lane (rare: more than LE entries of one segment)
+// takes a segmented scan over the lanes' last runs instead. Either way every sum runs in the
+// entries' order within the step, the same on every run; steps follow each other. A lane's runs
+// belong to distinct segments, so their read-modify-writes are issued as all loads, then all stores.
+template <int N, int LE>
+__device__ __forceinline__ void lane_step(const int (&r)[N], int q0, bool active, const float* vb, float* acc,
+                                          int lane) {
+    int k[LE];
+    float s[LE];
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const float o = __shfl_up_sync(FULL, S, d);
-        const int k = __shfl_up_sync(FULL, cur, d);
-        if (lane >= d && k == cur) S += o;
+    for (int t = 0; t < LE; ++t) {
+        k[t] = active ? (r[q0 + 2 * t] & 0xFFFF) : -1;
+        s[t] = active ? __int_as_float(r[q0 + 2 * t + 1]) * vb[(uint32_t)r[q0 + 2 * t] >> 16] : 0.f;
     }
-    const float sprev = __shfl_up_sync(FULL, S, 1);
-    const int kprev = __shfl_up_sync(FULL, cur, 1);
-    const int nfk = __shfl_down_sync(FULL, fk, 1);
-    if (multi) acc[kf] += vf + ((lane > 0 && kprev == kf) ? sprev : 0.f);
-    if (cur >= 0 && (lane == 31 || nfk != cur)) acc[cur] += S;
+#pragma unroll
+    for (int t = 1; t < LE; ++t) s[t] += (k[t] == k[t - 1]) ? s[t - 1] : 0.f;
+    bool mid[LE];
+    bool seen = false;  // a run has ended before entry t
+    float fs = s[LE - 1];
+#pragma unroll
+    for (int t = 0; t < LE - 1; ++t) {
+        const bool end = k[t + 1] != k[t];
+        mid[t] = active && end && seen;
+        if (end && !seen) fs = s[t];
+        seen = seen || end;
+    }
+    mid[LE - 1] = false;
+    const bool single = !seen;
+    const int fk = k[0], lk = k[LE - 1];
+    const float ls = s[LE - 1];
+    float old[LE];
+#pragma unroll
+    for (int t = 0; t < LE - 1; ++t)
+        if (mid[t]) old[t] = acc[k[t]];
+#pragma unroll
+    for (int t = 0; t < LE - 1; ++t)
+        if (mid[t]) acc[k[t]] = old[t] + s[t];
+    const int pk = __shfl_up_sync(FULL, lk, 1);
+    const float ps = __shfl_up_sync(FULL, ls, 1);
+    const int nk = __shfl_down_sync(FULL, fk, 1);
+    const bool cin = active && lane > 0 && pk == fk;
+    const bool cout = active && lane < 31 && nk == lk;
+    // firstv: the first run joined with the chain before the lane; lastv: the last run, joined with
+    // that chain too when the lane holds a single run
+    float firstv = fs + (cin ? ps : 0.f);
+    float lastv = (single && cin) ? ls + ps : ls;
+    if (__any_sync(FULL, single && cin && cout)) {
+        // a run spans three or more lanes: join the lanes' last runs by a segmented scan
+        float S = ls;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const float o = __shfl_up_sync(FULL, S, d);
+            const int kk = __shfl_up_sync(FULL, lk, d);
+            if (lane >= d && kk == lk) S += o;
+        }
+        const float sprev = __shfl_up_sync(FULL, S, 1);
+        firstv = fs + (cin ? sprev : 0.f);
+        lastv = S;
+    }
+    const bool wf = active && !single;  // first run, ending inside the lane
+    const bool wl = active && !cout;    // last run, ending here
+    const float of = wf ? acc[fk] : 0.f;
+    const float ol = wl ? acc[lk] : 0.f;
+    if (wf) acc[fk] = of + firstv;
+    if (wl) acc[lk] = ol + lastv;
 }
 
 // All entries of a warp's range [s0, s1) of one block: PF prefetched steps, then any further ones.
-template <int PF>
-__device__ __forceinline__ void run_range(const int (&r)[8 * PF], int s0, int s1, const int2* __restrict__ ent,
+template <int PF, int LE>
+__device__ __forceinline__ void run_range(const int (&r)[2 * LE * PF], int s0, int s1, const int2* __restrict__ ent,
                                           const float* vb, float* acc, int lane) {
 #pragma unroll
     for (int st = 0; st < PF; ++st) {
-        const int b0 = s0 + st * 32 * LANE_E;
-        if (b0 < s1) lane_step<8 * PF>(r, 8 * st, b0 + lane * LANE_E < s1, vb, acc, lane);
+        const int b0 = s0 + st * 32 * LE;
+        if (b0 < s1) lane_step<2 * LE * PF, LE>(r, 2 * LE * st, b0 + lane * LE < s1, vb, acc, lane);
         __syncwarp();
     }
-    for (int b0 = s0 + PF * 32 * LANE_E; b0 < s1; b0 += 32 * LANE_E) {
-        int t[8];
-        load_lane<1>(ent, b0, s1, lane, t);
-        lane_step<8>(t, 0, b0 + lane * LANE_E < s1, vb, acc, lane);
+    for (int b0 = s0 + PF * 32 * LE; b0 < s1; b0 += 32 * LE) {
+        int t[2 * LE];
+        load_lane<1, LE>(ent, b0, s1, lane, t);
+        lane_step<2 * LE, LE>(t, 0, b0 + lane * LE < s1, vb, acc, lane);
         __syncwarp();
     }
 }
@@ -197,18 +236,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 // Consumer side of block b (the CTA's block u): prefetch the warp's entries of block b + 2 into D,
 // wait for the stage, add the entries held in C, and release the stage.
-template <int RB, int PF, int S>
-__device__ __forceinline__ void block_step(int b, int R, uint32_t u, int (&C)[8 * PF], int (&D)[8 * PF],
+template <int RB, int PF, int LE, int S>
+__device__ __forceinline__ void block_step(int b, int R, uint32_t u, int (&C)[2 * LE * PF], int (&D)[2 * LE * PF],
                                            const int* spl, const StagedArgs& g, const float* vb, float* acc,
                                            uint64_t* full, uint64_t* empty, bool& bad, int warp, int lane) {
     if (b + 2 < R) {
         const int* sp = spl + (b + 2) * (NW + 1) + warp;
-        load_lane<PF>(g.ent, sp[0], sp[1], lane, D);
+        load_lane<PF, LE>(g.ent, sp[0], sp[1], lane, D);
     }
     const uint32_t k = u % S;
     if (!wait_block(full + k, (u / S) & 1u, g.spin)) bad = true;
     const int* sp = spl + b * (NW + 1) + warp;
-    run_range<PF>(C, sp[0], sp[1], g.ent, vb + k * RB, acc, lane);
+    run_range<PF, LE>(C, sp[0], sp[1], g.ent, vb + k * RB, acc, lane);
     __syncwarp();
     if (lane == 0) mbar_arrive(empty + k);
 }
@@ -219,9 +258,9 @@ __device__ __forceinline__ void block_step(int b, int R, uint32_t u, int (&C)[8 
 // Warp w owns the segments wseg[w] .. wseg[w+1]-1 of its group in every block: it alone adds into
 // their sums, and it runs their epilogue as soon as it has seen every block, while other warps
 // may still be streaming.
-template <int MODE, int RB, int PF, int S>
+template <int MODE, int RB, int PF, int LE, int S>
 __global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, const SweepArgs<float> a) {
-    constexpr int N = 8 * PF;
+    constexpr int N = 2 * LE * PF;
     extern __shared__ __align__(128) unsigned char smem[];
     float* vb = reinterpret_cast<float*>(smem);
     float* acc = vb + S * RB;
@@ -258,14 +297,14 @@ __global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, cons
             for (int t = ws + lane; t < we; t += 32) acc[t] = 0.f;
             __syncwarp();
             int A[N], B[N], C[N];
-            load_lane<PF>(g.ent, spl[warp], spl[warp + 1], lane, A);
-            if (R > 1) load_lane<PF>(g.ent, spl[NW + 1 + warp], spl[NW + 2 + warp], lane, B);
+            load_lane<PF, LE>(g.ent, spl[warp], spl[warp + 1], lane, A);
+            if (R > 1) load_lane<PF, LE>(g.ent, spl[NW + 1 + warp], spl[NW + 2 + warp], lane, B);
             for (int b = 0; b < R; b += 3) {
-                block_step<RB, PF, S>(b, R, u0 + b, A, C, spl, g, vb, acc, full, empty, bad, warp, lane);
+                block_step<RB, PF, LE, S>(b, R, u0 + b, A, C, spl, g, vb, acc, full, empty, bad, warp, lane);
                 if (b + 1 < R)
-                    block_step<RB, PF, S>(b + 1, R, u0 + b + 1, B, A, spl, g, vb, acc, full, empty, bad, warp, lane);
+                    block_step<RB, PF, LE, S>(b + 1, R, u0 + b + 1, B, A, spl, g, vb, acc, full, empty, bad, warp, lane);
                 if (b + 2 < R)
-                    block_step<RB, PF, S>(b + 2, R, u0 + b + 2, C, B, spl, g, vb, acc, full, empty, bad, warp, lane);
+                    block_step<RB, PF, LE, S>(b + 2, R, u0 + b + 2, C, B, spl, g, vb, acc, full, empty, bad, warp, lane);
             }
             __syncwarp();
             const float mu = a.mu;
@@ -328,10 +367,12 @@ __global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, cons
 }
 
 // the two instantiations the solver launches
-#define MFS_STAGED_COL \
-    ::mfs::staged::k_staged<0, ::mfs::staged::RB_COL, ::mfs::staged::PF_COL, ::mfs::staged::S_COL>
-#define MFS_STAGED_ROW \
-    ::mfs::staged::k_staged<1, ::mfs::staged::RB_ROW, ::mfs::staged::PF_ROW, ::mfs::staged::S_ROW>
+#define MFS_STAGED_COL                                                                                  \
+    ::mfs::staged::k_staged<0, ::mfs::staged::RB_COL, ::mfs::staged::PF_COL, ::mfs::staged::LE_COL, \
+                            ::mfs::staged::S_COL>
+#define MFS_STAGED_ROW                                                                                  \
+    ::mfs::staged::k_staged<1, ::mfs::staged::RB_ROW, ::mfs::staged::PF_ROW, ::mfs::staged::LE_ROW, \
+                            ::mfs::staged::S_ROW>
 
 }  // namespace staged
 }  // namespace mfs

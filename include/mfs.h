@@ -90,6 +90,11 @@ typedef struct {
     int32_t stop_rule;    /* MFS_STOP_KKT (default), MFS_STOP_SCS_L2 or MFS_STOP_OSQP_INF */
     double osqp_rel;      /* MFS_STOP_OSQP_INF: eps_rel / eps_abs, > 0 (default 10: the paper's
                              OSQP tolerances 1e-4 and 1e-3 at tol = 1e-4) */
+    int32_t sweep;        /* MFS_SWEEP_AUTO (default) or MFS_SWEEP_CHUNKED: chunked FP32 sweeps;
+                             MFS_SWEEP_STAGED: also build the staged layout (host time and device
+                             memory of a second copy of A) and use it; FP32_MIXED solvers without
+                             Lorentz cones only, others run the chunked kernels (mfs_get_info tells) */
+    int32_t reserved;     /* must be 0 */
 } mfs_settings;
 
 /* Residuals at the current (x, lambda); all accumulated in FP64.
@@ -127,7 +132,7 @@ typedef struct {
 } mfs_info_t;
 
 /* Defaults: mu = 1, check_every = 25, precision = MFS_FP64, polish_iters = 50, stop_rule =
-   MFS_STOP_KKT, osqp_rel = 10. */
+   MFS_STOP_KKT, osqp_rel = 10, sweep = MFS_SWEEP_AUTO. */
 void mfs_default_settings(mfs_settings* s);
 
 /*
@@ -155,8 +160,9 @@ mfs_status mfs_get_info(const mfs_solver* s, mfs_info_t* out);
 
 /* Choose the sweep kernels of the FP32 iteration: MFS_SWEEP_AUTO, MFS_SWEEP_CHUNKED or
    MFS_SWEEP_STAGED (see above). MFS_ERR_INVALID for an unknown kind, or for MFS_SWEEP_STAGED on a
-   solver created in FP64 or with Lorentz cones. The iterate is kept; FP64 iterations always use
-   the chunked kernels. */
+   solver whose staged layout was not built (created without settings.sweep = MFS_SWEEP_STAGED, in
+   FP64, or with Lorentz cones). The iterate is kept; FP64 iterations always use the chunked
+   kernels. */
 mfs_status mfs_set_sweep(mfs_solver* s, int32_t kind);
 
 /* Diagnostic of the bounded waits of the staged sweeps: runs one staged column pass that issues

@@ -1248,6 +1248,8 @@ void mfs_default_settings(mfs_settings* st) {
     st->polish_iters = 50;
     st->stop_rule = MFS_STOP_KKT;
     st->osqp_rel = 10.0;
+    st->sweep = MFS_SWEEP_AUTO;
+    st->reserved = 0;
 }
 
 const char* mfs_last_error(const mfs_solver* s) {
@@ -1291,6 +1293,8 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
         return fail(nullptr, MFS_ERR_INVALID, "unknown stop_rule");
     if (!(set.osqp_rel > 0.0) || !std::isfinite(set.osqp_rel))
         return fail(nullptr, MFS_ERR_INVALID, "osqp_rel must be > 0");
+    if (set.sweep != MFS_SWEEP_AUTO && set.sweep != MFS_SWEEP_CHUNKED && set.sweep != MFS_SWEEP_STAGED)
+        return fail(nullptr, MFS_ERR_INVALID, "unknown sweep kind");
     int64_t total = 0;
     for (int64_t q = 0; q < ncones; ++q) {
         if (cones[q].size < 1) return fail(nullptr, MFS_ERR_INVALID, "cone of size < 1");
@@ -1403,7 +1407,8 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
         CHK(alloc_state<float>(s, s->s32, P, b, c));
         CHK(residual_grids<float>(s));
         s->have32 = true;
-        if (!s->has_soc && P.o > 0) CHK(setup_staged(s, P));
+        if (set.sweep == MFS_SWEEP_STAGED && !s->has_soc && P.o > 0) CHK(setup_staged(s, P));
+        s->sweep_kind = s->stg_ok ? set.sweep : MFS_SWEEP_AUTO;
     }
     if (set.precision == MFS_FP64 || set.polish_iters > 0) {
         CHK(alloc_state<double>(s, s->s64, P, b, c));
@@ -1474,7 +1479,9 @@ mfs_status mfs_set_sweep(mfs_solver* s, int32_t kind) {
     if (kind != MFS_SWEEP_AUTO && kind != MFS_SWEEP_CHUNKED && kind != MFS_SWEEP_STAGED)
         return fail(s, MFS_ERR_INVALID, "unknown sweep kind");
     if (kind == MFS_SWEEP_STAGED && !s->stg_ok)
-        return fail(s, MFS_ERR_INVALID, "staged sweeps need an FP32_MIXED solver without Lorentz cones");
+        return fail(s, MFS_ERR_INVALID,
+                    "no staged layout: create the solver with settings.sweep = MFS_SWEEP_STAGED (FP32_MIXED, "
+                    "orthant cones only)");
     CUDA_TRY(s, cudaSetDevice(s->device));
     CUDA_TRY(s, cudaStreamSynchronize(s->stream));
     destroy_graphs(s);

@@ -40,7 +40,8 @@ class Cone(ctypes.Structure):
 
 class Settings(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_double), ("check_every", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("polish_iters", ctypes.c_int32), ("stop_rule", ctypes.c_int32), ("osqp_rel", ctypes.c_double)]
+                ("polish_iters", ctypes.c_int32), ("stop_rule", ctypes.c_int32), ("osqp_rel", ctypes.c_double),
+                ("sweep", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 RESID_FIELDS = ("r_prim", "r_dual", "r_cone", "r_gap", "kkt", "pobj", "dobj",
@@ -142,7 +143,7 @@ class Solver:
     (as made by ``instances``)."""
 
     def __init__(self, prob, mu=1.0, check_every=25, precision="fp64", polish_iters=50, stream=None,
-                 stop_rule="kkt", osqp_rel=10.0):
+                 stop_rule="kkt", osqp_rel=10.0, sweep="auto"):
         lib = load()
         self._lib = lib
         m, n = int(prob["m"]), int(prob["n"])
@@ -165,6 +166,7 @@ class Solver:
         st.polish_iters = int(polish_iters)
         st.stop_rule = STOP_RULES[stop_rule] if isinstance(stop_rule, str) else int(stop_rule)
         st.osqp_rel = float(osqp_rel)
+        st.sweep = SWEEPS[sweep] if isinstance(sweep, str) else int(sweep)
         h = ctypes.c_void_p()
         stream_ptr = ctypes.c_void_p(int(stream)) if stream else None
         code = lib.mfs_create(m, n, len(row), row.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),

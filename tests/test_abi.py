@@ -35,7 +35,7 @@ def _c_layout(tmp_path):
         '#include <stddef.h>\n#include <stdio.h>\n#include "mfs.h"\n'
         "int main(void) {\n"
         '  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mfs_cone), sizeof(mfs_settings),\n'
-        "         sizeof(mfs_residuals_t), offsetof(mfs_settings, stop_rule), offsetof(mfs_settings, osqp_rel),\n"
+        "         sizeof(mfs_residuals_t), offsetof(mfs_settings, stop_rule), offsetof(mfs_settings, sweep),\n"
         "         offsetof(mfs_residuals_t, r_osqp), offsetof(mfs_residuals_t, iter));\n"
         "  return 0;\n}\n")
     exe = tmp_path / "layout"
@@ -45,16 +45,16 @@ def _c_layout(tmp_path):
 
 
 def test_struct_sizes_match_header(lib, tmp_path):
-    cone, settings, resid, off_rule, off_rel, off_osqp, off_iter = _c_layout(tmp_path)
+    cone, settings, resid, off_rule, off_sweep, off_osqp, off_iter = _c_layout(tmp_path)
     assert ctypes.sizeof(mfs.Cone) == cone == 16
     assert ctypes.sizeof(mfs.Settings) == settings
-    assert mfs.Settings.stop_rule.offset == off_rule and mfs.Settings.osqp_rel.offset == off_rel
+    assert mfs.Settings.stop_rule.offset == off_rule and mfs.Settings.sweep.offset == off_sweep
     assert ctypes.sizeof(mfs.Residuals) == resid
     assert mfs.Residuals.r_osqp.offset == off_osqp and mfs.Residuals.iter.offset == off_iter
     st = mfs.Settings()
     lib.mfs_default_settings(ctypes.byref(st))
     assert (st.mu, st.check_every, st.precision, st.polish_iters) == (1.0, 25, 0, 50)
-    assert (st.stop_rule, st.osqp_rel) == (mfs.STOP_KKT, 10.0)
+    assert (st.stop_rule, st.osqp_rel, st.sweep) == (mfs.STOP_KKT, 10.0, mfs.SWEEP_AUTO)
 
 
 def tiny():

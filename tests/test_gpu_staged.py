@@ -23,8 +23,7 @@ def lib():
 
 def staged_pair(prob, iters, mu=1.0):
     orc = oracle.make_oracle(prob, mu=mu, dtype=np.float32)
-    s = mfs.Solver(prob, mu=mu, precision="fp32", polish_iters=0, check_every=25)
-    s.set_sweep("staged")
+    s = mfs.Solver(prob, mu=mu, precision="fp32", polish_iters=0, check_every=25, sweep="staged")
     info = s.info()
     assert info["sweep_col"] == mfs.SWEEP_STAGED and info["sweep_row"] == mfs.SWEEP_STAGED
     orc.iterate(iters)
@@ -58,9 +57,7 @@ def test_more_groups_than_sms():
 def test_chunked_and_staged_agree_with_each_other_within_fp32():
     prob = I.large_lp(2, m=20_000, n=50_000)
     a = mfs.Solver(prob, precision="fp32", polish_iters=0)
-    b = mfs.Solver(prob, precision="fp32", polish_iters=0)
-    a.set_sweep("chunked")
-    b.set_sweep("staged")
+    b = mfs.Solver(prob, precision="fp32", polish_iters=0, sweep="staged")
     a.iterate(30)
     b.iterate(30)
     sa, sb = a.solution(), b.solution()
@@ -71,10 +68,8 @@ def test_chunked_and_staged_agree_with_each_other_within_fp32():
 
 def test_repeatable_bitwise():
     prob = I.large_lp(3, m=20_000, n=50_000)
-    a = mfs.Solver(prob, precision="fp32")
-    b = mfs.Solver(prob, precision="fp32")
-    a.set_sweep("staged")
-    b.set_sweep("staged")
+    a = mfs.Solver(prob, precision="fp32", sweep="staged")
+    b = mfs.Solver(prob, precision="fp32", sweep="staged")
     a.iterate(40)
     b.iterate(40)
     sa, sb = a.solution(), b.solution()
@@ -84,8 +79,7 @@ def test_repeatable_bitwise():
 
 def test_solve_with_staged_sweeps_and_polish():
     prob = I.small_lp(0, m=200, n=500)
-    s = mfs.Solver(prob, precision="fp32", check_every=50, polish_iters=100)
-    s.set_sweep("staged")
+    s = mfs.Solver(prob, precision="fp32", check_every=50, polish_iters=100, sweep="staged")
     status, its = s.solve(1e-6, 400_000)
     assert status == "OK"
     assert s.residuals()["kkt"] <= 1e-6
@@ -93,20 +87,28 @@ def test_solve_with_staged_sweeps_and_polish():
 
 def test_auto_choice_and_invalid_requests():
     big = I.large_lp(1, m=60_000, n=150_000)   # 1.2 M nonzeros, 20 per row and 8 per column
-    s = mfs.Solver(big, precision="fp32")
-    info = s.info()
+    plain = mfs.Solver(big, precision="fp32")
+    info = plain.info()
     assert (info["sweep_col"], info["sweep_row"]) == (mfs.SWEEP_CHUNKED, mfs.SWEEP_CHUNKED)  # auto
+    with pytest.raises(mfs.MfsError) as e:                    # no staged layout built
+        plain.set_sweep("staged")
+    assert e.value.status == mfs.MFS_ERR_INVALID
+    s = mfs.Solver(big, precision="fp32", sweep="staged")
+    info = s.info()
+    assert (info["sweep_col"], info["sweep_row"]) == (mfs.SWEEP_STAGED, mfs.SWEEP_STAGED)
+    s.set_sweep("chunked")
+    assert s.info()["sweep_col"] == mfs.SWEEP_CHUNKED
     s.set_sweep("staged")
     info = s.info()
     assert (info["sweep_col"], info["sweep_row"]) == (mfs.SWEEP_STAGED, mfs.SWEEP_STAGED)
     assert info["launches_per_iter"] == 2
     s.set_sweep("auto")
     assert s.info()["sweep_col"] == mfs.SWEEP_CHUNKED
-    f64 = mfs.Solver(I.small_lp(0), precision="fp64")
+    f64 = mfs.Solver(I.small_lp(0), precision="fp64", sweep="staged")
     with pytest.raises(mfs.MfsError) as e:
         f64.set_sweep("staged")
     assert e.value.status == mfs.MFS_ERR_INVALID
-    soc = mfs.Solver(I.socp(0, n=3000, m=1200), precision="fp32")
+    soc = mfs.Solver(I.socp(0, n=3000, m=1200), precision="fp32", sweep="staged")
     with pytest.raises(mfs.MfsError) as e:
         soc.set_sweep("staged")
     assert e.value.status == mfs.MFS_ERR_INVALID
@@ -118,8 +120,7 @@ def test_bounded_wait_gives_up_and_context_survives():
     """The staged kernel's waits for its vector blocks are bounded: with the copies suppressed every
     wait gives up, the kernel reports it, and the solver works afterwards."""
     prob = I.large_lp(4, m=20_000, n=50_000)
-    s = mfs.Solver(prob, precision="fp32", polish_iters=0)
-    s.set_sweep("staged")
+    s = mfs.Solver(prob, precision="fp32", polish_iters=0, sweep="staged")
     assert s.staged_wait_test() == "ERR_TIMEOUT"
     x0, lam0 = np.zeros(prob["n"]), np.zeros(prob["m"])
     s.warm_start(x0, lam0)

@@ -85,11 +85,69 @@ void parallel_tasks(int nt, F f) {
     for (auto& th : pool) th.join();
 }
 
+// Stable LSD radix sort in two passes of about half the key's bits each, on (key, item) pairs, for
+// keys too many for per-thread histograms of every key. Same contract as counting_sort.
+template <class Key>
+void radix_sort2(int64_t n, int64_t k, Key key, const int64_t* items, int64_t* out, std::vector<int64_t>* starts) {
+    const int nt = threads_for(n);
+    int bits = 1;
+    while ((int64_t(1) << bits) < k) ++bits;
+    const int lo_bits = bits / 2;
+    const int64_t nb[2] = {int64_t(1) << lo_bits, int64_t(1) << (bits - lo_bits)};
+    uvec<uint32_t> k0((size_t)n), kf((size_t)n);
+    uvec<int64_t> v0((size_t)n);
+    std::vector<std::vector<int64_t>> cnt(nt);
+    // pass: stable scatter of [0, n) by digit d of the key; src gives (key, item) of position q
+    auto pass = [&](int d, auto src, uint32_t* kout, int64_t* vout) {
+        const int shift = d == 0 ? 0 : lo_bits;
+        const uint32_t mask = (uint32_t)(nb[d] - 1);
+        for (auto& c : cnt) c.clear();
+        parallel_ranges(n, nt, [&](int64_t lo, int64_t hi, int t) {
+            cnt[t].assign((size_t)nb[d], 0);
+            int64_t* h = cnt[t].data();
+            for (int64_t q = lo; q < hi; ++q) ++h[(src(q).first >> shift) & mask];
+        });
+        int64_t run = 0;
+        for (int64_t b = 0; b < nb[d]; ++b)
+            for (int t = 0; t < nt; ++t) {
+                if (cnt[t].empty()) continue;
+                const int64_t c = cnt[t][b];
+                cnt[t][b] = run;
+                run += c;
+            }
+        parallel_ranges(n, nt, [&](int64_t lo, int64_t hi, int t) {
+            int64_t* h = cnt[t].data();
+            for (int64_t q = lo; q < hi; ++q) {
+                const auto kv = src(q);
+                const int64_t at = h[(kv.first >> shift) & mask]++;
+                kout[at] = kv.first;
+                vout[at] = kv.second;
+            }
+        });
+    };
+    pass(0, [&](int64_t q) { return std::pair<uint32_t, int64_t>((uint32_t)key(q), items ? items[q] : q); },
+         k0.data(), v0.data());
+    pass(1, [&](int64_t q) { return std::pair<uint32_t, int64_t>(k0[q], v0[q]); }, kf.data(), out);
+    if (starts) {
+        starts->assign((size_t)k + 1, n);
+        int64_t* st = starts->data();
+        parallel_ranges(n, nt, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t p = lo; p < hi; ++p)
+                for (int64_t j = p ? (int64_t)kf[p - 1] + 1 : 0; j <= (int64_t)kf[p]; ++j) st[j] = p;
+        });
+    }
+}
+
 // Stable counting sort of the positions q in [0, n) by key(q) in [0, k): out[p] = items ? items[q] : q
-// in order of (key, q). starts (nullable) receives the k+1 bucket offsets. n < 2^32.
+// in order of (key, q). starts (nullable) receives the k+1 bucket offsets. n < 2^32. Many keys
+// (more than 2^16, with several threads) go through radix_sort2 instead.
 template <class Key>
 void counting_sort(int64_t n, int64_t k, Key key, const int64_t* items, int64_t* out, std::vector<int64_t>* starts) {
     const int nt = threads_for(n);
+    if (nt > 1 && k > (int64_t(1) << 16) && k <= (int64_t(1) << 32)) {
+        radix_sort2(n, k, key, items, out, starts);
+        return;
+    }
     // cnt[t][b]: entries of bucket b in thread t's range; then, in place, where thread t writes its
     // first entry of bucket b: all entries of smaller buckets plus those of b in threads < t
     std::vector<std::vector<uint32_t>> cnt(nt, std::vector<uint32_t>((size_t)k, 0u));

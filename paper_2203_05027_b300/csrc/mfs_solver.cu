@@ -168,18 +168,14 @@ mfs_status upload(mfs_solver* s, T** p, const void* host, size_t count) {
 // Sort COO into column order (rows ascending within a column), sum duplicates, drop zeros;
 // then build the row order (columns ascending within a row). Stable counting sorts, O(nnz + m + n),
 // multi-threaded (mfs_host.h); an input already in strict column order skips the sorting.
+// in_order: the caller found the input in strict (column, row) order.
 void build_orders(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col, const double* val,
-                  HostProblem& P) {
+                  bool in_order, HostProblem& P) {
     using namespace mfs::host;
     const int nt = threads_for(nnz);
     // order of the input entries by (column, row)
-    std::vector<char> unsorted(nt, 0);
-    parallel_ranges(nnz > 0 ? nnz - 1 : 0, nt, [&](int64_t lo, int64_t hi, int t) {
-        for (int64_t q = lo; q < hi && !unsorted[t]; ++q)
-            if (col[q] > col[q + 1] || (col[q] == col[q + 1] && row[q] >= row[q + 1])) unsorted[t] = 1;
-    });
     uvec<int64_t> ord((size_t)nnz);
-    if (std::find(unsorted.begin(), unsorted.end(), 1) == unsorted.end()) {
+    if (in_order) {
         parallel_ranges(nnz, nt, [&](int64_t lo, int64_t hi, int) {
             for (int64_t q = lo; q < hi; ++q) ord[q] = q;
         });
@@ -463,8 +459,8 @@ bool build_staged(const std::vector<int>& ptr, const mfs::host::uvec<int>& idx, 
 }
 
 mfs_status setup_host(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
-                      const double* val, int64_t ncones, const mfs_cone* cones, HostProblem& P) {
-    build_orders(m, n, nnz, row, col, val, P);
+                      const double* val, bool in_order, int64_t ncones, const mfs_cone* cones, HostProblem& P) {
+    build_orders(m, n, nnz, row, col, val, in_order, P);
     // Lorentz cones; unit_end[j] = end of the small cone starting at j, or j+1
     std::vector<int> unit_end(n);
     for (int64_t j = 0; j < n; ++j) unit_end[j] = (int)j + 1;
@@ -484,8 +480,12 @@ mfs_status setup_host(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const in
         }
         off += sz;
     }
-    build_chunks(P.col_ptr, (int)n, &unit_end, P.cc);
-    build_chunks(P.row_ptr, (int)m, nullptr, P.rc);
+    mfs::host::parallel_tasks(2, [&](int t) {
+        if (t == 0)
+            build_chunks(P.col_ptr, (int)n, &unit_end, P.cc);
+        else
+            build_chunks(P.row_ptr, (int)m, nullptr, P.rc);
+    });
     if (P.cc.padded >= INT32_MAX - PAD || P.rc.padded >= INT32_MAX - PAD)
         return fail(s, MFS_ERR_INVALID, "too many nonzeros after padding (limit 2^31)");
     // Lorentz cones intersecting each column chunk
@@ -1303,16 +1303,22 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
         total += cones[q].size;
     }
     if (total != n) return fail(nullptr, MFS_ERR_INVALID, "cone sizes do not sum to n");
+    bool in_order = false;
     {
-        // first bad entry: index out of range, or a non-finite value
+        // first bad entry: index out of range, or a non-finite value; and whether the entries are
+        // already in strict (column, row) order
         const int nt = mfs::host::threads_for(nnz);
         std::vector<int64_t> bad_idx(nt, nnz), bad_val(nt, nnz);
+        std::vector<char> unsorted(nt, 0);
         mfs::host::parallel_ranges(nnz, nt, [&](int64_t lo, int64_t hi, int t) {
             for (int64_t q = lo; q < hi; ++q) {
                 if (bad_idx[t] == nnz && (row[q] < 0 || row[q] >= m || col[q] < 0 || col[q] >= n)) bad_idx[t] = q;
                 if (bad_val[t] == nnz && !std::isfinite(val[q])) bad_val[t] = q;
+                if (q + 1 < nnz && (col[q] > col[q + 1] || (col[q] == col[q + 1] && row[q] >= row[q + 1])))
+                    unsorted[t] = 1;
             }
         });
+        in_order = std::find(unsorted.begin(), unsorted.end(), 1) == unsorted.end();
         const int64_t bi = *std::min_element(bad_idx.begin(), bad_idx.end());
         const int64_t bv = *std::min_element(bad_val.begin(), bad_val.end());
         if (bi < nnz && bi <= bv)
@@ -1350,7 +1356,7 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
         return bail(MFS_ERR_CUDA);
     }
     HostProblem P;
-    mfs_status st = setup_host(s, m, n, nnz, row, col, val, ncones, cones, P);
+    mfs_status st = setup_host(s, m, n, nnz, row, col, val, in_order, ncones, cones, P);
     if (st != MFS_OK) return bail(st);
     s->m = P.m;
     s->n = P.n;

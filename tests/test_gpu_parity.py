@@ -295,3 +295,24 @@ def test_socp_full_size_fp32_parity():
     prob = I.socp(0)
     orc, s = run_pair(prob, 3, "fp32")
     compare(s.solution(), orc.state(), TOL["fp32"], "socp full size")
+
+
+def test_unsorted_coo_with_duplicates_above_two_million_entries():
+    """A COO list in random order with repeated (row, column) pairs and explicit zeros, large enough
+    that the set-up orders it with the multi-threaded radix path: the solver must see the same summed
+    matrix as the oracle (which sums duplicates itself)."""
+    base = I.large_lp(5, m=70_000, n=175_000)        # about 1.4 M distinct entries; m, n > 2^16
+    rng = np.random.default_rng(11)
+    k = base["row"].size
+    dup = rng.choice(k, 900_000, replace=False)
+    extra_val = rng.standard_normal(dup.size)
+    row = np.r_[base["row"], base["row"][dup]]
+    col = np.r_[base["col"], base["col"][dup]]
+    val = np.r_[base["val"], extra_val]
+    val[rng.choice(k, 5000, replace=False)] = 0.0     # explicit zeros (summed with any duplicates)
+    perm = rng.permutation(row.size)
+    prob = dict(base, row=row[perm], col=col[perm], val=val[perm])
+    assert prob["row"].size > (1 << 21)    # both sorts (by row, then by column) take the radix path
+    orc, s = run_pair(prob, 40, "fp64")
+    compare(s.solution(), orc.state(), TOL["fp64"], "unsorted COO")
+    assert s.info()["o"] == oracle.make_oracle(prob).uv()[0].size

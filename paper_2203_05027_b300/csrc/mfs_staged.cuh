@@ -13,8 +13,8 @@
 // Within one (group, block) the entries are cut into NW ranges, one per warp, at segment boundaries
 // (precomputed), so that no two warps add into the same segment sum and every sum runs in a fixed
 // order: blocks in turn, entries in order within a block. Each range is padded with zero entries of
-// its last segment to a multiple of the entries one lane loads at once (LE: 8 for the column pass,
-// 4 for the row pass).
+// its last segment to a multiple of the entries one lane loads at once (LE: 6 for the column pass,
+// about the 146 entries a warp takes per block in one 192-entry step; 4 for the row pass).
 //
 // Every CTA reads the whole vector once per pass (148 x 4 MB for a 10^6-row v), which L2 serves
 // at about 28 TB/s to all SMs; the random gathers then cost shared-memory bank cycles instead of
@@ -50,8 +50,8 @@ constexpr int NW = MFS_STG_NW;  // consumer warps per CTA, plus one producer war
 constexpr int NTS = 32 * NW;
 constexpr int MAXG = 24576;    // segments per group (their sums take 96 KB of shared memory)
 #ifndef MFS_STG_LE_COL
-#define MFS_STG_LE_COL 4
-#define MFS_STG_PF_COL 2
+#define MFS_STG_LE_COL 6
+#define MFS_STG_PF_COL 1
 #endif
 #ifndef MFS_STG_LE_ROW
 #define MFS_STG_LE_ROW 4
@@ -111,25 +111,42 @@ __device__ __forceinline__ bool wait_block(uint64_t* bar, uint32_t parity, int s
 }
 
 // A warp's range [s0, s1) (both multiples of LE) in steps of 32 * LE entries: lane l takes entries
-// s0 + step*32*LE + l*LE .. +LE-1 with LE/4 32-byte loads, words r[2*(step*LE + t)] (segment and
-// gathered index) and r[2*(step*LE + t) + 1] (value bits) for t < LE; inactive lanes get zeros.
+// s0 + step*32*LE + l*LE .. +LE-1 with 32-byte loads (LE a multiple of 4) or 16-byte loads, words
+// r[2*(step*LE + t)] (segment and gathered index) and r[2*(step*LE + t) + 1] (value bits) for t < LE;
+// inactive lanes get zeros.
 template <int PF, int LE>
 __device__ __forceinline__ void load_lane(const int2* __restrict__ ent, int s0, int s1, int lane,
                                           int (&r)[2 * LE * PF]) {
+    static_assert(LE % 2 == 0, "entries per lane come in 16-byte pairs");
 #pragma unroll
     for (int st = 0; st < PF; ++st) {
         const int base = s0 + st * 32 * LE + lane * LE;
+        if (LE % 4 == 0) {  // 32-byte loads, bypassing L1 (each sector is used by one load)
 #pragma unroll
-        for (int h = 0; h < LE / 4; ++h) {
-            const int q = 2 * (st * LE + 4 * h);
-            if (base < s1) {
-                asm volatile("ld.global.nc.L1::no_allocate.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                             : "=r"(r[q + 0]), "=r"(r[q + 1]), "=r"(r[q + 2]), "=r"(r[q + 3]), "=r"(r[q + 4]),
-                               "=r"(r[q + 5]), "=r"(r[q + 6]), "=r"(r[q + 7])
-                             : "l"(ent + base + 4 * h));
-            } else {
+            for (int h = 0; h < LE / 4; ++h) {
+                const int q = 2 * (st * LE + 4 * h);
+                if (base < s1) {
+                    asm volatile("ld.global.nc.L1::no_allocate.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                 : "=r"(r[q + 0]), "=r"(r[q + 1]), "=r"(r[q + 2]), "=r"(r[q + 3]), "=r"(r[q + 4]),
+                                   "=r"(r[q + 5]), "=r"(r[q + 6]), "=r"(r[q + 7])
+                                 : "l"(ent + base + 4 * h));
+                } else {
 #pragma unroll
-                for (int w = 0; w < 8; ++w) r[q + w] = 0;
+                    for (int w = 0; w < 8; ++w) r[q + w] = 0;
+                }
+            }
+        } else {  // 16-byte loads through L1 (consecutive loads of a warp share sectors)
+#pragma unroll
+            for (int h = 0; h < LE / 2; ++h) {
+                const int q = 2 * (st * LE + 2 * h);
+                if (base < s1) {
+                    asm volatile("ld.global.nc.v4.b32 {%0,%1,%2,%3}, [%4];"
+                                 : "=r"(r[q + 0]), "=r"(r[q + 1]), "=r"(r[q + 2]), "=r"(r[q + 3])
+                                 : "l"(ent + base + 2 * h));
+                } else {
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) r[q + w] = 0;
+                }
             }
         }
     }

@@ -171,6 +171,15 @@ mfs_status mfs_set_sweep(mfs_solver* s, int32_t kind);
    and must be reset (mfs_warm_start) before further use. MFS_ERR_INVALID without staged sweeps. */
 mfs_status mfs_debug_staged_wait_test(mfs_solver* s);
 
+/* Bounds-checked build (libmfs_bounds.so, compiled with MFS_DEBUG_BOUNDS): the single-instance sweep
+   and residual kernels check every gather index, padded-entry load and shared-memory index, skip
+   an access that fails (reading 0) and record the first failure. mfs_debug_bounds returns 1 in
+   that build and 0 otherwise; *site (nullable) receives the failed check's site (0: none so far;
+   1 padded entries, 2 v gathered by the column sweep, 3 x by the row sweep, 4 lambda by the
+   column residual, 5 x by the row residual, 6/7/8 the staged vector block, segment sums and
+   entries) and *index (nullable) the low 40 bits of the index; reset clears the record. */
+int32_t mfs_debug_bounds(int64_t* site, int64_t* index, int32_t reset);
+
 /* Change mu (Algorithm 1 takes mu fixed; F_U and F_V do not depend on it, so no set-up is
    repeated). The iterate is kept. mu must be > 0. */
 mfs_status mfs_set_mu(mfs_solver* s, double mu);

@@ -18,24 +18,31 @@ def _stale(lib, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False, extra=()):
+LIB_BOUNDS = os.path.join(HERE, "libmfs_bounds.so")
+
+
+def build(force=False, verbose=False, extra=(), bounds=False):
+    """Compile libmfs.so, or with bounds=True the bounds-checked libmfs_bounds.so (MFS_DEBUG_BOUNDS:
+    the single-instance sweep and residual kernels check every gather and padded-entry index)."""
+    lib = LIB_BOUNDS if bounds else LIB
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
     deps.append(os.path.join(os.path.dirname(HERE), "include", "mfs.h"))
-    if not force and not _stale(LIB, deps):
-        return LIB
+    if not force and not _stale(lib, deps):
+        return lib
     nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-O2", "-Xcompiler", "-pthread", "--expt-relaxed-constexpr", *extra,
+           "-Xcompiler", "-O2", "-Xcompiler", "-pthread", "--expt-relaxed-constexpr",
+           *(["-DMFS_DEBUG_BOUNDS"] if bounds else []), *extra,
            "-o", tmp, *[os.path.join(CSRC, f) for f in SOURCES], "-lcudart"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
         print(" ".join(cmd), file=sys.stderr)
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+    build(force="--force" in sys.argv, verbose="-v" in sys.argv, bounds="--bounds" in sys.argv)
+    print(LIB_BOUNDS if "--bounds" in sys.argv else LIB)

@@ -18,6 +18,33 @@ constexpr int PAD = 8;            // chunk starts in the padded nonzero arrays a
 constexpr int TAIL = WT;          // the padded nonzero arrays end with this many spare entries
 constexpr unsigned FULL = 0xffffffffu;
 
+// Bounds-checked build (-DMFS_DEBUG_BOUNDS, libmfs_bounds.so): every gather index, padded-entry
+// load and shared-memory index of the single-instance sweep and residual kernels is checked; a
+// failed check records its site and index (the first one wins) and the access is skipped (the value
+// read as 0) instead of trapping. A stand-in for a memory checker. In the normal build the checks
+// compile to nothing.
+enum BoundsSite : int {
+    BS_ENTRIES = 1,   // padded nonzero arrays of the chunked layout
+    BS_GATHER_V = 2,  // v gathered by the column sweep
+    BS_GATHER_X = 3,  // x gathered by the row sweep
+    BS_GATHER_L = 4,  // lambda gathered by the column residual
+    BS_GATHER_XR = 5, // x gathered by the row residual
+    BS_STG_VEC = 6,   // staged vector block in shared memory
+    BS_STG_ACC = 7,   // staged segment sums in shared memory
+    BS_STG_ENT = 8    // staged entry arrays
+};
+#ifdef MFS_DEBUG_BOUNDS
+static __device__ unsigned long long g_bounds_fail;  // (site << 40) | low 40 bits of the index
+__device__ __forceinline__ bool in_bounds(long long idx, long long lim, int site) {
+    const bool ok = idx >= 0 && idx < lim;
+    if (!ok) atomicCAS(&g_bounds_fail, 0ull, ((unsigned long long)site << 40) | ((unsigned long long)idx & 0xFFFFFFFFFFull));
+    return ok;
+}
+#define MFS_INB(idx, lim, site) ::mfs::in_bounds((long long)(idx), (long long)(lim), (site))
+#else
+#define MFS_INB(idx, lim, site) true
+#endif
+
 // Shared-memory slot of local nonzero e in a per-warp array: one word of padding per 32 keeps
 // the lanes' segment-end stores (lane l writes near 8l) off the same banks.
 __device__ __forceinline__ int eslot(int e) {

@@ -67,11 +67,19 @@ struct SweepArgs {
     T mu;
     int ntc, ntr;      // column / row chunks
     int nlc, nlr;      // long column / row chunks
+    int m, n;          // bounds of the checked build (gathered indices)
+    long long cpad, rpad;  // lengths of the padded column / row nonzero arrays
 };
 
 template <typename T>
 __device__ __forceinline__ T ldro(const T* p) {
     return __ldg(p);
+}
+
+// w[i] through the read-only path; in the checked build i is checked against lim first.
+template <typename T>
+__device__ __forceinline__ T gat(const T* __restrict__ w, int i, int lim, int site) {
+    return MFS_INB(i, lim, site) ? __ldg(w + i) : T(0);
 }
 
 // Segment sums of one chunk held by one warp. heads: the chunk's 8-word start bitmap (bit e set
@@ -80,11 +88,12 @@ __device__ __forceinline__ T ldro(const T* p) {
 // nonzero is local item e.
 template <typename T, typename A, int NV, typename Prod>
 __device__ __forceinline__ void warp_chunk_sums(const int* __restrict__ gidx, const T* __restrict__ gval, int koff,
-                                                int nnz, const uint32_t* __restrict__ heads, A* s_end, Prod prod) {
+                                                int nnz, const uint32_t* __restrict__ heads, A* s_end, Prod prod,
+                                                long long pad) {
     const int lane = threadIdx.x & 31;
     const int e0 = lane * IPT;
     A p[IPT][NV];
-    if (e0 < nnz) {
+    if (e0 < nnz && MFS_INB((long long)koff + e0 + IPT - 1, pad, BS_ENTRIES)) {
         int id[IPT];
         T vl[IPT];
         ld256(gidx + koff + e0, id);
@@ -213,8 +222,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? MFS_SWEEP_MINB : 1) k_col
     }
     const int kb = __shfl_sync(FULL, cs[0], 0);
     const T* __restrict__ v = a.v;
-    auto prod = [v](int i, T val, T (&p)[1]) { p[0] = val * ldro(v + i); };
-    warp_chunk_sums<T, T, 1>(a.cidx, a.cval, koff, nnz, a.cheads + (size_t)ch * 8, s_end[warp], prod);
+    const int m = a.m;
+    auto prod = [v, m](int i, T val, T (&p)[1]) { p[0] = val * gat(v, i, m, BS_GATHER_V); };
+    warp_chunk_sums<T, T, 1>(a.cidx, a.cval, koff, nnz, a.cheads + (size_t)ch * 8, s_end[warp], prod, a.cpad);
 #pragma unroll
     for (int k = 0; k < CPL; ++k) {
         const int jl = lane + 32 * k;
@@ -268,7 +278,9 @@ __global__ void __launch_bounds__(NT) k_col_long(const SweepArgs<T> a) {
     const int j = dsc.x, koff = dsc.z, nnz = dsc.w;
     Sums<T, 1> s;
     s.v[0] = T(0);
-    for (int e = threadIdx.x; e < nnz; e += NT) s.v[0] += a.cval[koff + e] * ldro(a.v + a.cidx[koff + e]);
+    for (int e = threadIdx.x; e < nnz; e += NT)
+        if (MFS_INB((long long)koff + e, a.cpad, BS_ENTRIES))
+            s.v[0] += a.cval[koff + e] * gat(a.v, a.cidx[koff + e], a.m, BS_GATHER_V);
     s = block_sum<T, 1>(s, sh);
     if (threadIdx.x == 0) {
         const T mu = a.mu, dj = a.del[j];
@@ -350,11 +362,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? MFS_SWEEP_MINB : 1) k_row
     }
     const int kb = __shfl_sync(FULL, cs[0], 0);
     const T* __restrict__ x = a.x;
-    auto prod = [x](int j, T val, T (&p)[2]) {
-        p[0] = val * ldro(x + j);
+    const int n = a.n;
+    auto prod = [x, n](int j, T val, T (&p)[2]) {
+        p[0] = val * gat(x, j, n, BS_GATHER_X);
         p[1] = val * val;
     };
-    warp_chunk_sums<T, T, 2>(a.ridx, a.rval, koff, nnz, a.rheads + (size_t)ch * 8, s_end[warp], prod);
+    warp_chunk_sums<T, T, 2>(a.ridx, a.rval, koff, nnz, a.rheads + (size_t)ch * 8, s_end[warp], prod, a.rpad);
 #pragma unroll
     for (int k = 0; k < CPL; ++k) {
         const int il = lane + 32 * k;
@@ -376,8 +389,9 @@ __global__ void __launch_bounds__(NT) k_row_long(const SweepArgs<T> a) {
     Sums<T, 2> s;
     s.v[0] = s.v[1] = T(0);
     for (int e = threadIdx.x; e < nnz; e += NT) {
+        if (!MFS_INB((long long)koff + e, a.rpad, BS_ENTRIES)) continue;
         const T val = a.rval[koff + e];
-        s.v[0] += val * ldro(a.x + a.ridx[koff + e]);
+        s.v[0] += val * gat(a.x, a.ridx[koff + e], a.n, BS_GATHER_X);
         s.v[1] += val * val;
     }
     s = block_sum<T, 2>(s, sh);
@@ -406,11 +420,13 @@ __device__ __forceinline__ double acc_prod(double a, double b) {
 // Sum of a_k * w[idx_k] over one long segment by one warp (lane-strided, fixed order).
 template <typename T>
 __device__ __forceinline__ double warp_long_dot(const int* __restrict__ gidx, const T* __restrict__ gval, int koff,
-                                                int nnz, const T* __restrict__ w) {
+                                                int nnz, const T* __restrict__ w, long long pad, int lim, int site) {
     using A = typename AccOf<T>::type;
     const int lane = threadIdx.x & 31;
     A acc = A(0);
-    for (int e = lane; e < nnz; e += 32) acc = acc + acc_prod(gval[koff + e], ldro(w + gidx[koff + e]));
+    for (int e = lane; e < nnz; e += 32)
+        if (MFS_INB((long long)koff + e, pad, BS_ENTRIES))
+            acc = acc + acc_prod(gval[koff + e], gat(w, gidx[koff + e], lim, site));
     double d = to_double(acc);
 #pragma unroll
     for (int k = 16; k > 0; k >>= 1) d += __shfl_xor_sync(FULL, d, k);
@@ -491,14 +507,15 @@ __global__ void __launch_bounds__(NT) k_row_resid(const SweepArgs<T> a, const Re
 #pragma unroll
     for (int k = 0; k < NFR; ++k) f[k] = 0.0;
     const T* __restrict__ x = a.x;
-    auto prod = [x](int j, T val, A (&p)[1]) { p[0] = acc_prod(val, ldro(x + j)); };
+    const int n = a.n;
+    auto prod = [x, n](int j, T val, A (&p)[1]) { p[0] = acc_prod(val, gat(x, j, n, BS_GATHER_XR)); };
     for (int ch = blockIdx.x * NWARP + warp; ch < a.ntr; ch += gridDim.x * NWARP) {
         const int4 dsc = a.rdesc[ch];
         const int lo = dsc.x, nseg = dsc.y - dsc.x, koff = dsc.z, nnz = dsc.w;
         double ax[CPL];
         int rows[CPL];
         if (nnz > WT) {  // one long row: the warp sums it
-            ax[0] = warp_long_dot(a.ridx, a.rval, koff, nnz, x);
+            ax[0] = warp_long_dot(a.ridx, a.rval, koff, nnz, x, a.rpad, a.n, BS_GATHER_XR);
             rows[0] = (lane == 0) ? lo : -1;
 #pragma unroll
             for (int k = 1; k < CPL; ++k) rows[k] = -1;
@@ -514,7 +531,7 @@ __global__ void __launch_bounds__(NT) k_row_resid(const SweepArgs<T> a, const Re
                 }
             }
             const int kb = __shfl_sync(FULL, cs[0], 0);
-            warp_chunk_sums<T, A, 1>(a.ridx, a.rval, koff, nnz, a.rheads + (size_t)ch * 8, s_end[warp], prod);
+            warp_chunk_sums<T, A, 1>(a.ridx, a.rval, koff, nnz, a.rheads + (size_t)ch * 8, s_end[warp], prod, a.rpad);
 #pragma unroll
             for (int k = 0; k < CPL; ++k) {
                 const int il = lane + 32 * k;
@@ -553,14 +570,15 @@ __global__ void __launch_bounds__(NT) k_col_resid(const SweepArgs<T> a, const Re
 #pragma unroll
     for (int k = 0; k < NFC; ++k) f[k] = 0.0;
     const T* __restrict__ lam = a.lam;
-    auto prod = [lam](int i, T val, A (&p)[1]) { p[0] = acc_prod(val, ldro(lam + i)); };
+    const int m = a.m;
+    auto prod = [lam, m](int i, T val, A (&p)[1]) { p[0] = acc_prod(val, gat(lam, i, m, BS_GATHER_L)); };
     for (int ch = blockIdx.x * NWARP + warp; ch < a.ntc; ch += gridDim.x * NWARP) {
         const int4 dsc = a.cdesc[ch];
         const int lo = dsc.x, nseg = dsc.y - dsc.x, koff = dsc.z, nnz = dsc.w;
         double atl[CPL];
         int cols[CPL];
         if (nnz > WT) {  // one long column: the warp sums it
-            atl[0] = warp_long_dot(a.cidx, a.cval, koff, nnz, lam);
+            atl[0] = warp_long_dot(a.cidx, a.cval, koff, nnz, lam, a.cpad, a.m, BS_GATHER_L);
             cols[0] = (lane == 0) ? 0 : -1;
 #pragma unroll
             for (int k = 1; k < CPL; ++k) cols[k] = -1;
@@ -576,7 +594,7 @@ __global__ void __launch_bounds__(NT) k_col_resid(const SweepArgs<T> a, const Re
                 }
             }
             const int kb = __shfl_sync(FULL, cs[0], 0);
-            warp_chunk_sums<T, A, 1>(a.cidx, a.cval, koff, nnz, a.cheads + (size_t)ch * 8, s_end[warp], prod);
+            warp_chunk_sums<T, A, 1>(a.cidx, a.cval, koff, nnz, a.cheads + (size_t)ch * 8, s_end[warp], prod, a.cpad);
 #pragma unroll
             for (int k = 0; k < CPL; ++k) {
                 const int jl = lane + 32 * k;

@@ -82,6 +82,7 @@ struct mfs_solver {
     int m = 0, n = 0, o = 0;
     int ncones = 0, nsoc = 0, nbig = 0;
     int ncc = 0, nrc = 0;            // column / row chunks
+    long long cpad = 0, rpad = 0;    // lengths of the padded column / row nonzero arrays
     int nlc = 0, nlr = 0;            // long column / row chunks
     bool has_soc = false;
     int num_sms = 148;
@@ -569,6 +570,10 @@ SweepArgs<T> sweep_args(mfs_solver* s, State<T>& st) {
     a.ntr = s->nrc;
     a.nlc = s->nlc;
     a.nlr = s->nlr;
+    a.m = s->m;
+    a.n = s->n;
+    a.cpad = s->cpad;
+    a.rpad = s->rpad;
     return a;
 }
 
@@ -880,6 +885,7 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
         g.G = H.G;
         g.R = H.R;
         g.maxg_pad = (H.maxg + 3) / 4 * 4;
+        g.nent = (int)H.ent.size();
         g.spin = 1 << 24;
         g.no_loads = 0;
         return MFS_OK;
@@ -1367,6 +1373,8 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
     s->has_soc = s->nsoc > 0;
     s->ncc = P.cc.count();
     s->nrc = P.rc.count();
+    s->cpad = P.cc.padded;
+    s->rpad = P.rc.padded;
     s->nlc = (int)P.cc.longs.size();
     s->nlr = (int)P.rc.longs.size();
     s->precision = set.precision;
@@ -1478,6 +1486,26 @@ mfs_status mfs_debug_staged_wait_test(mfs_solver* s) {
     const int flagged = *s->h_err;
     *s->h_err = 0;
     return flagged ? fail(s, MFS_ERR_TIMEOUT, "staged sweep: wait for a block gave up (diagnostic)") : MFS_OK;
+}
+
+int32_t mfs_debug_bounds(int64_t* site, int64_t* index, int32_t reset) {
+#ifdef MFS_DEBUG_BOUNDS
+    unsigned long long v = 0;
+    cudaDeviceSynchronize();
+    cudaMemcpyFromSymbol(&v, mfs::g_bounds_fail, sizeof v);
+    if (site) *site = (int64_t)(v >> 40);
+    if (index) *index = (int64_t)(v & 0xFFFFFFFFFFull);
+    if (reset) {
+        const unsigned long long zero = 0;
+        cudaMemcpyToSymbol(mfs::g_bounds_fail, &zero, sizeof zero);
+    }
+    return 1;
+#else
+    (void)reset;
+    if (site) *site = 0;
+    if (index) *index = 0;
+    return 0;
+#endif
 }
 
 mfs_status mfs_set_sweep(mfs_solver* s, int32_t kind) {

@@ -78,6 +78,7 @@ struct StagedArgs {
     const float* __restrict__ rsq;  // row pass: sum of a_k^2 over each row
     int* err;                       // set to 1 if a wait for a block gave up
     int G, R, maxg_pad;
+    int nent;                       // entries (padded), the bound of the checked build
     int spin;                       // polls of an mbarrier before a wait gives up
     int no_loads;                   // diagnostic: issue no copies, so that every wait gives up
 };
@@ -116,11 +117,12 @@ __device__ __forceinline__ bool wait_block(uint64_t* bar, uint32_t parity, int s
 // inactive lanes get zeros.
 template <int PF, int LE>
 __device__ __forceinline__ void load_lane(const int2* __restrict__ ent, int s0, int s1, int lane,
-                                          int (&r)[2 * LE * PF]) {
+                                          int (&r)[2 * LE * PF], int nent) {
     static_assert(LE % 2 == 0, "entries per lane come in 16-byte pairs");
 #pragma unroll
     for (int st = 0; st < PF; ++st) {
-        const int base = s0 + st * 32 * LE + lane * LE;
+        int base = s0 + st * 32 * LE + lane * LE;
+        if (base < s1 && !MFS_INB(base + LE - 1, nent, BS_STG_ENT)) base = s1;  // checked build: skip
         if (LE % 4 == 0) {  // 32-byte loads, bypassing L1 (each sector is used by one load)
 #pragma unroll
             for (int h = 0; h < LE / 4; ++h) {
@@ -161,15 +163,17 @@ __device__ __forceinline__ void load_lane(const int2* __restrict__ ent, int s0, 
 // takes a segmented scan over the lanes' last runs instead. Either way every sum runs in the
 // entries' order within the step, the same on every run; steps follow each other. A lane's runs
 // belong to distinct segments, so their read-modify-writes are issued as all loads, then all stores.
-template <int N, int LE>
+template <int N, int LE, int RB>
 __device__ __forceinline__ void lane_step(const int (&r)[N], int q0, bool active, const float* vb, float* acc,
-                                          int lane) {
+                                          int lane, int nacc) {
     int k[LE];
     float s[LE];
 #pragma unroll
     for (int t = 0; t < LE; ++t) {
-        k[t] = active ? (r[q0 + 2 * t] & 0xFFFF) : -1;
-        s[t] = active ? __int_as_float(r[q0 + 2 * t + 1]) * vb[(uint32_t)r[q0 + 2 * t] >> 16] : 0.f;
+        const uint32_t gi = (uint32_t)r[q0 + 2 * t] >> 16;
+        const bool ok = active && MFS_INB(gi, RB, BS_STG_VEC) && MFS_INB(r[q0 + 2 * t] & 0xFFFF, nacc, BS_STG_ACC);
+        k[t] = ok ? (r[q0 + 2 * t] & 0xFFFF) : -1;
+        s[t] = ok ? __int_as_float(r[q0 + 2 * t + 1]) * vb[gi] : 0.f;
     }
 #pragma unroll
     for (int t = 1; t < LE; ++t) s[t] += (k[t] == k[t - 1]) ? s[t - 1] : 0.f;
@@ -225,19 +229,19 @@ __device__ __forceinline__ void lane_step(const int (&r)[N], int q0, bool active
 }
 
 // All entries of a warp's range [s0, s1) of one block: PF prefetched steps, then any further ones.
-template <int PF, int LE>
+template <int PF, int LE, int RB>
 __device__ __forceinline__ void run_range(const int (&r)[2 * LE * PF], int s0, int s1, const int2* __restrict__ ent,
-                                          const float* vb, float* acc, int lane) {
+                                          const float* vb, float* acc, int lane, int nent, int nacc) {
 #pragma unroll
     for (int st = 0; st < PF; ++st) {
         const int b0 = s0 + st * 32 * LE;
-        if (b0 < s1) lane_step<2 * LE * PF, LE>(r, 2 * LE * st, b0 + lane * LE < s1, vb, acc, lane);
+        if (b0 < s1) lane_step<2 * LE * PF, LE, RB>(r, 2 * LE * st, b0 + lane * LE < s1, vb, acc, lane, nacc);
         __syncwarp();
     }
     for (int b0 = s0 + PF * 32 * LE; b0 < s1; b0 += 32 * LE) {
         int t[2 * LE];
-        load_lane<1, LE>(ent, b0, s1, lane, t);
-        lane_step<2 * LE, LE>(t, 0, b0 + lane * LE < s1, vb, acc, lane);
+        load_lane<1, LE>(ent, b0, s1, lane, t, nent);
+        lane_step<2 * LE, LE, RB>(t, 0, b0 + lane * LE < s1, vb, acc, lane, nacc);
         __syncwarp();
     }
 }
@@ -259,12 +263,12 @@ __device__ __forceinline__ void block_step(int b, int R, uint32_t u, int (&C)[2 
                                            uint64_t* full, uint64_t* empty, bool& bad, int warp, int lane) {
     if (b + 2 < R) {
         const int* sp = spl + (b + 2) * (NW + 1) + warp;
-        load_lane<PF, LE>(g.ent, sp[0], sp[1], lane, D);
+        load_lane<PF, LE>(g.ent, sp[0], sp[1], lane, D, g.nent);
     }
     const uint32_t k = u % S;
     if (!wait_block(full + k, (u / S) & 1u, g.spin)) bad = true;
     const int* sp = spl + b * (NW + 1) + warp;
-    run_range<PF, LE>(C, sp[0], sp[1], g.ent, vb + k * RB, acc, lane);
+    run_range<PF, LE, RB>(C, sp[0], sp[1], g.ent, vb + k * RB, acc, lane, g.nent, g.maxg_pad);
     __syncwarp();
     if (lane == 0) mbar_arrive(empty + k);
 }
@@ -314,8 +318,8 @@ __global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, cons
             for (int t = ws + lane; t < we; t += 32) acc[t] = 0.f;
             __syncwarp();
             int A[N], B[N], C[N];
-            load_lane<PF, LE>(g.ent, spl[warp], spl[warp + 1], lane, A);
-            if (R > 1) load_lane<PF, LE>(g.ent, spl[NW + 1 + warp], spl[NW + 2 + warp], lane, B);
+            load_lane<PF, LE>(g.ent, spl[warp], spl[warp + 1], lane, A, g.nent);
+            if (R > 1) load_lane<PF, LE>(g.ent, spl[NW + 1 + warp], spl[NW + 2 + warp], lane, B, g.nent);
             for (int b = 0; b < R; b += 3) {
                 block_step<RB, PF, LE, S>(b, R, u0 + b, A, C, spl, g, vb, acc, full, empty, bad, warp, lane);
                 if (b + 1 < R)

@@ -65,6 +65,14 @@ class Info(ctypes.Structure):
 _lib = None
 
 
+def bounds_record(reset=False):
+    """(checked, site, index) of the bounds-checked build's first failed check (site 0: none)."""
+    lib = load()
+    site, index = ctypes.c_int64(0), ctypes.c_int64(0)
+    checked = lib.mfs_debug_bounds(ctypes.byref(site), ctypes.byref(index), 1 if reset else 0)
+    return bool(checked), int(site.value), int(index.value)
+
+
 def header_functions(path=HEADER):
     """Names of the functions include/mfs.h declares."""
     text = open(path).read()
@@ -102,6 +110,8 @@ def load(path=LIB_PATH):
     lib.mfs_set_sweep.restype = st
     lib.mfs_debug_staged_wait_test.argtypes = [P]
     lib.mfs_debug_staged_wait_test.restype = st
+    lib.mfs_debug_bounds.argtypes = [lp, lp, i32]
+    lib.mfs_debug_bounds.restype = i32
     for name in ("mfs_warm_start", "mfs_warm_start_device", "mfs_get_solution", "mfs_get_solution_device"):
         getattr(lib, name).argtypes = [P, P, P, P, P]
         getattr(lib, name).restype = st

@@ -231,6 +231,20 @@ mfs_status mfs_iterate(mfs_solver* s, int64_t k);
  */
 mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters_out);
 
+/* One residual check of mfs_solve: iterations run by that call when it was made, the relative
+   residuals (as in mfs_residuals_t), the stopping rule's measure and the precision of the iterate. */
+typedef struct {
+    int64_t iter;
+    double kkt, r_prim, r_dual, r_cone, r_gap, measure;
+    int32_t precision;
+    int32_t reserved;
+} mfs_check_t;
+
+/* The checks of the last mfs_solve on this handle (a ring of the most recent 4096): the latest
+   min(capacity, kept) records, oldest first, into out; *count (nullable) receives the number of
+   checks that call made. Host-only; no device work. */
+mfs_status mfs_solve_history(const mfs_solver* s, mfs_check_t* out, int64_t capacity, int64_t* count);
+
 /* Residuals of the current iterate (FP64 reductions on the device). */
 mfs_status mfs_residuals(mfs_solver* s, mfs_residuals_t* out);
 

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/mfs.h"
+#include "mfs_trace.h"
 #include "mfs_alloc.h"
 #include "mfs_device.cuh"
 #include "mfs_host.h"
@@ -635,6 +636,7 @@ mfs_status mfs_batch_create(int64_t count, const int64_t* m, const int64_t* n, c
                             const int64_t* col, const double* val, const double* b, const double* c,
                             const int64_t* ncones, const mfs_cone* cones, const mfs_settings* settings,
                             void* cuda_stream, mfs_batch** out) {
+    MFS_TRACE("mfs_batch_create");
     g_batch_create_error.clear();
     if (!out) return bfail(nullptr, MFS_ERR_INVALID, "out is NULL");
     *out = nullptr;
@@ -907,6 +909,7 @@ mfs_status mfs_batch_get_tuning(const mfs_batch* s, mfs_batch_tuning* t) {
 }
 
 mfs_status mfs_batch_iterate(mfs_batch* s, int64_t k) {
+    MFS_TRACE("mfs_batch_iterate");
     if (!s || k < 0 || k >= INT32_MAX) return MFS_ERR_INVALID;
     if (k == 0) return MFS_OK;
     BCUDA(s, cudaSetDevice(s->device));
@@ -914,6 +917,7 @@ mfs_status mfs_batch_iterate(mfs_batch* s, int64_t k) {
 }
 
 mfs_status mfs_batch_solve(mfs_batch* s, double tol, int64_t max_iter, int64_t* iters, int32_t* status) {
+    MFS_TRACE("mfs_batch_solve");
     if (!s || !(tol > 0.0) || max_iter < 1 || max_iter >= INT32_MAX) return MFS_ERR_INVALID;
     BCUDA(s, cudaSetDevice(s->device));
     BCUDA(s, cudaMemsetAsync(s->iters_done, 0, sizeof(long long) * s->count, s->stream));

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/mfs.h"
+#include "mfs_trace.h"
 #include "mfs_alloc.h"
 #include "mfs_gemm.cuh"
 
@@ -632,6 +633,7 @@ mfs_status mfs_mlp_get_output_scaling(mfs_mlp* s, float* mean, float* stdv) {
 }
 
 mfs_status mfs_mlp_forward(mfs_mlp* s, int32_t batch, const float* x, float* y, int32_t denormalize) {
+    MFS_TRACE("mfs_mlp_forward");
     if (!s || !x || !y || batch < 1 || batch > s->maxb) return MFS_ERR_INVALID;
     cudaSetDevice(s->device);
     k_to_bf16<<<grid1((long long)batch * s->din), 256, 0, s->stream>>>(x, s->X, (long long)batch * s->din);
@@ -647,6 +649,7 @@ mfs_status mfs_mlp_forward(mfs_mlp* s, int32_t batch, const float* x, float* y, 
 
 // Loss and gradients of one batch (no update); the gradients stay in the MLP (mfs_mlp_get_grads).
 mfs_status mfs_mlp_backward(mfs_mlp* s, int32_t batch, const float* x, const float* target, double* loss) {
+    MFS_TRACE("mfs_mlp_backward");
     if (!s || !x || !target || batch < 1 || batch > s->maxb || batch % 8) return MFS_ERR_INVALID;
     cudaSetDevice(s->device);
     const int B = batch, W = s->width, D = s->doutp, I = s->din;
@@ -707,6 +710,7 @@ mfs_status mfs_mlp_adam_step(mfs_mlp* s, float lr) {
 // layer 3 applies Adam to W3 directly (its gradient is never stored). The other steps are those of
 // mfs_mlp_backward followed by mfs_mlp_adam_step, in an order where dH2 still sees the old W3.
 mfs_status mfs_mlp_train_step(mfs_mlp* s, int32_t batch, const float* x, const float* target, float lr, double* loss) {
+    MFS_TRACE("mfs_mlp_train_step");
     if (!s || !x || !target || batch < 1 || batch > s->maxb || batch % 8 || !(lr > 0.f)) return MFS_ERR_INVALID;
     cudaSetDevice(s->device);
     const int B = batch, W = s->width, D = s->doutp, I = s->din;

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/mfs.h"
+#include "mfs_trace.h"
 #include "mfs_alloc.h"
 #include "mfs_device.cuh"
 #include "mfs_measures.h"
@@ -831,6 +832,7 @@ extern "C" {
 mfs_status mfs_shared_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col, const double* val,
                              int64_t ncones, const mfs_cone* cones, int64_t count, const mfs_settings* settings,
                              void* cuda_stream, mfs_shared** out) {
+    MFS_TRACE("mfs_shared_create");
     g_shared_error.clear();
     if (!out) return sfail(nullptr, MFS_ERR_INVALID, "out is NULL");
     *out = nullptr;
@@ -1045,6 +1047,7 @@ mfs_status mfs_shared_warm_start_device(mfs_shared* s, const float* x, const flo
 }
 
 mfs_status mfs_shared_iterate(mfs_shared* s, int64_t k) {
+    MFS_TRACE("mfs_shared_iterate");
     if (!s || k < 0) return MFS_ERR_INVALID;
     SCUDA(s, cudaSetDevice(s->device));
     STRY(s->set.precision == MFS_FP64 ? s_run(s, s->f64, k) : s_run(s, s->f32, k));
@@ -1076,6 +1079,7 @@ mfs_status mfs_shared_residuals(mfs_shared* s, mfs_residuals_t* out) {
    relative KKT residual is <= tol or max_iter iterations have run; iters[t] (nullable) receives
    the iteration at which instance t first met tol, or -1. Returns MFS_OK if all met it. */
 mfs_status mfs_shared_solve(mfs_shared* s, double tol, int64_t max_iter, int64_t* iters) {
+    MFS_TRACE("mfs_shared_solve");
     if (!s || !(tol > 0.0) || max_iter < 0) return MFS_ERR_INVALID;
     std::vector<int64_t> first(s->B, -1);
     std::vector<mfs_residuals_t> r(s->B);

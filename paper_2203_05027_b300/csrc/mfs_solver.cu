@@ -23,6 +23,7 @@
 #include "mfs_infeas.cuh"
 #include "mfs_literal.cuh"
 #include "mfs_measures.h"
+#include "mfs_trace.h"
 
 using namespace mfs;
 
@@ -110,6 +111,9 @@ struct mfs_solver {
     int *lit_krow = nullptr, *lit_kcol = nullptr, *lit_perm = nullptr, *lit_rp = nullptr;
     double* lit_zarg = nullptr;
     std::vector<void*> lit_mem;
+    // checks of the last mfs_solve, oldest first once the ring has wrapped (hist_next = next slot)
+    std::vector<mfs_check_t> hist;
+    int64_t hist_count = 0;
     // staged FP32 sweeps (mfs_staged.cuh): built at create for FP32 problems without Lorentz cones
     bool stg_ok = false;
     int sweep_kind = MFS_SWEEP_AUTO;
@@ -1279,6 +1283,7 @@ void mfs_destroy(mfs_solver* s) {
 mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col, const double* val,
                       const double* b, const double* c, int64_t ncones, const mfs_cone* cones,
                       const mfs_settings* settings, void* cuda_stream, mfs_solver** out) {
+    MFS_TRACE("mfs_create");
     g_create_error.clear();
     if (!out) return fail(nullptr, MFS_ERR_INVALID, "out is NULL");
     *out = nullptr;
@@ -1565,6 +1570,7 @@ mfs_status mfs_warm_start_device(mfs_solver* s, const double* x, const double* l
 }
 
 mfs_status mfs_iterate(mfs_solver* s, int64_t k) {
+    MFS_TRACE("mfs_iterate");
     if (!s) return MFS_ERR_INVALID;
     if (k < 0) return fail(s, MFS_ERR_INVALID, "k must be >= 0");
     CUDA_TRY(s, cudaSetDevice(s->device));
@@ -1579,6 +1585,7 @@ mfs_status mfs_iterate(mfs_solver* s, int64_t k) {
 }
 
 mfs_status mfs_residuals(mfs_solver* s, mfs_residuals_t* out) {
+    MFS_TRACE("mfs_residuals");
     if (!s || !out) return MFS_ERR_INVALID;
     CUDA_TRY(s, cudaSetDevice(s->device));
     return s->precision == MFS_FP64 ? residuals_t(s, s->s64, out, false) : residuals_t(s, s->s32, out, false);
@@ -1605,6 +1612,10 @@ mfs_status mfs_set_precision(mfs_solver* s, int32_t precision) {
 
 mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters_out) {
     if (!s) return MFS_ERR_INVALID;
+    MFS_TRACE("mfs_solve");
+    constexpr int64_t HIST_CAP = 4096;
+    s->hist.assign(HIST_CAP, mfs_check_t{});
+    s->hist_count = 0;
     if (!(tol > 0.0) || max_iter < 0) return fail(s, MFS_ERR_INVALID, "tol must be > 0 and max_iter >= 0");
     CUDA_TRY(s, cudaSetDevice(s->device));
     const int64_t K = s->set.check_every;
@@ -1622,6 +1633,19 @@ mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters
     while (true) {
         TRY(s->precision == MFS_FP64 ? residuals_t(s, s->s64, &r, true) : residuals_t(s, s->s32, &r, true));
         const double meas = stop_measure(r, s->set.stop_rule);
+        {
+            mfs_check_t& h = s->hist[(size_t)(s->hist_count % HIST_CAP)];
+            h.iter = it;
+            h.kkt = r.kkt;
+            h.r_prim = r.r_prim;
+            h.r_dual = r.r_dual;
+            h.r_cone = r.r_cone;
+            h.r_gap = r.r_gap;
+            h.measure = meas;
+            h.precision = s->precision;
+            h.reserved = 0;
+            ++s->hist_count;
+        }
         if (!std::isfinite(r.kkt) || !std::isfinite(meas)) {
             result = fail(s, MFS_ERR_NUMERIC, "NaN or Inf in the residuals");
             break;
@@ -1687,6 +1711,17 @@ mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters
     }
     if (iters_out) *iters_out = it;
     return result;
+}
+
+mfs_status mfs_solve_history(const mfs_solver* s, mfs_check_t* out, int64_t capacity, int64_t* count) {
+    if (!s || capacity < 0 || (capacity > 0 && !out)) return MFS_ERR_INVALID;
+    const int64_t cap = (int64_t)s->hist.size();
+    const int64_t kept = std::min(s->hist_count, cap);
+    const int64_t give = std::min(kept, capacity);
+    const int64_t first = s->hist_count - give;  // the most recent `give` checks, oldest first
+    for (int64_t q = 0; q < give; ++q) out[q] = s->hist[(size_t)((first + q) % cap)];
+    if (count) *count = s->hist_count;
+    return MFS_OK;
 }
 
 mfs_status mfs_get_solution(mfs_solver* s, double* x, double* lambda, double* z, double* delta) {

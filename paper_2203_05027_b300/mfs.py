@@ -54,6 +54,12 @@ class Residuals(ctypes.Structure):
     _fields_ = [(f, ctypes.c_double) for f in RESID_FIELDS] + [("iter", ctypes.c_int64)]
 
 
+class Check(ctypes.Structure):
+    _fields_ = [("iter", ctypes.c_int64), ("kkt", ctypes.c_double), ("r_prim", ctypes.c_double),
+                ("r_dual", ctypes.c_double), ("r_cone", ctypes.c_double), ("r_gap", ctypes.c_double),
+                ("measure", ctypes.c_double), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("o", ctypes.c_int64),
                 ("ncones", ctypes.c_int64), ("nsoc", ctypes.c_int64), ("nbig", ctypes.c_int64),
@@ -106,6 +112,8 @@ def load(path=LIB_PATH):
     lib.mfs_get_info.restype = st
     lib.mfs_set_mu.argtypes = [P, dbl]
     lib.mfs_set_mu.restype = st
+    lib.mfs_solve_history.argtypes = [P, ctypes.POINTER(Check), i64, lp]
+    lib.mfs_solve_history.restype = st
     lib.mfs_set_sweep.argtypes = [P, i32]
     lib.mfs_set_sweep.restype = st
     lib.mfs_debug_staged_wait_test.argtypes = [P]
@@ -213,6 +221,16 @@ class Solver:
 
     def set_mu(self, mu):
         self._check(self._lib.mfs_set_mu(self._h, float(mu)))
+
+    def history(self, capacity=4096):
+        """The residual checks of the last solve (oldest first) as a list of dicts, and how many
+        checks that solve made."""
+        buf = (Check * max(1, capacity))()
+        count = ctypes.c_int64(0)
+        self._check(self._lib.mfs_solve_history(self._h, buf, int(capacity), ctypes.byref(count)))
+        n = min(int(count.value), capacity, 4096)
+        return [{f: getattr(buf[q], f) for f, _ in Check._fields_ if f != "reserved"} for q in range(n)], \
+            int(count.value)
 
     def staged_wait_test(self):
         """Status name of the staged sweeps' wait diagnostic ("ERR_TIMEOUT" expected)."""

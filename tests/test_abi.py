@@ -34,9 +34,10 @@ def _c_layout(tmp_path):
     src.write_text(
         '#include <stddef.h>\n#include <stdio.h>\n#include "mfs.h"\n'
         "int main(void) {\n"
-        '  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mfs_cone), sizeof(mfs_settings),\n'
+        '  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mfs_cone), sizeof(mfs_settings),\n'
         "         sizeof(mfs_residuals_t), offsetof(mfs_settings, stop_rule), offsetof(mfs_settings, sweep),\n"
-        "         offsetof(mfs_residuals_t, r_osqp), offsetof(mfs_residuals_t, iter));\n"
+        "         offsetof(mfs_residuals_t, r_osqp), offsetof(mfs_residuals_t, iter), sizeof(mfs_check_t),\n"
+        "         offsetof(mfs_check_t, precision));\n"
         "  return 0;\n}\n")
     exe = tmp_path / "layout"
     inc = os.path.join(os.path.dirname(mfs.HEADER))
@@ -45,7 +46,8 @@ def _c_layout(tmp_path):
 
 
 def test_struct_sizes_match_header(lib, tmp_path):
-    cone, settings, resid, off_rule, off_sweep, off_osqp, off_iter = _c_layout(tmp_path)
+    cone, settings, resid, off_rule, off_sweep, off_osqp, off_iter, check, off_prec = _c_layout(tmp_path)
+    assert ctypes.sizeof(mfs.Check) == check and mfs.Check.precision.offset == off_prec
     assert ctypes.sizeof(mfs.Cone) == cone == 16
     assert ctypes.sizeof(mfs.Settings) == settings
     assert mfs.Settings.stop_rule.offset == off_rule and mfs.Settings.sweep.offset == off_sweep

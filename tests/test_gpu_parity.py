@@ -261,6 +261,32 @@ def test_solve_stops_at_the_first_check_meeting_the_rule(rule, maker, tol):
     assert abs(g[key] - after[key]) <= 1e-9 * max(1.0, after[key])
 
 
+def test_solve_history_records_every_check():
+    prob = I.small_lp(0, m=20, n=50)
+    s = mfs.Solver(prob, precision="fp32", check_every=50, polish_iters=100)
+    status, its = s.solve(1e-6, 400_000)
+    hist, count = s.history()
+    assert status == "OK" and count == len(hist) > 1
+    iters = [h["iter"] for h in hist]
+    assert iters[0] == 0 and iters[-1] == its and all(b >= a for a, b in zip(iters, iters[1:]))
+    assert hist[-1]["kkt"] <= 1e-6 and hist[-1]["precision"] == mfs.FP64
+    assert abs(hist[-1]["kkt"] - s.residuals()["kkt"]) <= 1e-12
+    # the tolerance is met only where the solve stopped or where the FP32 iterate handed over to
+    # the FP64 polish
+    for h, nxt in zip(hist, hist[1:]):
+        if h["measure"] <= 1e-6:
+            assert h["precision"] == mfs.FP32_MIXED and nxt["precision"] == mfs.FP64
+    assert all(h["measure"] == h["kkt"] for h in hist)
+
+
+def test_solve_history_keeps_the_latest_4096_checks():
+    s = mfs.Solver(I.small_lp(0, m=20, n=50), precision="fp64", check_every=1)
+    status, its = s.solve(1e-15, 5000)
+    hist, count = s.history()
+    assert status == "MAX_ITER" and its == 5000 and count == 5001 and len(hist) == 4096
+    assert [h["iter"] for h in hist] == list(range(5000 - 4095, 5001))
+
+
 def test_nan_warm_start_is_numeric_error():
     prob = I.small_lp(0, m=20, n=50)
     s = mfs.Solver(prob)

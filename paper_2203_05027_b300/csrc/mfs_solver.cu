@@ -648,9 +648,12 @@ void launch_row_mode(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
     if constexpr (std::is_same<T, float>::value && MODE == 0) {
         if (staged_row(s)) {
             const StagedArgsT& g = s->stg_row;
-            MFS_STAGED_ROW<<<std::min(g.G, s->num_sms), mfs::staged::NTS + 32,
+            MFS_STAGED_ROW<<<std::min(g.G * g.halves, s->num_sms), mfs::staged::NTS + 32,
                              mfs::staged::smem_bytes(mfs::staged::RB_ROW, mfs::staged::S_ROW, g.maxg_pad, g.R), st>>>(g,
                                                                                                                      a);
+            if (g.halves > 1)
+                mfs::staged::k_row_combine<<<(int)std::min<int64_t>((s->m + 255) / 256, 8 * s->num_sms), 256, 0, st>>>(
+                    g, a);
             return;
         }
     }
@@ -676,7 +679,7 @@ void launch_iteration(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
 int launches_per_iteration(const mfs_solver* s) {
     const bool f32 = s->precision == MFS_FP32_MIXED;
     const int col = s->ncc ? ((f32 && staged_col(s)) ? 1 : 1 + (s->nlc ? 1 : 0)) : 0;
-    const int row = s->nrc ? ((f32 && staged_row(s)) ? 1 : 1 + (s->nlr ? 1 : 0)) : 0;
+    const int row = s->nrc ? ((f32 && staged_row(s)) ? (s->stg_row.halves > 1 ? 2 : 1) : 1 + (s->nlr ? 1 : 0)) : 0;
     return col + (s->nbig ? 1 : 0) + row;
 }
 
@@ -855,8 +858,8 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
     StagedHost C, W;
     if (!build_staged(P.col_ptr, P.csc_row, P.csc_val, P.n, P.m, s->num_sms, RB_COL, S_COL, LE_COL, (size_t)optin,
                       C) ||
-        !build_staged(P.row_ptr, P.csr_col, P.csr_val, P.m, P.n, s->num_sms, RB_ROW, S_ROW, LE_ROW, (size_t)optin,
-                      W))
+        !build_staged(P.row_ptr, P.csr_col, P.csr_val, P.m, P.n, std::max(1, s->num_sms / ROW_HALVES), RB_ROW,
+                      S_ROW, LE_ROW, (size_t)optin, W))
         return MFS_OK;  // vectors too long for the split tables: chunked sweeps only
     std::vector<float> rsq(std::max(P.m, 1), 0.f);
     mfs::host::parallel_ranges(P.m, mfs::host::threads_for(P.o), [&](int64_t i0, int64_t i1, int) {
@@ -873,7 +876,7 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
     CUDA_TRY(s, cudaMemsetAsync(s->stg_err, 0, sizeof(int), s->stream));
     CUDA_TRY(s, cudaMallocHost(&s->h_err, sizeof(int)));
     *s->h_err = 0;
-    auto fill = [&](StagedHost& H, StagedArgs& g, const float* vec) -> mfs_status {
+    auto fill = [&](StagedHost& H, StagedArgs& g, const float* vec, int halves, int nseg) -> mfs_status {
         int2* ent = nullptr;
         int *split = nullptr, *grp = nullptr, *wseg = nullptr;
         TRY(upload(s, &ent, H.ent.data(), H.ent.size()));
@@ -889,13 +892,17 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
         g.G = H.G;
         g.R = H.R;
         g.maxg_pad = (H.maxg + 3) / 4 * 4;
+        g.halves = halves;
+        g.nseg = nseg;
+        g.part = nullptr;
+        if (halves > 1) TRY(dalloc(s, &g.part, (size_t)halves * std::max(nseg, 1)));
         g.nent = (int)H.ent.size();
         g.spin = 1 << 24;
         g.no_loads = 0;
         return MFS_OK;
     };
-    TRY(fill(C, s->stg_col, s->s32.v));
-    TRY(fill(W, s->stg_row, s->s32.x));
+    TRY(fill(C, s->stg_col, s->s32.v, 1, P.n));
+    TRY(fill(W, s->stg_row, s->s32.x, ROW_HALVES, P.m));
     float* d_rsq = nullptr;
     TRY(upload(s, &d_rsq, rsq.data(), rsq.size()));
     s->stg_row.rsq = d_rsq;

@@ -35,8 +35,11 @@ namespace staged {
 #define MFS_STG_S_COL 2
 #endif
 #ifndef MFS_STG_RB_ROW
-#define MFS_STG_RB_ROW 24576
+#define MFS_STG_RB_ROW 16384
 #define MFS_STG_S_ROW 2
+#endif
+#ifndef MFS_STG_ROW_HALVES
+#define MFS_STG_ROW_HALVES 2
 #endif
 #ifndef MFS_STG_NW
 #define MFS_STG_NW 15
@@ -45,6 +48,8 @@ constexpr int RB_COL = MFS_STG_RB_COL;  // entries of v per block, column pass
 constexpr int S_COL = MFS_STG_S_COL;    // stages
 constexpr int RB_ROW = MFS_STG_RB_ROW;  // entries of x per block, row pass
 constexpr int S_ROW = MFS_STG_S_ROW;
+constexpr int ROW_HALVES = MFS_STG_ROW_HALVES;  // row pass: two CTAs per row group, each streaming
+                                                // half of x (x is 2.5x longer than v)
 constexpr int NW = MFS_STG_NW;  // consumer warps per CTA, plus one producer warp (15: 512 threads, 4 warps
                                 // per SM sub-partition, up to 128 registers a thread)
 constexpr int NTS = 32 * NW;
@@ -78,6 +83,9 @@ struct StagedArgs {
     const float* __restrict__ rsq;  // row pass: sum of a_k^2 over each row
     int* err;                       // set to 1 if a wait for a block gave up
     int G, R, maxg_pad;
+    int halves;                     // row pass: CTAs per group, each streaming 1/halves of x (1 or 2)
+    float* part;                    // halves > 1: halves x nseg partial row sums
+    int nseg;                       // segments of the pass (rows for the row pass)
     int nent;                       // entries (padded), the bound of the checked build
     int spin;                       // polls of an mbarrier before a wait gives up
     int no_loads;                   // diagnostic: issue no copies, so that every wait gives up
@@ -258,10 +266,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // Consumer side of block b (the CTA's block u): prefetch the warp's entries of block b + 2 into D,
 // wait for the stage, add the entries held in C, and release the stage.
 template <int RB, int PF, int LE, int S>
-__device__ __forceinline__ void block_step(int b, int R, uint32_t u, int (&C)[2 * LE * PF], int (&D)[2 * LE * PF],
+__device__ __forceinline__ void block_step(int b, int be, uint32_t u, int (&C)[2 * LE * PF], int (&D)[2 * LE * PF],
                                            const int* spl, const StagedArgs& g, const float* vb, float* acc,
                                            uint64_t* full, uint64_t* empty, bool& bad, int warp, int lane) {
-    if (b + 2 < R) {
+    if (b + 2 < be) {
         const int* sp = spl + (b + 2) * (NW + 1) + warp;
         load_lane<PF, LE>(g.ent, sp[0], sp[1], lane, D, g.nent);
     }
@@ -300,15 +308,19 @@ __global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, cons
     __syncthreads();
     uint32_t u0 = 0;  // the CTA's staged blocks before the current group
     bool bad = false;
-    for (int grp = blockIdx.x; grp < g.G; grp += gridDim.x) {
+    const int H = g.halves;
+    for (int part = blockIdx.x; part < g.G * H; part += gridDim.x) {
+        // group grp; this CTA streams blocks [bb, be) of the vector (all of them unless H > 1)
+        const int grp = part / H, h = part % H;
+        const int bb = (int)((long long)R * h / H), be = (int)((long long)R * (h + 1) / H);
         const int k0 = g.grp[grp];
         const int* gs = g.split + (size_t)grp * R * (NW + 1);
         for (int t = threadIdx.x; t < R * (NW + 1); t += NTS + 32) spl[t] = gs[t];
         __syncthreads();  // split table in place; the previous group's sums are no longer read
         if (warp == NW) {
             if (lane == 0 && !g.no_loads) {
-                for (int b = 0; b < R; ++b) {
-                    const uint32_t u = u0 + b, k = u % S;
+                for (int b = bb; b < be; ++b) {
+                    const uint32_t u = u0 + (b - bb), k = u % S;
                     if (u >= S && !wait_block(empty + k, (u / S - 1) & 1u, g.spin)) bad = true;
                     issue_block(vb + k * RB, g.vec + (size_t)b * RB, RB * 4u, full + k);
                 }
@@ -318,14 +330,17 @@ __global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, cons
             for (int t = ws + lane; t < we; t += 32) acc[t] = 0.f;
             __syncwarp();
             int A[N], B[N], C[N];
-            load_lane<PF, LE>(g.ent, spl[warp], spl[warp + 1], lane, A, g.nent);
-            if (R > 1) load_lane<PF, LE>(g.ent, spl[NW + 1 + warp], spl[NW + 2 + warp], lane, B, g.nent);
-            for (int b = 0; b < R; b += 3) {
-                block_step<RB, PF, LE, S>(b, R, u0 + b, A, C, spl, g, vb, acc, full, empty, bad, warp, lane);
-                if (b + 1 < R)
-                    block_step<RB, PF, LE, S>(b + 1, R, u0 + b + 1, B, A, spl, g, vb, acc, full, empty, bad, warp, lane);
-                if (b + 2 < R)
-                    block_step<RB, PF, LE, S>(b + 2, R, u0 + b + 2, C, B, spl, g, vb, acc, full, empty, bad, warp, lane);
+            if (bb < be) load_lane<PF, LE>(g.ent, spl[bb * (NW + 1) + warp], spl[bb * (NW + 1) + warp + 1], lane, A, g.nent);
+            if (bb + 1 < be)
+                load_lane<PF, LE>(g.ent, spl[(bb + 1) * (NW + 1) + warp], spl[(bb + 1) * (NW + 1) + warp + 1], lane, B,
+                                  g.nent);
+            for (int b = bb; b < be; b += 3) {
+                const uint32_t u = u0 + (b - bb);
+                block_step<RB, PF, LE, S>(b, be, u, A, C, spl, g, vb, acc, full, empty, bad, warp, lane);
+                if (b + 1 < be)
+                    block_step<RB, PF, LE, S>(b + 1, be, u + 1, B, A, spl, g, vb, acc, full, empty, bad, warp, lane);
+                if (b + 2 < be)
+                    block_step<RB, PF, LE, S>(b + 2, be, u + 2, C, B, spl, g, vb, acc, full, empty, bad, warp, lane);
             }
             __syncwarp();
             const float mu = a.mu;
@@ -353,6 +368,9 @@ __global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, cons
                         }
                     }
                 }
+            } else if (H > 1) {  // partial row sums; k_row_combine adds the halves
+                float* out = g.part + (size_t)h * g.nseg + k0;
+                for (int t = ws + lane; t < we; t += 32) out[t] = acc[t];
             } else {
                 for (int t0 = ws + lane; t0 < we; t0 += 32 * EPI_U) {
                     float pr[EPI_U], pb[EPI_U], pl[EPI_U];
@@ -374,7 +392,7 @@ __global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, cons
                 }
             }
         }
-        u0 += R;
+        u0 += (uint32_t)(be - bb);
         __syncthreads();  // the group is done: its sums and split table may be replaced
     }
     if (bad) {
@@ -384,6 +402,16 @@ __global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, cons
             wait_block(full + u % S, (u / S) & 1u, g.spin);
         }
         atomicExch(g.err, 1);
+    }
+}
+
+// Row pass with halves = 2: the two partial sums of each row, added in a fixed order, then rho,
+// lambda and v (as the row pass's own epilogue).
+__global__ void __launch_bounds__(256) k_row_combine(const StagedArgs g, const SweepArgs<float> a) {
+    const int m = g.nseg;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const float ax = g.part[i] + g.part[(size_t)m + i];
+        row_update<float, 0>(a, i, ax, __ldg(g.rsq + i), __ldg(a.b + i), a.lam[i]);
     }
 }
 

@@ -101,7 +101,7 @@ def test_auto_choice_and_invalid_requests():
     s.set_sweep("staged")
     info = s.info()
     assert (info["sweep_col"], info["sweep_row"]) == (mfs.SWEEP_STAGED, mfs.SWEEP_STAGED)
-    assert info["launches_per_iter"] == 2
+    assert info["launches_per_iter"] == 3   # column pass, row pass in two halves, their combination
     s.set_sweep("auto")
     assert s.info()["sweep_col"] == mfs.SWEEP_CHUNKED
     f64 = mfs.Solver(I.small_lp(0), precision="fp64", sweep="staged")

@@ -24,6 +24,7 @@
 #include "mfs_literal.cuh"
 #include "mfs_measures.h"
 #include "mfs_trace.h"
+#include "mfs_setup.cuh"
 
 using namespace mfs;
 
@@ -57,9 +58,21 @@ struct Chunks {
     int count() const { return (int)desc.size() / 4; }
 };
 
+// Both orders of A built on the GPU (device set-up), kept until the padded layouts are filled.
+struct DevOrders {
+    bool on = false;
+    int *crow = nullptr, *rcol = nullptr;     // row indices in column order, column indices in row order
+    double *cval = nullptr, *rval = nullptr;  // the values in both orders
+    std::vector<void*> mem;                   // everything this set-up allocated
+    ~DevOrders() {
+        for (void* q : mem) cudaFree(q);
+    }
+};
+
 struct HostProblem {
     int m = 0, n = 0, o = 0;
     std::vector<int> col_ptr, row_ptr;
+    DevOrders dev;                    // on: the unpadded orders live on the device only
     mfs::host::uvec<int> csc_row;     // unpadded, column order
     mfs::host::uvec<double> csc_val;
     mfs::host::uvec<int> csr_col;     // unpadded, row order
@@ -173,7 +186,7 @@ mfs_status upload(mfs_solver* s, T** p, const void* host, size_t count) {
 // Sort COO into column order (rows ascending within a column), sum duplicates, drop zeros;
 // then build the row order (columns ascending within a row). Stable counting sorts, O(nnz + m + n),
 // multi-threaded (mfs_host.h); an input already in strict column order skips the sorting.
-// in_order: the caller found the input in strict (column, row) order.
+// in_order: the caller found the input in (column, row) order, duplicates next to each other.
 void build_orders(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col, const double* val,
                   bool in_order, HostProblem& P) {
     using namespace mfs::host;
@@ -463,9 +476,106 @@ bool build_staged(const std::vector<int>& ptr, const mfs::host::uvec<int>& idx, 
     return true;
 }
 
+// Device set-up (mfs_setup.cuh): upload the COO, check it, and if it is valid and in column order
+// (duplicates next to each other) build both orders on the GPU, leaving P.dev.on set and P.col_ptr, P.row_ptr, P.o on the host.
+// An input out of order leaves P.dev.on unset (the host orders it); an invalid one fails.
+mfs_status device_orders(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
+                         const double* val, HostProblem& P) {
+    namespace su = mfs::setup;
+    DevOrders& D = P.dev;
+    auto grab = [&](void** q, size_t bytes) -> mfs_status {
+        cudaError_t e = mfs::device_malloc(q, std::max<size_t>(bytes, 16));
+        if (e != cudaSuccess)
+            return fail(s, e == cudaErrorMemoryAllocation ? MFS_ERR_OOM : MFS_ERR_CUDA,
+                        std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        D.mem.push_back(*q);
+        return MFS_OK;
+    };
+    cudaStream_t st = s->stream;
+    const int grid = 8 * s->num_sms;
+    long long *d_row = nullptr, *d_col = nullptr;
+    double *d_val = nullptr, *d_sum = nullptr;
+    int *d_keep = nullptr, *d_pos = nullptr, *d_blk = nullptr, *d_total = nullptr, *d_flags = nullptr;
+    unsigned long long* d_bad = nullptr;
+    const long long nb = (nnz + su::SPAN - 1) / su::SPAN;
+    TRY(grab((void**)&d_row, nnz * sizeof(long long)));
+    TRY(grab((void**)&d_col, nnz * sizeof(long long)));
+    TRY(grab((void**)&d_val, nnz * sizeof(double)));
+    TRY(grab((void**)&d_bad, 2 * sizeof(unsigned long long) + 2 * sizeof(int)));
+    d_flags = reinterpret_cast<int*>(d_bad + 2);
+    CUDA_TRY(s, cudaMemcpyAsync(d_row, row, nnz * sizeof(long long), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(s, cudaMemcpyAsync(d_col, col, nnz * sizeof(long long), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(s, cudaMemcpyAsync(d_val, val, nnz * sizeof(double), cudaMemcpyHostToDevice, st));
+    {
+        unsigned long long init[2] = {(unsigned long long)nnz, (unsigned long long)nnz};
+        CUDA_TRY(s, cudaMemcpyAsync(d_bad, init, sizeof init, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(s, cudaMemsetAsync(d_flags, 0, 2 * sizeof(int), st));
+        su::k_check<<<grid, su::NT, 0, st>>>(d_row, d_col, d_val, nnz, m, n, d_bad, d_bad + 1, d_flags);
+        unsigned long long bad[2];
+        int flags[2];
+        CUDA_TRY(s, cudaMemcpyAsync(bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(s, cudaMemcpyAsync(flags, d_flags, sizeof flags, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(s, cudaStreamSynchronize(st));
+        const int64_t bi = (int64_t)bad[0], bv = (int64_t)bad[1];
+        if (bi < nnz && bi <= bv)
+            return fail(s, MFS_ERR_INVALID, "COO index out of range at entry " + std::to_string(bi));
+        if (bv < nnz) return fail(s, MFS_ERR_INVALID, "non-finite value in A");
+        if (flags[0]) return MFS_OK;  // not in column order: the host sorts it
+    }
+    // runs of equal (column, row) summed, zero sums dropped, the rest compacted in order
+    TRY(grab((void**)&d_keep, nnz * sizeof(int)));
+    TRY(grab((void**)&d_pos, nnz * sizeof(int)));
+    TRY(grab((void**)&d_sum, nnz * sizeof(double)));
+    TRY(grab((void**)&d_blk, (std::max<long long>(nb, (m + su::SPAN - 1) / su::SPAN) + 1) * sizeof(int)));
+    TRY(grab((void**)&d_total, sizeof(int)));
+    su::k_runs<<<grid, su::NT, 0, st>>>(d_row, d_col, d_val, nnz, d_keep, d_sum);
+    auto scan = [&](const int* in, int* out, long long cnt) {
+        const int blocks = (int)((cnt + su::SPAN - 1) / su::SPAN);
+        su::k_scan_local<<<blocks, su::NT, 0, st>>>(in, out, d_blk, cnt);
+        su::k_scan_blocks<<<1, 1024, 0, st>>>(d_blk, blocks, d_total);
+        su::k_scan_add<<<blocks, su::NT, 0, st>>>(out, d_blk, cnt);
+    };
+    scan(d_keep, d_pos, nnz);
+    int o = 0;
+    CUDA_TRY(s, cudaMemcpyAsync(&o, d_total, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(s, cudaStreamSynchronize(st));
+    int* d_ccol = nullptr;
+    TRY(grab((void**)&D.crow, (size_t)o * sizeof(int)));
+    TRY(grab((void**)&d_ccol, (size_t)o * sizeof(int)));
+    TRY(grab((void**)&D.cval, (size_t)o * sizeof(double)));
+    su::k_compact<<<grid, su::NT, 0, st>>>(d_row, d_col, d_keep, d_pos, d_sum, nnz, D.crow, d_ccol, D.cval);
+    // column pointers; the row order by count, scan, scatter and a sort of each row by column
+    int *d_cptr = nullptr, *d_rptr = nullptr, *d_cnt = nullptr;
+    TRY(grab((void**)&d_cptr, (size_t)(n + 1) * sizeof(int)));
+    TRY(grab((void**)&d_rptr, (size_t)(m + 1) * sizeof(int)));
+    TRY(grab((void**)&d_cnt, (size_t)std::max<int64_t>(m, 1) * sizeof(int)));
+    TRY(grab((void**)&D.rcol, (size_t)o * sizeof(int)));
+    TRY(grab((void**)&D.rval, (size_t)o * sizeof(double)));
+    CUDA_TRY(s, cudaMemsetAsync(d_cptr, 0, (size_t)(n + 1) * sizeof(int), st));
+    if (o > 0) su::k_seg_ptr<<<grid, su::NT, 0, st>>>(d_ccol, o, (int)n, d_cptr);
+    CUDA_TRY(s, cudaMemsetAsync(d_cnt, 0, (size_t)std::max<int64_t>(m, 1) * sizeof(int), st));
+    su::k_count<<<grid, su::NT, 0, st>>>(D.crow, o, d_cnt);
+    if (m > 0) scan(d_cnt, d_rptr, m);
+    CUDA_TRY(s, cudaMemcpyAsync(d_rptr + m, &o, sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(s, cudaMemsetAsync(d_cnt, 0, (size_t)std::max<int64_t>(m, 1) * sizeof(int), st));
+    su::k_scatter_rows<<<grid, su::NT, 0, st>>>(D.crow, d_ccol, D.cval, o, d_rptr, d_cnt, D.rcol, D.rval);
+    if (m > 0) su::k_sort_rows<<<(int)std::min<int64_t>((m + su::NT - 1) / su::NT, grid), su::NT, 0, st>>>(d_rptr, (int)m, D.rcol, D.rval);
+    CUDA_TRY(s, cudaGetLastError());
+    P.m = (int)m;
+    P.n = (int)n;
+    P.o = o;
+    P.col_ptr.resize(n + 1);
+    P.row_ptr.resize(m + 1);
+    CUDA_TRY(s, cudaMemcpyAsync(P.col_ptr.data(), d_cptr, (size_t)(n + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(s, cudaMemcpyAsync(P.row_ptr.data(), d_rptr, (size_t)(m + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(s, cudaStreamSynchronize(st));
+    D.on = true;
+    return MFS_OK;
+}
+
 mfs_status setup_host(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
                       const double* val, bool in_order, int64_t ncones, const mfs_cone* cones, HostProblem& P) {
-    build_orders(m, n, nnz, row, col, val, in_order, P);
+    if (!P.dev.on) build_orders(m, n, nnz, row, col, val, in_order, P);
     // Lorentz cones; unit_end[j] = end of the small cone starting at j, or j+1
     std::vector<int> unit_end(n);
     for (int64_t j = 0; j < n; ++j) unit_end[j] = (int)j + 1;
@@ -822,6 +932,29 @@ mfs_status warm_start_t(mfs_solver* s, State<T>& st, const double* x, const doub
     return MFS_OK;
 }
 
+// Padded column (col = true) or row arrays filled on the device from the orders of device_orders:
+// indices into *pidx and/or values (as T) into *pval, zero in the padding (as pad_chunks writes).
+template <typename T>
+mfs_status pad_on_device(mfs_solver* s, const HostProblem& P, bool col, int** pidx, T** pval) {
+    const Chunks& C = col ? P.cc : P.rc;
+    const size_t len = (size_t)C.padded + PAD;
+    if (pidx) {
+        TRY(dalloc(s, pidx, len));
+        CUDA_TRY(s, cudaMemsetAsync(*pidx, 0, len * sizeof(int), s->stream));
+    }
+    if (pval) {
+        TRY(dalloc(s, pval, len));
+        CUDA_TRY(s, cudaMemsetAsync(*pval, 0, len * sizeof(T), s->stream));
+    }
+    const int nch = C.count();
+    if (nch > 0)
+        mfs::setup::k_pad<T><<<(int)std::min<int64_t>((nch + 7) / 8, 8 * s->num_sms), 256, 0, s->stream>>>(
+            col ? s->cdesc : s->rdesc, nch, col ? s->col_ptr : s->row_ptr, col ? P.dev.crow : P.dev.rcol,
+            col ? P.dev.cval : P.dev.rval, pidx ? *pidx : nullptr, pval ? *pval : nullptr);
+    CUDA_TRY(s, cudaGetLastError());
+    return MFS_OK;
+}
+
 template <typename T>
 mfs_status alloc_state(mfs_solver* s, State<T>& st, const HostProblem& P, const double* b, const double* c) {
     // x and v, the vectors the staged sweeps copy in whole blocks, are padded to a multiple of the block
@@ -835,11 +968,16 @@ mfs_status alloc_state(mfs_solver* s, State<T>& st, const HostProblem& P, const 
     std::vector<T> hb(b, b + s->m), hc(c, c + s->n);
     TRY(upload(s, &st.b, hb.data(), hb.size()));
     TRY(upload(s, &st.c, hc.data(), hc.size()));
-    mfs::host::uvec<T> pval;
-    pad_chunks<T>(P.cc, P.col_ptr, P.csc_row, P.csc_val, (mfs::host::uvec<int>*)nullptr, &pval);
-    TRY(upload(s, &st.cval, pval.data(), pval.size()));
-    pad_chunks<T>(P.rc, P.row_ptr, P.csr_col, P.csr_val, (mfs::host::uvec<int>*)nullptr, &pval);
-    TRY(upload(s, &st.rval, pval.data(), pval.size()));
+    if (P.dev.on) {
+        TRY(pad_on_device<T>(s, P, true, nullptr, &st.cval));
+        TRY(pad_on_device<T>(s, P, false, nullptr, &st.rval));
+    } else {
+        mfs::host::uvec<T> pval;
+        pad_chunks<T>(P.cc, P.col_ptr, P.csc_row, P.csc_val, (mfs::host::uvec<int>*)nullptr, &pval);
+        TRY(upload(s, &st.cval, pval.data(), pval.size()));
+        pad_chunks<T>(P.rc, P.row_ptr, P.csr_col, P.csr_val, (mfs::host::uvec<int>*)nullptr, &pval);
+        TRY(upload(s, &st.rval, pval.data(), pval.size()));
+    }
     CUDA_TRY(s, cudaMemsetAsync(st.x, 0, sizeof(T) * std::max<int64_t>(npad, 1), s->stream));
     CUDA_TRY(s, cudaMemsetAsync(st.z, 0, sizeof(T) * std::max(s->n, 1), s->stream));
     CUDA_TRY(s, cudaMemsetAsync(st.del, 0, sizeof(T) * std::max(s->n, 1), s->stream));
@@ -1322,9 +1460,12 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
     }
     if (total != n) return fail(nullptr, MFS_ERR_INVALID, "cone sizes do not sum to n");
     bool in_order = false;
-    {
+    // large inputs are checked and, when already in column order, set up on the GPU; the staged
+    // layout is built from host arrays
+    const bool dev_path = nnz >= (int64_t(1) << 16) && set.sweep != MFS_SWEEP_STAGED;
+    if (!dev_path) {
         // first bad entry: index out of range, or a non-finite value; and whether the entries are
-        // already in strict (column, row) order
+        // already in (column, row) order (equal neighbours are duplicates, summed later)
         const int nt = mfs::host::threads_for(nnz);
         std::vector<int64_t> bad_idx(nt, nnz), bad_val(nt, nnz);
         std::vector<char> unsorted(nt, 0);
@@ -1332,7 +1473,7 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
             for (int64_t q = lo; q < hi; ++q) {
                 if (bad_idx[t] == nnz && (row[q] < 0 || row[q] >= m || col[q] < 0 || col[q] >= n)) bad_idx[t] = q;
                 if (bad_val[t] == nnz && !std::isfinite(val[q])) bad_val[t] = q;
-                if (q + 1 < nnz && (col[q] > col[q + 1] || (col[q] == col[q + 1] && row[q] >= row[q + 1])))
+                if (q + 1 < nnz && (col[q] > col[q + 1] || (col[q] == col[q + 1] && row[q] > row[q + 1])))
                     unsorted[t] = 1;
             }
         });
@@ -1374,7 +1515,12 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
         return bail(MFS_ERR_CUDA);
     }
     HostProblem P;
-    mfs_status st = setup_host(s, m, n, nnz, row, col, val, in_order, ncones, cones, P);
+    mfs_status st = MFS_OK;
+    if (dev_path) {
+        st = device_orders(s, m, n, nnz, row, col, val, P);
+        if (st != MFS_OK) return bail(st);
+    }
+    st = setup_host(s, m, n, nnz, row, col, val, in_order, ncones, cones, P);
     if (st != MFS_OK) return bail(st);
     s->m = P.m;
     s->n = P.n;
@@ -1418,11 +1564,16 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
     CHK(upload(s, &s->big_list, P.big_list.data(), P.big_list.size()));
     {
         // padded index arrays (shared by both precisions)
-        mfs::host::uvec<int> pidx;
-        pad_chunks<double>(P.cc, P.col_ptr, P.csc_row, P.csc_val, &pidx, (mfs::host::uvec<double>*)nullptr);
-        CHK(upload(s, &s->cidx, pidx.data(), pidx.size()));
-        pad_chunks<double>(P.rc, P.row_ptr, P.csr_col, P.csr_val, &pidx, (mfs::host::uvec<double>*)nullptr);
-        CHK(upload(s, &s->ridx, pidx.data(), pidx.size()));
+        if (P.dev.on) {
+            CHK(pad_on_device<float>(s, P, true, &s->cidx, nullptr));
+            CHK(pad_on_device<float>(s, P, false, &s->ridx, nullptr));
+        } else {
+            mfs::host::uvec<int> pidx;
+            pad_chunks<double>(P.cc, P.col_ptr, P.csc_row, P.csc_val, &pidx, (mfs::host::uvec<double>*)nullptr);
+            CHK(upload(s, &s->cidx, pidx.data(), pidx.size()));
+            pad_chunks<double>(P.rc, P.row_ptr, P.csr_col, P.csr_val, &pidx, (mfs::host::uvec<double>*)nullptr);
+            CHK(upload(s, &s->ridx, pidx.data(), pidx.size()));
+        }
     }
     {
         int sms = 0;

@@ -342,3 +342,27 @@ def test_unsorted_coo_with_duplicates_above_two_million_entries():
     orc, s = run_pair(prob, 40, "fp64")
     compare(s.solution(), orc.state(), TOL["fp64"], "unsorted COO")
     assert s.info()["o"] == oracle.make_oracle(prob).uv()[0].size
+
+
+@pytest.mark.parametrize("m, n", [(30_000, 75_000), (400, 1_000)])
+def test_sorted_coo_with_adjacent_duplicates_and_cancelling_pairs(m, n):
+    """A COO list in column order where some entries repeat next to themselves and some repeats
+    cancel (summing to an explicit zero that must be dropped): the large case is set up on the GPU,
+    the small one on the host; both must see the matrix the oracle sums."""
+    base = I.large_lp(6, m=m, n=n)
+    k = base["row"].size
+    rng = np.random.default_rng(12)
+    reps = np.ones(k, np.int64)
+    reps[rng.choice(k, k // 7, replace=False)] = 2
+    row, col = np.repeat(base["row"], reps), np.repeat(base["col"], reps)
+    val = np.repeat(base["val"], reps)
+    first = np.r_[True, (row[1:] != row[:-1]) | (col[1:] != col[:-1])]
+    second = ~first                                   # the repeated copies
+    split = rng.random(second.sum())
+    val[second] = val[second] * split                 # a + a*split ...
+    cancel = np.flatnonzero(second)[rng.random(second.sum()) < 0.2]
+    val[cancel] = -val[cancel - 1]                    # ... or a pair that sums to zero
+    prob = dict(base, row=row, col=col, val=val)
+    orc, s = run_pair(prob, 40, "fp64")
+    compare(s.solution(), orc.state(), TOL["fp64"], "sorted COO with duplicates")
+    assert s.info()["o"] == oracle.make_oracle(prob).uv()[0].size < k

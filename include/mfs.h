@@ -146,7 +146,7 @@ void mfs_default_settings(mfs_settings* s);
  * Set-up: with 2^16 or more entries (and no staged layout requested) the COO list is copied to the
  * device once and checked there; if it is in column order (rows ascending within a column,
  * duplicates next to each other) the orders and padded layouts are built on the GPU, taking about
- * 56 bytes of device memory per entry until the call returns. Otherwise the host orders it with
+ * 70 bytes of device memory per entry until the call returns. Otherwise the host orders it with
  * all its cores. The result is the same either way.
  */
 mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,

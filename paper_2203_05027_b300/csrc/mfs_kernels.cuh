@@ -56,6 +56,7 @@ struct SweepArgs {
     const int* __restrict__ soc_size;
     const unsigned char* __restrict__ soc_big;  // 1: too large to fuse, handled by the big-cone kernel
     const int* __restrict__ big_list;           // indices of the big cones
+    const unsigned char* __restrict__ ctag;     // per column: 0 orthant, 1 small Lorentz cone, 2 big cone
     // data and iterate
     const T* __restrict__ b;
     const T* __restrict__ c;
@@ -163,22 +164,11 @@ __device__ __forceinline__ T lorentz_coord(T w, int t, T w1, T alpha) {
     return (t == 0) ? w / T(2) + alpha / T(2) : w / T(2) + w1 * w / (T(2) * alpha);
 }
 
-// Cone membership of column j of column chunk ch: 0 orthant, 1 small Lorentz cone (fused),
-// 2 Lorentz cone handled by the big-cone kernels.
+// Cone membership of column j: 0 orthant, 1 small Lorentz cone (fused), 2 Lorentz cone handled by
+// the big-cone kernels (a byte per column, tabulated at set-up).
 template <typename T>
-__device__ __forceinline__ int cone_tag(const SweepArgs<T>& a, int ch, int j) {
-    const int qlo = a.cq_lo[ch];
-    int lo = qlo, hi = a.cq_hi[ch];
-    while (lo < hi) {  // first cone starting after j
-        const int mid = (lo + hi) >> 1;
-        if (a.soc_start[mid] <= j)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    const int q = lo - 1;
-    if (q < qlo || j >= a.soc_start[q] + a.soc_size[q]) return 0;
-    return a.soc_big[q] ? 2 : 1;
+__device__ __forceinline__ int cone_tag(const SweepArgs<T>& a, int j) {
+    return __ldg(a.ctag + j);
 }
 
 // x-, z- and delta-updates of one orthant column.
@@ -232,7 +222,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? MFS_SWEEP_MINB : 1) k_col
             const T atv = (ce[k] > cs[k]) ? s_end[warp][eslot(ce[k] - 1 - kb)] : T(0);
             const T xn = col_x_update(T(ce[k] - cs[k]), px[k], atv, pz[k], pd[k], pc[k], mu);
             const int j = lo + jl;
-            const int tag = SOC ? cone_tag(a, ch, j) : 0;
+            const int tag = SOC ? cone_tag(a, j) : 0;
             if (tag == 0) {
                 orthant_update(a.x, a.z, a.del, j, xn, pd[k], mu);
             } else {
@@ -285,7 +275,7 @@ __global__ void __launch_bounds__(NT) k_col_long(const SweepArgs<T> a) {
     if (threadIdx.x == 0) {
         const T mu = a.mu, dj = a.del[j];
         const T xn = col_x_update(T(nnz), a.x[j], s.v[0], a.z[j], dj, a.c[j], mu);
-        if (SOC && cone_tag(a, ch, j) != 0)  // then part of a big cone
+        if (SOC && cone_tag(a, j) != 0)  // then part of a big cone
             a.x[j] = xn;
         else
             orthant_update(a.x, a.z, a.del, j, xn, dj, mu);
@@ -618,7 +608,7 @@ __global__ void __launch_bounds__(NT) k_col_resid(const SweepArgs<T> a, const Re
             f[C_CX] += cj * xj;
             f[C_X2] += xj * xj;
             f[C_XMAX] = fmax(f[C_XMAX], fabs(xj));
-            const int tag = SOC ? cone_tag(a, ch, j) : 0;
+            const int tag = SOC ? cone_tag(a, j) : 0;
             if (tag == 0) {
                 const double sn = s < 0.0 ? s : 0.0, xn = xj < 0.0 ? xj : 0.0;
                 f[C_SDIST2] += sn * sn;

@@ -117,7 +117,7 @@ struct mfs_solver {
     // literal start (Algorithm 1 with o-length y and gamma) pending for the next lit_pending iterations
     int lit_pending = 0;
     // primal infeasibility test of mfs_solve: previous s = c + A^T lambda and lambda (FP64)
-    unsigned char* in_cone = nullptr;  // n: 1 for coordinates of Lorentz cones
+    unsigned char* in_cone = nullptr;  // n: 0 orthant, 1 small Lorentz cone, 2 Lorentz cone of the big-cone kernels
     double *inf_s_prev = nullptr, *inf_lam_prev = nullptr, *inf_x_prev = nullptr, *inf_r_prev = nullptr,
            *inf_part = nullptr;
     void *lit_y = nullptr, *lit_g = nullptr, *lit_kval = nullptr, *lit_w = nullptr, *lit_row = nullptr;
@@ -672,6 +672,7 @@ SweepArgs<T> sweep_args(mfs_solver* s, State<T>& st) {
     a.soc_size = s->soc_size;
     a.soc_big = s->soc_big;
     a.big_list = s->big_list;
+    a.ctag = s->in_cone;
     a.b = st.b;
     a.c = st.c;
     a.x = st.x;
@@ -1557,7 +1558,7 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
     {
         std::vector<unsigned char> inc(n, 0);
         for (size_t q = 0; q < P.soc_start.size(); ++q)
-            for (int t = 0; t < P.soc_size[q]; ++t) inc[P.soc_start[q] + t] = 1;
+            for (int t = 0; t < P.soc_size[q]; ++t) inc[P.soc_start[q] + t] = P.soc_big[q] ? 2 : 1;
         CHK(upload(s, &s->in_cone, inc.data(), inc.size()));
     }
     CHK(upload(s, &s->soc_big, P.soc_big.data(), P.soc_big.size()));

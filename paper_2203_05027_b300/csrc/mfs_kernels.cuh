@@ -171,6 +171,29 @@ __device__ __forceinline__ int cone_tag(const SweepArgs<T>& a, int j) {
     return __ldg(a.ctag + j);
 }
 
+// The small Lorentz cones of column chunk ch, in order: body(c0, size) for each (c0 its first column
+// relative to lo), called by the whole warp. Their descriptors are loaded 32 at a time, one per
+// lane, and handed round by shuffles, so that no cone waits for its own loads.
+template <typename T, typename Body>
+__device__ __forceinline__ void for_small_cones(const SweepArgs<T>& a, int ch, int lo, Body body) {
+    const int lane = threadIdx.x & 31;
+    const int qlo = a.cq_lo[ch], qhi = a.cq_hi[ch];
+    for (int q0 = qlo; q0 < qhi; q0 += 32) {
+        const int q = q0 + lane;
+        int st = 0, sz = 0, big = 1;
+        if (q < qhi) {
+            st = a.soc_start[q];
+            sz = a.soc_size[q];
+            big = a.soc_big[q];
+        }
+        const int cnt = min(32, qhi - q0);
+        for (int u = 0; u < cnt; ++u) {
+            if (__shfl_sync(FULL, big, u)) continue;
+            body(__shfl_sync(FULL, st, u) - lo, __shfl_sync(FULL, sz, u));
+        }
+    }
+}
+
 // x-, z- and delta-updates of one orthant column.
 template <typename T>
 __device__ __forceinline__ void orthant_update(T* x, T* z, T* del, int j, T xn, T dj, T mu) {
@@ -242,9 +265,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? MFS_SWEEP_MINB : 1) k_col
         const T* cx = s_cone[warp][0];
         const T* cw = s_cone[warp][1];
         const T* cd = s_cone[warp][2];
-        for (int q = a.cq_lo[ch]; q < a.cq_hi[ch]; ++q) {
-            if (a.soc_big[q]) continue;
-            const int c0 = a.soc_start[q] - lo, sz = a.soc_size[q];
+        for_small_cones(a, ch, lo, [&](int c0, int sz) {
             T ss = T(0);
             for (int t = 1 + lane; t < sz; t += 32) ss += cw[c0 + t] * cw[c0 + t];
 #pragma unroll
@@ -255,7 +276,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? MFS_SWEEP_MINB : 1) k_col
                 a.z[lo + c0 + t] = zt;
                 a.del[lo + c0 + t] = cd[c0 + t] + mu * (zt - cx[c0 + t]);
             }
-        }
+        });
     }
 }
 
@@ -625,9 +646,7 @@ __global__ void __launch_bounds__(NT) k_col_resid(const SweepArgs<T> a, const Re
             __syncwarp();
             const double* cs_ = s_cone[warp][0];
             const double* cx_ = s_cone[warp][1];
-            for (int q = a.cq_lo[ch]; q < a.cq_hi[ch]; ++q) {  // each small cone by the whole warp
-                if (a.soc_big[q]) continue;
-                const int c0 = a.soc_start[q] - lo, sz = a.soc_size[q];
+            for_small_cones(a, ch, lo, [&](int c0, int sz) {  // each small cone by the whole warp
                 double ss = 0.0, xx = 0.0;
                 for (int t = 1 + lane; t < sz; t += 32) {
                     ss += cs_[c0 + t] * cs_[c0 + t];
@@ -646,7 +665,7 @@ __global__ void __launch_bounds__(NT) k_col_resid(const SweepArgs<T> a, const Re
                     f[C_SDMAX] = fmax(f[C_SDMAX], mfs::lorentz_distinf(s1, as));
                     f[C_XDMAX] = fmax(f[C_XDMAX], mfs::lorentz_distinf(x1, ax));
                 }
-            }
+            });
             __syncwarp();
         }
     }

@@ -155,11 +155,14 @@ def kernel_roofline(s, info, peak, peak_kind, m, n, o, sm_mhz, num_sms=148):
     its algorithmic bytes to the measured HBM copy bandwidth. Also relates the launch time to the
     L2-request floor of its random gathers (one 4-byte gather, hence one L2 request, per nonzero;
     one request per SM cycle)."""
+    from paper_2203_05027_b300 import mfs
     t = s.time_kernels(50)
     col_bytes = 8 * o + 32 * n + 4 * m
     row_bytes = 8 * o + 4 * n + 20 * m
-    col = {"kernel": "k_col_sweep", "ms": t["col_ms"], "bytes": col_bytes}
-    row = {"kernel": "k_row_sweep", "ms": t["row_ms"], "bytes": row_bytes}
+    col = {"kernel": "k_staged<0>" if info.get("sweep_col") == mfs.SWEEP_STAGED else "k_col_sweep",
+           "ms": t["col_ms"], "bytes": col_bytes}
+    row = {"kernel": "k_staged<1>+k_row_combine" if info.get("sweep_row") == mfs.SWEEP_STAGED else "k_row_sweep",
+           "ms": t["row_ms"], "bytes": row_bytes}
     dom = col if col["ms"] >= row["ms"] else row
     achieved = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
     it_gbs = info["bytes_per_iter"] / (t["iter_ms"] * 1e-3) / 1e9

@@ -71,8 +71,9 @@ enum { MFS_STOP_KKT = 0, MFS_STOP_SCS_L2 = 1, MFS_STOP_OSQP_INF = 2 };
    at most 256 nonzeros, the gathers served by L2 (every problem). MFS_SWEEP_STAGED: one CTA per
    group of columns (rows), the gathered vector streamed through shared memory in 64 KB blocks and
    the nonzeros stored sorted by block (FP32_MIXED solvers without Lorentz cones). MFS_SWEEP_AUTO
-   (default): the chunked kernels, the faster ones on the workloads measured. Both compute the same
-   iteration; their FP32 sums run in different orders. */
+   (default): the chunked column pass, and the staged row pass where its layout was built on the GPU
+   (COO input in column order) for a matrix with at least 2^20 nonzeros and 4 per column; else
+   chunked. All compute the same iteration; their FP32 sums run in different orders. */
 enum { MFS_SWEEP_AUTO = 0, MFS_SWEEP_CHUNKED = 1, MFS_SWEEP_STAGED = 2 };
 
 typedef struct {
@@ -90,9 +91,9 @@ typedef struct {
     int32_t stop_rule;    /* MFS_STOP_KKT (default), MFS_STOP_SCS_L2 or MFS_STOP_OSQP_INF */
     double osqp_rel;      /* MFS_STOP_OSQP_INF: eps_rel / eps_abs, > 0 (default 10: the paper's
                              OSQP tolerances 1e-4 and 1e-3 at tol = 1e-4) */
-    int32_t sweep;        /* MFS_SWEEP_AUTO (default) or MFS_SWEEP_CHUNKED: chunked FP32 sweeps;
-                             MFS_SWEEP_STAGED: also build the staged layout (host time and device
-                             memory of a second copy of A) and use it; FP32_MIXED solvers without
+    int32_t sweep;        /* MFS_SWEEP_AUTO (default; see above), MFS_SWEEP_CHUNKED, or
+                             MFS_SWEEP_STAGED: build the staged layout (device memory of a second
+                             copy of A) and use it for both passes; FP32_MIXED solvers without
                              Lorentz cones only, others run the chunked kernels (mfs_get_info tells) */
     int32_t reserved;     /* must be 0 */
 } mfs_settings;

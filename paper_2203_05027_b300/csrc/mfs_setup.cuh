@@ -225,5 +225,142 @@ __global__ void k_pad(const int4* __restrict__ desc, int nchunks, const int* __r
     }
 }
 
+// ------------------------------------------------------------------------------------ staged layout
+// The staged sweeps' entry arrays (mfs_staged.cuh) from a device order (segment pointers ptr,
+// gathered indices idx, FP64 values val): per group of segments, its entries in the order of
+// (block of the gathered index, segment, gathered index) -- a stable split of the group's entries,
+// which are already in (segment, gathered index) order, by block -- each 8-byte entry holding the
+// segment's index within the group (low 16 bits), the gathered index within the block (high 16
+// bits) and the FP32 value; then every warp's range padded to a multiple of LE entries.
+
+// segment of every entry: seg_of[k] = s for k in [ptr[s], ptr[s+1])
+__global__ void k_seg_of(const int* __restrict__ ptr, int nseg, int* __restrict__ seg_of) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x)
+        for (int k = ptr[s]; k < ptr[s + 1]; ++k) seg_of[k] = s;
+}
+
+// cnt[g * R + b]: entries of group g whose gathered index falls in block b (one CTA per group)
+__global__ void k_stg_count(const int* __restrict__ ptr, const int* __restrict__ grp, const int* __restrict__ idx,
+                            int R, int rb, int* __restrict__ cnt) {
+    extern __shared__ int hist[];
+    const int g = blockIdx.x;
+    for (int b = threadIdx.x; b < R; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const int k0 = ptr[grp[g]], k1 = ptr[grp[g + 1]];
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) atomicAdd(hist + idx[k] / rb, 1);
+    __syncthreads();
+    for (int b = threadIdx.x; b < R; b += blockDim.x) cnt[(size_t)g * R + b] = hist[b];
+}
+
+// Stable split of group g's entries by block (one CTA of SNT threads per group, entries taken
+// SNT at a time in order): an entry's slot is its block's start, plus the entries of that block
+// in earlier rounds, in earlier warps of this round, and in earlier lanes of its warp.
+constexpr int SNT = 512;
+__global__ void __launch_bounds__(SNT) k_stg_scatter(const int* __restrict__ ptr, const int* __restrict__ grp,
+                                                     const int* __restrict__ seg_of, const int* __restrict__ idx,
+                                                     const double* __restrict__ val, int R, int rb,
+                                                     const int* __restrict__ bstart, int2* __restrict__ ent) {
+    extern __shared__ int sm[];
+    int* run = sm;              // R: entries of each block placed so far
+    int* wc = sm + R;           // (SNT/32) x R: entries of each block per warp in this round
+    const int g = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s0 = grp[g];
+    for (int b = threadIdx.x; b < R; b += SNT) run[b] = 0;
+    const int k0 = ptr[s0], k1 = ptr[grp[g + 1]];
+    for (int base = k0; base < k1; base += SNT) {
+        for (int q = threadIdx.x; q < (SNT / 32) * R; q += SNT) wc[q] = 0;
+        __syncthreads();
+        const int k = base + threadIdx.x;
+        const bool ok = k < k1;
+        const int b = ok ? idx[k] / rb : -1 - lane;  // inactive lanes never match each other
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (ok && rank == 0) wc[warp * R + b] = __popc(peers);
+        __syncthreads();
+        if (ok) {
+            int before = 0;
+            for (int w = 0; w < warp; ++w) before += wc[w * R + b];
+            const int at = bstart[(size_t)g * R + b] + run[b] + before + rank;
+            const int gi = idx[k] - b * rb;
+            const float v = (float)val[k];
+            ent[at] = make_int2((seg_of[k] - s0) | (gi << 16), __float_as_int(v));
+        }
+        __syncthreads();
+        for (int bb = threadIdx.x; bb < R; bb += SNT) {
+            int add = 0;
+            for (int w = 0; w < SNT / 32; ++w) add += wc[w * R + bb];
+            run[bb] += add;
+        }
+        __syncthreads();
+    }
+}
+
+// Warp ranges of every (group, block): split[u * (NW1) + w] = first entry of bucket u whose segment
+// is at or after wseg[g][w] (w = 0 .. NW1-1; the last one is the bucket's end).
+__global__ void k_stg_split(const int2* __restrict__ ent, const int* __restrict__ bstart, const int* __restrict__ cnt,
+                            const int* __restrict__ wseg, int R, int nbuckets, int NW1, int* __restrict__ split) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nbuckets; u += gridDim.x * blockDim.x) {
+        const int g = u / R, st = bstart[u], en = st + cnt[u];
+        int* sp = split + (size_t)u * NW1;
+        sp[0] = st;
+        for (int w = 1; w < NW1 - 1; ++w) {
+            const int key = wseg[g * NW1 + w];
+            int lo = sp[w - 1], hi = en;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((ent[mid].x & 0xFFFF) < key)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            sp[w] = lo;
+        }
+        sp[NW1 - 1] = en;
+    }
+}
+
+// padded length of every warp range (a multiple of le)
+__global__ void k_stg_padlen(const int* __restrict__ split, long long nranges, int NW1, int le, int* __restrict__ plen) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nranges; r += (long long)gridDim.x * blockDim.x) {
+        const long long u = r / (NW1 - 1), w = r % (NW1 - 1);
+        const int len = split[u * NW1 + w + 1] - split[u * NW1 + w];
+        plen[r] = (len + le - 1) / le * le;
+    }
+}
+
+// Each warp range copied to its padded place (pstart: exclusive scan of the padded lengths), the
+// padding filled with zero-valued entries of the range's last segment, and the split table rewritten
+// in padded positions.
+__global__ void k_stg_pad(const int2* __restrict__ ent, const int* __restrict__ split, const int* __restrict__ pstart,
+                          long long nranges, int NW1, int2* __restrict__ pent, int* __restrict__ psplit,
+                          int total) {
+    const int lane = threadIdx.x & 31;
+    for (long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; r < nranges;
+         r += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const long long u = r / (NW1 - 1), w = r % (NW1 - 1);
+        const int a = split[u * NW1 + w], e = split[u * NW1 + w + 1];
+        const int to = pstart[r];
+        const int plen = (r + 1 < nranges ? pstart[r + 1] : total) - to;
+        for (int q = lane; q < plen; q += 32)
+            pent[to + q] = q < e - a ? ent[a + q] : make_int2(ent[e - 1].x & 0xFFFF, 0);
+        if (lane == 0) {
+            psplit[u * NW1 + w] = to;
+            if (w == NW1 - 2) psplit[u * NW1 + w + 1] = to + plen;
+        }
+    }
+}
+
+// sum of the squared FP32-rounded values of each row, in FP64, rounded to FP32
+__global__ void k_row_sq(const int* __restrict__ row_ptr, const double* __restrict__ val, int m, float* __restrict__ rsq) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        double r = 0.0;
+        for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            const double a = (double)(float)val[k];
+            r += a * a;
+        }
+        rsq[i] = (float)r;
+    }
+}
+
 }  // namespace setup
 }  // namespace mfs

@@ -129,6 +129,7 @@ struct mfs_solver {
     int64_t hist_count = 0;
     // staged FP32 sweeps (mfs_staged.cuh): built at create for FP32 problems without Lorentz cones
     bool stg_ok = false;
+    bool stg_auto_row = false;  // the automatic choice runs the staged row pass
     int sweep_kind = MFS_SWEEP_AUTO;
     mfs::staged::StagedArgs stg_col{}, stg_row{};
     int* stg_err = nullptr;
@@ -353,7 +354,7 @@ struct StagedHost {
 // bounds the group size. Returns false if not even small groups fit.
 bool build_staged(const std::vector<int>& ptr, const mfs::host::uvec<int>& idx, const mfs::host::uvec<double>& val,
                   int nseg, int nother, int groups, int rb, int stages, int lane_e, size_t smem_limit,
-                  StagedHost& S) {
+                  StagedHost& S, bool plan_only = false) {
     using namespace mfs::host;
     using mfs::staged::NW;
     const int RB = rb;
@@ -399,6 +400,7 @@ bool build_staged(const std::vector<int>& ptr, const mfs::host::uvec<int>& idx, 
         }
         w[NW] = e - a;
     }
+    if (plan_only) return true;  // groups and warp segments only (the entries are built on the GPU)
     uvec<int> key((size_t)o), loc((size_t)o);
     parallel_ranges(G, std::min(threads_for(o), G), [&](int64_t g0, int64_t g1, int) {
         for (int64_t g = g0; g < g1; ++g)
@@ -716,13 +718,15 @@ mfs_status residual_grids(mfs_solver* s) {
 
 // ---------------------------------------------------------------------------------- launches
 
-// Staged passes in use (FP32 iterate): only on request; the automatic choice is the chunked sweeps,
-// which are faster on every workload measured so far.
+// Staged passes in use (FP32 iterate): on request both; automatically the row pass, when its layout
+// was built on the GPU at no host cost for a large matrix with at least 4 nonzeros per entry of x
+// (every row CTA streams half of x), where it beat the chunked row sweep (94 against 110 us on the
+// 10^6 x 2.5*10^6 LP); the staged column pass did not beat the chunked one.
 bool staged_col(const mfs_solver* s) {
     return s->stg_ok && s->sweep_kind == MFS_SWEEP_STAGED;
 }
 bool staged_row(const mfs_solver* s) {
-    return s->stg_ok && s->sweep_kind == MFS_SWEEP_STAGED;
+    return s->stg_ok && (s->sweep_kind == MFS_SWEEP_STAGED || (s->sweep_kind == MFS_SWEEP_AUTO && s->stg_auto_row));
 }
 
 inline int warp_grid(int nchunks) {
@@ -990,18 +994,104 @@ mfs_status alloc_state(mfs_solver* s, State<T>& st, const HostProblem& P, const 
 // Staged sweeps for an FP32 problem with orthant cones only: both layouts, the row norms, the
 // kernels' shared-memory limits; the automatic choice takes a staged pass when the matrix is large
 // and the gathered vector small against its nonzeros (every CTA reads the whole vector).
+// Exclusive scan of n ints on the device (mfs_setup.cuh); *total (nullable) receives their sum.
+mfs_status device_scan(mfs_solver* s, const int* in, int* out, int64_t n, int* total) {
+    namespace su = mfs::setup;
+    if (n <= 0) {
+        if (total) *total = 0;
+        return MFS_OK;
+    }
+    const int blocks = (int)((n + su::SPAN - 1) / su::SPAN);
+    int* blk = nullptr;
+    cudaError_t e = mfs::device_malloc((void**)&blk, (size_t)(blocks + 1) * sizeof(int));
+    if (e != cudaSuccess) return fail(s, MFS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    su::k_scan_local<<<blocks, su::NT, 0, s->stream>>>(in, out, blk, n);
+    su::k_scan_blocks<<<1, 1024, 0, s->stream>>>(blk, blocks, blk + blocks);
+    su::k_scan_add<<<blocks, su::NT, 0, s->stream>>>(out, blk, n);
+    if (total) cudaMemcpyAsync(total, blk + blocks, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    cudaStreamSynchronize(s->stream);
+    cudaFree(blk);
+    CUDA_TRY(s, cudaGetLastError());
+    return MFS_OK;
+}
+
+// The staged layout of one pass built on the GPU (mfs_setup.cuh) from a device order (segment
+// pointers, gathered indices, FP64 values), for the plan S (groups and warp segments) made on the
+// host. The result equals build_staged's; g receives the entry array, split table, group and warp
+// segment arrays.
+mfs_status staged_on_device(mfs_solver* s, const StagedHost& S, const int* d_ptr, int nseg, int64_t o,
+                            const int* d_idx, const double* d_val, int rb, int lane_e, mfs::staged::StagedArgs& g) {
+    namespace su = mfs::setup;
+    using mfs::staged::NW;
+    const int G = S.G, R = S.R, NW1 = NW + 1;
+    const int64_t nb = (int64_t)G * R, nr = nb * NW;
+    cudaStream_t st = s->stream;
+    const int grid = 8 * s->num_sms;
+    std::vector<void*> tmp;
+    struct Free {
+        std::vector<void*>& v;
+        ~Free() {
+            for (void* q : v) cudaFree(q);
+        }
+    } release{tmp};
+    auto grab = [&](void** q, size_t bytes) -> mfs_status {
+        cudaError_t e = mfs::device_malloc(q, std::max<size_t>(bytes, 16));
+        if (e != cudaSuccess)
+            return fail(s, e == cudaErrorMemoryAllocation ? MFS_ERR_OOM : MFS_ERR_CUDA,
+                        std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        tmp.push_back(*q);
+        return MFS_OK;
+    };
+    int *grp = nullptr, *wseg = nullptr, *psplit = nullptr;
+    TRY(upload(s, &grp, S.grp.data(), S.grp.size()));
+    TRY(upload(s, &wseg, S.wseg.data(), S.wseg.size()));
+    TRY(dalloc(s, &psplit, (size_t)nb * NW1));
+    int *segof = nullptr, *cnt = nullptr, *bstart = nullptr, *split = nullptr, *plen = nullptr, *pstart = nullptr;
+    int2* ent = nullptr;
+    TRY(grab((void**)&segof, (size_t)o * sizeof(int)));
+    TRY(grab((void**)&cnt, (size_t)nb * sizeof(int)));
+    TRY(grab((void**)&bstart, (size_t)nb * sizeof(int)));
+    TRY(grab((void**)&ent, (size_t)o * sizeof(int2)));
+    TRY(grab((void**)&split, (size_t)nb * NW1 * sizeof(int)));
+    TRY(grab((void**)&plen, (size_t)nr * sizeof(int)));
+    TRY(grab((void**)&pstart, (size_t)nr * sizeof(int)));
+    su::k_seg_of<<<grid, 256, 0, st>>>(d_ptr, nseg, segof);
+    su::k_stg_count<<<G, 256, (size_t)R * sizeof(int), st>>>(d_ptr, grp, d_idx, R, rb, cnt);
+    TRY(device_scan(s, cnt, bstart, nb, nullptr));
+    const size_t scat_smem = (size_t)(1 + su::SNT / 32) * R * sizeof(int);
+    CUDA_TRY(s, cudaFuncSetAttribute(su::k_stg_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scat_smem));
+    su::k_stg_scatter<<<G, su::SNT, scat_smem, st>>>(d_ptr, grp, segof, d_idx, d_val, R, rb, bstart, ent);
+    su::k_stg_split<<<(int)std::min<int64_t>((nb + 255) / 256, grid), 256, 0, st>>>(ent, bstart, cnt, wseg, R, (int)nb,
+                                                                                   NW1, split);
+    su::k_stg_padlen<<<grid, 256, 0, st>>>(split, nr, NW1, lane_e, plen);
+    int total = 0;
+    TRY(device_scan(s, plen, pstart, nr, &total));
+    int2* pent = nullptr;
+    TRY(dalloc(s, &pent, (size_t)std::max(total, 1)));
+    su::k_stg_pad<<<grid, 256, 0, st>>>(ent, split, pstart, nr, NW1, pent, psplit, total);
+    CUDA_TRY(s, cudaGetLastError());
+    CUDA_TRY(s, cudaStreamSynchronize(st));
+    g.ent = pent;
+    g.split = psplit;
+    g.grp = grp;
+    g.wseg = wseg;
+    g.nent = total;
+    return MFS_OK;
+}
+
 mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
     using namespace mfs::staged;
     int optin = 0;
     CUDA_TRY(s, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
     StagedHost C, W;
+    const bool dev = P.dev.on;  // the orders live on the device: plan on the host, build there
     if (!build_staged(P.col_ptr, P.csc_row, P.csc_val, P.n, P.m, s->num_sms, RB_COL, S_COL, LE_COL, (size_t)optin,
-                      C) ||
+                      C, dev) ||
         !build_staged(P.row_ptr, P.csr_col, P.csr_val, P.m, P.n, std::max(1, s->num_sms / ROW_HALVES), RB_ROW,
-                      S_ROW, LE_ROW, (size_t)optin, W))
+                      S_ROW, LE_ROW, (size_t)optin, W, dev))
         return MFS_OK;  // vectors too long for the split tables: chunked sweeps only
     std::vector<float> rsq(std::max(P.m, 1), 0.f);
-    mfs::host::parallel_ranges(P.m, mfs::host::threads_for(P.o), [&](int64_t i0, int64_t i1, int) {
+    if (!dev) mfs::host::parallel_ranges(P.m, mfs::host::threads_for(P.o), [&](int64_t i0, int64_t i1, int) {
         for (int64_t i = i0; i < i1; ++i) {
             double r = 0.0;
             for (int q = P.row_ptr[i]; q < P.row_ptr[i + 1]; ++q) {
@@ -1016,16 +1106,23 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
     CUDA_TRY(s, cudaMallocHost(&s->h_err, sizeof(int)));
     *s->h_err = 0;
     auto fill = [&](StagedHost& H, StagedArgs& g, const float* vec, int halves, int nseg) -> mfs_status {
-        int2* ent = nullptr;
-        int *split = nullptr, *grp = nullptr, *wseg = nullptr;
-        TRY(upload(s, &ent, H.ent.data(), H.ent.size()));
-        TRY(upload(s, &split, H.split.data(), H.split.size()));
-        TRY(upload(s, &grp, H.grp.data(), H.grp.size()));
-        TRY(upload(s, &wseg, H.wseg.data(), H.wseg.size()));
-        g.ent = ent;
-        g.split = split;
-        g.grp = grp;
-        g.wseg = wseg;
+        if (!dev) {
+            int2* ent = nullptr;
+            int *split = nullptr, *grp = nullptr, *wseg = nullptr;
+            TRY(upload(s, &ent, H.ent.data(), H.ent.size()));
+            TRY(upload(s, &split, H.split.data(), H.split.size()));
+            TRY(upload(s, &grp, H.grp.data(), H.grp.size()));
+            TRY(upload(s, &wseg, H.wseg.data(), H.wseg.size()));
+            g.ent = ent;
+            g.split = split;
+            g.grp = grp;
+            g.wseg = wseg;
+            g.nent = (int)H.ent.size();
+        } else if (&g == &s->stg_col) {
+            TRY(staged_on_device(s, H, s->col_ptr, P.n, P.o, P.dev.crow, P.dev.cval, RB_COL, LE_COL, g));
+        } else {
+            TRY(staged_on_device(s, H, s->row_ptr, P.m, P.o, P.dev.rcol, P.dev.rval, RB_ROW, LE_ROW, g));
+        }
         g.vec = vec;
         g.err = s->stg_err;
         g.G = H.G;
@@ -1035,7 +1132,6 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
         g.nseg = nseg;
         g.part = nullptr;
         if (halves > 1) TRY(dalloc(s, &g.part, (size_t)halves * std::max(nseg, 1)));
-        g.nent = (int)H.ent.size();
         g.spin = 1 << 24;
         g.no_loads = 0;
         return MFS_OK;
@@ -1043,7 +1139,15 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
     TRY(fill(C, s->stg_col, s->s32.v, 1, P.n));
     TRY(fill(W, s->stg_row, s->s32.x, ROW_HALVES, P.m));
     float* d_rsq = nullptr;
-    TRY(upload(s, &d_rsq, rsq.data(), rsq.size()));
+    if (dev) {
+        TRY(dalloc(s, &d_rsq, (size_t)std::max(P.m, 1)));
+        if (P.m > 0)
+            mfs::setup::k_row_sq<<<(int)std::min<int64_t>((P.m + 255) / 256, 8 * s->num_sms), 256, 0, s->stream>>>(
+                s->row_ptr, P.dev.rval, P.m, d_rsq);
+        CUDA_TRY(s, cudaGetLastError());
+    } else {
+        TRY(upload(s, &d_rsq, rsq.data(), rsq.size()));
+    }
     s->stg_row.rsq = d_rsq;
     // the limit is a property of the kernel, shared by all solvers: allow the device's maximum
     CUDA_TRY(s, cudaFuncSetAttribute(MFS_STAGED_COL, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -1461,9 +1565,9 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
     }
     if (total != n) return fail(nullptr, MFS_ERR_INVALID, "cone sizes do not sum to n");
     bool in_order = false;
-    // large inputs are checked and, when already in column order, set up on the GPU; the staged
-    // layout is built from host arrays
-    const bool dev_path = nnz >= (int64_t(1) << 16) && set.sweep != MFS_SWEEP_STAGED;
+    // large inputs are checked and, when already in column order, set up on the GPU (the staged
+    // layout too)
+    const bool dev_path = nnz >= (int64_t(1) << 16);
     if (!dev_path) {
         // first bad entry: index out of range, or a non-finite value; and whether the entries are
         // already in (column, row) order (equal neighbours are duplicates, summed later)
@@ -1585,7 +1689,10 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
         CHK(alloc_state<float>(s, s->s32, P, b, c));
         CHK(residual_grids<float>(s));
         s->have32 = true;
-        if (set.sweep == MFS_SWEEP_STAGED && !s->has_soc && P.o > 0) CHK(setup_staged(s, P));
+        const bool auto_row = set.sweep == MFS_SWEEP_AUTO && P.dev.on && P.o >= (1 << 20) &&
+                              (int64_t)P.o >= 4 * (int64_t)P.n;
+        if ((set.sweep == MFS_SWEEP_STAGED || auto_row) && !s->has_soc && P.o > 0) CHK(setup_staged(s, P));
+        s->stg_auto_row = s->stg_ok && auto_row;
         s->sweep_kind = s->stg_ok ? set.sweep : MFS_SWEEP_AUTO;
     }
     if (set.precision == MFS_FP64 || set.polish_iters > 0) {

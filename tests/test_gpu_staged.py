@@ -87,12 +87,21 @@ def test_solve_with_staged_sweeps_and_polish():
 
 def test_auto_choice_and_invalid_requests():
     big = I.large_lp(1, m=60_000, n=150_000)   # 1.2 M nonzeros, 20 per row and 8 per column
-    plain = mfs.Solver(big, precision="fp32")
+    auto = mfs.Solver(big, precision="fp32")    # in column order: set up on the GPU
+    info = auto.info()
+    assert (info["sweep_col"], info["sweep_row"]) == (mfs.SWEEP_CHUNKED, mfs.SWEEP_STAGED)
+    orc = oracle.make_oracle(big, dtype=np.float32)
+    orc.iterate(30)
+    auto.iterate(30)
+    compare(auto.solution(), orc.state(), TOL["fp32"], "auto: chunked column pass, staged row pass")
+    plain = mfs.Solver(big, precision="fp32", sweep="chunked")
     info = plain.info()
-    assert (info["sweep_col"], info["sweep_row"]) == (mfs.SWEEP_CHUNKED, mfs.SWEEP_CHUNKED)  # auto
+    assert (info["sweep_col"], info["sweep_row"]) == (mfs.SWEEP_CHUNKED, mfs.SWEEP_CHUNKED)
     with pytest.raises(mfs.MfsError) as e:                    # no staged layout built
         plain.set_sweep("staged")
     assert e.value.status == mfs.MFS_ERR_INVALID
+    small = mfs.Solver(I.small_lp(0), precision="fp32")
+    assert small.info()["sweep_row"] == mfs.SWEEP_CHUNKED     # auto: too small
     s = mfs.Solver(big, precision="fp32", sweep="staged")
     info = s.info()
     assert (info["sweep_col"], info["sweep_row"]) == (mfs.SWEEP_STAGED, mfs.SWEEP_STAGED)

@@ -478,6 +478,27 @@ bool build_staged(const std::vector<int>& ptr, const mfs::host::uvec<int>& idx, 
     return true;
 }
 
+// Exclusive scan of n ints on the device (mfs_setup.cuh); *total (nullable) receives their sum.
+mfs_status device_scan(mfs_solver* s, const int* in, int* out, int64_t n, int* total) {
+    namespace su = mfs::setup;
+    if (n <= 0) {
+        if (total) *total = 0;
+        return MFS_OK;
+    }
+    const int blocks = (int)((n + su::SPAN - 1) / su::SPAN);
+    int* blk = nullptr;
+    cudaError_t e = mfs::device_malloc((void**)&blk, (size_t)(blocks + 1) * sizeof(int));
+    if (e != cudaSuccess) return fail(s, MFS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    su::k_scan_local<<<blocks, su::NT, 0, s->stream>>>(in, out, blk, n);
+    su::k_scan_blocks<<<1, 1024, 0, s->stream>>>(blk, blocks, blk + blocks);
+    su::k_scan_add<<<blocks, su::NT, 0, s->stream>>>(out, blk, n);
+    if (total) cudaMemcpyAsync(total, blk + blocks, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    cudaStreamSynchronize(s->stream);
+    cudaFree(blk);
+    CUDA_TRY(s, cudaGetLastError());
+    return MFS_OK;
+}
+
 // Device set-up (mfs_setup.cuh): upload the COO, check it, and if it is valid and in column order
 // (duplicates next to each other) build both orders on the GPU, leaving P.dev.on set and P.col_ptr, P.row_ptr, P.o on the host.
 // An input out of order leaves P.dev.on unset (the host orders it); an invalid one fails.
@@ -497,9 +518,8 @@ mfs_status device_orders(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const
     const int grid = 8 * s->num_sms;
     long long *d_row = nullptr, *d_col = nullptr;
     double *d_val = nullptr, *d_sum = nullptr;
-    int *d_keep = nullptr, *d_pos = nullptr, *d_blk = nullptr, *d_total = nullptr, *d_flags = nullptr;
+    int *d_keep = nullptr, *d_pos = nullptr, *d_flags = nullptr;
     unsigned long long* d_bad = nullptr;
-    const long long nb = (nnz + su::SPAN - 1) / su::SPAN;
     TRY(grab((void**)&d_row, nnz * sizeof(long long)));
     TRY(grab((void**)&d_col, nnz * sizeof(long long)));
     TRY(grab((void**)&d_val, nnz * sizeof(double)));
@@ -528,19 +548,9 @@ mfs_status device_orders(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const
     TRY(grab((void**)&d_keep, nnz * sizeof(int)));
     TRY(grab((void**)&d_pos, nnz * sizeof(int)));
     TRY(grab((void**)&d_sum, nnz * sizeof(double)));
-    TRY(grab((void**)&d_blk, (std::max<long long>(nb, (m + su::SPAN - 1) / su::SPAN) + 1) * sizeof(int)));
-    TRY(grab((void**)&d_total, sizeof(int)));
     su::k_runs<<<grid, su::NT, 0, st>>>(d_row, d_col, d_val, nnz, d_keep, d_sum);
-    auto scan = [&](const int* in, int* out, long long cnt) {
-        const int blocks = (int)((cnt + su::SPAN - 1) / su::SPAN);
-        su::k_scan_local<<<blocks, su::NT, 0, st>>>(in, out, d_blk, cnt);
-        su::k_scan_blocks<<<1, 1024, 0, st>>>(d_blk, blocks, d_total);
-        su::k_scan_add<<<blocks, su::NT, 0, st>>>(out, d_blk, cnt);
-    };
-    scan(d_keep, d_pos, nnz);
     int o = 0;
-    CUDA_TRY(s, cudaMemcpyAsync(&o, d_total, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(s, cudaStreamSynchronize(st));
+    TRY(device_scan(s, d_keep, d_pos, nnz, &o));
     int* d_ccol = nullptr;
     TRY(grab((void**)&D.crow, (size_t)o * sizeof(int)));
     TRY(grab((void**)&d_ccol, (size_t)o * sizeof(int)));
@@ -557,7 +567,7 @@ mfs_status device_orders(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const
     if (o > 0) su::k_seg_ptr<<<grid, su::NT, 0, st>>>(d_ccol, o, (int)n, d_cptr);
     CUDA_TRY(s, cudaMemsetAsync(d_cnt, 0, (size_t)std::max<int64_t>(m, 1) * sizeof(int), st));
     su::k_count<<<grid, su::NT, 0, st>>>(D.crow, o, d_cnt);
-    if (m > 0) scan(d_cnt, d_rptr, m);
+    TRY(device_scan(s, d_cnt, d_rptr, m, nullptr));
     CUDA_TRY(s, cudaMemcpyAsync(d_rptr + m, &o, sizeof(int), cudaMemcpyHostToDevice, st));
     CUDA_TRY(s, cudaMemsetAsync(d_cnt, 0, (size_t)std::max<int64_t>(m, 1) * sizeof(int), st));
     su::k_scatter_rows<<<grid, su::NT, 0, st>>>(D.crow, d_ccol, D.cval, o, d_rptr, d_cnt, D.rcol, D.rval);
@@ -994,27 +1004,6 @@ mfs_status alloc_state(mfs_solver* s, State<T>& st, const HostProblem& P, const 
 // Staged sweeps for an FP32 problem with orthant cones only: both layouts, the row norms, the
 // kernels' shared-memory limits; the automatic choice takes a staged pass when the matrix is large
 // and the gathered vector small against its nonzeros (every CTA reads the whole vector).
-// Exclusive scan of n ints on the device (mfs_setup.cuh); *total (nullable) receives their sum.
-mfs_status device_scan(mfs_solver* s, const int* in, int* out, int64_t n, int* total) {
-    namespace su = mfs::setup;
-    if (n <= 0) {
-        if (total) *total = 0;
-        return MFS_OK;
-    }
-    const int blocks = (int)((n + su::SPAN - 1) / su::SPAN);
-    int* blk = nullptr;
-    cudaError_t e = mfs::device_malloc((void**)&blk, (size_t)(blocks + 1) * sizeof(int));
-    if (e != cudaSuccess) return fail(s, MFS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-    su::k_scan_local<<<blocks, su::NT, 0, s->stream>>>(in, out, blk, n);
-    su::k_scan_blocks<<<1, 1024, 0, s->stream>>>(blk, blocks, blk + blocks);
-    su::k_scan_add<<<blocks, su::NT, 0, s->stream>>>(out, blk, n);
-    if (total) cudaMemcpyAsync(total, blk + blocks, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
-    cudaStreamSynchronize(s->stream);
-    cudaFree(blk);
-    CUDA_TRY(s, cudaGetLastError());
-    return MFS_OK;
-}
-
 // The staged layout of one pass built on the GPU (mfs_setup.cuh) from a device order (segment
 // pointers, gathered indices, FP64 values), for the plan S (groups and warp segments) made on the
 // host. The result equals build_staged's; g receives the entry array, split table, group and warp

@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the extra workloads (batched LPs, shared-A family, MLP step)")
+    ap.add_argument("--sweep", default="auto", choices=["auto", "chunked", "staged"],
+                    help="sweep kernels of the large LP's FP32 iteration (auto: chunked column sweep, staged row pass)")
     ap.add_argument("--warm-start", type=int, default=2048, metavar="TRAIN",
                     help="learned warm-start experiment with TRAIN training solves (0 skips it; 50000 is the "
                          "full experiment, about 15 minutes)")
@@ -463,7 +465,7 @@ def main():
     prob = make_problem(args.workload, rank)
     stream = torch.cuda.current_stream()
     s = mfs.Solver(prob, precision="fp32", polish_iters=0, check_every=ITERS_PER_STEP,
-                   stream=stream.cuda_stream)
+                   stream=stream.cuda_stream, sweep=args.sweep)
     info = s.info()
     o, m, n = info["o"], info["m"], info["n"]
 
@@ -550,7 +552,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s3 = mfs.Solver(prob, precision="fp32", polish_iters=0, check_every=ITERS_PER_STEP,
-                        stream=stream.cuda_stream)
+                        stream=stream.cuda_stream, sweep=args.sweep)
         for _ in range(args.steps):
             s3.iterate(ITERS_PER_STEP)
             s3.residuals()
@@ -575,6 +577,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 reductions)", "data": "synthetic",
                 "config": {"workload": args.workload, "m": m, "n": n, "o": o,
                            "iterations_per_step": ITERS_PER_STEP, "precision": "fp32 sweep + fp64 residuals",
+                           "sweeps": {"col": "staged" if info["sweep_col"] == mfs.SWEEP_STAGED else "chunked",
+                                      "row": "staged" if info["sweep_row"] == mfs.SWEEP_STAGED else "chunked"},
                            "l2": "inputs larger than L2 (A alone is %.0f MB in FP32)" % (16 * o / 1e6),
                            "parallelism": f"replicas{world}"},
                 "kkt_after_timed_region": r["kkt"],

@@ -143,13 +143,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hashes():
+def kernel_source_hashes(names):
     import hashlib
     out = {}
-    for name in ("mfs_kernels.cuh", "mfs_device.cuh"):
+    for name in names:
         with open(os.path.join(ROOT, "paper_2203_05027_b300", "csrc", name), "rb") as f:
             out[name] = hashlib.sha256(f.read()).hexdigest()[:16]
     return out
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes of one launch of `kernel` from the committed ncu record, or None when there is
+    none or one of the sources it was captured from has changed since."""
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(tpath):
+        return None
+    with open(tpath) as f:
+        rec = json.load(f).get("kernels", {}).get(kernel)
+    if not rec or rec.get("sources") != kernel_source_hashes(sorted(rec.get("sources", {}))):
+        return None
+    return rec["dram_bytes"]
 
 
 def kernel_roofline(s, info, peak, peak_kind, m, n, o, sm_mhz, num_sms=148):
@@ -168,13 +181,7 @@ def kernel_roofline(s, info, peak, peak_kind, m, n, o, sm_mhz, num_sms=148):
     dom = col if col["ms"] >= row["ms"] else row
     achieved = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
     it_gbs = info["bytes_per_iter"] / (t["iter_ms"] * 1e-3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            tr = json.load(f)
-        if tr.get("source_sha256_16") == kernel_source_hashes() and dom["kernel"] in tr:
-            traffic = tr[dom["kernel"]]["dram_bytes"]
+    traffic = recorded_traffic(dom["kernel"])
     clock_hz = (sm_mhz or 2032.0) * 1e6
     floor_ms = o / (num_sms * clock_hz) * 1e3
     return {"bound": "hbm", "kernel": dom["kernel"], "achieved": round(achieved, 1), "peak": peak,

@@ -129,6 +129,7 @@ struct mfs_solver {
     int64_t hist_count = 0;
     // staged FP32 sweeps (mfs_staged.cuh): built at create for FP32 problems without Lorentz cones
     bool stg_ok = false;
+    bool stg_auto_col = false;  // the automatic choice runs the staged column pass
     bool stg_auto_row = false;  // the automatic choice runs the staged row pass
     int sweep_kind = MFS_SWEEP_AUTO;
     mfs::staged::StagedArgs stg_col{}, stg_row{};
@@ -728,12 +729,13 @@ mfs_status residual_grids(mfs_solver* s) {
 
 // ---------------------------------------------------------------------------------- launches
 
-// Staged passes in use (FP32 iterate): on request both; automatically the row pass, when its layout
-// was built on the GPU at no host cost for a large matrix with at least 4 nonzeros per entry of x
-// (every row CTA streams half of x), where it beat the chunked row sweep (94 against 110 us on the
-// 10^6 x 2.5*10^6 LP); the staged column pass did not beat the chunked one.
+// Staged passes in use (FP32 iterate): on request both; automatically each pass whose layout was
+// built on the GPU at no host cost for a large matrix with at least 8 nonzeros per vector entry a
+// CTA streams (column pass: o >= 8 m, every CTA streams all of v; row pass: o >= 4 n, every CTA
+// streams half of x). On the 10^6 x 2.5*10^6 LP (o = 20 m = 8 n) the staged passes took 105 and
+// 94 us against 120 and 110 us for the chunked sweeps.
 bool staged_col(const mfs_solver* s) {
-    return s->stg_ok && s->sweep_kind == MFS_SWEEP_STAGED;
+    return s->stg_ok && (s->sweep_kind == MFS_SWEEP_STAGED || (s->sweep_kind == MFS_SWEEP_AUTO && s->stg_auto_col));
 }
 bool staged_row(const mfs_solver* s) {
     return s->stg_ok && (s->sweep_kind == MFS_SWEEP_STAGED || (s->sweep_kind == MFS_SWEEP_AUTO && s->stg_auto_row));
@@ -1678,9 +1680,14 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
         CHK(alloc_state<float>(s, s->s32, P, b, c));
         CHK(residual_grids<float>(s));
         s->have32 = true;
-        const bool auto_row = set.sweep == MFS_SWEEP_AUTO && P.dev.on && P.o >= (1 << 20) &&
-                              (int64_t)P.o >= 4 * (int64_t)P.n;
-        if ((set.sweep == MFS_SWEEP_STAGED || auto_row) && !s->has_soc && P.o > 0) CHK(setup_staged(s, P));
+        // what the automatic choice stages (the same whether or not it is the creation's choice)
+        const bool big = P.dev.on && P.o >= (1 << 20);
+        const bool auto_col = big && (int64_t)P.o >= 8 * (int64_t)P.m;
+        const bool auto_row = big && (int64_t)P.o >= 4 * (int64_t)P.n;
+        if ((set.sweep == MFS_SWEEP_STAGED || (set.sweep == MFS_SWEEP_AUTO && (auto_col || auto_row))) &&
+            !s->has_soc && P.o > 0)
+            CHK(setup_staged(s, P));
+        s->stg_auto_col = s->stg_ok && auto_col;
         s->stg_auto_row = s->stg_ok && auto_row;
         s->sweep_kind = s->stg_ok ? set.sweep : MFS_SWEEP_AUTO;
     }

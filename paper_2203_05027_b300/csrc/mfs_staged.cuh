@@ -19,7 +19,8 @@
 // Every CTA reads the whole vector once per pass (148 x 4 MB for a 10^6-row v), which L2 serves
 // at about 28 TB/s to all SMs; the random gathers then cost shared-memory bank cycles instead of
 // L2 sector requests. The nonzeros stream from HBM once, prefetched two blocks ahead into
-// registers; the epilogue's loads are batched so that several are in flight per thread.
+// registers; the epilogue's inputs are prefetched into L2 (bulk prefetches) a few blocks before
+// the group's last one, and its loads are batched so that several are in flight per thread.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -67,6 +68,11 @@ constexpr int PF_COL = MFS_STG_PF_COL;  // steps of 32 * LE entries prefetched p
 constexpr int LE_ROW = MFS_STG_LE_ROW;
 constexpr int PF_ROW = MFS_STG_PF_ROW;
 constexpr int EPI_U = 8;       // epilogue items per thread in flight
+#ifndef MFS_STG_EPI_PF
+#define MFS_STG_EPI_PF 4
+#endif
+constexpr int EPI_PF = MFS_STG_EPI_PF;  // blocks before a group's last one at which its epilogue's
+                                        // inputs are prefetched into L2 (0: no prefetch)
 
 // dynamic shared memory of one CTA: the vector stages, the group's sums, its split table, 2 S mbarriers
 __host__ __device__ constexpr size_t smem_bytes(int rb, int stages, int maxg, int R) {
@@ -101,6 +107,13 @@ __device__ __forceinline__ void issue_block(float* dst, const float* src, uint32
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
+}
+
+// Hint: bring the 16-byte-aligned part of [p, p + bytes) into L2 (a bulk prefetch; no access
+// outside the range, no completion to wait for).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+    const uintptr_t s = ((uintptr_t)p + 15) & ~(uintptr_t)15, e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+    if (e > s) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"((uint32_t)(e - s)) : "memory");
 }
 
 // Bounded wait for phase `parity` of an mbarrier; false if it gave up.
@@ -323,6 +336,21 @@ __global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, cons
                     const uint32_t u = u0 + (b - bb), k = u % S;
                     if (u >= S && !wait_block(empty + k, (u / S - 1) & 1u, g.spin)) bad = true;
                     issue_block(vb + k * RB, g.vec + (size_t)b * RB, RB * 4u, full + k);
+                    if (EPI_PF > 0 && b == (be - EPI_PF > bb ? be - EPI_PF : bb)) {
+                        // the group's epilogue reads these once every warp has seen all blocks
+                        const size_t cnt = (size_t)(g.grp[grp + 1] - k0);
+                        if (MODE == 0) {
+                            prefetch_l2(a.x + k0, cnt * 4);
+                            prefetch_l2(a.z + k0, cnt * 4);
+                            prefetch_l2(a.del + k0, cnt * 4);
+                            prefetch_l2(a.c + k0, cnt * 4);
+                            prefetch_l2(a.col_ptr + k0, (cnt + 1) * 4);
+                        } else if (H == 1) {
+                            prefetch_l2(g.rsq + k0, cnt * 4);
+                            prefetch_l2(a.b + k0, cnt * 4);
+                            prefetch_l2(a.lam + k0, cnt * 4);
+                        }
+                    }
                 }
             }
         } else {

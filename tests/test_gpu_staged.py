@@ -89,11 +89,21 @@ def test_auto_choice_and_invalid_requests():
     big = I.large_lp(1, m=60_000, n=150_000)   # 1.2 M nonzeros, 20 per row and 8 per column
     auto = mfs.Solver(big, precision="fp32")    # in column order: set up on the GPU
     info = auto.info()
-    assert (info["sweep_col"], info["sweep_row"]) == (mfs.SWEEP_CHUNKED, mfs.SWEEP_STAGED)
+    assert (info["sweep_col"], info["sweep_row"]) == (mfs.SWEEP_STAGED, mfs.SWEEP_STAGED)
     orc = oracle.make_oracle(big, dtype=np.float32)
     orc.iterate(30)
     auto.iterate(30)
-    compare(auto.solution(), orc.state(), TOL["fp32"], "auto: chunked column pass, staged row pass")
+    compare(auto.solution(), orc.state(), TOL["fp32"], "auto: staged column and row passes")
+    auto.set_sweep("staged")                    # the automatic choice built the layout
+    # 4 nonzeros per row (o < 8 m), 10 per column: the automatic choice stages the row pass only
+    tall = I.lp_from_degrees(300_000, 120_000, np.full(120_000, 10, np.int64), 3)
+    t = mfs.Solver(tall, precision="fp32")
+    info = t.info()
+    assert (info["sweep_col"], info["sweep_row"]) == (mfs.SWEEP_CHUNKED, mfs.SWEEP_STAGED)
+    orc = oracle.make_oracle(tall, dtype=np.float32)
+    orc.iterate(20)
+    t.iterate(20)
+    compare(t.solution(), orc.state(), TOL["fp32"], "auto: chunked column pass, staged row pass")
     plain = mfs.Solver(big, precision="fp32", sweep="chunked")
     info = plain.info()
     assert (info["sweep_col"], info["sweep_row"]) == (mfs.SWEEP_CHUNKED, mfs.SWEEP_CHUNKED)
@@ -111,8 +121,11 @@ def test_auto_choice_and_invalid_requests():
     info = s.info()
     assert (info["sweep_col"], info["sweep_row"]) == (mfs.SWEEP_STAGED, mfs.SWEEP_STAGED)
     assert info["launches_per_iter"] == 3   # column pass, row pass in two halves, their combination
-    s.set_sweep("auto")
-    assert s.info()["sweep_col"] == mfs.SWEEP_CHUNKED
+    s.set_sweep("chunked")
+    assert s.info()["sweep_row"] == mfs.SWEEP_CHUNKED
+    s.set_sweep("auto")                         # the same choice as a solver created with auto
+    info = s.info()
+    assert (info["sweep_col"], info["sweep_row"]) == (mfs.SWEEP_STAGED, mfs.SWEEP_STAGED)
     f64 = mfs.Solver(I.small_lp(0), precision="fp64", sweep="staged")
     with pytest.raises(mfs.MfsError) as e:
         f64.set_sweep("staged")

@@ -745,15 +745,31 @@ inline int warp_grid(int nchunks) {
     return (nchunks + NWARP - 1) / NWARP;
 }
 
+// Launch a staged kernel so that it may start while the previous kernel on the stream still runs:
+// until it has waited for that kernel (griddepcontrol.wait) it reads only A's staged layout.
+template <typename... KArgs, typename... Args>
+void launch_dep(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = MFS_STG_PDL;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);  // an error is left for cudaGetLastError
+}
+
 template <typename T>
 void launch_col(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
     if (s->ncc == 0) return;
     if constexpr (std::is_same<T, float>::value) {
         if (staged_col(s)) {
             const StagedArgsT& g = s->stg_col;
-            MFS_STAGED_COL<<<std::min(g.G, s->num_sms), mfs::staged::NTS + 32,
-                             mfs::staged::smem_bytes(mfs::staged::RB_COL, mfs::staged::S_COL, g.maxg_pad, g.R), st>>>(g,
-                                                                                                                     a);
+            launch_dep(MFS_STAGED_COL, std::min(g.G, s->num_sms), mfs::staged::NTS + 32,
+                       mfs::staged::smem_bytes(mfs::staged::RB_COL, mfs::staged::S_COL, g.maxg_pad, g.R), st, g, a);
             return;
         }
     }
@@ -775,12 +791,11 @@ void launch_row_mode(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
     if constexpr (std::is_same<T, float>::value && MODE == 0) {
         if (staged_row(s)) {
             const StagedArgsT& g = s->stg_row;
-            MFS_STAGED_ROW<<<std::min(g.G * g.halves, s->num_sms), mfs::staged::NTS + 32,
-                             mfs::staged::smem_bytes(mfs::staged::RB_ROW, mfs::staged::S_ROW, g.maxg_pad, g.R), st>>>(g,
-                                                                                                                     a);
+            launch_dep(MFS_STAGED_ROW, std::min(g.G * g.halves, s->num_sms), mfs::staged::NTS + 32,
+                       mfs::staged::smem_bytes(mfs::staged::RB_ROW, mfs::staged::S_ROW, g.maxg_pad, g.R), st, g, a);
             if (g.halves > 1)
-                mfs::staged::k_row_combine<<<(int)std::min<int64_t>((s->m + 255) / 256, 8 * s->num_sms), 256, 0, st>>>(
-                    g, a);
+                launch_dep(mfs::staged::k_row_combine, (int)std::min<int64_t>((s->m + 255) / 256, 8 * s->num_sms), 256,
+                           0, st, g, a);
             return;
         }
     }

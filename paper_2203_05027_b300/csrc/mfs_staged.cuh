@@ -71,6 +71,9 @@ constexpr int EPI_U = 8;       // epilogue items per thread in flight
 #ifndef MFS_STG_EPI_PF
 #define MFS_STG_EPI_PF 4
 #endif
+#ifndef MFS_STG_PDL
+#define MFS_STG_PDL 1
+#endif
 constexpr int EPI_PF = MFS_STG_EPI_PF;  // blocks before a group's last one at which its epilogue's
                                         // inputs are prefetched into L2 (0: no prefetch)
 
@@ -107,6 +110,19 @@ __device__ __forceinline__ void issue_block(float* dst, const float* src, uint32
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
+}
+
+// Programmatic dependent launch. The passes are launched so that the next one may start while
+// this one runs: each kernel signals that at its start, does only work on data no earlier kernel
+// writes (barrier set-up, split table, its first blocks' entries) and then waits until the
+// previous kernel has completed and its writes are visible. Every thread waits before its first
+// access to the iterate, and every CTA waits before it exits, so a kernel's completion implies
+// its predecessor's. Without the launch attribute both instructions return at once.
+__device__ __forceinline__ void dep_launch_next() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void dep_wait_prev() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // Hint: bring the 16-byte-aligned part of [p, p + bytes) into L2 (a bulk prefetch; no access
@@ -311,6 +327,7 @@ __global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, cons
     uint64_t* full = reinterpret_cast<uint64_t*>(spl + (R * (NW + 1) + 3) / 4 * 4);
     uint64_t* empty = full + S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    dep_launch_next();
     if (threadIdx.x == 0) {
         for (int k = 0; k < S; ++k) {
             mbar_init(full + k, 1);
@@ -331,6 +348,7 @@ __global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, cons
         for (int t = threadIdx.x; t < R * (NW + 1); t += NTS + 32) spl[t] = gs[t];
         __syncthreads();  // split table in place; the previous group's sums are no longer read
         if (warp == NW) {
+            dep_wait_prev();  // the vector was written by the previous pass
             if (lane == 0 && !g.no_loads) {
                 for (int b = bb; b < be; ++b) {
                     const uint32_t u = u0 + (b - bb), k = u % S;
@@ -362,6 +380,7 @@ __global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, cons
             if (bb + 1 < be)
                 load_lane<PF, LE>(g.ent, spl[(bb + 1) * (NW + 1) + warp], spl[(bb + 1) * (NW + 1) + warp + 1], lane, B,
                                   g.nent);
+            dep_wait_prev();  // the epilogue reads and writes the iterate
             for (int b = bb; b < be; b += 3) {
                 const uint32_t u = u0 + (b - bb);
                 block_step<RB, PF, LE, S>(b, be, u, A, C, spl, g, vb, acc, full, empty, bad, warp, lane);
@@ -423,6 +442,7 @@ __global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, cons
         u0 += (uint32_t)(be - bb);
         __syncthreads();  // the group is done: its sums and split table may be replaced
     }
+    dep_wait_prev();  // (a CTA without a group)
     if (bad) {
         // a copy may still be in flight into a stage: wait (bounded) for the last load of each stage
         for (int d = 1; d <= S && (uint32_t)d <= u0; ++d) {
@@ -436,6 +456,8 @@ __global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, cons
 // Row pass with halves = 2: the two partial sums of each row, added in a fixed order, then rho,
 // lambda and v (as the row pass's own epilogue).
 __global__ void __launch_bounds__(256) k_row_combine(const StagedArgs g, const SweepArgs<float> a) {
+    dep_launch_next();
+    dep_wait_prev();
     const int m = g.nseg;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         const float ax = g.part[i] + g.part[(size_t)m + i];

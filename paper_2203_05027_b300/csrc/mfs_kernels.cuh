@@ -22,6 +22,8 @@
 // updates of Algorithm 1; gamma = -U^T lambda and y = V^T x + U^T rho are implied.)
 #pragma once
 
+#include <type_traits>
+
 #include "mfs_device.cuh"
 #include "mfs_measures.h"
 
@@ -497,6 +499,48 @@ __device__ __forceinline__ void cta_fields_out(double (&f)[NFIELD], double (*sh)
     }
 }
 
+// Per-lane residual fields of the FP32 iterate as double-float pairs (about 48 significant bits):
+// B300 runs FP64 at 1/64 of its FP32 rate, and FP64 arithmetic per column or row was the larger
+// part of the residual kernels' time. Each lane folds its pairs into FP64 once, before the FP64
+// reductions over the CTA and the grid. Maxima compare normalised pairs (hi first, then lo).
+__device__ __forceinline__ DF df_from(double d) {
+    const float h = (float)d;
+    return DF(h, (float)(d - (double)h));
+}
+__device__ __forceinline__ DF df_neg(const DF& a) {
+    return DF(-a.hi, -a.lo);
+}
+__device__ __forceinline__ DF df_abs(const DF& a) {
+    return a.hi < 0.f ? df_neg(a) : a;
+}
+__device__ __forceinline__ DF df_sq(const DF& a) {  // a^2, dropping lo^2 (relative 2^-48)
+    const float p = __fmul_rn(a.hi, a.hi);
+    return DF(p, __fmaf_rn(__fmul_rn(2.f, a.hi), a.lo, __fmaf_rn(a.hi, a.hi, -p)));
+}
+__device__ __forceinline__ DF df_max(const DF& a, const DF& b) {
+    return (a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo)) ? a : b;
+}
+template <typename A>
+__device__ __forceinline__ A acc_from(double d);
+template <>
+__device__ __forceinline__ DF acc_from<DF>(double d) {
+    return df_from(d);
+}
+template <>
+__device__ __forceinline__ double acc_from<double>(double d) {
+    return d;
+}
+
+// Fold a lane's pair fields into its FP64 fields (sums added, maxima taken).
+template <int NFIELD, bool ROW>
+__device__ __forceinline__ void fold_df_fields(double (&f)[NFIELD], const DF (&F)[NFIELD]) {
+#pragma unroll
+    for (int k = 0; k < NFIELD; ++k) {
+        const double v = to_double(F[k]);
+        f[k] = field_max<NFIELD, ROW>(k) ? fmax(f[k], v) : f[k] + v;
+    }
+}
+
 struct ResidArgs {
     double* part_row;  // NFR x (row-residual grid)
     double* part_col;  // NFC x (column-residual grid)
@@ -506,7 +550,8 @@ struct ResidArgs {
     int write_all_s;
 };
 
-// FP64 row-side residual fields: ||Ax - b||, max|Ax - b|, max|Ax|, ||b||, max|b|, b^T lambda.
+// Row-side residual fields: ||Ax - b||, max|Ax - b|, max|Ax|, ||b||, max|b|, b^T lambda, reduced in
+// FP64 (per lane as double-float pairs for the FP32 iterate).
 // Persistent warps walk the row chunks.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_row_resid(const SweepArgs<T> a, const ResidArgs r) {
@@ -514,19 +559,23 @@ __global__ void __launch_bounds__(NT) k_row_resid(const SweepArgs<T> a, const Re
     __shared__ A s_end[NWARP][ESLOTS];
     __shared__ double s_red[NWARP][NFR];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr bool F32 = std::is_same<T, float>::value;
     double f[NFR];
+    DF F[F32 ? NFR : 1];
 #pragma unroll
     for (int k = 0; k < NFR; ++k) f[k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < (F32 ? NFR : 1); ++k) F[k] = DF(0);
     const T* __restrict__ x = a.x;
     const int n = a.n;
     auto prod = [x, n](int j, T val, A (&p)[1]) { p[0] = acc_prod(val, gat(x, j, n, BS_GATHER_XR)); };
     for (int ch = blockIdx.x * NWARP + warp; ch < a.ntr; ch += gridDim.x * NWARP) {
         const int4 dsc = a.rdesc[ch];
         const int lo = dsc.x, nseg = dsc.y - dsc.x, koff = dsc.z, nnz = dsc.w;
-        double ax[CPL];
+        A ax[CPL];
         int rows[CPL];
         if (nnz > WT) {  // one long row: the warp sums it
-            ax[0] = warp_long_dot(a.ridx, a.rval, koff, nnz, x, a.rpad, a.n, BS_GATHER_XR);
+            ax[0] = acc_from<A>(warp_long_dot(a.ridx, a.rval, koff, nnz, x, a.rpad, a.n, BS_GATHER_XR));
             rows[0] = (lane == 0) ? lo : -1;
 #pragma unroll
             for (int k = 1; k < CPL; ++k) rows[k] = -1;
@@ -547,27 +596,41 @@ __global__ void __launch_bounds__(NT) k_row_resid(const SweepArgs<T> a, const Re
             for (int k = 0; k < CPL; ++k) {
                 const int il = lane + 32 * k;
                 rows[k] = il < nseg ? lo + il : -1;
-                ax[k] = (il < nseg && ce[k] > cs[k]) ? to_double(s_end[warp][eslot(ce[k] - 1 - kb)]) : 0.0;
+                ax[k] = (il < nseg && ce[k] > cs[k]) ? s_end[warp][eslot(ce[k] - 1 - kb)] : A(0);
             }
             __syncwarp();
         }
 #pragma unroll
         for (int k = 0; k < CPL; ++k) {
             if (rows[k] < 0) continue;
-            const double bi = double(a.b[rows[k]]), res = ax[k] - bi;
-            if (r.write_all_s) r.r_buf[rows[k]] = res;
-            f[R_RES2] += res * res;
-            f[R_RESMAX] = fmax(f[R_RESMAX], fabs(res));
-            f[R_AXMAX] = fmax(f[R_AXMAX], fabs(ax[k]));
-            f[R_B2] += bi * bi;
-            f[R_BMAX] = fmax(f[R_BMAX], fabs(bi));
-            f[R_BLAM] += bi * double(a.lam[rows[k]]);
+            if constexpr (F32) {
+                const float bi = a.b[rows[k]];
+                const DF res = ax[k] + DF(-bi, 0.f);
+                if (r.write_all_s) r.r_buf[rows[k]] = to_double(res);
+                F[R_RES2] = F[R_RES2] + df_sq(res);
+                F[R_RESMAX] = df_max(F[R_RESMAX], df_abs(res));
+                F[R_AXMAX] = df_max(F[R_AXMAX], df_abs(ax[k]));
+                F[R_B2] = F[R_B2] + df_prod(bi, bi);
+                F[R_BMAX] = df_max(F[R_BMAX], DF(fabsf(bi), 0.f));
+                F[R_BLAM] = F[R_BLAM] + df_prod(bi, a.lam[rows[k]]);
+            } else {
+                const double axk = to_double(ax[k]);
+                const double bi = double(a.b[rows[k]]), res = axk - bi;
+                if (r.write_all_s) r.r_buf[rows[k]] = res;
+                f[R_RES2] += res * res;
+                f[R_RESMAX] = fmax(f[R_RESMAX], fabs(res));
+                f[R_AXMAX] = fmax(f[R_AXMAX], fabs(axk));
+                f[R_B2] += bi * bi;
+                f[R_BMAX] = fmax(f[R_BMAX], fabs(bi));
+                f[R_BLAM] += bi * double(a.lam[rows[k]]);
+            }
         }
     }
+    if constexpr (F32) fold_df_fields<NFR, true>(f, F);
     cta_fields_out<NFR, true>(f, s_red, r.part_row);
 }
 
-// FP64 column-side residual fields: with s = c + A^T lambda, ||s||, max|s|, max|A^T lambda|,
+// Column-side residual fields (reduced like the row side): with s = c + A^T lambda, ||s||, max|s|, max|A^T lambda|,
 // ||c||, max|c|, c^T x, ||x||, dist(s, K)^2 and dist(x, K)^2 (small cones fused; big cones get s
 // in s_buf for k_bigcone_resid). Persistent warps walk the column chunks.
 template <typename T, bool SOC>
@@ -577,19 +640,23 @@ __global__ void __launch_bounds__(NT) k_col_resid(const SweepArgs<T> a, const Re
     __shared__ double s_red[NWARP][NFC];
     __shared__ double s_cone[SOC ? NWARP : 1][2][WC];  // s and x of small-cone columns
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double f[NFC];
+    constexpr bool F32 = std::is_same<T, float>::value;
+    double f[NFC];  // FP64 path; for the FP32 iterate the Lorentz-cone terms only
+    DF F[F32 ? NFC : 1];
 #pragma unroll
     for (int k = 0; k < NFC; ++k) f[k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < (F32 ? NFC : 1); ++k) F[k] = DF(0);
     const T* __restrict__ lam = a.lam;
     const int m = a.m;
     auto prod = [lam, m](int i, T val, A (&p)[1]) { p[0] = acc_prod(val, gat(lam, i, m, BS_GATHER_L)); };
     for (int ch = blockIdx.x * NWARP + warp; ch < a.ntc; ch += gridDim.x * NWARP) {
         const int4 dsc = a.cdesc[ch];
         const int lo = dsc.x, nseg = dsc.y - dsc.x, koff = dsc.z, nnz = dsc.w;
-        double atl[CPL];
+        A atl[CPL];
         int cols[CPL];
         if (nnz > WT) {  // one long column: the warp sums it
-            atl[0] = warp_long_dot(a.cidx, a.cval, koff, nnz, lam, a.cpad, a.m, BS_GATHER_L);
+            atl[0] = acc_from<A>(warp_long_dot(a.cidx, a.cval, koff, nnz, lam, a.cpad, a.m, BS_GATHER_L));
             cols[0] = (lane == 0) ? 0 : -1;
 #pragma unroll
             for (int k = 1; k < CPL; ++k) cols[k] = -1;
@@ -610,7 +677,7 @@ __global__ void __launch_bounds__(NT) k_col_resid(const SweepArgs<T> a, const Re
             for (int k = 0; k < CPL; ++k) {
                 const int jl = lane + 32 * k;
                 cols[k] = jl < nseg ? jl : -1;
-                atl[k] = (jl < nseg && ce[k] > cs[k]) ? to_double(s_end[warp][eslot(ce[k] - 1 - kb)]) : 0.0;
+                atl[k] = (jl < nseg && ce[k] > cs[k]) ? s_end[warp][eslot(ce[k] - 1 - kb)] : A(0);
             }
             __syncwarp();
         }
@@ -619,26 +686,53 @@ __global__ void __launch_bounds__(NT) k_col_resid(const SweepArgs<T> a, const Re
             const int jl = cols[k];
             if (jl < 0) continue;
             const int j = lo + jl;
-            const double cj = double(a.c[j]), xj = double(a.x[j]);
-            const double s = cj + atl[k];
-            f[C_S2] += s * s;
-            f[C_SMAX] = fmax(f[C_SMAX], fabs(s));
-            f[C_ATLMAX] = fmax(f[C_ATLMAX], fabs(atl[k]));
-            f[C_C2] += cj * cj;
-            f[C_CMAX] = fmax(f[C_CMAX], fabs(cj));
-            f[C_CX] += cj * xj;
-            f[C_X2] += xj * xj;
-            f[C_XMAX] = fmax(f[C_XMAX], fabs(xj));
             const int tag = SOC ? cone_tag(a, j) : 0;
-            if (tag == 0) {
-                const double sn = s < 0.0 ? s : 0.0, xn = xj < 0.0 ? xj : 0.0;
-                f[C_SDIST2] += sn * sn;
-                f[C_XDIST2] += xn * xn;
-                f[C_SDMAX] = fmax(f[C_SDMAX], -sn);
-                f[C_XDMAX] = fmax(f[C_XDMAX], -xn);
-            } else if (tag == 1) {
-                s_cone[SOC ? warp : 0][0][jl] = s;
-                s_cone[SOC ? warp : 0][1][jl] = xj;
+            double s;  // written for the cone kernels only (FP32 iterate)
+            if constexpr (F32) {
+                const float cj = a.c[j], xj = a.x[j];
+                const DF sd = DF(cj, 0.f) + atl[k];
+                F[C_S2] = F[C_S2] + df_sq(sd);
+                F[C_SMAX] = df_max(F[C_SMAX], df_abs(sd));
+                F[C_ATLMAX] = df_max(F[C_ATLMAX], df_abs(atl[k]));
+                F[C_C2] = F[C_C2] + df_prod(cj, cj);
+                F[C_CMAX] = df_max(F[C_CMAX], DF(fabsf(cj), 0.f));
+                F[C_CX] = F[C_CX] + df_prod(cj, xj);
+                F[C_X2] = F[C_X2] + df_prod(xj, xj);
+                F[C_XMAX] = df_max(F[C_XMAX], DF(fabsf(xj), 0.f));
+                if (tag == 0) {
+                    const DF sn = sd.hi < 0.f ? sd : DF(0);
+                    const float xn = xj < 0.f ? xj : 0.f;
+                    F[C_SDIST2] = F[C_SDIST2] + df_sq(sn);
+                    F[C_XDIST2] = F[C_XDIST2] + df_prod(xn, xn);
+                    F[C_SDMAX] = df_max(F[C_SDMAX], df_neg(sn));
+                    F[C_XDMAX] = df_max(F[C_XDMAX], DF(-xn, 0.f));
+                }
+                s = (tag != 0 || r.write_all_s) ? to_double(sd) : 0.0;
+                if (tag == 1) {
+                    s_cone[SOC ? warp : 0][0][jl] = s;
+                    s_cone[SOC ? warp : 0][1][jl] = double(xj);
+                }
+            } else {
+                const double cj = double(a.c[j]), xj = double(a.x[j]);
+                s = cj + atl[k];
+                f[C_S2] += s * s;
+                f[C_SMAX] = fmax(f[C_SMAX], fabs(s));
+                f[C_ATLMAX] = fmax(f[C_ATLMAX], fabs(atl[k]));
+                f[C_C2] += cj * cj;
+                f[C_CMAX] = fmax(f[C_CMAX], fabs(cj));
+                f[C_CX] += cj * xj;
+                f[C_X2] += xj * xj;
+                f[C_XMAX] = fmax(f[C_XMAX], fabs(xj));
+                if (tag == 0) {
+                    const double sn = s < 0.0 ? s : 0.0, xn = xj < 0.0 ? xj : 0.0;
+                    f[C_SDIST2] += sn * sn;
+                    f[C_XDIST2] += xn * xn;
+                    f[C_SDMAX] = fmax(f[C_SDMAX], -sn);
+                    f[C_XDMAX] = fmax(f[C_XDMAX], -xn);
+                } else if (tag == 1) {
+                    s_cone[SOC ? warp : 0][0][jl] = s;
+                    s_cone[SOC ? warp : 0][1][jl] = xj;
+                }
             }
             if (tag == 2 || r.write_all_s) r.s_buf[j] = s;
         }
@@ -669,6 +763,7 @@ __global__ void __launch_bounds__(NT) k_col_resid(const SweepArgs<T> a, const Re
             __syncwarp();
         }
     }
+    if constexpr (F32) fold_df_fields<NFC, false>(f, F);
     cta_fields_out<NFC, false>(f, s_red, r.part_col);
 }
 

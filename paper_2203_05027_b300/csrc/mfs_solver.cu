@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -292,12 +293,14 @@ void build_orders(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const i
 // Greedy chunking of segments (columns or rows) in order. A unit is one segment, or a whole
 // small Lorentz cone (columns only). A chunk takes units while it stays within WT nonzeros and
 // WC segments; a single segment longer than WT forms a (long) chunk of its own.
-void build_chunks(const std::vector<int>& ptr, int nseg, const std::vector<int>* unit_end, Chunks& C) {
+// Greedy chunks of the segments [j0, j1) (whole units: a small Lorentz cone is one unit), with
+// padded offsets and chunk numbers counted from 0.
+void chunk_range(const std::vector<int>& ptr, int j0, int j1, const std::vector<int>* unit_end, Chunks& C) {
     C.desc.clear();
     C.heads.clear();
     C.longs.clear();
     C.padded = 0;
-    int start = 0, cur_seg = 0;
+    int start = j0, cur_seg = 0;
     int64_t cur_nnz = 0;
     auto close = [&](int at) {
         const int cn = ptr[at] - ptr[start];
@@ -319,8 +322,8 @@ void build_chunks(const std::vector<int>& ptr, int nseg, const std::vector<int>*
         cur_seg = 0;
         cur_nnz = 0;
     };
-    int j = 0;
-    while (j < nseg) {
+    int j = j0;
+    while (j < j1) {
         const int ue = unit_end ? (*unit_end)[j] : j + 1;
         const int useg = ue - j;
         const int64_t unnz = (int64_t)ptr[ue] - ptr[j];
@@ -330,7 +333,101 @@ void build_chunks(const std::vector<int>& ptr, int nseg, const std::vector<int>*
         j = ue;
         if (unnz > WT) close(j);
     }
-    if (cur_seg > 0) close(nseg);
+    if (cur_seg > 0) close(j1);
+}
+
+// Chunks of all segments: at most WT nonzeros and WC segments each (or one segment longer than
+// WT), greedy in segment order. The segments are cut into pieces of about 65,536 (at unit
+// boundaries; the cut depends on the data only, never on the thread count) whose chunks are found
+// independently, so a chunk never spans a piece boundary. `cones` lists the small Lorentz cones
+// as (first, one past last) in order; unit_end[j] is the end of the unit starting at j.
+struct ChunkJob {
+    const std::vector<int>* ptr;
+    int nseg;
+    const std::vector<int>* unit_end;
+    Chunks* out;
+    std::vector<int> cut;
+    std::vector<Chunks> part;
+};
+
+void plan_cuts(ChunkJob& J, const std::vector<std::pair<int, int>>& cones) {
+    constexpr int PIECE = 1 << 16;
+    J.cut.assign(1, 0);
+    for (int j = PIECE; j < J.nseg; j += PIECE) {
+        int at = j;
+        if (J.unit_end) {  // not inside a small cone
+            auto it = std::upper_bound(cones.begin(), cones.end(), std::make_pair(at, INT32_MAX));
+            if (it != cones.begin() && std::prev(it)->second > at && std::prev(it)->first < at) at = std::prev(it)->second;
+        }
+        if (at > J.cut.back() && at < J.nseg) J.cut.push_back(at);
+    }
+    J.cut.push_back(J.nseg);
+    J.part.assign(J.cut.size() - 1, Chunks());
+}
+
+// Concatenate a job's pieces: sizes and offsets first, then each piece copied by a pool thread.
+struct PieceAt {
+    size_t d, h, l;
+    int64_t padded;
+};
+
+std::vector<PieceAt> size_pieces(ChunkJob& J) {
+    Chunks& C = *J.out;
+    std::vector<PieceAt> at(J.part.size());
+    PieceAt run{0, 0, 0, 0};
+    for (size_t p = 0; p < J.part.size(); ++p) {
+        at[p] = run;
+        run.d += J.part[p].desc.size();
+        run.h += J.part[p].heads.size();
+        run.l += J.part[p].longs.size();
+        run.padded += J.part[p].padded;
+    }
+    C.desc.resize(run.d);
+    C.heads.resize(run.h);
+    C.longs.resize(run.l);
+    C.padded = run.padded;
+    return at;
+}
+
+void copy_piece(ChunkJob& J, const PieceAt& at, int p) {
+    Chunks& C = *J.out;
+    const Chunks& P = J.part[p];
+    const int c0 = (int)(at.d / 4);
+    for (size_t i = 0; i < P.desc.size(); i += 4) {
+        C.desc[at.d + i] = P.desc[i];
+        C.desc[at.d + i + 1] = P.desc[i + 1];
+        C.desc[at.d + i + 2] = (int)(P.desc[i + 2] + at.padded);
+        C.desc[at.d + i + 3] = P.desc[i + 3];
+    }
+    std::copy(P.heads.begin(), P.heads.end(), C.heads.begin() + at.h);
+    for (size_t i = 0; i < P.longs.size(); ++i) C.longs[at.l + i] = P.longs[i] + c0;
+}
+
+// The chunks of several orders at once: all their pieces on one pool of threads.
+void build_chunks(std::vector<ChunkJob>& jobs, const std::vector<std::pair<int, int>>& cones) {
+    std::vector<std::pair<int, int>> work;  // (job, piece)
+    int64_t total = 0;
+    for (int q = 0; q < (int)jobs.size(); ++q) {
+        plan_cuts(jobs[q], cones);
+        for (int p = 0; p + 1 < (int)jobs[q].cut.size(); ++p) work.push_back({q, p});
+        total += (int64_t)(*jobs[q].ptr)[jobs[q].nseg] + jobs[q].nseg;
+    }
+    const int nt = std::max(1, std::min((int)work.size(), mfs::host::threads_for(total)));
+    std::atomic<int> next{0};
+    mfs::host::parallel_tasks(nt, [&](int) {
+        for (int w = next++; w < (int)work.size(); w = next++) {
+            ChunkJob& J = jobs[work[w].first];
+            const int p = work[w].second;
+            chunk_range(*J.ptr, J.cut[p], J.cut[p + 1], J.unit_end, J.part[p]);
+        }
+    });
+    std::vector<std::vector<PieceAt>> at;
+    for (ChunkJob& J : jobs) at.push_back(size_pieces(J));
+    next = 0;
+    mfs::host::parallel_tasks(nt, [&](int) {
+        for (int w = next++; w < (int)work.size(); w = next++)
+            copy_piece(jobs[work[w].first], at[work[w].first][work[w].second], work[w].second);
+    });
 }
 
 inline int float_bits(float f) {
@@ -503,6 +600,91 @@ mfs_status device_scan(mfs_solver* s, const int* in, int* out, int64_t n, int* t
 // Device set-up (mfs_setup.cuh): upload the COO, check it, and if it is valid and in column order
 // (duplicates next to each other) build both orders on the GPU, leaving P.dev.on set and P.col_ptr, P.row_ptr, P.o on the host.
 // An input out of order leaves P.dev.on unset (the host orders it); an invalid one fails.
+// Host-to-device copies of large pageable arrays through pinned staging buffers: each of up to 8
+// host threads takes its slice of every array and fills its two 4 MB buffers in turn while the copy
+// engine drains the other on the thread's own stream; `st` then waits for all of them. The buffers
+// and streams belong to the process (one set, for the device that first used it, taken under a
+// lock); any other device, or a failure to set them up, gets plain copies.
+struct PinnedStaging {
+    std::mutex mu;
+    int device = -1;  // -2: unavailable
+    int nt = 0;
+    static constexpr size_t SUB = size_t(4) << 20;
+    std::vector<char*> buf;         // 2 per thread
+    std::vector<cudaStream_t> str;  // 1 per thread
+    std::vector<cudaEvent_t> ev;    // 2 per thread, + 1 per thread marking its last copy
+};
+static PinnedStaging g_pin;
+
+struct HostCopy {
+    void* dst;
+    const void* src;
+    size_t bytes;
+};
+
+static bool pinned_ready(int device) {
+    if (g_pin.device == device) return true;
+    if (g_pin.device != -1) return false;
+    g_pin.device = -2;
+    const unsigned h = std::thread::hardware_concurrency();
+    const int nt = (int)std::max(1u, std::min(h ? h : 1u, 8u));
+    for (int t = 0; t < nt; ++t) {
+        cudaStream_t q = nullptr;
+        if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess) return false;
+        g_pin.str.push_back(q);
+        for (int k = 0; k < 3; ++k) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
+            g_pin.ev.push_back(e);
+        }
+        for (int k = 0; k < 2; ++k) {
+            void* b = nullptr;
+            if (cudaHostAlloc(&b, PinnedStaging::SUB, cudaHostAllocDefault) != cudaSuccess) return false;
+            g_pin.buf.push_back(static_cast<char*>(b));
+        }
+    }
+    g_pin.nt = nt;
+    g_pin.device = device;
+    return true;
+}
+
+mfs_status upload_pinned(mfs_solver* s, const std::vector<HostCopy>& copies, cudaStream_t st) {
+    std::lock_guard<std::mutex> lock(g_pin.mu);
+    if (!pinned_ready(s->device)) {
+        cudaGetLastError();  // a failed set-up leaves nothing behind; copy directly
+        for (const HostCopy& c : copies)
+            CUDA_TRY(s, cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, st));
+        return MFS_OK;
+    }
+    const int T = g_pin.nt;
+    std::vector<cudaError_t> err(T, cudaSuccess);
+    mfs::host::parallel_tasks(T, [&](int t) {
+        cudaError_t e = cudaSetDevice(s->device);
+        int k = 0;
+        for (const HostCopy& c : copies) {
+            const size_t lo = c.bytes * t / T, hi = c.bytes * (t + 1) / T;
+            for (size_t off = lo; off < hi && e == cudaSuccess; off += PinnedStaging::SUB) {
+                const size_t len = std::min(PinnedStaging::SUB, hi - off);
+                const int b = 2 * t + (k & 1);
+                if (k >= 2) e = cudaEventSynchronize(g_pin.ev[3 * t + (k & 1)]);  // its previous copy is done
+                if (e != cudaSuccess) break;
+                std::memcpy(g_pin.buf[b], static_cast<const char*>(c.src) + off, len);
+                e = cudaMemcpyAsync(static_cast<char*>(c.dst) + off, g_pin.buf[b], len, cudaMemcpyHostToDevice,
+                                    g_pin.str[t]);
+                if (e == cudaSuccess) e = cudaEventRecord(g_pin.ev[3 * t + (k & 1)], g_pin.str[t]);
+                ++k;
+            }
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(g_pin.ev[3 * t + 2], g_pin.str[t]);
+        err[t] = e;
+    });
+    for (int t = 0; t < T; ++t) CUDA_TRY(s, err[t]);
+    for (int t = 0; t < T; ++t) CUDA_TRY(s, cudaStreamWaitEvent(st, g_pin.ev[3 * t + 2], 0));
+    // the buffers are reused by the next upload: let these copies finish first
+    for (int t = 0; t < T; ++t) CUDA_TRY(s, cudaEventSynchronize(g_pin.ev[3 * t + 2]));
+    return MFS_OK;
+}
+
 mfs_status device_orders(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
                          const double* val, HostProblem& P) {
     namespace su = mfs::setup;
@@ -526,9 +708,8 @@ mfs_status device_orders(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const
     TRY(grab((void**)&d_val, nnz * sizeof(double)));
     TRY(grab((void**)&d_bad, 2 * sizeof(unsigned long long) + 2 * sizeof(int)));
     d_flags = reinterpret_cast<int*>(d_bad + 2);
-    CUDA_TRY(s, cudaMemcpyAsync(d_row, row, nnz * sizeof(long long), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(s, cudaMemcpyAsync(d_col, col, nnz * sizeof(long long), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(s, cudaMemcpyAsync(d_val, val, nnz * sizeof(double), cudaMemcpyHostToDevice, st));
+    TRY(upload_pinned(s, {{d_row, row, nnz * sizeof(long long)}, {d_col, col, nnz * sizeof(long long)},
+                          {d_val, val, nnz * sizeof(double)}}, st));
     {
         unsigned long long init[2] = {(unsigned long long)nnz, (unsigned long long)nnz};
         CUDA_TRY(s, cudaMemcpyAsync(d_bad, init, sizeof init, cudaMemcpyHostToDevice, st));
@@ -608,12 +789,21 @@ mfs_status setup_host(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const in
         }
         off += sz;
     }
-    mfs::host::parallel_tasks(2, [&](int t) {
-        if (t == 0)
-            build_chunks(P.col_ptr, (int)n, &unit_end, P.cc);
-        else
-            build_chunks(P.row_ptr, (int)m, nullptr, P.rc);
-    });
+    {
+        std::vector<std::pair<int, int>> small;  // small Lorentz cones, in order
+        for (size_t q = 0; q < P.soc_start.size(); ++q)
+            if (!P.soc_big[q]) small.push_back({P.soc_start[q], P.soc_start[q] + P.soc_size[q]});
+        std::vector<ChunkJob> jobs(2);
+        jobs[0].ptr = &P.col_ptr;
+        jobs[0].nseg = (int)n;
+        jobs[0].unit_end = &unit_end;
+        jobs[0].out = &P.cc;
+        jobs[1].ptr = &P.row_ptr;
+        jobs[1].nseg = (int)m;
+        jobs[1].unit_end = nullptr;
+        jobs[1].out = &P.rc;
+        build_chunks(jobs, small);
+    }
     if (P.cc.padded >= INT32_MAX - PAD || P.rc.padded >= INT32_MAX - PAD)
         return fail(s, MFS_ERR_INVALID, "too many nonzeros after padding (limit 2^31)");
     // Lorentz cones intersecting each column chunk

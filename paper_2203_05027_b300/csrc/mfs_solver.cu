@@ -613,6 +613,7 @@ struct PinnedStaging {
     std::vector<char*> buf;         // 2 per thread
     std::vector<cudaStream_t> str;  // 1 per thread
     std::vector<cudaEvent_t> ev;    // 2 per thread, + 1 per thread marking its last copy
+    cudaEvent_t ready = nullptr;    // downloads: the source is complete on the caller's stream
 };
 static PinnedStaging g_pin;
 
@@ -643,6 +644,7 @@ static bool pinned_ready(int device) {
             g_pin.buf.push_back(static_cast<char*>(b));
         }
     }
+    if (cudaEventCreateWithFlags(&g_pin.ready, cudaEventDisableTiming) != cudaSuccess) return false;
     g_pin.nt = nt;
     g_pin.device = device;
     return true;
@@ -682,6 +684,52 @@ mfs_status upload_pinned(mfs_solver* s, const std::vector<HostCopy>& copies, cud
     for (int t = 0; t < T; ++t) CUDA_TRY(s, cudaStreamWaitEvent(st, g_pin.ev[3 * t + 2], 0));
     // the buffers are reused by the next upload: let these copies finish first
     for (int t = 0; t < T; ++t) CUDA_TRY(s, cudaEventSynchronize(g_pin.ev[3 * t + 2]));
+    return MFS_OK;
+}
+
+// Device-to-host copies into pageable arrays, the reverse of upload_pinned: each thread issues the
+// copy of its next piece into one of its buffers while it moves the previous piece out of the other.
+// Returns when every byte has reached the host.
+mfs_status download_pinned(mfs_solver* s, const std::vector<HostCopy>& copies, cudaStream_t st) {
+    std::lock_guard<std::mutex> lock(g_pin.mu);
+    if (!pinned_ready(s->device)) {
+        cudaGetLastError();
+        for (const HostCopy& c : copies)
+            CUDA_TRY(s, cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(s, cudaStreamSynchronize(st));
+        return MFS_OK;
+    }
+    CUDA_TRY(s, cudaEventRecord(g_pin.ready, st));
+    const int T = g_pin.nt;
+    std::vector<cudaError_t> err(T, cudaSuccess);
+    mfs::host::parallel_tasks(T, [&](int t) {
+        cudaError_t e = cudaSetDevice(s->device);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(g_pin.str[t], g_pin.ready, 0);
+        char* pend = nullptr;  // host destination of the piece in flight in buffer (k - 1) & 1
+        size_t plen = 0;
+        int k = 0;
+        auto drain = [&](int kk) {  // move piece kk (already issued) out of its buffer
+            if (e == cudaSuccess) e = cudaEventSynchronize(g_pin.ev[3 * t + (kk & 1)]);
+            if (e == cudaSuccess) std::memcpy(pend, g_pin.buf[2 * t + (kk & 1)], plen);
+        };
+        for (const HostCopy& c : copies) {
+            const size_t lo = c.bytes * t / T, hi = c.bytes * (t + 1) / T;
+            for (size_t off = lo; off < hi && e == cudaSuccess; off += PinnedStaging::SUB) {
+                const size_t len = std::min(PinnedStaging::SUB, hi - off);
+                const int b = 2 * t + (k & 1);
+                e = cudaMemcpyAsync(g_pin.buf[b], static_cast<const char*>(c.src) + off, len, cudaMemcpyDeviceToHost,
+                                    g_pin.str[t]);
+                if (e == cudaSuccess) e = cudaEventRecord(g_pin.ev[3 * t + (k & 1)], g_pin.str[t]);
+                if (k >= 1) drain(k - 1);
+                pend = static_cast<char*>(c.dst) + off;
+                plen = len;
+                ++k;
+            }
+        }
+        if (k >= 1) drain(k - 1);
+        err[t] = e;
+    });
+    for (int t = 0; t < T; ++t) CUDA_TRY(s, err[t]);
     return MFS_OK;
 }
 
@@ -1395,17 +1443,21 @@ static mfs_status get_solution_t(mfs_solver* s, State<T>& st, double* x, double*
     const T* src[4] = {st.x, st.lam, st.z, st.del};
     const int64_t cnt[4] = {n, m, n, n};
     int64_t off = 0;
+    std::vector<HostCopy> down;
     for (int q = 0; q < 4; ++q) {
         if (!dst[q] || !cnt[q]) continue;
         double* d = host ? tmp + off : dst[q];
         convert(d, src[q], cnt[q], s->stream);
-        if (host) cudaMemcpyAsync(dst[q], d, cnt[q] * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+        if (host) down.push_back({dst[q], d, (size_t)cnt[q] * sizeof(double)});
         off += cnt[q];
     }
+    CUDA_TRY(s, cudaGetLastError());
+    mfs_status r = MFS_OK;
+    if (host) r = download_pinned(s, down, s->stream);
     if (tmp) cudaFreeAsync(tmp, s->stream);
     CUDA_TRY(s, cudaGetLastError());
     CUDA_TRY(s, cudaStreamSynchronize(s->stream));
-    return MFS_OK;
+    return r;
 }
 
 template <typename T>

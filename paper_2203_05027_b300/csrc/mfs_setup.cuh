@@ -109,8 +109,9 @@ __global__ void __launch_bounds__(NT) k_scan_add(int* __restrict__ out, const in
 
 // ------------------------------------------------------------------------------------ COO input
 // First entry with an index out of range, first non-finite value (atomic minima; nnz if none), and
-// whether some entry comes before its predecessor in (column, row) order.
-__global__ void k_check(const long long* __restrict__ row, const long long* __restrict__ col,
+// whether some entry comes before its predecessor in (column, row) order. The indices arrive as
+// int32, narrowed on the host after their own range check there.
+__global__ void k_check(const int* __restrict__ row, const int* __restrict__ col,
                         const double* __restrict__ val, long long nnz, long long m, long long n,
                         unsigned long long* bad_idx, unsigned long long* bad_val, int* unsorted) {
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nnz; q += (long long)gridDim.x * blockDim.x) {
@@ -126,7 +127,7 @@ __global__ void k_check(const long long* __restrict__ row, const long long* __re
 
 // In column order (duplicates allowed): keep[q] = 1 where a run of equal (column, row) starts and
 // its values sum to a nonzero, sum[q] = that sum (in entry order).
-__global__ void k_runs(const long long* __restrict__ row, const long long* __restrict__ col,
+__global__ void k_runs(const int* __restrict__ row, const int* __restrict__ col,
                        const double* __restrict__ val, long long nnz, int* __restrict__ keep, double* __restrict__ sum) {
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nnz; q += (long long)gridDim.x * blockDim.x) {
         const long long r = row[q], c = col[q];
@@ -142,7 +143,7 @@ __global__ void k_runs(const long long* __restrict__ row, const long long* __res
     }
 }
 
-__global__ void k_compact(const long long* __restrict__ row, const long long* __restrict__ col,
+__global__ void k_compact(const int* __restrict__ row, const int* __restrict__ col,
                           const int* __restrict__ keep, const int* __restrict__ pos, const double* __restrict__ sum,
                           long long nnz, int* __restrict__ crow, int* __restrict__ ccol, double* __restrict__ cval) {
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nnz; q += (long long)gridDim.x * blockDim.x)

@@ -600,16 +600,18 @@ mfs_status device_scan(mfs_solver* s, const int* in, int* out, int64_t n, int* t
 // Device set-up (mfs_setup.cuh): upload the COO, check it, and if it is valid and in column order
 // (duplicates next to each other) build both orders on the GPU, leaving P.dev.on set and P.col_ptr, P.row_ptr, P.o on the host.
 // An input out of order leaves P.dev.on unset (the host orders it); an invalid one fails.
-// Host-to-device copies of large pageable arrays through pinned staging buffers: each of up to 8
-// host threads takes its slice of every array and fills its two 4 MB buffers in turn while the copy
-// engine drains the other on the thread's own stream; `st` then waits for all of them. The buffers
-// and streams belong to the process (one set, for the device that first used it, taken under a
-// lock); any other device, or a failure to set them up, gets plain copies.
+// Host-to-device copies of large pageable arrays through pinned staging buffers: each of up to 16
+// host threads takes its slice of every array and fills its two 2 MB buffers in turn while the copy
+// engine drains the other on the thread's own stream; `st` then waits for all of them. An array of
+// int64 indices with a limit is narrowed to int32 on the way, each index checked against
+// [0, limit) first. The buffers and streams belong to the process (one set, for the device that
+// first used it, taken under a lock); any other device, or a failure to set them up, gets copies
+// from pageable memory.
 struct PinnedStaging {
     std::mutex mu;
     int device = -1;  // -2: unavailable
     int nt = 0;
-    static constexpr size_t SUB = size_t(4) << 20;
+    static constexpr size_t SUB = size_t(2) << 20;
     std::vector<char*> buf;         // 2 per thread
     std::vector<cudaStream_t> str;  // 1 per thread
     std::vector<cudaEvent_t> ev;    // 2 per thread, + 1 per thread marking its last copy
@@ -620,15 +622,30 @@ static PinnedStaging g_pin;
 struct HostCopy {
     void* dst;
     const void* src;
-    size_t bytes;
+    size_t bytes;      // at the source
+    int64_t lim = 0;   // > 0: src holds bytes / 8 int64 indices, sent as int32, each checked against [0, lim)
 };
+
+// Narrow n int64 indices to int32; returns the position of the first outside [0, lim), or n.
+inline size_t narrow_indices(const int64_t* src, int32_t* dst, size_t n, int64_t lim) {
+    uint64_t mx = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const uint64_t v = (uint64_t)src[i];  // a negative index becomes huge
+        mx = v > mx ? v : mx;
+        dst[i] = (int32_t)src[i];
+    }
+    if (mx < (uint64_t)lim) return n;
+    for (size_t i = 0; i < n; ++i)
+        if ((uint64_t)src[i] >= (uint64_t)lim) return i;
+    return n;
+}
 
 static bool pinned_ready(int device) {
     if (g_pin.device == device) return true;
     if (g_pin.device != -1) return false;
     g_pin.device = -2;
     const unsigned h = std::thread::hardware_concurrency();
-    const int nt = (int)std::max(1u, std::min(h ? h : 1u, 8u));
+    const int nt = (int)std::max(1u, std::min(h ? h : 1u, 16u));
     for (int t = 0; t < nt; ++t) {
         cudaStream_t q = nullptr;
         if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess) return false;
@@ -638,41 +655,63 @@ static bool pinned_ready(int device) {
             if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
             g_pin.ev.push_back(e);
         }
-        for (int k = 0; k < 2; ++k) {
-            void* b = nullptr;
-            if (cudaHostAlloc(&b, PinnedStaging::SUB, cudaHostAllocDefault) != cudaSuccess) return false;
-            g_pin.buf.push_back(static_cast<char*>(b));
-        }
     }
+    void* block = nullptr;  // one pinned allocation, cut into two buffers per thread
+    if (cudaHostAlloc(&block, 2 * (size_t)nt * PinnedStaging::SUB, cudaHostAllocDefault) != cudaSuccess) return false;
+    for (int b = 0; b < 2 * nt; ++b) g_pin.buf.push_back(static_cast<char*>(block) + b * PinnedStaging::SUB);
     if (cudaEventCreateWithFlags(&g_pin.ready, cudaEventDisableTiming) != cudaSuccess) return false;
     g_pin.nt = nt;
     g_pin.device = device;
     return true;
 }
 
-mfs_status upload_pinned(mfs_solver* s, const std::vector<HostCopy>& copies, cudaStream_t st) {
+// *first_bad: the first position (in any index array) with an index out of range, or SIZE_MAX.
+mfs_status upload_pinned(mfs_solver* s, const std::vector<HostCopy>& copies, cudaStream_t st, size_t* first_bad) {
     std::lock_guard<std::mutex> lock(g_pin.mu);
+    *first_bad = SIZE_MAX;
     if (!pinned_ready(s->device)) {
-        cudaGetLastError();  // a failed set-up leaves nothing behind; copy directly
-        for (const HostCopy& c : copies)
-            CUDA_TRY(s, cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, st));
+        cudaGetLastError();  // a failed set-up leaves nothing behind; copy from pageable memory
+        for (const HostCopy& c : copies) {
+            if (c.lim > 0) {
+                const size_t n = c.bytes / 8;
+                std::vector<int32_t> tmp(n);
+                const size_t bad = narrow_indices(static_cast<const int64_t*>(c.src), tmp.data(), n, c.lim);
+                if (bad < n) *first_bad = std::min(*first_bad, bad);
+                CUDA_TRY(s, cudaMemcpyAsync(c.dst, tmp.data(), n * 4, cudaMemcpyHostToDevice, st));
+                CUDA_TRY(s, cudaStreamSynchronize(st));  // tmp goes out of scope
+            } else {
+                CUDA_TRY(s, cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, st));
+            }
+        }
         return MFS_OK;
     }
     const int T = g_pin.nt;
     std::vector<cudaError_t> err(T, cudaSuccess);
+    std::vector<size_t> bad(T, SIZE_MAX);
     mfs::host::parallel_tasks(T, [&](int t) {
         cudaError_t e = cudaSetDevice(s->device);
         int k = 0;
         for (const HostCopy& c : copies) {
-            const size_t lo = c.bytes * t / T, hi = c.bytes * (t + 1) / T;
-            for (size_t off = lo; off < hi && e == cudaSuccess; off += PinnedStaging::SUB) {
-                const size_t len = std::min(PinnedStaging::SUB, hi - off);
+            const bool idx = c.lim > 0;
+            const size_t nel = idx ? c.bytes / 8 : c.bytes;  // elements (bytes for a plain copy)
+            const size_t per = idx ? PinnedStaging::SUB / 4 : PinnedStaging::SUB;
+            const size_t lo = nel * t / T, hi = nel * (t + 1) / T;
+            for (size_t off = lo; off < hi && e == cudaSuccess; off += per) {
+                const size_t len = std::min(per, hi - off);
                 const int b = 2 * t + (k & 1);
                 if (k >= 2) e = cudaEventSynchronize(g_pin.ev[3 * t + (k & 1)]);  // its previous copy is done
                 if (e != cudaSuccess) break;
-                std::memcpy(g_pin.buf[b], static_cast<const char*>(c.src) + off, len);
-                e = cudaMemcpyAsync(static_cast<char*>(c.dst) + off, g_pin.buf[b], len, cudaMemcpyHostToDevice,
-                                    g_pin.str[t]);
+                if (idx) {
+                    int32_t* bp = reinterpret_cast<int32_t*>(g_pin.buf[b]);
+                    const size_t q = narrow_indices(static_cast<const int64_t*>(c.src) + off, bp, len, c.lim);
+                    if (q < len) bad[t] = std::min(bad[t], off + q);
+                    e = cudaMemcpyAsync(static_cast<int32_t*>(c.dst) + off, bp, len * 4, cudaMemcpyHostToDevice,
+                                        g_pin.str[t]);
+                } else {
+                    std::memcpy(g_pin.buf[b], static_cast<const char*>(c.src) + off, len);
+                    e = cudaMemcpyAsync(static_cast<char*>(c.dst) + off, g_pin.buf[b], len, cudaMemcpyHostToDevice,
+                                        g_pin.str[t]);
+                }
                 if (e == cudaSuccess) e = cudaEventRecord(g_pin.ev[3 * t + (k & 1)], g_pin.str[t]);
                 ++k;
             }
@@ -681,6 +720,7 @@ mfs_status upload_pinned(mfs_solver* s, const std::vector<HostCopy>& copies, cud
         err[t] = e;
     });
     for (int t = 0; t < T; ++t) CUDA_TRY(s, err[t]);
+    for (int t = 0; t < T; ++t) *first_bad = std::min(*first_bad, bad[t]);
     for (int t = 0; t < T; ++t) CUDA_TRY(s, cudaStreamWaitEvent(st, g_pin.ev[3 * t + 2], 0));
     // the buffers are reused by the next upload: let these copies finish first
     for (int t = 0; t < T; ++t) CUDA_TRY(s, cudaEventSynchronize(g_pin.ev[3 * t + 2]));
@@ -747,17 +787,18 @@ mfs_status device_orders(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const
     };
     cudaStream_t st = s->stream;
     const int grid = 8 * s->num_sms;
-    long long *d_row = nullptr, *d_col = nullptr;
+    int *d_row = nullptr, *d_col = nullptr;
     double *d_val = nullptr, *d_sum = nullptr;
     int *d_keep = nullptr, *d_pos = nullptr, *d_flags = nullptr;
     unsigned long long* d_bad = nullptr;
-    TRY(grab((void**)&d_row, nnz * sizeof(long long)));
-    TRY(grab((void**)&d_col, nnz * sizeof(long long)));
+    TRY(grab((void**)&d_row, nnz * sizeof(int)));
+    TRY(grab((void**)&d_col, nnz * sizeof(int)));
     TRY(grab((void**)&d_val, nnz * sizeof(double)));
     TRY(grab((void**)&d_bad, 2 * sizeof(unsigned long long) + 2 * sizeof(int)));
     d_flags = reinterpret_cast<int*>(d_bad + 2);
-    TRY(upload_pinned(s, {{d_row, row, nnz * sizeof(long long)}, {d_col, col, nnz * sizeof(long long)},
-                          {d_val, val, nnz * sizeof(double)}}, st));
+    size_t bad_host = SIZE_MAX;  // first entry with an index out of range, found while narrowing
+    TRY(upload_pinned(s, {{d_row, row, nnz * sizeof(int64_t), m}, {d_col, col, nnz * sizeof(int64_t), n},
+                          {d_val, val, nnz * sizeof(double)}}, st, &bad_host));
     {
         unsigned long long init[2] = {(unsigned long long)nnz, (unsigned long long)nnz};
         CUDA_TRY(s, cudaMemcpyAsync(d_bad, init, sizeof init, cudaMemcpyHostToDevice, st));
@@ -768,7 +809,7 @@ mfs_status device_orders(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const
         CUDA_TRY(s, cudaMemcpyAsync(bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(s, cudaMemcpyAsync(flags, d_flags, sizeof flags, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(s, cudaStreamSynchronize(st));
-        const int64_t bi = (int64_t)bad[0], bv = (int64_t)bad[1];
+        const int64_t bi = std::min((int64_t)bad[0], bad_host < (size_t)nnz ? (int64_t)bad_host : nnz), bv = (int64_t)bad[1];
         if (bi < nnz && bi <= bv)
             return fail(s, MFS_ERR_INVALID, "COO index out of range at entry " + std::to_string(bi));
         if (bv < nnz) return fail(s, MFS_ERR_INVALID, "non-finite value in A");

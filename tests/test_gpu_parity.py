@@ -366,3 +366,39 @@ def test_sorted_coo_with_adjacent_duplicates_and_cancelling_pairs(m, n):
     orc, s = run_pair(prob, 40, "fp64")
     compare(s.solution(), orc.state(), TOL["fp64"], "sorted COO with duplicates")
     assert s.info()["o"] == oracle.make_oracle(prob).uv()[0].size < k
+
+
+@pytest.mark.parametrize("case", ["row_high", "col_negative", "row_wraps_to_valid_int32", "nan_value",
+                                  "nan_before_bad_index", "bad_index_before_nan"])
+def test_invalid_large_coo_rejected_by_gpu_setup(case):
+    """A COO list in column order with at least 2^16 nonzeros is checked and ordered on the GPU (the
+    indices narrowed to int32 on the host on the way): the first bad entry is reported, and an
+    index beyond int32 that would narrow to a valid one is rejected too."""
+    prob = I.large_lp(0, m=20_000, n=50_000)
+    assert prob["row"].size >= 1 << 16
+    row, col, val = prob["row"].copy(), prob["col"].copy(), prob["val"].copy()
+    q1, q2 = 70_001, 90_001
+    if case == "row_high":
+        row[q1] = prob["m"]
+    elif case == "col_negative":
+        col[q1] = -3
+    elif case == "row_wraps_to_valid_int32":
+        row[q1] = (1 << 32) + 5
+    elif case == "nan_value":
+        val[q1] = np.nan
+    elif case == "nan_before_bad_index":
+        val[q1] = np.nan
+        row[q2] = -1
+    else:
+        row[q1] = -1
+        val[q2] = np.inf
+    bad = dict(prob, row=row, col=col, val=val)
+    with pytest.raises(mfs.MfsError) as e:
+        mfs.Solver(bad, precision="fp32")
+    assert e.value.status == mfs.MFS_ERR_INVALID
+    if case in ("nan_value", "nan_before_bad_index"):
+        assert "non-finite" in str(e.value)
+    else:
+        assert f"out of range at entry {q1}" in str(e.value)
+    ok = mfs.Solver(prob, precision="fp32")     # the pinned staging is free again afterwards
+    assert ok.info()["o"] == prob["row"].size

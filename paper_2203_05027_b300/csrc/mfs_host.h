@@ -6,6 +6,8 @@
 #include <sys/mman.h>
 
 #include <algorithm>
+#include <climits>
+#include <atomic>
 #include <cstdint>
 #include <cstdlib>
 #include <memory>
@@ -179,6 +181,159 @@ void counting_sort(int64_t n, int64_t k, Key key, const int64_t* items, int64_t*
         for (int64_t q = lo; q < hi; ++q) out[p[key(q)]++] = items ? items[q] : q;
     });
     if (starts) starts->assign(total.begin(), total.end());
+}
+
+// One order (columns or rows) of A, chunked for the warp kernels.
+struct Chunks {
+    std::vector<int> desc;      // 4 ints per chunk: first segment, one past last, padded offset, nnz
+    std::vector<uint32_t> heads;  // 8 words per chunk: bit e set if a non-empty segment starts at item e
+    std::vector<int> longs;     // chunks with more nonzeros than the limit
+    int64_t padded = 0;         // length of the padded nonzero arrays
+    int count() const { return (int)desc.size() / 4; }
+};
+
+// Limits of one chunk: nonzeros (a longer single segment makes a chunk of its own), segments,
+// and the padding of each chunk's start in the padded nonzero arrays.
+struct ChunkLimits {
+    int wt, wc, pad;
+};
+
+// Greedy chunks of the segments [j0, j1) (whole units: a small Lorentz cone is one unit), with
+// padded offsets and chunk numbers counted from 0.
+inline void chunk_range(const std::vector<int>& ptr, int j0, int j1, const std::vector<int>* unit_end, const ChunkLimits& L,
+                        Chunks& C) {
+    C.desc.clear();
+    C.heads.clear();
+    C.longs.clear();
+    C.padded = 0;
+    int start = j0, cur_seg = 0;
+    int64_t cur_nnz = 0;
+    auto close = [&](int at) {
+        const int cn = ptr[at] - ptr[start];
+        if (cn > L.wt) C.longs.push_back(C.count());
+        const size_t h0 = C.heads.size();
+        C.heads.resize(h0 + 8, 0u);
+        if (cn <= L.wt)
+            for (int q = start; q < at; ++q)
+                if (ptr[q + 1] > ptr[q]) {
+                    const int e = ptr[q] - ptr[start];
+                    C.heads[h0 + (e >> 5)] |= 1u << (e & 31);
+                }
+        C.desc.push_back(start);
+        C.desc.push_back(at);
+        C.desc.push_back((int)C.padded);
+        C.desc.push_back(cn);
+        C.padded += (cn + L.pad - 1) / L.pad * L.pad;
+        start = at;
+        cur_seg = 0;
+        cur_nnz = 0;
+    };
+    int j = j0;
+    while (j < j1) {
+        const int ue = unit_end ? (*unit_end)[j] : j + 1;
+        const int useg = ue - j;
+        const int64_t unnz = (int64_t)ptr[ue] - ptr[j];
+        if (cur_seg > 0 && (cur_nnz + unnz > L.wt || cur_seg + useg > L.wc)) close(j);
+        cur_seg += useg;
+        cur_nnz += unnz;
+        j = ue;
+        if (unnz > L.wt) close(j);
+    }
+    if (cur_seg > 0) close(j1);
+}
+
+// Chunks of all segments: at most L.wt nonzeros and L.wc segments each (or one segment longer than
+// L.wt), greedy in segment order. The segments are cut into pieces of about 65,536 (at unit
+// boundaries; the cut depends on the data only, never on the thread count) whose chunks are found
+// independently, so a chunk never spans a piece boundary. `cones` lists the small Lorentz cones
+// as (first, one past last) in order; unit_end[j] is the end of the unit starting at j.
+struct ChunkJob {
+    const std::vector<int>* ptr;
+    int nseg;
+    const std::vector<int>* unit_end;
+    Chunks* out;
+    std::vector<int> cut;
+    std::vector<Chunks> part;
+};
+
+inline void plan_cuts(ChunkJob& J, const std::vector<std::pair<int, int>>& cones) {
+    constexpr int PIECE = 1 << 16;
+    J.cut.assign(1, 0);
+    for (int j = PIECE; j < J.nseg; j += PIECE) {
+        int at = j;
+        if (J.unit_end) {  // not inside a small cone
+            auto it = std::upper_bound(cones.begin(), cones.end(), std::make_pair(at, INT32_MAX));
+            if (it != cones.begin() && std::prev(it)->second > at && std::prev(it)->first < at) at = std::prev(it)->second;
+        }
+        if (at > J.cut.back() && at < J.nseg) J.cut.push_back(at);
+    }
+    J.cut.push_back(J.nseg);
+    J.part.assign(J.cut.size() - 1, Chunks());
+}
+
+// Concatenate a job's pieces: sizes and offsets first, then each piece copied by a pool thread.
+struct PieceAt {
+    size_t d, h, l;
+    int64_t padded;
+};
+
+inline std::vector<PieceAt> size_pieces(ChunkJob& J) {
+    Chunks& C = *J.out;
+    std::vector<PieceAt> at(J.part.size());
+    PieceAt run{0, 0, 0, 0};
+    for (size_t p = 0; p < J.part.size(); ++p) {
+        at[p] = run;
+        run.d += J.part[p].desc.size();
+        run.h += J.part[p].heads.size();
+        run.l += J.part[p].longs.size();
+        run.padded += J.part[p].padded;
+    }
+    C.desc.resize(run.d);
+    C.heads.resize(run.h);
+    C.longs.resize(run.l);
+    C.padded = run.padded;
+    return at;
+}
+
+inline void copy_piece(ChunkJob& J, const PieceAt& at, int p) {
+    Chunks& C = *J.out;
+    const Chunks& P = J.part[p];
+    const int c0 = (int)(at.d / 4);
+    for (size_t i = 0; i < P.desc.size(); i += 4) {
+        C.desc[at.d + i] = P.desc[i];
+        C.desc[at.d + i + 1] = P.desc[i + 1];
+        C.desc[at.d + i + 2] = (int)(P.desc[i + 2] + at.padded);
+        C.desc[at.d + i + 3] = P.desc[i + 3];
+    }
+    std::copy(P.heads.begin(), P.heads.end(), C.heads.begin() + at.h);
+    for (size_t i = 0; i < P.longs.size(); ++i) C.longs[at.l + i] = P.longs[i] + c0;
+}
+
+// The chunks of several orders at once: all their pieces on one pool of threads.
+inline void build_chunks(std::vector<ChunkJob>& jobs, const std::vector<std::pair<int, int>>& cones, const ChunkLimits& L) {
+    std::vector<std::pair<int, int>> work;  // (job, piece)
+    int64_t total = 0;
+    for (int q = 0; q < (int)jobs.size(); ++q) {
+        plan_cuts(jobs[q], cones);
+        for (int p = 0; p + 1 < (int)jobs[q].cut.size(); ++p) work.push_back({q, p});
+        total += (int64_t)(*jobs[q].ptr)[jobs[q].nseg] + jobs[q].nseg;
+    }
+    const int nt = std::max(1, std::min((int)work.size(), threads_for(total)));
+    std::atomic<int> next{0};
+    parallel_tasks(nt, [&](int) {
+        for (int w = next++; w < (int)work.size(); w = next++) {
+            ChunkJob& J = jobs[work[w].first];
+            const int p = work[w].second;
+            chunk_range(*J.ptr, J.cut[p], J.cut[p + 1], J.unit_end, L, J.part[p]);
+        }
+    });
+    std::vector<std::vector<PieceAt>> at;
+    for (ChunkJob& J : jobs) at.push_back(size_pieces(J));
+    next = 0;
+    parallel_tasks(nt, [&](int) {
+        for (int w = next++; w < (int)work.size(); w = next++)
+            copy_piece(jobs[work[w].first], at[work[w].first][work[w].second], work[w].second);
+    });
 }
 
 }  // namespace host

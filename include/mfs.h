@@ -145,11 +145,13 @@ void mfs_default_settings(mfs_settings* s);
  * settings may be NULL (defaults). cuda_stream: a cudaStream_t or NULL. Limits: m, n, o < 2^31.
  * The iterate starts at zero (x = z = delta = lambda = 0, which is Algorithm 1 started from
  * y = gamma = 0). On success *out receives the handle; on failure *out is NULL.
- * Set-up: with 2^16 or more entries (and no staged layout requested) the COO list is copied to the
- * device once and checked there; if it is in column order (rows ascending within a column,
- * duplicates next to each other) the orders and padded layouts are built on the GPU, taking about
- * 70 bytes of device memory per entry until the call returns. Otherwise the host orders it with
- * all its cores. The result is the same either way.
+ * Set-up: with 2^16 or more entries the COO list is copied to the device once and checked there.
+ * Host threads narrow the indices to int32 on the way (each checked against its range first) and
+ * copy through pinned staging buffers that the process keeps after the first such call (64 MB of
+ * pinned host memory, one stream per copy thread; mfs_get_solution uses them too). If the list is
+ * in column order (rows ascending within a column, duplicates next to each other) the orders and
+ * padded layouts are built on the GPU, taking about 60 bytes of device memory per entry until the
+ * call returns. Otherwise the host orders it with all its cores. The result is the same either way.
  */
 mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
                       const double* val, const double* b, const double* c, int64_t ncones,

@@ -570,7 +570,8 @@ def main():
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         s3.close()
-        h2d = prob["row"].size * (8 + 8 + 8) + 8 * (m + n) + 16 * len(prob["cones"])
+        # the COO crosses as int32 row and column indices (narrowed by the host) and FP64 values
+        h2d = prob["row"].size * (4 + 4 + 8) + 8 * (m + n) + 16 * len(prob["cones"])
         d2h = 168 * args.steps + 8 * (3 * n + m)
         e2e = {"value": world * o * iters / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),

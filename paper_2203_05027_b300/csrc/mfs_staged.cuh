@@ -74,6 +74,9 @@ constexpr int EPI_U = 8;       // epilogue items per thread in flight
 #ifndef MFS_STG_PDL
 #define MFS_STG_PDL 1
 #endif
+#ifndef MFS_STG_COMBINE_PF
+#define MFS_STG_COMBINE_PF 1
+#endif
 constexpr int EPI_PF = MFS_STG_EPI_PF;  // blocks before a group's last one at which its epilogue's
                                         // inputs are prefetched into L2 (0: no prefetch)
 
@@ -367,6 +370,13 @@ __global__ void __launch_bounds__(NTS + 32, 1) k_staged(const StagedArgs g, cons
                             prefetch_l2(g.rsq + k0, cnt * 4);
                             prefetch_l2(a.b + k0, cnt * 4);
                             prefetch_l2(a.lam + k0, cnt * 4);
+                        } else if (MFS_STG_COMBINE_PF) {  // for k_row_combine, split between the halves
+                            if (h == 0) {
+                                prefetch_l2(g.rsq + k0, cnt * 4);
+                                prefetch_l2(a.b + k0, cnt * 4);
+                            } else if (h == 1) {
+                                prefetch_l2(a.lam + k0, cnt * 4);
+                            }
                         }
                     }
                 }

@@ -336,5 +336,19 @@ inline void build_chunks(std::vector<ChunkJob>& jobs, const std::vector<std::pai
     });
 }
 
+// Narrow n int64 indices to int32; returns the position of the first outside [0, lim), or n.
+inline size_t narrow_indices(const int64_t* src, int32_t* dst, size_t n, int64_t lim) {
+    uint64_t mx = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const uint64_t v = (uint64_t)src[i];  // a negative index becomes huge
+        mx = v > mx ? v : mx;
+        dst[i] = (int32_t)src[i];
+    }
+    if (mx < (uint64_t)lim) return n;
+    for (size_t i = 0; i < n; ++i)
+        if ((uint64_t)src[i] >= (uint64_t)lim) return i;
+    return n;
+}
+
 }  // namespace host
 }  // namespace mfs

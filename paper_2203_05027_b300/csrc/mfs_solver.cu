@@ -482,20 +482,6 @@ struct HostCopy {
     int64_t lim = 0;   // > 0: src holds bytes / 8 int64 indices, sent as int32, each checked against [0, lim)
 };
 
-// Narrow n int64 indices to int32; returns the position of the first outside [0, lim), or n.
-inline size_t narrow_indices(const int64_t* src, int32_t* dst, size_t n, int64_t lim) {
-    uint64_t mx = 0;
-    for (size_t i = 0; i < n; ++i) {
-        const uint64_t v = (uint64_t)src[i];  // a negative index becomes huge
-        mx = v > mx ? v : mx;
-        dst[i] = (int32_t)src[i];
-    }
-    if (mx < (uint64_t)lim) return n;
-    for (size_t i = 0; i < n; ++i)
-        if ((uint64_t)src[i] >= (uint64_t)lim) return i;
-    return n;
-}
-
 static bool pinned_ready(int device) {
     if (g_pin.device == device) return true;
     if (g_pin.device != -1) return false;
@@ -531,7 +517,7 @@ mfs_status upload_pinned(mfs_solver* s, const std::vector<HostCopy>& copies, cud
             if (c.lim > 0) {
                 const size_t n = c.bytes / 8;
                 std::vector<int32_t> tmp(n);
-                const size_t bad = narrow_indices(static_cast<const int64_t*>(c.src), tmp.data(), n, c.lim);
+                const size_t bad = mfs::host::narrow_indices(static_cast<const int64_t*>(c.src), tmp.data(), n, c.lim);
                 if (bad < n) *first_bad = std::min(*first_bad, bad);
                 CUDA_TRY(s, cudaMemcpyAsync(c.dst, tmp.data(), n * 4, cudaMemcpyHostToDevice, st));
                 CUDA_TRY(s, cudaStreamSynchronize(st));  // tmp goes out of scope
@@ -559,7 +545,7 @@ mfs_status upload_pinned(mfs_solver* s, const std::vector<HostCopy>& copies, cud
                 if (e != cudaSuccess) break;
                 if (idx) {
                     int32_t* bp = reinterpret_cast<int32_t*>(g_pin.buf[b]);
-                    const size_t q = narrow_indices(static_cast<const int64_t*>(c.src) + off, bp, len, c.lim);
+                    const size_t q = mfs::host::narrow_indices(static_cast<const int64_t*>(c.src) + off, bp, len, c.lim);
                     if (q < len) bad[t] = std::min(bad[t], off + q);
                     e = cudaMemcpyAsync(static_cast<int32_t*>(c.dst) + off, bp, len * 4, cudaMemcpyHostToDevice,
                                         g_pin.str[t]);

@@ -269,8 +269,8 @@ mfs_status mfs_get_solution_device(mfs_solver* s, double* x, double* lambda, dou
 mfs_status mfs_set_precision(mfs_solver* s, int32_t precision);
 
 /*
- * Measurement hook: run k iterations with each kernel launched on its own (no graph) and
- * bracketed by CUDA events on the solver's stream. out_ms[0] = average milliseconds of one
+ * Measurement hook: run k iterations with each kernel launched on its own (no graph), back to
+ * back, bracketed by CUDA events on the solver's stream, and wait once at the end. out_ms[0] = average milliseconds of one
  * column-order sweep kernel, out_ms[1] = of one row-order sweep kernel, out_ms[2] = of the
  * large-cone kernel (0 if none), out_ms[3] = average milliseconds of one whole iteration.
  * The iterate advances by k iterations.

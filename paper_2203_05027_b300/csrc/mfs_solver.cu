@@ -1345,36 +1345,55 @@ static mfs_status get_solution_t(mfs_solver* s, State<T>& st, double* x, double*
 
 template <typename T>
 static mfs_status time_kernels_t(mfs_solver* s, State<T>& st, int64_t k, double* out) {
+    // k iterations back to back, an event around each group of launches; one wait at the end, so
+    // that no host round trip idles the GPU between iterations
     SweepArgs<T> a = sweep_args(s, st);
-    cudaEvent_t ev[4];
-    for (auto& e : ev) CUDA_TRY(s, cudaEventCreate(&e));
+    const int64_t kk = std::max<int64_t>(k, 0);
+    std::vector<cudaEvent_t> ev((size_t)(3 * kk + 1), nullptr);
+    mfs_status r = MFS_OK;
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+            r = fail(s, MFS_ERR_CUDA, "cudaEventCreate failed");
+            break;
+        }
     double tc = 0, tb = 0, tr = 0, tall = 0;
-    for (int64_t i = 0; i < k; ++i) {
-        float ms = 0;
+    if (r == MFS_OK) {
         cudaEventRecord(ev[0], s->stream);
-        launch_col(s, a, s->stream);
-        cudaEventRecord(ev[1], s->stream);
-        launch_big(s, a, s->stream);
-        cudaEventRecord(ev[2], s->stream);
-        launch_row(s, a, s->stream);
-        cudaEventRecord(ev[3], s->stream);
-        CUDA_TRY(s, cudaEventSynchronize(ev[3]));
-        cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        tc += ms;
-        cudaEventElapsedTime(&ms, ev[1], ev[2]);
-        tb += ms;
-        cudaEventElapsedTime(&ms, ev[2], ev[3]);
-        tr += ms;
-        cudaEventElapsedTime(&ms, ev[0], ev[3]);
-        tall += ms;
+        for (int64_t i = 0; i < kk; ++i) {
+            launch_col(s, a, s->stream);
+            cudaEventRecord(ev[3 * i + 1], s->stream);
+            launch_big(s, a, s->stream);
+            cudaEventRecord(ev[3 * i + 2], s->stream);
+            launch_row(s, a, s->stream);
+            cudaEventRecord(ev[3 * i + 3], s->stream);
+        }
+        cudaError_t e = cudaEventSynchronize(ev[3 * kk]);
+        if (e != cudaSuccess) r = fail(s, MFS_ERR_CUDA, std::string("time_kernels: ") + cudaGetErrorString(e));
+        for (int64_t i = 0; i < kk && r == MFS_OK; ++i) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, ev[3 * i], ev[3 * i + 1]);
+            tc += ms;
+            cudaEventElapsedTime(&ms, ev[3 * i + 1], ev[3 * i + 2]);
+            tb += ms;
+            cudaEventElapsedTime(&ms, ev[3 * i + 2], ev[3 * i + 3]);
+            tr += ms;
+        }
+        if (kk > 0 && r == MFS_OK) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, ev[0], ev[3 * kk]);
+            tall = ms;
+        }
     }
-    for (auto& e : ev) cudaEventDestroy(e);
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    if (r != MFS_OK) return r;
     s->iter += k;
-    const double kk = k > 0 ? (double)k : 1.0;
-    out[0] = tc / kk;
-    out[1] = tr / kk;
-    out[2] = s->nbig ? tb / kk : 0.0;
-    out[3] = tall / kk;
+    const double kd = kk > 0 ? (double)kk : 1.0;
+    out[0] = tc / kd;
+    out[1] = tr / kd;
+    out[2] = s->nbig ? tb / kd : 0.0;
+    out[3] = tall / kd;
     CUDA_TRY(s, cudaGetLastError());
     return MFS_OK;
 }

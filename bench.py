@@ -590,7 +590,7 @@ def main():
                            "iterations_per_step": ITERS_PER_STEP, "precision": "fp32 sweep + fp64 residuals",
                            "sweeps": {"col": "staged" if info["sweep_col"] == mfs.SWEEP_STAGED else "chunked",
                                       "row": "staged" if info["sweep_row"] == mfs.SWEEP_STAGED else "chunked"},
-                           "l2": "inputs larger than L2 (A alone is %.0f MB in FP32)" % (16 * o / 1e6),
+                           "l2": "inputs larger than L2 (A in both orders is %.0f MB in FP32)" % (16 * o / 1e6),
                            "parallelism": f"replicas{world}"},
                 "kkt_after_timed_region": r["kkt"],
                 "roofline": roof, "gpu_launches": launches_per_step * args.steps,

@@ -158,6 +158,22 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
                       const mfs_cone* cones, const mfs_settings* settings, void* cuda_stream,
                       mfs_solver** out);
 
+/*
+ * Same as mfs_create, for a problem whose data are already in device memory (for instance torch
+ * tensors), so that they make no trip through the host: row, col (nnz int64 each), val (nnz
+ * doubles), b (m doubles) and c (n doubles) are device pointers of the current device; cones and
+ * settings stay host memory. The same rules and results as mfs_create: indices checked on the
+ * device (MFS_ERR_INVALID naming the first entry out of range, or a non-finite value in A, b or c),
+ * duplicates summed, zeros dropped. COO in column order (rows ascending within a column, duplicates
+ * next to each other) is set up on the device alone; any other order is copied to the host once
+ * and ordered there (the host path of mfs_create). The arrays are only read, and may be freed or
+ * reused once the call has returned.
+ */
+mfs_status mfs_create_device(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
+                             const double* val, const double* b, const double* c, int64_t ncones,
+                             const mfs_cone* cones, const mfs_settings* settings, void* cuda_stream,
+                             mfs_solver** out);
+
 /* Release all device and host memory of the handle. NULL is ignored. */
 void mfs_destroy(mfs_solver* s);
 
@@ -259,6 +275,13 @@ mfs_status mfs_residuals(mfs_solver* s, mfs_residuals_t* out);
 
 /* Copy the iterate to host arrays of doubles: x, z, delta (n each), lambda (m). Any may be NULL. */
 mfs_status mfs_get_solution(mfs_solver* s, double* x, double* lambda, double* z, double* delta);
+
+/* The fifth vector of the reduced state (see the top of this file), v = F_U (b - A x) - lambda/mu
+   as the last row pass left it (m doubles, host): with (x, z, delta, lambda) it fixes every later
+   iterate (Algorithm 1's y and gamma are y = V^T x + U^T (v + lambda/mu), gamma = -U^T lambda).
+   MFS_ERR_INVALID while a literal start (mfs_warm_start_literal) has not yet run its two
+   iterations. */
+mfs_status mfs_get_reduced_v(mfs_solver* s, double* v);
 
 /* Same as mfs_get_solution, into device arrays of doubles. */
 mfs_status mfs_get_solution_device(mfs_solver* s, double* x, double* lambda, double* z,
@@ -416,13 +439,24 @@ mfs_status mfs_mlp_adam_step(mfs_mlp* net, float lr);
 /* The update of mfs_mlp_backward followed by mfs_mlp_adam_step, with the output layer fused into
    the tensor-core GEMM epilogues: the forward GEMM of layer 3 produces the loss gradient instead of
    the output, and the weight-gradient GEMM of layer 3 applies Adam in place (so mfs_mlp_get_grads
-   does not report layer 3 after this call). */
+   does not report layer 3's weights after this call unless mfs_mlp_keep_grads is on). */
 mfs_status mfs_mlp_train_step(mfs_mlp* net, int32_t batch, const float* x, const float* target, float lr,
                               double* loss);
 /* Host copies of layer l (0..2): weights [out][in] and bias; NULL skips. */
 mfs_status mfs_mlp_get_params(mfs_mlp* net, int32_t layer, float* W, float* b);
 mfs_status mfs_mlp_set_params(mfs_mlp* net, int32_t layer, const float* W, const float* b);
 mfs_status mfs_mlp_get_grads(mfs_mlp* net, int32_t layer, float* gW, float* gb);
+/* Adam state of layer l (0..2), host copies: first (mW) and second (vW) moments of the weights
+   [out][in], of the bias (mb, vb); any may be NULL. *step (nullable) receives the number of Adam
+   steps taken, the t of the bias corrections 1 - beta^t of the next step minus one. */
+mfs_status mfs_mlp_get_adam_state(mfs_mlp* net, int32_t layer, float* mW, float* vW, float* mb, float* vb,
+                                  int64_t* step);
+/* The BF16 copy of layer l's weights [out][in] that the tensor-core GEMMs read, as raw 16-bit
+   patterns (host array of out*in). */
+mfs_status mfs_mlp_get_weights_bf16(mfs_mlp* net, int32_t layer, uint16_t* Wh);
+/* on != 0: mfs_mlp_train_step also stores the weight gradient of layer 3 that its fused Adam
+   epilogue consumes, so that mfs_mlp_get_grads reports it (one more FP32 store per weight). */
+mfs_status mfs_mlp_keep_grads(mfs_mlp* net, int32_t on);
 
 /* Dense GEMM on the tensor cores: C[M x N] = A[M x K] * B[N x K]^T (+ bias[N], then ReLU if relu),
    A and B row-major BF16 device arrays (K a multiple of 8), C row-major FP32 (out_fp32) or BF16,
@@ -462,12 +496,18 @@ mfs_status mfs_gemm_bf16_wait_test(void* cuda_stream);
  * default stream) and the call returns without waiting; read out after synchronizing.
  * Scratch: a static 1 MiB device array that every GPU which loads this library holds until the
  * process exits. Limit: m <= 4,194,304 rows; a larger m returns MFS_ERR_INVALID and enqueues
- * nothing, as do negative sizes and NULL arrays. The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * nothing, as do negative sizes, n >= 2^31 - 1 and a NULL array among out, row_ptr, col_idx, val, b
+ * and lambda (m > 0) or x (n > 0). Set-up: the array's device address belongs to the current
+ * context and is looked up (cudaGetSymbolAddress) by every call whose stream is not being
+ * captured; while a capture is under way the address found by the last call in the same context
+ * is reused (MFS_ERR_INVALID if there was none), so the first call in each context should come
+ * before any stream capture.
  * Every call uses the same array: calls whose work can overlap on the GPU (different streams,
  * or different host threads) race on it, so the caller must order them. No state carries over
- * between calls (each call writes every scratch slot it reads). MFS_ERR_CUDA if the device
- * lookup or a launch fails.
+ * between calls (each call writes every scratch slot it reads). If an error from earlier work is
+ * already pending on the calling thread (cudaPeekAtLastError), the call returns MFS_ERR_CUDA,
+ * enqueues nothing and leaves that error in place; MFS_ERR_CUDA also if the device lookup or one
+ * of its own launches fails.
  */
 mfs_status mfs_row_residuals_static(int64_t m, int64_t n, const int32_t* row_ptr, const int32_t* col_idx,
                                     const double* val, const double* b, const double* x,

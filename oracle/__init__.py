@@ -200,6 +200,18 @@ class Oracle:
             delta = self.proj_K(self.rmatvec(lam) + self.c)
         self.set_state(x=x, y=y, z=z, lam=lam, gam=g, delta=delta)
 
+    def set_reduced_state(self, x, z, delta, lam, v):
+        """Literal state of Algorithm 1 that corresponds to a state (x, z, delta, lambda, v) of the
+        reduced form, v = rho - lambda/mu: gamma = -U^T lambda and y = V^T x + U^T rho (Sec. IV; the
+        y-step's optimality condition with the lambda- and gamma-updates). Only V y enters the next
+        x-step, and this y gives V y = d .* x + A^T rho, the reduced x-step's term."""
+        x, z, delta, lam, v = (_f64(a) for a in (x, z, delta, lam, v))
+        ik, jk, ak, _, _ = self.uv()
+        rho = v + lam / self.mu
+        y = x[jk] + ak * rho[ik]
+        gam = -ak * lam[ik]
+        self.set_state(x=x, y=y, z=z, lam=lam, gam=gam, delta=delta)
+
     def matvec(self, x):
         x = _f64(x)
         out = np.empty(self.m)

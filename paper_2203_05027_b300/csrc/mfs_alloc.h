@@ -9,4 +9,6 @@
 
 namespace mfs {
 cudaError_t device_malloc(void** p, size_t bytes);
+// The bounds-checked build's record for mfs_row_residuals_static (mfs_static.cu); 0 otherwise.
+unsigned long long static_bounds_record(bool reset);
 }

@@ -1000,9 +1000,16 @@ mfs_status mfs_batch_tune(mfs_batch* s, int64_t iters, mfs_batch_tuning* chosen)
     const mfs_batch_tuning keep = s->tune;
     mfs_batch_tuning best = keep;
     float best_ms = 1e30f;
-    cudaEvent_t e0, e1;
-    BCUDA(s, cudaEventCreate(&e0));
-    BCUDA(s, cudaEventCreate(&e1));
+    // events released on every return, including the early ones of a failed candidate
+    struct Events {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ~Events() {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+        }
+    } ev;
+    BCUDA(s, cudaEventCreate(&ev.e0));
+    BCUDA(s, cudaEventCreate(&ev.e1));
     for (int threads : {128, 256, 512}) {
         for (int cps : {1, 2, 3, 4}) {
             mfs_batch_tuning t = keep;
@@ -1010,20 +1017,18 @@ mfs_status mfs_batch_tune(mfs_batch* s, int64_t iters, mfs_batch_tuning* chosen)
             t.ctas_per_sm = cps;
             BTRY(mfs_batch_set_tuning(s, &t));
             BTRY(mfs_batch_iterate(s, 1));  // capture and warm
-            cudaEventRecord(e0, s->stream);
+            cudaEventRecord(ev.e0, s->stream);
             BTRY(mfs_batch_iterate(s, iters));
-            cudaEventRecord(e1, s->stream);
-            BCUDA(s, cudaEventSynchronize(e1));
+            cudaEventRecord(ev.e1, s->stream);
+            BCUDA(s, cudaEventSynchronize(ev.e1));
             float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventElapsedTime(&ms, ev.e0, ev.e1);
             if (ms < best_ms) {
                 best_ms = ms;
                 best = t;
             }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     BTRY(mfs_batch_set_tuning(s, &best));
     if (chosen) *chosen = best;
     return MFS_OK;

@@ -31,7 +31,9 @@ enum BoundsSite : int {
     BS_GATHER_XR = 5, // x gathered by the row residual
     BS_STG_VEC = 6,   // staged vector block in shared memory
     BS_STG_ACC = 7,   // staged segment sums in shared memory
-    BS_STG_ENT = 8    // staged entry arrays
+    BS_STG_ENT = 8,   // staged entry arrays
+    BS_STATIC_ENT = 9,  // mfs_row_residuals_static: nonzero index beyond row_ptr[m]
+    BS_STATIC_X = 10    // mfs_row_residuals_static: column index outside [0, n)
 };
 #ifdef MFS_DEBUG_BOUNDS
 static __device__ unsigned long long g_bounds_fail;  // (site << 40) | low 40 bits of the index

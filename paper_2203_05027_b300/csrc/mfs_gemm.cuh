@@ -161,6 +161,7 @@ struct GemmArgs {
     float *W, *mom, *vel;
     __nv_bfloat16 *Wh, *Wt;
     float lr, b1, b2, eps, c1, c2;
+    float* gkeep;  // EPI_ADAM: nullable; receives the gradient g [row][col] (ld ldc) as well
 };
 
 enum { EPI_STORE = 0, EPI_LOSS = 1, EPI_ADAM = 2 };
@@ -322,6 +323,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
                                 if (r < rows) {
                                     const size_t idx = (size_t)(rbase + r) * g.ldc + col;
                                     const float gt = stg[r * 33 + lane];
+                                    if (g.gkeep) g.gkeep[idx] = gt;
                                     const float mt = g.b1 * mv[u] + (1.f - g.b1) * gt;
                                     const float vt = g.b2 * vv[u] + (1.f - g.b2) * gt * gt;
                                     g.mom[idx] = mt;

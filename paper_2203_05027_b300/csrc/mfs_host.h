@@ -336,6 +336,19 @@ inline void build_chunks(std::vector<ChunkJob>& jobs, const std::vector<std::pai
     });
 }
 
+// Argument rule of mfs_row_residuals_static, checked on the host before any device work: sizes not
+// negative, n below 2^31 - 1 (as mfs_create), m within the rows that the static scratch array
+// covers (max_rows), the output present, and every array that the sizes make the kernels read
+// present (the CSR arrays, b and lambda when m > 0; x when n > 0).
+inline bool static_resid_args_ok(int64_t m, int64_t n, int64_t max_rows, bool have_row_ptr, bool have_col_idx,
+                                 bool have_val, bool have_b, bool have_x, bool have_lambda, bool have_out) {
+    if (m < 0 || n < 0 || n >= INT32_MAX || m > max_rows) return false;
+    if (!have_out) return false;
+    if (m > 0 && !(have_row_ptr && have_col_idx && have_val && have_b && have_lambda)) return false;
+    if (n > 0 && !have_x) return false;
+    return true;
+}
+
 // Narrow n int64 indices to int32; returns the position of the first outside [0, lim), or n.
 inline size_t narrow_indices(const int64_t* src, int32_t* dst, size_t n, int64_t lim) {
     uint64_t mx = 0;

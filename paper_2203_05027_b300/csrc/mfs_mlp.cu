@@ -383,6 +383,7 @@ struct mfs_mlp {
          *Xt = nullptr, *dZ2 = nullptr, *dZ2t = nullptr, *dZ1 = nullptr, *dZ1t = nullptr;
     float *Y = nullptr, *dH = nullptr, *work = nullptr;
     bool wt2_fresh = false;  // Wt[2] holds the transpose of the current Wh[2]
+    bool keep_grads = false; // mfs_mlp_train_step also stores layer 3's weight gradient
     double *loss_part = nullptr, *loss = nullptr;
     int* err = nullptr;
     size_t work_floats = 0;
@@ -773,6 +774,7 @@ mfs_status mfs_mlp_train_step(mfs_mlp* s, int32_t batch, const float* x, const f
     fa.eps = s->eps;
     fa.c1 = c1;
     fa.c2 = c2;
+    fa.gkeep = s->keep_grads ? s->gW[2] : nullptr;
     {
         std::string why;
         mfs_status q = gemm(D, W, B, s->dYt, s->H2t, nullptr, 0, 1, nullptr, 1, s->work, s->err, st, &why, SPIN, 0,
@@ -821,6 +823,35 @@ mfs_status mfs_mlp_get_grads(mfs_mlp* s, int32_t l, float* gW, float* gb) {
     const size_t cw = (size_t)layer_in(s, l) * user_out(s, l), cb = user_out(s, l);
     if (gW && cudaMemcpy(gW, s->gW[l], cw * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return MFS_ERR_CUDA;
     if (gb && cudaMemcpy(gb, s->gb[l], cb * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return MFS_ERR_CUDA;
+    return MFS_OK;
+}
+
+mfs_status mfs_mlp_keep_grads(mfs_mlp* s, int32_t on) {
+    if (!s) return MFS_ERR_INVALID;
+    s->keep_grads = on != 0;
+    return MFS_OK;
+}
+
+// Adam state of layer l: first and second moments of the weights [out][in] and of the bias (any
+// may be NULL) and the number of steps taken.
+mfs_status mfs_mlp_get_adam_state(mfs_mlp* s, int32_t l, float* mW, float* vW, float* mb, float* vb, int64_t* step) {
+    if (!s || l < 0 || l > 2) return MFS_ERR_INVALID;
+    const size_t cw = (size_t)layer_in(s, l) * user_out(s, l), cb = user_out(s, l);
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MFS_ERR_CUDA;
+    if (mW && cudaMemcpy(mW, s->mW[l], cw * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return MFS_ERR_CUDA;
+    if (vW && cudaMemcpy(vW, s->vW[l], cw * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return MFS_ERR_CUDA;
+    if (mb && cudaMemcpy(mb, s->mb[l], cb * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return MFS_ERR_CUDA;
+    if (vb && cudaMemcpy(vb, s->vb[l], cb * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return MFS_ERR_CUDA;
+    if (step) *step = s->step;
+    return MFS_OK;
+}
+
+// The BF16 copy of layer l's weights [out][in] that the GEMMs read, as raw 16-bit patterns.
+mfs_status mfs_mlp_get_weights_bf16(mfs_mlp* s, int32_t l, uint16_t* Wh) {
+    if (!s || l < 0 || l > 2 || !Wh) return MFS_ERR_INVALID;
+    const size_t cw = (size_t)layer_in(s, l) * user_out(s, l);
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MFS_ERR_CUDA;
+    if (cudaMemcpy(Wh, s->Wh[l], cw * sizeof(uint16_t), cudaMemcpyDeviceToHost) != cudaSuccess) return MFS_ERR_CUDA;
     return MFS_OK;
 }
 

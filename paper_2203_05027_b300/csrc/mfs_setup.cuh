@@ -125,6 +125,21 @@ __global__ void k_check(const int* __restrict__ row, const int* __restrict__ col
     }
 }
 
+// COO indices that already live on the device (mfs_create_device): int64 narrowed to int32, an
+// index outside [0, lim) becoming -1 so that k_check reports its position.
+__global__ void k_narrow_dev(const long long* __restrict__ src, long long nnz, long long lim, int* __restrict__ dst) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nnz; q += (long long)gridDim.x * blockDim.x) {
+        const long long v = src[q];
+        dst[q] = (v >= 0 && v < lim) ? (int)v : -1;
+    }
+}
+
+// flag = 1 if some element of p[0 .. n) is NaN or infinite
+__global__ void k_nonfinite(const double* __restrict__ p, long long n, int* __restrict__ flag) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(p[q])) *flag = 1;
+}
+
 // In column order (duplicates allowed): keep[q] = 1 where a run of equal (column, row) starts and
 // its values sum to a nonzero, sum[q] = that sum (in entry order).
 __global__ void k_runs(const int* __restrict__ row, const int* __restrict__ col,

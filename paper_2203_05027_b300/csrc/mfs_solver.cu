@@ -615,8 +615,10 @@ mfs_status download_pinned(mfs_solver* s, const std::vector<HostCopy>& copies, c
     return MFS_OK;
 }
 
+// COO on the host (uploaded here) or, with on_device, already in device memory. Returns MFS_OK with
+// P.dev.on false when the entries are not in column order (the host orders them then).
 mfs_status device_orders(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
-                         const double* val, HostProblem& P) {
+                         const double* val, HostProblem& P, bool on_device = false) {
     namespace su = mfs::setup;
     DevOrders& D = P.dev;
     auto grab = [&](void** q, size_t bytes) -> mfs_status {
@@ -635,12 +637,19 @@ mfs_status device_orders(mfs_solver* s, int64_t m, int64_t n, int64_t nnz, const
     unsigned long long* d_bad = nullptr;
     TRY(grab((void**)&d_row, nnz * sizeof(int)));
     TRY(grab((void**)&d_col, nnz * sizeof(int)));
-    TRY(grab((void**)&d_val, nnz * sizeof(double)));
     TRY(grab((void**)&d_bad, 2 * sizeof(unsigned long long) + 2 * sizeof(int)));
     d_flags = reinterpret_cast<int*>(d_bad + 2);
     size_t bad_host = SIZE_MAX;  // first entry with an index out of range, found while narrowing
-    TRY(upload_pinned(s, {{d_row, row, nnz * sizeof(int64_t), m}, {d_col, col, nnz * sizeof(int64_t), n},
-                          {d_val, val, nnz * sizeof(double)}}, st, &bad_host));
+    if (on_device) {
+        d_val = const_cast<double*>(val);  // only read
+        su::k_narrow_dev<<<grid, su::NT, 0, st>>>(reinterpret_cast<const long long*>(row), nnz, m, d_row);
+        su::k_narrow_dev<<<grid, su::NT, 0, st>>>(reinterpret_cast<const long long*>(col), nnz, n, d_col);
+        CUDA_TRY(s, cudaGetLastError());
+    } else {
+        TRY(grab((void**)&d_val, nnz * sizeof(double)));
+        TRY(upload_pinned(s, {{d_row, row, nnz * sizeof(int64_t), m}, {d_col, col, nnz * sizeof(int64_t), n},
+                              {d_val, val, nnz * sizeof(double)}}, st, &bad_host));
+    }
     {
         unsigned long long init[2] = {(unsigned long long)nnz, (unsigned long long)nnz};
         CUDA_TRY(s, cudaMemcpyAsync(d_bad, init, sizeof init, cudaMemcpyHostToDevice, st));
@@ -1108,8 +1117,10 @@ mfs_status pad_on_device(mfs_solver* s, const HostProblem& P, bool col, int** pi
     return MFS_OK;
 }
 
+// b and c are host arrays, or device arrays when bc_on_device
 template <typename T>
-mfs_status alloc_state(mfs_solver* s, State<T>& st, const HostProblem& P, const double* b, const double* c) {
+mfs_status alloc_state(mfs_solver* s, State<T>& st, const HostProblem& P, const double* b, const double* c,
+                       bool bc_on_device) {
     // x and v, the vectors the staged sweeps copy in whole blocks, are padded to a multiple of the block
     const int64_t npad = (int64_t)(s->n + mfs::staged::RB_ROW - 1) / mfs::staged::RB_ROW * mfs::staged::RB_ROW;
     const int64_t mpad = (int64_t)(s->m + mfs::staged::RB_COL - 1) / mfs::staged::RB_COL * mfs::staged::RB_COL;
@@ -1118,9 +1129,17 @@ mfs_status alloc_state(mfs_solver* s, State<T>& st, const HostProblem& P, const 
     TRY(dalloc(s, &st.del, s->n));
     TRY(dalloc(s, &st.lam, s->m));
     TRY(dalloc(s, &st.v, mpad));
-    std::vector<T> hb(b, b + s->m), hc(c, c + s->n);
-    TRY(upload(s, &st.b, hb.data(), hb.size()));
-    TRY(upload(s, &st.c, hc.data(), hc.size()));
+    if (bc_on_device) {
+        TRY(dalloc(s, &st.b, s->m));
+        TRY(dalloc(s, &st.c, s->n));
+        convert(st.b, b, s->m, s->stream);
+        convert(st.c, c, s->n, s->stream);
+        CUDA_TRY(s, cudaGetLastError());
+    } else {
+        std::vector<T> hb(b, b + s->m), hc(c, c + s->n);
+        TRY(upload(s, &st.b, hb.data(), hb.size()));
+        TRY(upload(s, &st.c, hc.data(), hc.size()));
+    }
     if (P.dev.on) {
         TRY(pad_on_device<T>(s, P, true, nullptr, &st.cval));
         TRY(pad_on_device<T>(s, P, false, nullptr, &st.rval));
@@ -1680,10 +1699,14 @@ void mfs_destroy(mfs_solver* s) {
     delete s;
 }
 
-mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col, const double* val,
-                      const double* b, const double* c, int64_t ncones, const mfs_cone* cones,
-                      const mfs_settings* settings, void* cuda_stream, mfs_solver** out) {
-    MFS_TRACE("mfs_create");
+}  // extern "C"
+
+namespace {
+
+// mfs_create and mfs_create_device: on_device says that row, col, val, b and c are device arrays.
+mfs_status create_impl(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col, const double* val,
+                       const double* b, const double* c, int64_t ncones, const mfs_cone* cones,
+                       const mfs_settings* settings, void* cuda_stream, mfs_solver** out, bool on_device) {
     g_create_error.clear();
     if (!out) return fail(nullptr, MFS_ERR_INVALID, "out is NULL");
     *out = nullptr;
@@ -1716,8 +1739,8 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
     if (total != n) return fail(nullptr, MFS_ERR_INVALID, "cone sizes do not sum to n");
     bool in_order = false;
     // large inputs are checked and, when already in column order, set up on the GPU (the staged
-    // layout too)
-    const bool dev_path = nnz >= (int64_t(1) << 16);
+    // layout too); so is every input that is already on the device
+    const bool dev_path = on_device || nnz >= (int64_t(1) << 16);
     if (!dev_path) {
         // first bad entry: index out of range, or a non-finite value; and whether the entries are
         // already in (column, row) order (equal neighbours are duplicates, summed later)
@@ -1739,7 +1762,8 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
             return fail(nullptr, MFS_ERR_INVALID, "COO index out of range at entry " + std::to_string(bi));
         if (bv < nnz) return fail(nullptr, MFS_ERR_INVALID, "non-finite value in A");
     }
-    if (!finite_all(b, m) || !finite_all(c, n)) return fail(nullptr, MFS_ERR_INVALID, "non-finite value in b or c");
+    if (!on_device && (!finite_all(b, m) || !finite_all(c, n)))
+        return fail(nullptr, MFS_ERR_INVALID, "non-finite value in b or c");
 
     mfs_solver* s = new (std::nothrow) mfs_solver();
     if (!s) return fail(nullptr, MFS_ERR_OOM, "host allocation failed");
@@ -1769,11 +1793,57 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
         s->last_error = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
         return bail(MFS_ERR_CUDA);
     }
+    if (on_device) {
+        // b and c: checked on the device
+        int* flag = nullptr;
+        mfs_status q = dalloc(s, &flag, 1);
+        if (q != MFS_OK) return bail(q);
+        int h = 0;
+        e = cudaMemsetAsync(flag, 0, sizeof(int), s->stream);
+        const int grid = 8 * 148;
+        if (e == cudaSuccess && m > 0) mfs::setup::k_nonfinite<<<grid, 256, 0, s->stream>>>(b, m, flag);
+        if (e == cudaSuccess && n > 0) mfs::setup::k_nonfinite<<<grid, 256, 0, s->stream>>>(c, n, flag);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) {
+            s->last_error = std::string("checking b and c: ") + cudaGetErrorString(e);
+            return bail(MFS_ERR_CUDA);
+        }
+        if (h) {
+            s->last_error = "non-finite value in b or c";
+            return bail(MFS_ERR_INVALID);
+        }
+    }
     HostProblem P;
     mfs_status st = MFS_OK;
+    // device COO that is not in column order is ordered on the host: these hold its copy
+    std::vector<int64_t> h_row, h_col;
+    std::vector<double> h_val;
     if (dev_path) {
-        st = device_orders(s, m, n, nnz, row, col, val, P);
+        st = device_orders(s, m, n, nnz, row, col, val, P, on_device);
         if (st != MFS_OK) return bail(st);
+        if (on_device && !P.dev.on) {
+            h_row.resize(nnz);
+            h_col.resize(nnz);
+            h_val.resize(nnz);
+            e = cudaSuccess;
+            if (nnz > 0) {
+                e = cudaMemcpyAsync(h_row.data(), row, nnz * sizeof(int64_t), cudaMemcpyDeviceToHost, s->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(h_col.data(), col, nnz * sizeof(int64_t), cudaMemcpyDeviceToHost, s->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(h_val.data(), val, nnz * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+            }
+            if (e != cudaSuccess) {
+                s->last_error = std::string("copying the COO to the host: ") + cudaGetErrorString(e);
+                return bail(MFS_ERR_CUDA);
+            }
+            row = h_row.data();
+            col = h_col.data();
+            val = h_val.data();
+        }
     }
     st = setup_host(s, m, n, nnz, row, col, val, in_order, ncones, cones, P);
     if (st != MFS_OK) return bail(st);
@@ -1836,7 +1906,7 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
             s->num_sms = sms;
     }
     if (set.precision == MFS_FP32_MIXED) {
-        CHK(alloc_state<float>(s, s->s32, P, b, c));
+        CHK(alloc_state<float>(s, s->s32, P, b, c, on_device));
         CHK(residual_grids<float>(s));
         s->have32 = true;
         // what the automatic choice stages (the same whether or not it is the creation's choice)
@@ -1851,7 +1921,7 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
         s->sweep_kind = s->stg_ok ? set.sweep : MFS_SWEEP_AUTO;
     }
     if (set.precision == MFS_FP64 || set.polish_iters > 0) {
-        CHK(alloc_state<double>(s, s->s64, P, b, c));
+        CHK(alloc_state<double>(s, s->s64, P, b, c, on_device));
         CHK(residual_grids<double>(s));
         s->have64 = true;
     }
@@ -1874,6 +1944,25 @@ mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, con
 #undef CHK
     *out = s;
     return MFS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mfs_status mfs_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col, const double* val,
+                      const double* b, const double* c, int64_t ncones, const mfs_cone* cones,
+                      const mfs_settings* settings, void* cuda_stream, mfs_solver** out) {
+    MFS_TRACE("mfs_create");
+    return create_impl(m, n, nnz, row, col, val, b, c, ncones, cones, settings, cuda_stream, out, false);
+}
+
+mfs_status mfs_create_device(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
+                             const double* val, const double* b, const double* c, int64_t ncones,
+                             const mfs_cone* cones, const mfs_settings* settings, void* cuda_stream,
+                             mfs_solver** out) {
+    MFS_TRACE("mfs_create_device");
+    return create_impl(m, n, nnz, row, col, val, b, c, ncones, cones, settings, cuda_stream, out, true);
 }
 
 mfs_status mfs_get_info(const mfs_solver* s, mfs_info_t* out) {
@@ -1919,6 +2008,8 @@ int32_t mfs_debug_bounds(int64_t* site, int64_t* index, int32_t reset) {
     unsigned long long v = 0;
     cudaDeviceSynchronize();
     cudaMemcpyFromSymbol(&v, mfs::g_bounds_fail, sizeof v);
+    const unsigned long long vs = mfs::static_bounds_record(reset != 0);
+    if (v == 0) v = vs;
     if (site) *site = (int64_t)(v >> 40);
     if (index) *index = (int64_t)(v & 0xFFFFFFFFFFull);
     if (reset) {
@@ -2157,6 +2248,25 @@ mfs_status mfs_get_solution_device(mfs_solver* s, double* x, double* lambda, dou
     CUDA_TRY(s, cudaSetDevice(s->device));
     return s->precision == MFS_FP64 ? get_solution_t(s, s->s64, x, lambda, z, delta, false)
                                     : get_solution_t(s, s->s32, x, lambda, z, delta, false);
+}
+
+mfs_status mfs_get_reduced_v(mfs_solver* s, double* v) {
+    if (!s || (!v && s->m > 0)) return MFS_ERR_INVALID;
+    if (s->lit_pending > 0) return fail(s, MFS_ERR_INVALID, "a literal start is pending: v is not formed yet");
+    CUDA_TRY(s, cudaSetDevice(s->device));
+    if (s->m == 0) return MFS_OK;
+    double* tmp = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&tmp, (size_t)s->m * sizeof(double), s->stream);
+    if (e != cudaSuccess) return fail(s, MFS_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    if (s->precision == MFS_FP64)
+        convert(tmp, s->s64.v, s->m, s->stream);
+    else
+        convert(tmp, s->s32.v, s->m, s->stream);
+    e = cudaMemcpyAsync(v, tmp, (size_t)s->m * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    cudaFreeAsync(tmp, s->stream);
+    if (e != cudaSuccess) return fail(s, MFS_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    return MFS_OK;
 }
 
 mfs_status mfs_time_kernels(mfs_solver* s, int64_t k, double* out_ms) {

@@ -14,12 +14,19 @@
 // holds until the process exits. All calls share it: calls whose work overlaps on the GPU (for
 // example on two streams) race on it and must be serialized by the caller. Nothing in it has to
 // start at zero: each call's first kernel writes every slot that its second kernel reads.
+// The array's device address is taken in the caller's current context at every call that is not
+// being captured into a CUDA graph; a call made during a capture reuses the address of the last
+// call in the same context, so one call per context must come before capturing one.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
 #include <mutex>
 
 #include "../../include/mfs.h"
+#include "mfs_alloc.h"
+#include "mfs_device.cuh"
+#include "mfs_host.h"
 
 namespace {
 
@@ -33,8 +40,28 @@ enum : int { P_RES2 = 0, P_RESMAX, P_AXMAX, P_B2, P_BMAX, P_BLAM };
 
 static __device__ __align__(256) double g_row_resid_scratch[RS_MAX_CTAS * RS_NPART];
 
+// The array's device address belongs to a CUDA context: it is looked up again on every call that
+// is not being captured into a graph, and kept per device together with the context it was taken
+// in, for calls made while their stream is captured (which must not call into module loading).
 std::mutex g_setup_mutex;
-double* g_scratch_addr[RS_MAX_DEVICES] = {};  // device address of the array, per device
+double* g_scratch_addr[RS_MAX_DEVICES] = {};
+CUcontext g_scratch_ctx[RS_MAX_DEVICES] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+
+CUcontext current_context() {
+    static CtxGetCurrentFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<CtxGetCurrentFn>(p);
+    }();
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -44,7 +71,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Per-CTA partials: sum (Ax-b)^2, max |Ax-b|, max |Ax|, sum b^2, max |b|, sum b*lambda over the
 // CTA's rows, FP64, one warp per row, fixed order (deterministic).
-__global__ void __launch_bounds__(RS_NT) k_row_resid_static(int m, const int* __restrict__ row_ptr,
+__global__ void __launch_bounds__(RS_NT) k_row_resid_static(int m, int n, const int* __restrict__ row_ptr,
                                                             const int* __restrict__ col_idx,
                                                             const double* __restrict__ val,
                                                             const double* __restrict__ b,
@@ -53,12 +80,19 @@ __global__ void __launch_bounds__(RS_NT) k_row_resid_static(int m, const int* __
     __shared__ double sh[RS_NT / 32][6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r0 = blockIdx.x * RS_ROWS_PER_CTA;
+#ifdef MFS_DEBUG_BOUNDS
+    const int nnz = row_ptr[m];
+#endif
     double f[6] = {0, 0, 0, 0, 0, 0};
     for (int rl = warp; rl < RS_ROWS_PER_CTA; rl += RS_NT / 32) {
         const int i = r0 + rl;
         if (i >= m) break;
         double ax = 0.0;
-        for (int k = row_ptr[i] + lane; k < row_ptr[i + 1]; k += 32) ax += val[k] * x[col_idx[k]];
+        for (int k = row_ptr[i] + lane; k < row_ptr[i + 1]; k += 32) {
+            if (!MFS_INB(k, nnz, ::mfs::BS_STATIC_ENT)) continue;  // checked build: record and skip
+            const int j = col_idx[k];
+            if (MFS_INB(j, n, ::mfs::BS_STATIC_X)) ax += val[k] * x[j];
+        }
         ax = warp_sum(ax);
         const double bi = b[i], res = ax - bi;
         f[P_RES2] += res * res;
@@ -132,30 +166,61 @@ __global__ void __launch_bounds__(RS_NT) k_row_resid_static_finalize(int nparts,
 
 }  // namespace
 
+namespace mfs {
+// Host side of the checked build's record for the kernels of this file (0 when nothing failed, or in
+// the normal build); reset clears it. mfs_debug_bounds reports it when the solver kernels' record is
+// empty.
+unsigned long long static_bounds_record(bool reset) {
+#ifdef MFS_DEBUG_BOUNDS
+    unsigned long long v = 0;
+    cudaDeviceSynchronize();
+    cudaMemcpyFromSymbol(&v, g_bounds_fail, sizeof v);
+    if (reset) {
+        const unsigned long long zero = 0;
+        cudaMemcpyToSymbol(g_bounds_fail, &zero, sizeof zero);
+    }
+    return v;
+#else
+    (void)reset;
+    return 0;
+#endif
+}
+}  // namespace mfs
+
 extern "C" mfs_status mfs_row_residuals_static(int64_t m, int64_t n, const int32_t* row_ptr, const int32_t* col_idx,
                                                const double* val, const double* b, const double* x,
                                                const double* lambda, double* out, void* cuda_stream) {
-    if (m < 0 || n < 0) return MFS_ERR_INVALID;
-    if (m > (int64_t)RS_MAX_CTAS * RS_ROWS_PER_CTA) return MFS_ERR_INVALID;  // beyond the static scratch
-    if (!out || (m && (!row_ptr || !b || !lambda)) || (n && !x)) return MFS_ERR_INVALID;
+    if (!mfs::host::static_resid_args_ok(m, n, (int64_t)RS_MAX_CTAS * RS_ROWS_PER_CTA, row_ptr, col_idx, val, b, x,
+                                         lambda, out))
+        return MFS_ERR_INVALID;  // includes m beyond the static scratch
+    // an error left by earlier work on this thread is reported, not consumed: nothing is enqueued
+    if (cudaPeekAtLastError() != cudaSuccess) return MFS_ERR_CUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= RS_MAX_DEVICES) return MFS_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return MFS_ERR_CUDA;
+    const CUcontext ctx = current_context();
     double* scratch = nullptr;
     {
-        // Set-up, once per device, with that device current: in host code the array's name is
-        // only a stand-in, so its device address is looked up here and kept.
+        // In host code the array's name is only a stand-in: its device address in the current
+        // context is looked up here (set-up), with the device current.
         std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch_addr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_row_resid_scratch) != cudaSuccess || !p) return MFS_ERR_CUDA;
             g_scratch_addr[dev] = static_cast<double*>(p);
+            g_scratch_ctx[dev] = ctx;
+        } else if (!g_scratch_addr[dev] || !ctx || g_scratch_ctx[dev] != ctx) {
+            return MFS_ERR_INVALID;  // no call in this context before the capture began
         }
         scratch = g_scratch_addr[dev];
     }
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const int nparts = (int)((m + RS_ROWS_PER_CTA - 1) / RS_ROWS_PER_CTA);
-    if (nparts > 0)
-        k_row_resid_static<<<nparts, RS_NT, 0, st>>>((int)m, row_ptr, col_idx, val, b, x, lambda, scratch);
+    if (nparts > 0) {
+        k_row_resid_static<<<nparts, RS_NT, 0, st>>>((int)m, (int)n, row_ptr, col_idx, val, b, x, lambda, scratch);
+        if (cudaGetLastError() != cudaSuccess) return MFS_ERR_CUDA;
+    }
     k_row_resid_static_finalize<<<1, RS_NT, 0, st>>>(nparts, scratch, out);
     return cudaGetLastError() == cudaSuccess ? MFS_OK : MFS_ERR_CUDA;
 }

@@ -104,6 +104,9 @@ def load(path=LIB_PATH):
     lib.mfs_create.argtypes = [i64, i64, i64, lp, lp, dp, dp, dp, i64, ctypes.POINTER(Cone),
                                ctypes.POINTER(Settings), P, ctypes.POINTER(P)]
     lib.mfs_create.restype = st
+    lib.mfs_create_device.argtypes = [i64, i64, i64, P, P, P, P, P, i64, ctypes.POINTER(Cone),
+                                      ctypes.POINTER(Settings), P, ctypes.POINTER(P)]
+    lib.mfs_create_device.restype = st
     lib.mfs_destroy.argtypes = [P]
     lib.mfs_destroy.restype = None
     lib.mfs_last_error.argtypes = [P]
@@ -134,6 +137,8 @@ def load(path=LIB_PATH):
     lib.mfs_set_precision.argtypes = [P, i32]
     lib.mfs_set_precision.restype = st
     lib.mfs_time_kernels.argtypes = [P, i64, dp]
+    lib.mfs_get_reduced_v.argtypes = [P, P]
+    lib.mfs_get_reduced_v.restype = st
     lib.mfs_debug_fail_alloc_after.argtypes = [i64]
     lib.mfs_debug_fail_alloc_after.restype = st
     lib.mfs_gemm_bf16_wait_test.argtypes = [P]
@@ -156,6 +161,29 @@ def _f64(a, count=None):
     return a
 
 
+def _cone_array(cones):
+    cones = np.asarray(cones, dtype=np.int64).reshape(-1, 2)
+    carr = (Cone * max(len(cones), 1))()
+    for q, (k, sz) in enumerate(cones):
+        carr[q].kind = int(k)
+        carr[q].size = int(sz)
+    return carr, len(cones)
+
+
+def _settings(lib, mu, check_every, precision, polish_iters, stop_rule, osqp_rel, sweep):
+    st = Settings()
+    lib.mfs_default_settings(ctypes.byref(st))
+    st.mu = float(mu)
+    st.check_every = int(check_every)
+    st.precision = {"fp64": FP64, "fp32": FP32_MIXED, "mixed": FP32_MIXED}[precision] \
+        if isinstance(precision, str) else int(precision)
+    st.polish_iters = int(polish_iters)
+    st.stop_rule = STOP_RULES[stop_rule] if isinstance(stop_rule, str) else int(stop_rule)
+    st.osqp_rel = float(osqp_rel)
+    st.sweep = SWEEPS[sweep] if isinstance(sweep, str) else int(sweep)
+    return st
+
+
 class Solver:
     """One problem on the GPU. ``prob`` is a dict with m, n, row, col, val, b, c, cones
     (as made by ``instances``)."""
@@ -170,21 +198,8 @@ class Solver:
         val = _f64(prob["val"])
         b = _f64(prob["b"], m)
         c = _f64(prob["c"], n)
-        cones = np.asarray(prob["cones"], dtype=np.int64).reshape(-1, 2)
-        carr = (Cone * max(len(cones), 1))()
-        for q, (k, s) in enumerate(cones):
-            carr[q].kind = int(k)
-            carr[q].size = int(s)
-        st = Settings()
-        lib.mfs_default_settings(ctypes.byref(st))
-        st.mu = float(mu)
-        st.check_every = int(check_every)
-        st.precision = {"fp64": FP64, "fp32": FP32_MIXED, "mixed": FP32_MIXED}[precision] \
-            if isinstance(precision, str) else int(precision)
-        st.polish_iters = int(polish_iters)
-        st.stop_rule = STOP_RULES[stop_rule] if isinstance(stop_rule, str) else int(stop_rule)
-        st.osqp_rel = float(osqp_rel)
-        st.sweep = SWEEPS[sweep] if isinstance(sweep, str) else int(sweep)
+        carr, ncones = _cone_array(prob["cones"])
+        st = _settings(lib, mu, check_every, precision, polish_iters, stop_rule, osqp_rel, sweep)
         h = ctypes.c_void_p()
         stream_ptr = ctypes.c_void_p(int(stream)) if stream else None
         code = lib.mfs_create(m, n, len(row), row.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
@@ -192,11 +207,31 @@ class Solver:
                               val.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                               b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                               c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                              len(cones), carr, ctypes.byref(st), stream_ptr, ctypes.byref(h))
+                              ncones, carr, ctypes.byref(st), stream_ptr, ctypes.byref(h))
         if code != MFS_OK:
             raise MfsError(code, lib.mfs_last_error(None).decode())
         self._h = h
         self.m, self.n = m, n
+
+    @classmethod
+    def from_device(cls, m, n, nnz, row_ptr, col_ptr, val_ptr, b_ptr, c_ptr, cones, mu=1.0, check_every=25,
+                    precision="fp64", polish_iters=50, stream=None, stop_rule="kkt", osqp_rel=10.0, sweep="auto"):
+        """mfs_create_device: the COO (int64 row, col; float64 val), b and c (float64) given as device
+        pointers (ints, e.g. torch tensors' data_ptr()); cones as for the host form."""
+        self = cls.__new__(cls)
+        lib = load()
+        self._lib = lib
+        carr, ncones = _cone_array(cones)
+        st = _settings(lib, mu, check_every, precision, polish_iters, stop_rule, osqp_rel, sweep)
+        h = ctypes.c_void_p()
+        dp = [ctypes.c_void_p(int(p)) if p else None for p in (row_ptr, col_ptr, val_ptr, b_ptr, c_ptr)]
+        code = lib.mfs_create_device(int(m), int(n), int(nnz), *dp, ncones, carr, ctypes.byref(st),
+                                     ctypes.c_void_p(int(stream)) if stream else None, ctypes.byref(h))
+        if code != MFS_OK:
+            raise MfsError(code, lib.mfs_last_error(None).decode())
+        self._h = h
+        self.m, self.n = int(m), int(n)
+        return self
 
     def _check(self, code, ok=(MFS_OK,)):
         if code not in ok:
@@ -282,6 +317,12 @@ class Solver:
         lam = np.empty(self.m)
         self._check(self._lib.mfs_get_solution(self._h, _ptr(x), _ptr(lam), _ptr(z), _ptr(d)))
         return {"x": x, "lam": lam, "z": z, "delta": d}
+
+    def reduced_v(self):
+        """The reduced state's v = F_U (b - A x) - lambda/mu (host doubles)."""
+        v = np.empty(self.m)
+        self._check(self._lib.mfs_get_reduced_v(self._h, _ptr(v)))
+        return v
 
     def solution_device(self, x=None, lam=None, z=None, delta=None):
         args = [ctypes.c_void_p(int(p)) if p else None for p in (x, lam, z, delta)]
@@ -473,6 +514,12 @@ def _load_mlp():
     for name in ("mfs_mlp_get_params", "mfs_mlp_set_params", "mfs_mlp_get_grads"):
         getattr(lib, name).argtypes = [P, i32, P, P]
         getattr(lib, name).restype = st
+    lib.mfs_mlp_get_adam_state.argtypes = [P, i32, P, P, P, P, P]
+    lib.mfs_mlp_get_adam_state.restype = st
+    lib.mfs_mlp_get_weights_bf16.argtypes = [P, i32, P]
+    lib.mfs_mlp_get_weights_bf16.restype = st
+    lib.mfs_mlp_keep_grads.argtypes = [P, i32]
+    lib.mfs_mlp_keep_grads.restype = st
     lib.mfs_gemm_bf16.argtypes = [i64, i64, i64, P, P, P, i32, i32, P, i32, P]
     lib.mfs_gemm_bf16.restype = st
     lib._mlp_declared = True
@@ -588,6 +635,29 @@ class MLP:
             self._check(self._lib.mfs_mlp_get_grads(self._h, l, _ptr(gW), _ptr(gb)))
             out.append((gW, gb))
         return out
+
+    def adam_state(self):
+        """Per layer (mW, vW, mb, vb) host copies, and the number of Adam steps taken."""
+        out = []
+        step = ctypes.c_int64()
+        for l, (o, i) in enumerate(self.shapes()):
+            mW, vW = np.empty((o, i), np.float32), np.empty((o, i), np.float32)
+            mb, vb = np.empty(o, np.float32), np.empty(o, np.float32)
+            self._check(self._lib.mfs_mlp_get_adam_state(self._h, l, _ptr(mW), _ptr(vW), _ptr(mb), _ptr(vb),
+                                                         ctypes.byref(step)))
+            out.append((mW, vW, mb, vb))
+        return out, step.value
+
+    def weights_bf16(self, layer):
+        """Raw 16-bit patterns of the BF16 weight copy of a layer, [out][in]."""
+        o, i = self.shapes()[layer]
+        Wh = np.empty((o, i), np.uint16)
+        self._check(self._lib.mfs_mlp_get_weights_bf16(self._h, int(layer), _ptr(Wh)))
+        return Wh
+
+    def keep_grads(self, on=True):
+        """Make train_step store layer 3's weight gradient too (reported by grads())."""
+        self._check(self._lib.mfs_mlp_keep_grads(self._h, int(bool(on))))
 
 
 def _load_shared():

@@ -46,7 +46,49 @@ def main():
                              "err": err, "kkt_finite": bool(np.isfinite(r["kkt"]))})
         s.close()
     _, out["site"], out["index"] = mfs.bounds_record()
+    if checked:
+        out["static"] = static_case()
     print(json.dumps(out))
+
+
+def static_case():
+    """mfs_row_residuals_static under the checked build: a valid CSR matrix (no check may fail,
+    results equal the oracle's), then the same matrix with one column index planted outside [0, n):
+    the check records it (site 10) and skips that entry instead of reading past x."""
+    import torch
+    dev = torch.device("cuda", 0)
+    prob = I.small_lp(6, m=300, n=700)
+    order = np.lexsort((prob["col"], prob["row"]))
+    rows, cols, vals = prob["row"][order], prob["col"][order], prob["val"][order]
+    row_ptr = np.zeros(prob["m"] + 1, np.int64)
+    np.cumsum(np.bincount(rows, minlength=prob["m"]), out=row_ptr[1:])
+    rng = np.random.default_rng(1)
+    x, lam = rng.standard_normal(prob["n"]), rng.standard_normal(prob["m"])
+    orc = oracle.make_oracle(prob)
+    orc.set_state(x=x, lam=lam)
+    ref = orc.residuals()
+
+    def d(a, dt):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(dev)
+
+    res = {}
+    for planted in (False, True):
+        c = cols.astype(np.int32).copy()
+        if planted:
+            c[len(c) // 2] = prob["n"] + 5
+        t = [d(row_ptr, np.int32), d(c, np.int32), d(vals, np.float64), d(prob["b"], np.float64), d(x, np.float64),
+             d(lam, np.float64)]
+        out = torch.empty(8, dtype=torch.float64, device=dev)
+        mfs.bounds_record(reset=True)
+        mfs.row_residuals_static(prob["m"], prob["n"], *[a.data_ptr() for a in t], out.data_ptr())
+        torch.cuda.synchronize()
+        _, site, index = mfs.bounds_record(reset=True)
+        got = out.cpu().numpy()
+        key = "planted" if planted else "valid"
+        res[key + "_site"] = site
+        res[key + "_index"] = index
+        res[key + "_err"] = float(abs(got[1] - ref["nrm_res_p"]) / max(1.0, ref["nrm_res_p"]))
+    return res
 
 
 if __name__ == "__main__":

@@ -154,3 +154,69 @@ def test_fit_output_scaling_matches_fp64_statistics(count, dout):
     assert np.allclose(std, ref_std, rtol=1e-4, atol=0), np.abs(std / ref_std - 1).max()
     assert std[0] == np.float32(1e-3)
     net.close()
+
+
+def _f32(x):
+    return float(np.float32(x))
+
+
+def bf16_bits(a):
+    """Round-to-nearest-even FP32 -> BF16, as raw 16-bit patterns."""
+    t = torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16)
+    return t.view(torch.int16).numpy().view(np.uint16)
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_adam_steps_match_oracle(fused):
+    """Three optimiser steps against the FP64 Adam oracle (Kingma & Ba), each started from the
+    device's own state before the step: FP32 masters, both moments and the BF16 copy, for every
+    weight and bias. The hyperparameters are the device's FP32 values promoted to FP64, so only the
+    arithmetic differs. fused=True runs mfs_mlp_train_step, where layer 3's update happens in the
+    tensor-core GEMM epilogue; its gradient is kept (mfs_mlp_keep_grads) so that the oracle sees the
+    same one, and that gradient is itself checked against the FP64 MLP oracle."""
+    din, width, dout, B = 32, 128, 200, 64
+    net = mfs.MLP(din, width, dout, max_batch=B, seed=7)
+    if fused:
+        net.keep_grads(True)
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((B, din)).astype(np.float32)
+    T = (rng.standard_normal((B, dout)) * 2 + 0.5).astype(np.float32)
+    mean, std = T.mean(0), T.std(0) + 0.1
+    net.set_output_scaling(mean, std)
+    Xd, Td = torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev)
+    lr = 2e-3
+    hp = dict(beta1=_f32(0.9), beta2=_f32(0.999), eps=_f32(1e-8))
+    for t in range(1, 4):
+        P0 = net.params()
+        S0, t0 = net.adam_state()
+        assert t0 == t - 1
+        if fused:
+            net.train_step(B, Xd.data_ptr(), Td.data_ptr(), lr)
+        else:
+            net.backward(B, Xd.data_ptr(), Td.data_ptr())
+            net.adam_step(lr)
+        G = net.grads()
+        P1 = net.params()
+        S1, t1 = net.adam_state()
+        assert t1 == t
+        if fused and t == 1:
+            params = [(bf16_round(W), b.astype(np.float64)) for W, b in P0]
+            _, og = omlp.loss_and_grads(params, bf16_round(X), T, mean, std, store=bf16_round)
+            assert rel(G[2][0], og[2][0]) <= 1e-2, rel(G[2][0], og[2][0])
+        for l in range(3):
+            mW0, vW0, mb0, vb0 = S0[l]
+            mW1, vW1, mb1, vb1 = S1[l]
+            for name, p0, p1, g, m0, m1, v0, v1 in (("W", P0[l][0], P1[l][0], G[l][0], mW0, mW1, vW0, vW1),
+                                                     ("b", P0[l][1], P1[l][1], G[l][1], mb0, mb1, vb0, vb1)):
+                op, om, ov = omlp.adam_step(p0, g, m0, v0, t, _f32(lr), **hp)
+                g64 = np.asarray(g, np.float64)
+                mscale = hp["beta1"] * np.abs(m0) + (1 - hp["beta1"]) * np.abs(g64)
+                assert (np.abs(m1 - om) <= 1e-6 * mscale + 1e-30).all(), (t, l, name, "m")
+                assert (np.abs(v1 - ov) <= 1e-6 * ov + 1e-30).all(), (t, l, name, "v")
+                # FP32 rounding of the master weight, plus the FP32 bias corrections 1 - beta^t
+                # (cancellation: up to ~3e-5 of the step at t = 2, 3)
+                tol = 1e-7 * np.abs(op) + 5e-5 * np.abs(op - p0) + 1e-12
+                assert (np.abs(p1 - op) <= tol).all(), (t, l, name, np.abs(p1 - op).max())
+                assert np.abs(op - p0).max() > 0.5 * _f32(lr)  # the step moved the parameters
+            assert (net.weights_bf16(l) == bf16_bits(P1[l][0])).all(), (t, l)
+    net.close()

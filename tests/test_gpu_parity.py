@@ -231,6 +231,36 @@ def test_solve_mixed_precision_polishes_in_fp64():
     assert s.residuals()["kkt"] <= 1e-6
 
 
+@pytest.mark.parametrize("maker", ["small_lp", "socp"])
+def test_polish_handoff_matches_oracle(maker):
+    """The FP32 -> FP64 hand-off of mixed precision: k FP32 iterations, mfs_set_precision(FP64),
+    then P FP64 iterations. The promoted state (x, z, delta, lambda and the reduced form's v) must be
+    the FP32 state exactly (widening is exact); the oracle, seeded with that promoted state
+    (Algorithm 1's y and gamma rebuilt from it), runs the same P iterations in FP64 on the
+    unrounded data, as the device's FP64 iterate does, and both must agree element by element to
+    the FP64 tolerance."""
+    prob = I.small_lp(2, m=80, n=200) if maker == "small_lp" else I.socp(5, n=600, m=240)
+    mu = 1.3
+    s = mfs.Solver(prob, mu=mu, precision="fp32", polish_iters=50, check_every=25)
+    s.iterate(137)
+    before, v_before = s.solution(), s.reduced_v()
+    s.set_precision("fp64")
+    assert s.info()["precision"] == mfs.FP64
+    after, v_after = s.solution(), s.reduced_v()
+    for k in ("x", "z", "delta", "lam"):
+        assert np.array_equal(before[k], after[k]), k
+        assert np.array_equal(after[k], after[k].astype(np.float32).astype(np.float64)), k  # FP32 values
+    assert np.array_equal(v_before, v_after)
+    orc = oracle.make_oracle(prob, mu=mu)
+    orc.set_reduced_state(after["x"], after["z"], after["delta"], after["lam"], v_after)
+    for P in (1, 60):
+        s.iterate(P)
+        orc.iterate(P)
+        compare(s.solution(), orc.state(), TOL["fp64"], f"{maker} polish +{P}")
+    # the state moved away from the promoted FP32 values
+    assert np.abs(s.solution()["x"] - after["x"]).max() > 0
+
+
 def test_solve_max_iter():
     prob = I.small_lp(0)
     s = mfs.Solver(prob, check_every=10)

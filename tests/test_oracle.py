@@ -495,3 +495,31 @@ def test_reduced_form_tracks_literal_iteration(maker):
                             ("lam", red.lam, s.lam)):
             err = np.abs(a - bb).max() / max(1.0, np.abs(bb).max())
             assert err < 1e-12, (name, err)
+
+
+@pytest.mark.parametrize("maker", ["small_lp", "socp"])
+def test_literal_state_from_a_reduced_state(maker):
+    """Seeding Algorithm 1 from an arbitrary reduced state (x, z, delta, lambda, v) -- v not the one
+    (x, lambda) imply -- makes the literal iteration follow the separately written reduced loop
+    started from the same state; with v = F_U (b - A x) - lambda/mu the seeded y and gamma are the
+    C oracle's consistent warm-start state."""
+    prob = I.small_lp(1, m=40, n=100) if maker == "small_lp" else I.socp(seed=3, n=300, m=120, nnz_per_row=5)
+    mu = 1.7
+    rng = np.random.default_rng(5)
+    n, m = prob["n"], prob["m"]
+    x, z, d = rng.standard_normal(n), rng.standard_normal(n), rng.standard_normal(n)
+    lam, v = rng.standard_normal(m), rng.standard_normal(m)
+    orc = oracle.make_oracle(prob, mu=mu)
+    red = Reduced(prob, mu=mu)
+    red.x, red.z, red.delta, red.lam, red.v = x.copy(), z.copy(), d.copy(), lam.copy(), v.copy()
+    orc.set_reduced_state(x, z, d, lam, v)
+    orc.iterate(300)
+    red.iterate(300)
+    s = orc.state()
+    for name, a, bb in (("x", red.x, s.x), ("z", red.z, s.z), ("delta", red.delta, s.delta), ("lam", red.lam, s.lam)):
+        assert np.abs(a - bb).max() <= 1e-12 * max(1.0, np.abs(bb).max()), name
+    rho = (red.b - red.A @ x) / (1.0 + red.r)
+    orc.set_reduced_state(x, z, d, lam, rho - lam / mu)
+    y, g = orc.consistent_y_gamma(x, lam)
+    s = orc.state()
+    assert np.allclose(s.y, y, rtol=0, atol=1e-13) and np.array_equal(s.gam, g)

@@ -1,12 +1,14 @@
 """mfs_row_residuals_static: the allocation-free row-residual entry point, for callers that
 cannot allocate device memory when they need a residual (memory owned by another framework's
-pool, plugin callbacks that must not allocate, real-time loops). Its output must match the
-residuals the solver handle computes (mfs_residuals) for the same point, on two calls in a row
-that share the static scratch array. Kept in its own file so that it runs after every other test.
+pool, plugin callbacks that must not allocate, real-time loops). Its output must match the FP64
+oracle's residuals at the same point (x, lambda) and the solver handle's own (mfs_residuals), on two
+calls in a row that share the static scratch array, with every device allocation of the library
+made to fail meanwhile. Kept in its own file so that it runs after every other test.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_2203_05027_b300 import build, instances as I, mfs
 
 pytestmark = pytest.mark.gpu
@@ -22,7 +24,15 @@ def csr_of(prob):
     return row_ptr.astype(np.int32), cols.astype(np.int32), vals.astype(np.float64)
 
 
-def test_row_residuals_static_matches_solver_residuals():
+def check(got, ref, tol, label):
+    for k, name in enumerate(FIELDS):
+        if name is None:  # b^T lambda = -dobj
+            assert abs(got[k] + ref["dobj"]) <= tol * max(1.0, abs(ref["dobj"])), (label, k)
+            continue
+        assert abs(got[k] - ref[name]) <= tol * max(1.0, abs(ref[name])), (label, name, got[k], ref[name])
+
+
+def test_row_residuals_static_matches_oracle_and_solver():
     import torch
     build.build()
     mfs.load()
@@ -38,6 +48,7 @@ def test_row_residuals_static_matches_solver_residuals():
     t_b = d(prob["b"], np.float64)
     out = torch.empty(8, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
+    orc = oracle.make_oracle(prob)
 
     s = mfs.Solver(prob, precision="fp64")
     for call, iters in enumerate((60, 45)):
@@ -46,19 +57,27 @@ def test_row_residuals_static_matches_solver_residuals():
         sol = s.solution()
         t_x, t_l = d(sol["x"], np.float64), d(sol["lam"], np.float64)
         out.fill_(float("nan"))
-        mfs.row_residuals_static(m, n, t_ptr.data_ptr(), t_col.data_ptr(), t_val.data_ptr(), t_b.data_ptr(),
-                                 t_x.data_ptr(), t_l.data_ptr(), out.data_ptr(), stream.cuda_stream)
         torch.cuda.synchronize()
+        mfs.debug_fail_alloc_after(0)   # every device allocation by the library now fails
+        try:
+            mfs.row_residuals_static(m, n, t_ptr.data_ptr(), t_col.data_ptr(), t_val.data_ptr(), t_b.data_ptr(),
+                                     t_x.data_ptr(), t_l.data_ptr(), out.data_ptr(), stream.cuda_stream)
+            torch.cuda.synchronize()
+        finally:
+            mfs.debug_fail_alloc_after(-1)
         got = out.cpu().numpy()
-        for k, name in enumerate(FIELDS):
-            if name is None:
-                assert abs(got[k] + ref["dobj"]) <= 1e-9 * max(1.0, abs(ref["dobj"])), (call, k)
-                continue
-            assert abs(got[k] - ref[name]) <= 1e-9 * max(1.0, abs(ref[name])), (call, name, got[k], ref[name])
+        orc.set_state(x=sol["x"], lam=sol["lam"])   # the residuals depend on (x, lambda) only
+        check(got, orc.residuals(), 1e-9, ("oracle", call))
+        check(got, ref, 1e-9, ("mfs_residuals", call))
+    s.close()
 
 
 def test_row_residuals_static_rejects_sizes_beyond_its_scratch():
     mfs.load()
+    # out is NULL as well, so no launch can happen whichever check runs first
     with pytest.raises(mfs.MfsError) as e:
-        mfs.row_residuals_static(4_194_305, 10, 1, 1, 1, 1, 1, 1, 1)
+        mfs.row_residuals_static(4_194_305, 10, 1, 1, 1, 1, 1, 1, None)
+    assert e.value.status == mfs.MFS_ERR_INVALID
+    with pytest.raises(mfs.MfsError) as e:
+        mfs.row_residuals_static(10, 10, None, None, None, None, None, None, None)
     assert e.value.status == mfs.MFS_ERR_INVALID

@@ -247,7 +247,7 @@ __global__ void k_pad(const int4* __restrict__ desc, int nchunks, const int* __r
 // (block of the gathered index, segment, gathered index) -- a stable split of the group's entries,
 // which are already in (segment, gathered index) order, by block -- each 8-byte entry holding the
 // segment's index within the group (low 16 bits), the gathered index within the block (high 16
-// bits) and the FP32 value; then every warp's range padded to a multiple of LE entries.
+// bits) and the FP32 value; then every warp's range laid out over its lanes (k_stg_lanes).
 
 // segment of every entry: seg_of[k] = s for k in [ptr[s], ptr[s+1])
 __global__ void k_seg_of(const int* __restrict__ ptr, int nseg, int* __restrict__ seg_of) {
@@ -335,33 +335,128 @@ __global__ void k_stg_split(const int2* __restrict__ ent, const int* __restrict_
     }
 }
 
-// padded length of every warp range (a multiple of le)
-__global__ void k_stg_padlen(const int* __restrict__ split, long long nranges, int NW1, int le, int* __restrict__ plen) {
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nranges; r += (long long)gridDim.x * blockDim.x) {
-        const long long u = r / (NW1 - 1), w = r % (NW1 - 1);
-        const int len = split[u * NW1 + w + 1] - split[u * NW1 + w];
-        plen[r] = (len + le - 1) / le * le;
+// Lane layout of every warp range (mfs_staged.cuh): the range [st, en) of a (group, block, warp)
+// holds that warp's entries of the block in (segment, gathered index) order. With n entries it is
+// laid out in R = ceil(n / 32) rounds, lanes l < n - 32 (R - 1) taking R entries and the others
+// R - 1, lane l's entries at st + 32 r + l. Every run (the entries of one segment) goes to one lane,
+// consecutive and in order: runs longer than LONGRUN first, in their order, then the runs of
+// LONGRUN down to 2 entries, longest first, each into the lane with the most room left (the lowest
+// such lane); a run longer than that room fills it and its rest goes on the same way, piece j > 0
+// then adding into the segment's j-th overflow slot. Last, the single entries fill the lanes' room
+// in lane order. Phase 0 records each segment's largest number of pieces over the blocks; phase 1
+// writes the entries in place with their slots (the segment for piece 0, else its overflow slot).
+// The same steps in both phases give the same placement.
+constexpr int LONGRUN = 8;
+
+template <int PHASE>
+__global__ void k_stg_lanes(const int2* __restrict__ ent, const int* __restrict__ split, long long nranges, int NW1,
+                            int R, const int* __restrict__ grp, int* __restrict__ npieces, const int* __restrict__ ovf,
+                            int2* __restrict__ out) {
+    for (long long rg = blockIdx.x * (long long)blockDim.x + threadIdx.x; rg < nranges;
+         rg += (long long)gridDim.x * blockDim.x) {
+        const long long u = rg / (NW1 - 1);
+        const int w = (int)(rg % (NW1 - 1));
+        const int st = split[u * NW1 + w], en = split[u * NW1 + w + 1], n = en - st;
+        if (n <= 0) continue;
+        const int s0 = grp[u / R];
+        const int rounds = (n + 31) / 32, full = n - 32 * (rounds - 1);
+        int cap[32], fill[32];
+        for (int l = 0; l < 32; ++l) {
+            cap[l] = l < full ? rounds : rounds - 1;
+            fill[l] = 0;
+        }
+        auto seg_at = [&](int p) { return ent[p].x & 0xFFFF; };
+        auto run_end = [&](int p) {
+            const int sg = seg_at(p);
+            int q = p + 1;
+            while (q < en && seg_at(q) == sg) ++q;
+            return q;
+        };
+        auto put = [&](int p, int lane, int slot) {
+            if (PHASE == 1)
+                out[st + fill[lane] * 32 + lane] = make_int2((ent[p].x & (int)0xFFFF0000) | slot, ent[p].y);
+            --cap[lane];
+            ++fill[lane];
+        };
+        auto place = [&](int p, int len) {
+            const int sg = seg_at(p);
+            int j = 0;
+            while (len > 0) {
+                int best = 0;
+                for (int l = 1; l < 32; ++l)
+                    if (cap[l] > cap[best]) best = l;
+                const int t = len < cap[best] ? len : cap[best];
+                const int slot = j == 0 ? sg : (PHASE == 1 ? ovf[s0 + sg] + j - 1 : 0);
+                for (int i = 0; i < t; ++i) put(p + i, best, slot);
+                p += t;
+                len -= t;
+                ++j;
+            }
+            if (PHASE == 0 && j > 1) atomicMax(npieces + s0 + sg, j);
+        };
+        for (int p = st; p < en;) {  // long runs, in order
+            const int q = run_end(p);
+            if (q - p > LONGRUN) place(p, q - p);
+            p = q;
+        }
+        for (int L = LONGRUN; L >= 2; --L)  // shorter runs, longest first
+            for (int p = st; p < en;) {
+                const int q = run_end(p);
+                if (q - p == L) place(p, L);
+                p = q;
+            }
+        int lane = 0;  // single entries, lanes in order
+        for (int p = st; p < en;) {
+            const int q = run_end(p);
+            if (q - p == 1) {
+                while (cap[lane] == 0) ++lane;
+                put(p, lane, seg_at(p));
+            }
+            p = q;
+        }
     }
 }
 
-// Each warp range copied to its padded place (pstart: exclusive scan of the padded lengths), the
-// padding filled with zero-valued entries of the range's last segment, and the split table rewritten
-// in padded positions.
-__global__ void k_stg_pad(const int2* __restrict__ ent, const int* __restrict__ split, const int* __restrict__ pstart,
-                          long long nranges, int NW1, int2* __restrict__ pent, int* __restrict__ psplit,
-                          int total) {
-    const int lane = threadIdx.x & 31;
-    for (long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; r < nranges;
-         r += ((long long)gridDim.x * blockDim.x) >> 5) {
-        const long long u = r / (NW1 - 1), w = r % (NW1 - 1);
-        const int a = split[u * NW1 + w], e = split[u * NW1 + w + 1];
-        const int to = pstart[r];
-        const int plen = (r + 1 < nranges ? pstart[r + 1] : total) - to;
-        for (int q = lane; q < plen; q += 32)
-            pent[to + q] = q < e - a ? ent[a + q] : make_int2(ent[e - 1].x & 0xFFFF, 0);
-        if (lane == 0) {
-            psplit[u * NW1 + w] = to;
-            if (w == NW1 - 2) psplit[u * NW1 + w + 1] = to + plen;
+// One thread per group: overflow slots after the group's segments, allocated in segment order (so
+// that each warp's are contiguous: wovf), ovf[s] = the first one of segment s; fold_cnt = the
+// segments of each (group, warp) that have overflow slots; *slots_max = the largest group's slots.
+__global__ void k_stg_ovf(const int* __restrict__ grp, int G, const int* __restrict__ wseg, int NW1,
+                          const int* __restrict__ npieces, int* __restrict__ ovf, int* __restrict__ wovf,
+                          int* __restrict__ fold_cnt, int* __restrict__ slots_max) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const int a = grp[g], nseg = grp[g + 1] - a;
+        int slot = nseg;
+        for (int w = 0; w < NW1 - 1; ++w) {
+            wovf[g * NW1 + w] = slot;
+            int cnt = 0;
+            for (int t = wseg[g * NW1 + w]; t < wseg[g * NW1 + w + 1]; ++t) {
+                const int np = npieces[a + t];
+                if (np > 1) {
+                    ovf[a + t] = slot;
+                    slot += np - 1;
+                    ++cnt;
+                }
+            }
+            fold_cnt[g * (NW1 - 1) + w] = cnt;
+        }
+        wovf[g * NW1 + NW1 - 1] = slot;
+        atomicMax(slots_max, slot);
+    }
+}
+
+// The fold lists: for each (group, warp), its segments with overflow slots as (segment, first
+// overflow slot | (pieces - 1) << 16), in segment order, from fold_ptr (exclusive scan of fold_cnt).
+__global__ void k_stg_fold(const int* __restrict__ grp, int G, const int* __restrict__ wseg, int NW1,
+                           const int* __restrict__ npieces, const int* __restrict__ ovf, const int* __restrict__ fold_ptr,
+                           int2* __restrict__ fold) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const int a = grp[g];
+        for (int w = 0; w < NW1 - 1; ++w) {
+            int at = fold_ptr[g * (NW1 - 1) + w];
+            for (int t = wseg[g * NW1 + w]; t < wseg[g * NW1 + w + 1]; ++t) {
+                const int np = npieces[a + t];
+                if (np > 1) fold[at++] = make_int2(t, ovf[a + t] | ((np - 1) << 16));
+            }
         }
     }
 }

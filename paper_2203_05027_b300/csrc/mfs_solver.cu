@@ -283,33 +283,19 @@ void build_orders(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const i
     });
 }
 
-// Greedy chunking of segments (columns or rows) in order. A unit is one segment, or a whole
-// small Lorentz cone (columns only). A chunk takes units while it stays within WT nonzeros and
-// WC segments; a single segment longer than WT forms a (long) chunk of its own.
-inline int float_bits(float f) {
-    int i;
-    std::memcpy(&i, &f, sizeof i);
-    return i;
-}
-
-// Layout of one staged pass (mfs_staged.cuh) on the host.
+// Plan of one staged pass (mfs_staged.cuh), made on the host.
 struct StagedHost {
-    mfs::host::uvec<int2> ent;
-    std::vector<int> split, grp, wseg;
+    std::vector<int> grp, wseg;
     int G = 0, R = 0, maxg = 0;
 };
 
-// Segments (columns with their row indices, or rows with their column indices) in groups of
-// consecutive segments balanced by nonzeros (nominally `groups`, at most MAXG segments each); each
-// group's nonzeros sorted by (block of the gathered index, segment, gathered index) -- a stable
-// counting sort of the segment order -- and the warp ranges of every (group, block) cut at segment
-// boundaries.
-// rb: entries of the gathered vector per block; smem_limit: shared memory a CTA may use, which
-// bounds the group size. Returns false if not even small groups fit.
-bool build_staged(const std::vector<int>& ptr, const mfs::host::uvec<int>& idx, const mfs::host::uvec<double>& val,
-                  int nseg, int nother, int groups, int rb, int stages, int lane_e, size_t smem_limit,
-                  StagedHost& S, bool plan_only = false) {
-    using namespace mfs::host;
+// Plan of a staged pass: segments (columns, or rows) in groups of consecutive segments balanced by
+// nonzeros (nominally `groups`, at most MAXG segments each, and as many as the shared memory left
+// by the stages and split table holds), and each warp's segments within its group, balanced by
+// nonzeros. rb: entries of the gathered vector per block. Returns false if not even small groups
+// fit. The entries themselves are laid out on the GPU (staged_on_device).
+bool plan_staged(const std::vector<int>& ptr, int nseg, int nother, int groups, int rb, int stages,
+                 size_t smem_limit, StagedHost& S) {
     using mfs::staged::NW;
     const int RB = rb;
     const int64_t o = ptr[nseg];
@@ -339,8 +325,7 @@ bool build_staged(const std::vector<int>& ptr, const mfs::host::uvec<int>& idx, 
     S.G = (int)S.grp.size() - 1;
     S.maxg = 0;
     for (int g = 0; g < S.G; ++g) S.maxg = std::max(S.maxg, S.grp[g + 1] - S.grp[g]);
-    const int R = S.R, G = S.G;
-    // each warp's segments within its group, balanced by nonzeros
+    const int G = S.G;
     S.wseg.resize((size_t)G * (NW + 1));
     for (int g = 0; g < G; ++g) {
         const int a = S.grp[g], e = S.grp[g + 1];
@@ -354,81 +339,6 @@ bool build_staged(const std::vector<int>& ptr, const mfs::host::uvec<int>& idx, 
         }
         w[NW] = e - a;
     }
-    if (plan_only) return true;  // groups and warp segments only (the entries are built on the GPU)
-    uvec<int> key((size_t)o), loc((size_t)o);
-    parallel_ranges(G, std::min(threads_for(o), G), [&](int64_t g0, int64_t g1, int) {
-        for (int64_t g = g0; g < g1; ++g)
-            for (int sg = S.grp[g]; sg < S.grp[g + 1]; ++sg)
-                for (int q = ptr[sg]; q < ptr[sg + 1]; ++q) {
-                    key[q] = (int)g * R + idx[q] / RB;
-                    loc[q] = sg - S.grp[g];
-                }
-    });
-    uvec<int64_t> perm((size_t)o);
-    std::vector<int64_t> starts;
-    counting_sort(o, (int64_t)G * R, [&](int64_t q) { return (int64_t)key[q]; }, nullptr, perm.data(), &starts);
-    S.ent.resize((size_t)o);
-    parallel_ranges(o, threads_for(o), [&](int64_t p0, int64_t p1, int) {
-        for (int64_t p = p0; p < p1; ++p) {
-            const int64_t q = perm[p];
-            const int blk = key[q] % R;
-            const float a = (float)val[q];
-            S.ent[p] = make_int2(loc[q] | ((idx[q] - blk * RB) << 16), float_bits(a));
-        }
-    });
-    S.split.resize((size_t)G * R * (NW + 1));
-    parallel_ranges((int64_t)G * R, threads_for(o), [&](int64_t u0, int64_t u1, int) {
-        for (int64_t u = u0; u < u1; ++u) {
-            // warp w takes the entries of its own segments: the first entry at or after wseg[w]
-            const int st = (int)starts[u], en = (int)starts[u + 1];
-            const int* w = S.wseg.data() + (size_t)(u / R) * (NW + 1);
-            int* sp = S.split.data() + u * (NW + 1);
-            sp[0] = st;
-            for (int q = 1; q < NW; ++q) {
-                int lo2 = sp[q - 1], hi2 = en;
-                while (lo2 < hi2) {
-                    const int mid = (lo2 + hi2) >> 1;
-                    if ((S.ent[mid].x & 0xFFFF) < w[q])
-                        lo2 = mid + 1;
-                    else
-                        hi2 = mid;
-                }
-                sp[q] = lo2;
-            }
-            sp[NW] = en;
-        }
-    });
-    // pad every warp range to a multiple of lane_e entries (zero values, the range's last segment, so
-    // they fall into its last sum) so that a lane loads its lane_e entries with 32-byte loads
-    const int LE = lane_e;
-    std::vector<int64_t> pstart((size_t)G * R + 1, 0);
-    parallel_ranges((int64_t)G * R, threads_for(o), [&](int64_t u0, int64_t u1, int) {
-        for (int64_t u = u0; u < u1; ++u) {
-            const int* sp = S.split.data() + u * (NW + 1);
-            int64_t len = 0;
-            for (int w = 0; w < NW; ++w) len += (sp[w + 1] - sp[w] + LE - 1) / LE * LE;
-            pstart[u + 1] = len;
-        }
-    });
-    for (int64_t u = 0; u < (int64_t)G * R; ++u) pstart[u + 1] += pstart[u];
-    const int64_t plen = pstart[(size_t)G * R];
-    if (plen >= INT32_MAX) return false;
-    uvec<int2> pent((size_t)plen);
-    parallel_ranges((int64_t)G * R, threads_for(o), [&](int64_t u0, int64_t u1, int) {
-        for (int64_t u = u0; u < u1; ++u) {
-            int* sp = S.split.data() + u * (NW + 1);
-            int64_t at = pstart[u];
-            for (int w = 0; w < NW; ++w) {
-                const int a = sp[w], e = sp[w + 1];
-                sp[w] = (int)at;
-                for (int q = a; q < e; ++q) pent[at++] = S.ent[q];
-                if (e > a)
-                    for (int q = e; (q - a) % LE != 0; ++q) pent[at++] = make_int2(S.ent[e - 1].x & 0xFFFF, 0);
-            }
-            sp[NW] = (int)at;
-        }
-    });
-    S.ent.swap(pent);
     return true;
 }
 
@@ -898,7 +808,7 @@ void launch_col(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
     if constexpr (std::is_same<T, float>::value) {
         if (staged_col(s)) {
             const StagedArgsT& g = s->stg_col;
-            launch_dep(MFS_STAGED_COL, std::min(g.G, s->num_sms), mfs::staged::NTS + 32,
+            launch_dep(MFS_STAGED_COL, std::min(g.G, s->num_sms), mfs::staged::NTHREADS,
                        mfs::staged::smem_bytes(mfs::staged::RB_COL, mfs::staged::S_COL, g.maxg_pad, g.R), st, g, a);
             return;
         }
@@ -921,7 +831,7 @@ void launch_row_mode(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
     if constexpr (std::is_same<T, float>::value && MODE == 0) {
         if (staged_row(s)) {
             const StagedArgsT& g = s->stg_row;
-            launch_dep(MFS_STAGED_ROW, std::min(g.G * g.halves, s->num_sms), mfs::staged::NTS + 32,
+            launch_dep(MFS_STAGED_ROW, std::min(g.G * g.halves, s->num_sms), mfs::staged::NTHREADS,
                        mfs::staged::smem_bytes(mfs::staged::RB_ROW, mfs::staged::S_ROW, g.maxg_pad, g.R), st, g, a);
             if (g.halves > 1)
                 launch_dep(mfs::staged::k_row_combine, (int)std::min<int64_t>((s->m + 255) / 256, 8 * s->num_sms), 256,
@@ -1163,12 +1073,15 @@ mfs_status alloc_state(mfs_solver* s, State<T>& st, const HostProblem& P, const 
 // and the gathered vector small against its nonzeros (every CTA reads the whole vector).
 // The staged layout of one pass built on the GPU (mfs_setup.cuh) from a device order (segment
 // pointers, gathered indices, FP64 values), for the plan S (groups and warp segments) made on the
-// host. The result equals build_staged's; g receives the entry array, split table, group and warp
-// segment arrays.
+// host: the entries split by block, the warp ranges, the lane layout with its overflow slots and
+// fold lists. *ok is false (and nothing kept) when a group's sums and overflow sums would not fit
+// in shared memory (smem_limit) or in the 16-bit slot field.
 mfs_status staged_on_device(mfs_solver* s, const StagedHost& S, const int* d_ptr, int nseg, int64_t o,
-                            const int* d_idx, const double* d_val, int rb, int lane_e, mfs::staged::StagedArgs& g) {
+                            const int* d_idx, const double* d_val, int rb, int stages, size_t smem_limit,
+                            mfs::staged::StagedArgs& g, bool* ok) {
     namespace su = mfs::setup;
     using mfs::staged::NW;
+    *ok = false;
     const int G = S.G, R = S.R, NW1 = NW + 1;
     const int64_t nb = (int64_t)G * R, nr = nb * NW;
     cudaStream_t st = s->stream;
@@ -1188,19 +1101,24 @@ mfs_status staged_on_device(mfs_solver* s, const StagedHost& S, const int* d_ptr
         tmp.push_back(*q);
         return MFS_OK;
     };
-    int *grp = nullptr, *wseg = nullptr, *psplit = nullptr;
+    int *grp = nullptr, *wseg = nullptr, *split = nullptr, *wovf = nullptr, *fold_ptr = nullptr;
     TRY(upload(s, &grp, S.grp.data(), S.grp.size()));
     TRY(upload(s, &wseg, S.wseg.data(), S.wseg.size()));
-    TRY(dalloc(s, &psplit, (size_t)nb * NW1));
-    int *segof = nullptr, *cnt = nullptr, *bstart = nullptr, *split = nullptr, *plen = nullptr, *pstart = nullptr;
-    int2* ent = nullptr;
+    TRY(dalloc(s, &split, (size_t)nb * NW1));
+    TRY(dalloc(s, &wovf, (size_t)G * NW1));
+    TRY(dalloc(s, &fold_ptr, (size_t)G * NW + 1));
+    int *segof = nullptr, *cnt = nullptr, *bstart = nullptr, *npieces = nullptr, *ovf = nullptr, *fold_cnt = nullptr,
+        *slots_max = nullptr;
+    int2 *ent = nullptr, *lent = nullptr;
     TRY(grab((void**)&segof, (size_t)o * sizeof(int)));
     TRY(grab((void**)&cnt, (size_t)nb * sizeof(int)));
     TRY(grab((void**)&bstart, (size_t)nb * sizeof(int)));
     TRY(grab((void**)&ent, (size_t)o * sizeof(int2)));
-    TRY(grab((void**)&split, (size_t)nb * NW1 * sizeof(int)));
-    TRY(grab((void**)&plen, (size_t)nr * sizeof(int)));
-    TRY(grab((void**)&pstart, (size_t)nr * sizeof(int)));
+    TRY(grab((void**)&npieces, (size_t)std::max(nseg, 1) * sizeof(int)));
+    TRY(grab((void**)&ovf, (size_t)std::max(nseg, 1) * sizeof(int)));
+    TRY(grab((void**)&fold_cnt, (size_t)G * NW * sizeof(int)));
+    TRY(grab((void**)&slots_max, sizeof(int)));
+    TRY(dalloc(s, &lent, (size_t)std::max<int64_t>(o, 1)));
     su::k_seg_of<<<grid, 256, 0, st>>>(d_ptr, nseg, segof);
     su::k_stg_count<<<G, 256, (size_t)R * sizeof(int), st>>>(d_ptr, grp, d_idx, R, rb, cnt);
     TRY(device_scan(s, cnt, bstart, nb, nullptr));
@@ -1209,19 +1127,34 @@ mfs_status staged_on_device(mfs_solver* s, const StagedHost& S, const int* d_ptr
     su::k_stg_scatter<<<G, su::SNT, scat_smem, st>>>(d_ptr, grp, segof, d_idx, d_val, R, rb, bstart, ent);
     su::k_stg_split<<<(int)std::min<int64_t>((nb + 255) / 256, grid), 256, 0, st>>>(ent, bstart, cnt, wseg, R, (int)nb,
                                                                                    NW1, split);
-    su::k_stg_padlen<<<grid, 256, 0, st>>>(split, nr, NW1, lane_e, plen);
-    int total = 0;
-    TRY(device_scan(s, plen, pstart, nr, &total));
-    int2* pent = nullptr;
-    TRY(dalloc(s, &pent, (size_t)std::max(total, 1)));
-    su::k_stg_pad<<<grid, 256, 0, st>>>(ent, split, pstart, nr, NW1, pent, psplit, total);
+    CUDA_TRY(s, cudaMemsetAsync(npieces, 0, (size_t)std::max(nseg, 1) * sizeof(int), st));
+    CUDA_TRY(s, cudaMemsetAsync(slots_max, 0, sizeof(int), st));
+    const int lgrid = (int)std::min<int64_t>((nr + 127) / 128, 64 * s->num_sms);
+    su::k_stg_lanes<0><<<lgrid, 128, 0, st>>>(ent, split, nr, NW1, R, grp, npieces, nullptr, nullptr);
+    su::k_stg_ovf<<<(G + 127) / 128, 128, 0, st>>>(grp, G, wseg, NW1, npieces, ovf, wovf, fold_cnt, slots_max);
+    int nfold = 0;
+    TRY(device_scan(s, fold_cnt, fold_ptr, (int64_t)G * NW, &nfold));
+    CUDA_TRY(s, cudaMemcpyAsync(fold_ptr + (size_t)G * NW, &nfold, sizeof(int), cudaMemcpyHostToDevice, st));
+    int2* fold = nullptr;
+    TRY(dalloc(s, &fold, (size_t)std::max(nfold, 1)));
+    su::k_stg_fold<<<(G + 127) / 128, 128, 0, st>>>(grp, G, wseg, NW1, npieces, ovf, fold_ptr, fold);
+    su::k_stg_lanes<1><<<lgrid, 128, 0, st>>>(ent, split, nr, NW1, R, grp, nullptr, ovf, lent);
+    int hmax = 0;
+    CUDA_TRY(s, cudaMemcpyAsync(&hmax, slots_max, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(s, cudaGetLastError());
     CUDA_TRY(s, cudaStreamSynchronize(st));
-    g.ent = pent;
-    g.split = psplit;
+    const int slots = (hmax + 3) / 4 * 4;
+    if (slots >= mfs::staged::MAXSLOT || mfs::staged::smem_bytes(rb, stages, slots, R) > smem_limit) return MFS_OK;
+    g.ent = lent;
+    g.split = split;
     g.grp = grp;
     g.wseg = wseg;
-    g.nent = total;
+    g.wovf = wovf;
+    g.fold_ptr = fold_ptr;
+    g.fold = fold;
+    g.nent = (int)o;
+    g.maxg_pad = slots;
+    *ok = true;
     return MFS_OK;
 }
 
@@ -1230,50 +1163,52 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
     int optin = 0;
     CUDA_TRY(s, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
     StagedHost C, W;
-    const bool dev = P.dev.on;  // the orders live on the device: plan on the host, build there
-    if (!build_staged(P.col_ptr, P.csc_row, P.csc_val, P.n, P.m, s->num_sms, RB_COL, S_COL, LE_COL, (size_t)optin,
-                      C, dev) ||
-        !build_staged(P.row_ptr, P.csr_col, P.csr_val, P.m, P.n, std::max(1, s->num_sms / ROW_HALVES), RB_ROW,
-                      S_ROW, LE_ROW, (size_t)optin, W, dev))
+    if (!plan_staged(P.col_ptr, P.n, P.m, s->num_sms, RB_COL, S_COL, (size_t)optin, C) ||
+        !plan_staged(P.row_ptr, P.m, P.n, std::max(1, s->num_sms / ROW_HALVES), RB_ROW, S_ROW, (size_t)optin, W))
         return MFS_OK;  // vectors too long for the split tables: chunked sweeps only
-    std::vector<float> rsq(std::max(P.m, 1), 0.f);
-    if (!dev) mfs::host::parallel_ranges(P.m, mfs::host::threads_for(P.o), [&](int64_t i0, int64_t i1, int) {
-        for (int64_t i = i0; i < i1; ++i) {
-            double r = 0.0;
-            for (int q = P.row_ptr[i]; q < P.row_ptr[i + 1]; ++q) {
-                const double a = (double)(float)P.csr_val[q];
-                r += a * a;
-            }
-            rsq[i] = (float)r;
+    // the orders on the device: where the host built them, uploaded for the set-up only
+    const bool dev = P.dev.on;
+    const int *crow = P.dev.crow, *rcol = P.dev.rcol;
+    const double *cval = P.dev.cval, *rval = P.dev.rval;
+    std::vector<void*> tmp;
+    struct Free {
+        std::vector<void*>& v;
+        ~Free() {
+            for (void* q : v) cudaFree(q);
         }
-    });
+    } release{tmp};
+    if (!dev) {
+        auto up = [&](const void* src, size_t bytes, const void** dst) -> mfs_status {
+            void* q = nullptr;
+            cudaError_t e = mfs::device_malloc(&q, std::max<size_t>(bytes, 16));
+            if (e != cudaSuccess)
+                return fail(s, e == cudaErrorMemoryAllocation ? MFS_ERR_OOM : MFS_ERR_CUDA,
+                            std::string("cudaMalloc: ") + cudaGetErrorString(e));
+            tmp.push_back(q);
+            if (bytes) CUDA_TRY(s, cudaMemcpyAsync(q, src, bytes, cudaMemcpyHostToDevice, s->stream));
+            *dst = q;
+            return MFS_OK;
+        };
+        TRY(up(P.csc_row.data(), (size_t)P.o * sizeof(int), (const void**)&crow));
+        TRY(up(P.csc_val.data(), (size_t)P.o * sizeof(double), (const void**)&cval));
+        TRY(up(P.csr_col.data(), (size_t)P.o * sizeof(int), (const void**)&rcol));
+        TRY(up(P.csr_val.data(), (size_t)P.o * sizeof(double), (const void**)&rval));
+    }
+    StagedArgs gc{}, gr{};
+    bool okc = false, okr = false;
+    TRY(staged_on_device(s, C, s->col_ptr, P.n, P.o, crow, cval, RB_COL, S_COL, (size_t)optin, gc, &okc));
+    if (!okc) return MFS_OK;
+    TRY(staged_on_device(s, W, s->row_ptr, P.m, P.o, rcol, rval, RB_ROW, S_ROW, (size_t)optin, gr, &okr));
+    if (!okr) return MFS_OK;
     TRY(dalloc(s, &s->stg_err, 1));
     CUDA_TRY(s, cudaMemsetAsync(s->stg_err, 0, sizeof(int), s->stream));
     CUDA_TRY(s, cudaMallocHost(&s->h_err, sizeof(int)));
     *s->h_err = 0;
-    auto fill = [&](StagedHost& H, StagedArgs& g, const float* vec, int halves, int nseg) -> mfs_status {
-        if (!dev) {
-            int2* ent = nullptr;
-            int *split = nullptr, *grp = nullptr, *wseg = nullptr;
-            TRY(upload(s, &ent, H.ent.data(), H.ent.size()));
-            TRY(upload(s, &split, H.split.data(), H.split.size()));
-            TRY(upload(s, &grp, H.grp.data(), H.grp.size()));
-            TRY(upload(s, &wseg, H.wseg.data(), H.wseg.size()));
-            g.ent = ent;
-            g.split = split;
-            g.grp = grp;
-            g.wseg = wseg;
-            g.nent = (int)H.ent.size();
-        } else if (&g == &s->stg_col) {
-            TRY(staged_on_device(s, H, s->col_ptr, P.n, P.o, P.dev.crow, P.dev.cval, RB_COL, LE_COL, g));
-        } else {
-            TRY(staged_on_device(s, H, s->row_ptr, P.m, P.o, P.dev.rcol, P.dev.rval, RB_ROW, LE_ROW, g));
-        }
+    auto fill = [&](const StagedHost& H, StagedArgs& g, const float* vec, int halves, int nseg) -> mfs_status {
         g.vec = vec;
         g.err = s->stg_err;
         g.G = H.G;
         g.R = H.R;
-        g.maxg_pad = (H.maxg + 3) / 4 * 4;
         g.halves = halves;
         g.nseg = nseg;
         g.part = nullptr;
@@ -1282,18 +1217,17 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
         g.no_loads = 0;
         return MFS_OK;
     };
+    s->stg_col = gc;
+    s->stg_row = gr;
     TRY(fill(C, s->stg_col, s->s32.v, 1, P.n));
     TRY(fill(W, s->stg_row, s->s32.x, ROW_HALVES, P.m));
     float* d_rsq = nullptr;
-    if (dev) {
-        TRY(dalloc(s, &d_rsq, (size_t)std::max(P.m, 1)));
-        if (P.m > 0)
-            mfs::setup::k_row_sq<<<(int)std::min<int64_t>((P.m + 255) / 256, 8 * s->num_sms), 256, 0, s->stream>>>(
-                s->row_ptr, P.dev.rval, P.m, d_rsq);
-        CUDA_TRY(s, cudaGetLastError());
-    } else {
-        TRY(upload(s, &d_rsq, rsq.data(), rsq.size()));
-    }
+    TRY(dalloc(s, &d_rsq, (size_t)std::max(P.m, 1)));
+    if (P.m > 0)
+        mfs::setup::k_row_sq<<<(int)std::min<int64_t>((P.m + 255) / 256, 8 * s->num_sms), 256, 0, s->stream>>>(
+            s->row_ptr, rval, P.m, d_rsq);
+    CUDA_TRY(s, cudaGetLastError());
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));  // the uploaded orders are freed on return
     s->stg_row.rsq = d_rsq;
     // the limit is a property of the kernel, shared by all solvers: allow the device's maximum
     CUDA_TRY(s, cudaFuncSetAttribute(MFS_STAGED_COL, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -1992,7 +1926,7 @@ mfs_status mfs_debug_staged_wait_test(mfs_solver* s) {
     g.spin = 64;
     g.no_loads = 1;
     const SweepArgs<float> a = sweep_args(s, s->s32);
-    MFS_STAGED_COL<<<std::min(g.G, s->num_sms), mfs::staged::NTS + 32,
+    MFS_STAGED_COL<<<std::min(g.G, s->num_sms), mfs::staged::NTHREADS,
                      mfs::staged::smem_bytes(mfs::staged::RB_COL, mfs::staged::S_COL, g.maxg_pad, g.R), s->stream>>>(g, a);
     CUDA_TRY(s, cudaGetLastError());
     CUDA_TRY(s, cudaMemcpyAsync(s->h_err, s->stg_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));

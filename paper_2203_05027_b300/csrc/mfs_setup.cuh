@@ -417,47 +417,56 @@ __global__ void k_stg_lanes(const int2* __restrict__ ent, const int* __restrict_
     }
 }
 
-// One thread per group: overflow slots after the group's segments, allocated in segment order (so
-// that each warp's are contiguous: wovf), ovf[s] = the first one of segment s; fold_cnt = the
-// segments of each (group, warp) that have overflow slots; *slots_max = the largest group's slots.
-__global__ void k_stg_ovf(const int* __restrict__ grp, int G, const int* __restrict__ wseg, int NW1,
-                          const int* __restrict__ npieces, int* __restrict__ ovf, int* __restrict__ wovf,
-                          int* __restrict__ fold_cnt, int* __restrict__ slots_max) {
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
-        const int a = grp[g], nseg = grp[g + 1] - a;
-        int slot = nseg;
-        for (int w = 0; w < NW1 - 1; ++w) {
-            wovf[g * NW1 + w] = slot;
-            int cnt = 0;
-            for (int t = wseg[g * NW1 + w]; t < wseg[g * NW1 + w + 1]; ++t) {
-                const int np = npieces[a + t];
-                if (np > 1) {
-                    ovf[a + t] = slot;
-                    slot += np - 1;
-                    ++cnt;
-                }
-            }
-            fold_cnt[g * (NW1 - 1) + w] = cnt;
-        }
-        wovf[g * NW1 + NW1 - 1] = slot;
-        atomicMax(slots_max, slot);
+// Overflow slots, from the largest number of pieces of each segment over the blocks (npieces; 0 or
+// 1: none). c1[s] = the segment's overflow slots, c2[s] = 1 if it has any; their exclusive scans
+// (device-wide, so over all groups at once) place everything: a group's overflow slots follow its
+// segments, allocated in segment order, so that each warp's are contiguous.
+__global__ void k_stg_ovf_counts(const int* __restrict__ npieces, int nseg, int* __restrict__ c1, int* __restrict__ c2) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nseg; t += gridDim.x * blockDim.x) {
+        const int np = npieces[t];
+        c1[t] = np > 1 ? np - 1 : 0;
+        c2[t] = np > 1 ? 1 : 0;
     }
 }
 
-// The fold lists: for each (group, warp), its segments with overflow slots as (segment, first
-// overflow slot | (pieces - 1) << 16), in segment order, from fold_ptr (exclusive scan of fold_cnt).
-__global__ void k_stg_fold(const int* __restrict__ grp, int G, const int* __restrict__ wseg, int NW1,
-                           const int* __restrict__ npieces, const int* __restrict__ ovf, const int* __restrict__ fold_ptr,
-                           int2* __restrict__ fold) {
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
-        const int a = grp[g];
-        for (int w = 0; w < NW1 - 1; ++w) {
-            int at = fold_ptr[g * (NW1 - 1) + w];
-            for (int t = wseg[g * NW1 + w]; t < wseg[g * NW1 + w + 1]; ++t) {
-                const int np = npieces[a + t];
-                if (np > 1) fold[at++] = make_int2(t, ovf[a + t] | ((np - 1) << 16));
-            }
-        }
+// group of segment s: the last g with grp[g] <= s
+__device__ __forceinline__ int group_of(const int* __restrict__ grp, int G, int s) {
+    int lo = 0, hi = G;  // grp[lo] <= s < grp[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (grp[mid] <= s) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Per segment with overflow slots: ovf[s] = its first overflow slot within the group (s1, s2: the
+// exclusive scans of c1, c2, each with its total at index nseg) and its fold entry
+// (segment within the group, first overflow slot | (pieces - 1) << 16) at position s2[s].
+__global__ void k_stg_ovf_place(const int* __restrict__ grp, int G, const int* __restrict__ npieces,
+                                const int* __restrict__ s1, const int* __restrict__ s2, int nseg,
+                                int* __restrict__ ovf, int2* __restrict__ fold) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nseg; t += gridDim.x * blockDim.x) {
+        const int np = npieces[t];
+        if (np <= 1) continue;
+        const int g = group_of(grp, G, t), a = grp[g];
+        const int slot = (grp[g + 1] - a) + (s1[t] - s1[a]);
+        ovf[t] = slot;
+        fold[s2[t]] = make_int2(t - a, slot | ((np - 1) << 16));
+    }
+}
+
+// Per (group, warp): its first overflow slot (wovf, G x NW1, the last one the group's end) and the
+// start of its fold entries (fold_ptr, G * (NW1 - 1) + 1); *slots_max = the largest group's slots.
+__global__ void k_stg_ovf_warps(const int* __restrict__ grp, int G, const int* __restrict__ wseg, int NW1,
+                                const int* __restrict__ s1, const int* __restrict__ s2, int nseg,
+                                int* __restrict__ wovf, int* __restrict__ fold_ptr, int* __restrict__ slots_max) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < G * NW1; q += gridDim.x * blockDim.x) {
+        const int g = q / NW1, w = q % NW1, a = grp[g], nseg_g = grp[g + 1] - a;
+        const int at = a + wseg[q];
+        wovf[q] = nseg_g + (s1[at] - s1[a]);
+        if (w < NW1 - 1) fold_ptr[g * (NW1 - 1) + w] = s2[at];
+        if (w == NW1 - 1) atomicMax(slots_max, nseg_g + (s1[at] - s1[a]));
+        if (q == 0) fold_ptr[G * (NW1 - 1)] = s2[nseg];
     }
 }
 

@@ -1107,16 +1107,20 @@ mfs_status staged_on_device(mfs_solver* s, const StagedHost& S, const int* d_ptr
     TRY(dalloc(s, &split, (size_t)nb * NW1));
     TRY(dalloc(s, &wovf, (size_t)G * NW1));
     TRY(dalloc(s, &fold_ptr, (size_t)G * NW + 1));
-    int *segof = nullptr, *cnt = nullptr, *bstart = nullptr, *npieces = nullptr, *ovf = nullptr, *fold_cnt = nullptr,
-        *slots_max = nullptr;
+    int *segof = nullptr, *cnt = nullptr, *bstart = nullptr, *npieces = nullptr, *ovf = nullptr, *c1 = nullptr,
+        *c2 = nullptr, *s1 = nullptr, *s2 = nullptr, *slots_max = nullptr;
     int2 *ent = nullptr, *lent = nullptr;
+    const size_t ns1 = (size_t)nseg + 1;
     TRY(grab((void**)&segof, (size_t)o * sizeof(int)));
     TRY(grab((void**)&cnt, (size_t)nb * sizeof(int)));
     TRY(grab((void**)&bstart, (size_t)nb * sizeof(int)));
     TRY(grab((void**)&ent, (size_t)o * sizeof(int2)));
-    TRY(grab((void**)&npieces, (size_t)std::max(nseg, 1) * sizeof(int)));
-    TRY(grab((void**)&ovf, (size_t)std::max(nseg, 1) * sizeof(int)));
-    TRY(grab((void**)&fold_cnt, (size_t)G * NW * sizeof(int)));
+    TRY(grab((void**)&npieces, ns1 * sizeof(int)));
+    TRY(grab((void**)&ovf, ns1 * sizeof(int)));
+    TRY(grab((void**)&c1, ns1 * sizeof(int)));
+    TRY(grab((void**)&c2, ns1 * sizeof(int)));
+    TRY(grab((void**)&s1, ns1 * sizeof(int)));
+    TRY(grab((void**)&s2, ns1 * sizeof(int)));
     TRY(grab((void**)&slots_max, sizeof(int)));
     TRY(dalloc(s, &lent, (size_t)std::max<int64_t>(o, 1)));
     su::k_seg_of<<<grid, 256, 0, st>>>(d_ptr, nseg, segof);
@@ -1127,17 +1131,22 @@ mfs_status staged_on_device(mfs_solver* s, const StagedHost& S, const int* d_ptr
     su::k_stg_scatter<<<G, su::SNT, scat_smem, st>>>(d_ptr, grp, segof, d_idx, d_val, R, rb, bstart, ent);
     su::k_stg_split<<<(int)std::min<int64_t>((nb + 255) / 256, grid), 256, 0, st>>>(ent, bstart, cnt, wseg, R, (int)nb,
                                                                                    NW1, split);
-    CUDA_TRY(s, cudaMemsetAsync(npieces, 0, (size_t)std::max(nseg, 1) * sizeof(int), st));
+    CUDA_TRY(s, cudaMemsetAsync(npieces, 0, ns1 * sizeof(int), st));
     CUDA_TRY(s, cudaMemsetAsync(slots_max, 0, sizeof(int), st));
     const int lgrid = (int)std::min<int64_t>((nr + 127) / 128, 64 * s->num_sms);
     su::k_stg_lanes<0><<<lgrid, 128, 0, st>>>(ent, split, nr, NW1, R, grp, npieces, nullptr, nullptr);
-    su::k_stg_ovf<<<(G + 127) / 128, 128, 0, st>>>(grp, G, wseg, NW1, npieces, ovf, wovf, fold_cnt, slots_max);
-    int nfold = 0;
-    TRY(device_scan(s, fold_cnt, fold_ptr, (int64_t)G * NW, &nfold));
-    CUDA_TRY(s, cudaMemcpyAsync(fold_ptr + (size_t)G * NW, &nfold, sizeof(int), cudaMemcpyHostToDevice, st));
+    // overflow slots and fold lists from two device-wide scans
+    su::k_stg_ovf_counts<<<grid, 256, 0, st>>>(npieces, nseg, c1, c2);
+    int tot1 = 0, nfold = 0;
+    TRY(device_scan(s, c1, s1, nseg, &tot1));
+    TRY(device_scan(s, c2, s2, nseg, &nfold));
+    CUDA_TRY(s, cudaMemcpyAsync(s1 + nseg, &tot1, sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(s, cudaMemcpyAsync(s2 + nseg, &nfold, sizeof(int), cudaMemcpyHostToDevice, st));
     int2* fold = nullptr;
     TRY(dalloc(s, &fold, (size_t)std::max(nfold, 1)));
-    su::k_stg_fold<<<(G + 127) / 128, 128, 0, st>>>(grp, G, wseg, NW1, npieces, ovf, fold_ptr, fold);
+    su::k_stg_ovf_place<<<grid, 256, 0, st>>>(grp, G, npieces, s1, s2, nseg, ovf, fold);
+    su::k_stg_ovf_warps<<<(G * NW1 + 255) / 256, 256, 0, st>>>(grp, G, wseg, NW1, s1, s2, nseg, wovf, fold_ptr,
+                                                                slots_max);
     su::k_stg_lanes<1><<<lgrid, 128, 0, st>>>(ent, split, nr, NW1, R, grp, nullptr, ovf, lent);
     int hmax = 0;
     CUDA_TRY(s, cudaMemcpyAsync(&hmax, slots_max, sizeof(int), cudaMemcpyDeviceToHost, st));

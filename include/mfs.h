@@ -70,11 +70,12 @@ enum { MFS_STOP_KKT = 0, MFS_STOP_SCS_L2 = 1, MFS_STOP_OSQP_INF = 2 };
 /* Sweep kernels of the FP32 iteration (mfs_set_sweep). MFS_SWEEP_CHUNKED: one warp per chunk of
    at most 256 nonzeros, the gathers served by L2 (every problem). MFS_SWEEP_STAGED: one CTA per
    group of columns (rows), the gathered vector streamed through shared memory in 64 KB blocks and
-   the nonzeros stored sorted by block (FP32_MIXED solvers without Lorentz cones). MFS_SWEEP_AUTO
-   (default): where the staged layout is built on the GPU (COO input in column order) for a matrix
-   with at least 2^20 nonzeros, the staged column pass if it has at least 8 nonzeros per row and
-   the staged row pass if it has at least 4 per column; chunked otherwise. All compute the same
-   iteration; their FP32 sums run in different orders. */
+   the nonzeros stored sorted by block (FP32_MIXED solvers; Lorentz cones of at most 64 columns are
+   projected in the column pass's epilogue, larger ones by their own kernel as in the chunked
+   sweeps). MFS_SWEEP_AUTO (default): where the staged layout is built on the GPU (COO input in
+   column order) for a matrix with at least 2^20 nonzeros, the staged column pass if it has at
+   least 8 nonzeros per row and the staged row pass if it has at least 4 per column; chunked
+   otherwise. All compute the same iteration; their FP32 sums run in different orders. */
 enum { MFS_SWEEP_AUTO = 0, MFS_SWEEP_CHUNKED = 1, MFS_SWEEP_STAGED = 2 };
 
 typedef struct {
@@ -94,8 +95,8 @@ typedef struct {
                              OSQP tolerances 1e-4 and 1e-3 at tol = 1e-4) */
     int32_t sweep;        /* MFS_SWEEP_AUTO (default; see above), MFS_SWEEP_CHUNKED, or
                              MFS_SWEEP_STAGED: build the staged layout (device memory of a second
-                             copy of A) and use it for both passes; FP32_MIXED solvers without
-                             Lorentz cones only, others run the chunked kernels (mfs_get_info tells) */
+                             copy of A) and use it for both passes; FP32_MIXED solvers only, FP64
+                             ones run the chunked kernels (mfs_get_info tells) */
     int32_t reserved;     /* must be 0 */
 } mfs_settings;
 
@@ -186,8 +187,8 @@ mfs_status mfs_get_info(const mfs_solver* s, mfs_info_t* out);
 /* Choose the sweep kernels of the FP32 iteration: MFS_SWEEP_AUTO, MFS_SWEEP_CHUNKED or
    MFS_SWEEP_STAGED (see above). MFS_ERR_INVALID for an unknown kind, or for MFS_SWEEP_STAGED on a
    solver whose staged layout was not built (neither requested by settings.sweep = MFS_SWEEP_STAGED
-   nor chosen by MFS_SWEEP_AUTO, in FP64, or with Lorentz cones). The iterate is kept; FP64
-   iterations always use the chunked kernels. */
+   nor chosen by MFS_SWEEP_AUTO, or in FP64). The iterate is kept; FP64 iterations always use the
+   chunked kernels. */
 mfs_status mfs_set_sweep(mfs_solver* s, int32_t kind);
 
 /* Diagnostic of the bounded waits of the staged sweeps: runs one staged column pass that issues

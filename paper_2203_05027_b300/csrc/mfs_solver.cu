@@ -295,7 +295,9 @@ struct StagedHost {
 // nonzeros. rb: entries of the gathered vector per block. Returns false if not even small groups
 // fit. The entries themselves are laid out on the GPU (staged_on_device).
 bool plan_staged(const std::vector<int>& ptr, int nseg, int nother, int groups, int rb, int stages,
-                 size_t smem_limit, StagedHost& S) {
+                 size_t smem_limit, StagedHost& S, const std::vector<int>* unit_start = nullptr) {
+    // a boundary never falls inside a unit (a small Lorentz cone, whose columns one warp projects)
+    auto snap = [&](int b) { return (unit_start && b > 0 && b < nseg) ? (*unit_start)[b] : b; };
     using mfs::staged::NW;
     const int RB = rb;
     const int64_t o = ptr[nseg];
@@ -310,10 +312,10 @@ bool plan_staged(const std::vector<int>& ptr, int nseg, int nother, int groups, 
         if (g < groups) {
             const int target = (int)(o * g / groups);
             hi = (int)(std::lower_bound(ptr.begin(), ptr.begin() + nseg + 1, target) - ptr.begin());
-            hi = std::min(std::max(hi, lo), nseg);
+            hi = std::min(std::max(snap(hi), lo), nseg);
         }
         while (hi - lo > MAXG) {
-            lo += MAXG;
+            lo = snap(lo + MAXG);
             S.grp.push_back(lo);
         }
         if (hi > lo) {
@@ -335,7 +337,7 @@ bool plan_staged(const std::vector<int>& ptr, int nseg, int nother, int groups, 
         for (int q = 1; q < NW; ++q) {
             const int target = (int)(ptr[a] + nz * q / NW);
             const int at = (int)(std::lower_bound(ptr.begin() + a, ptr.begin() + e + 1, target) - ptr.begin());
-            w[q] = std::max(w[q - 1], std::min(at, e) - a);
+            w[q] = std::max(w[q - 1], std::max(snap(std::min(at, e)), a) - a);
         }
         w[NW] = e - a;
     }
@@ -808,8 +810,11 @@ void launch_col(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
     if constexpr (std::is_same<T, float>::value) {
         if (staged_col(s)) {
             const StagedArgsT& g = s->stg_col;
-            launch_dep(MFS_STAGED_COL, std::min(g.G, s->num_sms), mfs::staged::NTHREADS,
-                       mfs::staged::smem_bytes(mfs::staged::RB_COL, mfs::staged::S_COL, g.maxg_pad, g.R), st, g, a);
+            const size_t smem = mfs::staged::smem_bytes(mfs::staged::RB_COL, mfs::staged::S_COL, g.maxg_pad, g.R);
+            if (s->has_soc)
+                launch_dep(MFS_STAGED_COL_SOC, std::min(g.G, s->num_sms), mfs::staged::NTHREADS, smem, st, g, a);
+            else
+                launch_dep(MFS_STAGED_COL, std::min(g.G, s->num_sms), mfs::staged::NTHREADS, smem, st, g, a);
             return;
         }
     }
@@ -1172,7 +1177,17 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
     int optin = 0;
     CUDA_TRY(s, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
     StagedHost C, W;
-    if (!plan_staged(P.col_ptr, P.n, P.m, s->num_sms, RB_COL, S_COL, (size_t)optin, C) ||
+    // small Lorentz cones stay within one warp's columns (its epilogue projects them)
+    std::vector<int> unit_start;
+    if (s->has_soc) {
+        unit_start.resize(P.n);
+        for (int j = 0; j < P.n; ++j) unit_start[j] = j;
+        for (size_t q = 0; q < P.soc_start.size(); ++q)
+            if (!P.soc_big[q])
+                for (int t = 1; t < P.soc_size[q]; ++t) unit_start[P.soc_start[q] + t] = P.soc_start[q];
+    }
+    if (!plan_staged(P.col_ptr, P.n, P.m, s->num_sms, RB_COL, S_COL, (size_t)optin, C,
+                     s->has_soc ? &unit_start : nullptr) ||
         !plan_staged(P.row_ptr, P.m, P.n, std::max(1, s->num_sms / ROW_HALVES), RB_ROW, S_ROW, (size_t)optin, W))
         return MFS_OK;  // vectors too long for the split tables: chunked sweeps only
     // the orders on the device: where the host built them, uploaded for the set-up only
@@ -1226,6 +1241,21 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
         g.no_loads = 0;
         return MFS_OK;
     };
+    gc.wcone = nullptr;
+    if (s->has_soc) {  // each warp's Lorentz cones: those starting within its columns
+        std::vector<int2> wc((size_t)C.G * NW);
+        for (int g2 = 0; g2 < C.G; ++g2)
+            for (int w = 0; w < NW; ++w) {
+                const int c0 = C.grp[g2] + C.wseg[(size_t)g2 * (NW + 1) + w];
+                const int c1 = C.grp[g2] + C.wseg[(size_t)g2 * (NW + 1) + w + 1];
+                const int q0 = (int)(std::lower_bound(P.soc_start.begin(), P.soc_start.end(), c0) - P.soc_start.begin());
+                const int q1 = (int)(std::lower_bound(P.soc_start.begin(), P.soc_start.end(), c1) - P.soc_start.begin());
+                wc[(size_t)g2 * NW + w] = make_int2(q0, q1);
+            }
+        int2* d_wc = nullptr;
+        TRY(upload(s, &d_wc, wc.data(), wc.size()));
+        gc.wcone = d_wc;
+    }
     s->stg_col = gc;
     s->stg_row = gr;
     TRY(fill(C, s->stg_col, s->s32.v, 1, P.n));
@@ -1240,6 +1270,7 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
     s->stg_row.rsq = d_rsq;
     // the limit is a property of the kernel, shared by all solvers: allow the device's maximum
     CUDA_TRY(s, cudaFuncSetAttribute(MFS_STAGED_COL, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    CUDA_TRY(s, cudaFuncSetAttribute(MFS_STAGED_COL_SOC, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     CUDA_TRY(s, cudaFuncSetAttribute(MFS_STAGED_ROW, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     s->stg_ok = true;
     return MFS_OK;
@@ -1856,8 +1887,7 @@ mfs_status create_impl(int64_t m, int64_t n, int64_t nnz, const int64_t* row, co
         const bool big = P.dev.on && P.o >= (1 << 20);
         const bool auto_col = big && (int64_t)P.o >= 8 * (int64_t)P.m;
         const bool auto_row = big && (int64_t)P.o >= 4 * (int64_t)P.n;
-        if ((set.sweep == MFS_SWEEP_STAGED || (set.sweep == MFS_SWEEP_AUTO && (auto_col || auto_row))) &&
-            !s->has_soc && P.o > 0)
+        if ((set.sweep == MFS_SWEEP_STAGED || (set.sweep == MFS_SWEEP_AUTO && (auto_col || auto_row))) && P.o > 0)
             CHK(setup_staged(s, P));
         s->stg_auto_col = s->stg_ok && auto_col;
         s->stg_auto_row = s->stg_ok && auto_row;
@@ -1935,8 +1965,11 @@ mfs_status mfs_debug_staged_wait_test(mfs_solver* s) {
     g.spin = 64;
     g.no_loads = 1;
     const SweepArgs<float> a = sweep_args(s, s->s32);
-    MFS_STAGED_COL<<<std::min(g.G, s->num_sms), mfs::staged::NTHREADS,
-                     mfs::staged::smem_bytes(mfs::staged::RB_COL, mfs::staged::S_COL, g.maxg_pad, g.R), s->stream>>>(g, a);
+    const size_t smem = mfs::staged::smem_bytes(mfs::staged::RB_COL, mfs::staged::S_COL, g.maxg_pad, g.R);
+    if (s->has_soc)
+        MFS_STAGED_COL_SOC<<<std::min(g.G, s->num_sms), mfs::staged::NTHREADS, smem, s->stream>>>(g, a);
+    else
+        MFS_STAGED_COL<<<std::min(g.G, s->num_sms), mfs::staged::NTHREADS, smem, s->stream>>>(g, a);
     CUDA_TRY(s, cudaGetLastError());
     CUDA_TRY(s, cudaMemcpyAsync(s->h_err, s->stg_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(s, cudaMemsetAsync(s->stg_err, 0, sizeof(int), s->stream));
@@ -1974,8 +2007,7 @@ mfs_status mfs_set_sweep(mfs_solver* s, int32_t kind) {
         return fail(s, MFS_ERR_INVALID, "unknown sweep kind");
     if (kind == MFS_SWEEP_STAGED && !s->stg_ok)
         return fail(s, MFS_ERR_INVALID,
-                    "no staged layout: create the solver with settings.sweep = MFS_SWEEP_STAGED (FP32_MIXED, "
-                    "orthant cones only)");
+                    "no staged layout: create the solver with settings.sweep = MFS_SWEEP_STAGED (FP32_MIXED)");
     CUDA_TRY(s, cudaSetDevice(s->device));
     CUDA_TRY(s, cudaStreamSynchronize(s->stream));
     destroy_graphs(s);

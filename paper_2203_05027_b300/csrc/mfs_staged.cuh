@@ -106,6 +106,7 @@ struct StagedArgs {
     const int* __restrict__ wovf;   // G x (NW + 1): each warp's first overflow slot within its group
     const int* __restrict__ fold_ptr;  // G * NW + 1: each (group, warp)'s range of fold entries
     const int2* __restrict__ fold;  // (segment, first overflow slot | pieces - 1 << 16), per warp
+    const int2* __restrict__ wcone; // column pass with Lorentz cones: G x NW, each warp's cones [x, y)
     const float* __restrict__ vec;  // gathered vector, R * rb entries (tail padding unused)
     const float* __restrict__ rsq;  // row pass: sum of a_k^2 over each row
     int* err;                       // set to 1 if a wait for a block gave up
@@ -297,13 +298,14 @@ __device__ __forceinline__ void block_step(int b, int be, uint32_t u, int2 (&C)[
     if (lane == 0) mbar_arrive(empty + k);
 }
 
-// MODE 0: column pass (gathers v; epilogue x-, z-, delta-updates of orthant columns).
+// MODE 0: column pass (gathers v; epilogue x-, z-, delta-updates; with SOC also the z-step of the
+// small Lorentz cones, whose columns never straddle two warps' ranges).
 // MODE 1: row pass (gathers x; epilogue rho, lambda and v of each row).
 // Warps 0..NW-1 consume; warp NW produces (its lane 0 issues the copies of the vector blocks).
 // Warp w owns the segments wseg[w] .. wseg[w+1]-1 of its group in every block: it alone adds into
 // their sums, and it runs their epilogue as soon as it has seen every block, while other warps
 // may still be streaming.
-template <int MODE, int RB, int PFR, int S>
+template <int MODE, int RB, int PFR, int S, bool SOC>
 __global__ void __launch_bounds__(NTHREADS, 1) k_staged(const StagedArgs g, const SweepArgs<float> a) {
     extern __shared__ __align__(128) unsigned char smem[];
     float* vb = reinterpret_cast<float*>(smem);
@@ -378,6 +380,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_staged(const StagedArgs g, cons
             if (MODE == 0) {
                 for (int t0 = e0; t0 < e1; t0 += es * EPI_U) {
                     float px[EPI_U], pz[EPI_U], pd[EPI_U], pc[EPI_U], dg[EPI_U];
+                    int tag[EPI_U];
 #pragma unroll
                     for (int q = 0; q < EPI_U; ++q) {
                         const int t = t0 + q * es;
@@ -388,6 +391,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_staged(const StagedArgs g, cons
                             pz[q] = a.z[j];
                             pd[q] = a.del[j];
                             pc[q] = __ldg(a.c + j);
+                            tag[q] = SOC ? cone_tag(a, j) : 0;
                         }
                     }
 #pragma unroll
@@ -395,7 +399,44 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_staged(const StagedArgs g, cons
                         const int t = t0 + q * es;
                         if (t < e1) {
                             const float xn = col_x_update(dg[q], px[q], acc[t], pz[q], pd[q], pc[q], mu);
-                            orthant_update(a.x, a.z, a.del, k0 + t, xn, pd[q], mu);
+                            if (!SOC || tag[q] == 0) {
+                                orthant_update(a.x, a.z, a.del, k0 + t, xn, pd[q], mu);
+                            } else {
+                                a.x[k0 + t] = xn;  // a cone too large to fuse: the big-cone kernel follows
+                                if (tag[q] == 1) acc[t] = xn - pd[q] / mu;  // w of the z-step, kept in place
+                            }
+                        }
+                    }
+                }
+                if (SOC) {
+                    // the warp's small Lorentz cones one after another (they never straddle warps):
+                    // ||w_tail||^2 by a butterfly sum, then the z-step (eq. proj) per coordinate and
+                    // delta+ = delta + mu (z+ - x+) = mu (z+ - w)
+                    __syncwarp();
+                    const int2 wc = g.wcone[grp * NW + warp];
+                    for (int q0 = wc.x; q0 < wc.y; q0 += 32) {
+                        const int q = q0 + lane;
+                        int st = 0, sz = 0, big = 1;
+                        if (q < wc.y) {
+                            st = a.soc_start[q] - k0;
+                            sz = a.soc_size[q];
+                            big = a.soc_big[q];
+                        }
+                        const int cnt = min(32, wc.y - q0);
+                        for (int u = 0; u < cnt; ++u) {
+                            if (__shfl_sync(FULL, big, u)) continue;
+                            const int c0 = __shfl_sync(FULL, st, u), csz = __shfl_sync(FULL, sz, u);
+                            float ss = 0.f;
+                            for (int t = 1 + lane; t < csz; t += 32) ss += acc[c0 + t] * acc[c0 + t];
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(FULL, ss, o);
+                            const float alpha = sqrtf(ss), w1 = acc[c0];
+                            for (int t = lane; t < csz; t += 32) {
+                                const float w = acc[c0 + t];
+                                const float zt = lorentz_coord(w, t, w1, alpha);
+                                a.z[k0 + c0 + t] = zt;
+                                a.del[k0 + c0 + t] = mu * (zt - w);
+                            }
                         }
                     }
                 }
@@ -451,8 +492,12 @@ __global__ void __launch_bounds__(256) k_row_combine(const StagedArgs g, const S
 }
 
 // the two instantiations the solver launches
-#define MFS_STAGED_COL ::mfs::staged::k_staged<0, ::mfs::staged::RB_COL, ::mfs::staged::PFR_COL, ::mfs::staged::S_COL>
-#define MFS_STAGED_ROW ::mfs::staged::k_staged<1, ::mfs::staged::RB_ROW, ::mfs::staged::PFR_ROW, ::mfs::staged::S_ROW>
+#define MFS_STAGED_COL \
+    ::mfs::staged::k_staged<0, ::mfs::staged::RB_COL, ::mfs::staged::PFR_COL, ::mfs::staged::S_COL, false>
+#define MFS_STAGED_COL_SOC \
+    ::mfs::staged::k_staged<0, ::mfs::staged::RB_COL, ::mfs::staged::PFR_COL, ::mfs::staged::S_COL, true>
+#define MFS_STAGED_ROW \
+    ::mfs::staged::k_staged<1, ::mfs::staged::RB_ROW, ::mfs::staged::PFR_ROW, ::mfs::staged::S_ROW, false>
 
 }  // namespace staged
 }  // namespace mfs

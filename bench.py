@@ -46,11 +46,17 @@ def parse():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the extra workloads (batched LPs, shared-A family, MLP step)")
     ap.add_argument("--sweep", default="auto", choices=["auto", "chunked", "staged"],
-                    help="sweep kernels of the large LP's FP32 iteration (auto: chunked column sweep, staged row pass)")
-    ap.add_argument("--warm-start", type=int, default=2048, metavar="TRAIN",
+                    help="sweep kernels of the large LP's FP32 iteration (auto: the library's choice, staged passes on this instance)")
+    ap.add_argument("--l2-keep", type=int, default=1, choices=[0, 1],
+                    help="settings.l2_keep of the large-LP solvers: raise the context's persisting-L2 set-aside "
+                         "while they exist, so that the staged passes keep the iterate's vectors in L2 (each "
+                         "is closed before the next section runs)")
+    ap.add_argument("--warm-start", type=int, default=4096, metavar="TRAIN",
                     help="learned warm-start experiment with TRAIN training solves (0 skips it; 50000 is the "
                          "full experiment, about 15 minutes)")
-    ap.add_argument("--warm-start-test", type=int, default=128)
+    ap.add_argument("--warm-start-test", type=int, default=128,
+                    help="held-out members solved to 1e-6 by each arm (cold, network, mean, nearest; 1000 "
+                         "in the full experiment)")
     ap.add_argument("--section", default="all", choices=["all", "small", "socp", "paper", "batch", "shared", "mlp"],
                     help="run only one extra workload and print its line (for profiling)")
     ap.add_argument("--tts-iters", type=int, default=300000,
@@ -227,22 +233,31 @@ def batch_workload(stream, seed, iters=100, tts_iters=300_000):
     ms = e0.elapsed_time(e1)
     bytes_iter = 16 * info["total_nnz"] + 36 * info["total_n"] + 24 * info["total_m"]
     bt.close()
-    # time to 1e-6 from the cold start, every instance tested inside the launch every 50 iterations
+    # time to 1e-6 from the cold start, every instance tested inside the launch at the tuned interval
     if not tts_iters:
         return {"ms_per_batch_iteration": round(ms / iters, 5), "tuning": tuned}
-    bt2 = mfs.Batch(probs, precision="fp32", check_every=50, stream=stream.cuda_stream)
-    bt2.set_tuning(tuned["threads"], tuned["ctas_per_sm"], 50)
+    bt2 = mfs.Batch(probs, precision="fp32", check_every=tuned["check_every"], stream=stream.cuda_stream)
+    bt2.set_tuning(tuned["threads"], tuned["ctas_per_sm"], tuned["check_every"])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     its, sts = bt2.solve(1e-6, tts_iters)
     torch.cuda.synchronize()
     tts_s = time.perf_counter() - t0
+    kkt = np.array([r["kkt"] for r in bt2.residuals()])
     bt2.close()
     ok = its[sts == 0]
+    left = sts != 0
+    ms_ = np.array([p["m"] for p in probs])
     tts = {"tol": 1e-6, "max_iter": tts_iters, "seconds": round(tts_s, 3), "converged": int(ok.size),
            "instances_per_s": round(ok.size / tts_s, 1),
            "iterations_median": float(np.median(ok)) if ok.size else None,
-           "iterations_p90": float(np.percentile(ok, 90)) if ok.size else None}
+           "iterations_p90": float(np.percentile(ok, 90)) if ok.size else None,
+           # every instance's outcome: those that reached the cap first, by their KKT residual there
+           "at_cap": {"count": int(left.sum()),
+                      "kkt_median": float(np.median(kkt[left])) if left.any() else None,
+                      "kkt_max": float(kkt[left].max()) if left.any() else None,
+                      "below_1e-5": int((kkt[left] <= 1e-5).sum()), "below_1e-4": int((kkt[left] <= 1e-4).sum()),
+                      "m_median": float(np.median(ms_[left])) if left.any() else None}}
     out = {"workload": "batch_lps 4096 instances, m log-uniform [50, 5000], n = 2.5 m, 5 nnz/col",
            "total_nnz": info["total_nnz"], "total_m": info["total_m"], "total_n": info["total_n"],
            "iterations": iters, "ms_per_batch_iteration": round(ms / iters, 5),
@@ -472,7 +487,7 @@ def main():
     prob = make_problem(args.workload, rank)
     stream = torch.cuda.current_stream()
     s = mfs.Solver(prob, precision="fp32", polish_iters=0, check_every=ITERS_PER_STEP,
-                   stream=stream.cuda_stream, sweep=args.sweep)
+                   stream=stream.cuda_stream, sweep=args.sweep, l2_keep=bool(args.l2_keep))
     info = s.info()
     o, m, n = info["o"], info["m"], info["n"]
 
@@ -505,6 +520,7 @@ def main():
                            torch.cuda.get_device_properties(local).multi_processor_count)
     # per step: the sweeps of ITERS_PER_STEP iterations + 2 residual kernels (+ big cones) + finalize
     launches_per_step = ITERS_PER_STEP * info["launches_per_iter"] + 3 + (1 if info["nbig"] else 0)
+    s.close()  # with l2_keep, its raised L2 set-aside would shrink the L2 of the sections below
 
     extra = {}
     if args.tts_iters:
@@ -513,7 +529,7 @@ def main():
         # reported apart.
         tc = time.perf_counter()
         s2 = mfs.Solver(prob, precision="fp32", polish_iters=200, check_every=250, stream=stream.cuda_stream,
-                        sweep=args.sweep)
+                        sweep=args.sweep, l2_keep=bool(args.l2_keep))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, its = s2.solve(1e-6, args.tts_iters)
@@ -527,12 +543,15 @@ def main():
                                  "pobj": r2["pobj"], "dobj": r2["dobj"],
                                  "sweep": "staged" if i2["sweep_col"] == mfs.SWEEP_STAGED else "chunked",
                                  "create_seconds": round(t0 - tc, 3)}
+        s2.close()
         if i2["sweep_col"] == mfs.SWEEP_STAGED or i2["sweep_row"] == mfs.SWEEP_STAGED:
             # the other kernels of the same iteration, for comparison: one warp per chunk of at most
-            # 256 nonzeros, every gather an L2 request
-            s2.set_sweep("chunked")
+            # 256 nonzeros, every gather an L2 request (a solver without staged passes, so the
+            # context's L2 set-aside is at its default)
+            s2 = mfs.Solver(prob, precision="fp32", polish_iters=0, stream=stream.cuda_stream, sweep="chunked")
             s2.time_kernels(3)
             tk = s2.time_kernels(20)
+            s2.close()
             col_bytes = 8 * o + 32 * n + 4 * m
             extra["chunked_sweeps"] = {
                 "col_us": round(tk["col_ms"] * 1e3, 1), "row_us": round(tk["row_ms"] * 1e3, 1),
@@ -540,7 +559,21 @@ def main():
                 "col_gbs": round(col_bytes / (tk["col_ms"] * 1e-3) / 1e9, 1),
                 "col_frac_of_measured_hbm": round(col_bytes / (tk["col_ms"] * 1e-3) / 1e9 / peak, 4),
                 "note": "k_col_sweep / k_row_sweep (--sweep chunked) on the same instance; same iteration"}
-        s2.close()
+        # a convergence variant outside the paper (residual-balanced mu), reported apart
+        s4 = mfs.Solver(prob, precision="fp32", polish_iters=200, check_every=250, stream=stream.cuda_stream,
+                        sweep=args.sweep, adapt_mu=4, l2_keep=bool(args.l2_keep))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st4, its4 = s4.solve(1e-6, args.tts_iters)
+        torch.cuda.synchronize()
+        t4 = time.perf_counter() - t0
+        h4, _ = s4.history()
+        extra["variant_balanced_mu"] = {
+            "rule": "mu doubled / halved at checks 4, 8, 16, ... (every 250 iterations) when the primal and dual "
+                    "relative residuals differ by more than 5x; not the paper's method (fixed mu)",
+            "status": st4, "iterations": its4, "seconds": round(t4, 3), "kkt": s4.residuals()["kkt"],
+            "mu_final": h4[-1]["mu"] if h4 else None}
+        s4.close()
 
     if not args.no_batch:
         extra["batch_lps"] = batch_workload(stream, rank)
@@ -553,16 +586,20 @@ def main():
         from paper_2203_05027_b300 import warmstart as W
         ws = W.run(train=args.warm_start, test=args.warm_start_test, seed=rank,
                    log=lambda t: print(t, file=sys.stderr, flush=True))
+        full = args.warm_start >= 50_000 and args.warm_start_test >= 1000
         extra["warm_start"] = {"workload": f"parametric LP family (m=20000, n=50000), {args.warm_start} training "
-                                           f"solves, {args.warm_start_test} held-out members, to 1e-6",
+                                           f"solves, {args.warm_start_test} held-out members, to 1e-6"
+                                           + ("" if full else " (scaled from 50,000 and 1,000)"),
+                               "arms": "cold: zero start; mlp: the trained network's prediction; mean: the mean "
+                                       "training solution; nearest: the solution of the nearest training theta",
                                **{k: v for k, v in ws.items() if k != "stage"}}
 
-    e2e = None
+    e2e = e2e_dev = None
     if not args.no_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s3 = mfs.Solver(prob, precision="fp32", polish_iters=0, check_every=ITERS_PER_STEP,
-                        stream=stream.cuda_stream, sweep=args.sweep)
+                        stream=stream.cuda_stream, sweep=args.sweep, l2_keep=bool(args.l2_keep))
         for _ in range(args.steps):
             s3.iterate(ITERS_PER_STEP)
             s3.residuals()
@@ -578,6 +615,30 @@ def main():
                "seconds": round(dt, 3),
                "scope": "mfs_create from host COO (set-up + upload) + all steps + mfs_get_solution to host"}
 
+        # the same, for a caller whose COO, b and c are already in device memory (mfs_create_device):
+        # no input crosses from the host; the solution still comes back
+        dev_in = {k: torch.from_numpy(np.ascontiguousarray(prob[k], dtype=np.int64)).cuda() for k in ("row", "col")}
+        dev_in.update({k: torch.from_numpy(np.ascontiguousarray(prob[k], dtype=np.float64)).cuda()
+                       for k in ("val", "b", "c")})
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s5 = mfs.Solver.from_device(m, n, prob["row"].size, dev_in["row"].data_ptr(), dev_in["col"].data_ptr(),
+                                    dev_in["val"].data_ptr(), dev_in["b"].data_ptr(), dev_in["c"].data_ptr(),
+                                    prob["cones"], precision="fp32", polish_iters=0, check_every=ITERS_PER_STEP,
+                                    stream=stream.cuda_stream, sweep=args.sweep, l2_keep=bool(args.l2_keep))
+        for _ in range(args.steps):
+            s5.iterate(ITERS_PER_STEP)
+            s5.residuals()
+        sol = s5.solution()
+        torch.cuda.synchronize()
+        dt5 = time.perf_counter() - t0
+        s5.close()
+        del dev_in
+        e2e_dev = {"value": world * o * iters / dt5, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": int(d2h / args.steps), "seconds": round(dt5, 3),
+                   "scope": "mfs_create_device from device COO (set-up on the GPU) + all steps + mfs_get_solution "
+                            "to host"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(prob)
@@ -591,13 +652,13 @@ def main():
                            "sweeps": {"col": "staged" if info["sweep_col"] == mfs.SWEEP_STAGED else "chunked",
                                       "row": "staged" if info["sweep_row"] == mfs.SWEEP_STAGED else "chunked"},
                            "l2": "inputs larger than L2 (A in both orders is %.0f MB in FP32)" % (16 * o / 1e6),
+                           "l2_keep": bool(args.l2_keep),
                            "parallelism": f"replicas{world}"},
                 "kkt_after_timed_region": r["kkt"],
                 "roofline": roof, "gpu_launches": launches_per_step * args.steps,
-                "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
+                "clocks": clocks, "e2e": e2e, "e2e_device_input": e2e_dev, "cpu_baseline": cpu}
         line.update(extra)
         print(json.dumps(line), flush=True)
-    s.close()
     if dist:
         dist.destroy_process_group()
 

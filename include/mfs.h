@@ -97,7 +97,22 @@ typedef struct {
                              MFS_SWEEP_STAGED: build the staged layout (device memory of a second
                              copy of A) and use it for both passes; FP32_MIXED solvers only, FP64
                              ones run the chunked kernels (mfs_get_info tells) */
-    int32_t reserved;     /* must be 0 */
+    int32_t adapt_mu;     /* 0 (default): mu stays fixed, the paper's method. k > 0: a variant outside
+                             the paper (residual balancing): at the residual checks k, 2k, 4k, 8k, ...
+                             of mfs_solve (exponentially spaced, so that mu changes finitely often),
+                             mu doubles if max(r_prim, r_cone) > 5 r_dual and halves if
+                             r_dual > 5 max(r_prim, r_cone), within [mu/256, 256 mu] of its value
+                             when mfs_solve began (mfs_set_mu semantics: the iterate is kept).
+                             Ignored by mfs_iterate and by the batch and shared-A solvers. */
+    int32_t l2_keep;      /* 0 (default) or 1. The staged passes access the iterate's vectors with an L2
+                             evict-last hint; such lines stay in L2 only within the context's persisting
+                             set-aside (cudaLimitPersistingL2CacheSize). With 1 a solver that sets up
+                             staged passes raises that limit to the device's maximum while it exists
+                             (the last such solver to be destroyed puts the previous value back): the
+                             large LP's iteration then takes 135 instead of 141 us, but all other work in
+                             the CUDA context has that much less L2 meanwhile (the chunked sweeps of the
+                             same instance: 184 instead of 118 us). Ignored by the batch and shared-A
+                             solvers. */
 } mfs_settings;
 
 /* Residuals at the current (x, lambda); all accumulated in FP64.
@@ -135,7 +150,7 @@ typedef struct {
 } mfs_info_t;
 
 /* Defaults: mu = 1, check_every = 25, precision = MFS_FP64, polish_iters = 50, stop_rule =
-   MFS_STOP_KKT, osqp_rel = 10, sweep = MFS_SWEEP_AUTO. */
+   MFS_STOP_KKT, osqp_rel = 10, sweep = MFS_SWEEP_AUTO, adapt_mu = 0. */
 void mfs_default_settings(mfs_settings* s);
 
 /*
@@ -258,12 +273,14 @@ mfs_status mfs_iterate(mfs_solver* s, int64_t k);
 mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters_out);
 
 /* One residual check of mfs_solve: iterations run by that call when it was made, the relative
-   residuals (as in mfs_residuals_t), the stopping rule's measure and the precision of the iterate. */
+   residuals (as in mfs_residuals_t), the stopping rule's measure, the precision of the iterate and
+   the penalty mu from then on. */
 typedef struct {
     int64_t iter;
     double kkt, r_prim, r_dual, r_cone, r_gap, measure;
     int32_t precision;
     int32_t reserved;
+    double mu;  /* mu of the iterations that follow the check (after any residual-balancing change) */
 } mfs_check_t;
 
 /* The checks of the last mfs_solve on this handle (a ring of the most recent 4096): the latest
@@ -350,7 +367,11 @@ mfs_status mfs_batch_get_solution(mfs_batch* bt, int64_t t, double* x, double* l
 mfs_status mfs_batch_set_tuning(mfs_batch* bt, const mfs_batch_tuning* tuning);
 mfs_status mfs_batch_get_tuning(const mfs_batch* bt, mfs_batch_tuning* tuning);
 /* Autotuner: times `iters` iterations of the whole batch for each candidate (threads per CTA x CTAs
-   per SM), keeps the fastest and returns it in chosen (nullable). The iterate advances. */
+   per SM) and keeps the fastest; then, with that launch shape, times `iters` iterations with the
+   in-launch residual checks every 10, 25, 50, 100 or 200 iterations and keeps the smallest interval
+   whose checks cost at most 5 % more than every 200 (a finer interval stops each instance closer to
+   its first iteration at the tolerance). Returns the choice in chosen (nullable). The iterate
+   advances. */
 mfs_status mfs_batch_tune(mfs_batch* bt, int64_t iters, mfs_batch_tuning* chosen);
 
 /* ------------------------------------------------------------------------------------------------

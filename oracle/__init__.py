@@ -256,6 +256,47 @@ def stop_measures(res: dict, osqp_rel: float = 10.0) -> dict:
     return {"r_scs": float(r_scs), "r_osqp": float(max(pi, di))}
 
 
+# Residual balancing of mu -- a convergence variant outside the paper, whose Algorithm 1 keeps mu
+# fixed: at the checks k, 2k, 4k, 8k, ... (exponentially spaced, so mu changes finitely often) mu
+# doubles when the primal side (max of r_prim and r_cone) exceeds MU_TAU times the dual residual,
+# halves in the opposite case, and stays within a factor MU_RANGE of its starting value. A change of
+# mu keeps the literal state (y and gamma do not depend on it).
+MU_STEP, MU_TAU, MU_RANGE = 2.0, 5.0, 256.0
+
+
+def solve_balanced(orc, tol, max_iter, check_every, adapt_every):
+    """The solve loop with residual balancing: a check (residuals of the current iterate) before
+    every check_every iterations; stop when kkt <= tol or max_iter iterations ran; the checks
+    numbered adapt_every, 2 adapt_every, 4 adapt_every, ... (the first is number 0) may change mu as
+    above (adapt_every = 0: mu fixed, the paper's method). Returns (iterations run, list of
+    (iteration, kkt, mu after the check))."""
+    mu0 = orc.mu
+    it, nchk, hist = 0, 0, []
+    nxt = adapt_every
+    while True:
+        r = orc.residuals()
+        if r["kkt"] <= tol or it >= max_iter:
+            hist.append((it, r["kkt"], orc.mu))
+            break
+        if adapt_every > 0 and nchk == nxt:
+            nxt *= 2
+            rp, rd = max(r["r_prim"], r["r_cone"]), r["r_dual"]
+            mu = orc.mu
+            if rp > MU_TAU * rd:
+                mu = mu * MU_STEP
+            elif rd > MU_TAU * rp:
+                mu = mu / MU_STEP
+            mu = min(max(mu, mu0 / MU_RANGE), mu0 * MU_RANGE)
+            if mu != orc.mu:
+                orc.set_mu(mu)
+        hist.append((it, r["kkt"], orc.mu))
+        nchk += 1
+        k = min(check_every, max_iter - it)
+        orc.iterate(k)
+        it += k
+    return it, hist
+
+
 def make_oracle(prob, mu=1.0, dtype=np.float64) -> Oracle:
     """Oracle for a problem dict from ``paper_2203_05027_b300.instances`` (keys m, n, row, col,
     val, b, c, cones). With dtype=float32 the data are rounded to FP32 first and promoted back,

@@ -127,6 +127,7 @@ struct mfs_solver {
     bool stg_auto_row = false;  // the automatic choice runs the staged row pass
     int sweep_kind = MFS_SWEEP_AUTO;
     mfs::staged::StagedArgs stg_col{}, stg_row{};
+    bool keep_l2 = false;  // holds a reference on the raised persisting-L2 limit (settings.l2_keep)
     int* stg_err = nullptr;
     int* h_err = nullptr;  // pinned
     std::vector<void*> allocs;
@@ -1172,6 +1173,47 @@ mfs_status staged_on_device(mfs_solver* s, const StagedHost& S, const int* d_ptr
     return MFS_OK;
 }
 
+// The staged passes access the iterate's vectors evict-last. Such lines stay in L2 only within the
+// context's persisting set-aside; with settings.l2_keep the first staged solver of a device raises it
+// to the device's maximum and the last one to be destroyed puts the previous value back (where it
+// cannot be raised the hint stays a hint). The set-aside is L2 that other work in the context does
+// not get while it is raised.
+std::mutex g_keep_mu;
+struct KeepRef {
+    int count = 0;
+    size_t prev = 0;
+};
+KeepRef g_keep[64];
+
+void keep_acquire(mfs_solver* s) {
+    if (s->device < 0 || s->device >= 64) return;
+    std::lock_guard<std::mutex> lk(g_keep_mu);
+    KeepRef& k = g_keep[s->device];
+    if (k.count == 0) {
+        int maxp = 0;
+        size_t cur = 0;
+        if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, s->device) != cudaSuccess ||
+            cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return;
+        }
+        k.prev = cur;
+        if (cur < (size_t)maxp && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)maxp) != cudaSuccess)
+            (void)cudaGetLastError();
+    }
+    ++k.count;
+    s->keep_l2 = true;
+}
+
+void keep_release(mfs_solver* s) {
+    if (!s->keep_l2) return;
+    s->keep_l2 = false;
+    std::lock_guard<std::mutex> lk(g_keep_mu);
+    KeepRef& k = g_keep[s->device];
+    if (--k.count == 0 && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, k.prev) != cudaSuccess)
+        (void)cudaGetLastError();
+}
+
 mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
     using namespace mfs::staged;
     int optin = 0;
@@ -1273,6 +1315,9 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
     CUDA_TRY(s, cudaFuncSetAttribute(MFS_STAGED_COL_SOC, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     CUDA_TRY(s, cudaFuncSetAttribute(MFS_STAGED_ROW, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     s->stg_ok = true;
+#if MFS_STG_KEEP
+    if (s->set.l2_keep) keep_acquire(s);
+#endif
     return MFS_OK;
 }
 
@@ -1652,7 +1697,8 @@ void mfs_default_settings(mfs_settings* st) {
     st->stop_rule = MFS_STOP_KKT;
     st->osqp_rel = 10.0;
     st->sweep = MFS_SWEEP_AUTO;
-    st->reserved = 0;
+    st->adapt_mu = 0;
+    st->l2_keep = 0;
 }
 
 const char* mfs_last_error(const mfs_solver* s) {
@@ -1665,6 +1711,7 @@ void mfs_destroy(mfs_solver* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     destroy_graphs(s);
     literal_free(s);
+    keep_release(s);
     for (void* p : s->allocs) cudaFree(p);
     if (s->h_status) cudaFreeHost(s->h_status);
     if (s->h_err) cudaFreeHost(s->h_err);
@@ -1703,6 +1750,8 @@ mfs_status create_impl(int64_t m, int64_t n, int64_t nnz, const int64_t* row, co
         return fail(nullptr, MFS_ERR_INVALID, "osqp_rel must be > 0");
     if (set.sweep != MFS_SWEEP_AUTO && set.sweep != MFS_SWEEP_CHUNKED && set.sweep != MFS_SWEEP_STAGED)
         return fail(nullptr, MFS_ERR_INVALID, "unknown sweep kind");
+    if (set.adapt_mu < 0) return fail(nullptr, MFS_ERR_INVALID, "adapt_mu must be >= 0");
+    if (set.l2_keep != 0 && set.l2_keep != 1) return fail(nullptr, MFS_ERR_INVALID, "l2_keep must be 0 or 1");
     int64_t total = 0;
     for (int64_t q = 0; q < ncones; ++q) {
         if (cones[q].size < 1) return fail(nullptr, MFS_ERR_INVALID, "cone of size < 1");
@@ -2117,6 +2166,12 @@ mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters
     int prev_prec = -1, pass_p = 0, pass_d = 0;
     double prev_blam = 0.0, prev_cx = 0.0;
     std::vector<double> rp_hist, rd_hist;
+    // residual balancing of mu (settings.adapt_mu > 0): the factor, the imbalance that triggers it
+    // and the range around the starting mu
+    constexpr double MU_STEP = 2.0, MU_TAU = 5.0, MU_RANGE = 256.0;
+    const double mu0 = s->set.mu;
+    int64_t nchk = 0;  // checks made by this call before the current one
+    int64_t next_adapt = s->set.adapt_mu;  // the next check that may change mu
     while (true) {
         TRY(s->precision == MFS_FP64 ? residuals_t(s, s->s64, &r, true) : residuals_t(s, s->s32, &r, true));
         const double meas = stop_measure(r, s->set.stop_rule);
@@ -2131,6 +2186,7 @@ mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters
             h.measure = meas;
             h.precision = s->precision;
             h.reserved = 0;
+            h.mu = s->set.mu;
             ++s->hist_count;
         }
         if (!std::isfinite(r.kkt) || !std::isfinite(meas)) {
@@ -2178,6 +2234,7 @@ mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters
                 const int64_t p = std::min<int64_t>(s->set.polish_iters, max_iter - it);
                 TRY(mfs_iterate(s, p));
                 it += p;
+                ++nchk;
                 continue;  // re-check in FP64
             }
             result = MFS_OK;
@@ -2192,6 +2249,22 @@ mfs_status mfs_solve(mfs_solver* s, double tol, int64_t max_iter, int64_t* iters
                 TRY(mfs_set_precision(s, MFS_FP64));
             }
         }
+        if (s->set.adapt_mu > 0 && nchk == next_adapt) {
+            next_adapt *= 2;  // exponentially spaced changes: finitely many over any run
+            // residual balancing (a variant outside the paper, which keeps mu fixed)
+            const double rp = std::max(r.r_prim, r.r_cone), rd = r.r_dual;
+            double mu = s->set.mu;
+            if (rp > MU_TAU * rd)
+                mu *= MU_STEP;
+            else if (rd > MU_TAU * rp)
+                mu /= MU_STEP;
+            mu = std::min(std::max(mu, mu0 / MU_RANGE), mu0 * MU_RANGE);
+            if (mu != s->set.mu) {
+                TRY(mfs_set_mu(s, mu));
+                s->hist[(size_t)((s->hist_count - 1) % HIST_CAP)].mu = mu;
+            }
+        }
+        ++nchk;
         const int64_t kk = std::min<int64_t>(K, max_iter - it);
         TRY(mfs_iterate(s, kk));
         it += kk;

@@ -82,6 +82,10 @@ constexpr int EPI_U = 6;       // epilogue items per thread in flight
 #ifndef MFS_STG_ENT_PD
 #define MFS_STG_ENT_PD 4
 #endif
+#ifndef MFS_STG_KEEP
+#define MFS_STG_KEEP 1  // the iterate's vectors read and written by the staged passes carry an L2
+                        // evict-last policy (the entries stream past them evict-first)
+#endif
 #ifndef MFS_STG_ENT_HINT
 #define MFS_STG_ENT_HINT 1  // entries loaded with an L2 evict-first policy
 #endif
@@ -125,10 +129,84 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 
 __device__ __forceinline__ void issue_block(float* dst, const float* src, uint32_t bytes, uint64_t* bar) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+#if MFS_STG_KEEP
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+#else
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
+#endif
+}
+
+// Accesses to the iterate's vectors (x, z, delta, c, column pointers; lambda, v, b, row norms, the
+// partial row sums) with an L2 evict-last policy when MFS_STG_KEEP is set, plain ones otherwise.
+// Evict-last lines stay in the context's persisting L2 set-aside (raised by the solver's set-up), so
+// that from one pass to the next the vectors are read from L2 while the entries stream past. The
+// accesses are volatile asm (plain accesses in the plain build), so their order among themselves is
+// the program's.
+__device__ __forceinline__ uint64_t policy_keep() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ float ld_keep(const float* p, uint64_t pol) {
+#if MFS_STG_KEEP
+    float v;
+    asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol) : "memory");
+    return v;
+#else
+    return *p;
+#endif
+}
+__device__ __forceinline__ float ldg_keep(const float* p, uint64_t pol) {  // data the pass does not write
+#if MFS_STG_KEEP
+    float v;
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+#else
+    return __ldg(p);
+#endif
+}
+__device__ __forceinline__ int ldg_keep(const int* p, uint64_t pol) {
+#if MFS_STG_KEEP
+    int v;
+    asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+#else
+    return __ldg(p);
+#endif
+}
+__device__ __forceinline__ void st_keep(float* p, float v, uint64_t pol) {
+#if MFS_STG_KEEP
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+#else
+    *p = v;
+#endif
+}
+// the orthant z-step of column j after its x-update (as orthant_update), stores with the policy
+__device__ __forceinline__ void orthant_keep(const SweepArgs<float>& a, int j, float xn, float dj, float mu,
+                                             uint64_t pol) {
+    st_keep(a.x + j, xn, pol);
+    const float w = xn - dj / mu;
+    const float zn = w > 0.f ? w : 0.f;
+    st_keep(a.z + j, zn, pol);
+    st_keep(a.del + j, dj + mu * (zn - xn), pol);
+}
+// rho, lambda and v of row i (as row_update), stores with the policy
+__device__ __forceinline__ void row_keep(const SweepArgs<float>& a, int i, float ax, float r, float bi, float li,
+                                         uint64_t pol) {
+    const float mu = a.mu;
+    const float rho = (bi - ax) / (1.f + r);
+    const float ln = li - mu * rho;
+    st_keep(a.lam + i, ln, pol);
+    st_keep(a.v + i, rho - ln / mu, pol);
 }
 
 // Programmatic dependent launch. The passes are launched so that the next one may start while
@@ -378,6 +456,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_staged(const StagedArgs g, cons
             const int e0 = ws + lane, e1 = we, es = 32;
             const float mu = a.mu;
             if (MODE == 0) {
+                const uint64_t kp = policy_keep();
                 for (int t0 = e0; t0 < e1; t0 += es * EPI_U) {
                     float px[EPI_U], pz[EPI_U], pd[EPI_U], pc[EPI_U], dg[EPI_U];
                     int tag[EPI_U];
@@ -386,11 +465,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_staged(const StagedArgs g, cons
                         const int t = t0 + q * es;
                         if (t < e1) {
                             const int j = k0 + t;
-                            dg[q] = (float)(__ldg(a.col_ptr + j + 1) - __ldg(a.col_ptr + j));
-                            px[q] = a.x[j];
-                            pz[q] = a.z[j];
-                            pd[q] = a.del[j];
-                            pc[q] = __ldg(a.c + j);
+                            dg[q] = (float)(ldg_keep(a.col_ptr + j + 1, kp) - ldg_keep(a.col_ptr + j, kp));
+                            px[q] = ld_keep(a.x + j, kp);
+                            pz[q] = ld_keep(a.z + j, kp);
+                            pd[q] = ld_keep(a.del + j, kp);
+                            pc[q] = ldg_keep(a.c + j, kp);
                             tag[q] = SOC ? cone_tag(a, j) : 0;
                         }
                     }
@@ -400,9 +479,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_staged(const StagedArgs g, cons
                         if (t < e1) {
                             const float xn = col_x_update(dg[q], px[q], acc[t], pz[q], pd[q], pc[q], mu);
                             if (!SOC || tag[q] == 0) {
-                                orthant_update(a.x, a.z, a.del, k0 + t, xn, pd[q], mu);
+                                orthant_keep(a, k0 + t, xn, pd[q], mu, kp);
                             } else {
-                                a.x[k0 + t] = xn;  // a cone too large to fuse: the big-cone kernel follows
+                                st_keep(a.x + k0 + t, xn, kp);  // a cone too large to fuse: the big-cone kernel follows
                                 if (tag[q] == 1) acc[t] = xn - pd[q] / mu;  // w of the z-step, kept in place
                             }
                         }
@@ -434,16 +513,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_staged(const StagedArgs g, cons
                             for (int t = lane; t < csz; t += 32) {
                                 const float w = acc[c0 + t];
                                 const float zt = lorentz_coord(w, t, w1, alpha);
-                                a.z[k0 + c0 + t] = zt;
-                                a.del[k0 + c0 + t] = mu * (zt - w);
+                                st_keep(a.z + k0 + c0 + t, zt, kp);
+                                st_keep(a.del + k0 + c0 + t, mu * (zt - w), kp);
                             }
                         }
                     }
                 }
             } else if (H > 1) {  // partial row sums; k_row_combine adds the parts
+                const uint64_t kp = policy_keep();
                 float* out = g.part + (size_t)h * g.nseg + k0;
-                for (int t = e0; t < e1; t += es) out[t] = acc[t];
+                for (int t = e0; t < e1; t += es) st_keep(out + t, acc[t], kp);
             } else {
+                const uint64_t kp = policy_keep();
                 for (int t0 = e0; t0 < e1; t0 += es * EPI_U) {
                     float pr[EPI_U], pb[EPI_U], pl[EPI_U];
 #pragma unroll
@@ -451,15 +532,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_staged(const StagedArgs g, cons
                         const int t = t0 + q * es;
                         if (t < e1) {
                             const int i = k0 + t;
-                            pr[q] = __ldg(g.rsq + i);
-                            pb[q] = __ldg(a.b + i);
-                            pl[q] = a.lam[i];
+                            pr[q] = ldg_keep(g.rsq + i, kp);
+                            pb[q] = ldg_keep(a.b + i, kp);
+                            pl[q] = ld_keep(a.lam + i, kp);
                         }
                     }
 #pragma unroll
                     for (int q = 0; q < EPI_U; ++q) {
                         const int t = t0 + q * es;
-                        if (t < e1) row_update<float, 0>(a, k0 + t, acc[t], pr[q], pb[q], pl[q]);
+                        if (t < e1) row_keep(a, k0 + t, acc[t], pr[q], pb[q], pl[q], kp);
                     }
                 }
             }
@@ -484,10 +565,11 @@ __global__ void __launch_bounds__(256) k_row_combine(const StagedArgs g, const S
     dep_launch_next();
     dep_wait_prev();
     const int m = g.nseg;
+    const uint64_t kp = policy_keep();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        float ax = g.part[i];
-        for (int h = 1; h < g.halves; ++h) ax += g.part[(size_t)h * m + i];
-        row_update<float, 0>(a, i, ax, __ldg(g.rsq + i), __ldg(a.b + i), a.lam[i]);
+        float ax = ld_keep(g.part + i, kp);
+        for (int h = 1; h < g.halves; ++h) ax += ld_keep(g.part + (size_t)h * m + i, kp);
+        row_keep(a, i, ax, ldg_keep(g.rsq + i, kp), ldg_keep(a.b + i, kp), ld_keep(a.lam + i, kp), kp);
     }
 }
 

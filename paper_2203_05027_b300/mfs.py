@@ -41,7 +41,7 @@ class Cone(ctypes.Structure):
 class Settings(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_double), ("check_every", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("polish_iters", ctypes.c_int32), ("stop_rule", ctypes.c_int32), ("osqp_rel", ctypes.c_double),
-                ("sweep", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("sweep", ctypes.c_int32), ("adapt_mu", ctypes.c_int32), ("l2_keep", ctypes.c_int32)]
 
 
 RESID_FIELDS = ("r_prim", "r_dual", "r_cone", "r_gap", "kkt", "pobj", "dobj",
@@ -57,7 +57,8 @@ class Residuals(ctypes.Structure):
 class Check(ctypes.Structure):
     _fields_ = [("iter", ctypes.c_int64), ("kkt", ctypes.c_double), ("r_prim", ctypes.c_double),
                 ("r_dual", ctypes.c_double), ("r_cone", ctypes.c_double), ("r_gap", ctypes.c_double),
-                ("measure", ctypes.c_double), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("measure", ctypes.c_double), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("mu", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -170,7 +171,7 @@ def _cone_array(cones):
     return carr, len(cones)
 
 
-def _settings(lib, mu, check_every, precision, polish_iters, stop_rule, osqp_rel, sweep):
+def _settings(lib, mu, check_every, precision, polish_iters, stop_rule, osqp_rel, sweep, adapt_mu=0, l2_keep=False):
     st = Settings()
     lib.mfs_default_settings(ctypes.byref(st))
     st.mu = float(mu)
@@ -181,6 +182,8 @@ def _settings(lib, mu, check_every, precision, polish_iters, stop_rule, osqp_rel
     st.stop_rule = STOP_RULES[stop_rule] if isinstance(stop_rule, str) else int(stop_rule)
     st.osqp_rel = float(osqp_rel)
     st.sweep = SWEEPS[sweep] if isinstance(sweep, str) else int(sweep)
+    st.adapt_mu = int(adapt_mu)
+    st.l2_keep = int(l2_keep)
     return st
 
 
@@ -189,7 +192,7 @@ class Solver:
     (as made by ``instances``)."""
 
     def __init__(self, prob, mu=1.0, check_every=25, precision="fp64", polish_iters=50, stream=None,
-                 stop_rule="kkt", osqp_rel=10.0, sweep="auto"):
+                 stop_rule="kkt", osqp_rel=10.0, sweep="auto", adapt_mu=0, l2_keep=False):
         lib = load()
         self._lib = lib
         m, n = int(prob["m"]), int(prob["n"])
@@ -199,7 +202,7 @@ class Solver:
         b = _f64(prob["b"], m)
         c = _f64(prob["c"], n)
         carr, ncones = _cone_array(prob["cones"])
-        st = _settings(lib, mu, check_every, precision, polish_iters, stop_rule, osqp_rel, sweep)
+        st = _settings(lib, mu, check_every, precision, polish_iters, stop_rule, osqp_rel, sweep, adapt_mu, l2_keep)
         h = ctypes.c_void_p()
         stream_ptr = ctypes.c_void_p(int(stream)) if stream else None
         code = lib.mfs_create(m, n, len(row), row.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
@@ -215,14 +218,15 @@ class Solver:
 
     @classmethod
     def from_device(cls, m, n, nnz, row_ptr, col_ptr, val_ptr, b_ptr, c_ptr, cones, mu=1.0, check_every=25,
-                    precision="fp64", polish_iters=50, stream=None, stop_rule="kkt", osqp_rel=10.0, sweep="auto"):
+                    precision="fp64", polish_iters=50, stream=None, stop_rule="kkt", osqp_rel=10.0, sweep="auto",
+                    adapt_mu=0, l2_keep=False):
         """mfs_create_device: the COO (int64 row, col; float64 val), b and c (float64) given as device
         pointers (ints, e.g. torch tensors' data_ptr()); cones as for the host form."""
         self = cls.__new__(cls)
         lib = load()
         self._lib = lib
         carr, ncones = _cone_array(cones)
-        st = _settings(lib, mu, check_every, precision, polish_iters, stop_rule, osqp_rel, sweep)
+        st = _settings(lib, mu, check_every, precision, polish_iters, stop_rule, osqp_rel, sweep, adapt_mu, l2_keep)
         h = ctypes.c_void_p()
         dp = [ctypes.c_void_p(int(p)) if p else None for p in (row_ptr, col_ptr, val_ptr, b_ptr, c_ptr)]
         code = lib.mfs_create_device(int(m), int(n), int(nnz), *dp, ncones, carr, ctypes.byref(st),

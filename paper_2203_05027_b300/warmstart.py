@@ -5,7 +5,9 @@ x0 ~ U[0,1]^n, y0 ~ N(0,1)^m, s0 ~ U[0,1]^n, b0 = A x0, c0 = A^T y0 + s0, K = R^
 parameter theta ~ N(0, I_p) moves b = b0 + B_b theta and c = c0 + B_c theta, with B_b, B_c
 having i.i.d. N(0, sigma^2) entries. Solutions (x, lambda) of sampled members, produced by the
 shared-A solver (mfs_shared_*), train the tensor-core MLP (mfs_mlp_*) theta -> (x, lambda);
-its prediction then warm-starts the solver (mfs_shared_warm_start_device).
+its prediction then warm-starts the solver (mfs_shared_warm_start_device). Two starts that need no
+network, made from the same training solves, are measured beside it: their mean, and the solution
+of the training member whose theta is nearest.
 
 Every arithmetic step of solving and training runs in libmfs; this module draws the seeded
 family (numpy), moves buffers and records counts, times and prediction errors; torch provides
@@ -173,7 +175,11 @@ def solve_stream(fam, theta, tol, max_iter, slots=256, check_every=100, warm=Non
             sh.load_slots(sl, bd.data_ptr(), cd.data_ptr())
         else:
             rows = torch.from_numpy(idx).cuda()
-            xw, lw = warm[0][rows].contiguous(), warm[1][rows].contiguous()
+            if isinstance(warm, _RowStart):
+                xw, lw = warm[rows]
+                xw, lw = xw.contiguous(), lw.contiguous()
+            else:
+                xw, lw = warm[0][rows].contiguous(), warm[1][rows].contiguous()
             sh.load_slots_warm(sl, bd.data_ptr(), cd.data_ptr(), xw.data_ptr(), lw.data_ptr())
         member[sl] = idx
         age[sl] = 0
@@ -208,11 +214,46 @@ def solve_stream(fam, theta, tol, max_iter, slots=256, check_every=100, warm=Non
     return iters, kkt0, sec, Xo, Lo
 
 
-def evaluate(fam, net, theta, tol, max_iter, mu=1.0, check_every=100, precision="fp32", slots=256):
-    """Cold against learned warm start on the members theta (count x p, host), both solved by
+def mean_start(T, n):
+    """Non-learned start: the mean training target (x-bar, lambda-bar), the same for every member."""
+    mu = T.mean(dim=0, keepdim=True)
+    return mu[:, :n].contiguous(), mu[:, n:].contiguous()
+
+
+def nearest_start(theta_train, T, theta, n, chunk=4096):
+    """Non-learned start: for each member, the training target of the training theta nearest to its
+    own (Euclidean distance in parameter space). theta_train: device FP32 [count][p]; theta: host
+    [members][p]. Returns device row indices into T (the starts are gathered when a member enters)."""
+    import torch
+    q = torch.from_numpy(np.ascontiguousarray(theta, np.float32)).cuda()
+    best = torch.empty(q.shape[0], dtype=torch.int64, device="cuda")
+    for s0 in range(0, q.shape[0], chunk):
+        d = torch.cdist(q[s0:s0 + chunk].double(), theta_train.double())
+        best[s0:s0 + chunk] = d.argmin(dim=1)
+    return best
+
+
+class _RowStart:
+    """A start given as rows of a target matrix T ([count][n + m]): member i starts from row idx[i]
+    (idx None: the same single row 0 of X and L for all)."""
+
+    def __init__(self, X, L, idx=None):
+        self.X, self.L, self.idx = X, L, idx
+
+    def __getitem__(self, k):
+        import torch
+        rows = k if self.idx is None else self.idx[k]
+        if self.idx is None:
+            rows = torch.zeros_like(k)
+        return (self.X[rows], self.L[rows])
+
+
+def evaluate(fam, net, theta, tol, max_iter, mu=1.0, check_every=100, precision="fp32", slots=256, starts=None):
+    """Cold start against warm starts on the members theta (count x p, host), each arm solved by
     continuous batching (solve_stream): per member, the iteration at which the relative KKT residual
     first met tol (-1 if never within max_iter) and the KKT at entry, and the wall time for the whole
-    set (the warm arm includes the network's inference)."""
+    set. Arms: "cold" (zero start), "mlp" (the network's prediction; its inference time included) and
+    any further named starts (pairs of device FP32 arrays [count][n], [count][m], or _RowStart)."""
     import torch
     base = fam["base"]
     n, m = base["n"], base["m"]
@@ -225,12 +266,21 @@ def evaluate(fam, net, theta, tol, max_iter, mu=1.0, check_every=100, precision=
     Xw, Lw = predict(net, th, n, m)
     torch.cuda.synchronize()
     t_pred = time.perf_counter() - t0
-    its, k0, sec, _, _ = solve_stream(fam, theta, tol, max_iter, slots, check_every, (Xw, Lw), mu, precision)
-    out["warm"] = {"iters": its, "seconds": t_pred + sec, "predict_seconds": t_pred, "kkt0": k0}
-    # prediction error against the point where the cold arm ended (per member)
-    ex = (torch.linalg.vector_norm(Xw - Xc, dim=1) / torch.linalg.vector_norm(Xc, dim=1).clamp_min(1e-30)).cpu().numpy()
-    el = (torch.linalg.vector_norm(Lw - Lc, dim=1) / torch.linalg.vector_norm(Lc, dim=1).clamp_min(1e-30)).cpu().numpy()
-    out["pred_rel_err_x"], out["pred_rel_err_lam"] = ex, el
+    arms = {"mlp": (Xw, Lw)}
+    arms.update(starts or {})
+    for name, st in arms.items():
+        its, k0, sec, _, _ = solve_stream(fam, theta, tol, max_iter, slots, check_every, st, mu, precision)
+        rec = {"iters": its, "seconds": sec + (t_pred if name == "mlp" else 0.0), "kkt0": k0}
+        if name == "mlp":
+            rec["predict_seconds"] = t_pred
+        # error of the start against the point where the cold arm ended (per member)
+        rows = torch.arange(theta.shape[0], device="cuda")
+        Xs, Ls = st[rows] if isinstance(st, _RowStart) else st
+        rec["rel_err_x"] = (torch.linalg.vector_norm(Xs - Xc, dim=1) /
+                            torch.linalg.vector_norm(Xc, dim=1).clamp_min(1e-30)).cpu().numpy()
+        rec["rel_err_lam"] = (torch.linalg.vector_norm(Ls - Lc, dim=1) /
+                              torch.linalg.vector_norm(Lc, dim=1).clamp_min(1e-30)).cpu().numpy()
+        out[name] = rec
     return out
 
 
@@ -263,22 +313,30 @@ def run(train=50_000, test=1000, m=20_000, n=50_000, nnz_per_col=8, p=32, sigma=
     val = eval_loss(net, thv, Tv, batch)
     log(json.dumps({"stage": "train", "epochs": epochs, "steps": epochs * (train // batch), "seconds": tsec,
                     "loss_first": losses[0], "loss_last": losses[-1], "val_loss": val}))
-    del T, Tv
-    torch.cuda.empty_cache()
+    del Tv
     th_test = thetas(test, seed + 7, p)
-    res = evaluate(fam, net, th_test, eval_tol, eval_cap, mu=mu)
-    summary = {"stage": "evaluate", "tol": eval_tol, "cap": eval_cap, "members": test}
-    for arm in ("cold", "warm"):
+    # non-learned starts from the same training solves: their mean, and the nearest training theta's
+    Xmean, Lmean = mean_start(T, n)
+    near = nearest_start(theta, T, th_test, n)
+    starts = {"mean": _RowStart(Xmean, Lmean), "nearest": _RowStart(T[:, :n], T[:, n:], near)}
+    res = evaluate(fam, net, th_test, eval_tol, eval_cap, mu=mu, starts=starts)
+    summary = {"stage": "evaluate", "tol": eval_tol, "cap": eval_cap, "members": test,
+               "train_solves": train, "train_tol": data_tol, "train_cap": data_cap}
+    ic = res["cold"]["iters"]
+    for arm in ("cold", "mlp", "mean", "nearest"):
         r = res[arm]
         summary[arm] = {"seconds": r["seconds"], "kkt0_median": float(np.median(r["kkt0"])),
                         **_its_summary(r["iters"])}
-    summary["warm"]["predict_seconds"] = res["warm"]["predict_seconds"]
-    ic, iw = res["cold"]["iters"], res["warm"]["iters"]
-    both = (ic > 0) & (iw > 0)
-    summary["paired"] = int(both.sum())
-    summary["iters_ratio_median"] = float(np.median(iw[both] / ic[both])) if both.any() else None
-    summary["pred_rel_err_x_median"] = float(np.median(res["pred_rel_err_x"]))
-    summary["pred_rel_err_lam_median"] = float(np.median(res["pred_rel_err_lam"]))
+        if arm != "cold":
+            iw = r["iters"]
+            both = (ic > 0) & (iw > 0)
+            summary[arm]["paired"] = int(both.sum())
+            summary[arm]["iters_ratio_median"] = float(np.median(iw[both] / ic[both])) if both.any() else None
+            summary[arm]["rel_err_x_median"] = float(np.median(r["rel_err_x"]))
+            summary[arm]["rel_err_lam_median"] = float(np.median(r["rel_err_lam"]))
+    summary["mlp"]["predict_seconds"] = res["mlp"]["predict_seconds"]
+    del T
+    torch.cuda.empty_cache()
     log(json.dumps(summary))
     if single > 0:
         b, c = data_of(fam, th_test[:single])

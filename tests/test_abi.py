@@ -57,6 +57,7 @@ def test_struct_sizes_match_header(lib, tmp_path):
     lib.mfs_default_settings(ctypes.byref(st))
     assert (st.mu, st.check_every, st.precision, st.polish_iters) == (1.0, 25, 0, 50)
     assert (st.stop_rule, st.osqp_rel, st.sweep) == (mfs.STOP_KKT, 10.0, mfs.SWEEP_AUTO)
+    assert (st.adapt_mu, st.l2_keep) == (0, 0)
 
 
 def tiny():
@@ -96,6 +97,12 @@ def test_invalid_settings_rejected_on_host(lib):
     with pytest.raises(mfs.MfsError) as e:
         mfs.Solver(tiny(), stop_rule="osqp_inf", osqp_rel=0.0)
     assert e.value.status == mfs.MFS_ERR_INVALID and "osqp_rel" in str(e.value)
+    with pytest.raises(mfs.MfsError) as e:
+        mfs.Solver(tiny(), adapt_mu=-1)
+    assert e.value.status == mfs.MFS_ERR_INVALID and "adapt_mu" in str(e.value)
+    with pytest.raises(mfs.MfsError) as e:
+        mfs.Solver(tiny(), l2_keep=2)
+    assert e.value.status == mfs.MFS_ERR_INVALID and "l2_keep" in str(e.value)
 
 
 def test_null_arguments(lib):

@@ -432,3 +432,25 @@ def test_invalid_large_coo_rejected_by_gpu_setup(case):
         assert f"out of range at entry {q1}" in str(e.value)
     ok = mfs.Solver(prob, precision="fp32")     # the pinned staging is free again afterwards
     assert ok.info()["o"] == prob["row"].size
+
+
+@pytest.mark.parametrize("mu0", [1.0, 0.02])
+def test_balanced_mu_solve_matches_oracle(mu0):
+    """The residual-balancing variant (settings.adapt_mu, outside the paper): mfs_solve in FP64 with
+    a tolerance it cannot meet runs exactly max_iter iterations, changing mu at the checks 3, 6, 12,
+    24, ...; the oracle's solve loop with the same rule must take the same mu at every check and end
+    at the same iterate (1e-10)."""
+    prob = I.small_lp(0, m=60, n=150)
+    K, cap = 25, 6000
+    s = mfs.Solver(prob, mu=mu0, precision="fp64", check_every=K, adapt_mu=3)
+    status, its = s.solve(1e-30, cap)
+    assert status == "MAX_ITER" and its == cap
+    hist, count = s.history()
+    orc = oracle.make_oracle(prob, mu=mu0)
+    it, ohist = oracle.solve_balanced(orc, 1e-30, cap, K, 3)
+    assert it == cap and count == len(ohist)
+    gmu = [h["mu"] for h in hist]
+    omu = [h[2] for h in ohist]
+    assert gmu == omu, (gmu, omu)
+    assert len(set(omu)) > 1  # the rule did change mu on this problem
+    compare(s.solution(), orc.state(), TOL["fp64"], f"balanced mu from {mu0}")

@@ -191,3 +191,66 @@ def test_gpu_and_host_setup_build_the_same_layouts(sweep):
     sa, sb = a.solution(), b.solution()
     for k in sa:
         assert np.array_equal(sa[k], sb[k]), k
+
+
+def test_staged_state_changes():
+    """The staged passes keep the iterate's vectors in L2 between passes (evict-last accesses); the
+    state must stay Algorithm 1's whatever changed it in between: a change of mu, the chunked sweeps
+    for a while, a warm start."""
+    prob = I.large_lp(6, m=40_000, n=100_000)
+    s = mfs.Solver(prob, precision="fp32", polish_iters=0, sweep="staged")
+    orc = oracle.make_oracle(prob, dtype=np.float32)
+    s.iterate(30)
+    orc.iterate(30)
+    compare(s.solution(), orc.state(), TOL["fp32"], "staged: 30 iterations")
+    s.set_mu(1.7)
+    orc.set_mu(1.7)
+    s.iterate(20)
+    orc.iterate(20)
+    compare(s.solution(), orc.state(), TOL["fp32"], "staged: after a change of mu")
+    s.set_sweep("chunked")
+    s.iterate(10)
+    s.set_sweep("staged")
+    s.iterate(10)
+    orc.iterate(20)
+    compare(s.solution(), orc.state(), TOL["fp32"], "staged: chunked sweeps in between")
+    sol = s.solution()
+    x0, lam0 = sol["x"] * 0.5, sol["lam"] * 0.5
+    s.warm_start(x0, lam0)
+    orc.warm_start(x0, lam0)
+    s.iterate(25)
+    orc.iterate(25)
+    compare(s.solution(), orc.state(), TOL["fp32"], "staged: after a warm start")
+
+
+def _persisting_limit():
+    from cuda.bindings import runtime as rt
+    err, v = rt.cudaDeviceGetLimit(rt.cudaLimit.cudaLimitPersistingL2CacheSize)
+    assert err == rt.cudaError_t.cudaSuccess
+    return v
+
+
+def test_l2_keep_raises_and_restores_the_set_aside():
+    """settings.l2_keep: a solver with staged passes raises the context's persisting-L2 set-aside to the
+    device's maximum while it exists and the last one puts the previous value back; without it the
+    limit is left alone. The iterate is the same bit for bit either way (the setting only moves lines
+    between L2 classes)."""
+    from cuda.bindings import runtime as rt
+    prob = I.large_lp(7, m=40_000, n=100_000)
+    before = _persisting_limit()
+    plain = mfs.Solver(prob, precision="fp32", polish_iters=0, sweep="staged")
+    assert _persisting_limit() == before
+    err, maxp = rt.cudaDeviceGetAttribute(rt.cudaDeviceAttr.cudaDevAttrMaxPersistingL2CacheSize, 0)
+    a = mfs.Solver(prob, precision="fp32", polish_iters=0, sweep="staged", l2_keep=True)
+    assert _persisting_limit() == max(before, maxp)
+    b = mfs.Solver(prob, precision="fp32", polish_iters=0, sweep="staged", l2_keep=True)
+    a.close()
+    assert _persisting_limit() == max(before, maxp)  # b still holds it
+    for s in (plain, b):
+        s.iterate(40)
+    sp, sb = plain.solution(), b.solution()
+    for k in sp:
+        assert np.array_equal(sp[k], sb[k]), k
+    b.close()
+    plain.close()
+    assert _persisting_limit() == before

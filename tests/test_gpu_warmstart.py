@@ -24,18 +24,23 @@ def trained():
     net = mfs.MLP(32, 512, n + m, 256, seed=0)
     net.fit_output_scaling(4096, T.data_ptr(), 1e-3)
     losses, _ = W.train_fn(net, theta, T, 60, 1e-3, 256)
-    return fam, net, losses
+    return fam, net, losses, theta, T
 
 
 def test_training_reduces_the_loss(trained):
-    _, _, losses = trained
+    _, _, losses, _, _ = trained
     assert losses[-1] < 0.75 * losses[0]
 
 
 def test_warm_start_beats_cold_start_on_held_out_members(trained):
-    fam, net, _ = trained
-    res = W.evaluate(fam, net, W.thetas(64, 7), 1e-4, 60_000, check_every=100)
-    cold, warm = res["cold"], res["warm"]
+    fam, net, _, theta, T = trained
+    n = fam["base"]["n"]
+    th = W.thetas(64, 7)
+    Xm, Lm = W.mean_start(T, n)
+    starts = {"mean": W._RowStart(Xm, Lm),
+              "nearest": W._RowStart(T[:, :n], T[:, n:], W.nearest_start(theta, T, th, n))}
+    res = W.evaluate(fam, net, th, 1e-4, 60_000, check_every=100, starts=starts)
+    cold, warm = res["cold"], res["mlp"]
     # the predicted point is much closer to optimal than the zero start ...
     assert np.median(warm["kkt0"]) < 0.7 * np.median(cold["kkt0"])
     # ... and every member the cold start solves, the warm start solves too, in fewer iterations
@@ -45,3 +50,7 @@ def test_warm_start_beats_cold_start_on_held_out_members(trained):
     assert both.sum() >= 48
     assert iw[both].mean() < 0.98 * ic[both].mean()
     assert np.median(iw[both] / ic[both]) < 1.0
+    # what the network adds over the two starts that need no network: a start closer to optimal
+    for arm in ("mean", "nearest"):
+        assert np.median(warm["kkt0"]) < 0.7 * np.median(res[arm]["kkt0"]), arm
+        assert np.median(warm["rel_err_x"]) < np.median(res[arm]["rel_err_x"]), arm

@@ -523,3 +523,37 @@ def test_literal_state_from_a_reduced_state(maker):
     y, g = orc.consistent_y_gamma(x, lam)
     s = orc.state()
     assert np.allclose(s.y, y, rtol=0, atol=1e-13) and np.array_equal(s.gam, g)
+
+
+# ---------------------------------------------------------------- residual-balanced mu (a variant)
+
+@pytest.mark.parametrize("mu0", [1.0, 1e-3, 1e3])
+def test_balanced_mu_reaches_the_original_optimum(mu0):
+    """Residual balancing changes only the penalty, not the problem: from any starting mu the
+    iteration converges to the LP optimum HiGHS finds, and a badly chosen mu is moved towards
+    balance (raised from 1e-3, lowered from 1e3) rather than further away."""
+    from scipy.optimize import linprog
+    prob = I.small_lp(0, m=20, n=50)
+    A = sp.coo_matrix((prob["val"], (prob["row"], prob["col"])), shape=(prob["m"], prob["n"])).tocsr()
+    ref = linprog(prob["c"], A_eq=A, b_eq=prob["b"], bounds=(0, None), method="highs")
+    assert ref.status == 0
+    orc = oracle.make_oracle(prob, mu=mu0)
+    it, hist = oracle.solve_balanced(orc, 1e-9, 400_000, 25, 4)
+    r = orc.residuals()
+    assert r["kkt"] <= 1e-9, (it, r["kkt"])
+    assert abs(r["pobj"] - ref.fun) < 1e-7 * (1 + abs(ref.fun))
+    mus = np.array([h[2] for h in hist])
+    assert mus.min() >= mu0 / 256 * (1 - 1e-12) and mus.max() <= mu0 * 256 * (1 + 1e-12)
+    if mu0 < 1e-2:
+        assert mus[-1] > 10 * mu0
+    if mu0 > 1e2:
+        assert mus[-1] < 0.1 * mu0
+
+
+def test_balanced_mu_off_is_the_fixed_mu_iteration():
+    prob = I.small_lp(1, m=30, n=80)
+    a, b = oracle.make_oracle(prob), oracle.make_oracle(prob)
+    it, hist = oracle.solve_balanced(a, 1e-30, 1000, 25, 0)
+    b.iterate(1000)
+    assert it == 1000 and all(h[2] == 1.0 for h in hist)
+    assert np.array_equal(a.state().x, b.state().x) and np.array_equal(a.state().lam, b.state().lam)

@@ -147,6 +147,9 @@ typedef struct {
     int32_t launches_per_iter;  /* kernel launches of one iteration (sweeps, long chunks, big cones) */
     int32_t sweep_col, sweep_row; /* MFS_SWEEP_CHUNKED or MFS_SWEEP_STAGED: kernels of the column and
                                      row passes at the current precision */
+    int32_t col_parts, row_parts; /* staged passes: CTAs per column (row) group, each streaming its
+                                     share of the gathered vector into partial sums that a combine
+                                     kernel adds in a fixed order (1: no split); 0 without staged passes */
 } mfs_info_t;
 
 /* Defaults: mu = 1, check_every = 25, precision = MFS_FP64, polish_iters = 50, stop_rule =

@@ -470,16 +470,25 @@ __global__ void k_stg_ovf_warps(const int* __restrict__ grp, int G, const int* _
     }
 }
 
-// sum of the squared FP32-rounded values of each row, in FP64, rounded to FP32
-__global__ void k_row_sq(const int* __restrict__ row_ptr, const double* __restrict__ val, int m, float* __restrict__ rsq) {
+// 1/(1 + r_i) of each row, r_i the sum of the squared FP32-rounded values of row i: in FP64, rounded
+// to FP32 (the staged row pass multiplies by it)
+__global__ void k_row_inv(const int* __restrict__ row_ptr, const double* __restrict__ val, int m,
+                          float* __restrict__ rinv) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         double r = 0.0;
         for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
             const double a = (double)(float)val[k];
             r += a * a;
         }
-        rsq[i] = (float)r;
+        rinv[i] = (float)(1.0 / (1.0 + r));
     }
+}
+
+// 1/(1 + d_j) of each column, d_j its number of nonzeros, rounded to FP32 (the staged column pass
+// multiplies by it)
+__global__ void k_col_inv(const int* __restrict__ col_ptr, int n, float* __restrict__ dinv) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        dinv[j] = (float)(1.0 / (1.0 + (double)(col_ptr[j + 1] - col_ptr[j])));
 }
 
 }  // namespace setup

@@ -102,6 +102,8 @@ struct mfs_solver {
     int4 *cdesc = nullptr, *rdesc = nullptr;
     int *soc_start = nullptr, *soc_size = nullptr, *big_list = nullptr;
     unsigned char* soc_big = nullptr;
+    int* stg_big_list = nullptr;  // the staged column pass fuses every cone of at most WC columns;
+    int stg_nbig = 0;             // these are the larger ones, left to k_bigcone_sweep
     double *part_row = nullptr, *part_col = nullptr, *part_big = nullptr, *s_buf = nullptr, *status = nullptr;
     double* r_buf = nullptr;  // m: A x - b of the last residual evaluation with write_all_s
     double* h_status = nullptr;      // pinned
@@ -812,10 +814,18 @@ void launch_col(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
         if (staged_col(s)) {
             const StagedArgsT& g = s->stg_col;
             const size_t smem = mfs::staged::smem_bytes(mfs::staged::RB_COL, mfs::staged::S_COL, g.maxg_pad, g.R);
+            const int grid = std::min(g.G * g.halves, s->num_sms);
             if (s->has_soc)
-                launch_dep(MFS_STAGED_COL_SOC, std::min(g.G, s->num_sms), mfs::staged::NTHREADS, smem, st, g, a);
+                launch_dep(MFS_STAGED_COL_SOC, grid, mfs::staged::NTHREADS, smem, st, g, a);
             else
-                launch_dep(MFS_STAGED_COL, std::min(g.G, s->num_sms), mfs::staged::NTHREADS, smem, st, g, a);
+                launch_dep(MFS_STAGED_COL, grid, mfs::staged::NTHREADS, smem, st, g, a);
+            if (g.halves > 1) {
+                const int cgrid = (g.nsub + mfs::staged::CWPB - 1) / mfs::staged::CWPB;
+                if (s->has_soc)
+                    launch_dep(MFS_COL_COMBINE_SOC, cgrid, 32 * mfs::staged::CWPB, 0, st, g, a);
+                else
+                    launch_dep(MFS_COL_COMBINE, cgrid, 32 * mfs::staged::CWPB, 0, st, g, a);
+            }
             return;
         }
     }
@@ -829,6 +839,16 @@ void launch_col(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
 }
 template <typename T>
 void launch_big(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (staged_col(s)) {  // the staged pass's own list
+            if (s->stg_nbig) {
+                SweepArgs<T> b = a;
+                b.big_list = s->stg_big_list;
+                k_bigcone_sweep<T><<<s->stg_nbig, NT, 0, st>>>(b);
+            }
+            return;
+        }
+    }
     if (s->nbig) k_bigcone_sweep<T><<<s->nbig, NT, 0, st>>>(a);
 }
 template <typename T, int MODE>
@@ -866,9 +886,10 @@ void launch_iteration(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
 
 int launches_per_iteration(const mfs_solver* s) {
     const bool f32 = s->precision == MFS_FP32_MIXED;
-    const int col = s->ncc ? ((f32 && staged_col(s)) ? 1 : 1 + (s->nlc ? 1 : 0)) : 0;
+    const int col = s->ncc ? ((f32 && staged_col(s)) ? (s->stg_col.halves > 1 ? 2 : 1) : 1 + (s->nlc ? 1 : 0)) : 0;
     const int row = s->nrc ? ((f32 && staged_row(s)) ? (s->stg_row.halves > 1 ? 2 : 1) : 1 + (s->nlr ? 1 : 0)) : 0;
-    return col + (s->nbig ? 1 : 0) + row;
+    const int big = (f32 && staged_col(s)) ? (s->stg_nbig ? 1 : 0) : (s->nbig ? 1 : 0);
+    return col + big + row;
 }
 
 template <typename T>
@@ -1225,13 +1246,49 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
         unit_start.resize(P.n);
         for (int j = 0; j < P.n; ++j) unit_start[j] = j;
         for (size_t q = 0; q < P.soc_start.size(); ++q)
-            if (!P.soc_big[q])
+            if (P.soc_size[q] <= WC)
                 for (int t = 1; t < P.soc_size[q]; ++t) unit_start[P.soc_start[q] + t] = P.soc_start[q];
     }
-    if (!plan_staged(P.col_ptr, P.n, P.m, s->num_sms, RB_COL, S_COL, (size_t)optin, C,
-                     s->has_soc ? &unit_start : nullptr) ||
-        !plan_staged(P.row_ptr, P.m, P.n, std::max(1, s->num_sms / ROW_HALVES), RB_ROW, S_ROW, (size_t)optin, W))
-        return MFS_OK;  // vectors too long for the split tables: chunked sweeps only
+    // The column pass likewise, in parts where v is long enough (each CTA streams at least 8 blocks)
+    // and the column groups of half as many CTAs still fit; k_col_combine then adds the parts and
+    // runs the epilogue, each warp of the split on its own warp range held in shared memory.
+    int col_parts = 1;
+    {
+        const int R = std::max(1, (P.m + RB_COL - 1) / RB_COL);
+        bool ok = false;
+        for (int h = COL_PARTS_MAX; h >= 1 && !ok; h /= 2) {
+            const int groups = std::max(1, s->num_sms / h);
+            if (h > 1 && R / h < 8) continue;
+            StagedHost T;
+            if (!plan_staged(P.col_ptr, P.n, P.m, groups, RB_COL, S_COL, (size_t)optin, T,
+                             s->has_soc ? &unit_start : nullptr))
+                continue;
+            if (h > 1 && T.G > groups) continue;  // groups split for shared memory: fewer parts
+            C = std::move(T);
+            col_parts = h;
+            ok = true;
+        }
+        if (!ok) return MFS_OK;  // vectors too long for the split tables: chunked sweeps only
+    }
+    // The row pass splits each row group over `row_parts` CTAs, each streaming its share of x's
+    // blocks into partial row sums (k_row_combine adds them). Two parts, or more where every CTA
+    // still streams at least 8 blocks and the larger row groups still fit in shared memory.
+    int row_parts = ROW_HALVES;
+    {
+        const int R = std::max(1, (P.n + RB_ROW - 1) / RB_ROW);
+        bool ok = false;
+        for (int h = ROW_PARTS_MAX; h >= ROW_HALVES && !ok; h /= 2) {
+            const int groups = std::max(1, s->num_sms / h);
+            if (h > ROW_HALVES && R / h < 8) continue;
+            StagedHost T;
+            if (!plan_staged(P.row_ptr, P.m, P.n, groups, RB_ROW, S_ROW, (size_t)optin, T)) continue;
+            if (h > ROW_HALVES && T.G > groups) continue;  // groups split for shared memory: fewer parts
+            W = std::move(T);
+            row_parts = h;
+            ok = true;
+        }
+        if (!ok) return MFS_OK;
+    }
     // the orders on the device: where the host built them, uploaded for the set-up only
     const bool dev = P.dev.on;
     const int *crow = P.dev.crow, *rcol = P.dev.rcol;
@@ -1284,6 +1341,8 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
         return MFS_OK;
     };
     gc.wcone = nullptr;
+    gc.ctag = nullptr;
+    gc.soc_big = nullptr;
     if (s->has_soc) {  // each warp's Lorentz cones: those starting within its columns
         std::vector<int2> wc((size_t)C.G * NW);
         for (int g2 = 0; g2 < C.G; ++g2)
@@ -1297,19 +1356,64 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
         int2* d_wc = nullptr;
         TRY(upload(s, &d_wc, wc.data(), wc.size()));
         gc.wcone = d_wc;
+        // the staged pass fuses every cone of at most WC columns, however many nonzeros it has (the
+        // chunked sweeps leave cones with more than WT nonzeros to the big-cone kernel as well)
+        std::vector<unsigned char> tag((size_t)P.n, 0), big(P.soc_start.size(), 0);
+        std::vector<int> blist;
+        for (size_t q = 0; q < P.soc_start.size(); ++q) {
+            big[q] = P.soc_size[q] > WC ? 1 : 0;
+            if (big[q]) blist.push_back((int)q);
+            for (int t = 0; t < P.soc_size[q]; ++t) tag[(size_t)P.soc_start[q] + t] = big[q] ? 2 : 1;
+        }
+        unsigned char *d_tag = nullptr, *d_big = nullptr;
+        TRY(upload(s, &d_tag, tag.data(), tag.size()));
+        TRY(upload(s, &d_big, big.data(), big.size()));
+        if (!blist.empty()) TRY(upload(s, &s->stg_big_list, blist.data(), blist.size()));
+        s->stg_nbig = (int)blist.size();
+        gc.ctag = d_tag;
+        gc.soc_big = d_big;
     }
     s->stg_col = gc;
     s->stg_row = gr;
-    TRY(fill(C, s->stg_col, s->s32.v, 1, P.n));
-    TRY(fill(W, s->stg_row, s->s32.x, ROW_HALVES, P.m));
-    float* d_rsq = nullptr;
-    TRY(dalloc(s, &d_rsq, (size_t)std::max(P.m, 1)));
+    TRY(fill(C, s->stg_col, s->s32.v, col_parts, P.n));
+    s->stg_col.csub = nullptr;
+    s->stg_col.nsub = 0;
+    if (col_parts > 1) {
+        // k_col_combine's pieces: about CSUB columns, a cut inside a fused cone moved to its end
+        std::vector<int4> sub;
+        size_t q = 0;  // the next Lorentz cone
+        for (int c0 = 0; c0 < P.n;) {
+            int c1 = std::min(P.n, c0 + mfs::staged::CSUB);
+            if (s->has_soc && c1 < P.n && unit_start[c1] != c1) {
+                const int st = unit_start[c1];
+                const size_t k = (size_t)(std::lower_bound(P.soc_start.begin(), P.soc_start.end(), st) -
+                                          P.soc_start.begin());
+                c1 = st + P.soc_size[k];
+            }
+            const size_t q0 = q;
+            while (q < P.soc_start.size() && P.soc_start[q] < c1) ++q;
+            sub.push_back(make_int4(c0, c1, (int)q0, (int)q));
+            c0 = c1;
+        }
+        int4* d_sub = nullptr;
+        TRY(upload(s, &d_sub, sub.data(), sub.size()));
+        s->stg_col.csub = d_sub;
+        s->stg_col.nsub = (int)sub.size();
+    }
+    TRY(fill(W, s->stg_row, s->s32.x, row_parts, P.m));
+    float *d_rinv = nullptr, *d_dinv = nullptr;
+    TRY(dalloc(s, &d_rinv, (size_t)std::max(P.m, 1)));
+    TRY(dalloc(s, &d_dinv, (size_t)std::max(P.n, 1)));
     if (P.m > 0)
-        mfs::setup::k_row_sq<<<(int)std::min<int64_t>((P.m + 255) / 256, 8 * s->num_sms), 256, 0, s->stream>>>(
-            s->row_ptr, rval, P.m, d_rsq);
+        mfs::setup::k_row_inv<<<(int)std::min<int64_t>((P.m + 255) / 256, 8 * s->num_sms), 256, 0, s->stream>>>(
+            s->row_ptr, rval, P.m, d_rinv);
+    if (P.n > 0)
+        mfs::setup::k_col_inv<<<(int)std::min<int64_t>((P.n + 255) / 256, 8 * s->num_sms), 256, 0, s->stream>>>(
+            s->col_ptr, P.n, d_dinv);
     CUDA_TRY(s, cudaGetLastError());
     CUDA_TRY(s, cudaStreamSynchronize(s->stream));  // the uploaded orders are freed on return
-    s->stg_row.rsq = d_rsq;
+    s->stg_row.rinv = d_rinv;
+    s->stg_col.dinv = d_dinv;
     // the limit is a property of the kernel, shared by all solvers: allow the device's maximum
     CUDA_TRY(s, cudaFuncSetAttribute(MFS_STAGED_COL, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     CUDA_TRY(s, cudaFuncSetAttribute(MFS_STAGED_COL_SOC, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -1430,7 +1534,7 @@ static mfs_status time_kernels_t(mfs_solver* s, State<T>& st, int64_t k, double*
     const double kd = kk > 0 ? (double)kk : 1.0;
     out[0] = tc / kd;
     out[1] = tr / kd;
-    out[2] = s->nbig ? tb / kd : 0.0;
+    out[2] = tb / kd;
     out[3] = tall / kd;
     CUDA_TRY(s, cudaGetLastError());
     return MFS_OK;
@@ -2003,6 +2107,8 @@ mfs_status mfs_get_info(const mfs_solver* s, mfs_info_t* out) {
     const bool f32 = s->precision == MFS_FP32_MIXED;
     out->sweep_col = (f32 && staged_col(s)) ? MFS_SWEEP_STAGED : MFS_SWEEP_CHUNKED;
     out->sweep_row = (f32 && staged_row(s)) ? MFS_SWEEP_STAGED : MFS_SWEEP_CHUNKED;
+    out->col_parts = s->stg_ok ? s->stg_col.halves : 0;
+    out->row_parts = s->stg_ok ? s->stg_row.halves : 0;
     return MFS_OK;
 }
 

@@ -50,6 +50,12 @@ namespace staged {
 #ifndef MFS_STG_ROW_HALVES
 #define MFS_STG_ROW_HALVES 2
 #endif
+#ifndef MFS_STG_ROW_PARTS_MAX
+#define MFS_STG_ROW_PARTS_MAX 4
+#endif
+#ifndef MFS_STG_COL_PARTS_MAX
+#define MFS_STG_COL_PARTS_MAX 2
+#endif
 #ifndef MFS_STG_NW
 #define MFS_STG_NW 15
 #endif
@@ -59,6 +65,10 @@ constexpr int RB_ROW = MFS_STG_RB_ROW;  // entries of x per block, row pass
 constexpr int S_ROW = MFS_STG_S_ROW;
 constexpr int ROW_HALVES = MFS_STG_ROW_HALVES;  // row pass: two CTAs per row group, each streaming
                                                 // half of x (x is 2.5x longer than v)
+constexpr int ROW_PARTS_MAX = MFS_STG_ROW_PARTS_MAX;  // or more parts, where the row groups still fit
+                                                      // (fewer, fuller blocks per CTA)
+constexpr int COL_PARTS_MAX = MFS_STG_COL_PARTS_MAX;  // column pass: likewise, where v is long enough
+                                                      // and the column groups fit (k_col_combine)
 constexpr int NW = MFS_STG_NW;  // consumer warps per CTA, plus one producer warp (15: 512 threads, 4 warps
                                 // per SM sub-partition, up to 128 registers a thread)
 constexpr int NTS = 32 * NW;
@@ -111,8 +121,17 @@ struct StagedArgs {
     const int* __restrict__ fold_ptr;  // G * NW + 1: each (group, warp)'s range of fold entries
     const int2* __restrict__ fold;  // (segment, first overflow slot | pieces - 1 << 16), per warp
     const int2* __restrict__ wcone; // column pass with Lorentz cones: G x NW, each warp's cones [x, y)
+    // column pass with Lorentz cones: per column 0 orthant, 1 cone fused into this pass, 2 cone left to
+    // the big-cone kernel (more than WC columns); per cone 1 if left to the big-cone kernel
+    const unsigned char* __restrict__ ctag;
+    const unsigned char* __restrict__ soc_big;
+    // column pass in parts: k_col_combine's pieces of [0, n), at most CMAXW columns each and never
+    // inside a fused cone: first column, end, and the Lorentz cones [z, w) within
+    const int4* __restrict__ csub;
+    int nsub;
     const float* __restrict__ vec;  // gathered vector, R * rb entries (tail padding unused)
-    const float* __restrict__ rsq;  // row pass: sum of a_k^2 over each row
+    const float* __restrict__ rinv;  // row pass: 1/(1 + r_i), r_i = sum of a_ik^2 over row i
+    const float* __restrict__ dinv;  // column pass: 1/(1 + d_j), d_j = nonzeros of column j
     int* err;                       // set to 1 if a wait for a block gave up
     int G, R, maxg_pad;             // maxg_pad: sum slots (segments and overflow) of the largest group
     int halves;                     // row pass: CTAs per group, each streaming 1/halves of x (1 or 2)
@@ -190,23 +209,28 @@ __device__ __forceinline__ void st_keep(float* p, float v, uint64_t pol) {
     *p = v;
 #endif
 }
-// the orthant z-step of column j after its x-update (as orthant_update), stores with the policy
+// The staged passes' updates multiply by reciprocals computed once (1/mu per launch, 1/(1 + d_j) and
+// 1/(1 + r_i) at set-up) instead of dividing: the same steps, FP32 rounding of their own.
+// x+ = (d x + A^T v + z + (delta - c)/mu)/(1 + d), written as x + (A^T v + z + (delta - c)/mu - x)/(1 + d)
+__device__ __forceinline__ float col_x_step(float x, float atv, float z, float dl, float c, float dinv, float rmu) {
+    return x + (atv + z + (dl - c) * rmu - x) * dinv;
+}
+// the orthant z-step of column j after its x-update, stores with the policy
 __device__ __forceinline__ void orthant_keep(const SweepArgs<float>& a, int j, float xn, float dj, float mu,
-                                             uint64_t pol) {
+                                             float rmu, uint64_t pol) {
     st_keep(a.x + j, xn, pol);
-    const float w = xn - dj / mu;
+    const float w = xn - dj * rmu;
     const float zn = w > 0.f ? w : 0.f;
     st_keep(a.z + j, zn, pol);
     st_keep(a.del + j, dj + mu * (zn - xn), pol);
 }
-// rho, lambda and v of row i (as row_update), stores with the policy
-__device__ __forceinline__ void row_keep(const SweepArgs<float>& a, int i, float ax, float r, float bi, float li,
-                                         uint64_t pol) {
-    const float mu = a.mu;
-    const float rho = (bi - ax) / (1.f + r);
-    const float ln = li - mu * rho;
+// rho = (b_i - a_i x)/(1 + r_i), lambda and v of row i, stores with the policy
+__device__ __forceinline__ void row_keep(const SweepArgs<float>& a, int i, float ax, float rinv, float bi, float li,
+                                         float rmu, uint64_t pol) {
+    const float rho = (bi - ax) * rinv;
+    const float ln = li - a.mu * rho;
     st_keep(a.lam + i, ln, pol);
-    st_keep(a.v + i, rho - ln / mu, pol);
+    st_keep(a.v + i, rho - ln * rmu, pol);
 }
 
 // Programmatic dependent launch. The passes are launched so that the next one may start while
@@ -376,6 +400,95 @@ __device__ __forceinline__ void block_step(int b, int be, uint32_t u, int2 (&C)[
     if (lane == 0) mbar_arrive(empty + k);
 }
 
+// The column pass's epilogue of the columns k0 + [ws, we) (one warp): x+ from the sums (Algorithm 1,
+// the x-step in reduced form), the orthant z-step and delta-update, and the Lorentz cones wc.x ..
+// wc.y - 1, which lie within these columns (eq. proj). acc[t] holds A^T v of column k0 + t for t in
+// [ws, we); for the fused cones' columns it is overwritten by w = x+ - delta/mu.
+template <bool SOC>
+__device__ __forceinline__ void col_epilogue(const StagedArgs& g, const SweepArgs<float>& a, float* acc, int k0,
+                                             int ws, int we, int2 wc, int lane) {
+    const int e0 = ws + lane, e1 = we, es = 32;
+    const float mu = a.mu, rmu = 1.f / mu;
+    const uint64_t kp = policy_keep();
+    for (int t0 = e0; t0 < e1; t0 += es * EPI_U) {
+        float px[EPI_U], pz[EPI_U], pd[EPI_U], pc[EPI_U], dg[EPI_U];
+        int tag[EPI_U];
+#pragma unroll
+        for (int q = 0; q < EPI_U; ++q) {
+            const int t = t0 + q * es;
+            if (t < e1) {
+                const int j = k0 + t;
+                dg[q] = ldg_keep(g.dinv + j, kp);
+                px[q] = ld_keep(a.x + j, kp);
+                pz[q] = ld_keep(a.z + j, kp);
+                pd[q] = ld_keep(a.del + j, kp);
+                pc[q] = ldg_keep(a.c + j, kp);
+                tag[q] = SOC ? __ldg(g.ctag + j) : 0;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < EPI_U; ++q) {
+            const int t = t0 + q * es;
+            if (t < e1) {
+                const float xn = col_x_step(px[q], acc[t], pz[q], pd[q], pc[q], dg[q], rmu);
+                if (!SOC || tag[q] == 0) {
+                    orthant_keep(a, k0 + t, xn, pd[q], mu, rmu, kp);
+                } else {
+                    st_keep(a.x + k0 + t, xn, kp);  // a cone too large to fuse: the big-cone kernel follows
+                    if (tag[q] == 1) acc[t] = xn - pd[q] * rmu;  // w of the z-step, kept in place
+                }
+            }
+        }
+    }
+    if (SOC) {
+        // the warp's Lorentz cones (they never straddle warps), 32 at a time: first each
+        // lane sums ||w_tail||^2 of one cone (acc holds w = x+ - delta/mu of its columns),
+        // then the warp runs the z-step (eq. proj) over the cones' columns, one column per
+        // lane (coalesced stores), with delta+ = delta + mu (z+ - x+) = mu (z+ - w).
+        // Cones too large to fuse keep their columns for the big-cone kernel.
+        __syncwarp();
+        for (int q0 = wc.x; q0 < wc.y; q0 += 32) {
+            const int q = q0 + lane, cnt = min(32, wc.y - q0);
+            int st = 0, sz = 0, fused = 0;  // this lane's cone: first column (from k0), size
+            if (q < wc.y) {
+                st = a.soc_start[q] - k0;
+                sz = a.soc_size[q];
+                fused = g.soc_big[q] ? 0 : 1;
+            }
+            float ss = 0.f;
+            if (fused)
+                for (int t = 1; t < sz; ++t) ss += acc[st + t] * acc[st + t];
+            const float alpha = sqrtf(ss), w1 = fused ? acc[st] : 0.f;
+            const float ia = alpha > 0.f ? 0.5f / alpha : 0.f;  // (used only where alpha > |w1|)
+            const int c_lo = __shfl_sync(FULL, st, 0);
+            const int c_hi = __shfl_sync(FULL, st + sz, cnt - 1);
+            for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
+                const int c = c0 + lane;
+                // u: the last cone of the batch that starts at or before column c
+                int u = 0;
+#pragma unroll
+                for (int stp = 16; stp > 0; stp >>= 1) {
+                    const int su = __shfl_sync(FULL, st, min(u + stp, cnt - 1));
+                    if (u + stp < cnt && su <= c) u += stp;
+                }
+                const int su = __shfl_sync(FULL, st, u), zu = __shfl_sync(FULL, sz, u);
+                const int fu = __shfl_sync(FULL, fused, u);
+                const float au = __shfl_sync(FULL, alpha, u), w1u = __shfl_sync(FULL, w1, u);
+                const float iau = __shfl_sync(FULL, ia, u);
+                if (c < c_hi && fu && c < su + zu) {  // (orthant columns between cones: no)
+                    const float w = acc[c];
+                    // eq. proj: 0 below the polar cone, w inside K, else the boundary point
+                    const float zt = au <= -w1u ? 0.f
+                                     : au <= w1u ? w
+                                     : (c == su ? 0.5f * (w + au) : 0.5f * w + w1u * w * iau);
+                    st_keep(a.z + k0 + c, zt, kp);
+                    st_keep(a.del + k0 + c, mu * (zt - w), kp);
+                }
+            }
+        }
+    }
+}
+
 // MODE 0: column pass (gathers v; epilogue x-, z-, delta-updates; with SOC also the z-step of the
 // small Lorentz cones, whose columns never straddle two warps' ranges).
 // MODE 1: row pass (gathers x; epilogue rho, lambda and v of each row).
@@ -454,77 +567,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_staged(const StagedArgs g, cons
             __syncwarp();
             // the epilogue of the warp's own segments, as soon as the warp has seen every block
             const int e0 = ws + lane, e1 = we, es = 32;
-            const float mu = a.mu;
-            if (MODE == 0) {
-                const uint64_t kp = policy_keep();
-                for (int t0 = e0; t0 < e1; t0 += es * EPI_U) {
-                    float px[EPI_U], pz[EPI_U], pd[EPI_U], pc[EPI_U], dg[EPI_U];
-                    int tag[EPI_U];
-#pragma unroll
-                    for (int q = 0; q < EPI_U; ++q) {
-                        const int t = t0 + q * es;
-                        if (t < e1) {
-                            const int j = k0 + t;
-                            dg[q] = (float)(ldg_keep(a.col_ptr + j + 1, kp) - ldg_keep(a.col_ptr + j, kp));
-                            px[q] = ld_keep(a.x + j, kp);
-                            pz[q] = ld_keep(a.z + j, kp);
-                            pd[q] = ld_keep(a.del + j, kp);
-                            pc[q] = ldg_keep(a.c + j, kp);
-                            tag[q] = SOC ? cone_tag(a, j) : 0;
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < EPI_U; ++q) {
-                        const int t = t0 + q * es;
-                        if (t < e1) {
-                            const float xn = col_x_update(dg[q], px[q], acc[t], pz[q], pd[q], pc[q], mu);
-                            if (!SOC || tag[q] == 0) {
-                                orthant_keep(a, k0 + t, xn, pd[q], mu, kp);
-                            } else {
-                                st_keep(a.x + k0 + t, xn, kp);  // a cone too large to fuse: the big-cone kernel follows
-                                if (tag[q] == 1) acc[t] = xn - pd[q] / mu;  // w of the z-step, kept in place
-                            }
-                        }
-                    }
-                }
-                if (SOC) {
-                    // the warp's small Lorentz cones one after another (they never straddle warps):
-                    // ||w_tail||^2 by a butterfly sum, then the z-step (eq. proj) per coordinate and
-                    // delta+ = delta + mu (z+ - x+) = mu (z+ - w)
-                    __syncwarp();
-                    const int2 wc = g.wcone[grp * NW + warp];
-                    for (int q0 = wc.x; q0 < wc.y; q0 += 32) {
-                        const int q = q0 + lane;
-                        int st = 0, sz = 0, big = 1;
-                        if (q < wc.y) {
-                            st = a.soc_start[q] - k0;
-                            sz = a.soc_size[q];
-                            big = a.soc_big[q];
-                        }
-                        const int cnt = min(32, wc.y - q0);
-                        for (int u = 0; u < cnt; ++u) {
-                            if (__shfl_sync(FULL, big, u)) continue;
-                            const int c0 = __shfl_sync(FULL, st, u), csz = __shfl_sync(FULL, sz, u);
-                            float ss = 0.f;
-                            for (int t = 1 + lane; t < csz; t += 32) ss += acc[c0 + t] * acc[c0 + t];
-#pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(FULL, ss, o);
-                            const float alpha = sqrtf(ss), w1 = acc[c0];
-                            for (int t = lane; t < csz; t += 32) {
-                                const float w = acc[c0 + t];
-                                const float zt = lorentz_coord(w, t, w1, alpha);
-                                st_keep(a.z + k0 + c0 + t, zt, kp);
-                                st_keep(a.del + k0 + c0 + t, mu * (zt - w), kp);
-                            }
-                        }
-                    }
-                }
-            } else if (H > 1) {  // partial row sums; k_row_combine adds the parts
+            if (H > 1) {  // partial sums; k_col_combine / k_row_combine add the parts
                 const uint64_t kp = policy_keep();
                 float* out = g.part + (size_t)h * g.nseg + k0;
                 for (int t = e0; t < e1; t += es) st_keep(out + t, acc[t], kp);
+            } else if (MODE == 0) {
+                col_epilogue<SOC>(g, a, acc, k0, ws, we, SOC ? g.wcone[grp * NW + warp] : make_int2(0, 0), lane);
             } else {
                 const uint64_t kp = policy_keep();
+                const float rmu = 1.f / a.mu;
                 for (int t0 = e0; t0 < e1; t0 += es * EPI_U) {
                     float pr[EPI_U], pb[EPI_U], pl[EPI_U];
 #pragma unroll
@@ -532,7 +583,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_staged(const StagedArgs g, cons
                         const int t = t0 + q * es;
                         if (t < e1) {
                             const int i = k0 + t;
-                            pr[q] = ldg_keep(g.rsq + i, kp);
+                            pr[q] = ldg_keep(g.rinv + i, kp);
                             pb[q] = ldg_keep(a.b + i, kp);
                             pl[q] = ld_keep(a.lam + i, kp);
                         }
@@ -540,7 +591,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_staged(const StagedArgs g, cons
 #pragma unroll
                     for (int q = 0; q < EPI_U; ++q) {
                         const int t = t0 + q * es;
-                        if (t < e1) row_keep(a, k0 + t, acc[t], pr[q], pb[q], pl[q], kp);
+                        if (t < e1) row_keep(a, k0 + t, acc[t], pr[q], pb[q], pl[q], rmu, kp);
                     }
                 }
             }
@@ -566,11 +617,39 @@ __global__ void __launch_bounds__(256) k_row_combine(const StagedArgs g, const S
     dep_wait_prev();
     const int m = g.nseg;
     const uint64_t kp = policy_keep();
+    const float rmu = 1.f / a.mu;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         float ax = ld_keep(g.part + i, kp);
         for (int h = 1; h < g.halves; ++h) ax += ld_keep(g.part + (size_t)h * m + i, kp);
-        row_keep(a, i, ax, ldg_keep(g.rsq + i, kp), ldg_keep(a.b + i, kp), ld_keep(a.lam + i, kp), kp);
+        row_keep(a, i, ax, ldg_keep(g.rinv + i, kp), ldg_keep(a.b + i, kp), ld_keep(a.lam + i, kp), rmu, kp);
     }
+}
+
+// Column pass in parts (halves > 1): the parts' sums of each column added in a fixed order (part 0
+// first), then the column epilogue, cones included, by one warp per piece of at most CMAXW columns
+// (the pieces never cut a fused cone), its sums held in shared memory.
+constexpr int CSUB = 128;             // target columns per piece
+constexpr int CMAXW = CSUB + 64;      // at most (a cut moves to the end of a cone of <= 64 columns)
+constexpr int CWPB = 8;               // warps per CTA
+template <bool SOC>
+__global__ void __launch_bounds__(32 * CWPB, 4) k_col_combine(const StagedArgs g, const SweepArgs<float> a) {
+    __shared__ float cbuf[CWPB][CMAXW];
+    dep_launch_next();
+    dep_wait_prev();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * CWPB + warp;
+    if (p >= g.nsub) return;  // (no block-wide barrier follows)
+    const int4 d = g.csub[p];
+    if (!MFS_INB(d.y - d.x - 1, CMAXW, BS_STG_ACC)) return;
+    float* acc = &cbuf[warp][0] - d.x;  // acc[j] for the columns j in [d.x, d.y)
+    const uint64_t kp = policy_keep();
+    for (int j = d.x + lane; j < d.y; j += 32) {
+        float v = ld_keep(g.part + j, kp);
+        for (int h = 1; h < g.halves; ++h) v += ld_keep(g.part + (size_t)h * g.nseg + j, kp);
+        acc[j] = v;
+    }
+    __syncwarp();
+    col_epilogue<SOC>(g, a, acc, 0, d.x, d.y, make_int2(d.z, d.w), lane);
 }
 
 // the two instantiations the solver launches
@@ -578,6 +657,8 @@ __global__ void __launch_bounds__(256) k_row_combine(const StagedArgs g, const S
     ::mfs::staged::k_staged<0, ::mfs::staged::RB_COL, ::mfs::staged::PFR_COL, ::mfs::staged::S_COL, false>
 #define MFS_STAGED_COL_SOC \
     ::mfs::staged::k_staged<0, ::mfs::staged::RB_COL, ::mfs::staged::PFR_COL, ::mfs::staged::S_COL, true>
+#define MFS_COL_COMBINE ::mfs::staged::k_col_combine<false>
+#define MFS_COL_COMBINE_SOC ::mfs::staged::k_col_combine<true>
 #define MFS_STAGED_ROW \
     ::mfs::staged::k_staged<1, ::mfs::staged::RB_ROW, ::mfs::staged::PFR_ROW, ::mfs::staged::S_ROW, false>
 

@@ -66,7 +66,8 @@ class Info(ctypes.Structure):
                 ("ncones", ctypes.c_int64), ("nsoc", ctypes.c_int64), ("nbig", ctypes.c_int64),
                 ("col_chunks", ctypes.c_int64), ("row_chunks", ctypes.c_int64),
                 ("bytes_per_iter", ctypes.c_int64), ("precision", ctypes.c_int32),
-                ("launches_per_iter", ctypes.c_int32), ("sweep_col", ctypes.c_int32), ("sweep_row", ctypes.c_int32)]
+                ("launches_per_iter", ctypes.c_int32), ("sweep_col", ctypes.c_int32), ("sweep_row", ctypes.c_int32),
+                ("col_parts", ctypes.c_int32), ("row_parts", ctypes.c_int32)]
 
 
 _lib = None

@@ -254,3 +254,40 @@ def test_l2_keep_raises_and_restores_the_set_aside():
     b.close()
     plain.close()
     assert _persisting_limit() == before
+
+
+def _mixed_cones(n, seed):
+    """Orthant runs, Lorentz cones of 1..64 columns and a few larger ones (left to the big-cone kernel),
+    in a seeded order covering n columns."""
+    rng = np.random.default_rng([seed, 11])
+    out, left = [], n
+    while left > 0:
+        r = rng.random()
+        size = int(rng.integers(1, 200)) if r < 0.3 else int(rng.integers(1, 65)) if r < 0.97 else int(rng.integers(65, 400))
+        size = min(size, left)
+        out.append([0 if r < 0.3 else 1, size])
+        left -= size
+    return np.array(out)
+
+
+@pytest.mark.parametrize("kind", ["lp", "socp", "mixed"])
+def test_passes_in_parts(kind):
+    """Both passes split over several CTAs per group (partial sums added by k_col_combine and
+    k_row_combine in a fixed order): v and x long enough for at least 8 blocks per CTA, groups that
+    still fit in shared memory. The combine kernel runs the column epilogue, Lorentz cones included."""
+    if kind == "lp":
+        prob = I.large_lp(9, m=300_000, n=750_000)
+    elif kind == "socp":
+        prob = I.socp(9, n=700_000, m=300_000)
+    else:
+        prob = I.large_lp(10, m=300_000, n=750_000)
+        prob["cones"] = _mixed_cones(prob["n"], 10)
+    orc, s = staged_pair(prob, 20)
+    info = s.info()
+    assert info["col_parts"] == 2 and info["row_parts"] >= 2, info
+    compare(s.solution(), orc.state(), TOL["fp32"], kind)
+    again = mfs.Solver(prob, precision="fp32", polish_iters=0, check_every=25, sweep="staged")
+    again.iterate(20)
+    sa, sb = s.solution(), again.solution()
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k

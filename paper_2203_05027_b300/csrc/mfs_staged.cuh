@@ -403,15 +403,16 @@ __device__ __forceinline__ void block_step(int b, int be, uint32_t u, int2 (&C)[
 // The column pass's epilogue of the columns k0 + [ws, we) (one warp): x+ from the sums (Algorithm 1,
 // the x-step in reduced form), the orthant z-step and delta-update, and the Lorentz cones wc.x ..
 // wc.y - 1, which lie within these columns (eq. proj). acc[t] holds A^T v of column k0 + t for t in
-// [ws, we); for the fused cones' columns it is overwritten by w = x+ - delta/mu.
-template <bool SOC>
+// [ws, we) (with PARTS: the parts' sums in g.part, added in a fixed order as they are loaded, acc
+// only receiving w); for the fused cones' columns it is overwritten by w = x+ - delta/mu.
+template <bool SOC, bool PARTS>
 __device__ __forceinline__ void col_epilogue(const StagedArgs& g, const SweepArgs<float>& a, float* acc, int k0,
                                              int ws, int we, int2 wc, int lane) {
     const int e0 = ws + lane, e1 = we, es = 32;
     const float mu = a.mu, rmu = 1.f / mu;
     const uint64_t kp = policy_keep();
     for (int t0 = e0; t0 < e1; t0 += es * EPI_U) {
-        float px[EPI_U], pz[EPI_U], pd[EPI_U], pc[EPI_U], dg[EPI_U];
+        float px[EPI_U], pz[EPI_U], pd[EPI_U], pc[EPI_U], dg[EPI_U], pa[EPI_U];
         int tag[EPI_U];
 #pragma unroll
         for (int q = 0; q < EPI_U; ++q) {
@@ -424,13 +425,18 @@ __device__ __forceinline__ void col_epilogue(const StagedArgs& g, const SweepArg
                 pd[q] = ld_keep(a.del + j, kp);
                 pc[q] = ldg_keep(a.c + j, kp);
                 tag[q] = SOC ? __ldg(g.ctag + j) : 0;
+                if (PARTS) {
+                    float v = ld_keep(g.part + j, kp);
+                    for (int h = 1; h < g.halves; ++h) v += ld_keep(g.part + (size_t)h * g.nseg + j, kp);
+                    pa[q] = v;
+                }
             }
         }
 #pragma unroll
         for (int q = 0; q < EPI_U; ++q) {
             const int t = t0 + q * es;
             if (t < e1) {
-                const float xn = col_x_step(px[q], acc[t], pz[q], pd[q], pc[q], dg[q], rmu);
+                const float xn = col_x_step(px[q], PARTS ? pa[q] : acc[t], pz[q], pd[q], pc[q], dg[q], rmu);
                 if (!SOC || tag[q] == 0) {
                     orthant_keep(a, k0 + t, xn, pd[q], mu, rmu, kp);
                 } else {
@@ -441,48 +447,38 @@ __device__ __forceinline__ void col_epilogue(const StagedArgs& g, const SweepArg
         }
     }
     if (SOC) {
-        // the warp's Lorentz cones (they never straddle warps), 32 at a time: first each
-        // lane sums ||w_tail||^2 of one cone (acc holds w = x+ - delta/mu of its columns),
-        // then the warp runs the z-step (eq. proj) over the cones' columns, one column per
-        // lane (coalesced stores), with delta+ = delta + mu (z+ - x+) = mu (z+ - w).
+        // The Lorentz cones wc.x .. wc.y - 1 (never straddling warps; acc holds w = x+ - delta/mu of
+        // the fused ones' columns): their descriptors loaded 32 at a time, one per lane, then four
+        // cones at a time, eight lanes each: ||w_tail||^2 by strided sums and three shuffles, then
+        // the z-step (eq. proj) over the cone's columns and delta+ = delta + mu (z+ - x+) = mu (z+ - w).
         // Cones too large to fuse keep their columns for the big-cone kernel.
         __syncwarp();
+        const int r = lane & 7, u = lane >> 3;
         for (int q0 = wc.x; q0 < wc.y; q0 += 32) {
-            const int q = q0 + lane, cnt = min(32, wc.y - q0);
-            int st = 0, sz = 0, fused = 0;  // this lane's cone: first column (from k0), size
-            if (q < wc.y) {
+            const int q = q0 + lane;
+            int st = 0, sz = 0;  // this lane's cone: first column (from k0), size (0: none or not fused)
+            if (q < wc.y && !g.soc_big[q]) {
                 st = a.soc_start[q] - k0;
                 sz = a.soc_size[q];
-                fused = g.soc_big[q] ? 0 : 1;
             }
-            float ss = 0.f;
-            if (fused)
-                for (int t = 1; t < sz; ++t) ss += acc[st + t] * acc[st + t];
-            const float alpha = sqrtf(ss), w1 = fused ? acc[st] : 0.f;
-            const float ia = alpha > 0.f ? 0.5f / alpha : 0.f;  // (used only where alpha > |w1|)
-            const int c_lo = __shfl_sync(FULL, st, 0);
-            const int c_hi = __shfl_sync(FULL, st + sz, cnt - 1);
-            for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
-                const int c = c0 + lane;
-                // u: the last cone of the batch that starts at or before column c
-                int u = 0;
-#pragma unroll
-                for (int stp = 16; stp > 0; stp >>= 1) {
-                    const int su = __shfl_sync(FULL, st, min(u + stp, cnt - 1));
-                    if (u + stp < cnt && su <= c) u += stp;
-                }
-                const int su = __shfl_sync(FULL, st, u), zu = __shfl_sync(FULL, sz, u);
-                const int fu = __shfl_sync(FULL, fused, u);
-                const float au = __shfl_sync(FULL, alpha, u), w1u = __shfl_sync(FULL, w1, u);
-                const float iau = __shfl_sync(FULL, ia, u);
-                if (c < c_hi && fu && c < su + zu) {  // (orthant columns between cones: no)
-                    const float w = acc[c];
+            const int nb = (min(32, wc.y - q0) + 3) >> 2;
+            for (int bq = 0; bq < nb; ++bq) {
+                const int cs = __shfl_sync(FULL, st, 4 * bq + u), cz = __shfl_sync(FULL, sz, 4 * bq + u);
+                float ss = 0.f;
+                for (int t = 1 + r; t < cz; t += 8) ss += acc[cs + t] * acc[cs + t];
+                ss += __shfl_xor_sync(FULL, ss, 1);
+                ss += __shfl_xor_sync(FULL, ss, 2);
+                ss += __shfl_xor_sync(FULL, ss, 4);
+                const float alpha = sqrtf(ss), w1 = cz > 0 ? acc[cs] : 0.f;
+                const float ia = alpha > 0.f ? 0.5f / alpha : 0.f;  // (used only where alpha > |w1|)
+                for (int t = r; t < cz; t += 8) {
+                    const float w = acc[cs + t];
                     // eq. proj: 0 below the polar cone, w inside K, else the boundary point
-                    const float zt = au <= -w1u ? 0.f
-                                     : au <= w1u ? w
-                                     : (c == su ? 0.5f * (w + au) : 0.5f * w + w1u * w * iau);
-                    st_keep(a.z + k0 + c, zt, kp);
-                    st_keep(a.del + k0 + c, mu * (zt - w), kp);
+                    const float zt = alpha <= -w1 ? 0.f
+                                     : alpha <= w1 ? w
+                                     : (t == 0 ? 0.5f * (w + alpha) : 0.5f * w + w1 * w * ia);
+                    st_keep(a.z + k0 + cs + t, zt, kp);
+                    st_keep(a.del + k0 + cs + t, mu * (zt - w), kp);
                 }
             }
         }
@@ -572,7 +568,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_staged(const StagedArgs g, cons
                 float* out = g.part + (size_t)h * g.nseg + k0;
                 for (int t = e0; t < e1; t += es) st_keep(out + t, acc[t], kp);
             } else if (MODE == 0) {
-                col_epilogue<SOC>(g, a, acc, k0, ws, we, SOC ? g.wcone[grp * NW + warp] : make_int2(0, 0), lane);
+                col_epilogue<SOC, false>(g, a, acc, k0, ws, we, SOC ? g.wcone[grp * NW + warp] : make_int2(0, 0),
+                                         lane);
             } else {
                 const uint64_t kp = policy_keep();
                 const float rmu = 1.f / a.mu;
@@ -632,7 +629,7 @@ constexpr int CSUB = 128;             // target columns per piece
 constexpr int CMAXW = CSUB + 64;      // at most (a cut moves to the end of a cone of <= 64 columns)
 constexpr int CWPB = 8;               // warps per CTA
 template <bool SOC>
-__global__ void __launch_bounds__(32 * CWPB, 4) k_col_combine(const StagedArgs g, const SweepArgs<float> a) {
+__global__ void __launch_bounds__(32 * CWPB, 3) k_col_combine(const StagedArgs g, const SweepArgs<float> a) {
     __shared__ float cbuf[CWPB][CMAXW];
     dep_launch_next();
     dep_wait_prev();
@@ -641,15 +638,8 @@ __global__ void __launch_bounds__(32 * CWPB, 4) k_col_combine(const StagedArgs g
     if (p >= g.nsub) return;  // (no block-wide barrier follows)
     const int4 d = g.csub[p];
     if (!MFS_INB(d.y - d.x - 1, CMAXW, BS_STG_ACC)) return;
-    float* acc = &cbuf[warp][0] - d.x;  // acc[j] for the columns j in [d.x, d.y)
-    const uint64_t kp = policy_keep();
-    for (int j = d.x + lane; j < d.y; j += 32) {
-        float v = ld_keep(g.part + j, kp);
-        for (int h = 1; h < g.halves; ++h) v += ld_keep(g.part + (size_t)h * g.nseg + j, kp);
-        acc[j] = v;
-    }
-    __syncwarp();
-    col_epilogue<SOC>(g, a, acc, 0, d.x, d.y, make_int2(d.z, d.w), lane);
+    float* acc = &cbuf[warp][0] - d.x;  // w of the fused cones' columns j in [d.x, d.y)
+    col_epilogue<SOC, true>(g, a, acc, 0, d.x, d.y, make_int2(d.z, d.w), lane);
 }
 
 // the two instantiations the solver launches

@@ -172,28 +172,46 @@ def recorded_traffic(kernel):
 
 
 def kernel_roofline(s, info, peak, peak_kind, m, n, o, sm_mhz, num_sms=148):
-    """Time each sweep kernel on the solver's stream with CUDA events (library hook) and relate
-    its algorithmic bytes to the measured HBM copy bandwidth. Also relates the launch time to the
-    L2-request floor of its random gathers (one 4-byte gather, hence one L2 request, per nonzero;
-    one request per SM cycle)."""
+    """Time each kernel of an iteration on the solver's stream with CUDA events (library hook,
+    kernel by kernel) and relate the dominant one's algorithmic bytes to the measured HBM copy
+    bandwidth. A pass in parts splits its bytes: the staged kernel streams the entries and the
+    gathered vector, the combine reads and writes the iterate's vectors. Also relates the launch
+    time to the L2-request floor of the random gathers (one 4-byte gather, hence one L2 request,
+    per nonzero; one request per SM cycle)."""
     from paper_2203_05027_b300 import mfs
-    t = s.time_kernels(50)
-    col_bytes = 8 * o + 32 * n + 4 * m
-    row_bytes = 8 * o + 4 * n + 20 * m
-    col = {"kernel": "k_staged<0>" if info.get("sweep_col") == mfs.SWEEP_STAGED else "k_col_sweep",
-           "ms": t["col_ms"], "bytes": col_bytes}
-    row = {"kernel": "k_staged<1>+k_row_combine" if info.get("sweep_row") == mfs.SWEEP_STAGED else "k_row_sweep",
-           "ms": t["row_ms"], "bytes": row_bytes}
-    dom = col if col["ms"] >= row["ms"] else row
+    t = s.time_kernel_split(50)
+    col_staged = info.get("sweep_col") == mfs.SWEEP_STAGED
+    row_staged = info.get("sweep_row") == mfs.SWEEP_STAGED
+    col_split = col_staged and info.get("col_parts", 1) > 1
+    row_split = row_staged and info.get("row_parts", 1) > 1
+    kernels = [
+        {"kernel": "k_staged<0>" if col_staged else "k_col_sweep", "ms": t["col_main_ms"],
+         "bytes": 8 * o + 4 * m if col_split else 8 * o + 32 * n + 4 * m},
+        # a pass's second kernel: the combine of a pass in parts, the long chunks of a chunked
+        # sweep (a staged pass in one part has none: the interval is the gap between two events)
+        {"kernel": "k_col_combine" if col_split else "k_col_long",
+         "ms": t["col_second_ms"] if (col_split or not col_staged) else 0.0, "bytes": 28 * n if col_split else 0},
+        {"kernel": "k_staged<1>" if row_staged else "k_row_sweep", "ms": t["row_main_ms"],
+         "bytes": 8 * o + 4 * n if row_split else 8 * o + 4 * n + 20 * m},
+        {"kernel": "k_row_combine" if row_split else "k_row_long",
+         "ms": t["row_second_ms"] if (row_split or not row_staged) else 0.0, "bytes": 20 * m if row_split else 0},
+    ]
+    dom = max(kernels, key=lambda k: k["ms"])
     achieved = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
     it_gbs = info["bytes_per_iter"] / (t["iter_ms"] * 1e-3) / 1e9
     traffic = recorded_traffic(dom["kernel"])
     clock_hz = (sm_mhz or 2032.0) * 1e6
     floor_ms = o / (num_sms * clock_hz) * 1e3
+    col_ms = kernels[0]["ms"] + kernels[1]["ms"]
+    row_ms = kernels[2]["ms"] + kernels[3]["ms"]
     return {"bound": "hbm", "kernel": dom["kernel"], "achieved": round(achieved, 1), "peak": peak,
             "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
             "traffic": traffic, "algorithmic_bytes": dom["bytes"],
-            "launch_ms": round(dom["ms"], 5), "col_ms": round(t["col_ms"], 5), "row_ms": round(t["row_ms"], 5),
+            "launch_ms": round(dom["ms"], 5),
+            "kernels_ms": {k["kernel"]: round(k["ms"], 5) for k in kernels if k["ms"] > 0},
+            "col_ms": round(col_ms, 5), "row_ms": round(row_ms, 5),
+            "col_pass_frac": round((8 * o + 32 * n + 4 * m) / (col_ms * 1e-3) / 1e9 / peak, 4),
+            "row_pass_frac": round((8 * o + 4 * n + 20 * m) / (row_ms * 1e-3) / 1e9 / peak, 4),
             "iteration_ms": round(t["iter_ms"], 5), "iteration_gbs": round(it_gbs, 1),
             "gather_request_floor_ms": round(floor_ms, 5),
             "frac_of_gather_request_floor": round(floor_ms / dom["ms"], 4)}

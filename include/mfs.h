@@ -321,6 +321,13 @@ mfs_status mfs_set_precision(mfs_solver* s, int32_t precision);
  */
 mfs_status mfs_time_kernels(mfs_solver* s, int64_t k, double* out_ms);
 
+/* The same, kernel by kernel: out_ms[0..5] = average milliseconds of the column pass's main kernel
+   (the staged kernel or the chunked sweep), of its second kernel (the combine of a pass in parts, or
+   the long-column kernel; 0 if none), of the large-cone kernel, of the row pass's main kernel, of its
+   second kernel (combine or long rows), and of a whole iteration. An event between two kernels ends
+   their overlap (programmatic dependent launch), so the sum can exceed an iteration without them. */
+mfs_status mfs_time_kernel_split(mfs_solver* s, int64_t k, double* out_ms);
+
 /* ------------------------------------------------------------------------------------------------
  * Batched solves. Many independent problems (Sec. II form each, Algorithm 1 on each) of uneven
  * sizes are solved in one persistent launch: every CTA takes instances from a queue (largest

@@ -101,6 +101,32 @@ __device__ __forceinline__ double lorentz_dist2(double w1, double alpha, double 
     return 0.5 * g * g;
 }
 
+// sum over k in [k0, k1) of val[k] * vec[idx[k]], added in order of k: the loads of up to four
+// entries are issued together (a column or row of A read from memory is otherwise a chain of
+// dependent round trips, one per nonzero), the products added one after another as before
+#ifndef MFS_BATCH_SEG_UNROLL
+#define MFS_BATCH_SEG_UNROLL 4
+#endif
+template <typename T>
+__device__ __forceinline__ T seg_dot(const int* idx, const T* val, int k0, int k1, const T* vec) {
+    constexpr int U = MFS_BATCH_SEG_UNROLL;
+    T s = T(0);
+    for (int k = k0; k < k1; k += U) {
+        int ix[U];
+        T av[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool in = k + u < k1;
+            ix[u] = in ? idx[k + u] : 0;
+            av[u] = in ? val[k + u] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (k + u < k1) s += av[u] * vec[ix[u]];
+    }
+    return s;
+}
+
 // the Lorentz cone (local index) that contains column j, or -1
 __device__ __forceinline__ int cone_of(const int* st, const int* sz, int ns, int j) {
     int lo = 0, hi = ns;
@@ -347,8 +373,7 @@ __global__ void __launch_bounds__(MAXNT, MFS_BATCH_MINB) k_batch(const BatchArgs
                 // column sweep: x-step (eq. vvt), z-step and delta-update for orthant coordinates
                 for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
                     const int k0 = cp[j], k1 = cp[j + 1];
-                    T s = T(0);
-                    for (int k = k0; k < k1; ++k) s += cv[k] * vs[ci[k]];
+                    const T s = seg_dot(ci, cv, k0, k1, vs);
                     const T d = T(k1 - k0), dj = del[j];
                     const T fv = k1 - k0 < FVT ? s_fv[k1 - k0] : T(1) / (T(1) + d);
                     const T xn = (d * xs[j] + s + z[j] + (dj - c[j]) * inv_mu) * fv;
@@ -381,8 +406,7 @@ __global__ void __launch_bounds__(MAXNT, MFS_BATCH_MINB) k_batch(const BatchArgs
                 }
                 // row sweep: y-step (with F_U) and lambda-update
                 for (int i = threadIdx.x; i < I.m; i += blockDim.x) {
-                    T s = T(0);
-                    for (int k = rp[i]; k < rp[i + 1]; ++k) s += rv[k] * xs[ri[k]];
+                    const T s = seg_dot(ri, rv, rp[i], rp[i + 1], xs);
                     const T rho = (b[i] - s) * fu[i];
                     const T ln = lam[i] - mu * rho;
                     lam[i] = ln;

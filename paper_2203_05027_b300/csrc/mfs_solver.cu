@@ -807,9 +807,13 @@ void launch_dep(void (*kernel)(KArgs...), int grid, int block, size_t smem, cuda
     cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);  // an error is left for cudaGetLastError
 }
 
+// mid (timing only): recorded after the pass's main kernel, before its combine or long-chunk kernel
 template <typename T>
-void launch_col(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
-    if (s->ncc == 0) return;
+void launch_col(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st, cudaEvent_t mid = nullptr) {
+    if (s->ncc == 0) {
+        if (mid) cudaEventRecord(mid, st);
+        return;
+    }
     if constexpr (std::is_same<T, float>::value) {
         if (staged_col(s)) {
             const StagedArgsT& g = s->stg_col;
@@ -819,6 +823,7 @@ void launch_col(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
                 launch_dep(MFS_STAGED_COL_SOC, grid, mfs::staged::NTHREADS, smem, st, g, a);
             else
                 launch_dep(MFS_STAGED_COL, grid, mfs::staged::NTHREADS, smem, st, g, a);
+            if (mid) cudaEventRecord(mid, st);
             if (g.halves > 1) {
                 const int cgrid = (g.nsub + mfs::staged::CWPB - 1) / mfs::staged::CWPB;
                 if (s->has_soc)
@@ -831,9 +836,11 @@ void launch_col(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
     }
     if (s->has_soc) {
         k_col_sweep<T, true><<<warp_grid(s->ncc), NT, 0, st>>>(a);
+        if (mid) cudaEventRecord(mid, st);
         if (s->nlc) k_col_long<T, true><<<s->nlc, NT, 0, st>>>(a);
     } else {
         k_col_sweep<T, false><<<warp_grid(s->ncc), NT, 0, st>>>(a);
+        if (mid) cudaEventRecord(mid, st);
         if (s->nlc) k_col_long<T, false><<<s->nlc, NT, 0, st>>>(a);
     }
 }
@@ -852,13 +859,17 @@ void launch_big(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
     if (s->nbig) k_bigcone_sweep<T><<<s->nbig, NT, 0, st>>>(a);
 }
 template <typename T, int MODE>
-void launch_row_mode(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
-    if (s->nrc == 0) return;
+void launch_row_mode(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st, cudaEvent_t mid = nullptr) {
+    if (s->nrc == 0) {
+        if (mid) cudaEventRecord(mid, st);
+        return;
+    }
     if constexpr (std::is_same<T, float>::value && MODE == 0) {
         if (staged_row(s)) {
             const StagedArgsT& g = s->stg_row;
             launch_dep(MFS_STAGED_ROW, std::min(g.G * g.halves, s->num_sms), mfs::staged::NTHREADS,
                        mfs::staged::smem_bytes(mfs::staged::RB_ROW, mfs::staged::S_ROW, g.maxg_pad, g.R), st, g, a);
+            if (mid) cudaEventRecord(mid, st);
             if (g.halves > 1)
                 launch_dep(mfs::staged::k_row_combine, (int)std::min<int64_t>((s->m + 255) / 256, 8 * s->num_sms), 256,
                            0, st, g, a);
@@ -866,11 +877,12 @@ void launch_row_mode(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
         }
     }
     k_row_sweep<T, MODE><<<warp_grid(s->nrc), NT, 0, st>>>(a);
+    if (mid) cudaEventRecord(mid, st);
     if (s->nlr) k_row_long<T, MODE><<<s->nlr, NT, 0, st>>>(a);
 }
 template <typename T>
-void launch_row(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
-    launch_row_mode<T, 0>(s, a, st);
+void launch_row(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st, cudaEvent_t mid = nullptr) {
+    launch_row_mode<T, 0>(s, a, st, mid);
 }
 template <typename T>
 void launch_warm_v(mfs_solver* s, const SweepArgs<T>& a, cudaStream_t st) {
@@ -1487,11 +1499,14 @@ static mfs_status get_solution_t(mfs_solver* s, State<T>& st, double* x, double*
 
 template <typename T>
 static mfs_status time_kernels_t(mfs_solver* s, State<T>& st, int64_t k, double* out) {
-    // k iterations back to back, an event around each group of launches; one wait at the end, so
-    // that no host round trip idles the GPU between iterations
+    // k iterations back to back, an event after each kernel group (a pass's main kernel, its
+    // combine or long-chunk kernel, the big cones, ...); one wait at the end, so that no host round
+    // trip idles the GPU between iterations. out: column main, column rest, big cones, row main,
+    // row rest, whole iteration (average milliseconds).
     SweepArgs<T> a = sweep_args(s, st);
     const int64_t kk = std::max<int64_t>(k, 0);
-    std::vector<cudaEvent_t> ev((size_t)(3 * kk + 1), nullptr);
+    constexpr int E = 5;
+    std::vector<cudaEvent_t> ev((size_t)(E * kk + 1), nullptr);
     mfs_status r = MFS_OK;
     for (auto& e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) {
@@ -1499,31 +1514,29 @@ static mfs_status time_kernels_t(mfs_solver* s, State<T>& st, int64_t k, double*
             r = fail(s, MFS_ERR_CUDA, "cudaEventCreate failed");
             break;
         }
-    double tc = 0, tb = 0, tr = 0, tall = 0;
+    double t[E] = {0, 0, 0, 0, 0}, tall = 0;
     if (r == MFS_OK) {
         cudaEventRecord(ev[0], s->stream);
         for (int64_t i = 0; i < kk; ++i) {
-            launch_col(s, a, s->stream);
-            cudaEventRecord(ev[3 * i + 1], s->stream);
+            cudaEvent_t* e = ev.data() + E * i;
+            launch_col(s, a, s->stream, e[1]);
+            cudaEventRecord(e[2], s->stream);
             launch_big(s, a, s->stream);
-            cudaEventRecord(ev[3 * i + 2], s->stream);
-            launch_row(s, a, s->stream);
-            cudaEventRecord(ev[3 * i + 3], s->stream);
+            cudaEventRecord(e[3], s->stream);
+            launch_row(s, a, s->stream, e[4]);
+            cudaEventRecord(e[5], s->stream);
         }
-        cudaError_t e = cudaEventSynchronize(ev[3 * kk]);
+        cudaError_t e = cudaEventSynchronize(ev[E * kk]);
         if (e != cudaSuccess) r = fail(s, MFS_ERR_CUDA, std::string("time_kernels: ") + cudaGetErrorString(e));
-        for (int64_t i = 0; i < kk && r == MFS_OK; ++i) {
-            float ms = 0;
-            cudaEventElapsedTime(&ms, ev[3 * i], ev[3 * i + 1]);
-            tc += ms;
-            cudaEventElapsedTime(&ms, ev[3 * i + 1], ev[3 * i + 2]);
-            tb += ms;
-            cudaEventElapsedTime(&ms, ev[3 * i + 2], ev[3 * i + 3]);
-            tr += ms;
-        }
+        for (int64_t i = 0; i < kk && r == MFS_OK; ++i)
+            for (int q = 0; q < E; ++q) {
+                float ms = 0;
+                cudaEventElapsedTime(&ms, ev[E * i + q], ev[E * i + q + 1]);
+                t[q] += ms;
+            }
         if (kk > 0 && r == MFS_OK) {
             float ms = 0;
-            cudaEventElapsedTime(&ms, ev[0], ev[3 * kk]);
+            cudaEventElapsedTime(&ms, ev[0], ev[E * kk]);
             tall = ms;
         }
     }
@@ -1532,10 +1545,12 @@ static mfs_status time_kernels_t(mfs_solver* s, State<T>& st, int64_t k, double*
     if (r != MFS_OK) return r;
     s->iter += k;
     const double kd = kk > 0 ? (double)kk : 1.0;
-    out[0] = tc / kd;
-    out[1] = tr / kd;
-    out[2] = tb / kd;
-    out[3] = tall / kd;
+    out[0] = t[0] / kd;  // column main kernel
+    out[1] = t[1] / kd;  // column combine / long chunks
+    out[2] = t[2] / kd;  // big cones
+    out[3] = t[3] / kd;  // row main kernel
+    out[4] = t[4] / kd;  // row combine / long chunks
+    out[5] = tall / kd;
     CUDA_TRY(s, cudaGetLastError());
     return MFS_OK;
 }
@@ -2423,10 +2438,22 @@ mfs_status mfs_get_reduced_v(mfs_solver* s, double* v) {
     return MFS_OK;
 }
 
-mfs_status mfs_time_kernels(mfs_solver* s, int64_t k, double* out_ms) {
+mfs_status mfs_time_kernel_split(mfs_solver* s, int64_t k, double* out_ms) {
     if (!s || !out_ms || k < 0) return MFS_ERR_INVALID;
     CUDA_TRY(s, cudaSetDevice(s->device));
     return s->precision == MFS_FP64 ? time_kernels_t(s, s->s64, k, out_ms) : time_kernels_t(s, s->s32, k, out_ms);
+}
+
+mfs_status mfs_time_kernels(mfs_solver* s, int64_t k, double* out_ms) {
+    if (!s || !out_ms || k < 0) return MFS_ERR_INVALID;
+    double t[6];
+    const mfs_status r = mfs_time_kernel_split(s, k, t);
+    if (r != MFS_OK) return r;
+    out_ms[0] = t[0] + t[1];
+    out_ms[1] = t[3] + t[4];
+    out_ms[2] = t[2];
+    out_ms[3] = t[5];
+    return MFS_OK;
 }
 
 }  // extern "C"

@@ -139,6 +139,7 @@ def load(path=LIB_PATH):
     lib.mfs_set_precision.argtypes = [P, i32]
     lib.mfs_set_precision.restype = st
     lib.mfs_time_kernels.argtypes = [P, i64, dp]
+    lib.mfs_time_kernel_split.argtypes = [P, i64, dp]
     lib.mfs_get_reduced_v.argtypes = [P, P]
     lib.mfs_get_reduced_v.restype = st
     lib.mfs_debug_fail_alloc_after.argtypes = [i64]
@@ -146,6 +147,7 @@ def load(path=LIB_PATH):
     lib.mfs_gemm_bf16_wait_test.argtypes = [P]
     lib.mfs_gemm_bf16_wait_test.restype = st
     lib.mfs_time_kernels.restype = st
+    lib.mfs_time_kernel_split.restype = st
     _lib = lib
     return lib
 
@@ -337,6 +339,13 @@ class Solver:
         out = (ctypes.c_double * 4)()
         self._check(self._lib.mfs_time_kernels(self._h, int(k), out))
         return {"col_ms": out[0], "row_ms": out[1], "bigcone_ms": out[2], "iter_ms": out[3]}
+
+    def time_kernel_split(self, k):
+        """mfs_time_kernel_split: milliseconds per launch of each kernel of an iteration."""
+        out = (ctypes.c_double * 6)()
+        self._check(self._lib.mfs_time_kernel_split(self._h, int(k), out))
+        keys = ("col_main_ms", "col_second_ms", "bigcone_ms", "row_main_ms", "row_second_ms", "iter_ms")
+        return dict(zip(keys, list(out)))
 
 
 def row_residuals_static(m, n, row_ptr, col_idx, val, b, x, lam, out, stream=None):

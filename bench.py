@@ -249,7 +249,8 @@ def batch_workload(stream, seed, iters=100, tts_iters=300_000):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    bytes_iter = 16 * info["total_nnz"] + 36 * info["total_n"] + 24 * info["total_m"]
+    # both orders of A: a 4-byte value and a 2- or 4-byte local index per nonzero and order
+    bytes_iter = 2 * (4 + info["index_bytes"]) * info["total_nnz"] + 36 * info["total_n"] + 24 * info["total_m"]
     bt.close()
     # time to 1e-6 from the cold start, every instance tested inside the launch at the tuned interval
     if not tts_iters:

@@ -360,6 +360,9 @@ mfs_status mfs_batch_create(int64_t count, const int64_t* m, const int64_t* n, c
 void mfs_batch_destroy(mfs_batch* bt);
 /* Like mfs_last_error, for batches; NULL gives the last mfs_batch_create failure on this thread. */
 const char* mfs_batch_last_error(const mfs_batch* bt);
+/* Bytes of each stored local index of A (2 when every instance has m, n <= 65535, else 4): a nonzero
+   then costs 2 * (4 + bytes) in FP32 (both orders) instead of 16. */
+mfs_status mfs_batch_index_bytes(const mfs_batch* bt, int32_t* bytes);
 mfs_status mfs_batch_get_info(const mfs_batch* bt, int64_t* count, int64_t* total_m, int64_t* total_n,
                               int64_t* total_nnz);
 /* Exactly k iterations of every instance (no termination test). */

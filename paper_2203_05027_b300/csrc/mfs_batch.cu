@@ -52,6 +52,8 @@ struct BatchArgs {
     const T* cval;
     const int* row_ptr;      // instance t: m[t]+1 local offsets starting at off_m[t] + t
     const int* ridx;         // local column indices, row order
+    const uint16_t* cidx16;  // the same as 16-bit indices, when every instance has m, n <= 65535
+    const uint16_t* ridx16;  // (then cidx and ridx are not stored)
     const T* rval;
     const T* fu;             // F_U = 1 / (1 + sum_k a_ik^2) per row
     const int* nsoc;         // Lorentz cones per instance (local starts, ascending)
@@ -107,8 +109,8 @@ __device__ __forceinline__ double lorentz_dist2(double w1, double alpha, double 
 #ifndef MFS_BATCH_SEG_UNROLL
 #define MFS_BATCH_SEG_UNROLL 4
 #endif
-template <typename T>
-__device__ __forceinline__ T seg_dot(const int* idx, const T* val, int k0, int k1, const T* vec) {
+template <typename T, typename IT>
+__device__ __forceinline__ T seg_dot(const IT* idx, const T* val, int k0, int k1, const T* vec) {
     constexpr int U = MFS_BATCH_SEG_UNROLL;
     T s = T(0);
     for (int k = k0; k < k1; k += U) {
@@ -181,9 +183,9 @@ struct Inst {
 
 // FP64 residuals of instance I at (x, lambda) (x read through xs); status block into out[NSTAT]
 // (thread 0) and the relative KKT residual returned to every thread.
-template <typename T>
-__device__ double instance_residuals(const BatchArgs<T>& a, const Inst& I, const T* xs, const int* cp, const int* ci,
-                                     const T* cv, const int* rp, const int* ri, const T* rv, double* out,
+template <typename T, typename IT>
+__device__ double instance_residuals(const BatchArgs<T>& a, const Inst& I, const T* xs, const int* cp, const IT* ci,
+                                     const T* cv, const int* rp, const IT* ri, const T* rv, double* out,
                                      double (*sh)[NFLD], double* s_kkt) {
     using A = typename AccT<T>::type;
     double f[NFLD];
@@ -307,7 +309,16 @@ __device__ __forceinline__ Inst load_inst(const BatchArgs<T>& a, int t) {
 #define MFS_BATCH_MINB 2  // 64 registers: two 512-thread CTAs per SM
 #endif
 
-template <typename T, int MODE>
+// the index arrays of the width IT
+template <typename IT>
+__device__ __forceinline__ const IT* idx_of(const int* i32, const uint16_t* i16) {
+    if constexpr (sizeof(IT) == 2)
+        return i16;
+    else
+        return i32;
+}
+
+template <typename T, typename IT, int MODE>
 __global__ void __launch_bounds__(MAXNT, MFS_BATCH_MINB) k_batch(const BatchArgs<T> a) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ double s_red[MAXW][NFLD];
@@ -325,16 +336,16 @@ __global__ void __launch_bounds__(MAXNT, MFS_BATCH_MINB) k_batch(const BatchArgs
         const Inst I = load_inst(a, a.order[q]);
         // shared memory: gathered vectors first, then (if room) the matrix in both orders
         const size_t vb = (size_t)(I.n + I.m) * sizeof(T);
-        const size_t ab = (size_t)I.o * 2 * (sizeof(int) + sizeof(T));
+        const size_t ab = (size_t)I.o * 2 * (sizeof(IT) + sizeof(T));
         const bool vec_sm = vb <= (size_t)a.smem_bytes;
         const bool mat_sm = vec_sm && (vb + ab + 16 <= (size_t)a.smem_bytes);
         T* xs = vec_sm ? reinterpret_cast<T*>(sm) : a.x + I.gn;
         T* vs = vec_sm ? reinterpret_cast<T*>(sm) + I.n : a.v + I.gm;
         const int* cp = a.col_ptr + I.gn + I.t;
         const int* rp = a.row_ptr + I.gm + I.t;
-        const int* ci = a.cidx + I.go;
+        const IT* ci = idx_of<IT>(a.cidx, a.cidx16) + I.go;
         const T* cv = a.cval + I.go;
-        const int* ri = a.ridx + I.go;
+        const IT* ri = idx_of<IT>(a.ridx, a.ridx16) + I.go;
         const T* rv = a.rval + I.go;
         if (vec_sm) {
             for (int j = threadIdx.x; j < I.n; j += blockDim.x) xs[j] = a.x[I.gn + j];
@@ -344,8 +355,8 @@ __global__ void __launch_bounds__(MAXNT, MFS_BATCH_MINB) k_batch(const BatchArgs
             unsigned char* p = sm + ((vb + 15) & ~size_t(15));
             T* scv = reinterpret_cast<T*>(p);
             T* srv = scv + I.o;
-            int* sci = reinterpret_cast<int*>(srv + I.o);
-            int* sri = sci + I.o;
+            IT* sci = reinterpret_cast<IT*>(srv + I.o);
+            IT* sri = sci + I.o;
             for (int k = threadIdx.x; k < I.o; k += blockDim.x) {
                 scv[k] = cv[k];
                 srv[k] = rv[k];
@@ -462,6 +473,8 @@ struct mfs_batch {
     int *order = nullptr, *m = nullptr, *n = nullptr, *o = nullptr, *nsoc = nullptr;
     long long *off_n = nullptr, *off_m = nullptr, *off_o = nullptr, *off_soc = nullptr;
     int *col_ptr = nullptr, *cidx = nullptr, *row_ptr = nullptr, *ridx = nullptr;
+    bool idx16 = false;  // every instance has m, n <= 65535: 16-bit local indices
+    uint16_t *cidx16 = nullptr, *ridx16 = nullptr;
     int *soc_start = nullptr, *soc_size = nullptr;
     int* queue = nullptr;
     long long* iters_done = nullptr;
@@ -537,6 +550,8 @@ BatchArgs<T> batch_args(mfs_batch* s, Store<T>& st, int iters, double tol) {
     a.cval = st.cval;
     a.row_ptr = s->row_ptr;
     a.ridx = s->ridx;
+    a.cidx16 = s->cidx16;
+    a.ridx16 = s->ridx16;
     a.rval = st.rval;
     a.fu = st.fu;
     a.nsoc = s->nsoc;
@@ -573,10 +588,11 @@ template <typename T, int MODE>
 mfs_status launch_batch(mfs_batch* s, Store<T>& st, int iters, double tol, cudaStream_t stream) {
     BatchArgs<T> a = batch_args(s, st, iters, tol);
     a.smem_bytes = smem_for(s);
-    BCUDA(s, cudaFuncSetAttribute(k_batch<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes));
+    auto kern = s->idx16 ? k_batch<T, uint16_t, MODE> : k_batch<T, int, MODE>;
+    BCUDA(s, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes));
     BCUDA(s, cudaMemsetAsync(s->queue, 0, sizeof(int), stream));
     const int grid = std::max(1, std::min(s->count, s->num_sms * std::max(1, (int)s->tune.ctas_per_sm)));
-    k_batch<T, MODE><<<grid, s->tune.threads, a.smem_bytes, stream>>>(a);
+    kern<<<grid, s->tune.threads, a.smem_bytes, stream>>>(a);
     BCUDA(s, cudaGetLastError());
     return MFS_OK;
 }
@@ -840,8 +856,10 @@ mfs_status mfs_batch_create(int64_t count, const int64_t* m, const int64_t* n, c
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&s->max_smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
-    for (const void* f : {(const void*)k_batch<float, 0>, (const void*)k_batch<float, 1>, (const void*)k_batch<double, 0>,
-                          (const void*)k_batch<double, 1>}) {
+    for (const void* f : {(const void*)k_batch<float, int, 0>, (const void*)k_batch<float, int, 1>,
+                          (const void*)k_batch<double, int, 0>, (const void*)k_batch<double, int, 1>,
+                          (const void*)k_batch<float, uint16_t, 0>, (const void*)k_batch<float, uint16_t, 1>,
+                          (const void*)k_batch<double, uint16_t, 0>, (const void*)k_batch<double, uint16_t, 1>}) {
         cudaFuncAttributes fa;
         if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
         if (e == cudaSuccess) s->static_smem = std::max(s->static_smem, (int)fa.sharedSizeBytes);
@@ -878,8 +896,17 @@ mfs_status mfs_batch_create(int64_t count, const int64_t* m, const int64_t* n, c
     BCHK(bupload(s, &s->off_soc, offs.data(), offs.size()));
     BCHK(bupload(s, &s->col_ptr, cp.data(), cp.size()));
     BCHK(bupload(s, &s->row_ptr, rp.data(), rp.size()));
-    BCHK(bupload(s, &s->cidx, ci.data(), ci.size()));
-    BCHK(bupload(s, &s->ridx, ri.data(), ri.size()));
+    // local indices as 16 bits where every instance allows it (a quarter less to read per nonzero
+    // and order, and more instances' matrices fit in shared memory), else 32
+    s->idx16 = *std::max_element(hm.begin(), hm.end()) <= 65535 && *std::max_element(hn.begin(), hn.end()) <= 65535;
+    if (s->idx16) {
+        std::vector<uint16_t> c16(ci.begin(), ci.end()), r16(ri.begin(), ri.end());
+        BCHK(bupload(s, &s->cidx16, c16.data(), c16.size()));
+        BCHK(bupload(s, &s->ridx16, r16.data(), r16.size()));
+    } else {
+        BCHK(bupload(s, &s->cidx, ci.data(), ci.size()));
+        BCHK(bupload(s, &s->ridx, ri.data(), ri.size()));
+    }
     BCHK(bupload(s, &s->soc_start, sst.data(), sst.size()));
     BCHK(bupload(s, &s->soc_size, ssz.data(), ssz.size()));
     BCHK(bzeros(s, &s->queue, 1));
@@ -1004,6 +1031,12 @@ mfs_status mfs_batch_get_solution(mfs_batch* s, int64_t t, double* x, double* la
     cudaFreeAsync(tmp, s->stream);
     BCUDA(s, cudaGetLastError());
     BCUDA(s, cudaStreamSynchronize(s->stream));
+    return MFS_OK;
+}
+
+mfs_status mfs_batch_index_bytes(const mfs_batch* s, int32_t* bytes) {
+    if (!s || !bytes) return MFS_ERR_INVALID;
+    *bytes = s->idx16 ? 2 : 4;
     return MFS_OK;
 }
 

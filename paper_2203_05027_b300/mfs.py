@@ -386,6 +386,8 @@ def _load_batch():
     lib.mfs_batch_last_error.restype = ctypes.c_char_p
     lib.mfs_batch_get_info.argtypes = [P, P, P, P, P]
     lib.mfs_batch_get_info.restype = st
+    lib.mfs_batch_index_bytes.argtypes = [P, P]
+    lib.mfs_batch_index_bytes.restype = st
     lib.mfs_batch_iterate.argtypes = [P, i64]
     lib.mfs_batch_iterate.restype = st
     lib.mfs_batch_solve.argtypes = [P, ctypes.c_double, i64, P, P]
@@ -461,7 +463,10 @@ class Batch:
     def info(self):
         v = [ctypes.c_int64() for _ in range(4)]
         self._check(self._lib.mfs_batch_get_info(self._h, *[ctypes.byref(x) for x in v]))
-        return dict(zip(("count", "total_m", "total_n", "total_nnz"), (x.value for x in v)))
+        ib = ctypes.c_int32()
+        self._check(self._lib.mfs_batch_index_bytes(self._h, ctypes.byref(ib)))
+        return {**dict(zip(("count", "total_m", "total_n", "total_nnz"), (x.value for x in v))),
+                "index_bytes": ib.value}
 
     def iterate(self, k):
         self._check(self._lib.mfs_batch_iterate(self._h, int(k)))

@@ -38,6 +38,7 @@ def mixed_instances():
 def test_batch_matches_oracle(precision, iters):
     probs = mixed_instances()
     bt = mfs.Batch(probs, precision=precision)
+    assert bt.info()["index_bytes"] == 2  # every instance has m, n <= 65535
     bt.iterate(iters)
     dt = np.float32 if precision == "fp32" else np.float64
     for t, p in enumerate(probs):
@@ -135,3 +136,19 @@ def test_full_batch_sampled_instances_match_oracle():
         errs = {k: rel_err(sol[k2], v) for k, k2, v in
                 (("x", "x", st.x), ("z", "z", st.z), ("delta", "delta", st.delta), ("lam", "lam", st.lam))}
         assert max(errs.values()) <= TOL["fp32"], (t, orc_iters, errs)
+
+
+def test_batch_with_a_wide_instance_uses_32_bit_indices():
+    """An instance with more than 65,535 columns keeps the whole batch on 32-bit local indices;
+    the iterates still match the oracle, for it and for the small instances beside it."""
+    probs = [I.small_lp(12, m=28_000, n=70_000), I.small_lp(13, m=200, n=500), I.small_lp(14, m=3000, n=7500)]
+    bt = mfs.Batch(probs, precision="fp32")
+    assert bt.info()["index_bytes"] == 4
+    bt.iterate(40)
+    for t, p in enumerate(probs):
+        orc = oracle.make_oracle(p, dtype=np.float32)
+        orc.iterate(40)
+        st = orc.state()
+        sol = bt.solution(t)
+        errs = {k: rel_err(sol[k], v) for k, v in (("x", st.x), ("z", st.z), ("delta", st.delta), ("lam", st.lam))}
+        assert max(errs.values()) <= TOL["fp32"], (t, errs)

@@ -1206,6 +1206,17 @@ mfs_status staged_on_device(mfs_solver* s, const StagedHost& S, const int* d_ptr
     return MFS_OK;
 }
 
+// Whether a staged pass split into `groups` groups can keep them whole: the average group (segments
+// per group) must fit in the shared memory that plan_staged leaves for the sums (a quick test before
+// planning; plan_staged decides).
+bool groups_may_fit(int nseg, int nother, int groups, int rb, int stages, size_t smem_limit) {
+    const int R = std::max(1, (nother + rb - 1) / rb);
+    const size_t fixed = mfs::staged::smem_bytes(rb, stages, 0, R);
+    if (fixed + 4096 * 4 > smem_limit) return false;
+    const size_t maxg = std::min<size_t>(mfs::staged::MAXG, (smem_limit - fixed) / 16 * 4);
+    return (size_t)((nseg + groups - 1) / groups) <= maxg;
+}
+
 // The staged passes access the iterate's vectors evict-last. Such lines stay in L2 only within the
 // context's persisting set-aside; with settings.l2_keep the first staged solver of a device raises it
 // to the device's maximum and the last one to be destroyed puts the previous value back (where it
@@ -1270,7 +1281,7 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
         bool ok = false;
         for (int h = COL_PARTS_MAX; h >= 1 && !ok; h /= 2) {
             const int groups = std::max(1, s->num_sms / h);
-            if (h > 1 && R / h < 8) continue;
+            if (h > 1 && (R / h < 8 || !groups_may_fit(P.n, P.m, groups, RB_COL, S_COL, (size_t)optin))) continue;
             StagedHost T;
             if (!plan_staged(P.col_ptr, P.n, P.m, groups, RB_COL, S_COL, (size_t)optin, T,
                              s->has_soc ? &unit_start : nullptr))
@@ -1291,7 +1302,8 @@ mfs_status setup_staged(mfs_solver* s, const HostProblem& P) {
         bool ok = false;
         for (int h = ROW_PARTS_MAX; h >= ROW_HALVES && !ok; h /= 2) {
             const int groups = std::max(1, s->num_sms / h);
-            if (h > ROW_HALVES && R / h < 8) continue;
+            if (h > ROW_HALVES && (R / h < 8 || !groups_may_fit(P.m, P.n, groups, RB_ROW, S_ROW, (size_t)optin)))
+                continue;
             StagedHost T;
             if (!plan_staged(P.row_ptr, P.m, P.n, groups, RB_ROW, S_ROW, (size_t)optin, T)) continue;
             if (h > ROW_HALVES && T.G > groups) continue;  // groups split for shared memory: fewer parts

@@ -4,7 +4,11 @@ The GPU runs the reduced form on (x, z, delta, lambda); the oracle runs the lite
 with o-length y and gamma. After a fixed number of iterations both must agree element by element:
 max_i |gpu_i - oracle_i| <= tol * max_i |oracle_i| for each of x, z, delta, lambda, with
 tol = 1e-10 in FP64 mode and 1e-4 in FP32 mode (the oracle then runs on the FP32-rounded A, b, c
-promoted to FP64, so only the arithmetic differs).
+promoted to FP64, so only the arithmetic differs). Each element is also checked against its own size:
+|gpu_i - oracle_i| <= etol * (|oracle_i| + floor * max_j |oracle_j|), with (etol, floor) = (1e-8, 1e-6)
+in FP64 and (5e-3, 1e-3) in FP32, so that small entries are not checked only relative to the largest
+(the measured worst cases: 5e-10 in FP64 after 300 iterations of a power-law LP, 8e-4 in FP32 after
+2000 iterations of the small LP).
 """
 import numpy as np
 import pytest
@@ -15,6 +19,7 @@ from paper_2203_05027_b300 import build, instances as I, mfs
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-10, "fp32": 1e-4}
+ELEMENTWISE = {1e-10: (1e-8, 1e-6), 1e-4: (5e-3, 1e-3)}  # tol -> (etol, floor)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -29,11 +34,24 @@ def rel_err(g, o):
     return d / scale if scale > 0 else d
 
 
+def elem_err(g, o, floor):
+    if not o.size:
+        return 0.0
+    scale = np.abs(o).max()
+    den = np.abs(o) + floor * scale
+    return float((np.abs(g - o) / np.where(den > 0, den, 1.0)).max())
+
+
 def compare(sol, st, tol, label=""):
-    errs = {"x": rel_err(sol["x"], st.x), "z": rel_err(sol["z"], st.z),
-            "delta": rel_err(sol["delta"], st.delta), "lam": rel_err(sol["lam"], st.lam)}
+    pairs = (("x", st.x), ("z", st.z), ("delta", st.delta), ("lam", st.lam))
+    errs = {k: rel_err(sol[k], v) for k, v in pairs}
     bad = {k: v for k, v in errs.items() if not v <= tol}
     assert not bad, (label, errs)
+    if tol in ELEMENTWISE:
+        etol, floor = ELEMENTWISE[tol]
+        eerrs = {k: elem_err(sol[k], v, floor) for k, v in pairs}
+        ebad = {k: v for k, v in eerrs.items() if not v <= etol}
+        assert not ebad, (label, "element-wise", eerrs)
     return errs
 
 
@@ -339,17 +357,17 @@ def test_repeatable_bitwise():
         assert np.array_equal(sa[k], sb[k]), k
 
 
-# ------------------------------------------------------------------ full-size workloads (few iterations)
+# ------------------------------------------------------------------ full-size workloads (the bench's launch configuration)
 
 def test_large_lp_full_size_fp32_parity():
     prob = I.large_lp(0)
-    orc, s = run_pair(prob, 3, "fp32")
+    orc, s = run_pair(prob, 20, "fp32")
     compare(s.solution(), orc.state(), TOL["fp32"], "large_lp full size")
 
 
 def test_socp_full_size_fp32_parity():
     prob = I.socp(0)
-    orc, s = run_pair(prob, 3, "fp32")
+    orc, s = run_pair(prob, 50, "fp32")
     compare(s.solution(), orc.state(), TOL["fp32"], "socp full size")
 
 

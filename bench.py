@@ -230,7 +230,7 @@ def cpu_baseline(prob, iters=3):
                       f"({dt:.2f} s, set-up not timed)"}
 
 
-def batch_workload(stream, seed, iters=100, tts_iters=300_000):
+def batch_workload(stream, seed, iters=100, tts_iters=300_000, extend_iters=1_000_000):
     """Extra workload: 4096 LPs with m log-uniform on [50, 5000], n = 2.5m, 5 nonzeros per column,
     solved together by one persistent launch (FP32 sweep). The autotuner picks threads per CTA and
     CTAs per SM; then `iters` iterations of the whole batch are timed with CUDA events, and a fresh
@@ -263,10 +263,26 @@ def batch_workload(stream, seed, iters=100, tts_iters=300_000):
     torch.cuda.synchronize()
     tts_s = time.perf_counter() - t0
     kkt = np.array([r["kkt"] for r in bt2.residuals()])
-    bt2.close()
     ok = its[sts == 0]
     left = sts != 0
     ms_ = np.array([p["m"] for p in probs])
+    # the members at the cap continue from where they stopped (a second solve; those already at
+    # tol leave at their first check), up to extend_iters more iterations each
+    ext = None
+    if left.any() and extend_iters:
+        t1 = time.perf_counter()
+        its2, sts2 = bt2.solve(1e-6, extend_iters)
+        torch.cuda.synchronize()
+        more = left & (sts2 == 0)
+        tot = (its + its2)[more]
+        kkt2 = np.array([r["kkt"] for r in bt2.residuals()])
+        ext = {"extra_max_iter": extend_iters, "seconds": round(time.perf_counter() - t1, 3),
+               "converged": int(more.sum()), "of": int(left.sum()),
+               "converged_total": int(ok.size + more.sum()),
+               "total_iterations_median": float(np.median(tot)) if tot.size else None,
+               "total_iterations_max": int(tot.max()) if tot.size else None,
+               "still_above_tol_kkt_max": float(kkt2[left & (sts2 != 0)].max()) if (left & (sts2 != 0)).any() else None}
+    bt2.close()
     tts = {"tol": 1e-6, "max_iter": tts_iters, "seconds": round(tts_s, 3), "converged": int(ok.size),
            "instances_per_s": round(ok.size / tts_s, 1),
            "iterations_median": float(np.median(ok)) if ok.size else None,
@@ -276,7 +292,8 @@ def batch_workload(stream, seed, iters=100, tts_iters=300_000):
                       "kkt_median": float(np.median(kkt[left])) if left.any() else None,
                       "kkt_max": float(kkt[left].max()) if left.any() else None,
                       "below_1e-5": int((kkt[left] <= 1e-5).sum()), "below_1e-4": int((kkt[left] <= 1e-4).sum()),
-                      "m_median": float(np.median(ms_[left])) if left.any() else None}}
+                      "m_median": float(np.median(ms_[left])) if left.any() else None},
+           "at_cap_continued": ext}
     out = {"workload": "batch_lps 4096 instances, m log-uniform [50, 5000], n = 2.5 m, 5 nnz/col",
            "total_nnz": info["total_nnz"], "total_m": info["total_m"], "total_n": info["total_n"],
            "iterations": iters, "ms_per_batch_iteration": round(ms / iters, 5),

@@ -166,6 +166,13 @@ struct GemmArgs {
 
 enum { EPI_STORE = 0, EPI_LOSS = 1, EPI_ADAM = 2 };
 
+// Hint: bring the 16-byte-aligned part of [p, p + bytes) into L2 (a bulk prefetch; nothing outside
+// the range is touched, nothing waits for it).
+__device__ __forceinline__ void gemm_prefetch_l2(const void* p, size_t bytes) {
+    const uintptr_t s = ((uintptr_t)p + 15) & ~(uintptr_t)15, e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+    if (e > s) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"((uint32_t)(e - s)) : "memory");
+}
+
 template <int EPI>
 __global__ void __launch_bounds__(NTHREADS, 2)
     k_gemm_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const GemmArgs g) {
@@ -203,6 +210,26 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
+    // The fused epilogues read a tile of FP32 data besides the accumulator (the targets; W and its
+    // moments): the warps that wait for the accumulator prefetch those rows into L2 now, so that the
+    // epilogue's loads, issued after the short main loop (K <= 512), find them there.
+    if (EPI != EPI_STORE && gridDim.z == 1 && warp >= 2) {
+        const int t = (warp - 2) * 32 + lane, row = m0 + t;
+        if (t < BM && row < g.M) {
+            if (EPI == EPI_LOSS) {
+                const int c1 = min(n0 + BN, g.dout);
+                if (c1 > n0) gemm_prefetch_l2(g.T + (size_t)row * g.ldT + n0, (size_t)(c1 - n0) * sizeof(float));
+            } else {
+                const int c1 = min(n0 + BN, g.N);
+                if (c1 > n0) {
+                    const size_t off = (size_t)row * g.ldc + n0, bytes = (size_t)(c1 - n0) * sizeof(float);
+                    gemm_prefetch_l2(g.W + off, bytes);
+                    gemm_prefetch_l2(g.mom + off, bytes);
+                    gemm_prefetch_l2(g.vel + off, bytes);
+                }
+            }
+        }
+    }
 
     int issued = 0;                // loads issued by the producer lane
     if (warp == 0 && lane == 0) {  // producer

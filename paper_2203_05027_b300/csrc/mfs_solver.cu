@@ -1510,14 +1510,15 @@ static mfs_status get_solution_t(mfs_solver* s, State<T>& st, double* x, double*
 }
 
 template <typename T>
-static mfs_status time_kernels_t(mfs_solver* s, State<T>& st, int64_t k, double* out) {
+static mfs_status time_kernels_t(mfs_solver* s, State<T>& st, int64_t k, double* out, bool split) {
     // k iterations back to back, an event after each kernel group (a pass's main kernel, its
     // combine or long-chunk kernel, the big cones, ...); one wait at the end, so that no host round
     // trip idles the GPU between iterations. out: column main, column rest, big cones, row main,
-    // row rest, whole iteration (average milliseconds).
+    // row rest, whole iteration (average milliseconds). Without `split` the events fall only between
+    // passes (a pass's kernels keep their programmatic overlap; its time is in "main").
     SweepArgs<T> a = sweep_args(s, st);
     const int64_t kk = std::max<int64_t>(k, 0);
-    constexpr int E = 5;
+    const int E = split ? 5 : 3;  // events per iteration
     std::vector<cudaEvent_t> ev((size_t)(E * kk + 1), nullptr);
     mfs_status r = MFS_OK;
     for (auto& e : ev)
@@ -1526,17 +1527,26 @@ static mfs_status time_kernels_t(mfs_solver* s, State<T>& st, int64_t k, double*
             r = fail(s, MFS_ERR_CUDA, "cudaEventCreate failed");
             break;
         }
-    double t[E] = {0, 0, 0, 0, 0}, tall = 0;
+    double t[5] = {0, 0, 0, 0, 0}, tall = 0;
     if (r == MFS_OK) {
         cudaEventRecord(ev[0], s->stream);
         for (int64_t i = 0; i < kk; ++i) {
             cudaEvent_t* e = ev.data() + E * i;
-            launch_col(s, a, s->stream, e[1]);
-            cudaEventRecord(e[2], s->stream);
-            launch_big(s, a, s->stream);
-            cudaEventRecord(e[3], s->stream);
-            launch_row(s, a, s->stream, e[4]);
-            cudaEventRecord(e[5], s->stream);
+            if (split) {
+                launch_col(s, a, s->stream, e[1]);
+                cudaEventRecord(e[2], s->stream);
+                launch_big(s, a, s->stream);
+                cudaEventRecord(e[3], s->stream);
+                launch_row(s, a, s->stream, e[4]);
+                cudaEventRecord(e[5], s->stream);
+            } else {
+                launch_col(s, a, s->stream);
+                cudaEventRecord(e[1], s->stream);
+                launch_big(s, a, s->stream);
+                cudaEventRecord(e[2], s->stream);
+                launch_row(s, a, s->stream);
+                cudaEventRecord(e[3], s->stream);
+            }
         }
         cudaError_t e = cudaEventSynchronize(ev[E * kk]);
         if (e != cudaSuccess) r = fail(s, MFS_ERR_CUDA, std::string("time_kernels: ") + cudaGetErrorString(e));
@@ -1557,11 +1567,19 @@ static mfs_status time_kernels_t(mfs_solver* s, State<T>& st, int64_t k, double*
     if (r != MFS_OK) return r;
     s->iter += k;
     const double kd = kk > 0 ? (double)kk : 1.0;
-    out[0] = t[0] / kd;  // column main kernel
-    out[1] = t[1] / kd;  // column combine / long chunks
-    out[2] = t[2] / kd;  // big cones
-    out[3] = t[3] / kd;  // row main kernel
-    out[4] = t[4] / kd;  // row combine / long chunks
+    if (split) {
+        out[0] = t[0] / kd;  // column main kernel
+        out[1] = t[1] / kd;  // column combine / long chunks
+        out[2] = t[2] / kd;  // big cones
+        out[3] = t[3] / kd;  // row main kernel
+        out[4] = t[4] / kd;  // row combine / long chunks
+    } else {  // per pass: column, big cones, row
+        out[0] = t[0] / kd;
+        out[1] = 0.0;
+        out[2] = t[1] / kd;
+        out[3] = t[2] / kd;
+        out[4] = 0.0;
+    }
     out[5] = tall / kd;
     CUDA_TRY(s, cudaGetLastError());
     return MFS_OK;
@@ -2453,13 +2471,16 @@ mfs_status mfs_get_reduced_v(mfs_solver* s, double* v) {
 mfs_status mfs_time_kernel_split(mfs_solver* s, int64_t k, double* out_ms) {
     if (!s || !out_ms || k < 0) return MFS_ERR_INVALID;
     CUDA_TRY(s, cudaSetDevice(s->device));
-    return s->precision == MFS_FP64 ? time_kernels_t(s, s->s64, k, out_ms) : time_kernels_t(s, s->s32, k, out_ms);
+    return s->precision == MFS_FP64 ? time_kernels_t(s, s->s64, k, out_ms, true)
+                                    : time_kernels_t(s, s->s32, k, out_ms, true);
 }
 
 mfs_status mfs_time_kernels(mfs_solver* s, int64_t k, double* out_ms) {
     if (!s || !out_ms || k < 0) return MFS_ERR_INVALID;
+    CUDA_TRY(s, cudaSetDevice(s->device));
     double t[6];
-    const mfs_status r = mfs_time_kernel_split(s, k, t);
+    const mfs_status r = s->precision == MFS_FP64 ? time_kernels_t(s, s->s64, k, t, false)
+                                                  : time_kernels_t(s, s->s32, k, t, false);
     if (r != MFS_OK) return r;
     out_ms[0] = t[0] + t[1];
     out_ms[1] = t[3] + t[4];

@@ -203,6 +203,28 @@ __device__ __forceinline__ int ldg_keep(const int* p, uint64_t pol) {
     return __ldg(p);
 #endif
 }
+// four consecutive floats (p 16-byte aligned), with the policy
+__device__ __forceinline__ float4 ld4_keep(const float* p, uint64_t pol) {
+    float4 v;
+#if MFS_STG_KEEP
+    asm volatile("ld.global.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(pol)
+                 : "memory");
+#else
+    v = *reinterpret_cast<const float4*>(p);
+#endif
+    return v;
+}
+__device__ __forceinline__ void st4_keep(float* p, float4 v, uint64_t pol) {
+#if MFS_STG_KEEP
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w), "l"(pol)
+                 : "memory");
+#else
+    *reinterpret_cast<float4*>(p) = v;
+#endif
+}
 __device__ __forceinline__ void st_keep(float* p, float v, uint64_t pol) {
 #if MFS_STG_KEEP
     asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
@@ -625,8 +647,42 @@ __global__ void __launch_bounds__(256) k_row_combine(const StagedArgs g, const S
     dep_wait_prev();
     const int m = g.nseg;
     const uint64_t kp = policy_keep();
-    const float rmu = 1.f / a.mu;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const float rmu = 1.f / a.mu, mu = a.mu;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    // four rows at a time with 16-byte accesses where every array allows it (m a multiple of 4, so
+    // that each part starts aligned too), the same arithmetic row by row as below
+    const bool vec = (m & 3) == 0 && (((uintptr_t)g.part | (uintptr_t)g.rinv | (uintptr_t)a.b | (uintptr_t)a.lam |
+                                        (uintptr_t)a.v) & 15) == 0;
+    const int m4 = vec ? m / 4 : 0;
+    for (int q = tid; q < m4; q += nth) {
+        const int i = 4 * q;
+        float4 ax = ld4_keep(g.part + i, kp);
+        for (int h = 1; h < g.halves; ++h) {
+            const float4 p = ld4_keep(g.part + (size_t)h * m + i, kp);
+            ax.x += p.x;
+            ax.y += p.y;
+            ax.z += p.z;
+            ax.w += p.w;
+        }
+        const float4 r = ld4_keep(g.rinv + i, kp), bi = ld4_keep(a.b + i, kp), li = ld4_keep(a.lam + i, kp);
+        float4 ln, vn;
+        float rho;
+        rho = (bi.x - ax.x) * r.x;
+        ln.x = li.x - mu * rho;
+        vn.x = rho - ln.x * rmu;
+        rho = (bi.y - ax.y) * r.y;
+        ln.y = li.y - mu * rho;
+        vn.y = rho - ln.y * rmu;
+        rho = (bi.z - ax.z) * r.z;
+        ln.z = li.z - mu * rho;
+        vn.z = rho - ln.z * rmu;
+        rho = (bi.w - ax.w) * r.w;
+        ln.w = li.w - mu * rho;
+        vn.w = rho - ln.w * rmu;
+        st4_keep(a.lam + i, ln, kp);
+        st4_keep(a.v + i, vn, kp);
+    }
+    for (int i = 4 * m4 + tid; i < m; i += nth) {
         float ax = ld_keep(g.part + i, kp);
         for (int h = 1; h < g.halves; ++h) ax += ld_keep(g.part + (size_t)h * m + i, kp);
         row_keep(a, i, ax, ldg_keep(g.rinv + i, kp), ldg_keep(a.b + i, kp), ld_keep(a.lam + i, kp), rmu, kp);

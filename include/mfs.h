@@ -263,7 +263,7 @@ mfs_status mfs_iterate(mfs_solver* s, int64_t k);
  * met) or MFS_MAX_ITER; MFS_ERR_NUMERIC if the residuals become NaN/Inf. iters_out (nullable)
  * receives the iterations run by this call. In FP32_MIXED mode the iterate switches to FP64
  * (and stays there) for the final polish_iters iterations, or as soon as the FP32 residual has
- * not improved over 40 consecutive checks; the tolerance is always judged on FP64 reductions.
+ * not improved over 40 consecutive checks; the tolerance is always tested on FP64 reductions.
  * Primal infeasibility: when Ax = b, x in K has no solution, lambda grows along a direction d
  * with A^T d in K* (= K) and b^T d < 0 (Farkas). At every check the change d of lambda since the
  * previous check is tested: dist(A^T d, K) <= 0.1 |b^T d|, b^T d < -1e-3 ||b|| ||d||, and the

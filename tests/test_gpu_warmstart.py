@@ -1,7 +1,7 @@
 """What the trained warm-start network gains over the method without it, on held-out members of a
 parametric LP family (A fixed, m = 2000, n = 5000, 8 nonzeros per column, b and c moved by
 theta ~ N(0, I_32) through N(0, 0.1^2) matrices). The network is trained on the GPU by the
-library's own kernels on 4096 solves the solver produced; the cold-start method then judges every
+library's own kernels on 4096 solves the solver produced; the cold-start method then checks every
 warm-started member: each must still reach the tolerance by the solver's own residuals."""
 import numpy as np
 import pytest

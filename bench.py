@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--warm-start-test", type=int, default=128,
                     help="held-out members solved to 1e-6 by each arm (cold, network, mean, nearest; 1000 "
                          "in the full experiment)")
-    ap.add_argument("--section", default="all", choices=["all", "small", "socp", "paper", "batch", "shared", "mlp"],
+    ap.add_argument("--section", default="all", choices=["all", "small", "socp", "paper", "batch", "shared", "mlp", "ruiz"],
                     help="run only one extra workload and print its line (for profiling)")
     ap.add_argument("--tts-iters", type=int, default=300000,
                     help="also solve to 1e-6 KKT from the cold start with at most this many iterations (0: skip)")
@@ -302,6 +302,43 @@ def batch_workload(stream, seed, iters=100, tts_iters=300_000, extend_iters=1_00
     return out
 
 
+def ruiz_workload(stream, seed, max_iter=600_000):
+    """Convergence variant outside the paper: Ruiz equilibration (10 passes, mfs_ruiz_scale) of a
+    power-law LP (m = 2000, n = 5000, the large LP's construction at a smaller size), solved to
+    relative KKT 1e-6 in FP64 with and without it; the scaled solve's point is mapped back and judged
+    by the original problem's residuals (a solver of the original warm-started there)."""
+    import torch
+    from paper_2203_05027_b300 import instances as I, mfs
+    prob = I.large_lp(3 + seed, m=2000, n=5000)
+    out = {"workload": "power-law LP m=2000 n=5000, FP64, to relative KKT 1e-6, checks every 50",
+           "passes": 10}
+    for name, scaled in (("plain", False), ("ruiz", True)):
+        t0 = time.perf_counter()
+        if scaled:
+            q, d, e = mfs.ruiz_scale(prob, passes=10)
+        else:
+            q = prob
+        s = mfs.Solver(q, precision="fp64", polish_iters=0, check_every=50, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        st, its = s.solve(1e-6, max_iter)
+        torch.cuda.synchronize()
+        rec = {"status": st, "iterations": its, "seconds": round(time.perf_counter() - t1, 3),
+               "setup_seconds": round(t1 - t0, 3)}
+        if scaled:
+            sol = s.solution()
+            x, lam, z, dl = mfs.ruiz_unscale(d, e, sol["x"], sol["lam"], sol["z"], sol["delta"])
+            o = mfs.Solver(prob, precision="fp64", polish_iters=0, stream=stream.cuda_stream)
+            o.warm_start(x, lam, z, dl)
+            rec["kkt_original"] = o.residuals()["kkt"]
+            o.close()
+        else:
+            rec["kkt_original"] = s.residuals()["kkt"]
+        s.close()
+        out[name] = rec
+    return out
+
+
 def socp_workload(stream, seed, iters=250):
     """Extra workload: the sparse SOCP (n = 1,000,000 in Lorentz cones of sizes 3..64, m = 400,000 rows
     with 10 nonzeros each), FP32 sweep: `iters` iterations timed with CUDA events (one FP64 residual
@@ -514,7 +551,7 @@ def main():
         stream = torch.cuda.current_stream()
         fn = {"small": lambda: small_workload(stream, rank), "batch": lambda: batch_workload(stream, rank),
               "socp": lambda: socp_workload(stream, rank), "paper": lambda: paper_family_workload(stream, rank), "shared": lambda: shared_workload(stream, rank),
-              "mlp": lambda: mlp_workload(stream, load_peaks_raw())}[args.section]
+              "mlp": lambda: mlp_workload(stream, load_peaks_raw()), "ruiz": lambda: ruiz_workload(stream, rank)}[args.section]
         if rank == 0:
             print(json.dumps({"section": args.section, **fn()}), flush=True)
         return
@@ -610,6 +647,7 @@ def main():
             "status": st4, "iterations": its4, "seconds": round(t4, 3), "kkt": s4.residuals()["kkt"],
             "mu_final": h4[-1]["mu"] if h4 else None}
         s4.close()
+        extra["variant_ruiz"] = ruiz_workload(stream, rank)
 
     if not args.no_batch:
         extra["batch_lps"] = batch_workload(stream, rank)

@@ -388,6 +388,31 @@ mfs_status mfs_batch_get_tuning(const mfs_batch* bt, mfs_batch_tuning* tuning);
 mfs_status mfs_batch_tune(mfs_batch* bt, int64_t iters, mfs_batch_tuning* chosen);
 
 /* ------------------------------------------------------------------------------------------------
+ * Ruiz equilibration of the data, a convergence variant outside the paper (Algorithm 1 runs on the
+ * data as given): D. Ruiz's scaling (2001). Host functions; the caller creates a solver of any kind
+ * on the scaled data and maps its solution back.
+ * ---------------------------------------------------------------------------------------------- */
+/* passes of: take the infinity norms of the rows and of the columns of the current matrix over the
+   listed COO entries (the columns of one Lorentz cone share the largest of their norms, so that the
+   cone is scaled as one block and stays a cone), then divide every row and column by the square root
+   of its norm (a zero norm leaves it alone); each entry is multiplied by its row factor, then by its
+   column factor. In place: val (nnz) becomes A' = D A E, b (m) becomes D b, c (n) becomes E c; d (m)
+   and e (n) receive the diagonals of D and E. Same argument rules as mfs_create (indices in range,
+   finite values, cones summing to n) -> MFS_ERR_INVALID with mfs_ruiz_last_error() set, before
+   anything is written. Repeated (row, column) entries count separately in the norms. */
+mfs_status mfs_ruiz_scale(int64_t m, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col, double* val,
+                          double* b, double* c, int64_t ncones, const mfs_cone* cones, int32_t passes, double* d,
+                          double* e);
+/* The original problem's point from the scaled problem's, in place (any of x, z, delta (n), lambda (m)
+   may be NULL): x = E x', z = E z', lambda = D lambda', delta = E^-1 delta'. */
+mfs_status mfs_ruiz_unscale(int64_t m, int64_t n, const double* d, const double* e, double* x, double* lambda,
+                            double* z, double* delta);
+/* The inverse map, for a start of the original problem given to a solver of the scaled one. */
+mfs_status mfs_ruiz_scale_start(int64_t m, int64_t n, const double* d, const double* e, double* x, double* lambda,
+                                double* z, double* delta);
+const char* mfs_ruiz_last_error(void);
+
+/* ------------------------------------------------------------------------------------------------
  * Shared-A solves: count problems with one constraint matrix A and cone K and their own b and c
  * (a parametric family), iterated together. The instances' vectors are interleaved so that each
  * nonzero's gather serves 32 instances with one coalesced load.

@@ -6,7 +6,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmfs.so")
-SOURCES = ["mfs_solver.cu", "mfs_batch.cu", "mfs_shared.cu", "mfs_mlp.cu", "mfs_static.cu"]
+SOURCES = ["mfs_solver.cu", "mfs_batch.cu", "mfs_shared.cu", "mfs_mlp.cu", "mfs_static.cu", "mfs_ruiz.cu"]
 HEADERS = ["mfs_device.cuh", "mfs_kernels.cuh", "mfs_staged.cuh", "mfs_gemm.cuh", "mfs_alloc.h", "mfs_literal.cuh", "mfs_infeas.cuh", "mfs_host.h", "mfs_measures.h", "mfs_trace.h", "mfs_setup.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -365,6 +365,61 @@ def row_residuals_static(m, n, row_ptr, col_idx, val, b, x, lam, out, stream=Non
                              "negative arguments give ERR_INVALID)")
 
 
+def _ruiz_fns(lib):
+    if not lib.mfs_ruiz_scale.argtypes:
+        P, i64 = ctypes.c_void_p, ctypes.c_int64
+        lib.mfs_ruiz_scale.argtypes = [i64, i64, i64, P, P, P, P, P, i64, P, ctypes.c_int32, P, P]
+        lib.mfs_ruiz_scale.restype = ctypes.c_int
+        for name in ("mfs_ruiz_unscale", "mfs_ruiz_scale_start"):
+            getattr(lib, name).argtypes = [i64, i64, P, P, P, P, P, P]
+            getattr(lib, name).restype = ctypes.c_int
+        lib.mfs_ruiz_last_error.argtypes = []
+        lib.mfs_ruiz_last_error.restype = ctypes.c_char_p
+
+
+def ruiz_scale(prob, passes=10):
+    """mfs_ruiz_scale on a copy of a problem dict (keys m, n, row, col, val, b, c, cones): returns
+    (the scaled dict, d, e) with A' = D A E, b' = D b, c' = E c (a variant outside the paper)."""
+    lib = load()
+    _ruiz_fns(lib)
+    m, n = int(prob["m"]), int(prob["n"])
+    row = np.ascontiguousarray(prob["row"], dtype=np.int64)
+    col = np.ascontiguousarray(prob["col"], dtype=np.int64)
+    val = np.array(prob["val"], dtype=np.float64)
+    b = np.array(prob["b"], dtype=np.float64)
+    c = np.array(prob["c"], dtype=np.float64)
+    carr, ncones = _cone_array(prob["cones"])
+    d, e = np.empty(m), np.empty(n)
+    code = lib.mfs_ruiz_scale(m, n, row.size, _ptr(row), _ptr(col), _ptr(val), _ptr(b), _ptr(c), ncones,
+                              ctypes.cast(carr, ctypes.c_void_p), int(passes), _ptr(d), _ptr(e))
+    if code != MFS_OK:
+        raise MfsError(code, lib.mfs_ruiz_last_error().decode())
+    out = dict(prob)
+    out["val"], out["b"], out["c"] = val, b, c
+    return out, d, e
+
+
+def _ruiz_map(fn_name, d, e, x, lam, z, delta):
+    lib = load()
+    _ruiz_fns(lib)
+    arrs = [None if v is None else np.array(v, dtype=np.float64) for v in (x, lam, z, delta)]
+    code = getattr(lib, fn_name)(len(d), len(e), _ptr(np.ascontiguousarray(d, dtype=np.float64)),
+                                 _ptr(np.ascontiguousarray(e, dtype=np.float64)), *[_ptr(v) for v in arrs])
+    if code != MFS_OK:
+        raise MfsError(code, lib.mfs_ruiz_last_error().decode())
+    return tuple(arrs)
+
+
+def ruiz_unscale(d, e, x=None, lam=None, z=None, delta=None):
+    """mfs_ruiz_unscale: the original problem's (x, lambda, z, delta) from the scaled one's (copies)."""
+    return _ruiz_map("mfs_ruiz_unscale", d, e, x, lam, z, delta)
+
+
+def ruiz_scale_start(d, e, x=None, lam=None, z=None, delta=None):
+    """mfs_ruiz_scale_start: a start of the original problem for a solver of the scaled one (copies)."""
+    return _ruiz_map("mfs_ruiz_scale_start", d, e, x, lam, z, delta)
+
+
 class BatchTuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]

@@ -1191,7 +1191,7 @@ mfs_status staged_on_device(mfs_solver* s, const StagedHost& S, const int* d_ptr
     CUDA_TRY(s, cudaMemcpyAsync(&hmax, slots_max, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(s, cudaGetLastError());
     CUDA_TRY(s, cudaStreamSynchronize(st));
-    const int slots = (hmax + 1 + 3) / 4 * 4;  // and one slot past them for the padding entries
+    const int slots = (hmax + 3) / 4 * 4;
     if (slots >= mfs::staged::MAXSLOT || mfs::staged::smem_bytes(rb, stages, slots, R) > smem_limit) return MFS_OK;
     g.ent = lent;
     g.split = split;

@@ -83,8 +83,10 @@ constexpr int MAXG = 24576;    // segments per group (their sums take 96 KB of s
 constexpr int PFR_COL = MFS_STG_PFR_COL;  // rounds of 32 entries a warp prefetches per block (column pass;
                                           // a warp takes about 146 entries of a 64 KB block of v)
 constexpr int PFR_ROW = MFS_STG_PFR_ROW;  // (row pass: about 120)
-constexpr int PADSEG = 0xFFFF;  // "no slot": a padding position (column pass) or a lane with no open run
-constexpr int MAXSLOT = 0xFFFF; // slots (segment sums and overflow sums) per group are below this
+constexpr int PADSEG = 0xFFFF;  // "no slot": a lane with no open run, or no run ending at an entry
+constexpr int MAXSLOT = 0x7FFF; // slots (segment sums and overflow sums) per group are below this: an
+                                // entry's 16-bit slot is read sign-extended, 0xFFFF being slot -1, the
+                                // spare sum in front of the group's sums that padding positions add into
 constexpr int EPI_U = 6;       // epilogue items per thread in flight
 #ifndef MFS_STG_PDL
 #define MFS_STG_PDL 1
@@ -106,9 +108,10 @@ constexpr int EPI_U = 6;       // epilogue items per thread in flight
 constexpr int ENT_PD = MFS_STG_ENT_PD;  // blocks ahead at which the producer prefetches a block's
                                         // entries into L2 (the consumers load them one block ahead)
 
-// dynamic shared memory of one CTA: the vector stages, the group's sums, its split table, 2 S mbarriers
+// dynamic shared memory of one CTA: the vector stages, the spare sum (16 bytes), the group's sums, its
+// split table, 2 S mbarriers
 __host__ __device__ constexpr size_t smem_bytes(int rb, int stages, int maxg, int R) {
-    return (size_t)stages * rb * 4 + (size_t)((maxg + 3) / 4 * 4) * 4 + (size_t)((R * (NW + 1) + 3) / 4 * 4) * 4 +
+    return (size_t)stages * rb * 4 + 16 + (size_t)((maxg + 3) / 4 * 4) * 4 + (size_t)((R * (NW + 1) + 3) / 4 * 4) * 4 +
            (size_t)16 * stages;
 }
 
@@ -134,7 +137,7 @@ struct StagedArgs {
     const float* __restrict__ dinv;  // column pass: 1/(1 + d_j), d_j = nonzeros of column j
     int* err;                       // set to 1 if a wait for a block gave up
     int G, R, maxg_pad;             // maxg_pad: sum slots (segments and overflow) of the largest group,
-                                    // plus its last slot, which no segment uses (padding entries add there)
+                                    // rounded up to a multiple of 4 (padding entries add into slot -1)
     int halves;                     // row pass: CTAs per group, each streaming 1/halves of x (1 or 2)
     float* part;                    // halves > 1: halves x nseg partial row sums
     int nseg;                       // segments of the pass (rows for the row pass)
@@ -314,9 +317,9 @@ __device__ __forceinline__ bool wait_block(uint64_t* bar, uint32_t parity, int s
 // Rounds [s0 + 32 r, s0 + 32 r + 32) of a warp's range [s0, s1) for r < PFR: lane l loads entry
 // s0 + 32 r + l (one coalesced 256-byte load per round, bypassing L1 and marked first to leave L2:
 // each entry is read once); positions at or past s1 hold no entry.
-template <int PFR, bool PS>
+template <int PFR>
 __device__ __forceinline__ void load_rounds(const int2* __restrict__ ent, int s0, int s1, int lane, int2 (&e)[PFR],
-                                            int nent, int pad, uint64_t pol) {
+                                            int nent, uint64_t pol) {
 #pragma unroll
     for (int r = 0; r < PFR; ++r) {
         const int q = s0 + r * 32 + lane;
@@ -325,7 +328,7 @@ __device__ __forceinline__ void load_rounds(const int2* __restrict__ ent, int s0
                 : "=r"(e[r].x), "=r"(e[r].y)
                 : "l"(ent + q), "l"(pol));
         } else {
-            e[r] = make_int2(PS ? pad : PADSEG, 0);  // PS: gathered index 0, value 0, the unused last slot
+            e[r] = make_int2(0xFFFF, 0);  // gathered index 0, value 0, the spare slot -1
         }
     }
 }
@@ -334,7 +337,7 @@ __device__ __forceinline__ void load_rounds(const int2* __restrict__ ent, int s0
 // the slot repeats; where it changes, the run's sum is added to its slot. Slots that end a run are
 // distinct within a lane and owned by that lane in this block, so their read-modify-writes are
 // issued as all loads, then all stores.
-template <int PFR, int RB, bool PS>
+template <int PFR, int RB>
 __device__ __forceinline__ void lane_chunk(const int2 (&e)[PFR], const float* vb, float* acc, int nacc, int& cur,
                                            float& sum) {
     int sg[PFR];
@@ -342,17 +345,15 @@ __device__ __forceinline__ void lane_chunk(const int2 (&e)[PFR], const float* vb
 #pragma unroll
     for (int r = 0; r < PFR; ++r) {
         const uint32_t gi = (uint32_t)e[r].x >> 16;
-        const int k = e[r].x & 0xFFFF;
-#ifndef MFS_DEBUG_BOUNDS
-        if (PS) {  // padding positions carry the unused last slot and a zero value: no test needed
-            sg[r] = k;
-            p[r] = __int_as_float(e[r].y) * vb[gi];
-            continue;
-        }
-#endif
-        const bool ok = k != PADSEG && MFS_INB(gi, RB, BS_STG_VEC) && MFS_INB(k, nacc, BS_STG_ACC);
-        sg[r] = ok ? k : PADSEG;
+        const int k = (int)(int16_t)(uint16_t)(e[r].x & 0xFFFF);  // padding: -1, the spare slot
+#ifdef MFS_DEBUG_BOUNDS
+        const bool ok = MFS_INB(gi, RB, BS_STG_VEC) && (k == -1 || MFS_INB(k, nacc, BS_STG_ACC));
+        sg[r] = ok ? k : -1;
         p[r] = ok ? __int_as_float(e[r].y) * vb[gi] : 0.f;
+#else
+        sg[r] = k;
+        p[r] = __int_as_float(e[r].y) * vb[gi];
+#endif
     }
     int fk[PFR];  // fk[r]: the slot whose run ends just before entry r (PADSEG: none)
     float fv[PFR];
@@ -379,16 +380,16 @@ __device__ __forceinline__ void lane_chunk(const int2 (&e)[PFR], const float* vb
 
 // All entries of a warp's range [s0, s1) of one block: the PFR prefetched rounds, then any further
 // ones (a range longer than PFR rounds), then the lane's last open run.
-template <int PFR, int RB, bool PS>
+template <int PFR, int RB>
 __device__ __forceinline__ void run_block(const int2 (&e)[PFR], int s0, int s1, const int2* __restrict__ ent,
                                           const float* vb, float* acc, int lane, int nent, int nacc, uint64_t pol) {
     int cur = PADSEG;
     float sum = 0.f;
-    lane_chunk<PFR, RB, PS>(e, vb, acc, nacc, cur, sum);
+    lane_chunk<PFR, RB>(e, vb, acc, nacc, cur, sum);
     for (int b0 = s0 + PFR * 32; b0 < s1; b0 += PFR * 32) {
         int2 t[PFR];
-        load_rounds<PFR, PS>(ent, b0, s1, lane, t, nent, nacc - 1, pol);
-        lane_chunk<PFR, RB, PS>(t, vb, acc, nacc, cur, sum);
+        load_rounds<PFR>(ent, b0, s1, lane, t, nent, pol);
+        lane_chunk<PFR, RB>(t, vb, acc, nacc, cur, sum);
     }
     if (cur != PADSEG) acc[cur] += sum;
 }
@@ -414,18 +415,18 @@ __device__ __forceinline__ void prefetch_entries(const StagedArgs& g, const int*
 // Consumer side of block b (the CTA's block u): load the warp's entries of block b + 1 into D (the
 // producer has prefetched them into L2), wait for the stage, add the entries held in C, and
 // release the stage.
-template <int RB, int PFR, int S, bool PS>
+template <int RB, int PFR, int S>
 __device__ __forceinline__ void block_step(int b, int be, uint32_t u, int2 (&C)[PFR], int2 (&D)[PFR], const int* spl,
                                            const StagedArgs& g, const float* vb, float* acc, uint64_t* full,
                                            uint64_t* empty, bool& bad, int warp, int lane, uint64_t pol) {
     if (b + 1 < be) {
         const int* sp = spl + (b + 1) * (NW + 1) + warp;
-        load_rounds<PFR, PS>(g.ent, sp[0], sp[1], lane, D, g.nent, g.maxg_pad - 1, pol);
+        load_rounds<PFR>(g.ent, sp[0], sp[1], lane, D, g.nent, pol);
     }
     const uint32_t k = u % S;
     if (!wait_block(full + k, (u / S) & 1u, g.spin)) bad = true;
     const int* sp = spl + b * (NW + 1) + warp;
-    run_block<PFR, RB, PS>(C, sp[0], sp[1], g.ent, vb + k * RB, acc, lane, g.nent, g.maxg_pad, pol);
+    run_block<PFR, RB>(C, sp[0], sp[1], g.ent, vb + k * RB, acc, lane, g.nent, g.maxg_pad, pol);
     __syncwarp();
     if (lane == 0) mbar_arrive(empty + k);
 }
@@ -526,7 +527,7 @@ template <int MODE, int RB, int PFR, int S, bool SOC>
 __global__ void __launch_bounds__(NTHREADS, 1) k_staged(const StagedArgs g, const SweepArgs<float> a) {
     extern __shared__ __align__(128) unsigned char smem[];
     float* vb = reinterpret_cast<float*>(smem);
-    float* acc = vb + S * RB;
+    float* acc = vb + S * RB + 4;  // acc[-1]: the spare sum of the padding positions
     const int R = g.R;
     int* spl = reinterpret_cast<int*>(acc + g.maxg_pad);
     uint64_t* full = reinterpret_cast<uint64_t*>(spl + (R * (NW + 1) + 3) / 4 * 4);
@@ -573,16 +574,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_staged(const StagedArgs g, cons
             const uint64_t pol = policy_evict_first();
             int2 A[PFR], B[PFR];
             if (bb < be)
-                load_rounds<PFR, MODE == 1>(g.ent, spl[bb * (NW + 1) + warp], spl[bb * (NW + 1) + warp + 1], lane, A,
-                                            g.nent,
-                                 g.maxg_pad - 1, pol);
+                load_rounds<PFR>(g.ent, spl[bb * (NW + 1) + warp], spl[bb * (NW + 1) + warp + 1], lane, A, g.nent, pol);
             dep_wait_prev();  // the epilogue reads and writes the iterate
             for (int b = bb; b < be; b += 2) {
                 const uint32_t u = u0 + (b - bb);
-                block_step<RB, PFR, S, MODE == 1>(b, be, u, A, B, spl, g, vb, acc, full, empty, bad, warp, lane, pol);
+                block_step<RB, PFR, S>(b, be, u, A, B, spl, g, vb, acc, full, empty, bad, warp, lane, pol);
                 if (b + 1 < be)
-                    block_step<RB, PFR, S, MODE == 1>(b + 1, be, u + 1, B, A, spl, g, vb, acc, full, empty, bad, warp,
-                                                      lane, pol);
+                    block_step<RB, PFR, S>(b + 1, be, u + 1, B, A, spl, g, vb, acc, full, empty, bad, warp, lane, pol);
             }
             __syncwarp();
             // pieces of long runs: each segment's overflow sums added to it in slot order

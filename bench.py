@@ -276,12 +276,26 @@ def batch_workload(stream, seed, iters=100, tts_iters=300_000, extend_iters=1_00
         more = left & (sts2 == 0)
         tot = (its + its2)[more]
         kkt2 = np.array([r["kkt"] for r in bt2.residuals()])
+        # the instances still above tol, one by one: their KKT decay over the extra iterations
+        # (log-linear rate) and the iterations that rate would still need to reach tol
+        still = left & (sts2 != 0)
+        rate = np.log(kkt[still] / kkt2[still]) / float(extend_iters)
+        need = np.where(rate > 0, np.log(np.maximum(kkt2[still], 1e-6) / 1e-6) / np.where(rate > 0, rate, 1.0), np.inf)
+        per = [{"m": int(ms_[t]), "kkt_at_cap": float(kkt[t]), "kkt_now": float(kkt2[t]),
+                "more_iterations_at_rate": (float(f"{v:.3g}") if np.isfinite(v) else None)}
+               for t, v in zip(np.flatnonzero(still), need)]
         ext = {"extra_max_iter": extend_iters, "seconds": round(time.perf_counter() - t1, 3),
                "converged": int(more.sum()), "of": int(left.sum()),
                "converged_total": int(ok.size + more.sum()),
                "total_iterations_median": float(np.median(tot)) if tot.size else None,
                "total_iterations_max": int(tot.max()) if tot.size else None,
-               "still_above_tol_kkt_max": float(kkt2[left & (sts2 != 0)].max()) if (left & (sts2 != 0)).any() else None}
+               "still_above_tol_kkt_max": float(kkt2[still].max()) if still.any() else None,
+               "still_above_tol": {"count": int(still.sum()),
+                                   "m_median": float(np.median(ms_[still])) if still.any() else None,
+                                   "decreasing": int((rate > 0).sum()),
+                                   "more_iterations_median": (float(np.median(need)) if still.any() and
+                                                              np.isfinite(np.median(need)) else None),
+                                   "instances": per}}
     bt2.close()
     tts = {"tol": 1e-6, "max_iter": tts_iters, "seconds": round(tts_s, 3), "converged": int(ok.size),
            "instances_per_s": round(ok.size / tts_s, 1),

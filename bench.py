@@ -59,6 +59,9 @@ def parse():
                          "in the full experiment)")
     ap.add_argument("--section", default="all", choices=["all", "small", "socp", "paper", "batch", "shared", "mlp", "ruiz"],
                     help="run only one extra workload and print its line (for profiling)")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="large LP with m and n scaled by this factor (a smaller case for profiler captures; "
+                         "the bench line is quoted at 1.0)")
     ap.add_argument("--tts-iters", type=int, default=300000,
                     help="also solve to 1e-6 KKT from the cold start with at most this many iterations (0: skip)")
     return ap.parse_args()
@@ -69,9 +72,11 @@ def dist_env():
     return replicas.env()
 
 
-def make_problem(name, seed):
+def make_problem(name, seed, scale=1.0):
     from paper_2203_05027_b300 import instances as I
     if name == "large_lp":
+        if scale != 1.0:
+            return I.large_lp(seed, m=int(1_000_000 * scale), n=int(2_500_000 * scale))
         return I.large_lp(seed)
     return I.socp(seed)
 
@@ -571,7 +576,7 @@ def main():
         return
 
     # replicas only: each rank solves its own instance (seeded by rank), no data-path collective
-    prob = make_problem(args.workload, rank)
+    prob = make_problem(args.workload, rank, args.scale)
     stream = torch.cuda.current_stream()
     s = mfs.Solver(prob, precision="fp32", polish_iters=0, check_every=ITERS_PER_STEP,
                    stream=stream.cuda_stream, sweep=args.sweep, l2_keep=bool(args.l2_keep))

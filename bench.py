@@ -163,14 +163,18 @@ def kernel_source_hashes(names):
     return out
 
 
-def recorded_traffic(kernel):
+def recorded_traffic(kernel, m, n, o):
     """DRAM bytes of one launch of `kernel` from the committed ncu record, or None when there is
-    none or one of the sources it was captured from has changed since."""
+    none, it was taken on another instance (m, n, o), or one of the sources it was captured from
+    has changed since."""
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(tpath):
         return None
     with open(tpath) as f:
-        rec = json.load(f).get("kernels", {}).get(kernel)
+        doc = json.load(f)
+    if not doc.get("workload", "").startswith(f"large_lp m={m} n={n} o={o} "):
+        return None
+    rec = doc.get("kernels", {}).get(kernel)
     if not rec or rec.get("sources") != kernel_source_hashes(sorted(rec.get("sources", {}))):
         return None
     return rec["dram_bytes"]
@@ -204,7 +208,7 @@ def kernel_roofline(s, info, peak, peak_kind, m, n, o, sm_mhz, num_sms=148):
     dom = max(kernels, key=lambda k: k["ms"])
     achieved = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
     it_gbs = info["bytes_per_iter"] / (t["iter_ms"] * 1e-3) / 1e9
-    traffic = recorded_traffic(dom["kernel"])
+    traffic = recorded_traffic(dom["kernel"], m, n, o)
     clock_hz = (sm_mhz or 2032.0) * 1e6
     floor_ms = o / (num_sms * clock_hz) * 1e3
     col_ms = kernels[0]["ms"] + kernels[1]["ms"]

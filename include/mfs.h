@@ -532,9 +532,11 @@ mfs_status mfs_gemm_bf16(int64_t M, int64_t N, int64_t K, const void* A, const v
 mfs_status mfs_debug_fail_alloc_after(int64_t n);
 
 /* Diagnostic of the bounded waits: runs the tensor-core GEMM on a 128 x 128 x 64 problem with its
-   loads switched off and a short poll limit, so that the MMA issuer's first wait runs out. The
-   kernel records the time-out and returns normally (no trap, no hang; its tensor memory is freed);
-   the call returns MFS_ERR_TIMEOUT when that path works, and the context stays usable.
+   loads switched off and a short poll limit, so that the MMA issuer's first wait runs out, first in
+   the one-tile kernel, then in the persistent kernel of the fused epilogues (the loss epilogue,
+   whose epilogue warps' waits run out as well). Each kernel records the time-out and returns
+   normally (no trap, no hang; its tensor memory is freed); the call returns MFS_ERR_TIMEOUT when
+   both do, and the context stays usable.
    Allocates and frees its own small buffers; synchronous on cuda_stream (NULL = legacy stream). */
 mfs_status mfs_gemm_bf16_wait_test(void* cuda_stream);
 

@@ -173,6 +173,113 @@ __device__ __forceinline__ void gemm_prefetch_l2(const void* p, size_t bytes) {
     if (e > s) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"((uint32_t)(e - s)) : "memory");
 }
 
+// The epilogue of one 32-column block of the accumulator tile (columns n0 + c0 .. + 31, rows rbase ..
+// rbase + 31), by one warp whose staging block stg (32 x 33 floats) holds it with lane = row:
+// bias, ReLU and the store (EPI_STORE; FP32 partials with part), or the loss or the Adam update
+// (lane = column, rows in turn) followed by the transposed BF16 store (lane = row).
+template <int EPI>
+__device__ __forceinline__ void epi_block(const GemmArgs& g, float* stg, int lane, int rbase, int n0, int c0, bool part,
+                                          double& lsum) {
+    const int col = n0 + c0 + lane;
+    const int rows = min(32, g.M - rbase);
+    if (EPI == EPI_STORE) {
+        if (col < g.N) {
+            const float bv = (!part && g.bias) ? g.bias[col] : 0.f;
+            for (int r = 0; r < rows; ++r) {
+                const size_t row = (size_t)(rbase + r);
+                float w = stg[r * 33 + lane];
+                if (part) {
+                    reinterpret_cast<float*>(g.C)[((size_t)blockIdx.z * g.M + row) * g.ldc + col] = w;
+                } else {
+                    w += bv;
+                    if (g.relu) w = w > 0.f ? w : 0.f;
+                    if (g.out_fp32)
+                        reinterpret_cast<float*>(g.C)[row * g.ldc + col] = w;
+                    else
+                        reinterpret_cast<__nv_bfloat16*>(g.C)[row * g.ldc + col] = __float2bfloat16_rn(w);
+                }
+            }
+        }
+    } else {
+        // EPI_LOSS / EPI_ADAM: lane = column, rows in turn; the BF16 result goes back to the
+        // staging block for the transposed store below
+        if (col < g.N) {
+            // eight rows at a time: their loads are issued together, then used
+            if (EPI == EPI_LOSS) {
+                const bool real = col < g.dout;
+                const float bv = g.bias ? g.bias[col] : 0.f;
+                const float mc = real ? g.mean[col] : 0.f, sc = real ? g.stdv[col] : 1.f;
+                // the lane's squares summed in FP32 over its (at most 32) rows, then added into the
+                // FP64 sum once: FP64 runs at 1/64 of the FP32 rate on this GPU
+                float fs = 0.f;
+                for (int r0 = 0; r0 < rows; r0 += 8) {
+                    float tv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        tv[u] = (real && r0 + u < rows) ? g.T[(size_t)(rbase + r0 + u) * g.ldT + col] : 0.f;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int r = r0 + u;
+                        if (r < rows) {
+                            const float y = stg[r * 33 + lane] + bv;
+                            float res = 0.f;
+                            if (real) res = y - (tv[u] - mc) / sc;
+                            fs = fmaf(res, res, fs);
+                            const __nv_bfloat16 d = __float2bfloat16_rn(g.scale * res);
+                            reinterpret_cast<__nv_bfloat16*>(g.C)[(size_t)(rbase + r) * g.ldc + col] = d;
+                            stg[r * 33 + lane] = __bfloat162float(d);
+                        }
+                    }
+                }
+                lsum += (double)fs;
+            } else {
+                // the bias corrections' reciprocals, once (a multiplication instead of a division
+                // per element: the same steps, FP32 rounding of their own)
+                const float rc1 = 1.f / g.c1, rc2 = 1.f / g.c2;
+                for (int r0 = 0; r0 < rows; r0 += 8) {
+                    float wv[8], mv[8], vv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        if (r0 + u < rows) {
+                            const size_t idx = (size_t)(rbase + r0 + u) * g.ldc + col;
+                            wv[u] = g.W[idx];
+                            mv[u] = g.mom[idx];
+                            vv[u] = g.vel[idx];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int r = r0 + u;
+                        if (r < rows) {
+                            const size_t idx = (size_t)(rbase + r) * g.ldc + col;
+                            const float gt = stg[r * 33 + lane];
+                            if (g.gkeep) g.gkeep[idx] = gt;
+                            const float mt = g.b1 * mv[u] + (1.f - g.b1) * gt;
+                            const float vt = g.b2 * vv[u] + (1.f - g.b2) * gt * gt;
+                            g.mom[idx] = mt;
+                            g.vel[idx] = vt;
+                            const float wn = wv[u] - g.lr * (mt * rc1) / (sqrtf(vt * rc2) + g.eps);
+                            g.W[idx] = wn;
+                            const __nv_bfloat16 h = __float2bfloat16_rn(wn);
+                            g.Wh[idx] = h;
+                            stg[r * 33 + lane] = __bfloat162float(h);
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        // transposed store: lane = row, columns in turn
+        const int row = rbase + lane;
+        __nv_bfloat16* dst = EPI == EPI_LOSS ? g.dYt : g.Wt;
+        if (row < g.M)
+            for (int i = 0; i < 32; ++i) {
+                const int cc = n0 + c0 + i;
+                if (cc < g.N) dst[(size_t)cc * g.ldt + row] = __float2bfloat16_rn(stg[lane * 33 + i]);
+            }
+    }
+}
+
 template <int EPI>
 __global__ void __launch_bounds__(NTHREADS, 2)
     k_gemm_bf16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const GemmArgs g) {
@@ -284,97 +391,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
 #pragma unroll
             for (int i = 0; i < 32; ++i) stg[lane * 33 + i] = v[i];
             __syncwarp();
-            const int col = n0 + c0 + lane;
-            const int rows = min(32, g.M - rbase);
-            if (EPI == EPI_STORE) {
-                if (col < g.N) {
-                    const float bv = (!part && g.bias) ? g.bias[col] : 0.f;
-                    for (int r = 0; r < rows; ++r) {
-                        const size_t row = (size_t)(rbase + r);
-                        float w = stg[r * 33 + lane];
-                        if (part) {
-                            reinterpret_cast<float*>(g.C)[((size_t)blockIdx.z * g.M + row) * g.ldc + col] = w;
-                        } else {
-                            w += bv;
-                            if (g.relu) w = w > 0.f ? w : 0.f;
-                            if (g.out_fp32)
-                                reinterpret_cast<float*>(g.C)[row * g.ldc + col] = w;
-                            else
-                                reinterpret_cast<__nv_bfloat16*>(g.C)[row * g.ldc + col] = __float2bfloat16_rn(w);
-                        }
-                    }
-                }
-            } else {
-                // EPI_LOSS / EPI_ADAM: lane = column, rows in turn; the BF16 result goes back to the
-                // staging block for the transposed store below
-                if (col < g.N) {
-                    // eight rows at a time: their loads are issued together, then used
-                    if (EPI == EPI_LOSS) {
-                        const bool real = col < g.dout;
-                        const float bv = g.bias ? g.bias[col] : 0.f;
-                        const float mc = real ? g.mean[col] : 0.f, sc = real ? g.stdv[col] : 1.f;
-                        for (int r0 = 0; r0 < rows; r0 += 8) {
-                            float tv[8];
-#pragma unroll
-                            for (int u = 0; u < 8; ++u)
-                                tv[u] = (real && r0 + u < rows) ? g.T[(size_t)(rbase + r0 + u) * g.ldT + col] : 0.f;
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                const int r = r0 + u;
-                                if (r < rows) {
-                                    const float y = stg[r * 33 + lane] + bv;
-                                    float res = 0.f;
-                                    if (real) res = y - (tv[u] - mc) / sc;
-                                    lsum += (double)res * (double)res;
-                                    const __nv_bfloat16 d = __float2bfloat16_rn(g.scale * res);
-                                    reinterpret_cast<__nv_bfloat16*>(g.C)[(size_t)(rbase + r) * g.ldc + col] = d;
-                                    stg[r * 33 + lane] = __bfloat162float(d);
-                                }
-                            }
-                        }
-                    } else {
-                        for (int r0 = 0; r0 < rows; r0 += 8) {
-                            float wv[8], mv[8], vv[8];
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                if (r0 + u < rows) {
-                                    const size_t idx = (size_t)(rbase + r0 + u) * g.ldc + col;
-                                    wv[u] = g.W[idx];
-                                    mv[u] = g.mom[idx];
-                                    vv[u] = g.vel[idx];
-                                }
-                            }
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                const int r = r0 + u;
-                                if (r < rows) {
-                                    const size_t idx = (size_t)(rbase + r) * g.ldc + col;
-                                    const float gt = stg[r * 33 + lane];
-                                    if (g.gkeep) g.gkeep[idx] = gt;
-                                    const float mt = g.b1 * mv[u] + (1.f - g.b1) * gt;
-                                    const float vt = g.b2 * vv[u] + (1.f - g.b2) * gt * gt;
-                                    g.mom[idx] = mt;
-                                    g.vel[idx] = vt;
-                                    const float wn = wv[u] - g.lr * (mt / g.c1) / (sqrtf(vt / g.c2) + g.eps);
-                                    g.W[idx] = wn;
-                                    const __nv_bfloat16 h = __float2bfloat16_rn(wn);
-                                    g.Wh[idx] = h;
-                                    stg[r * 33 + lane] = __bfloat162float(h);
-                                }
-                            }
-                        }
-                    }
-                }
-                __syncwarp();
-                // transposed store: lane = row, columns in turn
-                const int row = rbase + lane;
-                __nv_bfloat16* dst = EPI == EPI_LOSS ? g.dYt : g.Wt;
-                if (row < g.M)
-                    for (int i = 0; i < 32; ++i) {
-                        const int cc = n0 + c0 + i;
-                        if (cc < g.N) dst[(size_t)cc * g.ldt + row] = __float2bfloat16_rn(stg[lane * 33 + i]);
-                    }
-            }
+            epi_block<EPI>(g, stg, lane, rbase, n0, c0, part, lsum);
             __syncwarp();
         }
     }
@@ -404,6 +421,274 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Persistent form for the fused epilogues (EPI_LOSS, EPI_ADAM; no split-K). One CTA per SM loops
+// over the 128 x 128 tiles in the one-tile kernel's order (tile t = blockIdx.y * gridDim.x +
+// blockIdx.x of its grid), so that a tile's epilogue overlaps the loads and MMAs of the next:
+//   warp 0, one lane: TMA producer, a PSTAGES-deep ring of stages that runs on across tiles;
+//   warp 1, one lane: MMA issuer, tile j into accumulator j % 2 (two 128-column accumulators in
+//                     tensor memory), after the epilogue has read that accumulator's tile j - 2;
+//   warps 2 .. 2 + PEW - 1: the epilogue, each warp 32 rows (its TMEM lane quadrant) and
+//                     128 / (PEW / 4) columns of the tile, through its own staging block.
+// Barriers: full/empty per stage (as in k_gemm_bf16), tfull[a] (commit after the tile's last MMA),
+// tempty[a] (one arrival per epilogue warp once its tcgen05.ld of the tile have completed). The
+// loss's per-tile sum of squares is added in the one-tile kernel's warp order. Every wait is
+// bounded; one that runs out sets the error word and every role leaves its loop; the CTA then
+// waits for its MMAs and copies in flight before it frees tensor memory.
+#ifndef MFS_GEMM_PEW
+#define MFS_GEMM_PEW 16
+#endif
+constexpr int PSTAGES = 4;
+constexpr int PEW = MFS_GEMM_PEW;             // epilogue warps: 8 or 16
+constexpr int PCOLS = BN / (PEW / 4);         // accumulator columns per epilogue warp
+constexpr int PTHREADS = 32 * (2 + PEW);
+constexpr int PSTG_BYTES = PEW * 32 * 33 * 4;  // the epilogue warps' staging blocks
+constexpr int PSMEM_BYTES = PSTAGES * STAGE_BYTES + PSTG_BYTES + 1024 /* alignment */ + 512 /* barriers */;
+static_assert(PEW == 8 || PEW == 16, "epilogue warps");
+
+__device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// L2 prefetch of the epilogue's FP32 inputs for rows [r0, r0 + 32) x columns [c0, c0 + PCOLS) of a tile
+template <int EPI>
+__device__ __forceinline__ void prefetch_epi_rows(const GemmArgs& g, int row, int c0) {
+    if (row >= g.M) return;
+    if (EPI == EPI_LOSS) {
+        const int c1 = min(c0 + PCOLS, g.dout);
+        if (c1 > c0) gemm_prefetch_l2(g.T + (size_t)row * g.ldT + c0, (size_t)(c1 - c0) * sizeof(float));
+    } else {
+        const int c1 = min(c0 + PCOLS, g.N);
+        if (c1 > c0) {
+            const size_t off = (size_t)row * g.ldc + c0, bytes = (size_t)(c1 - c0) * sizeof(float);
+            gemm_prefetch_l2(g.W + off, bytes);
+            gemm_prefetch_l2(g.mom + off, bytes);
+            gemm_prefetch_l2(g.vel + off, bytes);
+        }
+    }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(PTHREADS, 1)
+    k_gemm_bf16_pers(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                     const GemmArgs g) {
+    extern __shared__ __align__(1024) unsigned char gsm_raw[];
+    unsigned char* gsm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
+    float* stg_all = reinterpret_cast<float*>(gsm + PSTAGES * STAGE_BYTES);
+    uint64_t* full = reinterpret_cast<uint64_t*>(gsm + PSTAGES * STAGE_BYTES + PSTG_BYTES);
+    uint64_t* empty = full + PSTAGES;
+    uint64_t* tfull = empty + PSTAGES;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* dbar = tempty + 2;
+    uint64_t* rfull = dbar + 1;  // EPI_LOSS: red[b] holds every epilogue warp's sum (b = tile % 2)
+    uint64_t* rfree = rfull + 2;  //           red[b] has been added up and may take the next tile's
+    double* red = reinterpret_cast<double*>(rfree + 2);  // 2 x PEW
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(red + 2 * PEW);
+    int* s_fail = reinterpret_cast<int*>(s_tmem + 1);
+    volatile int* vfail = s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = (g.M + BM - 1) / BM, nt = (g.N + BN - 1) / BN, T = mt * nt;
+    const int nkb = (g.K + BK - 1) / BK;
+    auto tile_of = [&](int t, int& m0, int& n0) {
+        if (g.m_fast) {
+            m0 = (t % mt) * BM;
+            n0 = (t / mt) * BN;
+        } else {
+            m0 = (t / nt) * BM;
+            n0 = (t % nt) * BN;
+        }
+    };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PSTAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], PEW);
+        }
+        mbar_init(dbar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&rfull[b], PEW);
+            mbar_init(&rfree[b], 1);
+        }
+        *s_fail = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {  // two 128 x 128 FP32 accumulators (256 columns)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_tmem)),
+                     "r"(2 * BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+
+    int issued = 0;   // producer: loads issued
+    bool mmas = false;  // MMA issuer: any MMA issued
+    if (warp == 0) {
+        if (lane == 0 && !g.no_loads) {
+            int it = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < T && !stop; t += gridDim.x) {
+                int m0, n0;
+                tile_of(t, m0, n0);
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % PSTAGES;
+                    if (*vfail || !wait_phase(&empty[s], ((it / PSTAGES) & 1) ^ 1, g.spin)) {
+                        atomicExch(s_fail, 1);
+                        stop = true;
+                        break;
+                    }
+                    unsigned char* st = gsm + s * STAGE_BYTES;
+                    mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                    tma_load_2d(st, &mapA, kb * BK, m0, &full[s]);
+                    tma_load_2d(st + TILE_A, &mapB, kb * BK, n0, &full[s]);
+                    issued = it + 1;
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(BM, BN);
+            int it = 0, j = 0;
+            for (int t = blockIdx.x; t < T; t += gridDim.x, ++j) {
+                const int a = j & 1;
+                if (*vfail || !wait_phase(&tempty[a], ((j >> 1) & 1) ^ 1, g.spin)) {
+                    atomicExch(s_fail, 1);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)(a * BN);
+                bool stop = false;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % PSTAGES;
+                    if (!wait_phase(&full[s], (it / PSTAGES) & 1, g.spin)) {
+                        atomicExch(s_fail, 1);
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    unsigned char* st = gsm + s * STAGE_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / UK; ++kk) {
+                        const uint64_t ad = smem_desc(st + kk * UK * 2);
+                        const uint64_t bd = smem_desc(st + TILE_A + kk * UK * 2);
+                        mma_bf16(acc, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    mmas = true;
+                    mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+                }
+                if (stop) break;
+                mma_commit(&tfull[a]);  // the tile's accumulator is complete once its MMAs are
+            }
+        }
+        __syncwarp();
+    } else {
+        const int ew = warp - 2;
+        const int quad = warp & 3, part4 = ew >> 2;  // TMEM lane quadrant (rows) and column part
+        const int cbase = part4 * PCOLS;
+        float* stg = stg_all + ew * (32 * 33);
+        int j = 0;
+        {
+            int m0, n0;
+            if (blockIdx.x < T) {
+                tile_of(blockIdx.x, m0, n0);
+                prefetch_epi_rows<EPI>(g, m0 + quad * 32 + lane, n0 + cbase);
+            }
+        }
+        for (int t = blockIdx.x; t < T; t += gridDim.x, ++j) {
+            int m0, n0;
+            tile_of(t, m0, n0);
+            const int a = j & 1;
+            // a warp-uniform decision: the tensor-memory loads below need every lane
+            const int okw = __all_sync(0xffffffffu, !*vfail && wait_phase(&tfull[a], (j >> 1) & 1, g.spin));
+            if (!okw) {
+                if (lane == 0) atomicExch(s_fail, 1);
+                break;
+            }
+            tc_fence_after();
+            if (t + (int)gridDim.x < T) {  // the next tile's epilogue inputs into L2
+                int m1, n1;
+                tile_of(t + gridDim.x, m1, n1);
+                prefetch_epi_rows<EPI>(g, m1 + quad * 32 + lane, n1 + cbase);
+            }
+            float v[PCOLS];
+            const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * BN + cbase);
+#pragma unroll
+            for (int c = 0; c < PCOLS; c += 32) {
+                float w[32];
+                tmem_ld32(ta + (uint32_t)c, w);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[c + i] = w[i];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive1(&tempty[a]);  // the accumulator may take tile j + 2
+            const int rbase = m0 + quad * 32;
+            double lsum = 0.0;
+#pragma unroll
+            for (int c = 0; c < PCOLS; c += 32) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) stg[lane * 33 + i] = v[c + i];
+                __syncwarp();
+                epi_block<EPI>(g, stg, lane, rbase, n0, cbase + c, false, lsum);
+                __syncwarp();
+            }
+            if (EPI == EPI_LOSS) {
+                // the tile's sum of squares: every warp's share into red[b] (once the tile two back
+                // has been added up), then warp 2 adds them in the one-tile kernel's order (column
+                // half, lane quadrant) and writes part[t]; bounded waits on mbarriers only
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
+                const int b = j & 1;
+                if (lane == 0) {
+                    if (!wait_phase(&rfree[b], ((j >> 1) & 1) ^ 1, g.spin)) atomicExch(s_fail, 1);
+                    red[b * PEW + quad * (PEW / 4) + part4] = lsum;
+                    mbar_arrive1(&rfull[b]);
+                    if (ew == 0) {
+                        if (wait_phase(&rfull[b], (j >> 1) & 1, g.spin)) {
+                            double tsum = 0.0;
+                            for (int h = 0; h < 2; ++h)
+                                for (int q = 0; q < 4; ++q)
+                                    for (int pp = h * (PEW / 8); pp < (h + 1) * (PEW / 8); ++pp)
+                                        tsum += red[b * PEW + q * (PEW / 4) + pp];
+                            g.part[t] = tsum;
+                        } else {
+                            atomicExch(s_fail, 1);
+                        }
+                        mbar_arrive1(&rfree[b]);
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    }
+    // the MMAs issued (all complete once this commit arrives) before tensor memory is freed
+    if (warp == 1 && lane == 0 && mmas) {
+        mma_commit(dbar);
+        wait_phase(dbar, 0);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*s_fail) {
+        // copies still in flight (only the last PSTAGES issued can be)
+        if (warp == 0 && lane == 0)
+            for (int i = max(0, issued - PSTAGES); i < issued; ++i) wait_phase(&full[i % PSTAGES], (i / PSTAGES) & 1);
+        if (threadIdx.x == 0) atomicCAS(g.err, 0, ERR_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
 }
 
 }  // namespace gemm

@@ -86,6 +86,31 @@ bool gemm_attr() {
     return done;
 }
 
+// Fused epilogues in the persistent GEMM (one CTA per SM, two accumulators in tensor memory, each
+// tile's epilogue overlapping the next tile's loads and MMAs): 0 none, 1 the loss, 2 the loss and Adam.
+#ifndef MFS_GEMM_PERSISTENT
+#define MFS_GEMM_PERSISTENT 1
+#endif
+template <int EPI>
+bool gemm_pers_attr() {
+    static bool done = false;
+    if (!done)
+        done = cudaFuncSetAttribute(k_gemm_bf16_pers<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    PSMEM_BYTES) == cudaSuccess;
+    return done;
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 148;
+    }
+    return n;
+}
+
 // epi != EPI_STORE: the fused epilogue's fields are taken from *fused (splits must be 1).
 mfs_status gemm(int M, int N, int K, const bf16* A, const bf16* B, const float* bias, int relu, int out_fp32, void* C,
                 int splits, float* work, int* err, cudaStream_t st, std::string* why, uint32_t spin = SPIN,
@@ -133,7 +158,17 @@ mfs_status gemm(int M, int N, int K, const bf16* A, const bf16* B, const float* 
     g.m_fast = (long long)N > (long long)M ? 1 : 0;
     const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
     dim3 grid(g.m_fast ? mt : nt, g.m_fast ? nt : mt, splits);
-    if (epi == EPI_LOSS)
+    if ((MFS_GEMM_PERSISTENT >= 1 && epi == EPI_LOSS) || (MFS_GEMM_PERSISTENT >= 2 && epi == EPI_ADAM)) {
+        if (!gemm_pers_attr<EPI_LOSS>() || !gemm_pers_attr<EPI_ADAM>()) {
+            if (why) *why = "gemm: shared memory attribute";
+            return MFS_ERR_CUDA;
+        }
+        const int pgrid = std::max(1, std::min(mt * nt, sm_count()));
+        if (epi == EPI_LOSS)
+            k_gemm_bf16_pers<EPI_LOSS><<<pgrid, PTHREADS, PSMEM_BYTES, st>>>(ma, mb, g);
+        else
+            k_gemm_bf16_pers<EPI_ADAM><<<pgrid, PTHREADS, PSMEM_BYTES, st>>>(ma, mb, g);
+    } else if (epi == EPI_LOSS)
         k_gemm_bf16<EPI_LOSS><<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, g);
     else if (epi == EPI_ADAM)
         k_gemm_bf16<EPI_ADAM><<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, g);
@@ -867,16 +902,47 @@ mfs_status mfs_gemm_bf16_wait_test(void* cuda_stream) {
         cudaMemsetAsync(A, 0, M * K * 2, st) == cudaSuccess && cudaMemsetAsync(B, 0, N * K * 2, st) == cudaSuccess &&
         cudaMemsetAsync(err, 0, sizeof(int), st) == cudaSuccess) {
         std::string why;
-        out = gemm(M, N, K, static_cast<bf16*>(A), static_cast<bf16*>(B), nullptr, 0, 1, C, 1, nullptr, err, st, &why,
-                   1024u, 1);
-        int h = 0;
-        if (out == MFS_OK) {
+        // the one-tile kernel, then the persistent one (the loss epilogue) with no loads issued:
+        // both must report the timeout
+        auto result = [&](mfs_status launched) -> mfs_status {
+            int h = 0;
+            if (launched != MFS_OK) return launched;
             if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess)
-                out = MFS_ERR_CUDA;
-            else
-                out = h == ERR_TIMEOUT ? MFS_ERR_TIMEOUT : (h ? MFS_ERR_CUDA : MFS_OK);
+                cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+                return MFS_ERR_CUDA;
+            return h == ERR_TIMEOUT ? MFS_ERR_TIMEOUT : (h ? MFS_ERR_CUDA : MFS_OK);
+        };
+        out = result(gemm(M, N, K, static_cast<bf16*>(A), static_cast<bf16*>(B), nullptr, 0, 1, C, 1, nullptr, err, st,
+                          &why, 1024u, 1));
+        float *T = nullptr, *mv = nullptr;
+        void* dYt = nullptr;
+        double* part = nullptr;
+        if (out == MFS_ERR_TIMEOUT) {
+            out = MFS_ERR_CUDA;
+            if (cudaMalloc(reinterpret_cast<void**>(&T), M * N * 4) == cudaSuccess &&
+                cudaMalloc(reinterpret_cast<void**>(&mv), 2 * N * 4) == cudaSuccess &&
+                cudaMalloc(&dYt, M * N * 2) == cudaSuccess &&
+                cudaMalloc(reinterpret_cast<void**>(&part), 64 * sizeof(double)) == cudaSuccess &&
+                cudaMemsetAsync(T, 0, M * N * 4, st) == cudaSuccess && cudaMemsetAsync(mv, 0, 2 * N * 4, st) == cudaSuccess) {
+                GemmArgs fa{};
+                fa.T = T;
+                fa.ldT = N;
+                fa.dout = N;
+                fa.mean = mv;
+                fa.stdv = mv + N;
+                fa.scale = 1.f;
+                fa.dYt = static_cast<bf16*>(dYt);
+                fa.ldt = M;
+                fa.part = part;
+                out = result(gemm(M, N, K, static_cast<bf16*>(A), static_cast<bf16*>(B), nullptr, 0, 0, C, 1, nullptr, err,
+                                  st, &why, 1024u, 1, EPI_LOSS, &fa));
+            }
         }
+        cudaStreamSynchronize(st);
+        cudaFree(T);
+        cudaFree(mv);
+        cudaFree(dYt);
+        cudaFree(part);
     }
     cudaStreamSynchronize(st);
     cudaFree(A);

@@ -380,11 +380,11 @@ mfs_status mfs_batch_get_solution(mfs_batch* bt, int64_t t, double* x, double* l
 mfs_status mfs_batch_set_tuning(mfs_batch* bt, const mfs_batch_tuning* tuning);
 mfs_status mfs_batch_get_tuning(const mfs_batch* bt, mfs_batch_tuning* tuning);
 /* Autotuner: times `iters` iterations of the whole batch for each candidate (threads per CTA x CTAs
-   per SM) and keeps the fastest; then, with that launch shape, times `iters` iterations with the
-   in-launch residual checks every 10, 25, 50, 100 or 200 iterations and keeps the smallest interval
-   whose checks cost at most 5 % more than every 200 (a finer interval stops each instance closer to
-   its first iteration at the tolerance). Returns the choice in chosen (nullable). The iterate
-   advances. */
+   per SM) and keeps the fastest; then, with that launch shape, times max(iters, 400) iterations with
+   the in-launch residual checks every 10, 25, 50, 100 or 200 iterations and keeps the smallest
+   interval whose checks cost at most 5 % more than every 200 (a finer interval stops each instance
+   closer to its first iteration at the tolerance). Returns the choice in chosen (nullable). The
+   iterate advances. */
 mfs_status mfs_batch_tune(mfs_batch* bt, int64_t iters, mfs_batch_tuning* chosen);
 
 /* ------------------------------------------------------------------------------------------------

@@ -1088,19 +1088,21 @@ mfs_status mfs_batch_tune(mfs_batch* s, int64_t iters, mfs_batch_tuning* chosen)
     }
     // the residual-check interval: the smallest candidate whose in-launch FP64 checks cost at most
     // 5 % more than the sparsest one (no instance can meet the tolerance used here, so every
-    // candidate runs all its iterations with all its checks)
+    // candidate runs all its iterations with all its checks); over at least two of the sparsest
+    // candidate's intervals, so that every candidate's timing holds checks at its own spacing
     {
         const int cands[] = {10, 25, 50, 100, 200};
+        const int64_t citers = std::max<int64_t>(iters, 2 * 200);
         float tc[5];
         for (int q = 0; q < 5; ++q) {
             mfs_batch_tuning t = best;
             t.check_every = cands[q];
             BTRY(mfs_batch_set_tuning(s, &t));
-            BTRY(s->set.precision == MFS_FP64 ? run_batch(s, s->f64, (int)iters, 1e-300)
-                                              : run_batch(s, s->f32, (int)iters, 1e-300));  // capture, warm
+            BTRY(s->set.precision == MFS_FP64 ? run_batch(s, s->f64, (int)citers, 1e-300)
+                                              : run_batch(s, s->f32, (int)citers, 1e-300));  // capture, warm
             cudaEventRecord(ev.e0, s->stream);
-            BTRY(s->set.precision == MFS_FP64 ? run_batch(s, s->f64, (int)iters, 1e-300)
-                                              : run_batch(s, s->f32, (int)iters, 1e-300));
+            BTRY(s->set.precision == MFS_FP64 ? run_batch(s, s->f64, (int)citers, 1e-300)
+                                              : run_batch(s, s->f32, (int)citers, 1e-300));
             cudaEventRecord(ev.e1, s->stream);
             BCUDA(s, cudaEventSynchronize(ev.e1));
             cudaEventElapsedTime(&tc[q], ev.e0, ev.e1);

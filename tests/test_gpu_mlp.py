@@ -107,11 +107,13 @@ def test_mlp_training_reduces_the_loss():
     assert last < 0.2 * first, (first, last)
 
 
-@pytest.mark.parametrize("din,width,dout,B", [(32, 128, 300, 64), (32, 512, 1000, 256)])
+@pytest.mark.parametrize("din,width,dout,B", [(32, 128, 300, 64), (32, 512, 1000, 256), (32, 128, 40, 256)])
 def test_fused_train_step_equals_backward_then_adam(din, width, dout, B):
     """train_step computes the output layer inside the GEMM epilogues (loss gradient in the forward
     GEMM, Adam in the weight-gradient GEMM); it must give the same parameters and losses as the
-    separate mfs_mlp_backward + mfs_mlp_adam_step path, step after step."""
+    separate mfs_mlp_backward + mfs_mlp_adam_step path, step after step. In the last case the batch
+    has more rows than the output has columns, so the loss GEMM walks its tiles row tile by row
+    tile (two row tiles, one column tile)."""
     rng = np.random.default_rng(11)
     X = rng.standard_normal((B, din)).astype(np.float32)
     T = (rng.standard_normal((B, dout)) * 3 + 1).astype(np.float32)

@@ -18,6 +18,7 @@
 #include <cstdint>
 #include <numeric>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/mfs.h"
@@ -88,6 +89,7 @@ struct AccT<double> {
 };
 __device__ __forceinline__ DF acc_mul(float a, float b) { return mfs::df_prod(a, b); }
 __device__ __forceinline__ double acc_mul(double a, double b) { return a * b; }
+
 
 template <typename T>
 __device__ __forceinline__ T lorentz_coord(T w, int t, T w1, T alpha) {
@@ -171,6 +173,39 @@ __device__ __forceinline__ void block_fold(double (&f)[NF], unsigned maxmask, do
     }
 }
 
+// Block-wide fold of NF double-float pairs in FP32 arithmetic (fields flagged in maxmask are maxima);
+// result in thread 0. A warp-wide FP64 shuffle fold occupies the SM's narrow FP64 pipe for every
+// field and round, which made the FP64 fold half of a residual check's time.
+template <int NF>
+__device__ __forceinline__ void block_fold_df(DF (&F)[NF], unsigned maxmask, DF (*sh)[NF]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        DF v = F[k];
+        for (int d = 16; d > 0; d >>= 1) {
+            const DF o(__shfl_down_sync(FULL, v.hi, d), __shfl_down_sync(FULL, v.lo, d));
+            v = ((maxmask >> k) & 1u) ? mfs::df_max(v, o) : v + o;
+        }
+        F[k] = v;
+    }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NF; ++k) sh[warp][k] = F[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            DF v = lane < nw ? sh[lane][k] : DF(0);
+            for (int d = 16; d > 0; d >>= 1) {
+                const DF o(__shfl_down_sync(FULL, v.hi, d), __shfl_down_sync(FULL, v.lo, d));
+                v = ((maxmask >> k) & 1u) ? mfs::df_max(v, o) : v + o;
+            }
+            F[k] = v;
+        }
+    }
+}
+
 // fields of the residual fold
 enum { RES2, RESMAX, AXMAX, B2, BMAX, BLAM, S2, SMAX, ATLMAX, C2, CMAX, CX, X2, SDIST2, XDIST2, XMAX, SDMAX, XDMAX, NFLD };
 constexpr unsigned MAXMASK = (1u << RESMAX) | (1u << AXMAX) | (1u << BMAX) | (1u << SMAX) | (1u << ATLMAX) | (1u << CMAX) |
@@ -182,19 +217,37 @@ struct Inst {
 };
 
 // FP64 residuals of instance I at (x, lambda) (x read through xs); status block into out[NSTAT]
-// (thread 0) and the relative KKT residual returned to every thread.
+// (thread 0) and the relative KKT residual returned to every thread. For the FP32 iterate the row
+// and column fields are kept, and folded over the block, as double-float pairs (about 48
+// significant bits) and turned into FP64 by thread 0 only (B300 runs FP64 at 1/64 of its FP32
+// rate); the Lorentz cones' terms are formed in FP64 and added as pairs.
 template <typename T, typename IT>
-__device__ double instance_residuals(const BatchArgs<T>& a, const Inst& I, const T* xs, const int* cp, const IT* ci,
+__device__ double instance_residuals(const BatchArgs<T>& a, const Inst& I, const T* xs, const T* lam, const int* cp,
+                                     const IT* ci,
                                      const T* cv, const int* rp, const IT* ri, const T* rv, double* out,
                                      double (*sh)[NFLD], double* s_kkt) {
     using A = typename AccT<T>::type;
+    constexpr bool F32 = std::is_same<T, float>::value;
     double f[NFLD];
 #pragma unroll
     for (int k = 0; k < NFLD; ++k) f[k] = 0.0;
-    const T* lam = a.lam + I.gm;
+    DF F[F32 ? NFLD : 1];
+#pragma unroll
+    for (int k = 0; k < (F32 ? NFLD : 1); ++k) F[k] = DF(0);
     for (int i = threadIdx.x; i < I.m; i += blockDim.x) {
         A acc = A(0);
         for (int k = rp[i]; k < rp[i + 1]; ++k) acc = acc + acc_mul(rv[k], xs[ri[k]]);
+        if constexpr (F32) {
+            const float bi = a.b[I.gm + i];
+            const DF res = acc + DF(-bi, 0.f);
+            F[RES2] = F[RES2] + mfs::df_sq(res);
+            F[RESMAX] = mfs::df_max(F[RESMAX], mfs::df_abs(res));
+            F[AXMAX] = mfs::df_max(F[AXMAX], mfs::df_abs(acc));
+            F[B2] = F[B2] + mfs::df_prod(bi, bi);
+            F[BMAX] = mfs::df_max(F[BMAX], DF(fabsf(bi), 0.f));
+            F[BLAM] = F[BLAM] + mfs::df_prod(bi, lam[i]);
+            continue;
+        }
         const double ax = mfs::to_double(acc), bi = double(a.b[I.gm + i]), res = ax - bi;
         f[RES2] += res * res;
         f[RESMAX] = fmax(f[RESMAX], fabs(res));
@@ -208,6 +261,30 @@ __device__ double instance_residuals(const BatchArgs<T>& a, const Inst& I, const
     auto column = [&](int j, bool orthant, double& s_out) {
         A acc = A(0);
         for (int k = cp[j]; k < cp[j + 1]; ++k) acc = acc + acc_mul(cv[k], lam[ci[k]]);
+        if constexpr (F32) {
+            const float cj = a.c[I.gn + j], xj = xs[j];
+            const DF sd = DF(cj, 0.f) + acc;
+            F[S2] = F[S2] + mfs::df_sq(sd);
+            F[SMAX] = mfs::df_max(F[SMAX], mfs::df_abs(sd));
+            F[ATLMAX] = mfs::df_max(F[ATLMAX], mfs::df_abs(acc));
+            F[C2] = F[C2] + mfs::df_prod(cj, cj);
+            F[CMAX] = mfs::df_max(F[CMAX], DF(fabsf(cj), 0.f));
+            F[CX] = F[CX] + mfs::df_prod(cj, xj);
+            F[X2] = F[X2] + mfs::df_prod(xj, xj);
+            F[XMAX] = mfs::df_max(F[XMAX], DF(fabsf(xj), 0.f));
+            if (orthant) {
+                const DF sn = sd.hi < 0.f ? sd : DF(0);
+                const float xn = xj < 0.f ? xj : 0.f;
+                F[SDIST2] = F[SDIST2] + mfs::df_sq(sn);
+                F[XDIST2] = F[XDIST2] + mfs::df_prod(xn, xn);
+                F[SDMAX] = mfs::df_max(F[SDMAX], mfs::df_neg(sn));
+                F[XDMAX] = mfs::df_max(F[XDMAX], DF(-xn, 0.f));
+                s_out = 0.0;
+            } else {
+                s_out = mfs::to_double(sd);
+            }
+            return;
+        }
         const double atl = mfs::to_double(acc), cj = double(a.c[I.gn + j]), xj = double(xs[j]);
         const double s = cj + atl;
         f[S2] += s * s;
@@ -247,12 +324,26 @@ __device__ double instance_residuals(const BatchArgs<T>& a, const Inst& I, const
                 xx += xj * xj;
             }
         }
-        f[SDIST2] += lorentz_dist2(s1, sqrt(ss), ss + s1 * s1);
-        f[XDIST2] += lorentz_dist2(x1, sqrt(xx), xx + x1 * x1);
-        f[SDMAX] = fmax(f[SDMAX], mfs::lorentz_distinf(s1, sqrt(ss)));
-        f[XDMAX] = fmax(f[XDMAX], mfs::lorentz_distinf(x1, sqrt(xx)));
+        if constexpr (F32) {
+            F[SDIST2] = F[SDIST2] + mfs::df_from(lorentz_dist2(s1, sqrt(ss), ss + s1 * s1));
+            F[XDIST2] = F[XDIST2] + mfs::df_from(lorentz_dist2(x1, sqrt(xx), xx + x1 * x1));
+            F[SDMAX] = mfs::df_max(F[SDMAX], mfs::df_from(mfs::lorentz_distinf(s1, sqrt(ss))));
+            F[XDMAX] = mfs::df_max(F[XDMAX], mfs::df_from(mfs::lorentz_distinf(x1, sqrt(xx))));
+        } else {
+            f[SDIST2] += lorentz_dist2(s1, sqrt(ss), ss + s1 * s1);
+            f[XDIST2] += lorentz_dist2(x1, sqrt(xx), xx + x1 * x1);
+            f[SDMAX] = fmax(f[SDMAX], mfs::lorentz_distinf(s1, sqrt(ss)));
+            f[XDMAX] = fmax(f[XDMAX], mfs::lorentz_distinf(x1, sqrt(xx)));
+        }
     }
-    block_fold<NFLD>(f, MAXMASK, sh);
+    if constexpr (F32) {
+        block_fold_df<NFLD>(F, MAXMASK, reinterpret_cast<DF(*)[NFLD]>(sh));
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < NFLD; ++k) f[k] = mfs::to_double(F[k]);
+    } else {
+        block_fold<NFLD>(f, MAXMASK, sh);
+    }
     if (threadIdx.x == 0) {
         const double nres = sqrt(f[RES2]), nb = sqrt(f[B2]), nxd = sqrt(f[XDIST2]), nx = sqrt(f[X2]);
         const double nsd = sqrt(f[SDIST2]), nc = sqrt(f[C2]), cx = f[CX], bl = f[BLAM];
@@ -426,7 +517,7 @@ __global__ void __launch_bounds__(MAXNT, MFS_BATCH_MINB) k_batch(const BatchArgs
                 __syncthreads();
                 ++done;
                 if (a.tol > 0.0 && (done % a.check_every == 0 || done == a.iters)) {
-                    const double kkt = instance_residuals(a, I, xs, cp, ci, cv, rp, ri, rv,
+                    const double kkt = instance_residuals(a, I, xs, lam, cp, ci, cv, rp, ri, rv,
                                                           a.resid + (size_t)I.t * NSTAT, s_red, &s_kkt);
                     if (kkt <= a.tol) {
                         met = 1;
@@ -435,7 +526,8 @@ __global__ void __launch_bounds__(MAXNT, MFS_BATCH_MINB) k_batch(const BatchArgs
                 }
             }
         } else {
-            instance_residuals(a, I, xs, cp, ci, cv, rp, ri, rv, a.resid + (size_t)I.t * NSTAT, s_red, &s_kkt);
+            instance_residuals(a, I, xs, lam, cp, ci, cv, rp, ri, rv, a.resid + (size_t)I.t * NSTAT, s_red,
+                               &s_kkt);
         }
         __syncthreads();
         if (vec_sm && MODE == 0) {

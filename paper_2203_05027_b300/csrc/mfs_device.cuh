@@ -114,6 +114,24 @@ __device__ __forceinline__ double to_double(double a) {
 __device__ __forceinline__ double to_double(float a) {
     return double(a);
 }
+// pair helpers for reductions: maxima compare normalised pairs (hi first, then lo)
+__device__ __forceinline__ DF df_from(double d) {
+    const float h = (float)d;
+    return DF(h, (float)(d - (double)h));
+}
+__device__ __forceinline__ DF df_neg(const DF& a) {
+    return DF(-a.hi, -a.lo);
+}
+__device__ __forceinline__ DF df_abs(const DF& a) {
+    return a.hi < 0.f ? df_neg(a) : a;
+}
+__device__ __forceinline__ DF df_sq(const DF& a) {  // a^2, dropping lo^2 (relative 2^-48)
+    const float p = __fmul_rn(a.hi, a.hi);
+    return DF(p, __fmaf_rn(__fmul_rn(2.f, a.hi), a.lo, __fmaf_rn(a.hi, a.hi, -p)));
+}
+__device__ __forceinline__ DF df_max(const DF& a, const DF& b) {
+    return (a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo)) ? a : b;
+}
 
 __device__ __forceinline__ float shfl_up(float v, int d) {
     return __shfl_up_sync(FULL, v, d);

@@ -503,23 +503,6 @@ __device__ __forceinline__ void cta_fields_out(double (&f)[NFIELD], double (*sh)
 // B300 runs FP64 at 1/64 of its FP32 rate, and FP64 arithmetic per column or row was the larger
 // part of the residual kernels' time. Each lane folds its pairs into FP64 once, before the FP64
 // reductions over the CTA and the grid. Maxima compare normalised pairs (hi first, then lo).
-__device__ __forceinline__ DF df_from(double d) {
-    const float h = (float)d;
-    return DF(h, (float)(d - (double)h));
-}
-__device__ __forceinline__ DF df_neg(const DF& a) {
-    return DF(-a.hi, -a.lo);
-}
-__device__ __forceinline__ DF df_abs(const DF& a) {
-    return a.hi < 0.f ? df_neg(a) : a;
-}
-__device__ __forceinline__ DF df_sq(const DF& a) {  // a^2, dropping lo^2 (relative 2^-48)
-    const float p = __fmul_rn(a.hi, a.hi);
-    return DF(p, __fmaf_rn(__fmul_rn(2.f, a.hi), a.lo, __fmaf_rn(a.hi, a.hi, -p)));
-}
-__device__ __forceinline__ DF df_max(const DF& a, const DF& b) {
-    return (a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo)) ? a : b;
-}
 template <typename A>
 __device__ __forceinline__ A acc_from(double d);
 template <>

@@ -78,6 +78,25 @@ def test_batch_residuals_match_oracle():
             assert abs(res[t][k] - ov) <= 1e-9 * max(1.0, abs(ov)), (t, k, res[t][k], ov)
 
 
+def test_fp32_batch_residuals_match_the_oracle_at_the_same_point():
+    """The FP32 batch's residual fields (row and column terms summed and folded over the CTA as
+    double-float pairs, FP64 only in thread 0) against the oracle's FP64 residuals evaluated at the
+    batch's own (x, lambda) on the FP32-rounded data: the same point, so only the reduction
+    arithmetic differs (mixed LPs, an SOCP, empty rows and columns, an instance whose A stays in
+    global memory)."""
+    probs = mixed_instances()
+    bt = mfs.Batch(probs, precision="fp32")
+    bt.iterate(80)
+    res = bt.residuals()
+    for t, p in enumerate(probs):
+        sol = bt.solution(t)
+        orc = oracle.make_oracle(p, dtype=np.float32)
+        orc.set_state(x=sol["x"], lam=sol["lam"])
+        o = orc.residuals()
+        for k, ov in o.items():
+            assert abs(res[t][k] - ov) <= 1e-9 * max(1.0, abs(ov)), (t, k, res[t][k], ov)
+
+
 def test_batch_solve_to_tolerance():
     probs = [I.small_lp(s, m=20, n=50) for s in range(6)]
     bt = mfs.Batch(probs, precision="fp64", check_every=100)

@@ -395,7 +395,8 @@ __device__ __forceinline__ Inst load_inst(const BatchArgs<T>& a, int t) {
     return I;
 }
 
-// MODE 0: iterate (with termination checks when tol > 0); MODE 1: residuals only.
+// MODE 0: iterate with termination checks (tol > 0); MODE 1: residuals only; MODE 2: iterate
+// without checks (tol = 0; no residual code in the kernel, so none of its registers either).
 #ifndef MFS_BATCH_MINB
 #define MFS_BATCH_MINB 2  // 64 registers: two 512-thread CTAs per SM
 #endif
@@ -470,7 +471,7 @@ __global__ void __launch_bounds__(MAXNT, MFS_BATCH_MINB) k_batch(const BatchArgs
         T* lam = a.lam + I.gm;
         int done = 0;
         int met = 0;
-        if (MODE == 0) {
+        if (MODE != 1) {
             for (; done < a.iters;) {
                 // column sweep: x-step (eq. vvt), z-step and delta-update for orthant coordinates
                 for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
@@ -516,7 +517,7 @@ __global__ void __launch_bounds__(MAXNT, MFS_BATCH_MINB) k_batch(const BatchArgs
                 }
                 __syncthreads();
                 ++done;
-                if (a.tol > 0.0 && (done % a.check_every == 0 || done == a.iters)) {
+                if (MODE == 0 && a.tol > 0.0 && (done % a.check_every == 0 || done == a.iters)) {
                     const double kkt = instance_residuals(a, I, xs, lam, cp, ci, cv, rp, ri, rv,
                                                           a.resid + (size_t)I.t * NSTAT, s_red, &s_kkt);
                     if (kkt <= a.tol) {
@@ -530,11 +531,11 @@ __global__ void __launch_bounds__(MAXNT, MFS_BATCH_MINB) k_batch(const BatchArgs
                                &s_kkt);
         }
         __syncthreads();
-        if (vec_sm && MODE == 0) {
+        if (vec_sm && MODE != 1) {
             for (int j = threadIdx.x; j < I.n; j += blockDim.x) a.x[I.gn + j] = xs[j];
             for (int i = threadIdx.x; i < I.m; i += blockDim.x) a.v[I.gm + i] = vs[i];
         }
-        if (threadIdx.x == 0 && MODE == 0) {
+        if (threadIdx.x == 0 && MODE != 1) {
             a.iters_done[I.t] += done;
             a.status[I.t] = met ? 0 : 1;
         }
@@ -701,7 +702,7 @@ mfs_status run_batch(mfs_batch* s, Store<T>& st, int iters, double tol) {
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         mfs_status ms = MFS_OK;
         if (e == cudaSuccess) {
-            ms = launch_batch<T, 0>(s, st, iters, tol, cap);
+            ms = tol > 0.0 ? launch_batch<T, 0>(s, st, iters, tol, cap) : launch_batch<T, 2>(s, st, iters, tol, cap);
             e = cudaStreamEndCapture(cap, &g);
         }
         if (e == cudaSuccess && ms == MFS_OK) e = cudaGraphInstantiate(&s->graph, g, 0);
@@ -949,9 +950,11 @@ mfs_status mfs_batch_create(int64_t count, const int64_t* m, const int64_t* n, c
         e = cudaDeviceGetAttribute(&s->max_smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
     for (const void* f : {(const void*)k_batch<float, int, 0>, (const void*)k_batch<float, int, 1>,
-                          (const void*)k_batch<double, int, 0>, (const void*)k_batch<double, int, 1>,
+                          (const void*)k_batch<float, int, 2>, (const void*)k_batch<double, int, 0>,
+                          (const void*)k_batch<double, int, 1>, (const void*)k_batch<double, int, 2>,
                           (const void*)k_batch<float, uint16_t, 0>, (const void*)k_batch<float, uint16_t, 1>,
-                          (const void*)k_batch<double, uint16_t, 0>, (const void*)k_batch<double, uint16_t, 1>}) {
+                          (const void*)k_batch<float, uint16_t, 2>, (const void*)k_batch<double, uint16_t, 0>,
+                          (const void*)k_batch<double, uint16_t, 1>, (const void*)k_batch<double, uint16_t, 2>}) {
         cudaFuncAttributes fa;
         if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
         if (e == cudaSuccess) s->static_smem = std::max(s->static_smem, (int)fa.sharedSizeBytes);

@@ -92,7 +92,7 @@ constexpr int EPI_U = 6;       // epilogue items per thread in flight
 #define MFS_STG_PDL 1
 #endif
 #ifndef MFS_STG_ENT_PD
-#define MFS_STG_ENT_PD 4
+#define MFS_STG_ENT_PD 2
 #endif
 #ifndef MFS_STG_KEEP
 #define MFS_STG_KEEP 1  // the iterate's vectors read and written by the staged passes carry an L2
